@@ -1,0 +1,328 @@
+#!/usr/bin/env python3
+"""Benchmark: randomized PCA of a tall float32 matrix on one GB300 (or N replicas).
+
+Workload (the throughput configuration of the tall-skinny PCA setting):
+A is 200000 x 1000 float32, A = U diag(sigma) V^T with Haar factors and
+sigma_i = |1/i + 1e-3 xi_i|, centred columns; k = 50, p = 10, q = 2, seeded
+Gaussian Omega (1000 x 60) given as input.  One step = one full rsvd() solve
+(centring, sketch, q re-orthonormalised power iterations, Rayleigh-Ritz, small
+SVD, Ritz vectors) through the C ABI.  A (0.8 GB) is larger than L2 (129 MB),
+so no L2 flush is needed between steps.
+
+Metric: rSVD GFLOP/s = algorithmic FLOPs per solve x solves / device time,
+with the FLOP count of the paper's randomized PCA step list (Sec. 3.1.2) in the
+2-flop multiply-add convention:
+    F = 2mnl(2q+2) + 2ml^2(q+1) + 2ml^2 + 2nl^2.
+
+``--impl reference`` times the FP64 CPU oracle (the only reference this
+project has) on the host cores on a bounded row sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "rpca_fp32_200000x1000"
+SMS, FP32_LANES = 152, 128
+
+
+def alg_flops(m, n, k, p, q):
+    l = k + p
+    return 2.0 * m * n * l * (2 * q + 2) + 2.0 * m * l * l * (q + 1) + 2.0 * m * l * l + 2.0 * n * l * l
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except Exception:
+                self.proc.kill()
+        sm = []
+        mx = None
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_for(kernel_src: str, kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        e = rec[kernel]
+        with open(os.path.join(ROOT, "paper_1906_12085_gb300", "csrc", kernel_src), "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()[:16]
+        if e.get("source_sha256_16") != h or e.get("workload") != WORKLOAD:
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def oracle_sample(A_host32, Om32, k, q, rows):
+    """Time the FP64 oracle on the first `rows` rows (centred) of the workload matrix."""
+    import numpy as np
+
+    import oracle
+    a = np.ascontiguousarray(A_host32[:rows].astype(np.float64))
+    om = Om32.astype(np.float64)
+    t0 = time.perf_counter()
+    ac, mu, fro2 = oracle.center(a)
+    oracle.rsvd(ac, om, q=q, k=k)
+    return time.perf_counter() - t0
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np
+    import torch
+
+    import synth
+    w = synth.WORKLOADS[WORKLOAD]
+    m, n, k, p, q = w["m"], w["n"], w["k"], w["p"], w["q"]
+    rows = args.sample_rows
+    # the sample: the first `rows` rows of the same recipe (same n, k, p, q and Omega)
+    A, sigma, extras = synth.workload(WORKLOAD, m=rows)
+    A32 = A.float().numpy()
+    Om = extras["omega"].numpy()
+    flops = alg_flops(rows, n, k, p, q)
+    for _ in range(args.warmup):
+        oracle_sample(A32, Om, k, q, rows)
+    ts = [oracle_sample(A32, Om, k, q, rows) for _ in range(args.steps)]
+    total = sum(ts)
+    val = flops * len(ts) / total / 1e9
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": "rSVD GFLOP/s", "value": val, "unit": "GFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(ts), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": m, "n": n, "k": k, "p": p, "q": q, "sample_rows": rows},
+        "cpu_baseline": {"value": val, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": f"first {rows} of {m} rows (same n, k, p, q, Omega); FP64 C oracle, OpenMP"},
+        "e2e": {"value": val, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    del np, torch, sigma
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1906_12085_gb300 as g
+    import synth
+    from paper_1906_12085_gb300 import build as gbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    gbuild.build()
+
+    w = synth.WORKLOADS[WORKLOAD]
+    m, n, k, p, q = w["m"], w["n"], w["k"], w["p"], w["q"]
+    l = k + p
+    A64, sigma, extras = synth.workload(WORKLOAD, device=dev)
+    A0 = A64.float().contiguous()           # pristine copy (inputs are re-centred in place each step)
+    del A64
+    Om = extras["omega"].to(dev).contiguous()
+    A = A0.clone()
+    S = torch.zeros(k, dtype=torch.float64, device=dev)
+    U = torch.zeros(m, k, dtype=torch.float32, device=dev)
+    V = torch.zeros(n, k, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    plan = g.rsvd_plan_create(m, n, k, p, q, g.RSVD_F32, stream)
+
+    def step():
+        g.check(g.rsvd(plan, A, None, Om, S, U, V), "rsvd")
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    g.check(g.rsvd_plan_sync(plan), "warm-up solve status")
+    g.rsvd_plan_profile(plan, True)
+    g.rsvd_plan_profile_read(plan)  # clear
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    sampler.start()
+    launches0 = g.rsvd_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    launches = g.rsvd_launch_count() - launches0
+    ms = e0.elapsed_time(e1)
+    clocks = sampler.stop()
+    prof = g.rsvd_plan_profile_read(plan)
+    g.rsvd_plan_profile(plan, False)
+    st = g.rsvd_plan_sync(plan)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    ms_max = float(t.item())
+    flops = alg_flops(m, n, k, p, q)
+    value = world * flops * args.steps / (ms_max * 1e-3) / 1e9
+
+    # dominant kernel group and its roofline (float32 products on CUDA cores: ALU-bound)
+    pk, src = peaks()
+    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    alu_peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
+    ax_ms, ax_n = prof["ax"]
+    atx_ms, atx_n = prof["atx"]
+    if ax_ms >= atx_ms:
+        dom, dom_ms, dom_n, dom_src, dom_kernel = "gemm_nn (Y = A Z)", ax_ms, ax_n, "k_gemm.cu", "gemm_nn_kernel"
+    else:
+        dom, dom_ms, dom_n, dom_src, dom_kernel = "gemm_tn (Z = A^T Q)", atx_ms, atx_n, "k_gemm.cu", "gemm_tn_kernel"
+    per_launch_flops = 2.0 * m * n * l
+    achieved = per_launch_flops / (dom_ms / dom_n * 1e-3) / 1e12 if dom_n else None
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": (achieved / alu_peak) if achieved else None,
+                "traffic": traffic_for(dom_src, dom_kernel),
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (unit counts and max clock)",
+                "stage_ms_per_step": {kk: vv[0] / args.steps for kk, vv in prof.items()}}
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if rank == 0 or world > 1:
+        Ah = A0.cpu().pin_memory()
+        Omh = Om.cpu().pin_memory()
+        Sh = torch.empty_like(S, device="cpu").pin_memory()
+        Uh = torch.empty_like(U, device="cpu").pin_memory()
+        Vh = torch.empty_like(V, device="cpu").pin_memory()
+        n_e2e = max(1, min(args.steps, 10))
+        torch.cuda.synchronize(dev)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(n_e2e):
+            A.copy_(Ah, non_blocking=True)
+            Om.copy_(Omh, non_blocking=True)
+            step()
+            Sh.copy_(S, non_blocking=True)
+            Uh.copy_(U, non_blocking=True)
+            Vh.copy_(V, non_blocking=True)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        ems = f0.elapsed_time(f1)
+        e2e = {"value": flops * n_e2e / (ems * 1e-3) / 1e9, "unit": "GFLOP/s",
+               "h2d_bytes_per_step": Ah.numel() * 4 + Omh.numel() * 4,
+               "d2h_bytes_per_step": Sh.numel() * 8 + Uh.numel() * 4 + Vh.numel() * 4,
+               "ms_per_step": ems / n_e2e}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rows = args.cpu_baseline_rows
+        Ah32 = A0[:rows].cpu().numpy()
+        tsec = oracle_sample(Ah32, Om.cpu().numpy(), k, q, rows)
+        cpu = {"value": alg_flops(rows, n, k, p, q) / tsec / 1e9, "unit": "GFLOP/s", "cores": os.cpu_count(),
+               "kind": "oracle",
+               "sample": f"first {rows} of {m} rows (same n, k, p, q, Omega); FP64 C oracle, OpenMP, one solve"}
+
+    if rank == 0:
+        line = {
+            "metric": "rSVD GFLOP/s", "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "m": m, "n": n, "k": k, "p": p, "q": q,
+                       "l2": "inputs larger than L2 (A is 0.8 GB), no flush",
+                       "parallelism": f"replicas{world}"},
+            "solves_per_s": world * args.steps / (ms_max * 1e-3),
+            "status": st,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clocks, "peaks_source": src,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--sample-rows", type=int, default=40000, help="rows per reference-arm step")
+    ap.add_argument("--cpu-baseline-rows", type=int, default=100000, help="rows of the cpu_baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,180 @@
+/*
+ * gb300-rsvd: truncated, randomized and exact SVD / PCA of tall zero-mean
+ * matrices (m >> n) on one GB300 GPU (sm_103a), after the methods compared in
+ * arXiv:1906.12085 ("Tutorial: Complexity analysis of Singular Value
+ * Decomposition and its variants").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Matrices are ROW-MAJOR and dense; a row is one example (Sec. 2.2, the
+ *   "each row of A represents an example" case).  A is m x n with m >= n.
+ * - Every matrix / vector pointer is a caller-owned DEVICE pointer unless a
+ *   parameter says otherwise.  The plan owns only its workspace.
+ * - Calls are asynchronous on the plan's CUDA stream (the stream passed to
+ *   rsvd_plan_create; NULL means the legacy default stream).  Argument errors
+ *   are returned immediately; numerical conditions found on the device
+ *   (Cholesky breakdown, Jacobi non-convergence, K > k) are accumulated in a
+ *   device status word that rsvd_plan_sync() and pca_threshold() return.
+ * - Element types follow the plan's dtype:
+ *     RSVD_F64 : A, Omega, U, V are double;
+ *     RSVD_F32 : A, Omega, U, V are float;
+ *   singular values S are always double.
+ * - Outputs are sorted by descending singular value.  Sign convention: the
+ *   largest-magnitude entry of every right singular vector v_i is positive
+ *   (u_i is flipped with it).
+ * - Centring: by default every solve first centres A IN PLACE (A <- A - 1 mu^T,
+ *   Sec. 1 assumption that each feature has zero mean) and records
+ *   ||A||_F^2 of the centred matrix (Eq. sumeigen).  RSVD_FLAG_NO_CENTER
+ *   skips the subtraction (A is taken as already centred) but still records
+ *   ||A||_F^2.
+ * - Plans are not thread-safe: one plan serves one solve at a time.
+ */
+#ifndef GB300_RSVD_H
+#define GB300_RSVD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RSVD_F64 = 0,      /* float64 storage and arithmetic                       */
+    RSVD_F32 = 1,      /* float32 storage, float32 products with float32 sums   */
+    RSVD_BF16 = 2,     /* reserved: bfloat16 storage (precision form)           */
+    RSVD_FP8_E4M3 = 3  /* reserved: e4m3 storage with per-column scales         */
+} rsvd_dtype;
+
+typedef enum {
+    RSVD_OK = 0,
+    RSVD_ERR_ARG = -1,          /* invalid argument (sizes, NULL pointers, method)     */
+    RSVD_ERR_OOM = -2,          /* device workspace allocation failed                  */
+    RSVD_ERR_CHOL = -3,         /* Cholesky breakdown even after the shifted retry     */
+    RSVD_ERR_NOCONV = -4,       /* a Jacobi solver hit its sweep cap                   */
+    RSVD_ERR_TIMEOUT = -5,      /* reserved for bounded device waits                   */
+    RSVD_ERR_CUDA = -6,         /* a CUDA runtime call or kernel launch failed         */
+    RSVD_ERR_UNSUPPORTED = -8,  /* size or dtype outside what this build implements    */
+    RSVD_WARN_K_GT_k = 1        /* the threshold t is not reached within the k values  */
+} rsvd_status;
+
+/* svd_exact methods */
+enum {
+    RSVD_EXACT_GRAM = 0,        /* Sec. 2.3 / 3.1.3: A^T A, eigen-decomposition, u_i = A v_i / sigma_i */
+    RSVD_EXACT_QR_JACOBI = 1    /* A = QR (CholeskyQR2), one-sided Jacobi SVD of R, U = Q U_R        */
+};
+
+/* plan flags */
+enum { RSVD_FLAG_NO_CENTER = 1 };
+
+typedef struct rsvd_plan *rsvd_plan_t;
+
+/*
+ * Create a plan for m x n matrices (m >= n >= 1), target rank k, oversampling
+ * p (sketch width l = k + p <= n) and q power iterations (Sec. 3.1.2: l is the
+ * width of G, q plays the role of i).  The plan allocates its device
+ * workspace once (cudaMalloc) and launches everything on `cuda_stream`
+ * (a cudaStream_t, may be NULL).  For svd_exact the plan needs n <= 112 (the
+ * n x n eigen / SVD problem is solved in one CTA's shared memory); for rsvd
+ * l <= 112.  Returns RSVD_ERR_ARG on inconsistent sizes, RSVD_ERR_UNSUPPORTED
+ * for a dtype this build does not implement, RSVD_ERR_OOM if the workspace
+ * cannot be allocated.  On error *plan is set to NULL.
+ */
+rsvd_status rsvd_plan_create(rsvd_plan_t *plan, int64_t m, int64_t n, int k, int p, int q,
+                             rsvd_dtype dtype, void *cuda_stream);
+
+/* Free the plan and its workspace (synchronises the plan's stream first). NULL is a no-op. */
+rsvd_status rsvd_plan_destroy(rsvd_plan_t plan);
+
+/* Bytes of device workspace owned by the plan (used for HBM admission). 0 for NULL. */
+size_t rsvd_plan_workspace_bytes(rsvd_plan_t plan);
+
+/* Set RSVD_FLAG_* bits for subsequent solves. */
+rsvd_status rsvd_plan_set_flags(rsvd_plan_t plan, unsigned flags);
+
+/* Wait for the plan's stream; return the device status of the last solve
+ * (RSVD_OK, RSVD_ERR_CHOL, RSVD_ERR_NOCONV, or RSVD_ERR_CUDA) and clear it. */
+rsvd_status rsvd_plan_sync(rsvd_plan_t plan);
+
+/*
+ * Randomized PCA (Sec. 3.1.2, steps 2-7, with the power step re-orthonormalised
+ * after each half step):
+ *   Y = A Omega;  Q = orth(Y);
+ *   repeat q times: Z = A^T Q, Q_Z = orth(Z), Y = A Q_Z, Q = orth(Y);
+ *   T = A^T Q (= B^T with B = Q^T A);  T = Vt Sigma W^T;  U = Q W.
+ * orth() is CholeskyQR2 (R_ii > 0), which in exact arithmetic equals the
+ * Householder QR the step list names.
+ *   A      : m x n, row-major, centred in place unless RSVD_FLAG_NO_CENTER.
+ *   col_scales : must be NULL for RSVD_F32 / RSVD_F64 (reserved for e4m3).
+ *   Omega  : n x l Gaussian test matrix (caller-drawn), row-major.
+ *   S      : k doubles; U : m x k; V : n x k (row-major).
+ */
+rsvd_status rsvd(rsvd_plan_t plan, void *A, const float *col_scales, const void *Omega,
+                 double *S, void *U, void *V);
+
+/*
+ * All n singular triplets of A (Sec. 2.1 definition).
+ *   method RSVD_EXACT_GRAM: the paper's "Truncated SVD" route (Sec. 2.3 and the
+ *     step list of Sec. 3.1.3): G = A^T A, cyclic Jacobi eigen-decomposition,
+ *     sigma_i = sqrt(lambda_i), u_i = A v_i / sigma_i (columns with
+ *     sigma_i <= n * eps * sigma_1 are returned as zero vectors).
+ *   method RSVD_EXACT_QR_JACOBI: A = Q R by CholeskyQR2, R = U_R Sigma V^T by
+ *     one-sided Jacobi, U = Q U_R (backward stable; no squaring of cond(A)).
+ *   S : n doubles; U : m x n; V : n x n.  Requires n <= 112 and dtype RSVD_F64
+ *   or RSVD_F32.
+ */
+rsvd_status svd_exact(rsvd_plan_t plan, void *A, int method, double *S, void *U, void *V);
+
+/*
+ * Truncated SVD by Golub-Kahan-Lanczos bidiagonalisation with full
+ * reorthogonalisation (classical Gram-Schmidt twice) for `steps` steps from
+ * the unit start vector v1 (n floats for RSVD_F32, n doubles for RSVD_F64),
+ * then the SVD of the steps x steps bidiagonal; returns the leading k Ritz
+ * triplets.  S : k doubles; U : m x k; V : n x k.  Requires k <= steps <= n.
+ * Returns RSVD_ERR_UNSUPPORTED until the Lanczos kernels are built.
+ */
+rsvd_status svd_truncated_krylov(rsvd_plan_t plan, void *A, const void *v1, int steps,
+                                 double *S, void *U, void *V);
+
+/*
+ * Sec. 2.4 cumulative explained variance: the minimal K with
+ *   sum_{i<=K} sigma_i^2 >= t * ||A||_F^2
+ * over the singular values of the plan's last solve, with the denominator
+ * from Eq. (sumeigen).  Synchronises the stream and writes K to the HOST int
+ * *K.  If the values returned by the last solve do not reach t, *K is their
+ * count and the result is RSVD_WARN_K_GT_k.  t must lie in (0, 1].
+ */
+rsvd_status pca_threshold(rsvd_plan_t plan, double t, int *K);
+
+/* Host copy of ||A||_F^2 (after centring) recorded by the last solve; synchronises. */
+rsvd_status rsvd_plan_fro2(rsvd_plan_t plan, double *fro2);
+
+/*
+ * Tracing: per-stage CUDA-event timing.  When enabled, the plan records a
+ * pair of events on its stream around every kernel group of a stage; the
+ * read call synchronises the stream, writes the summed milliseconds and the
+ * number of timed groups per stage (arrays of `nstages` entries, host
+ * memory) since the previous read, and clears them.  Stages:
+ */
+enum {
+    RSVD_STAGE_CENTER = 0,  /* column means, centring, ||A||_F^2                      */
+    RSVD_STAGE_AX = 1,      /* products A X with X skinny (sketch, power step, U)     */
+    RSVD_STAGE_ATX = 2,     /* products A^T X (power step, T = A^T Q, Gram of A)      */
+    RSVD_STAGE_ORTH = 3,    /* CholeskyQR2 of the m-row and n-row blocks              */
+    RSVD_STAGE_SMALL = 4,   /* small SVD / eigen problems (Jacobi), K selection       */
+    RSVD_STAGE_FINISH = 5,  /* Ritz vectors, sign convention, output copies           */
+    RSVD_STAGE_COUNT = 6
+};
+rsvd_status rsvd_plan_profile(rsvd_plan_t plan, int enable);
+rsvd_status rsvd_plan_profile_read(rsvd_plan_t plan, double *ms, int *groups, int nstages);
+
+/* Process-wide number of kernels this library has launched (all plans). */
+uint64_t rsvd_launch_count(void);
+
+/* Static description of a status code. */
+const char *rsvd_status_string(rsvd_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB300_RSVD_H */

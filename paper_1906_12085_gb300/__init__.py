@@ -1,0 +1,221 @@
+"""gb300-rsvd: tall-skinny SVD / PCA on one GB300 (sm_103a), after arXiv:1906.12085.
+
+Thin ctypes binding over the C ABI of ``include/rsvd.h``.  The functions keep
+the C names and argument order; tensors are passed as device pointers
+(``tensor.data_ptr()``) and the CUDA stream defaults to torch's current
+stream.  PyTorch is used only to own device memory and streams: every step
+of every solve runs in the kernels of ``libgb300rsvd.so``.  If the library
+has not been built, importing the binding's functions raises; there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+__all__ = [
+    "RSVD_F64", "RSVD_F32", "RSVD_BF16", "RSVD_FP8_E4M3",
+    "RSVD_OK", "RSVD_ERR_ARG", "RSVD_ERR_OOM", "RSVD_ERR_CHOL", "RSVD_ERR_NOCONV", "RSVD_ERR_TIMEOUT",
+    "RSVD_ERR_CUDA", "RSVD_ERR_UNSUPPORTED", "RSVD_WARN_K_GT_k", "RSVD_EXACT_GRAM", "RSVD_EXACT_QR_JACOBI",
+    "RSVD_FLAG_NO_CENTER", "RsvdError", "lib", "library_path", "header_functions",
+    "rsvd_plan_create", "rsvd_plan_destroy", "rsvd_plan_workspace_bytes", "rsvd_plan_set_flags",
+    "rsvd_plan_sync", "rsvd", "svd_exact", "svd_truncated_krylov", "pca_threshold", "rsvd_plan_fro2",
+    "rsvd_status_string", "check", "rsvd_plan_profile", "rsvd_plan_profile_read", "rsvd_launch_count",
+    "STAGES",
+]
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+HEADER = os.path.join(ROOT, "include", "rsvd.h")
+
+RSVD_F64, RSVD_F32, RSVD_BF16, RSVD_FP8_E4M3 = 0, 1, 2, 3
+RSVD_OK, RSVD_ERR_ARG, RSVD_ERR_OOM, RSVD_ERR_CHOL, RSVD_ERR_NOCONV = 0, -1, -2, -3, -4
+RSVD_ERR_TIMEOUT, RSVD_ERR_CUDA, RSVD_ERR_UNSUPPORTED, RSVD_WARN_K_GT_k = -5, -6, -8, 1
+RSVD_EXACT_GRAM, RSVD_EXACT_QR_JACOBI = 0, 1
+RSVD_FLAG_NO_CENTER = 1
+# tracing stages (RSVD_STAGE_* in include/rsvd.h)
+STAGES = ("center", "ax", "atx", "orth", "small", "finish")
+
+
+class RsvdError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        super().__init__(f"{what}: status {status} ({rsvd_status_string(status)})")
+        self.status = status
+
+
+def library_path() -> str:
+    return os.path.join(HERE, "libgb300rsvd.so")
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libgb300rsvd.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1906_12085_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    i64, i32, vp, dp = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+    L.rsvd_plan_create.argtypes = [ctypes.POINTER(vp), i64, i64, i32, i32, i32, i32, vp]
+    L.rsvd_plan_destroy.argtypes = [vp]
+    L.rsvd_plan_workspace_bytes.argtypes = [vp]
+    L.rsvd_plan_workspace_bytes.restype = ctypes.c_size_t
+    L.rsvd_plan_set_flags.argtypes = [vp, ctypes.c_uint]
+    L.rsvd_plan_sync.argtypes = [vp]
+    L.rsvd.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    L.svd_exact.argtypes = [vp, vp, i32, vp, vp, vp]
+    L.svd_truncated_krylov.argtypes = [vp, vp, vp, i32, vp, vp, vp]
+    L.pca_threshold.argtypes = [vp, ctypes.c_double, ctypes.POINTER(i32)]
+    L.rsvd_plan_fro2.argtypes = [vp, dp]
+    L.rsvd_plan_profile.argtypes = [vp, i32]
+    L.rsvd_plan_profile_read.argtypes = [vp, dp, ctypes.POINTER(i32), i32]
+    L.rsvd_launch_count.argtypes = []
+    L.rsvd_launch_count.restype = ctypes.c_uint64
+    L.rsvd_status_string.argtypes = [i32]
+    L.rsvd_status_string.restype = ctypes.c_char_p
+    for f in ("rsvd_plan_create", "rsvd_plan_destroy", "rsvd_plan_set_flags", "rsvd_plan_sync", "rsvd",
+              "svd_exact", "svd_truncated_krylov", "pca_threshold", "rsvd_plan_fro2", "rsvd_plan_profile",
+              "rsvd_plan_profile_read"):
+        getattr(L, f).restype = i32
+    _lib = L
+    return L
+
+
+def header_functions() -> list[str]:
+    """Names of the functions include/rsvd.h declares."""
+    with open(HEADER) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b([a-z_][a-z0-9_]*)\s*\(", text)) -
+                  {"if", "while", "for", "sizeof", "return", "defined"})
+
+
+def rsvd_status_string(status: int) -> str:
+    try:
+        return lib().rsvd_status_string(int(status)).decode()
+    except Exception:  # message formatting must not mask the original error
+        return "?"
+
+
+def check(status: int, what: str = "call", allow=(RSVD_OK,)) -> int:
+    if status not in allow:
+        raise RsvdError(status, what)
+    return status
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_contiguous():
+        raise ValueError("tensors must be contiguous (row-major)")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Plan:
+    """Owning handle of an rsvd_plan_t (destroyed on close / garbage collection)."""
+
+    def __init__(self, handle: int, m, n, k, p, q, dtype):
+        self.handle = handle
+        self.m, self.n, self.k, self.p, self.q, self.dtype = m, n, k, p, q, dtype
+
+    @property
+    def l(self):
+        return self.k + self.p
+
+    def close(self):
+        if self.handle:
+            lib().rsvd_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def rsvd_plan_create(m: int, n: int, k: int, p: int, q: int, dtype: int = RSVD_F32, stream=None) -> Plan:
+    h = ctypes.c_void_p()
+    st = lib().rsvd_plan_create(ctypes.byref(h), m, n, k, p, q, dtype, _stream(stream))
+    check(st, "rsvd_plan_create")
+    return Plan(h.value, m, n, k, p, q, dtype)
+
+
+def rsvd_plan_destroy(plan: Plan) -> int:
+    plan.close()
+    return RSVD_OK
+
+
+def rsvd_plan_workspace_bytes(plan: Plan) -> int:
+    return int(lib().rsvd_plan_workspace_bytes(plan.handle))
+
+
+def rsvd_plan_set_flags(plan: Plan, flags: int) -> int:
+    return lib().rsvd_plan_set_flags(plan.handle, flags)
+
+
+def rsvd_plan_sync(plan: Plan) -> int:
+    return lib().rsvd_plan_sync(plan.handle)
+
+
+def rsvd(plan: Plan, A, col_scales, Omega, S, U, V) -> int:
+    return lib().rsvd(plan.handle, _ptr(A), _ptr(col_scales), _ptr(Omega), _ptr(S), _ptr(U), _ptr(V))
+
+
+def svd_exact(plan: Plan, A, method: int, S, U, V) -> int:
+    return lib().svd_exact(plan.handle, _ptr(A), int(method), _ptr(S), _ptr(U), _ptr(V))
+
+
+def svd_truncated_krylov(plan: Plan, A, v1, steps: int, S, U, V) -> int:
+    return lib().svd_truncated_krylov(plan.handle, _ptr(A), _ptr(v1), int(steps), _ptr(S), _ptr(U), _ptr(V))
+
+
+def pca_threshold(plan: Plan, t: float) -> tuple[int, int]:
+    K = ctypes.c_int(0)
+    st = lib().pca_threshold(plan.handle, float(t), ctypes.byref(K))
+    return st, int(K.value)
+
+
+def rsvd_plan_fro2(plan: Plan) -> float:
+    f = ctypes.c_double(0.0)
+    check(lib().rsvd_plan_fro2(plan.handle, ctypes.byref(f)), "rsvd_plan_fro2")
+    return f.value
+
+
+def rsvd_plan_profile(plan: Plan, enable: bool) -> int:
+    return lib().rsvd_plan_profile(plan.handle, 1 if enable else 0)
+
+
+def rsvd_plan_profile_read(plan: Plan) -> dict:
+    """Per-stage {name: (milliseconds, groups)} since the previous read (synchronises)."""
+    n = len(STAGES)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int * n)()
+    check(lib().rsvd_plan_profile_read(plan.handle, ms, cnt, n), "rsvd_plan_profile_read")
+    return {STAGES[i]: (ms[i], cnt[i]) for i in range(n)}
+
+
+def rsvd_launch_count() -> int:
+    return int(lib().rsvd_launch_count())

@@ -1,0 +1,98 @@
+// Internal declarations shared by the CUDA translation units of gb300-rsvd.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rsvd.h"
+
+namespace gbr {
+
+// Bits of the device status word (OR-ed by kernels, read by rsvd_plan_sync).
+enum StatusBits : int {
+    ST_CHOL = 1,      // Cholesky breakdown after the shifted retry
+    ST_NOCONV = 2,    // Jacobi sweep cap reached
+    ST_SHIFT = 4,     // shifted Cholesky was needed (informational)
+    ST_RANKDEF = 8,   // a singular value fell below n*eps*sigma_1 (informational)
+};
+
+// Largest l (or n for svd_exact) whose l x l working set fits one CTA's shared memory.
+constexpr int kSmallMaxF64 = 112;
+
+// Count of kernel launches issued by the library (reported by rsvd_launch_count).
+void note_launch(int count = 1);
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
+
+// ---------------------------------------------------------------- centring
+// mu = column means of A (m x n, ld), A <- A - 1 mu^T, *fro2 = ||A||_F^2 (float64).
+// part: scratch of centre_partials(m, n) doubles.
+template <typename T>
+cudaError_t center_columns(T *A, int64_t m, int64_t n, int64_t lda, bool subtract, double *mu,
+                           double *fro2, double *part, cudaStream_t s);
+int64_t center_partials(int64_t m, int64_t n);
+
+// ---------------------------------------------------------------- products
+// C (M x N) = A (M x K) * B (K x N); all row-major with leading dimensions.
+template <typename T>
+cudaError_t gemm_nn(int64_t M, int64_t N, int64_t K, const T *A, int64_t lda, const T *B, int64_t ldb,
+                    T *C, int64_t ldc, cudaStream_t s);
+
+// C (N x L) = A^T B with A rows x N (lda) and B rows x L (ldb): split over row
+// chunks into `part`, then summed in chunk order (deterministic).
+template <typename T>
+cudaError_t gemm_tn(int64_t rows, int64_t N, int64_t L, const T *A, int64_t lda, const T *B, int64_t ldb,
+                    T *C, int64_t ldc, T *part, int64_t part_elems, cudaStream_t s);
+// scratch elements gemm_tn needs for these sizes
+int64_t gemm_tn_partials(int64_t rows, int64_t N, int64_t L);
+
+// ---------------------------------------------------------- small dense
+// Upper Cholesky R^T R = G (+ shift) of the leading l x l block of G (ldg), then
+// R^{-1}.  Writes R, Rinv (float64, l x l dense, ld l) and Rinv_c (element type
+// Tc, lp x lp, zero padded).  On a non-positive pivot retries once with the
+// shift 11 (rows*l + l(l+1)) u tr(G) (shifted CholeskyQR); on a second
+// breakdown sets ST_CHOL and returns the identity.
+template <typename TG, typename Tc>
+cudaError_t chol_inv(const TG *G, int64_t ldg, int l, int64_t rows, double unit_roundoff, double *R,
+                     double *Rinv, Tc *Rinv_c, int lp, int *status, cudaStream_t s);
+
+// R = R2 * R1 for upper-triangular l x l float64 matrices (ld l).
+cudaError_t trmm_upper(const double *R2, const double *R1, double *R, int l, cudaStream_t s);
+
+// One-sided Jacobi SVD of the l x l float64 matrix R (ld l), arithmetic in Ta:
+// R W = U_R diag(sig).  Outputs sorted descending: sig (l doubles), U_R and W
+// in element type To (lp x lp, zero padded, ld lp).
+template <typename Ta, typename To>
+cudaError_t jacobi_osvd(const double *R, int l, int lp, double *sig, To *UR, To *W, int *status,
+                        cudaStream_t s);
+
+// Cyclic (parallel-ordered) two-sided Jacobi eigen-decomposition of the n x n
+// symmetric float64 matrix G (ld n): lam descending (n doubles), V (n x n, ld n).
+cudaError_t jacobi_eig(const double *G, int n, double *lam, double *V, int *status, cudaStream_t s);
+
+// Vs[:, i] = V[:, i] / sigma_i (zero column when sigma_i <= n eps sigma_1), sigma_i = sqrt(max(lam_i,0)).
+template <typename T>
+cudaError_t gram_finish(const double *lam, const double *V, int n, double *sig, T *Vs, int *status,
+                        cudaStream_t s);
+
+// For each column j < cols of Vt (rows x cols, ld): if its largest-|entry|
+// (first one) is negative, negate that column of Vt and of W (wrows, ldw).
+template <typename T>
+cudaError_t sign_normalize(T *Vt, int64_t rows, int cols, int64_t ldv, T *W, int64_t wrows, int64_t ldw,
+                           cudaStream_t s);
+
+// dst[r * ldd + c] = src[r * lds + c] for r < rows, c < cols; zero for cols <= c < cols_pad.
+template <typename Ts, typename Td>
+cudaError_t copy2d(const Ts *src, int64_t lds, Td *dst, int64_t ldd, int64_t rows, int64_t cols,
+                   int64_t cols_pad, cudaStream_t s);
+
+// dst[i] = src[i] for i < count (float64)
+cudaError_t copy_f64(const double *src, double *dst, int64_t count, cudaStream_t s);
+
+// K selection (Sec. 2.4 with Eq. sumeigen): *K = minimal count with
+// sum sigma_i^2 >= t * fro2; *reached = 0 if not reached within count.
+cudaError_t pca_select(const double *sigma, int count, const double *fro2, double t, int *K, int *reached,
+                       cudaStream_t s);
+
+}  // namespace gbr

@@ -1,0 +1,445 @@
+// Plan object, solver sequencing and the C ABI declared in include/rsvd.h.
+//
+// Every step of every solve is a kernel of this library launched on the
+// plan's stream; the host only sequences launches and reads back status / K.
+#include <cuda_runtime.h>
+#include <float.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace gbr;
+
+namespace {
+std::atomic<uint64_t> g_launches{0};
+}
+void gbr::note_launch(int count) { g_launches.fetch_add((uint64_t)count, std::memory_order_relaxed); }
+
+struct rsvd_plan {
+    int64_t m = 0, n = 0;
+    int k = 0, p = 0, q = 0, l = 0, lp = 0;  // lp: l padded to a multiple of 16 (zero columns)
+    int nx = 0;                              // n if svd_exact is supported (n <= kSmallMaxF64), else 0
+    int wide = 0;                            // width of the m-row work buffers
+    rsvd_dtype dtype = RSVD_F32;
+    cudaStream_t stream = nullptr;
+    unsigned flags = 0;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    // carved workspace
+    double *mu = nullptr, *fro2 = nullptr, *cpart = nullptr;
+    void *Y = nullptr, *Qb = nullptr, *Tmp = nullptr;   // m x wide
+    void *Ob = nullptr, *Z = nullptr, *Qz = nullptr, *Tn = nullptr, *Vt = nullptr, *Tmpn = nullptr;  // n x max(lp, nx)
+    void *part = nullptr;
+    int64_t part_elems = 0;
+    void *G = nullptr, *Rinv_c = nullptr, *UR = nullptr, *Wm = nullptr;  // s x s, s = max(lp, nx)
+    double *G64 = nullptr, *R1 = nullptr, *R1i = nullptr, *R2 = nullptr, *R2i = nullptr, *Rt = nullptr;
+    double *lam = nullptr, *Vfull = nullptr, *sig = nullptr;
+    int *status = nullptr, *Kdev = nullptr;
+    int last_count = 0;
+    // tracing: event pairs recorded around stage groups while profiling is on
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> ev_stage;
+    size_t ev_used = 0;
+};
+
+namespace {
+
+size_t esize(rsvd_dtype d) { return d == RSVD_F64 ? 8 : 4; }
+
+struct Carver {
+    size_t off = 0;
+    char *base = nullptr;
+    void *take(size_t bytes) {
+        off = (off + 255) & ~(size_t)255;
+        void *p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    }
+};
+
+void carve(rsvd_plan *P, Carver &c) {
+    const size_t es = esize(P->dtype);
+    const int64_t m = P->m, n = P->n;
+    const int64_t sq = P->lp > P->nx ? P->lp : P->nx;   // small square side
+    const int64_t nw = sq;                               // width of the n-row buffers
+    P->mu = (double *)c.take(sizeof(double) * n);
+    P->fro2 = (double *)c.take(sizeof(double));
+    P->cpart = (double *)c.take(sizeof(double) * center_partials(m, n));
+    P->Y = c.take(es * m * P->wide);
+    P->Qb = c.take(es * m * P->wide);
+    P->Tmp = c.take(es * m * P->wide);
+    P->Ob = c.take(es * n * nw);
+    P->Z = c.take(es * n * nw);
+    P->Qz = c.take(es * n * nw);
+    P->Tn = c.take(es * n * nw);
+    P->Vt = c.take(es * n * nw);
+    P->Tmpn = c.take(es * n * nw);
+    // split-K scratch: the largest of the products the solvers issue
+    int64_t pe = 0;
+    auto upd = [&](int64_t rows, int64_t N, int64_t L) {
+        const int64_t e = gemm_tn_partials(rows, N, L);
+        if (e > pe) pe = e;
+    };
+    upd(m, n, P->lp);          // Z = A^T Q, T = A^T Q
+    upd(m, P->lp, P->lp);      // Gram of Y
+    upd(n, P->lp, P->lp);      // Gram of Z, T
+    if (P->nx) {
+        upd(m, P->nx, P->nx);  // A^T A and Gram of A
+    }
+    P->part_elems = pe;
+    P->part = c.take(es * (pe > 0 ? pe : 1));
+    P->G = c.take(es * sq * sq);
+    P->Rinv_c = c.take(es * sq * sq);
+    P->UR = c.take(es * sq * sq);
+    P->Wm = c.take(es * sq * sq);
+    P->G64 = (double *)c.take(sizeof(double) * sq * sq);
+    P->R1 = (double *)c.take(sizeof(double) * sq * sq);
+    P->R1i = (double *)c.take(sizeof(double) * sq * sq);
+    P->R2 = (double *)c.take(sizeof(double) * sq * sq);
+    P->R2i = (double *)c.take(sizeof(double) * sq * sq);
+    P->Rt = (double *)c.take(sizeof(double) * sq * sq);
+    P->lam = (double *)c.take(sizeof(double) * sq);
+    P->Vfull = (double *)c.take(sizeof(double) * sq * sq);
+    P->sig = (double *)c.take(sizeof(double) * (n > sq ? n : sq));
+    P->status = (int *)c.take(sizeof(int));
+    P->Kdev = (int *)c.take(2 * sizeof(int));
+}
+
+// Records a pair of events around a stage group when tracing is enabled.
+struct Span {
+    rsvd_plan *P;
+    int stage;
+    size_t idx = (size_t)-1;
+    Span(rsvd_plan *P_, int stage_) : P(P_), stage(stage_) {
+        if (!P->prof) return;
+        if (P->ev.size() < P->ev_used + 2) {
+            for (int i = 0; i < 64; i++) {
+                cudaEvent_t e;
+                if (cudaEventCreate(&e) != cudaSuccess) return;
+                P->ev.push_back(e);
+            }
+            P->ev_stage.resize(P->ev.size() / 2);
+        }
+        idx = P->ev_used;
+        P->ev_used += 2;
+        cudaEventRecord(P->ev[idx], P->stream);
+    }
+    ~Span() {
+        if (idx == (size_t)-1) return;
+        cudaEventRecord(P->ev[idx + 1], P->stream);
+        P->ev_stage[idx / 2] = stage;
+    }
+};
+
+#define CK(...)                                        \
+    do {                                               \
+        cudaError_t e_ = (__VA_ARGS__);                \
+        if (e_ != cudaSuccess) return RSVD_ERR_CUDA;   \
+    } while (0)
+
+template <typename T> constexpr double unit_roundoff();
+template <> constexpr double unit_roundoff<float>() { return FLT_EPSILON / 2; }
+template <> constexpr double unit_roundoff<double>() { return DBL_EPSILON / 2; }
+
+// CholeskyQR2 of X (rows x w, ld): Qo = X R^{-1} with R = R2 R1 (written to Rt
+// when want_r).  R1 from chol(X^T X); Q1 = X R1^{-1} into Tmp; R2 from
+// chol(Q1^T Q1); Qo = Q1 R2^{-1}.
+template <typename T>
+rsvd_status cqr2(rsvd_plan *P, const T *X, int64_t rows, int w, int ld, T *Qo, T *Tmp, bool want_r) {
+    cudaStream_t s = P->stream;
+    T *G = (T *)P->G, *Ric = (T *)P->Rinv_c, *part = (T *)P->part;
+    const double u = unit_roundoff<T>();
+    CK(gemm_tn<T>(rows, ld, ld, X, ld, X, ld, G, ld, part, P->part_elems, s));
+    CK(chol_inv<T, T>(G, ld, w, rows, u, P->R1, P->R1i, Ric, ld, P->status, s));
+    CK(gemm_nn<T>(rows, ld, ld, X, ld, Ric, ld, Tmp, ld, s));
+    CK(gemm_tn<T>(rows, ld, ld, Tmp, ld, Tmp, ld, G, ld, part, P->part_elems, s));
+    CK(chol_inv<T, T>(G, ld, w, rows, u, P->R2, P->R2i, Ric, ld, P->status, s));
+    CK(gemm_nn<T>(rows, ld, ld, Tmp, ld, Ric, ld, Qo, ld, s));
+    if (want_r) CK(trmm_upper(P->R2, P->R1, P->Rt, w, s));
+    return RSVD_OK;
+}
+
+template <typename T>
+rsvd_status center(rsvd_plan *P, T *A) {
+    CK(center_columns<T>(A, P->m, P->n, P->n, !(P->flags & RSVD_FLAG_NO_CENTER), P->mu, P->fro2, P->cpart,
+                         P->stream));
+    return RSVD_OK;
+}
+
+// Sec. 3.1.2 with re-orthonormalised power steps; see rsvd() in include/rsvd.h.
+template <typename T>
+rsvd_status run_rsvd(rsvd_plan *P, T *A, const T *Omega, double *S, T *U, T *V) {
+    cudaStream_t s = P->stream;
+    const int64_t m = P->m, n = P->n;
+    const int l = P->l, lp = P->lp, k = P->k;
+    T *Y = (T *)P->Y, *Q = (T *)P->Qb, *Tmp = (T *)P->Tmp;
+    T *Ob = (T *)P->Ob, *Z = (T *)P->Z, *Qz = (T *)P->Qz, *Tn = (T *)P->Tn, *Vt = (T *)P->Vt, *Tmpn = (T *)P->Tmpn;
+    T *part = (T *)P->part;
+    rsvd_status st;
+    {
+        Span sp(P, RSVD_STAGE_CENTER);
+        if ((st = center<T>(P, A))) return st;                                // A <- A - 1 mu^T, ||A||_F^2
+    }
+    CK(copy2d<T, T>(Omega, l, Ob, lp, n, l, lp, s));                          // G padded to lp columns
+    {
+        Span sp(P, RSVD_STAGE_AX);
+        CK(gemm_nn<T>(m, lp, n, A, n, Ob, lp, Y, lp, s));                     // H(0) = A G
+    }
+    {
+        Span sp(P, RSVD_STAGE_ORTH);
+        if ((st = cqr2<T>(P, Y, m, l, lp, Q, Tmp, false))) return st;         // Q = orth(H)
+    }
+    for (int it = 0; it < P->q; it++) {                                      // H(i) = A (A^T H(i-1))
+        {
+            Span sp(P, RSVD_STAGE_ATX);
+            CK(gemm_tn<T>(m, n, lp, A, n, Q, lp, Z, lp, part, P->part_elems, s));
+        }
+        {
+            Span sp(P, RSVD_STAGE_ORTH);
+            if ((st = cqr2<T>(P, Z, n, l, lp, Qz, Tmpn, false))) return st;
+        }
+        {
+            Span sp(P, RSVD_STAGE_AX);
+            CK(gemm_nn<T>(m, lp, n, A, n, Qz, lp, Y, lp, s));
+        }
+        {
+            Span sp(P, RSVD_STAGE_ORTH);
+            if ((st = cqr2<T>(P, Y, m, l, lp, Q, Tmp, false))) return st;
+        }
+    }
+    {
+        Span sp(P, RSVD_STAGE_ATX);
+        CK(gemm_tn<T>(m, n, lp, A, n, Q, lp, Tn, lp, part, P->part_elems, s));  // T = A^T Q  (= B^T)
+    }
+    T *UR = (T *)P->UR, *W = (T *)P->Wm;
+    {
+        Span sp(P, RSVD_STAGE_SMALL);
+        if ((st = cqr2<T>(P, Tn, n, l, lp, Qz, Tmpn, true))) return st;       // T = Q_T R
+        CK(jacobi_osvd<T, T>(P->Rt, l, lp, P->sig, UR, W, P->status, s));     // R = U_R Sigma W^T
+    }
+    {
+        Span sp(P, RSVD_STAGE_FINISH);
+        CK(gemm_nn<T>(n, lp, lp, Qz, lp, UR, lp, Vt, lp, s));                 // Vt = Q_T U_R
+        CK(sign_normalize<T>(Vt, n, l, lp, W, l, lp, s));
+        CK(gemm_nn<T>(m, k, lp, Q, lp, W, lp, U, k, s));                      // U = Q W (leading k)
+        CK(copy2d<T, T>(Vt, lp, V, k, n, k, k, s));
+        CK(copy_f64(P->sig, S, k, s));
+    }
+    P->last_count = k;
+    return RSVD_OK;
+}
+
+// Sec. 2.3 / Sec. 3.1.3 Gram route, and the CholeskyQR2 + one-sided Jacobi route.
+template <typename T>
+rsvd_status run_exact(rsvd_plan *P, T *A, int method, double *S, T *U, T *V) {
+    cudaStream_t s = P->stream;
+    const int64_t m = P->m, n = P->n;
+    const int nn = (int)n;
+    rsvd_status st;
+    {
+        Span sp(P, RSVD_STAGE_CENTER);
+        if ((st = center<T>(P, A))) return st;
+    }
+    if (method == RSVD_EXACT_GRAM) {
+        T *G = (T *)P->G, *Vs = (T *)P->UR;
+        {
+            Span sp(P, RSVD_STAGE_ATX);
+            CK(gemm_tn<T>(m, n, n, A, n, A, n, G, n, (T *)P->part, P->part_elems, s));  // step 1: A^T A
+        }
+        {
+            Span sp(P, RSVD_STAGE_SMALL);
+            CK(copy2d<T, double>(G, n, P->G64, n, n, n, n, s));
+            CK(jacobi_eig(P->G64, nn, P->lam, P->Vfull, P->status, s));              // step 2: eigen-decomposition
+            CK(gram_finish<T>(P->lam, P->Vfull, nn, P->sig, Vs, P->status, s));       // step 3: sigma = sqrt(lambda)
+        }
+        {
+            Span sp(P, RSVD_STAGE_AX);
+            CK(gemm_nn<T>(m, n, n, A, n, Vs, n, U, n, s));                            // step 4: u_i = A v_i / sigma_i
+        }
+        Span sp(P, RSVD_STAGE_FINISH);
+        CK(copy2d<double, T>(P->Vfull, n, V, n, n, n, n, s));
+    } else {
+        T *Qw = (T *)P->Qb, *Tmp = (T *)P->Tmp, *UR = (T *)P->UR, *W = (T *)P->Wm;
+        {
+            Span sp(P, RSVD_STAGE_ORTH);
+            if ((st = cqr2<T>(P, A, m, nn, nn, Qw, Tmp, true))) return st;           // A = Q R
+        }
+        {
+            Span sp(P, RSVD_STAGE_SMALL);
+            if (sizeof(T) == 8) CK(jacobi_osvd<double, T>(P->Rt, nn, nn, P->sig, UR, W, P->status, s));
+            else CK(jacobi_osvd<float, T>(P->Rt, nn, nn, P->sig, UR, W, P->status, s));
+        }
+        Span sp(P, RSVD_STAGE_FINISH);
+        CK(gemm_nn<T>(m, n, n, Qw, n, UR, n, U, n, s));                               // U = Q U_R
+        CK(copy2d<T, T>(W, n, V, n, n, n, n, s));
+    }
+    {
+        Span sp(P, RSVD_STAGE_FINISH);
+        CK(sign_normalize<T>(V, n, nn, n, U, m, n, s));
+        CK(copy_f64(P->sig, S, n, s));
+    }
+    P->last_count = nn;
+    return RSVD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rsvd_status rsvd_plan_create(rsvd_plan_t *plan, int64_t m, int64_t n, int k, int p, int q, rsvd_dtype dtype,
+                             void *cuda_stream) {
+    if (!plan) return RSVD_ERR_ARG;
+    *plan = nullptr;
+    if (m < 1 || n < 1 || m < n || k < 1 || p < 0 || q < 0) return RSVD_ERR_ARG;
+    if ((int64_t)k + p > n) return RSVD_ERR_ARG;
+    if (dtype != RSVD_F32 && dtype != RSVD_F64) return RSVD_ERR_UNSUPPORTED;
+    if (k + p > kSmallMaxF64) return RSVD_ERR_UNSUPPORTED;
+    rsvd_plan *P = new (std::nothrow) rsvd_plan();
+    if (!P) return RSVD_ERR_OOM;
+    P->m = m;
+    P->n = n;
+    P->k = k;
+    P->p = p;
+    P->q = q;
+    P->l = k + p;
+    P->lp = (int)round_up(P->l, 16);
+    P->nx = n <= kSmallMaxF64 ? (int)n : 0;
+    P->wide = P->lp > P->nx ? P->lp : P->nx;
+    P->dtype = dtype;
+    P->stream = (cudaStream_t)cuda_stream;
+    Carver c;
+    carve(P, c);
+    P->ws_bytes = c.off;
+    if (cudaMalloc(&P->ws, P->ws_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete P;
+        return RSVD_ERR_OOM;
+    }
+    Carver c2;
+    c2.base = (char *)P->ws;
+    carve(P, c2);
+    if (cudaMemsetAsync(P->ws, 0, P->ws_bytes, P->stream) != cudaSuccess ||
+        cudaStreamSynchronize(P->stream) != cudaSuccess) {
+        cudaFree(P->ws);
+        delete P;
+        return RSVD_ERR_CUDA;
+    }
+    *plan = P;
+    return RSVD_OK;
+}
+
+rsvd_status rsvd_plan_destroy(rsvd_plan_t P) {
+    if (!P) return RSVD_OK;
+    cudaStreamSynchronize(P->stream);
+    for (cudaEvent_t e : P->ev) cudaEventDestroy(e);
+    cudaFree(P->ws);
+    delete P;
+    return RSVD_OK;
+}
+
+size_t rsvd_plan_workspace_bytes(rsvd_plan_t P) { return P ? P->ws_bytes : 0; }
+
+rsvd_status rsvd_plan_set_flags(rsvd_plan_t P, unsigned flags) {
+    if (!P || (flags & ~(unsigned)RSVD_FLAG_NO_CENTER)) return RSVD_ERR_ARG;
+    P->flags = flags;
+    return RSVD_OK;
+}
+
+rsvd_status rsvd_plan_sync(rsvd_plan_t P) {
+    if (!P) return RSVD_ERR_ARG;
+    int st = 0;
+    if (cudaMemcpyAsync(&st, P->status, sizeof(int), cudaMemcpyDeviceToHost, P->stream) != cudaSuccess)
+        return RSVD_ERR_CUDA;
+    if (cudaStreamSynchronize(P->stream) != cudaSuccess) return RSVD_ERR_CUDA;
+    if (cudaMemsetAsync(P->status, 0, sizeof(int), P->stream) != cudaSuccess) return RSVD_ERR_CUDA;
+    if (st & ST_CHOL) return RSVD_ERR_CHOL;
+    if (st & ST_NOCONV) return RSVD_ERR_NOCONV;
+    return RSVD_OK;
+}
+
+rsvd_status rsvd(rsvd_plan_t P, void *A, const float *col_scales, const void *Omega, double *S, void *U, void *V) {
+    if (!P || !A || !Omega || !S || !U || !V) return RSVD_ERR_ARG;
+    if (col_scales) return RSVD_ERR_ARG;
+    if (P->dtype == RSVD_F32) return run_rsvd<float>(P, (float *)A, (const float *)Omega, S, (float *)U, (float *)V);
+    return run_rsvd<double>(P, (double *)A, (const double *)Omega, S, (double *)U, (double *)V);
+}
+
+rsvd_status svd_exact(rsvd_plan_t P, void *A, int method, double *S, void *U, void *V) {
+    if (!P || !A || !S || !U || !V) return RSVD_ERR_ARG;
+    if (method != RSVD_EXACT_GRAM && method != RSVD_EXACT_QR_JACOBI) return RSVD_ERR_ARG;
+    if (!P->nx) return RSVD_ERR_UNSUPPORTED;
+    if (P->dtype == RSVD_F32) return run_exact<float>(P, (float *)A, method, S, (float *)U, (float *)V);
+    return run_exact<double>(P, (double *)A, method, S, (double *)U, (double *)V);
+}
+
+rsvd_status svd_truncated_krylov(rsvd_plan_t P, void *A, const void *v1, int steps, double *S, void *U, void *V) {
+    if (!P || !A || !v1 || !S || !U || !V) return RSVD_ERR_ARG;
+    if (steps < P->k || steps > P->n) return RSVD_ERR_ARG;
+    return RSVD_ERR_UNSUPPORTED;
+}
+
+rsvd_status pca_threshold(rsvd_plan_t P, double t, int *K) {
+    if (!P || !K || !(t > 0.0) || t > 1.0) return RSVD_ERR_ARG;
+    if (P->last_count <= 0) return RSVD_ERR_ARG;
+    int host[2] = {0, 0};
+    if (pca_select(P->sig, P->last_count, P->fro2, t, P->Kdev, P->Kdev + 1, P->stream) != cudaSuccess)
+        return RSVD_ERR_CUDA;
+    if (cudaMemcpyAsync(host, P->Kdev, 2 * sizeof(int), cudaMemcpyDeviceToHost, P->stream) != cudaSuccess)
+        return RSVD_ERR_CUDA;
+    rsvd_status st = rsvd_plan_sync(P);
+    *K = host[0];
+    if (st != RSVD_OK) return st;
+    return host[1] ? RSVD_OK : RSVD_WARN_K_GT_k;
+}
+
+rsvd_status rsvd_plan_fro2(rsvd_plan_t P, double *fro2) {
+    if (!P || !fro2) return RSVD_ERR_ARG;
+    if (cudaMemcpyAsync(fro2, P->fro2, sizeof(double), cudaMemcpyDeviceToHost, P->stream) != cudaSuccess)
+        return RSVD_ERR_CUDA;
+    return cudaStreamSynchronize(P->stream) == cudaSuccess ? RSVD_OK : RSVD_ERR_CUDA;
+}
+
+rsvd_status rsvd_plan_profile(rsvd_plan_t P, int enable) {
+    if (!P) return RSVD_ERR_ARG;
+    P->prof = enable != 0;
+    return RSVD_OK;
+}
+
+rsvd_status rsvd_plan_profile_read(rsvd_plan_t P, double *ms, int *groups, int nstages) {
+    if (!P || !ms || !groups || nstages < 1) return RSVD_ERR_ARG;
+    for (int i = 0; i < nstages; i++) { ms[i] = 0.0; groups[i] = 0; }
+    if (cudaStreamSynchronize(P->stream) != cudaSuccess) return RSVD_ERR_CUDA;
+    for (size_t i = 0; i + 1 < P->ev_used; i += 2) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, P->ev[i], P->ev[i + 1]) != cudaSuccess) return RSVD_ERR_CUDA;
+        const int st = P->ev_stage[i / 2];
+        if (st >= 0 && st < nstages) { ms[st] += t; groups[st] += 1; }
+    }
+    P->ev_used = 0;
+    return RSVD_OK;
+}
+
+uint64_t rsvd_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char *rsvd_status_string(rsvd_status s) {
+    switch (s) {
+        case RSVD_OK: return "ok";
+        case RSVD_ERR_ARG: return "invalid argument";
+        case RSVD_ERR_OOM: return "device allocation failed";
+        case RSVD_ERR_CHOL: return "Cholesky breakdown";
+        case RSVD_ERR_NOCONV: return "Jacobi did not converge";
+        case RSVD_ERR_TIMEOUT: return "device wait timed out";
+        case RSVD_ERR_CUDA: return "CUDA error";
+        case RSVD_ERR_UNSUPPORTED: return "unsupported size or dtype";
+        case RSVD_WARN_K_GT_k: return "threshold not reached within the returned values";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

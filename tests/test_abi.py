@@ -1,0 +1,67 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function
+include/rsvd.h declares, and rejects invalid arguments before touching CUDA."""
+import ctypes
+import subprocess
+
+import pytest
+
+import paper_1906_12085_gb300 as g
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1906_12085_gb300 import build
+    build.build()
+
+
+def test_library_exports_every_header_function():
+    names = g.header_functions()
+    assert {"rsvd_plan_create", "rsvd", "svd_exact", "svd_truncated_krylov", "pca_threshold"} <= set(names)
+    L = g.lib()
+    missing = [f for f in names if not hasattr(L, f)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", g.library_path()], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    assert set(names) <= exported
+
+
+def test_library_has_no_oracle_dependency():
+    """The product library links neither the oracle library nor any of its symbols."""
+    out = subprocess.run(["nm", "-D", g.library_path()], capture_output=True, text=True).stdout
+    assert "orc_" not in out
+    ldd = subprocess.run(["ldd", g.library_path()], capture_output=True, text=True).stdout
+    assert "liboracle" not in ldd
+
+
+@pytest.mark.parametrize("args", [
+    (10, 20, 1, 0, 0, g.RSVD_F32),      # m < n
+    (100, 20, 0, 0, 0, g.RSVD_F32),     # k < 1
+    (100, 20, 15, 10, 0, g.RSVD_F32),   # l = k + p > n
+    (100, 20, 5, -1, 0, g.RSVD_F32),    # p < 0
+    (100, 20, 5, 1, -2, g.RSVD_F32),    # q < 0
+    (0, 0, 1, 0, 0, g.RSVD_F32),
+])
+def test_plan_create_rejects_bad_sizes(args):
+    h = ctypes.c_void_p(12345)
+    st = g.lib().rsvd_plan_create(ctypes.byref(h), *args, None)
+    assert st == g.RSVD_ERR_ARG
+    assert h.value is None
+
+
+def test_plan_create_rejects_unbuilt_dtypes():
+    h = ctypes.c_void_p()
+    for dt in (g.RSVD_BF16, g.RSVD_FP8_E4M3, 7):
+        assert g.lib().rsvd_plan_create(ctypes.byref(h), 100, 20, 4, 2, 1, dt, None) == g.RSVD_ERR_UNSUPPORTED
+
+
+def test_null_plan_arguments():
+    L = g.lib()
+    assert L.rsvd_plan_destroy(None) == g.RSVD_OK
+    assert L.rsvd_plan_workspace_bytes(None) == 0
+    assert L.rsvd(None, None, None, None, None, None, None) == g.RSVD_ERR_ARG
+    assert L.svd_exact(None, None, 0, None, None, None) == g.RSVD_ERR_ARG
+    assert L.svd_truncated_krylov(None, None, None, 1, None, None, None) == g.RSVD_ERR_ARG
+    K = ctypes.c_int(0)
+    assert L.pca_threshold(None, 0.9, ctypes.byref(K)) == g.RSVD_ERR_ARG
+    assert L.rsvd_plan_sync(None) == g.RSVD_ERR_ARG
+    assert g.rsvd_status_string(g.RSVD_ERR_CHOL) == "Cholesky breakdown"
