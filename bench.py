@@ -33,7 +33,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "rpca_fp32_200000x1000"
-SMS, FP32_LANES = 152, 128
 
 
 def alg_flops(m, n, k, p, q):
@@ -232,22 +231,26 @@ def run_ours(args):
     flops = alg_flops(m, n, k, p, q)
     value = world * flops * args.steps / (ms_max * 1e-3) / 1e9
 
-    # dominant kernel group and its roofline (float32 products on CUDA cores: ALU-bound)
+    # dominant kernel group and its roofline.  The float32 products run as 3xTF32 on
+    # tcgen05: at l = 60 (64 padded) their arithmetic intensity is 2*64 flop / 4 B = 32
+    # flop/B, below the 3xTF32 ridge (TF32 dense / 3 / HBM ~ 46 flop/B), so they are
+    # HBM-bound; algorithmic bytes per launch = one read of A (4mn).
     pk, src = peaks()
-    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
-    alu_peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
+    hbm = float(pk.get("hbm_gbs", 6800.0))
     ax_ms, ax_n = prof["ax"]
     atx_ms, atx_n = prof["atx"]
     if ax_ms >= atx_ms:
-        dom, dom_ms, dom_n, dom_src, dom_kernel = "gemm_nn (Y = A Z)", ax_ms, ax_n, "k_gemm.cu", "gemm_nn_kernel"
+        dom, dom_ms, dom_n, dom_kernel = "tc_nn_kernel (Y = A Z, 3xTF32 tcgen05)", ax_ms, ax_n, "tc_nn_kernel"
     else:
-        dom, dom_ms, dom_n, dom_src, dom_kernel = "gemm_tn (Z = A^T Q)", atx_ms, atx_n, "k_gemm.cu", "gemm_tn_kernel"
-    per_launch_flops = 2.0 * m * n * l
-    achieved = per_launch_flops / (dom_ms / dom_n * 1e-3) / 1e12 if dom_n else None
-    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": (achieved / alu_peak) if achieved else None,
-                "traffic": traffic_for(dom_src, dom_kernel),
-                "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (unit counts and max clock)",
+        dom, dom_ms, dom_n, dom_kernel = ("tc_tn_kernel + sum_chunks_kernel (Z = A^T Q, 3xTF32 tcgen05)", atx_ms,
+                                          atx_n, "tc_tn_kernel")
+    per_launch_bytes = 4.0 * m * n
+    achieved = per_launch_bytes / (dom_ms / dom_n * 1e-3) / 1e9 if dom_n else None
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": (achieved / hbm) if achieved else None,
+                "traffic": traffic_for("k_tc.cu", dom_kernel),
+                "algorithmic_bytes_per_launch": per_launch_bytes,
+                "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback 6800 GB/s",
                 "stage_ms_per_step": {kk: vv[0] / args.steps for kk, vv in prof.items()}}
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region

@@ -14,6 +14,7 @@ enum StatusBits : int {
     ST_NOCONV = 2,    // Jacobi sweep cap reached
     ST_SHIFT = 4,     // shifted Cholesky was needed (informational)
     ST_RANKDEF = 8,   // a singular value fell below n*eps*sigma_1 (informational)
+    ST_TIMEOUT = 16,  // a bounded device wait gave up (pipeline stalled)
 };
 
 // Largest l (or n for svd_exact) whose l x l working set fits one CTA's shared memory.
@@ -49,11 +50,11 @@ int64_t gemm_tn_partials(int64_t rows, int64_t N, int64_t L);
 
 // ---------------------------------------------------------- small dense
 // Upper Cholesky R^T R = G (+ shift) of the leading l x l block of G (ldg), then
-// R^{-1}.  Writes R, Rinv (float64, l x l dense, ld l) and Rinv_c (element type
-// Tc, lp x lp, zero padded).  On a non-positive pivot retries once with the
-// shift 11 (rows*l + l(l+1)) u tr(G) (shifted CholeskyQR); on a second
-// breakdown sets ST_CHOL and returns the identity.
-template <typename TG, typename Tc>
+// R^{-1}, arithmetic in Tk.  Writes R, Rinv (float64, l x l dense, ld l) and
+// Rinv_c (element type Tc, lp x lp, zero padded).  On a non-positive pivot
+// retries once with the shift 11 (rows*l + l(l+1)) u tr(G) (shifted
+// CholeskyQR); on a second breakdown sets ST_CHOL and returns R = 0, R^{-1} = I.
+template <typename TG, typename Tk, typename Tc>
 cudaError_t chol_inv(const TG *G, int64_t ldg, int l, int64_t rows, double unit_roundoff, double *R,
                      double *Rinv, Tc *Rinv_c, int lp, int *status, cudaStream_t s);
 
@@ -94,5 +95,22 @@ cudaError_t copy_f64(const double *src, double *dst, int64_t count, cudaStream_t
 // sum sigma_i^2 >= t * fro2; *reached = 0 if not reached within count.
 cudaError_t pca_select(const double *sigma, int count, const double *fro2, double t, int *K, int *reached,
                        cudaStream_t s);
+
+// ------------------------------------------------------ tensor-core path
+// true when the driver exposes TMA descriptor encoding (cuTensorMapEncodeTiled)
+bool tc_available();
+// th / tl (N x ldt) = tf32 hi / lo split of Z^T for Z rows x cols row-major (ldz); zero beyond.
+cudaError_t tc_split_transpose(const float *Z, int64_t rows, int cols, int64_t ldz, int N, float *th, float *tl,
+                               int64_t ldt, cudaStream_t s);
+// Y (m x N) = A (m x n) Z with Z given as its transposed tf32 split (N x ldb each);
+// 3xTF32 on tcgen05.  N in {16, 32, ..., 128}; A, lda*4 and ldb*4 16-byte aligned.
+cudaError_t tc_gemm_nn(int64_t m, int n, int N, const float *A, int64_t lda, const float *Bth, const float *Btl,
+                       int64_t ldb, float *Y, int64_t ldy, int *status, cudaStream_t s);
+// C (ncols x N, ldc) = A^T Q for A rows x ncols (lda) and Q rows x N (ldq), 3xTF32 on
+// tcgen05, split over row chunks into `part` (tc_gemm_tn_partials elements) and
+// summed in chunk order.  N in {16, ..., 128}; pointers and leading dimensions 16-byte aligned.
+cudaError_t tc_gemm_tn(int64_t rows, int ncols, int N, const float *A, int64_t lda, const float *Q, int64_t ldq,
+                       float *C, int64_t ldc, float *part, int64_t part_elems, int *status, cudaStream_t s);
+int64_t tc_gemm_tn_partials(int64_t rows, int ncols, int N);
 
 }  // namespace gbr

@@ -64,13 +64,17 @@ __global__ void __launch_bounds__(kThreads) colsum_kernel(const T *__restrict__ 
     }
 }
 
+// one warp per column: lanes sum interleaved chunks, then a fixed xor tree
 __global__ void colmean_kernel(const double *__restrict__ part, int64_t chunks, int64_t n, int64_t m,
                                double *__restrict__ mu) {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (c >= n) return;
     double s = 0.0;
-    for (int64_t k = 0; k < chunks; k++) s += part[k * n + c];
-    mu[c] = s / (double)m;
+    for (int64_t k = lane; k < chunks; k += 32) s += part[k * n + c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) mu[c] = s / (double)m;
 }
 
 __device__ __forceinline__ double block_sum(double v, double *red) {
@@ -160,7 +164,7 @@ cudaError_t center_columns(T *A, int64_t m, int64_t n, int64_t lda, bool subtrac
     if (subtract) {
         if (vec) colsum_kernel<T, V><<<(unsigned)chunks, kThreads, 0, s>>>(A, m, n, lda, rpc, colpart);
         else colsum_kernel<T, 1><<<(unsigned)chunks, kThreads, 0, s>>>(A, m, n, lda, rpc, colpart);
-        colmean_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(colpart, chunks, n, m, mu);
+        colmean_kernel<<<(unsigned)ceil_div(n, 8), 256, 0, s>>>(colpart, chunks, n, m, mu);
         note_launch(2);
     } else {
         cudaMemsetAsync(mu, 0, sizeof(double) * n, s);

@@ -35,50 +35,49 @@ template <> struct Eps<float> { static constexpr double v = FLT_EPSILON; };
 template <> struct Eps<double> { static constexpr double v = DBL_EPSILON; };
 
 // ------------------------------------------------------------ Cholesky + inverse
-template <typename TG, typename Tc>
+// Right-looking upper Cholesky R^T R = G with one barrier per column: the
+// scaled row j of R goes to a separate buffer, so the trailing update (which
+// reads the unscaled row j of the working matrix) never races with it.  The
+// inverse solves R x = e_c column by column, one column per thread, with no
+// barriers (R is read-only by then).  Arithmetic in Tk.
+template <typename TG, typename Tk, typename Tc>
 __global__ void chol_inv_kernel(const TG *__restrict__ G, int64_t ldg, int l, double shift_coef,
                                 double *__restrict__ R, double *__restrict__ Rinv, Tc *__restrict__ Rinv_c, int lp,
                                 int *__restrict__ status) {
-    extern __shared__ double sm[];
-    double *M = sm;           // l x l working matrix (upper triangle used)
-    double *col = sm + l * l; // l scratch
-    __shared__ int bad;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Tk *M = reinterpret_cast<Tk *>(smraw);  // l x l working matrix (upper triangle)
+    Tk *Rs = M + l * l;                     // l x l factor R (upper), then its inverse in place by columns
     __shared__ double trace;
     const int tid = threadIdx.x, nt = blockDim.x;
     int used = 0;  // 0: plain, 1: shifted, 2: breakdown fallback (R = 0, R^{-1} = I)
     for (int attempt = 0; attempt < 3; attempt++) {
         for (int idx = tid; idx < l * l; idx += nt) {
             const int i = idx / l, j = idx % l;
-            M[idx] = attempt == 2 ? (i == j ? 1.0 : 0.0) : (double)G[(int64_t)min(i, j) * ldg + max(i, j)];
+            M[idx] = attempt == 2 ? Tk(i == j ? 1 : 0) : (Tk)G[(int64_t)min(i, j) * ldg + max(i, j)];
+            Rs[idx] = Tk(0);
         }
         __syncthreads();
         if (tid == 0) {
             double tr = 0.0;
-            for (int i = 0; i < l; i++) tr += M[i * l + i];
+            for (int i = 0; i < l; i++) tr += (double)M[i * l + i];
             trace = tr;
-            bad = 0;
         }
         __syncthreads();
         if (attempt == 1) {  // shifted CholeskyQR: G + s I with s = 11 (rows l + l(l+1)) u tr(G)
-            const double sh = shift_coef * trace;
+            const Tk sh = (Tk)(shift_coef * trace);
             for (int i = tid; i < l; i += nt) M[i * l + i] += sh;
             __syncthreads();
         }
+        bool bad = false;
         for (int j = 0; j < l; j++) {
-            if (tid == 0) {
-                const double d = M[j * l + j];
-                if (!(d > 0.0) || !isfinite(d)) bad = 1;
-                else M[j * l + j] = sqrt(d);
-            }
-            __syncthreads();
-            if (bad) break;
-            const double rjj = M[j * l + j];
-            for (int c = j + 1 + tid; c < l; c += nt) M[j * l + c] /= rjj;
-            __syncthreads();
+            const Tk d = M[j * l + j];
+            if (!(d > Tk(0)) || !isfinite((double)d)) { bad = true; break; }  // uniform: every thread reads d
+            const Tk rinv = Tk(1) / sqrt(d), dinv = Tk(1) / d;
+            for (int c = j + tid; c < l; c += nt) Rs[j * l + c] = M[j * l + c] * rinv;
             const int nr = l - j - 1;
             for (int idx = tid; idx < nr * nr; idx += nt) {
                 const int r = j + 1 + idx / nr, c = j + 1 + idx % nr;
-                if (c >= r) M[r * l + c] -= M[j * l + r] * M[j * l + c];
+                if (c >= r) M[r * l + c] -= M[j * l + r] * M[j * l + c] * dinv;
             }
             __syncthreads();
         }
@@ -89,32 +88,26 @@ __global__ void chol_inv_kernel(const TG *__restrict__ G, int64_t ldg, int l, do
         }
         __syncthreads();
     }
-    for (int idx = tid; idx < l * l; idx += nt) {
-        const int i = idx / l, j = idx % l;
-        R[idx] = (j >= i && used < 2) ? M[idx] : 0.0;
+    for (int idx = tid; idx < l * l; idx += nt) R[idx] = used < 2 ? (double)Rs[idx] : 0.0;
+    __syncthreads();
+    // column c of R^{-1}: back substitution R x = e_c (rows c..0), written over column c of Rs
+    Tk *X = M;  // reuse: X[i * l + c]
+    for (int c = tid; c < l; c += nt) {
+        for (int i = 0; i < l; i++) X[i * l + c] = Tk(0);
+        for (int k = c; k >= 0; k--) {
+            Tk acc = (k == c) ? Tk(1) : Tk(0);
+            for (int t = k + 1; t <= c; t++) acc -= Rs[k * l + t] * X[t * l + c];
+            X[k * l + c] = acc / Rs[k * l + k];
+        }
     }
     __syncthreads();
-    // in-place upper-triangular inverse, column by column:
-    // X_ij = -(sum_{k=i}^{j-1} X_ik R_kj) / R_jj, X_jj = 1 / R_jj
-    for (int j = 0; j < l; j++) {
-        const double rjj = M[j * l + j];
-        for (int i = tid; i < j; i += nt) {
-            double s = 0.0;
-            for (int k = i; k < j; k++) s += M[i * l + k] * M[k * l + j];
-            col[i] = -s / rjj;
-        }
-        __syncthreads();
-        for (int i = tid; i < j; i += nt) M[i * l + j] = col[i];
-        if (tid == 0) M[j * l + j] = 1.0 / rjj;
-        __syncthreads();
-    }
     for (int idx = tid; idx < l * l; idx += nt) {
         const int i = idx / l, j = idx % l;
-        Rinv[idx] = j >= i ? M[idx] : 0.0;
+        Rinv[idx] = j >= i ? (double)X[idx] : 0.0;
     }
     for (int idx = tid; idx < lp * lp; idx += nt) {
         const int i = idx / lp, j = idx % lp;
-        Rinv_c[idx] = (i < l && j < l && j >= i) ? (Tc)M[i * l + j] : Tc(0);
+        Rinv_c[idx] = (i < l && j < l && j >= i) ? (Tc)X[i * l + j] : Tc(0);
     }
 }
 
@@ -133,7 +126,8 @@ template <typename Ta, typename To>
 __global__ void __launch_bounds__(1024) jacobi_osvd_kernel(const double *__restrict__ R, int l, int lp,
                                                            double *__restrict__ sig, To *__restrict__ UR,
                                                            To *__restrict__ W, int *__restrict__ status,
-                                                           int max_sweeps) {
+                                                           int max_sweeps, int gsize) {
+    // gsize lanes (16 or 32) rotate one column pair; a warp holds 32 / gsize pairs
     extern __shared__ __align__(16) unsigned char smraw[];
     const int L = l + (l & 1);
     Ta *X = reinterpret_cast<Ta *>(smraw);  // X[p * L + i]: column p of the rotated matrix
@@ -142,12 +136,16 @@ __global__ void __launch_bounds__(1024) jacobi_osvd_kernel(const double *__restr
     int *perm = reinterpret_cast<int *>(nrm + L);
     __shared__ int rotated;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int gl = lane % gsize, gpw = 32 / gsize;               // lane in group, groups per warp
+    const int grp = warp * gpw + lane / gsize, ngrp = nw * gpw;
+    const unsigned gmask = gsize == 32 ? 0xffffffffu : (0xffffu << (lane & 16));
     for (int idx = tid; idx < L * L; idx += nt) {
         const int p = idx / L, i = idx % L;
         X[idx] = (p < l && i < l) ? (Ta)R[i * l + p] : Ta(0);
         V[idx] = (p == i) ? Ta(1) : Ta(0);
     }
-    const Ta tol = (Ta)(sqrt((double)l) * Eps<Ta>::v);
+    // rotate when |x_p . x_q| > tol ||x_p|| ||x_q||
+    const Ta tol = (Ta)((double)l * Eps<Ta>::v);
     int sweep = 0;
     bool converged = false;
     __syncthreads();
@@ -155,25 +153,38 @@ __global__ void __launch_bounds__(1024) jacobi_osvd_kernel(const double *__restr
         if (tid == 0) rotated = 0;
         __syncthreads();
         for (int r = 0; r < L - 1; r++) {
-            for (int pr = warp; pr < L / 2; pr += nw) {
-                const int a = rr_pos(pr, r, L), b = rr_pos(L - 1 - pr, r, L);
-                if (a >= l || b >= l) continue;
-                const int p = min(a, b), q = max(a, b);
-                Ta al = 0, be = 0, ga = 0;
-                for (int i = lane; i < l; i += 32) {
-                    const Ta xp = X[p * L + i], xq = X[q * L + i];
-                    al += xp * xp;
-                    be += xq * xq;
-                    ga += xp * xq;
+            for (int pr0 = 0; pr0 < L / 2; pr0 += ngrp) {
+                const int pr = pr0 + grp;
+                const bool act = pr < L / 2;
+                int p = 0, q = 1;
+                if (act) {
+                    const int a = rr_pos(pr, r, L), b = rr_pos(L - 1 - pr, r, L);
+                    p = min(a, b);
+                    q = max(a, b);
                 }
-                al = warp_sum(al);
-                be = warp_sum(be);
-                ga = warp_sum(ga);
-                if (ga != Ta(0) && fabs(ga) > tol * sqrt(al * be)) {
+                const bool live = act && q < l;
+                Ta al = 0, be = 0, ga = 0;
+                if (live)
+                    for (int i = gl; i < l; i += gsize) {
+                        const Ta xp = X[p * L + i], xq = X[q * L + i];
+                        al += xp * xp;
+                        be += xq * xq;
+                        ga += xp * xq;
+                    }
+                // three interleaved reductions inside the group
+                for (int o = gsize >> 1; o > 0; o >>= 1) {
+                    const Ta a1 = __shfl_xor_sync(gmask, al, o);
+                    const Ta b1 = __shfl_xor_sync(gmask, be, o);
+                    const Ta g1 = __shfl_xor_sync(gmask, ga, o);
+                    al += a1;
+                    be += b1;
+                    ga += g1;
+                }
+                if (live && ga != Ta(0) && fabs(ga) > tol * sqrt(al * be)) {
                     const Ta zeta = (be - al) / (Ta(2) * ga);
                     const Ta t = (zeta >= Ta(0) ? Ta(1) : Ta(-1)) / (fabs(zeta) + sqrt(Ta(1) + zeta * zeta));
                     const Ta c = Ta(1) / sqrt(Ta(1) + t * t), s = c * t;
-                    for (int i = lane; i < L; i += 32) {
+                    for (int i = gl; i < L; i += gsize) {
                         const Ta xp = X[p * L + i], xq = X[q * L + i];
                         X[p * L + i] = c * xp - s * xq;
                         X[q * L + i] = s * xp + c * xq;
@@ -181,7 +192,7 @@ __global__ void __launch_bounds__(1024) jacobi_osvd_kernel(const double *__restr
                         V[p * L + i] = c * vp - s * vq;
                         V[q * L + i] = s * vp + c * vq;
                     }
-                    if (lane == 0) rotated = 1;
+                    if (gl == 0) rotated = 1;
                 }
             }
             __syncthreads();
@@ -412,13 +423,13 @@ __global__ void pca_select_kernel(const double *__restrict__ sigma, int count, c
 
 }  // namespace
 
-template <typename TG, typename Tc>
+template <typename TG, typename Tk, typename Tc>
 cudaError_t chol_inv(const TG *G, int64_t ldg, int l, int64_t rows, double u, double *R, double *Rinv, Tc *Rinv_c,
                      int lp, int *status, cudaStream_t s) {
-    const size_t smem = sizeof(double) * ((size_t)l * l + l);
-    cudaFuncSetAttribute(chol_inv_kernel<TG, Tc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = sizeof(Tk) * 2 * (size_t)l * l;
+    cudaFuncSetAttribute(chol_inv_kernel<TG, Tk, Tc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const double coef = 11.0 * ((double)rows * l + (double)l * (l + 1)) * u;
-    chol_inv_kernel<TG, Tc><<<1, 512, smem, s>>>(G, ldg, l, coef, R, Rinv, Rinv_c, lp, status);
+    chol_inv_kernel<TG, Tk, Tc><<<1, 256, smem, s>>>(G, ldg, l, coef, R, Rinv, Rinv_c, lp, status);
     note_launch();
     return cudaGetLastError();
 }
@@ -434,8 +445,10 @@ cudaError_t jacobi_osvd(const double *R, int l, int lp, double *sig, To *UR, To 
     const int L = l + (l & 1);
     const size_t smem = sizeof(Ta) * (2 * (size_t)L * L + 1) + sizeof(double) * L + sizeof(int) * L + 16;
     cudaFuncSetAttribute(jacobi_osvd_kernel<Ta, To>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int threads = L / 2 * 32 < 1024 ? (L / 2 * 32 < 64 ? 64 : L / 2 * 32) : 1024;
-    jacobi_osvd_kernel<Ta, To><<<1, threads, smem, s>>>(R, l, lp, sig, UR, W, status, 40);
+    const int gsize = l <= 64 ? 16 : 32;
+    int threads = (L / 2) * gsize;
+    threads = threads < 64 ? 64 : threads > 1024 ? 1024 : (threads + 31) / 32 * 32;
+    jacobi_osvd_kernel<Ta, To><<<1, threads, smem, s>>>(R, l, lp, sig, UR, W, status, 40, gsize);
     note_launch();
     return cudaGetLastError();
 }
@@ -490,12 +503,11 @@ cudaError_t pca_select(const double *sigma, int count, const double *fro2, doubl
     return cudaGetLastError();
 }
 
-#define INST_CHOL(TG, TC)                                                                                        \
-    template cudaError_t chol_inv<TG, TC>(const TG *, int64_t, int, int64_t, double, double *, double *, TC *, int, \
-                                          int *, cudaStream_t);
-INST_CHOL(float, float)
-INST_CHOL(double, double)
-INST_CHOL(double, float)
+#define INST_CHOL(TG, TK, TC)                                                                                   \
+    template cudaError_t chol_inv<TG, TK, TC>(const TG *, int64_t, int, int64_t, double, double *, double *, TC *, \
+                                              int, int *, cudaStream_t);
+INST_CHOL(float, float, float)
+INST_CHOL(double, double, double)
 template cudaError_t jacobi_osvd<float, float>(const double *, int, int, double *, float *, float *, int *,
                                                cudaStream_t);
 template cudaError_t jacobi_osvd<double, float>(const double *, int, int, double *, float *, float *, int *,

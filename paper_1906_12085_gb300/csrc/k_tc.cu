@@ -1,0 +1,628 @@
+// Tensor-core (tcgen05) products for the float32 path with float32 accuracy.
+//
+// Each float32 operand x is split into two tf32 values, x = hi + lo with
+// hi = rn_tf32(x) and lo = rn_tf32(x - hi); a product is accumulated as
+// hi*hi + hi*lo + lo*hi in float32 in TMEM (lo*lo is below float32
+// resolution).  Operands reach shared memory by TMA; the split (and, for the
+// transposed product, the transpose into the K-major layout the MMA reads)
+// happens in shared memory between the TMA landing and the MMA, so the tall
+// operand is read from HBM exactly once.
+//
+//   tc_gemm_nn : Y (m x N) = A (m x n) Z (n x N)            (sketch, power step, Q = Y R^-1)
+//   tc_gemm_tn : part[chunk] = A[rows of chunk]^T Q[rows]   (power step, T = A^T Q, Gram)
+//
+// Both kernels are persistent (one CTA per SM) with warp roles:
+//   warp 0      TMA producer (one elected lane)
+//   warp 1      TMEM owner and MMA issuer (one elected lane)
+//   warps 2-9   split / transpose workers (256 threads)
+//   warps 10-13 epilogue: TMEM -> registers -> HBM (one TMEM lane quarter each)
+// Two TMEM accumulators alternate between tiles so the epilogue of one tile
+// overlaps the main loop of the next.  Every wait is bounded; a stalled
+// pipeline sets ST_TIMEOUT in the status word and the CTA drains and exits.
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+#include "tc_ptx.cuh"
+
+namespace gbr {
+namespace {
+
+using namespace tc;
+
+constexpr int TM = 128;    // MMA M: rows of A (NN) or columns of A (TN) per tile
+constexpr int TBK = 32;    // fp32 elements of K per stage (one 128-byte swizzle row)
+constexpr int NSPLIT = 256;
+constexpr int NEPI = 128;
+constexpr int NTHR = 64 + NSPLIT + NEPI;
+constexpr int EPI_WARP0 = (64 + NSPLIT) / 32;
+constexpr uint32_t A_STAGE = TM * 128;  // bytes of one 128 x 32 fp32 stage
+constexpr uint32_t TMEM_COLS = 256;     // two accumulators of up to 128 columns
+constexpr uint32_t ACC_STRIDE = 128;
+
+__device__ __forceinline__ float rna_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void split4(const float *x, float4 &h, float4 &l) {
+    h.x = rna_tf32(x[0]); l.x = rna_tf32(x[0] - h.x);
+    h.y = rna_tf32(x[1]); l.y = rna_tf32(x[1] - h.y);
+    h.z = rna_tf32(x[2]); l.z = rna_tf32(x[2] - h.z);
+    h.w = rna_tf32(x[3]); l.w = rna_tf32(x[3] - h.w);
+}
+
+// byte offset of the 16-byte chunk `cc` (K position 4cc..4cc+3) of row `r` in
+// the 128-byte-swizzled K-major layout (8-row atoms of 1024 bytes)
+__device__ __forceinline__ uint32_t kmajor_off(int r, int cc) {
+    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((cc ^ (r & 7)) << 4));
+}
+
+// Shared barrier block placed after the stage buffers.
+template <int S>
+struct Bars {
+    uint64_t full[S], split[S], empty[S];
+    uint64_t acc_full[2], acc_empty[2];
+    uint32_t tmem;
+    int abort_flag;
+};
+
+// Bounded wait that also honours the CTA-wide abort flag.
+__device__ __forceinline__ bool wait_ok(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    if (*abort_flag) return false;
+    if (mbar_wait(bar, parity)) return true;
+    *abort_flag = 1;
+    return false;
+}
+
+// 12 MMAs of one stage: D (+)= Ah Bh + Ah Bl + Al Bh over the 4 K=8 slices.
+template <int N>
+__device__ __forceinline__ void mma_stage(uint32_t d, const uint8_t *ah, const uint8_t *al, const uint8_t *bh,
+                                          const uint8_t *bl, bool first) {
+    constexpr uint32_t idesc = idesc_tf32(TM, N);
+#pragma unroll
+    for (int kk = 0; kk < TBK / 8; kk++) {
+        const uint32_t off = kk * 32;
+        const uint64_t dah = sdesc_kmajor_sw128(ah, off), dal = sdesc_kmajor_sw128(al, off);
+        const uint64_t dbh = sdesc_kmajor_sw128(bh, off), dbl = sdesc_kmajor_sw128(bl, off);
+        mma_tf32(d, dah, dbh, idesc, (first && kk == 0) ? 0u : 1u);
+        mma_tf32(d, dah, dbl, idesc, 1u);
+        mma_tf32(d, dal, dbh, idesc, 1u);
+    }
+}
+
+// ======================================================================= NN
+template <int N>
+struct NNCfg {
+    static constexpr uint32_t B_STAGE = N * 128;
+    static constexpr uint32_t STAGE = 2 * A_STAGE + 2 * B_STAGE;
+    static constexpr int S = (200 * 1024) / STAGE > 6 ? 6 : (200 * 1024) / STAGE;
+    static constexpr uint32_t SMEM = S * STAGE + 1024 + sizeof(Bars<S>) + 64;
+};
+
+template <int N>
+__global__ void __launch_bounds__(NTHR, 1)
+    tc_nn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBh,
+                 const __grid_constant__ CUtensorMap tmBl, int64_t m, int n, float *__restrict__ Y, int64_t ldy,
+                 int *__restrict__ status) {
+    using C = NNCfg<N>;
+    constexpr int S = C::S;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *sA = base;                    // raw fp32, split in place to hi
+    uint8_t *sAl = sA + S * A_STAGE;       // lo
+    uint8_t *sBh = sAl + S * A_STAGE;
+    uint8_t *sBl = sBh + S * C::B_STAGE;
+    Bars<S> *bar = reinterpret_cast<Bars<S> *>(sBl + S * C::B_STAGE);
+    volatile int *abort_flag = &bar->abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t ntiles = (m + TM - 1) / TM;
+    const int nkb = (n + TBK - 1) / TBK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; s++) {
+            mbar_init(&bar->full[s], 1);
+            mbar_init(&bar->split[s], NSPLIT);
+            mbar_init(&bar->empty[s], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&bar->acc_full[b], 1);
+            mbar_init(&bar->acc_empty[b], NEPI);
+        }
+        bar->abort_flag = 0;
+        mbar_fence_init();
+    }
+    if (warp == 1) tmem_alloc(&bar->tmem, TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = bar->tmem;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            tma_prefetch_desc(&tmA);
+            tma_prefetch_desc(&tmBh);
+            tma_prefetch_desc(&tmBl);
+            uint32_t g = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x)
+                for (int kb = 0; kb < nkb; kb++, g++) {
+                    const int s = g % S;
+                    if (!(ok = wait_ok(&bar->empty[s], ((g / S) & 1) ^ 1, abort_flag))) break;
+                    mbar_arrive_expect_tx(&bar->full[s], A_STAGE + 2 * C::B_STAGE);
+                    tma_load_2d(sA + s * A_STAGE, &tmA, kb * TBK, (int32_t)(t * TM), &bar->full[s]);
+                    tma_load_2d(sBh + s * C::B_STAGE, &tmBh, kb * TBK, 0, &bar->full[s]);
+                    tma_load_2d(sBl + s * C::B_STAGE, &tmBl, kb * TBK, 0, &bar->full[s]);
+                }
+            for (uint32_t k = g > (uint32_t)S ? g - S : 0; k < g; k++) mbar_wait(&bar->full[k % S], (k / S) & 1);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            uint32_t g = 0, it = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x, it++) {
+                const uint32_t b = it & 1;
+                if (!(ok = wait_ok(&bar->acc_empty[b], ((it >> 1) & 1) ^ 1, abort_flag))) break;
+                tc_fence_after();
+                const uint32_t d = tmem + b * ACC_STRIDE;
+                for (int kb = 0; kb < nkb; kb++, g++) {
+                    const int s = g % S;
+                    if (!(ok = wait_ok(&bar->split[s], (g / S) & 1, abort_flag))) break;
+                    tc_fence_after();
+                    mma_stage<N>(d, sA + s * A_STAGE, sAl + s * A_STAGE, sBh + s * C::B_STAGE, sBl + s * C::B_STAGE,
+                                 kb == 0);
+                    mma_commit(&bar->empty[s]);
+                }
+                if (ok) mma_commit(&bar->acc_full[b]);
+            }
+        }
+    } else if (warp < EPI_WARP0) {
+        const int wt = threadIdx.x - 64;
+        uint32_t g = 0;
+        bool ok = true;
+        for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x)
+            for (int kb = 0; kb < nkb; kb++, g++) {
+                const int s = g % S;
+                if (!(ok = wait_ok(&bar->full[s], (g / S) & 1, abort_flag))) break;
+                float4 *a = reinterpret_cast<float4 *>(sA + s * A_STAGE);
+                float4 *lo = reinterpret_cast<float4 *>(sAl + s * A_STAGE);
+#pragma unroll
+                for (int e = 0; e < (int)(A_STAGE / 16) / NSPLIT; e++) {
+                    const int idx = wt + e * NSPLIT;
+                    const float4 v = a[idx];
+                    float4 h, l;
+                    split4(&v.x, h, l);
+                    a[idx] = h;
+                    lo[idx] = l;
+                }
+                fence_proxy_async_smem();
+                mbar_arrive(&bar->split[s]);
+            }
+    } else {
+        const int q = warp & 3;
+        uint32_t it = 0;
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, it++) {
+            const uint32_t b = it & 1;
+            if (!wait_ok(&bar->acc_full[b], (it >> 1) & 1, abort_flag)) break;
+            tc_fence_after();
+            const int64_t row = t * TM + q * 32 + lane;
+#pragma unroll
+            for (int c0 = 0; c0 < N; c0 += 32) {
+                float v[32];
+                tmem_ld32(tmem + b * ACC_STRIDE + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+                if (row < m) {
+                    float *dst = Y + row * ldy + c0;
+                    if (c0 + 32 <= N && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+#pragma unroll
+                        for (int j = 0; j < 32; j += 4)
+                            *reinterpret_cast<float4 *>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; j++)
+                            if (c0 + j < N) dst[j] = v[j];
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&bar->acc_empty[b]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, TMEM_COLS);
+    }
+    if (threadIdx.x == 0 && bar->abort_flag) atomicOr(status, (int)ST_TIMEOUT);
+}
+
+// ======================================================================= TN
+// Tile t = (chunk, column tile): D (128 columns of A x N) = sum over the chunk's
+// rows r of A[r][c] Q[r][j].  Raw A and Q stages land unswizzled (row-major
+// 32 x 128 and 32 x N); workers write their tf32 hi/lo parts transposed into
+// the K-major swizzled layout (rows = column index of A or Q, K = row of A).
+template <int N>
+struct TNCfg {
+    static constexpr uint32_t RAW_A = 32 * TM * 4;     // 16 KB
+    static constexpr uint32_t RAW_Q = 32 * N * 4;
+    static constexpr uint32_t RAW = RAW_A + RAW_Q;
+    static constexpr uint32_t SPL_B = N * 128;
+    static constexpr uint32_t SPL = 2 * A_STAGE + 2 * SPL_B;
+    static constexpr int SR = 3;  // raw stages
+    static constexpr int SS = 2;  // split stages
+    static constexpr uint32_t SMEM = SR * RAW + SS * SPL + 1024 + sizeof(Bars<SR + SS>) + 64;
+};
+
+template <int N>
+__global__ void __launch_bounds__(NTHR, 1)
+    tc_tn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmQ, int64_t rows,
+                 int ncols, int64_t rpc, int nchunks, float *__restrict__ part, int *__restrict__ status) {
+    using C = TNCfg<N>;
+    constexpr int SR = C::SR, SS = C::SS;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *sSplit = base;                 // SS x (Ahi, Alo, Qhi, Qlo), 1024-aligned pieces
+    uint8_t *sRaw = base + SS * C::SPL;     // SR x (rawA, rawQ)
+    // barrier roles: full[0..SR) raw landed, split[0..SS) split ready, empty[0..SR) raw free,
+    // empty[SR..SR+SS) split buffer free (MMA done)
+    Bars<SR + SS> *bar = reinterpret_cast<Bars<SR + SS> *>(sRaw + SR * C::RAW);
+    volatile int *abort_flag = &bar->abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntn = (ncols + TM - 1) / TM;
+    const int64_t ntiles = (int64_t)ntn * nchunks;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < SR; s++) {
+            mbar_init(&bar->full[s], 1);
+            mbar_init(&bar->empty[s], NSPLIT);
+        }
+        for (int s = 0; s < SS; s++) {
+            mbar_init(&bar->split[s], NSPLIT);
+            mbar_init(&bar->empty[SR + s], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&bar->acc_full[b], 1);
+            mbar_init(&bar->acc_empty[b], NEPI);
+        }
+        bar->abort_flag = 0;
+        mbar_fence_init();
+    }
+    if (warp == 1) tmem_alloc(&bar->tmem, TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = bar->tmem;
+
+    auto tile_rows = [&](int64_t t, int64_t &r0, int64_t &r1, int &c0) {
+        const int64_t chunk = t / ntn;
+        c0 = (int)(t % ntn) * TM;
+        r0 = chunk * rpc;
+        r1 = r0 + rpc < rows ? r0 + rpc : rows;
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            tma_prefetch_desc(&tmA);
+            tma_prefetch_desc(&tmQ);
+            uint32_t g = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
+                int64_t r0, r1;
+                int c0;
+                tile_rows(t, r0, r1, c0);
+                const int nkb = (int)((r1 - r0 + TBK - 1) / TBK);
+                for (int kb = 0; kb < nkb; kb++, g++) {
+                    const int s = g % SR;
+                    if (!(ok = wait_ok(&bar->empty[s], ((g / SR) & 1) ^ 1, abort_flag))) break;
+                    uint8_t *raw = sRaw + s * C::RAW;
+                    mbar_arrive_expect_tx(&bar->full[s], C::RAW);
+                    tma_load_2d(raw, &tmA, c0, (int32_t)(r0 + kb * TBK), &bar->full[s]);
+                    tma_load_2d(raw + C::RAW_A, &tmQ, 0, (int32_t)(r0 + kb * TBK), &bar->full[s]);
+                }
+            }
+            for (uint32_t k = g > (uint32_t)SR ? g - SR : 0; k < g; k++) mbar_wait(&bar->full[k % SR], (k / SR) & 1);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            uint32_t g = 0, it = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x, it++) {
+                int64_t r0, r1;
+                int c0;
+                tile_rows(t, r0, r1, c0);
+                const int nkb = (int)((r1 - r0 + TBK - 1) / TBK);
+                const uint32_t b = it & 1;
+                if (!(ok = wait_ok(&bar->acc_empty[b], ((it >> 1) & 1) ^ 1, abort_flag))) break;
+                tc_fence_after();
+                const uint32_t d = tmem + b * ACC_STRIDE;
+                for (int kb = 0; kb < nkb; kb++, g++) {
+                    const int s = g % SS;
+                    if (!(ok = wait_ok(&bar->split[s], (g / SS) & 1, abort_flag))) break;
+                    tc_fence_after();
+                    uint8_t *sp = sSplit + s * C::SPL;
+                    mma_stage<N>(d, sp, sp + A_STAGE, sp + 2 * A_STAGE, sp + 2 * A_STAGE + C::SPL_B, kb == 0);
+                    mma_commit(&bar->empty[SR + s]);
+                }
+                if (ok) mma_commit(&bar->acc_full[b]);
+            }
+        }
+    } else if (warp < EPI_WARP0) {
+        const int wt = threadIdx.x - 64;
+        uint32_t g = 0;
+        bool ok = true;
+        for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
+            int64_t r0, r1;
+            int c0;
+            tile_rows(t, r0, r1, c0);
+            const int nkb = (int)((r1 - r0 + TBK - 1) / TBK);
+            for (int kb = 0; kb < nkb; kb++, g++) {
+                const int sr = g % SR, ss = g % SS;
+                if (!(ok = wait_ok(&bar->full[sr], (g / SR) & 1, abort_flag))) break;
+                if (!(ok = wait_ok(&bar->empty[SR + ss], ((g / SS) & 1) ^ 1, abort_flag))) break;
+                const float *rawA = reinterpret_cast<const float *>(sRaw + sr * C::RAW);
+                const float *rawQ = reinterpret_cast<const float *>(sRaw + sr * C::RAW + C::RAW_A);
+                uint8_t *sp = sSplit + ss * C::SPL;
+                const int valid = (int)(r1 - (r0 + (int64_t)kb * TBK));  // rows of this stage inside the chunk
+                {   // A: thread -> column i, 16 consecutive K (= rows)
+                    const int i = wt & (TM - 1), kh = wt >> 7;
+#pragma unroll
+                    for (int c4 = 0; c4 < 4; c4++) {
+                        float x[4];
+#pragma unroll
+                        for (int e = 0; e < 4; e++) {
+                            const int k = kh * 16 + c4 * 4 + e;
+                            x[e] = k < valid ? rawA[k * TM + i] : 0.f;
+                        }
+                        float4 h, l;
+                        split4(x, h, l);
+                        const uint32_t off = kmajor_off(i, kh * 4 + c4);
+                        *reinterpret_cast<float4 *>(sp + off) = h;
+                        *reinterpret_cast<float4 *>(sp + A_STAGE + off) = l;
+                    }
+                }
+                for (int idx = wt; idx < N * 8; idx += NSPLIT) {  // Q: (column j, 4-row chunk cc)
+                    const int j = idx % N, cc = idx / N;
+                    float x[4];
+#pragma unroll
+                    for (int e = 0; e < 4; e++) x[e] = rawQ[(cc * 4 + e) * N + j];
+                    float4 h, l;
+                    split4(x, h, l);
+                    const uint32_t off = kmajor_off(j, cc);
+                    *reinterpret_cast<float4 *>(sp + 2 * A_STAGE + off) = h;
+                    *reinterpret_cast<float4 *>(sp + 2 * A_STAGE + C::SPL_B + off) = l;
+                }
+                fence_proxy_async_smem();
+                mbar_arrive(&bar->empty[sr]);   // raw stage consumed
+                mbar_arrive(&bar->split[ss]);   // split stage ready
+            }
+        }
+    } else {
+        const int q = warp & 3;
+        uint32_t it = 0;
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, it++) {
+            int64_t r0, r1;
+            int c0;
+            tile_rows(t, r0, r1, c0);
+            const int64_t chunk = t / ntn;
+            const uint32_t b = it & 1;
+            if (!wait_ok(&bar->acc_full[b], (it >> 1) & 1, abort_flag)) break;
+            tc_fence_after();
+            const int c = c0 + q * 32 + lane;
+#pragma unroll
+            for (int j0 = 0; j0 < N; j0 += 32) {
+                float v[32];
+                tmem_ld32(tmem + b * ACC_STRIDE + ((uint32_t)(q * 32) << 16) + (uint32_t)j0, v);
+                if (c < ncols) {
+                    float *dst = part + (chunk * ncols + c) * (int64_t)N + j0;
+                    if (j0 + 32 <= N) {
+#pragma unroll
+                        for (int j = 0; j < 32; j += 4)
+                            *reinterpret_cast<float4 *>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; j++)
+                            if (j0 + j < N) dst[j] = v[j];
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&bar->acc_empty[b]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, TMEM_COLS);
+    }
+    if (threadIdx.x == 0 && bar->abort_flag) atomicOr(status, (int)ST_TIMEOUT);
+}
+
+// ==================================================================== helpers
+// th / tl (N x ldt) = tf32 split of Z^T, Z rows x cols row-major (ldz); zero beyond.
+__global__ void split_transpose_kernel(const float *__restrict__ Z, int64_t rows, int cols, int64_t ldz, int N,
+                                       float *__restrict__ th, float *__restrict__ tl, int64_t ldt) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)N * ldt) return;
+    const int64_t j = idx / ldt, r = idx % ldt;
+    const float x = (j < cols && r < rows) ? Z[r * ldz + j] : 0.f;
+    const float h = rna_tf32(x);
+    th[idx] = h;
+    tl[idx] = rna_tf32(x - h);
+}
+
+// C[i * ldc + j] = sum_{s < chunks} part[s][i][j] (N x L per chunk), in chunk order
+__global__ void sum_chunks_kernel(const float *__restrict__ part, int64_t chunks, int64_t N, int64_t L,
+                                  float *__restrict__ C, int64_t ldc) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * L) return;
+    const int64_t stride = N * L;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    int64_t c = 0;
+    for (; c + 4 <= chunks; c += 4) {
+        s0 += part[(c + 0) * stride + idx];
+        s1 += part[(c + 1) * stride + idx];
+        s2 += part[(c + 2) * stride + idx];
+        s3 += part[(c + 3) * stride + idx];
+    }
+    for (; c < chunks; c++) s0 += part[c * stride + idx];
+    C[(idx / L) * ldc + idx % L] = (s0 + s1) + (s2 + s3);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// Row-major fp32 matrix rows x cols (leading dimension ld elements) as a TMA map
+// with a box of box_rows x box_cols; swizzled (box_cols must be 32) or plain.
+bool make_map(CUtensorMap *map, const float *ptr, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+              int box_cols, bool swizzle) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    if ((reinterpret_cast<uintptr_t>(ptr) & 15) || ((ld * 4) & 15)) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+    cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(ptr), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    }
+    return n;
+}
+
+template <int N>
+cudaError_t launch_nn(const CUtensorMap &a, const CUtensorMap &bh, const CUtensorMap &bl, int64_t m, int n, float *Y,
+                      int64_t ldy, int *status, cudaStream_t s) {
+    using C = NNCfg<N>;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(tc_nn_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        attr = true;
+    }
+    const int64_t tiles = ceil_div(m, TM);
+    const int grid = (int)(tiles < num_sms() ? tiles : num_sms());
+    tc_nn_kernel<N><<<grid, NTHR, C::SMEM, s>>>(a, bh, bl, m, n, Y, ldy, status);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t launch_tn(const CUtensorMap &a, const CUtensorMap &qm, int64_t rows, int ncols, int64_t rpc, int nchunks,
+                      float *part, int *status, cudaStream_t s) {
+    using C = TNCfg<N>;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(tc_tn_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        attr = true;
+    }
+    const int64_t tiles = ceil_div(ncols, TM) * nchunks;
+    const int grid = (int)(tiles < num_sms() ? tiles : num_sms());
+    tc_tn_kernel<N><<<grid, NTHR, C::SMEM, s>>>(a, qm, rows, ncols, rpc, nchunks, part, status);
+    note_launch();
+    return cudaGetLastError();
+}
+
+struct TNSplit {
+    int64_t rpc;
+    int chunks;
+};
+
+TNSplit tn_split(int64_t rows, int ncols) {
+    const int64_t ntn = ceil_div(ncols, TM);
+    const int64_t target = 2 * (int64_t)num_sms();
+    int64_t chunks = ceil_div(target, ntn);
+    const int64_t maxc = ceil_div(rows, 4 * TBK);  // at least four stages per tile
+    if (chunks > maxc) chunks = maxc;
+    if (chunks < 1) chunks = 1;
+    const int64_t rpc = round_up(ceil_div(rows, chunks), TBK);
+    return {rpc, (int)ceil_div(rows, rpc)};
+}
+
+}  // namespace
+
+bool tc_available() { return encode_fn() != nullptr; }
+
+cudaError_t tc_split_transpose(const float *Z, int64_t rows, int cols, int64_t ldz, int N, float *th, float *tl,
+                               int64_t ldt, cudaStream_t s) {
+    const int64_t total = (int64_t)N * ldt;
+    split_transpose_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, s>>>(Z, rows, cols, ldz, N, th, tl, ldt);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t tc_gemm_nn(int64_t m, int n, int N, const float *A, int64_t lda, const float *Bth, const float *Btl,
+                       int64_t ldb, float *Y, int64_t ldy, int *status, cudaStream_t s) {
+    if (N % 16 || N < 16 || N > 128) return cudaErrorInvalidValue;
+    CUtensorMap ma, mbh, mbl;
+    if (!make_map(&ma, A, m, n, lda, TM, TBK, true) || !make_map(&mbh, Bth, N, n, ldb, N, TBK, true) ||
+        !make_map(&mbl, Btl, N, n, ldb, N, TBK, true))
+        return cudaErrorInvalidValue;
+    switch (N) {
+        case 16: return launch_nn<16>(ma, mbh, mbl, m, n, Y, ldy, status, s);
+        case 32: return launch_nn<32>(ma, mbh, mbl, m, n, Y, ldy, status, s);
+        case 48: return launch_nn<48>(ma, mbh, mbl, m, n, Y, ldy, status, s);
+        case 64: return launch_nn<64>(ma, mbh, mbl, m, n, Y, ldy, status, s);
+        case 80: return launch_nn<80>(ma, mbh, mbl, m, n, Y, ldy, status, s);
+        case 96: return launch_nn<96>(ma, mbh, mbl, m, n, Y, ldy, status, s);
+        case 112: return launch_nn<112>(ma, mbh, mbl, m, n, Y, ldy, status, s);
+        case 128: return launch_nn<128>(ma, mbh, mbl, m, n, Y, ldy, status, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+int64_t tc_gemm_tn_partials(int64_t rows, int ncols, int N) {
+    const TNSplit sp = tn_split(rows, ncols);
+    return (int64_t)sp.chunks * ncols * N;
+}
+
+cudaError_t tc_gemm_tn(int64_t rows, int ncols, int N, const float *A, int64_t lda, const float *Q, int64_t ldq,
+                       float *C, int64_t ldc, float *part, int64_t part_elems, int *status, cudaStream_t s) {
+    if (N % 16 || N < 16 || N > 128) return cudaErrorInvalidValue;
+    const TNSplit sp = tn_split(rows, ncols);
+    if (part == nullptr || part_elems < (int64_t)sp.chunks * ncols * N) return cudaErrorInvalidValue;
+    CUtensorMap ma, mq;
+    if (!make_map(&ma, A, rows, ncols, lda, TBK, TM, false) || !make_map(&mq, Q, rows, N, ldq, TBK, N, false))
+        return cudaErrorInvalidValue;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (N) {
+        case 16: e = launch_tn<16>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, s); break;
+        case 32: e = launch_tn<32>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, s); break;
+        case 48: e = launch_tn<48>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, s); break;
+        case 64: e = launch_tn<64>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, s); break;
+        case 80: e = launch_tn<80>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, s); break;
+        case 96: e = launch_tn<96>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, s); break;
+        case 112: e = launch_tn<112>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, s); break;
+        case 128: e = launch_tn<128>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, s); break;
+    }
+    if (e != cudaSuccess) return e;
+    const int64_t total = (int64_t)ncols * N;
+    sum_chunks_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, s>>>(part, sp.chunks, ncols, N, C, ldc);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace gbr

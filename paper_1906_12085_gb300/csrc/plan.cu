@@ -41,6 +41,12 @@ struct rsvd_plan {
     double *lam = nullptr, *Vfull = nullptr, *sig = nullptr;
     int *status = nullptr, *Kdev = nullptr;
     int last_count = 0;
+    // tensor-core path (float32): transposed tf32 split of the small operand, split-K partials
+    bool tc = false;
+    int64_t ldt = 0;          // leading dimension of Bth / Btl (>= max(n, wide), multiple of 4)
+    float *Bth = nullptr, *Btl = nullptr;
+    float *tcpart = nullptr;
+    int64_t tcpart_elems = 0;
     // tracing: event pairs recorded around stage groups while profiling is on
     bool prof = false;
     std::vector<cudaEvent_t> ev;
@@ -109,6 +115,16 @@ void carve(rsvd_plan *P, Carver &c) {
     P->sig = (double *)c.take(sizeof(double) * (n > sq ? n : sq));
     P->status = (int *)c.take(sizeof(int));
     P->Kdev = (int *)c.take(2 * sizeof(int));
+    if (P->tc) {
+        P->ldt = round_up(n > P->wide ? n : P->wide, 4);
+        P->Bth = (float *)c.take(sizeof(float) * P->lp * P->ldt);
+        P->Btl = (float *)c.take(sizeof(float) * P->lp * P->ldt);
+        int64_t te = tc_gemm_tn_partials(m, (int)n, P->lp);
+        const int64_t t2 = tc_gemm_tn_partials(m, P->lp, P->lp);
+        if (t2 > te) te = t2;
+        P->tcpart_elems = te;
+        P->tcpart = (float *)c.take(sizeof(float) * te);
+    }
 }
 
 // Records a pair of events around a stage group when tracing is enabled.
@@ -147,6 +163,46 @@ template <typename T> constexpr double unit_roundoff();
 template <> constexpr double unit_roundoff<float>() { return FLT_EPSILON / 2; }
 template <> constexpr double unit_roundoff<double>() { return DBL_EPSILON / 2; }
 
+// Products with the skinny operand on the right.  The float32 plan uses the
+// tcgen05 3xTF32 kernels when TMA can address the operands (16-byte aligned
+// pointers and rows) and the CUDA-core kernels otherwise; float64 always uses
+// the CUDA-core kernels.
+inline bool al16(const void *p, int64_t ld, size_t es) {
+    return (reinterpret_cast<uintptr_t>(p) & 15) == 0 && ((ld * (int64_t)es) & 15) == 0;
+}
+
+// Y (rows x N) = X (rows x K) B, B row-major K x N (ldb), N = lp.
+template <typename T>
+cudaError_t prod_nn(rsvd_plan *P, int64_t rows, int64_t K, const T *X, int64_t ldx, const T *B, int64_t ldb, T *Y,
+                    int64_t ldy) {
+    if constexpr (sizeof(T) == 4) {
+        if (P->tc && al16(X, ldx, 4) && (ldy % 4) == 0 && K <= P->ldt) {
+            cudaError_t e = tc_split_transpose(B, K, P->lp, ldb, P->lp, P->Bth, P->Btl, P->ldt, P->stream);
+            if (e == cudaSuccess)
+                e = tc_gemm_nn(rows, (int)K, P->lp, X, ldx, P->Bth, P->Btl, P->ldt, Y, ldy, P->status, P->stream);
+            if (e != cudaErrorInvalidValue) return e;
+            cudaGetLastError();
+        }
+    }
+    return gemm_nn<T>(rows, P->lp, K, X, ldx, B, ldb, Y, ldy, P->stream);
+}
+
+// C (ncols x N) = X^T Q with X rows x ncols (ldx), Q rows x N (ldq), N = lp.
+template <typename T>
+cudaError_t prod_tn(rsvd_plan *P, int64_t rows, int64_t ncols, const T *X, int64_t ldx, const T *Q, int64_t ldq,
+                    T *C, int64_t ldc) {
+    if constexpr (sizeof(T) == 4) {
+        if (P->tc && al16(X, ldx, 4) && al16(Q, ldq, 4) &&
+            tc_gemm_tn_partials(rows, (int)ncols, P->lp) <= P->tcpart_elems) {
+            cudaError_t e = tc_gemm_tn(rows, (int)ncols, P->lp, X, ldx, Q, ldq, C, ldc, P->tcpart, P->tcpart_elems,
+                                       P->status, P->stream);
+            if (e != cudaErrorInvalidValue) return e;
+            cudaGetLastError();
+        }
+    }
+    return gemm_tn<T>(rows, ncols, P->lp, X, ldx, Q, ldq, C, ldc, (T *)P->part, P->part_elems, P->stream);
+}
+
 // CholeskyQR2 of X (rows x w, ld): Qo = X R^{-1} with R = R2 R1 (written to Rt
 // when want_r).  R1 from chol(X^T X); Q1 = X R1^{-1} into Tmp; R2 from
 // chol(Q1^T Q1); Qo = Q1 R2^{-1}.
@@ -155,12 +211,17 @@ rsvd_status cqr2(rsvd_plan *P, const T *X, int64_t rows, int w, int ld, T *Qo, T
     cudaStream_t s = P->stream;
     T *G = (T *)P->G, *Ric = (T *)P->Rinv_c, *part = (T *)P->part;
     const double u = unit_roundoff<T>();
-    CK(gemm_tn<T>(rows, ld, ld, X, ld, X, ld, G, ld, part, P->part_elems, s));
-    CK(chol_inv<T, T>(G, ld, w, rows, u, P->R1, P->R1i, Ric, ld, P->status, s));
-    CK(gemm_nn<T>(rows, ld, ld, X, ld, Ric, ld, Tmp, ld, s));
-    CK(gemm_tn<T>(rows, ld, ld, Tmp, ld, Tmp, ld, G, ld, part, P->part_elems, s));
-    CK(chol_inv<T, T>(G, ld, w, rows, u, P->R2, P->R2i, Ric, ld, P->status, s));
-    CK(gemm_nn<T>(rows, ld, ld, Tmp, ld, Ric, ld, Qo, ld, s));
+    const bool skinny = ld == P->lp;  // the l-wide blocks of the randomized solver
+    if (skinny) CK(prod_tn<T>(P, rows, ld, X, ld, X, ld, G, ld));
+    else CK(gemm_tn<T>(rows, ld, ld, X, ld, X, ld, G, ld, part, P->part_elems, s));
+    CK(chol_inv<T, T, T>(G, ld, w, rows, u, P->R1, P->R1i, Ric, ld, P->status, s));
+    if (skinny) CK(prod_nn<T>(P, rows, ld, X, ld, Ric, ld, Tmp, ld));
+    else CK(gemm_nn<T>(rows, ld, ld, X, ld, Ric, ld, Tmp, ld, s));
+    if (skinny) CK(prod_tn<T>(P, rows, ld, Tmp, ld, Tmp, ld, G, ld));
+    else CK(gemm_tn<T>(rows, ld, ld, Tmp, ld, Tmp, ld, G, ld, part, P->part_elems, s));
+    CK(chol_inv<T, T, T>(G, ld, w, rows, u, P->R2, P->R2i, Ric, ld, P->status, s));
+    if (skinny) CK(prod_nn<T>(P, rows, ld, Tmp, ld, Ric, ld, Qo, ld));
+    else CK(gemm_nn<T>(rows, ld, ld, Tmp, ld, Ric, ld, Qo, ld, s));
     if (want_r) CK(trmm_upper(P->R2, P->R1, P->Rt, w, s));
     return RSVD_OK;
 }
@@ -180,7 +241,6 @@ rsvd_status run_rsvd(rsvd_plan *P, T *A, const T *Omega, double *S, T *U, T *V) 
     const int l = P->l, lp = P->lp, k = P->k;
     T *Y = (T *)P->Y, *Q = (T *)P->Qb, *Tmp = (T *)P->Tmp;
     T *Ob = (T *)P->Ob, *Z = (T *)P->Z, *Qz = (T *)P->Qz, *Tn = (T *)P->Tn, *Vt = (T *)P->Vt, *Tmpn = (T *)P->Tmpn;
-    T *part = (T *)P->part;
     rsvd_status st;
     {
         Span sp(P, RSVD_STAGE_CENTER);
@@ -189,7 +249,7 @@ rsvd_status run_rsvd(rsvd_plan *P, T *A, const T *Omega, double *S, T *U, T *V) 
     CK(copy2d<T, T>(Omega, l, Ob, lp, n, l, lp, s));                          // G padded to lp columns
     {
         Span sp(P, RSVD_STAGE_AX);
-        CK(gemm_nn<T>(m, lp, n, A, n, Ob, lp, Y, lp, s));                     // H(0) = A G
+        CK(prod_nn<T>(P, m, n, A, n, Ob, lp, Y, lp));                          // H(0) = A G
     }
     {
         Span sp(P, RSVD_STAGE_ORTH);
@@ -198,7 +258,7 @@ rsvd_status run_rsvd(rsvd_plan *P, T *A, const T *Omega, double *S, T *U, T *V) 
     for (int it = 0; it < P->q; it++) {                                      // H(i) = A (A^T H(i-1))
         {
             Span sp(P, RSVD_STAGE_ATX);
-            CK(gemm_tn<T>(m, n, lp, A, n, Q, lp, Z, lp, part, P->part_elems, s));
+            CK(prod_tn<T>(P, m, n, A, n, Q, lp, Z, lp));
         }
         {
             Span sp(P, RSVD_STAGE_ORTH);
@@ -206,7 +266,7 @@ rsvd_status run_rsvd(rsvd_plan *P, T *A, const T *Omega, double *S, T *U, T *V) 
         }
         {
             Span sp(P, RSVD_STAGE_AX);
-            CK(gemm_nn<T>(m, lp, n, A, n, Qz, lp, Y, lp, s));
+            CK(prod_nn<T>(P, m, n, A, n, Qz, lp, Y, lp));
         }
         {
             Span sp(P, RSVD_STAGE_ORTH);
@@ -215,7 +275,7 @@ rsvd_status run_rsvd(rsvd_plan *P, T *A, const T *Omega, double *S, T *U, T *V) 
     }
     {
         Span sp(P, RSVD_STAGE_ATX);
-        CK(gemm_tn<T>(m, n, lp, A, n, Q, lp, Tn, lp, part, P->part_elems, s));  // T = A^T Q  (= B^T)
+        CK(prod_tn<T>(P, m, n, A, n, Q, lp, Tn, lp));                           // T = A^T Q  (= B^T)
     }
     T *UR = (T *)P->UR, *W = (T *)P->Wm;
     {
@@ -313,6 +373,7 @@ rsvd_status rsvd_plan_create(rsvd_plan_t *plan, int64_t m, int64_t n, int k, int
     P->wide = P->lp > P->nx ? P->lp : P->nx;
     P->dtype = dtype;
     P->stream = (cudaStream_t)cuda_stream;
+    P->tc = dtype == RSVD_F32 && P->lp <= 128 && tc_available();
     Carver c;
     carve(P, c);
     P->ws_bytes = c.off;
@@ -360,6 +421,7 @@ rsvd_status rsvd_plan_sync(rsvd_plan_t P) {
     if (cudaMemsetAsync(P->status, 0, sizeof(int), P->stream) != cudaSuccess) return RSVD_ERR_CUDA;
     if (st & ST_CHOL) return RSVD_ERR_CHOL;
     if (st & ST_NOCONV) return RSVD_ERR_NOCONV;
+    if (st & ST_TIMEOUT) return RSVD_ERR_TIMEOUT;
     return RSVD_OK;
 }
 
