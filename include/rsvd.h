@@ -146,6 +146,37 @@ rsvd_status svd_truncated_krylov(rsvd_plan_t plan, void *A, const void *v1, int 
  */
 rsvd_status pca_threshold(rsvd_plan_t plan, double t, int *K);
 
+/*
+ * svd_exact_gram_static: svd_exact with method RSVD_EXACT_GRAM for callers that
+ * cannot allocate device memory.  The paper has no counterpart: this is an
+ * interface addition, not a method.
+ *
+ * Who needs it: code that runs where device memory is owned by someone else
+ * or where cudaMalloc / cudaFree are not allowed -- a plugin inside a host
+ * framework that hands out memory only from its own pool, a process under a
+ * hard device-memory budget fixed at start-up, or a latency-critical loop
+ * that must not hit cudaMalloc's and cudaFree's implicit device-wide
+ * synchronisation.  Such a caller still passes A, S, U and V; the entry point
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
+ *
+ * Scratch: a file-scope 12 MiB static device array.  Every GPU that loads the
+ * library holds it until process exit.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the one array, which keeps the previous call's contents: the status word is
+ * cleared at the start of every call, and calls that overlap on the GPU (two
+ * streams, two host threads) race and must be serialised by the caller.
+ *
+ * Arguments: A m x n row-major (centred in place, as svd_exact does), S n
+ * doubles, U m x n, V n x n (float64 for RSVD_F64, float32 for RSVD_F32),
+ * cuda_stream a cudaStream_t (may be NULL).  Limit: n <= 64 (any m >= n);
+ * larger n returns RSVD_ERR_UNSUPPORTED.  The call synchronises the stream
+ * and returns RSVD_OK, RSVD_ERR_NOCONV (Jacobi sweep cap), RSVD_ERR_ARG or
+ * RSVD_ERR_CUDA.  Results equal svd_exact's Gram route on the same input.
+ */
+rsvd_status svd_exact_gram_static(void *A, int64_t m, int64_t n, rsvd_dtype dtype, double *S, void *U, void *V,
+                                  void *cuda_stream);
+
 /* Host copy of ||A||_F^2 (after centring) recorded by the last solve; synchronises. */
 rsvd_status rsvd_plan_fro2(rsvd_plan_t plan, double *fro2);
 

@@ -22,7 +22,7 @@ __all__ = [
     "rsvd_plan_create", "rsvd_plan_destroy", "rsvd_plan_workspace_bytes", "rsvd_plan_set_flags",
     "rsvd_plan_sync", "rsvd", "svd_exact", "svd_truncated_krylov", "pca_threshold", "rsvd_plan_fro2",
     "rsvd_status_string", "check", "rsvd_plan_profile", "rsvd_plan_profile_read", "rsvd_launch_count",
-    "STAGES",
+    "STAGES", "svd_exact_gram_static",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -76,6 +76,8 @@ def lib() -> ctypes.CDLL:
     L.rsvd_plan_profile_read.argtypes = [vp, dp, ctypes.POINTER(i32), i32]
     L.rsvd_launch_count.argtypes = []
     L.rsvd_launch_count.restype = ctypes.c_uint64
+    L.svd_exact_gram_static.argtypes = [vp, i64, i64, i32, vp, vp, vp, vp]
+    L.svd_exact_gram_static.restype = i32
     L.rsvd_status_string.argtypes = [i32]
     L.rsvd_status_string.restype = ctypes.c_char_p
     for f in ("rsvd_plan_create", "rsvd_plan_destroy", "rsvd_plan_set_flags", "rsvd_plan_sync", "rsvd",
@@ -219,3 +221,12 @@ def rsvd_plan_profile_read(plan: Plan) -> dict:
 
 def rsvd_launch_count() -> int:
     return int(lib().rsvd_launch_count())
+
+
+def svd_exact_gram_static(A, dtype: int, S, U, V, stream=None) -> int:
+    """Gram-route exact SVD with no device allocation (scratch in the library's static array).
+
+    For callers that cannot allocate device memory; see include/rsvd.h.
+    Synchronises the stream before returning."""
+    m, n = A.shape
+    return lib().svd_exact_gram_static(_ptr(A), m, n, int(dtype), _ptr(S), _ptr(U), _ptr(V), _stream(stream))
