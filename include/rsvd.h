@@ -127,11 +127,20 @@ rsvd_status svd_exact(rsvd_plan_t plan, void *A, int method, double *S, void *U,
 
 /*
  * Truncated SVD by Golub-Kahan-Lanczos bidiagonalisation with full
- * reorthogonalisation (classical Gram-Schmidt twice) for `steps` steps from
- * the unit start vector v1 (n floats for RSVD_F32, n doubles for RSVD_F64),
- * then the SVD of the steps x steps bidiagonal; returns the leading k Ritz
- * triplets.  S : k doubles; U : m x k; V : n x k.  Requires k <= steps <= n.
- * Returns RSVD_ERR_UNSUPPORTED until the Lanczos kernels are built.
+ * reorthogonalisation (classical Gram-Schmidt applied twice against every
+ * previous basis vector) for `steps` steps from the start vector v1 (n
+ * floats for RSVD_F32, n doubles for RSVD_F64; normalised internally):
+ *   u_j = (A v_j - beta_{j-1} u_{j-1}) reorthogonalised / alpha_j,
+ *   v_{j+1} = (A^T u_j - alpha_j v_j) reorthogonalised / beta_j,
+ * then the SVD of the steps x steps upper bidiagonal B (alpha on the
+ * diagonal, beta above) by one-sided Jacobi, B = X Sigma Y^T, and the leading
+ * k Ritz triplets: S k doubles, U = U_s X (m x k), V = V_s Y (n x k).
+ * This is the Krylov route of the library; the paper's own Krylov method
+ * (Sec. 3.1.1, a block power basis) is a different algorithm.
+ * Requires k <= steps <= n and steps <= 160 (RSVD_F32) / 112 (RSVD_F64)
+ * (RSVD_ERR_UNSUPPORTED otherwise).  The first call on a plan allocates the
+ * Lanczos workspace (steps x m + (steps+1) x n elements and small buffers)
+ * with cudaMalloc; later calls with no more steps reuse it.
  */
 rsvd_status svd_truncated_krylov(rsvd_plan_t plan, void *A, const void *v1, int steps,
                                  double *S, void *U, void *V);

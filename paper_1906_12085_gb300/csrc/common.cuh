@@ -19,6 +19,8 @@ enum StatusBits : int {
 
 // Largest l (or n for svd_exact) whose l x l working set fits one CTA's shared memory.
 constexpr int kSmallMaxF64 = 112;
+// Largest Lanczos step count whose bidiagonal SVD fits one CTA in float32.
+constexpr int kGklMaxStepsF32 = 160;
 
 // Count of kernel launches issued by the library (reported by rsvd_launch_count).
 void note_launch(int count = 1);
@@ -68,6 +70,12 @@ template <typename Ta, typename To>
 cudaError_t jacobi_osvd(const double *R, int l, int lp, double *sig, To *UR, To *W, int *status,
                         cudaStream_t s);
 
+// Float64 Rayleigh-quotient refinement of the singular values returned by
+// jacobi_osvd: sig[i] = u_i^T R w_i / (||u_i|| ||w_i||) (R upper triangular or
+// bidiagonal, l x l, ld l; UR, W ld lp).
+template <typename To>
+cudaError_t sv_refine(const double *R, int l, int lp, const To *UR, const To *W, double *sig, cudaStream_t s);
+
 // Cyclic (parallel-ordered) two-sided Jacobi eigen-decomposition of the n x n
 // symmetric float64 matrix G (ld n): lam descending (n doubles), V (n x n, ld n).
 cudaError_t jacobi_eig(const double *G, int n, double *lam, double *V, int *status, cudaStream_t s);
@@ -112,5 +120,22 @@ cudaError_t tc_gemm_nn(int64_t m, int n, int N, const float *A, int64_t lda, con
 cudaError_t tc_gemm_tn(int64_t rows, int ncols, int N, const float *A, int64_t lda, const float *Q, int64_t ldq,
                        float *C, int64_t ldc, float *part, int64_t part_elems, int *status, cudaStream_t s);
 int64_t tc_gemm_tn_partials(int64_t rows, int ncols, int N);
+
+// ------------------------------------------------------ Golub-Kahan-Lanczos
+// y = A v - beta[0] * uprev (beta / uprev may be NULL)
+template <typename T>
+cudaError_t gkl_gemv_n(const T *A, int64_t m, int n, int64_t lda, const T *v, const T *beta, const T *uprev, T *y,
+                       cudaStream_t s);
+// z = A^T u - alpha[0] * vprev (alpha / vprev may be NULL); part: gkl_gemv_chunks(m) * n float64 scratch
+template <typename T>
+cudaError_t gkl_gemv_t(const T *A, int64_t m, int n, int64_t lda, const T *u, const T *alpha, const T *vprev, T *z,
+                       double *part, cudaStream_t s);
+int64_t gkl_gemv_chunks(int64_t m);
+int64_t gkl_reorth_blocks(int64_t len);
+template <typename T>
+cudaError_t gkl_reorth_normalize(const T *Bt, int64_t ld, int cnt, T *w, int64_t len, T *coef, T *part, T *sq,
+                                 T *nrm, T *out, int *status, cudaStream_t s);
+template <typename T>
+cudaError_t gkl_bidiag(const T *alpha, const T *beta, int steps, double *B, cudaStream_t s);
 
 }  // namespace gbr

@@ -1,0 +1,323 @@
+// Golub-Kahan-Lanczos bidiagonalisation with full reorthogonalisation: the
+// HBM-bound kernels of svd_truncated_krylov.
+//
+// One step j (alpha, beta and every reorthogonalisation coefficient stay in
+// device memory; the host only launches):
+//   w  = A v_j - beta_{j-1} u_{j-1}          gemv_n     (one read of A)
+//   w -= U (U^T w), twice (CGS2)             multi_dot + multi_axpy (reads of U)
+//   alpha_j = ||w||, u_j = w / alpha_j       multi_axpy (norm fused) + scale_store
+//   z  = A^T u_j - alpha_j v_j               gemv_t + colsum_sub (one read of A)
+//   z -= V (V^T z), twice; beta_j = ||z||; v_{j+1} = z / beta_j
+// The Krylov bases are stored transposed (U^T: steps x m, V^T: (steps+1) x n)
+// so every basis vector is contiguous.
+#include "common.cuh"
+
+namespace gbr {
+namespace {
+
+constexpr int GT = 256;
+
+template <typename T> struct V4;
+template <> struct V4<float> { using type = float4; static constexpr int n = 4; };
+template <> struct V4<double> { using type = double2; static constexpr int n = 2; };
+
+template <typename T>
+__device__ __forceinline__ T warp_red(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// y[r] = A[r] . v - (beta ? beta[0] : 0) * uprev[r]; one warp per row, v staged in shared memory.
+template <typename T, bool VEC>
+__global__ void __launch_bounds__(GT) gemv_n_kernel(const T *__restrict__ A, int64_t m, int n, int64_t lda,
+                                                    const T *__restrict__ v, const T *__restrict__ beta,
+                                                    const T *__restrict__ uprev, T *__restrict__ y) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    T *vs = reinterpret_cast<T *>(sm_raw);
+    for (int c = threadIdx.x; c < n; c += GT) vs[c] = v[c];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (GT / 32);
+    const T b = beta ? beta[0] : T(0);
+    for (int64_t r = (int64_t)blockIdx.x * (GT / 32) + (threadIdx.x >> 5); r < m; r += warps) {
+        const T *row = A + r * lda;
+        T acc = T(0);
+        if constexpr (VEC) {
+            using V = typename V4<T>::type;
+            constexpr int E = V4<T>::n;
+#pragma unroll 4
+            for (int c = lane * E; c < n; c += 32 * E) {
+                const V a = *reinterpret_cast<const V *>(row + c);
+                const T *pa = reinterpret_cast<const T *>(&a);
+#pragma unroll
+                for (int e = 0; e < E; e++) acc += pa[e] * vs[c + e];
+            }
+        } else {
+            for (int c = lane; c < n; c += 32) acc += row[c] * vs[c];
+        }
+        acc = warp_red(acc);
+        if (lane == 0) y[r] = uprev ? acc - b * uprev[r] : acc;
+    }
+}
+
+// part[chunk][c] = sum over the chunk's rows of u[r] A[r][c]; block = (chunk, column block of GT*E columns).
+// Products are summed in the element type over 32-row groups and the group sums
+// in float64, so the 1M-row sums keep float64-level accumulation error at the
+// cost of one float64 add per 32 rows.
+template <typename T, bool VEC>
+__global__ void __launch_bounds__(GT) gemv_t_kernel(const T *__restrict__ A, int64_t m, int n, int64_t lda,
+                                                    const T *__restrict__ u, int64_t rpc, double *__restrict__ part) {
+    constexpr int E = VEC ? V4<T>::n : 1;
+    const int64_t r0 = (int64_t)blockIdx.x * rpc;
+    const int64_t r1 = min(m, r0 + rpc);
+    const int c0 = (blockIdx.y * GT + threadIdx.x) * E;
+    if (c0 >= n) return;
+    double acc[E];
+#pragma unroll
+    for (int e = 0; e < E; e++) acc[e] = 0.0;
+    for (int64_t g = r0; g < r1; g += 32) {
+        const int64_t ge = min(r1, g + 32);
+        T sub[E];
+#pragma unroll
+        for (int e = 0; e < E; e++) sub[e] = T(0);
+#pragma unroll 8
+        for (int64_t r = g; r < ge; r++) {
+            const T ur = u[r];
+            if constexpr (VEC) {
+                using V = typename V4<T>::type;
+                const V a = *reinterpret_cast<const V *>(A + r * lda + c0);
+                const T *pa = reinterpret_cast<const T *>(&a);
+#pragma unroll
+                for (int e = 0; e < E; e++) sub[e] += ur * pa[e];
+            } else {
+                sub[0] += ur * A[r * lda + c0];
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < E; e++) acc[e] += (double)sub[e];
+    }
+#pragma unroll
+    for (int e = 0; e < E; e++)
+        if (c0 + e < n) part[(int64_t)blockIdx.x * n + c0 + e] = acc[e];
+}
+
+// z[c] = sum_k part[k][c] - (alpha ? alpha[0] : 0) * vprev[c]; 8 row groups x 32 columns per block, fixed order
+template <typename T>
+__global__ void colsum_sub_kernel(const double *__restrict__ part, int64_t chunks, int n, const T *__restrict__ alpha,
+                                  const T *__restrict__ vprev, T *__restrict__ z) {
+    __shared__ double red[8][33];
+    const int cx = threadIdx.x & 31, gy = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + cx;
+    double s = 0.0;
+    if (c < n)
+        for (int64_t k = gy; k < chunks; k += 8) s += part[k * n + c];
+    red[gy][cx] = s;
+    __syncthreads();
+    if (gy == 0 && c < n) {
+        double t = red[0][cx];
+        for (int g = 1; g < 8; g++) t += red[g][cx];
+        z[c] = alpha ? (T)(t - (double)alpha[0] * (double)vprev[c]) : (T)t;
+    }
+}
+
+// part[b][i] = sum over rows of block b of Bt[i][r] w[r], i < cnt (Bt cnt x len, ld).
+// Four basis vectors per sweep (independent accumulators); warp sums land in
+// shared memory and are combined once at the end, in warp order.
+template <typename T>
+__global__ void __launch_bounds__(GT) multi_dot_kernel(const T *__restrict__ Bt, int64_t ld, int cnt,
+                                                       const T *__restrict__ w, int64_t len, int64_t rpb,
+                                                       T *__restrict__ part) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    T *red = reinterpret_cast<T *>(sm_raw);  // cnt x (GT / 32)
+    const int64_t r0 = (int64_t)blockIdx.x * rpb;
+    const int64_t r1 = min(len, r0 + rpb);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i0 = 0; i0 < cnt; i0 += 4) {
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+        const int nq = cnt - i0 < 4 ? cnt - i0 : 4;
+        for (int64_t r = r0 + threadIdx.x; r < r1; r += GT) {
+            const T wr = w[r];
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                if (q < nq) acc[q] += Bt[(int64_t)(i0 + q) * ld + r] * wr;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const T t = warp_red(acc[q]);
+            if (lane == 0 && q < nq) red[(i0 + q) * (GT / 32) + wid] = t;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt; i += GT) {
+        T t = red[i * (GT / 32)];
+        for (int k = 1; k < GT / 32; k++) t += red[i * (GT / 32) + k];
+        part[(int64_t)blockIdx.x * cnt + i] = t;
+    }
+}
+
+// coef[i] = sum_b part[b][i] (fixed order), one warp per i
+template <typename T>
+__global__ void sum_parts_kernel(const T *__restrict__ part, int64_t nblk, int cnt, T *__restrict__ coef) {
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= cnt) return;
+    T s = T(0);
+    for (int64_t b = lane; b < nblk; b += 32) s += part[b * cnt + i];
+    s = warp_red(s);
+    if (lane == 0) coef[i] = s;
+}
+
+// w[r] -= sum_i coef[i] Bt[i][r]; sq[b] = sum over the block's rows of w[r]^2 (after the update)
+template <typename T>
+__global__ void __launch_bounds__(GT) multi_axpy_kernel(const T *__restrict__ Bt, int64_t ld, int cnt,
+                                                        const T *__restrict__ coef, T *__restrict__ w, int64_t len,
+                                                        int64_t rpb, T *__restrict__ sq) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    T *cs = reinterpret_cast<T *>(sm_raw);
+    __shared__ T red[GT / 32];
+    for (int i = threadIdx.x; i < cnt; i += GT) cs[i] = coef[i];
+    __syncthreads();
+    const int64_t r0 = (int64_t)blockIdx.x * rpb;
+    const int64_t r1 = min(len, r0 + rpb);
+    T s2 = T(0);
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += GT) {
+        T x = w[r];
+        for (int i = 0; i < cnt; i++) x -= cs[i] * Bt[(int64_t)i * ld + r];
+        w[r] = x;
+        s2 += x * x;
+    }
+    s2 = warp_red(s2);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        T t = red[0];
+        for (int k = 1; k < GT / 32; k++) t += red[k];
+        sq[blockIdx.x] = t;
+    }
+}
+
+// nrm[0] = sqrt(sum_b sq[b]) (fixed order); out[r] = w[r] / nrm[0] in a second kernel
+template <typename T>
+__global__ void norm_kernel(const T *__restrict__ sq, int64_t nblk, T *__restrict__ nrm) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int64_t b = threadIdx.x; b < nblk; b += blockDim.x) s += (double)sq[b];
+    s = warp_red(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += red[k];
+        nrm[0] = (T)sqrt(t);
+    }
+}
+
+template <typename T>
+__global__ void scale_store_kernel(const T *__restrict__ w, int64_t len, const T *__restrict__ nrm,
+                                   T *__restrict__ out, int *__restrict__ status) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const T d = nrm[0];
+    if (r == 0 && !(d > T(0))) atomicOr(status, (int)ST_RANKDEF);
+    if (r < len) out[r] = d > T(0) ? w[r] / d : T(0);
+}
+
+// dense s x s upper bidiagonal (float64): diag alpha, superdiag beta[0..s-2]
+template <typename T>
+__global__ void bidiag_kernel(const T *__restrict__ alpha, const T *__restrict__ beta, int s, double *__restrict__ B) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= s * s) return;
+    const int i = idx / s, j = idx % s;
+    B[idx] = j == i ? (double)alpha[i] : (j == i + 1 ? (double)beta[i] : 0.0);
+}
+
+}  // namespace
+
+int64_t gkl_gemv_chunks(int64_t m) {
+    const int64_t rpc = m < 4096 ? 64 : 2048;
+    return ceil_div(m, rpc);
+}
+
+template <typename T>
+cudaError_t gkl_gemv_n(const T *A, int64_t m, int n, int64_t lda, const T *v, const T *beta, const T *uprev, T *y,
+                       cudaStream_t s) {
+    constexpr int E = V4<T>::n;
+    const bool vec = (n % E == 0) && (lda % E == 0) && ((uintptr_t)A % 16 == 0);
+    int64_t blocks = ceil_div(m, GT / 32);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    const size_t smem = sizeof(T) * (size_t)n;
+    if (smem > 48 * 1024) {
+        cudaFuncSetAttribute(gemv_n_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(gemv_n_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    if (vec) gemv_n_kernel<T, true><<<(unsigned)blocks, GT, smem, s>>>(A, m, n, lda, v, beta, uprev, y);
+    else gemv_n_kernel<T, false><<<(unsigned)blocks, GT, smem, s>>>(A, m, n, lda, v, beta, uprev, y);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t gkl_gemv_t(const T *A, int64_t m, int n, int64_t lda, const T *u, const T *alpha, const T *vprev, T *z,
+                       double *part, cudaStream_t s) {
+    constexpr int E = V4<T>::n;
+    const bool vec = (n % E == 0) && (lda % E == 0) && ((uintptr_t)A % 16 == 0);
+    const int64_t rpc = m < 4096 ? 64 : 2048;
+    const int64_t chunks = ceil_div(m, rpc);
+    const int cols_per_block = GT * (vec ? E : 1);
+    dim3 grid((unsigned)chunks, (unsigned)ceil_div(n, cols_per_block));
+    if (vec) gemv_t_kernel<T, true><<<grid, GT, 0, s>>>(A, m, n, lda, u, rpc, part);
+    else gemv_t_kernel<T, false><<<grid, GT, 0, s>>>(A, m, n, lda, u, rpc, part);
+    colsum_sub_kernel<T><<<(unsigned)ceil_div(n, 32), 256, 0, s>>>(part, chunks, n, alpha, vprev, z);
+    note_launch(2);
+    return cudaGetLastError();
+}
+
+constexpr int64_t kReorthRows = 2048;
+int64_t gkl_reorth_blocks(int64_t len) { return ceil_div(len, kReorthRows); }
+
+// w <- w - B (B^T w) twice (classical Gram-Schmidt, twice) against the first cnt rows of
+// Bt (cnt x len, ld); then nrm[0] = ||w|| and out = w / nrm[0].  coef: cnt scratch,
+// part: blocks * max(cnt, 1) scratch, sq: blocks scratch (blocks = gkl_reorth_blocks(len)).
+template <typename T>
+cudaError_t gkl_reorth_normalize(const T *Bt, int64_t ld, int cnt, T *w, int64_t len, T *coef, T *part, T *sq,
+                                 T *nrm, T *out, int *status, cudaStream_t s) {
+    const int64_t rpb = kReorthRows;
+    const int64_t nblk = ceil_div(len, rpb);
+    const size_t smem_c = sizeof(T) * (size_t)(cnt > 0 ? cnt : 1);
+    const size_t smem_d = sizeof(T) * (size_t)(cnt > 0 ? cnt : 1) * (GT / 32);
+    for (int pass = 0; pass < 2 && cnt > 0; pass++) {
+        multi_dot_kernel<T><<<(unsigned)nblk, GT, smem_d, s>>>(Bt, ld, cnt, w, len, rpb, part);
+        sum_parts_kernel<T><<<(unsigned)ceil_div(cnt, 8), 256, 0, s>>>(part, nblk, cnt, coef);
+        multi_axpy_kernel<T><<<(unsigned)nblk, GT, smem_c, s>>>(Bt, ld, cnt, coef, w, len, rpb, sq);
+        note_launch(3);
+    }
+    if (cnt == 0) {  // norm only
+        multi_axpy_kernel<T><<<(unsigned)nblk, GT, smem_c, s>>>(Bt, ld, 0, coef, w, len, rpb, sq);
+        note_launch();
+    }
+    norm_kernel<T><<<1, 1024, 0, s>>>(sq, nblk, nrm);
+    scale_store_kernel<T><<<(unsigned)ceil_div(len, 256), 256, 0, s>>>(w, len, nrm, out, status);
+    note_launch(2);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t gkl_bidiag(const T *alpha, const T *beta, int steps, double *B, cudaStream_t s) {
+    bidiag_kernel<T><<<(unsigned)ceil_div((int64_t)steps * steps, 256), 256, 0, s>>>(alpha, beta, steps, B);
+    note_launch();
+    return cudaGetLastError();
+}
+
+#define INST_GKL(T)                                                                                                  \
+    template cudaError_t gkl_gemv_n<T>(const T *, int64_t, int, int64_t, const T *, const T *, const T *, T *,        \
+                                       cudaStream_t);                                                                \
+    template cudaError_t gkl_gemv_t<T>(const T *, int64_t, int, int64_t, const T *, const T *, const T *, T *,       \
+                                       double *,                                                                     \
+                                       cudaStream_t);                                                                \
+    template cudaError_t gkl_reorth_normalize<T>(const T *, int64_t, int, T *, int64_t, T *, T *, T *, T *, T *,     \
+                                                 int *, cudaStream_t);                                               \
+    template cudaError_t gkl_bidiag<T>(const T *, const T *, int, double *, cudaStream_t);
+INST_GKL(float)
+INST_GKL(double)
+
+}  // namespace gbr

@@ -20,7 +20,29 @@ namespace {
 
 __device__ __forceinline__ int rr_pos(int k, int r, int L) {
     // position k of round r in the circle method: player 0 fixed, the rest rotate
-    return k == 0 ? 0 : 1 + ((k - 1 + r) % (L - 1));
+    // (k - 1 + r < 2 (L - 1), so one conditional subtraction replaces the modulo)
+    if (k == 0) return 0;
+    int x = k - 1 + r;
+    if (x >= L - 1) x -= L - 1;
+    return 1 + x;
+}
+
+// Jacobi rotation (c, s) annihilating gamma for column norms^2 alpha, beta:
+// zeta = (beta - alpha) / (2 gamma), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
+// c = 1 / sqrt(1 + t^2), s = c t.
+__device__ __forceinline__ void jrot(float al, float be, float ga, float &c, float &s) {
+    // zeta and t only choose the angle (fast division is enough); c is computed
+    // with the IEEE square root and division so that c^2 + s^2 = 1 to rounding
+    const float zeta = __fdividef(be - al, 2.f * ga);
+    const float t = copysignf(1.f, zeta) * __frcp_rn(fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+    c = 1.f / sqrtf(fmaf(t, t, 1.f));
+    s = c * t;
+}
+__device__ __forceinline__ void jrot(double al, double be, double ga, double &c, double &s) {
+    const double zeta = (be - al) / (2.0 * ga);
+    const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+    c = 1.0 / sqrt(1.0 + t * t);
+    s = c * t;
 }
 
 template <typename T>
@@ -35,49 +57,90 @@ template <> struct Eps<float> { static constexpr double v = FLT_EPSILON; };
 template <> struct Eps<double> { static constexpr double v = DBL_EPSILON; };
 
 // ------------------------------------------------------------ Cholesky + inverse
-// Right-looking upper Cholesky R^T R = G with one barrier per column: the
-// scaled row j of R goes to a separate buffer, so the trailing update (which
-// reads the unscaled row j of the working matrix) never races with it.  The
-// inverse solves R x = e_c column by column, one column per thread, with no
-// barriers (R is read-only by then).  Arithmetic in Tk.
-template <typename TG, typename Tk, typename Tc>
-__global__ void chol_inv_kernel(const TG *__restrict__ G, int64_t ldg, int l, double shift_coef,
-                                double *__restrict__ R, double *__restrict__ Rinv, Tc *__restrict__ Rinv_c, int lp,
-                                int *__restrict__ status) {
+// Upper Cholesky R^T R = G and the inverse of R in one CTA of 256 threads laid
+// out as a 16 x 16 grid.  Thread (ty, tx) keeps the entries (ty + 16a, tx + 16b),
+// a, b < LB, in registers; each elimination step only broadcasts one row through
+// a double-buffered shared row, so a step costs one barrier.
+//   Cholesky (right-looking): with the current row j (unscaled) in the buffer,
+//     R[j][c] = M[j][c] / sqrt(M[j][j]),  M[r][c] -= M[j][r] M[j][c] / M[j][j]  (j < r <= c).
+//   Inverse (back substitution on R X = I from the bottom row up):
+//     X[k][:] /= R[k][k],  X[i][:] -= R[i][k] X[k][:]  (i < k).
+// Arithmetic in Tk; l <= 16 * LB.
+template <typename TG, typename Tk, typename Tc, int LB>
+__global__ void __launch_bounds__(256) chol_inv_kernel(const TG *__restrict__ G, int64_t ldg, int l,
+                                                       double shift_coef, double *__restrict__ R,
+                                                       double *__restrict__ Rinv, Tc *__restrict__ Rinv_c, int lp,
+                                                       int *__restrict__ status) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    Tk *M = reinterpret_cast<Tk *>(smraw);  // l x l working matrix (upper triangle)
-    Tk *Rs = M + l * l;                     // l x l factor R (upper), then its inverse in place by columns
+    Tk *Rs = reinterpret_cast<Tk *>(smraw);  // l x l factor R
+    Tk *rowbuf = Rs + l * l;                 // 2 x 16 LB broadcast rows
     __shared__ double trace;
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    constexpr int W = 16 * LB;
+    Tk M[LB][LB];
     int used = 0;  // 0: plain, 1: shifted, 2: breakdown fallback (R = 0, R^{-1} = I)
     for (int attempt = 0; attempt < 3; attempt++) {
-        for (int idx = tid; idx < l * l; idx += nt) {
-            const int i = idx / l, j = idx % l;
-            M[idx] = attempt == 2 ? Tk(i == j ? 1 : 0) : (Tk)G[(int64_t)min(i, j) * ldg + max(i, j)];
-            Rs[idx] = Tk(0);
-        }
-        __syncthreads();
-        if (tid == 0) {
+#pragma unroll
+        for (int a = 0; a < LB; a++)
+#pragma unroll
+            for (int b = 0; b < LB; b++) {
+                const int r = ty + 16 * a, c = tx + 16 * b;
+                Tk v = Tk(0);
+                if (r < l && c < l) v = attempt == 2 ? Tk(r == c ? 1 : 0) : (Tk)G[(int64_t)min(r, c) * ldg + max(r, c)];
+                M[a][b] = v;
+            }
+        if (attempt == 1 && tid < 32) {  // trace for the shift (only after a breakdown)
             double tr = 0.0;
-            for (int i = 0; i < l; i++) tr += (double)M[i * l + i];
-            trace = tr;
+            for (int i = tid; i < l; i += 32) tr += (double)G[(int64_t)i * ldg + i];
+            tr = warp_sum(tr);
+            if (tid == 0) trace = tr;
         }
+        for (int i = tid; i < l * l; i += 256) Rs[i] = Tk(0);
         __syncthreads();
         if (attempt == 1) {  // shifted CholeskyQR: G + s I with s = 11 (rows l + l(l+1)) u tr(G)
             const Tk sh = (Tk)(shift_coef * trace);
-            for (int i = tid; i < l; i += nt) M[i * l + i] += sh;
-            __syncthreads();
+#pragma unroll
+            for (int a = 0; a < LB; a++)
+#pragma unroll
+                for (int b = 0; b < LB; b++)
+                    if (ty + 16 * a == tx + 16 * b && ty + 16 * a < l) M[a][b] += sh;
         }
+        // publish row 0
+        if (ty == 0)
+#pragma unroll
+            for (int b = 0; b < LB; b++) rowbuf[tx + 16 * b] = M[0][b];
+        __syncthreads();
         bool bad = false;
         for (int j = 0; j < l; j++) {
-            const Tk d = M[j * l + j];
-            if (!(d > Tk(0)) || !isfinite((double)d)) { bad = true; break; }  // uniform: every thread reads d
-            const Tk rinv = Tk(1) / sqrt(d), dinv = Tk(1) / d;
-            for (int c = j + tid; c < l; c += nt) Rs[j * l + c] = M[j * l + c] * rinv;
-            const int nr = l - j - 1;
-            for (int idx = tid; idx < nr * nr; idx += nt) {
-                const int r = j + 1 + idx / nr, c = j + 1 + idx % nr;
-                if (c >= r) M[r * l + c] -= M[j * l + r] * M[j * l + c] * dinv;
+            const Tk *row = rowbuf + (j & 1) * W;
+            const Tk d = row[j];
+            if (!(d > Tk(0)) || !(d < Tk(3.0e38))) { bad = true; break; }  // uniform: every thread reads d
+            const Tk dinv = Tk(1) / d, rinv = Tk(1) / sqrt(d);
+            if (ty == 0)
+#pragma unroll
+                for (int b = 0; b < LB; b++) {
+                    const int c = tx + 16 * b;
+                    if (c >= j && c < l) Rs[j * l + c] = row[c] * rinv;
+                }
+#pragma unroll
+            for (int a = 0; a < LB; a++) {
+                const int r = ty + 16 * a;
+                if (r > j && r < l) {
+                    const Tk f = row[r] * dinv;
+#pragma unroll
+                    for (int b = 0; b < LB; b++) {
+                        const int c = tx + 16 * b;
+                        if (c >= r && c < l) M[a][b] -= f * row[c];
+                    }
+                }
+            }
+            if (j + 1 < l) {
+                Tk *nxt = rowbuf + ((j + 1) & 1) * W;
+#pragma unroll
+                for (int a = 0; a < LB; a++)
+                    if (ty + 16 * a == j + 1)
+#pragma unroll
+                        for (int b = 0; b < LB; b++) nxt[tx + 16 * b] = M[a][b];
             }
             __syncthreads();
         }
@@ -88,27 +151,60 @@ __global__ void chol_inv_kernel(const TG *__restrict__ G, int64_t ldg, int l, do
         }
         __syncthreads();
     }
-    for (int idx = tid; idx < l * l; idx += nt) R[idx] = used < 2 ? (double)Rs[idx] : 0.0;
+    for (int i = tid; i < l * l; i += 256) R[i] = used < 2 ? (double)Rs[i] : 0.0;
+    // inverse: X in registers (reusing M), identity to start
+#pragma unroll
+    for (int a = 0; a < LB; a++)
+#pragma unroll
+        for (int b = 0; b < LB; b++) M[a][b] = Tk((ty + 16 * a == tx + 16 * b) ? 1 : 0);
     __syncthreads();
-    // column c of R^{-1}: back substitution R x = e_c (rows c..0), written over column c of Rs
-    Tk *X = M;  // reuse: X[i * l + c]
-    for (int c = tid; c < l; c += nt) {
-        for (int i = 0; i < l; i++) X[i * l + c] = Tk(0);
-        for (int k = c; k >= 0; k--) {
-            Tk acc = (k == c) ? Tk(1) : Tk(0);
-            for (int t = k + 1; t <= c; t++) acc -= Rs[k * l + t] * X[t * l + c];
-            X[k * l + c] = acc / Rs[k * l + k];
+    {   // publish the scaled last row
+        const int k = l - 1;
+        Tk *buf = rowbuf + (k & 1) * W;
+        const Tk inv = Tk(1) / Rs[k * l + k];
+#pragma unroll
+        for (int a = 0; a < LB; a++)
+            if (ty + 16 * a == k)
+#pragma unroll
+                for (int b = 0; b < LB; b++) {
+                    M[a][b] *= inv;
+                    buf[tx + 16 * b] = M[a][b];
+                }
+    }
+    __syncthreads();
+    for (int k = l - 1; k >= 0; k--) {
+        const Tk *row = rowbuf + (k & 1) * W;
+#pragma unroll
+        for (int a = 0; a < LB; a++) {
+            const int i = ty + 16 * a;
+            if (i < k) {
+                const Tk f = Rs[i * l + k];
+#pragma unroll
+                for (int b = 0; b < LB; b++) M[a][b] -= f * row[tx + 16 * b];
+            }
         }
+        if (k > 0) {
+            Tk *nxt = rowbuf + ((k - 1) & 1) * W;
+            const Tk inv = Tk(1) / Rs[(k - 1) * l + (k - 1)];
+#pragma unroll
+            for (int a = 0; a < LB; a++)
+                if (ty + 16 * a == k - 1)
+#pragma unroll
+                    for (int b = 0; b < LB; b++) {
+                        M[a][b] *= inv;
+                        nxt[tx + 16 * b] = M[a][b];
+                    }
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    for (int idx = tid; idx < l * l; idx += nt) {
-        const int i = idx / l, j = idx % l;
-        Rinv[idx] = j >= i ? (double)X[idx] : 0.0;
-    }
-    for (int idx = tid; idx < lp * lp; idx += nt) {
-        const int i = idx / lp, j = idx % lp;
-        Rinv_c[idx] = (i < l && j < l && j >= i) ? (Tc)X[i * l + j] : Tc(0);
-    }
+#pragma unroll
+    for (int a = 0; a < LB; a++)
+#pragma unroll
+        for (int b = 0; b < LB; b++) {
+            const int i = ty + 16 * a, j = tx + 16 * b;
+            if (i < l && j < l) Rinv[i * l + j] = j >= i ? (double)M[a][b] : 0.0;
+            if (i < lp && j < lp) Rinv_c[i * lp + j] = (i < l && j < l && j >= i) ? (Tc)M[a][b] : Tc(0);
+        }
 }
 
 __global__ void trmm_upper_kernel(const double *__restrict__ R2, const double *__restrict__ R1, double *__restrict__ R,
@@ -181,9 +277,8 @@ __global__ void __launch_bounds__(1024) jacobi_osvd_kernel(const double *__restr
                     ga += g1;
                 }
                 if (live && ga != Ta(0) && fabs(ga) > tol * sqrt(al * be)) {
-                    const Ta zeta = (be - al) / (Ta(2) * ga);
-                    const Ta t = (zeta >= Ta(0) ? Ta(1) : Ta(-1)) / (fabs(zeta) + sqrt(Ta(1) + zeta * zeta));
-                    const Ta c = Ta(1) / sqrt(Ta(1) + t * t), s = c * t;
+                    Ta c, s;
+                    jrot(al, be, ga, c, s);
                     for (int i = gl; i < L; i += gsize) {
                         const Ta xp = X[p * L + i], xq = X[q * L + i];
                         X[p * L + i] = c * xp - s * xq;
@@ -202,35 +297,77 @@ __global__ void __launch_bounds__(1024) jacobi_osvd_kernel(const double *__restr
         if (!any) { converged = true; break; }
     }
     if (!converged && tid == 0) atomicOr(status, (int)ST_NOCONV);
+    Ta *nrm_t = reinterpret_cast<Ta *>(nrm);
     for (int p = warp; p < l; p += nw) {
         Ta s = 0;
         for (int i = lane; i < l; i += 32) s += X[p * L + i] * X[p * L + i];
         s = warp_sum(s);
-        if (lane == 0) nrm[p] = sqrt((double)s);
+        if (lane == 0) nrm_t[p] = sqrt(s);
     }
     __syncthreads();
-    if (tid == 0) {  // descending order, stable in the column index
-        for (int i = 0; i < l; i++) perm[i] = i;
-        for (int i = 0; i < l; i++) {
-            int best = i;
-            for (int j = i + 1; j < l; j++)
-                if (nrm[perm[j]] > nrm[perm[best]]) best = j;
-            const int t = perm[i]; perm[i] = perm[best]; perm[best] = t;
+    // descending order, stable in the column index: rank of column p among all columns
+    for (int p = tid; p < l; p += nt) {
+        const Ta v = nrm_t[p];
+        int rank = 0;
+        for (int j = 0; j < l; j++) {
+            const Ta w = nrm_t[j];
+            rank += (w > v) || (w == v && j < p);
         }
+        perm[rank] = p;
     }
     __syncthreads();
-    for (int o = tid; o < l; o += nt) sig[o] = nrm[perm[o]];
+    // the accumulated rotations are orthogonal up to rounding; renormalise their columns
+    Ta *vn = reinterpret_cast<Ta *>(perm + L);  // L entries after perm (see the launcher's size)
+    for (int p = warp; p < l; p += nw) {
+        Ta s = 0;
+        for (int i = lane; i < l; i += 32) s += V[p * L + i] * V[p * L + i];
+        s = warp_sum(s);
+        if (lane == 0) vn[p] = Ta(1) / sqrt(s);
+    }
+    __syncthreads();
+    for (int o = tid; o < l; o += nt) sig[o] = (double)nrm_t[perm[o]];
     for (int idx = tid; idx < lp * lp; idx += nt) {
         const int i = idx / lp, o = idx % lp;
         To u = To(0), w = To(0);
         if (i < l && o < l) {
             const int p = perm[o];
-            const double sp = nrm[p];
-            u = sp > 0.0 ? (To)((double)X[p * L + i] / sp) : To(0);
-            w = (To)V[p * L + i];
+            const Ta sp = nrm_t[p];
+            u = sp > Ta(0) ? (To)(X[p * L + i] / sp) : To(0);
+            w = (To)(V[p * L + i] * vn[p]);
         }
         UR[idx] = u;
         W[idx] = w;
+    }
+}
+
+// sig[i] = x_i^T R w_i / (||x_i|| ||w_i||) in float64 for the columns x_i of UR and
+// w_i of W (ld lp): the Rayleigh quotient of the Jacobi singular vectors, whose
+// error is quadratic in the vectors' error.  One block per singular value.
+template <typename To>
+__global__ void sv_refine_kernel(const double *__restrict__ R, int l, int lp, const To *__restrict__ UR,
+                                 const To *__restrict__ W, double *__restrict__ sig) {
+    __shared__ double red[3][32];
+    const int i = blockIdx.x;
+    double acc = 0.0, nx = 0.0, nw = 0.0;
+    for (int r = threadIdx.x; r < l; r += blockDim.x) {
+        double rw = 0.0;
+        for (int c = r; c < l; c++) rw += R[r * l + c] * (double)W[c * lp + i];   // R upper triangular or bidiagonal
+        const double x = (double)UR[r * lp + i];
+        acc += x * rw;
+        nx += x * x;
+        const double w = (double)W[r * lp + i];
+        nw += w * w;
+    }
+    acc = warp_sum(acc);
+    nx = warp_sum(nx);
+    nw = warp_sum(nw);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { red[0][wid] = acc; red[1][wid] = nx; red[2][wid] = nw; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, x = 0.0, w = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) { a += red[0][k]; x += red[1][k]; w += red[2][k]; }
+        if (x > 0.0 && w > 0.0) sig[i] = fabs(a) / sqrt(x * w);
     }
 }
 
@@ -426,10 +563,15 @@ __global__ void pca_select_kernel(const double *__restrict__ sigma, int count, c
 template <typename TG, typename Tk, typename Tc>
 cudaError_t chol_inv(const TG *G, int64_t ldg, int l, int64_t rows, double u, double *R, double *Rinv, Tc *Rinv_c,
                      int lp, int *status, cudaStream_t s) {
-    const size_t smem = sizeof(Tk) * 2 * (size_t)l * l;
-    cudaFuncSetAttribute(chol_inv_kernel<TG, Tk, Tc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const double coef = 11.0 * ((double)rows * l + (double)l * (l + 1)) * u;
-    chol_inv_kernel<TG, Tk, Tc><<<1, 256, smem, s>>>(G, ldg, l, coef, R, Rinv, Rinv_c, lp, status);
+    if (l <= 64) {
+        const size_t smem = sizeof(Tk) * ((size_t)l * l + 2 * 64);
+        chol_inv_kernel<TG, Tk, Tc, 4><<<1, 256, smem, s>>>(G, ldg, l, coef, R, Rinv, Rinv_c, lp, status);
+    } else {
+        const size_t smem = sizeof(Tk) * ((size_t)l * l + 2 * 128);
+        cudaFuncSetAttribute(chol_inv_kernel<TG, Tk, Tc, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        chol_inv_kernel<TG, Tk, Tc, 8><<<1, 256, smem, s>>>(G, ldg, l, coef, R, Rinv, Rinv_c, lp, status);
+    }
     note_launch();
     return cudaGetLastError();
 }
@@ -443,7 +585,9 @@ cudaError_t trmm_upper(const double *R2, const double *R1, double *R, int l, cud
 template <typename Ta, typename To>
 cudaError_t jacobi_osvd(const double *R, int l, int lp, double *sig, To *UR, To *W, int *status, cudaStream_t s) {
     const int L = l + (l & 1);
-    const size_t smem = sizeof(Ta) * (2 * (size_t)L * L + 1) + sizeof(double) * L + sizeof(int) * L + 16;
+    // X, V (L x L each), norms (L doubles), permutation (L ints), column scales (L x Ta)
+    const size_t smem = sizeof(Ta) * (2 * (size_t)L * L + 1) + sizeof(double) * L + sizeof(int) * L +
+                        sizeof(double) * L + 16;
     cudaFuncSetAttribute(jacobi_osvd_kernel<Ta, To>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int gsize = l <= 64 ? 16 : 32;
     int threads = (L / 2) * gsize;
@@ -452,6 +596,16 @@ cudaError_t jacobi_osvd(const double *R, int l, int lp, double *sig, To *UR, To 
     note_launch();
     return cudaGetLastError();
 }
+
+template <typename To>
+cudaError_t sv_refine(const double *R, int l, int lp, const To *UR, const To *W, double *sig, cudaStream_t s) {
+    sv_refine_kernel<To><<<l, 128, 0, s>>>(R, l, lp, UR, W, sig);
+    note_launch();
+    return cudaGetLastError();
+}
+template cudaError_t sv_refine<float>(const double *, int, int, const float *, const float *, double *, cudaStream_t);
+template cudaError_t sv_refine<double>(const double *, int, int, const double *, const double *, double *,
+                                       cudaStream_t);
 
 cudaError_t jacobi_eig(const double *G, int n, double *lam, double *V, int *status, cudaStream_t s) {
     const int L = n + (n & 1);

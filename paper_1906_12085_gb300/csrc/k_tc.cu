@@ -1,23 +1,29 @@
 // Tensor-core (tcgen05) products for the float32 path with float32 accuracy.
 //
-// Each float32 operand x is split into two tf32 values, x = hi + lo with
-// hi = rn_tf32(x) and lo = rn_tf32(x - hi); a product is accumulated as
-// hi*hi + hi*lo + lo*hi in float32 in TMEM (lo*lo is below float32
-// resolution).  Operands reach shared memory by TMA; the split (and, for the
-// transposed product, the transpose into the K-major layout the MMA reads)
-// happens in shared memory between the TMA landing and the MMA, so the tall
-// operand is read from HBM exactly once.
+// Each float32 value x of an operand is split into two tf32 values, x = hi + lo
+// with hi = x with its low 13 mantissa bits cleared and lo = rn_tf32(x - hi);
+// a product is accumulated as hi*hi + hi*lo + lo*hi in float32 in TMEM (lo*lo
+// is below float32 resolution).
 //
 //   tc_gemm_nn : Y (m x N) = A (m x n) Z (n x N)            (sketch, power step, Q = Y R^-1)
 //   tc_gemm_tn : part[chunk] = A[rows of chunk]^T Q[rows]   (power step, T = A^T Q, Gram)
 //
+// The tall operand A reaches shared memory by TMA, is split by the worker
+// warps in registers and stored straight into tensor memory (tcgen05.st); the
+// MMA reads A from TMEM and only the small operand (Z^T or Q^T, already split)
+// from shared memory.  A TMEM lane is a row of the MMA's A operand, so the
+// transposed product needs no shared-memory transpose of A: a worker thread
+// reads one column of the raw A tile and stores it into its own lane.
+//
 // Both kernels are persistent (one CTA per SM) with warp roles:
 //   warp 0      TMA producer (one elected lane)
 //   warp 1      TMEM owner and MMA issuer (one elected lane)
-//   warps 2-9   split / transpose workers (256 threads)
+//   warps 2-9   split workers (256 threads; warp w serves TMEM lane quarter w % 4,
+//               the two warps of a quarter take 16 K columns each)
 //   warps 10-13 epilogue: TMEM -> registers -> HBM (one TMEM lane quarter each)
-// Two TMEM accumulators alternate between tiles so the epilogue of one tile
-// overlaps the main loop of the next.  Every wait is bounded; a stalled
+// TMEM holds two accumulators (columns 0-255) that alternate between tiles, so
+// the epilogue of one tile overlaps the main loop of the next, and four A
+// stages of hi and lo (columns 256-511).  Every wait is bounded; a stalled
 // pipeline sets ST_TIMEOUT in the status word and the CTA drains and exits.
 #include <cudaTypedefs.h>
 
@@ -36,8 +42,10 @@ constexpr int NEPI = 128;
 constexpr int NTHR = 64 + NSPLIT + NEPI;
 constexpr int EPI_WARP0 = (64 + NSPLIT) / 32;
 constexpr uint32_t A_STAGE = TM * 128;  // bytes of one 128 x 32 fp32 stage
-constexpr uint32_t TMEM_COLS = 256;     // two accumulators of up to 128 columns
-constexpr uint32_t ACC_STRIDE = 128;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t ACC_STRIDE = 128;    // accumulator b at columns [128 b, 128 b + N)
+constexpr int TS = 4;                   // TMEM A stages
+constexpr uint32_t A_COL0 = 256;        // A stage s: hi at 256 + 64 s, lo at 256 + 64 s + 32
 
 __device__ __forceinline__ float rna_tf32(float x) {
     uint32_t r;
@@ -52,6 +60,13 @@ __device__ __forceinline__ void split4(const float *x, float4 &h, float4 &l) {
     h.w = rna_tf32(x[3]); l.w = rna_tf32(x[3] - h.w);
 }
 
+// truncating split for the A operand: hi keeps the tf32 bits, lo the exact rest rounded to tf32
+__device__ __forceinline__ void split_tr(float x, uint32_t &h, uint32_t &l) {
+    const uint32_t hb = __float_as_uint(x) & 0xFFFFE000u;
+    h = hb;
+    l = __float_as_uint(rna_tf32(x - __uint_as_float(hb)));
+}
+
 // byte offset of the 16-byte chunk `cc` (K position 4cc..4cc+3) of row `r` in
 // the 128-byte-swizzled K-major layout (8-row atoms of 1024 bytes)
 __device__ __forceinline__ uint32_t kmajor_off(int r, int cc) {
@@ -62,6 +77,7 @@ __device__ __forceinline__ uint32_t kmajor_off(int r, int cc) {
 template <int S>
 struct Bars {
     uint64_t full[S], split[S], empty[S];
+    uint64_t tempty[TS];  // TMEM A stage free (NN)
     uint64_t acc_full[2], acc_empty[2];
     uint32_t tmem;
     int abort_flag;
@@ -75,19 +91,47 @@ __device__ __forceinline__ bool wait_ok(uint64_t *bar, uint32_t parity, volatile
     return false;
 }
 
-// 12 MMAs of one stage: D (+)= Ah Bh + Ah Bl + Al Bh over the 4 K=8 slices.
+// 12 MMAs of one stage: D (+)= Ah Bh + Ah Bl + Al Bh over the 4 K=8 slices; A in TMEM.
 template <int N>
-__device__ __forceinline__ void mma_stage(uint32_t d, const uint8_t *ah, const uint8_t *al, const uint8_t *bh,
+__device__ __forceinline__ void mma_stage(uint32_t d, uint32_t a_hi, uint32_t a_lo, const uint8_t *bh,
                                           const uint8_t *bl, bool first) {
     constexpr uint32_t idesc = idesc_tf32(TM, N);
 #pragma unroll
     for (int kk = 0; kk < TBK / 8; kk++) {
-        const uint32_t off = kk * 32;
-        const uint64_t dah = sdesc_kmajor_sw128(ah, off), dal = sdesc_kmajor_sw128(al, off);
-        const uint64_t dbh = sdesc_kmajor_sw128(bh, off), dbl = sdesc_kmajor_sw128(bl, off);
-        mma_tf32(d, dah, dbh, idesc, (first && kk == 0) ? 0u : 1u);
-        mma_tf32(d, dah, dbl, idesc, 1u);
-        mma_tf32(d, dal, dbh, idesc, 1u);
+        const uint64_t dbh = sdesc_kmajor_sw128(bh, kk * 32), dbl = sdesc_kmajor_sw128(bl, kk * 32);
+        mma_tf32_ta(d, a_hi + kk * 8, dbh, idesc, (first && kk == 0) ? 0u : 1u);
+        mma_tf32_ta(d, a_hi + kk * 8, dbl, idesc, 1u);
+        mma_tf32_ta(d, a_lo + kk * 8, dbh, idesc, 1u);
+    }
+}
+
+// Store a worker's 16 split values (K columns 16h..16h+15 of its lane) into TMEM stage s.
+__device__ __forceinline__ void store_a(uint32_t tmem, int q, int h, int s, const uint32_t *hi, const uint32_t *lo) {
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    const uint32_t col = A_COL0 + (uint32_t)s * 64 + (uint32_t)h * 16;
+    tmem_st16(tmem + lane_base + col, hi);
+    tmem_st16(tmem + lane_base + col + 32, lo);
+}
+
+// Epilogue: one TMEM lane quarter of accumulator b -> N floats per row at dst (row stride ld).
+template <int N>
+__device__ __forceinline__ void drain_acc(uint32_t tmem, uint32_t b, int q, int lane, float *dst, bool valid) {
+#pragma unroll
+    for (int c0 = 0; c0 < N; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + b * ACC_STRIDE + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+        if (valid) {
+            float *p = dst + c0;
+            if (c0 + 32 <= N && ((reinterpret_cast<uintptr_t>(p) & 15) == 0)) {
+#pragma unroll
+                for (int j = 0; j < 32; j += 4)
+                    *reinterpret_cast<float4 *>(p + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; j++)
+                    if (c0 + j < N) p[j] = v[j];
+            }
+        }
     }
 }
 
@@ -95,9 +139,11 @@ __device__ __forceinline__ void mma_stage(uint32_t d, const uint8_t *ah, const u
 template <int N>
 struct NNCfg {
     static constexpr uint32_t B_STAGE = N * 128;
-    static constexpr uint32_t STAGE = 2 * A_STAGE + 2 * B_STAGE;
+    static constexpr uint32_t STAGE = A_STAGE + 2 * B_STAGE;     // shared-memory stage: raw A + B hi/lo
     static constexpr int S = (200 * 1024) / STAGE > 6 ? 6 : (200 * 1024) / STAGE;
-    static constexpr uint32_t SMEM = S * STAGE + 1024 + sizeof(Bars<S>) + 64;
+    // at least 120 KB so that only one CTA (which owns all 512 TMEM columns) fits on an SM
+    static constexpr uint32_t SMEM_NEED = S * STAGE + 1024 + sizeof(Bars<S>) + 64;
+    static constexpr uint32_t SMEM = SMEM_NEED > 120 * 1024 ? SMEM_NEED : 120 * 1024;
 };
 
 template <int N>
@@ -109,9 +155,8 @@ __global__ void __launch_bounds__(NTHR, 1)
     constexpr int S = C::S;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint8_t *sA = base;                    // raw fp32, split in place to hi
-    uint8_t *sAl = sA + S * A_STAGE;       // lo
-    uint8_t *sBh = sAl + S * A_STAGE;
+    uint8_t *sA = base;                    // raw fp32 A stages (TMA, 128-byte swizzle)
+    uint8_t *sBh = sA + S * A_STAGE;
     uint8_t *sBl = sBh + S * C::B_STAGE;
     Bars<S> *bar = reinterpret_cast<Bars<S> *>(sBl + S * C::B_STAGE);
     volatile int *abort_flag = &bar->abort_flag;
@@ -123,8 +168,11 @@ __global__ void __launch_bounds__(NTHR, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; s++) {
             mbar_init(&bar->full[s], 1);
-            mbar_init(&bar->split[s], NSPLIT);
             mbar_init(&bar->empty[s], 1);
+        }
+        for (int t = 0; t < TS; t++) {
+            mbar_init(&bar->split[t], NSPLIT);  // TMEM A stage t written
+            mbar_init(&bar->tempty[t], 1);      // TMEM A stage t consumed by the MMAs
         }
         for (int b = 0; b < 2; b++) {
             mbar_init(&bar->acc_full[b], 1);
@@ -167,37 +215,40 @@ __global__ void __launch_bounds__(NTHR, 1)
                 tc_fence_after();
                 const uint32_t d = tmem + b * ACC_STRIDE;
                 for (int kb = 0; kb < nkb; kb++, g++) {
-                    const int s = g % S;
-                    if (!(ok = wait_ok(&bar->split[s], (g / S) & 1, abort_flag))) break;
+                    const int s = g % S, ts = g % TS;
+                    if (!(ok = wait_ok(&bar->split[ts], (g / TS) & 1, abort_flag))) break;
                     tc_fence_after();
-                    mma_stage<N>(d, sA + s * A_STAGE, sAl + s * A_STAGE, sBh + s * C::B_STAGE, sBl + s * C::B_STAGE,
-                                 kb == 0);
+                    const uint32_t a = tmem + A_COL0 + (uint32_t)ts * 64;
+                    mma_stage<N>(d, a, a + 32, sBh + s * C::B_STAGE, sBl + s * C::B_STAGE, kb == 0);
                     mma_commit(&bar->empty[s]);
+                    mma_commit(&bar->tempty[ts]);
                 }
                 if (ok) mma_commit(&bar->acc_full[b]);
             }
         }
     } else if (warp < EPI_WARP0) {
-        const int wt = threadIdx.x - 64;
+        const int q = warp & 3, h = (warp - 2) >> 2, r = q * 32 + lane;
         uint32_t g = 0;
         bool ok = true;
         for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x)
             for (int kb = 0; kb < nkb; kb++, g++) {
-                const int s = g % S;
+                const int s = g % S, ts = g % TS;
                 if (!(ok = wait_ok(&bar->full[s], (g / S) & 1, abort_flag))) break;
-                float4 *a = reinterpret_cast<float4 *>(sA + s * A_STAGE);
-                float4 *lo = reinterpret_cast<float4 *>(sAl + s * A_STAGE);
+                if (!(ok = wait_ok(&bar->tempty[ts], ((g / TS) & 1) ^ 1, abort_flag))) break;
+                const uint8_t *raw = sA + s * A_STAGE;
+                uint32_t hi[16], lo[16];
 #pragma unroll
-                for (int e = 0; e < (int)(A_STAGE / 16) / NSPLIT; e++) {
-                    const int idx = wt + e * NSPLIT;
-                    const float4 v = a[idx];
-                    float4 h, l;
-                    split4(&v.x, h, l);
-                    a[idx] = h;
-                    lo[idx] = l;
+                for (int c4 = 0; c4 < 4; c4++) {
+                    const float4 v = *reinterpret_cast<const float4 *>(raw + kmajor_off(r, h * 4 + c4));
+                    split_tr(v.x, hi[c4 * 4 + 0], lo[c4 * 4 + 0]);
+                    split_tr(v.y, hi[c4 * 4 + 1], lo[c4 * 4 + 1]);
+                    split_tr(v.z, hi[c4 * 4 + 2], lo[c4 * 4 + 2]);
+                    split_tr(v.w, hi[c4 * 4 + 3], lo[c4 * 4 + 3]);
                 }
-                fence_proxy_async_smem();
-                mbar_arrive(&bar->split[s]);
+                store_a(tmem, q, h, ts, hi, lo);
+                tmem_wait_st();
+                tc_fence_before();
+                mbar_arrive(&bar->split[ts]);
             }
     } else {
         const int q = warp & 3;
@@ -207,23 +258,7 @@ __global__ void __launch_bounds__(NTHR, 1)
             if (!wait_ok(&bar->acc_full[b], (it >> 1) & 1, abort_flag)) break;
             tc_fence_after();
             const int64_t row = t * TM + q * 32 + lane;
-#pragma unroll
-            for (int c0 = 0; c0 < N; c0 += 32) {
-                float v[32];
-                tmem_ld32(tmem + b * ACC_STRIDE + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-                if (row < m) {
-                    float *dst = Y + row * ldy + c0;
-                    if (c0 + 32 <= N && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
-#pragma unroll
-                        for (int j = 0; j < 32; j += 4)
-                            *reinterpret_cast<float4 *>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 32; j++)
-                            if (c0 + j < N) dst[j] = v[j];
-                    }
-                }
-            }
+            drain_acc<N>(tmem, b, q, lane, Y + row * ldy, row < m);
             tc_fence_before();
             mbar_arrive(&bar->acc_empty[b]);
         }
@@ -240,18 +275,20 @@ __global__ void __launch_bounds__(NTHR, 1)
 // ======================================================================= TN
 // Tile t = (chunk, column tile): D (128 columns of A x N) = sum over the chunk's
 // rows r of A[r][c] Q[r][j].  Raw A and Q stages land unswizzled (row-major
-// 32 x 128 and 32 x N); workers write their tf32 hi/lo parts transposed into
-// the K-major swizzled layout (rows = column index of A or Q, K = row of A).
+// 32 x 128 and 32 x N).  A worker thread owns TMEM lane i = column i of the
+// A tile and stores its split column there; Q is split and transposed into
+// the K-major swizzled layout in shared memory (rows = column j of Q).
 template <int N>
 struct TNCfg {
     static constexpr uint32_t RAW_A = 32 * TM * 4;     // 16 KB
     static constexpr uint32_t RAW_Q = 32 * N * 4;
     static constexpr uint32_t RAW = RAW_A + RAW_Q;
     static constexpr uint32_t SPL_B = N * 128;
-    static constexpr uint32_t SPL = 2 * A_STAGE + 2 * SPL_B;
-    static constexpr int SR = 3;  // raw stages
-    static constexpr int SS = 2;  // split stages
-    static constexpr uint32_t SMEM = SR * RAW + SS * SPL + 1024 + sizeof(Bars<SR + SS>) + 64;
+    static constexpr uint32_t SPL = 2 * SPL_B;
+    static constexpr int SS = TS;  // split stages (Q hi/lo in smem, A hi/lo in TMEM)
+    static constexpr int SR = (208 * 1024 - SS * SPL) / RAW > 6 ? 6 : (208 * 1024 - SS * SPL) / RAW;
+    static constexpr uint32_t SMEM_NEED = SR * RAW + SS * SPL + 1024 + sizeof(Bars<SR + SS>) + 64;
+    static constexpr uint32_t SMEM = SMEM_NEED > 120 * 1024 ? SMEM_NEED : 120 * 1024;
 };
 
 template <int N>
@@ -262,10 +299,10 @@ __global__ void __launch_bounds__(NTHR, 1)
     constexpr int SR = C::SR, SS = C::SS;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint8_t *sSplit = base;                 // SS x (Ahi, Alo, Qhi, Qlo), 1024-aligned pieces
+    uint8_t *sSplit = base;                 // SS x (Qhi, Qlo), 1024-aligned
     uint8_t *sRaw = base + SS * C::SPL;     // SR x (rawA, rawQ)
     // barrier roles: full[0..SR) raw landed, split[0..SS) split ready, empty[0..SR) raw free,
-    // empty[SR..SR+SS) split buffer free (MMA done)
+    // empty[SR..SR+SS) split stage free (MMA done)
     Bars<SR + SS> *bar = reinterpret_cast<Bars<SR + SS> *>(sRaw + SR * C::RAW);
     volatile int *abort_flag = &bar->abort_flag;
 
@@ -342,7 +379,8 @@ __global__ void __launch_bounds__(NTHR, 1)
                     if (!(ok = wait_ok(&bar->split[s], (g / SS) & 1, abort_flag))) break;
                     tc_fence_after();
                     uint8_t *sp = sSplit + s * C::SPL;
-                    mma_stage<N>(d, sp, sp + A_STAGE, sp + 2 * A_STAGE, sp + 2 * A_STAGE + C::SPL_B, kb == 0);
+                    const uint32_t a = tmem + A_COL0 + (uint32_t)s * 64;
+                    mma_stage<N>(d, a, a + 32, sp, sp + C::SPL_B, kb == 0);
                     mma_commit(&bar->empty[SR + s]);
                 }
                 if (ok) mma_commit(&bar->acc_full[b]);
@@ -350,6 +388,7 @@ __global__ void __launch_bounds__(NTHR, 1)
         }
     } else if (warp < EPI_WARP0) {
         const int wt = threadIdx.x - 64;
+        const int q = warp & 3, h = (warp - 2) >> 2, i = q * 32 + lane;
         uint32_t g = 0;
         bool ok = true;
         for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
@@ -365,35 +404,29 @@ __global__ void __launch_bounds__(NTHR, 1)
                 const float *rawQ = reinterpret_cast<const float *>(sRaw + sr * C::RAW + C::RAW_A);
                 uint8_t *sp = sSplit + ss * C::SPL;
                 const int valid = (int)(r1 - (r0 + (int64_t)kb * TBK));  // rows of this stage inside the chunk
-                {   // A: thread -> column i, 16 consecutive K (= rows)
-                    const int i = wt & (TM - 1), kh = wt >> 7;
+                {   // A column i, rows 16h..16h+15 -> TMEM lane i
+                    uint32_t hi[16], lo[16];
 #pragma unroll
-                    for (int c4 = 0; c4 < 4; c4++) {
-                        float x[4];
-#pragma unroll
-                        for (int e = 0; e < 4; e++) {
-                            const int k = kh * 16 + c4 * 4 + e;
-                            x[e] = k < valid ? rawA[k * TM + i] : 0.f;
-                        }
-                        float4 h, l;
-                        split4(x, h, l);
-                        const uint32_t off = kmajor_off(i, kh * 4 + c4);
-                        *reinterpret_cast<float4 *>(sp + off) = h;
-                        *reinterpret_cast<float4 *>(sp + A_STAGE + off) = l;
+                    for (int e = 0; e < 16; e++) {
+                        const int k = h * 16 + e;
+                        split_tr(k < valid ? rawA[k * TM + i] : 0.f, hi[e], lo[e]);
                     }
+                    store_a(tmem, q, h, ss, hi, lo);
                 }
                 for (int idx = wt; idx < N * 8; idx += NSPLIT) {  // Q: (column j, 4-row chunk cc)
                     const int j = idx % N, cc = idx / N;
                     float x[4];
 #pragma unroll
                     for (int e = 0; e < 4; e++) x[e] = rawQ[(cc * 4 + e) * N + j];
-                    float4 h, l;
-                    split4(x, h, l);
+                    float4 hq, lq;
+                    split4(x, hq, lq);
                     const uint32_t off = kmajor_off(j, cc);
-                    *reinterpret_cast<float4 *>(sp + 2 * A_STAGE + off) = h;
-                    *reinterpret_cast<float4 *>(sp + 2 * A_STAGE + C::SPL_B + off) = l;
+                    *reinterpret_cast<float4 *>(sp + off) = hq;
+                    *reinterpret_cast<float4 *>(sp + C::SPL_B + off) = lq;
                 }
                 fence_proxy_async_smem();
+                tmem_wait_st();
+                tc_fence_before();
                 mbar_arrive(&bar->empty[sr]);   // raw stage consumed
                 mbar_arrive(&bar->split[ss]);   // split stage ready
             }
@@ -410,23 +443,7 @@ __global__ void __launch_bounds__(NTHR, 1)
             if (!wait_ok(&bar->acc_full[b], (it >> 1) & 1, abort_flag)) break;
             tc_fence_after();
             const int c = c0 + q * 32 + lane;
-#pragma unroll
-            for (int j0 = 0; j0 < N; j0 += 32) {
-                float v[32];
-                tmem_ld32(tmem + b * ACC_STRIDE + ((uint32_t)(q * 32) << 16) + (uint32_t)j0, v);
-                if (c < ncols) {
-                    float *dst = part + (chunk * ncols + c) * (int64_t)N + j0;
-                    if (j0 + 32 <= N) {
-#pragma unroll
-                        for (int j = 0; j < 32; j += 4)
-                            *reinterpret_cast<float4 *>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 32; j++)
-                            if (j0 + j < N) dst[j] = v[j];
-                    }
-                }
-            }
+            drain_acc<N>(tmem, b, q, lane, part + (chunk * ncols + c) * (int64_t)N, c < ncols);
             tc_fence_before();
             mbar_arrive(&bar->acc_empty[b]);
         }
@@ -453,22 +470,25 @@ __global__ void split_transpose_kernel(const float *__restrict__ Z, int64_t rows
     tl[idx] = rna_tf32(x - h);
 }
 
-// C[i * ldc + j] = sum_{s < chunks} part[s][i][j] (N x L per chunk), in chunk order
+// C[i * ldc + j] = sum_{s < chunks} part[s][i][j] (N x L per chunk).  A block covers 32
+// consecutive outputs with 8 row groups taking interleaved chunks; the groups are
+// combined in a fixed order, so the sum is deterministic.
 __global__ void sum_chunks_kernel(const float *__restrict__ part, int64_t chunks, int64_t N, int64_t L,
                                   float *__restrict__ C, int64_t ldc) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= N * L) return;
+    __shared__ float red[8][33];
+    const int cx = threadIdx.x & 31, gy = threadIdx.x >> 5;
+    const int64_t idx = (int64_t)blockIdx.x * 32 + cx;
     const int64_t stride = N * L;
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-    int64_t c = 0;
-    for (; c + 4 <= chunks; c += 4) {
-        s0 += part[(c + 0) * stride + idx];
-        s1 += part[(c + 1) * stride + idx];
-        s2 += part[(c + 2) * stride + idx];
-        s3 += part[(c + 3) * stride + idx];
+    float s = 0.f;
+    if (idx < stride)
+        for (int64_t c = gy; c < chunks; c += 8) s += part[c * stride + idx];
+    red[gy][cx] = s;
+    __syncthreads();
+    if (gy == 0 && idx < stride) {
+        float t = red[0][cx];
+        for (int g = 1; g < 8; g++) t += red[g][cx];
+        C[(idx / L) * ldc + idx % L] = t;
     }
-    for (; c < chunks; c++) s0 += part[c * stride + idx];
-    C[(idx / L) * ldc + idx % L] = (s0 + s1) + (s2 + s3);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -620,7 +640,7 @@ cudaError_t tc_gemm_tn(int64_t rows, int ncols, int N, const float *A, int64_t l
     }
     if (e != cudaSuccess) return e;
     const int64_t total = (int64_t)ncols * N;
-    sum_chunks_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, s>>>(part, sp.chunks, ncols, N, C, ldc);
+    sum_chunks_kernel<<<(unsigned)ceil_div(total, 32), 256, 0, s>>>(part, sp.chunks, ncols, N, C, ldc);
     note_launch();
     return cudaGetLastError();
 }

@@ -47,6 +47,14 @@ struct rsvd_plan {
     float *Bth = nullptr, *Btl = nullptr;
     float *tcpart = nullptr;
     int64_t tcpart_elems = 0;
+    // Golub-Kahan-Lanczos workspace, allocated on the first Krylov solve and grown with `steps`
+    void *gkl_ws = nullptr;
+    int gkl_cap = 0;
+    // CUDA graph of the last rsvd solve, replayed while the caller's pointers and flags repeat
+    cudaGraphExec_t graph = nullptr;
+    const void *gkey[6] = {};
+    unsigned gflags = 0;
+    uint64_t glaunches = 0;
     // tracing: event pairs recorded around stage groups while profiling is on
     bool prof = false;
     std::vector<cudaEvent_t> ev;
@@ -282,6 +290,7 @@ rsvd_status run_rsvd(rsvd_plan *P, T *A, const T *Omega, double *S, T *U, T *V) 
         Span sp(P, RSVD_STAGE_SMALL);
         if ((st = cqr2<T>(P, Tn, n, l, lp, Qz, Tmpn, true))) return st;       // T = Q_T R
         CK(jacobi_osvd<T, T>(P->Rt, l, lp, P->sig, UR, W, P->status, s));     // R = U_R Sigma W^T
+        CK(sv_refine<T>(P->Rt, l, lp, UR, W, P->sig, s));                     // sigma_i = u_i^T R w_i (float64)
     }
     {
         Span sp(P, RSVD_STAGE_FINISH);
@@ -334,6 +343,7 @@ rsvd_status run_exact(rsvd_plan *P, T *A, int method, double *S, T *U, T *V) {
             Span sp(P, RSVD_STAGE_SMALL);
             if (sizeof(T) == 8) CK(jacobi_osvd<double, T>(P->Rt, nn, nn, P->sig, UR, W, P->status, s));
             else CK(jacobi_osvd<float, T>(P->Rt, nn, nn, P->sig, UR, W, P->status, s));
+            CK(sv_refine<T>(P->Rt, nn, nn, UR, W, P->sig, s));
         }
         Span sp(P, RSVD_STAGE_FINISH);
         CK(gemm_nn<T>(m, n, n, Qw, n, UR, n, U, n, s));                               // U = Q U_R
@@ -346,6 +356,121 @@ rsvd_status run_exact(rsvd_plan *P, T *A, int method, double *S, T *U, T *V) {
     }
     P->last_count = nn;
     return RSVD_OK;
+}
+
+// Golub-Kahan-Lanczos with full reorthogonalisation (CGS2), then the SVD of the
+// steps x steps bidiagonal and the Ritz vectors; see svd_truncated_krylov().
+struct GklBufs {
+    void *Ut, *Vt, *w, *z, *part, *coef, *sq, *alpha, *beta, *nrm, *X, *Y;
+    double *B, *gpart;
+};
+
+GklBufs gkl_carve(rsvd_plan *P, int steps, char *base, size_t *bytes) {
+    const size_t es = esize(P->dtype);
+    const int64_t m = P->m, n = P->n;
+    const int64_t sp = round_up(steps, 16);
+    const int64_t nblk = gkl_reorth_blocks(m > n ? m : n);
+    Carver c;
+    c.base = base;
+    GklBufs b;
+    b.Ut = c.take(es * steps * m);
+    b.Vt = c.take(es * (steps + 1) * n);
+    b.w = c.take(es * m);
+    b.z = c.take(es * n);
+    b.part = c.take(es * nblk * (steps + 1));
+    b.gpart = (double *)c.take(sizeof(double) * gkl_gemv_chunks(m) * n);
+    b.coef = c.take(es * (steps + 1));
+    b.sq = c.take(es * nblk);
+    b.alpha = c.take(es * steps);
+    b.beta = c.take(es * steps);
+    b.nrm = c.take(es * 2);
+    b.X = c.take(es * sp * sp);
+    b.Y = c.take(es * sp * sp);
+    b.B = (double *)c.take(sizeof(double) * steps * steps);
+    *bytes = c.off;
+    return b;
+}
+
+template <typename T>
+rsvd_status run_gkl(rsvd_plan *P, T *A, const T *v1, int steps, double *S, T *U, T *V) {
+    cudaStream_t s = P->stream;
+    const int64_t m = P->m, n = P->n;
+    const int k = P->k, sp = (int)round_up(steps, 16);
+    size_t bytes = 0;
+    gkl_carve(P, steps, nullptr, &bytes);
+    if (steps > P->gkl_cap) {
+        if (P->gkl_ws) {
+            cudaStreamSynchronize(s);
+            cudaFree(P->gkl_ws);
+            P->gkl_ws = nullptr;
+            P->gkl_cap = 0;
+        }
+        if (cudaMalloc(&P->gkl_ws, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return RSVD_ERR_OOM;
+        }
+        P->gkl_cap = steps;
+    }
+    GklBufs b = gkl_carve(P, steps, (char *)P->gkl_ws, &bytes);
+    T *Ut = (T *)b.Ut, *Vt = (T *)b.Vt, *w = (T *)b.w, *z = (T *)b.z, *part = (T *)b.part, *coef = (T *)b.coef;
+    T *sq = (T *)b.sq, *alpha = (T *)b.alpha, *beta = (T *)b.beta, *nrm = (T *)b.nrm;
+    rsvd_status st;
+    {
+        Span sp_(P, RSVD_STAGE_CENTER);
+        if ((st = center<T>(P, A))) return st;
+    }
+    {   // v_1 = v1 / ||v1||
+        Span sp_(P, RSVD_STAGE_ORTH);
+        CK(copy2d<T, T>(v1, 1, z, 1, n, 1, 1, s));
+        CK(gkl_reorth_normalize<T>(Vt, n, 0, z, n, coef, part, sq, nrm, Vt, P->status, s));
+    }
+    for (int j = 0; j < steps; j++) {
+        {
+            Span sp_(P, RSVD_STAGE_AX);   // w = A v_j - beta_{j-1} u_{j-1}
+            CK(gkl_gemv_n<T>(A, m, (int)n, n, Vt + (int64_t)j * n, j ? beta + j - 1 : nullptr,
+                             j ? Ut + (int64_t)(j - 1) * m : nullptr, w, s));
+        }
+        {
+            Span sp_(P, RSVD_STAGE_ORTH);  // CGS2 against u_0..u_{j-1}; alpha_j = ||w||; u_j = w / alpha_j
+            CK(gkl_reorth_normalize<T>(Ut, m, j, w, m, coef, part, sq, alpha + j, Ut + (int64_t)j * m, P->status, s));
+        }
+        {
+            Span sp_(P, RSVD_STAGE_ATX);  // z = A^T u_j - alpha_j v_j
+            CK(gkl_gemv_t<T>(A, m, (int)n, n, Ut + (int64_t)j * m, alpha + j, Vt + (int64_t)j * n, z, b.gpart, s));
+        }
+        {
+            Span sp_(P, RSVD_STAGE_ORTH);  // CGS2 against v_0..v_j; beta_j = ||z||; v_{j+1} = z / beta_j
+            CK(gkl_reorth_normalize<T>(Vt, n, j + 1, z, n, coef, part, sq, beta + j, Vt + (int64_t)(j + 1) * n,
+                                       P->status, s));
+        }
+    }
+    T *X = (T *)b.X, *Y = (T *)b.Y;
+    {
+        Span sp_(P, RSVD_STAGE_SMALL);  // B = X Sigma Y^T (one-sided Jacobi on the dense bidiagonal)
+        CK(gkl_bidiag<T>(alpha, beta, steps, b.B, s));
+        if (sizeof(T) == 8) CK(jacobi_osvd<double, T>(b.B, steps, sp, P->sig, X, Y, P->status, s));
+        else CK(jacobi_osvd<float, T>(b.B, steps, sp, P->sig, X, Y, P->status, s));
+        CK(sv_refine<T>(b.B, steps, sp, X, Y, P->sig, s));
+    }
+    {
+        Span sp_(P, RSVD_STAGE_FINISH);  // Ritz vectors U_s X, V_s Y (leading k)
+        CK(gemm_tn<T>(steps, m, k, Ut, m, X, sp, U, k, (T *)P->part, P->part_elems, s));
+        CK(gemm_tn<T>(steps, n, k, Vt, n, Y, sp, V, k, (T *)P->part, P->part_elems, s));
+        CK(sign_normalize<T>(V, n, k, k, U, m, k, s));
+        CK(copy_f64(P->sig, S, k, s));
+    }
+    P->last_count = k;
+    return RSVD_OK;
+}
+
+rsvd_status rsvd_direct(rsvd_plan_t P, void *A, const void *Omega, double *S, void *U, void *V) {
+    if (P->dtype == RSVD_F32) return run_rsvd<float>(P, (float *)A, (const float *)Omega, S, (float *)U, (float *)V);
+    return run_rsvd<double>(P, (double *)A, (const double *)Omega, S, (double *)U, (double *)V);
+}
+
+void drop_graph(rsvd_plan *P) {
+    if (P->graph) cudaGraphExecDestroy(P->graph);
+    P->graph = nullptr;
 }
 
 }  // namespace
@@ -399,6 +524,8 @@ rsvd_status rsvd_plan_destroy(rsvd_plan_t P) {
     if (!P) return RSVD_OK;
     cudaStreamSynchronize(P->stream);
     for (cudaEvent_t e : P->ev) cudaEventDestroy(e);
+    drop_graph(P);
+    if (P->gkl_ws) cudaFree(P->gkl_ws);
     cudaFree(P->ws);
     delete P;
     return RSVD_OK;
@@ -428,8 +555,44 @@ rsvd_status rsvd_plan_sync(rsvd_plan_t P) {
 rsvd_status rsvd(rsvd_plan_t P, void *A, const float *col_scales, const void *Omega, double *S, void *U, void *V) {
     if (!P || !A || !Omega || !S || !U || !V) return RSVD_ERR_ARG;
     if (col_scales) return RSVD_ERR_ARG;
-    if (P->dtype == RSVD_F32) return run_rsvd<float>(P, (float *)A, (const float *)Omega, S, (float *)U, (float *)V);
-    return run_rsvd<double>(P, (double *)A, (const double *)Omega, S, (double *)U, (double *)V);
+    // Tracing records events between launches and the legacy stream cannot be captured:
+    // both run the launches directly.
+    if (P->prof || P->stream == nullptr) return rsvd_direct(P, A, Omega, S, U, V);
+    const void *key[6] = {A, Omega, S, U, V, P};
+    bool hit = P->graph && P->gflags == P->flags;
+    for (int i = 0; hit && i < 6; i++) hit = P->gkey[i] == key[i];
+    if (!hit) {
+        drop_graph(P);
+        cudaGraph_t g = nullptr;
+        const uint64_t before = rsvd_launch_count();
+        if (cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+            cudaGetLastError();
+            return rsvd_direct(P, A, Omega, S, U, V);
+        }
+        const rsvd_status st = rsvd_direct(P, A, Omega, S, U, V);
+        const cudaError_t ce = cudaStreamEndCapture(P->stream, &g);
+        const uint64_t captured = rsvd_launch_count() - before;
+        g_launches.fetch_sub(captured, std::memory_order_relaxed);  // captured, not yet executed
+        if (st != RSVD_OK || ce != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return st != RSVD_OK ? st : RSVD_ERR_CUDA;
+        }
+        cudaError_t ie = cudaGraphInstantiate(&P->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            P->graph = nullptr;
+            cudaGetLastError();
+            return rsvd_direct(P, A, Omega, S, U, V);
+        }
+        for (int i = 0; i < 6; i++) P->gkey[i] = key[i];
+        P->gflags = P->flags;
+        P->glaunches = captured;
+    }
+    if (cudaGraphLaunch(P->graph, P->stream) != cudaSuccess) return RSVD_ERR_CUDA;
+    note_launch((int)P->glaunches);
+    P->last_count = P->k;
+    return RSVD_OK;
 }
 
 rsvd_status svd_exact(rsvd_plan_t P, void *A, int method, double *S, void *U, void *V) {
@@ -442,8 +605,11 @@ rsvd_status svd_exact(rsvd_plan_t P, void *A, int method, double *S, void *U, vo
 
 rsvd_status svd_truncated_krylov(rsvd_plan_t P, void *A, const void *v1, int steps, double *S, void *U, void *V) {
     if (!P || !A || !v1 || !S || !U || !V) return RSVD_ERR_ARG;
-    if (steps < P->k || steps > P->n) return RSVD_ERR_ARG;
-    return RSVD_ERR_UNSUPPORTED;
+    if (steps < P->k || steps > P->n || steps < 1) return RSVD_ERR_ARG;
+    if (steps > (P->dtype == RSVD_F64 ? kSmallMaxF64 : kGklMaxStepsF32)) return RSVD_ERR_UNSUPPORTED;
+    if (P->dtype == RSVD_F32)
+        return run_gkl<float>(P, (float *)A, (const float *)v1, steps, S, (float *)U, (float *)V);
+    return run_gkl<double>(P, (double *)A, (const double *)v1, steps, S, (double *)U, (double *)V);
 }
 
 rsvd_status pca_threshold(rsvd_plan_t P, double t, int *K) {
