@@ -22,11 +22,12 @@
  * - Outputs are sorted by descending singular value.  Sign convention: the
  *   largest-magnitude entry of every right singular vector v_i is positive
  *   (u_i is flipped with it).
- * - Centring: by default every solve first centres A IN PLACE (A <- A - 1 mu^T,
- *   Sec. 1 assumption that each feature has zero mean) and records
- *   ||A||_F^2 of the centred matrix (Eq. sumeigen).  RSVD_FLAG_NO_CENTER
- *   skips the subtraction (A is taken as already centred) but still records
- *   ||A||_F^2.
+ * - Centring (Sec. 1 assumption that each feature has zero mean): by default
+ *   every solve works on the centred matrix A - 1 mu^T (mu = column means) and
+ *   records ||A - 1 mu^T||_F^2 (Eq. sumeigen).  rsvd and svd_truncated_krylov
+ *   never write A: the means are subtracted inside the products.  svd_exact
+ *   centres A IN PLACE.  RSVD_FLAG_NO_CENTER takes A as already centred
+ *   (mu = 0) but still records ||A||_F^2.
  * - Plans are not thread-safe: one plan serves one solve at a time.
  */
 #ifndef GB300_RSVD_H
@@ -104,7 +105,7 @@ rsvd_status rsvd_plan_sync(rsvd_plan_t plan);
  *   T = A^T Q (= B^T with B = Q^T A);  T = Vt Sigma W^T;  U = Q W.
  * orth() is CholeskyQR2 (R_ii > 0), which in exact arithmetic equals the
  * Householder QR the step list names.
- *   A      : m x n, row-major, centred in place unless RSVD_FLAG_NO_CENTER.
+ *   A      : m x n, row-major, read only (centred on the fly).
  *   col_scales : must be NULL for RSVD_F32 / RSVD_F64 (reserved for e4m3).
  *   Omega  : n x l Gaussian test matrix (caller-drawn), row-major.
  *   S      : k doubles; U : m x k; V : n x k (row-major).

@@ -35,6 +35,26 @@ template <typename T>
 cudaError_t center_columns(T *A, int64_t m, int64_t n, int64_t lda, bool subtract, double *mu,
                            double *fro2, double *part, cudaStream_t s);
 int64_t center_partials(int64_t m, int64_t n);
+// mu = column means (float64) and mu_t = the same in T, zero padded to npad entries (A read only).
+template <typename T>
+cudaError_t column_means(const T *A, int64_t m, int64_t n, int64_t lda, double *mu, T *mu_t, int64_t npad,
+                         double *part, cudaStream_t s);
+// *fro2 = ||A - 1 mu^T||_F^2 (mu may be NULL: ||A||_F^2), A read only.
+template <typename T>
+cudaError_t centered_fro2(const T *A, int64_t m, int64_t n, int64_t lda, const double *mu, double *fro2, double *part,
+                          cudaStream_t s);
+// out[c] = sum_r X[r][c] (dsum: float64 copy, cols entries; part: center_partials(rows, cols))
+template <typename T>
+cudaError_t column_sums(const T *X, int64_t rows, int64_t cols, int64_t ld, double *dsum, T *out, double *part,
+                        cudaStream_t s);
+// *out = sum of count doubles (fixed order)
+cudaError_t sum_f64(const double *x, int64_t count, double *out, cudaStream_t s);
+// C[r][c] -= (x ? x[r] : 1) * y[c] for r < rows, c < cols
+template <typename T>
+cudaError_t rank1_sub(T *C, int64_t rows, int64_t cols, int64_t ldc, const T *x, const T *y, cudaStream_t s);
+// c[j] = sum_k mu[k] B[k][j], j < N (float64 accumulation)
+template <typename T>
+cudaError_t vecmat(const T *mu, const T *B, int64_t K, int64_t N, int64_t ldb, T *c, cudaStream_t s);
 
 // ---------------------------------------------------------------- products
 // C (M x N) = A (M x K) * B (K x N); all row-major with leading dimensions.
@@ -110,26 +130,34 @@ bool tc_available();
 // th / tl (N x ldt) = tf32 hi / lo split of Z^T for Z rows x cols row-major (ldz); zero beyond.
 cudaError_t tc_split_transpose(const float *Z, int64_t rows, int cols, int64_t ldz, int N, float *th, float *tl,
                                int64_t ldt, cudaStream_t s);
-// Y (m x N) = A (m x n) Z with Z given as its transposed tf32 split (N x ldb each);
+// Y (m x N) = (A - 1 mu^T) Z with Z given as its transposed tf32 split (N x ldb each);
 // 3xTF32 on tcgen05.  N in {16, 32, ..., 128}; A, lda*4 and ldb*4 16-byte aligned.
+// mu (optional, 16-byte aligned, zero padded to a multiple of 32): column means
+// subtracted on the fly.  ssq (optional, tc_gemm_nn_grid(m) doubles): per-CTA
+// sums of the squared centred entries, i.e. ||A - 1 mu^T||_F^2 in parts.
 cudaError_t tc_gemm_nn(int64_t m, int n, int N, const float *A, int64_t lda, const float *Bth, const float *Btl,
-                       int64_t ldb, float *Y, int64_t ldy, int *status, cudaStream_t s);
-// C (ncols x N, ldc) = A^T Q for A rows x ncols (lda) and Q rows x N (ldq), 3xTF32 on
+                       int64_t ldb, float *Y, int64_t ldy, int *status, cudaStream_t s, const float *mu = nullptr,
+                       double *ssq = nullptr);
+int tc_gemm_nn_grid(int64_t m);
+// C (ncols x N, ldc) = (A - 1 mu^T)^T Q for A rows x ncols (lda) and Q rows x N (ldq), 3xTF32 on
 // tcgen05, split over row chunks into `part` (tc_gemm_tn_partials elements) and
-// summed in chunk order.  N in {16, ..., 128}; pointers and leading dimensions 16-byte aligned.
+// summed in chunk order.  N in {16, ..., 128}; pointers and leading dimensions 16-byte
+// aligned; mu optional (zero padded to a multiple of 128).
 cudaError_t tc_gemm_tn(int64_t rows, int ncols, int N, const float *A, int64_t lda, const float *Q, int64_t ldq,
-                       float *C, int64_t ldc, float *part, int64_t part_elems, int *status, cudaStream_t s);
+                       float *C, int64_t ldc, float *part, int64_t part_elems, int *status, cudaStream_t s,
+                       const float *mu = nullptr);
 int64_t tc_gemm_tn_partials(int64_t rows, int ncols, int N);
 
 // ------------------------------------------------------ Golub-Kahan-Lanczos
-// y = A v - beta[0] * uprev (beta / uprev may be NULL)
+// y = (A - 1 mu^T) v - beta[0] * uprev (beta / uprev / mu may be NULL)
 template <typename T>
 cudaError_t gkl_gemv_n(const T *A, int64_t m, int n, int64_t lda, const T *v, const T *beta, const T *uprev, T *y,
-                       cudaStream_t s);
-// z = A^T u - alpha[0] * vprev (alpha / vprev may be NULL); part: gkl_gemv_chunks(m) * n float64 scratch
+                       cudaStream_t s, const T *mu = nullptr);
+// z = (A - 1 mu^T)^T u - alpha[0] * vprev (alpha / vprev / mu may be NULL);
+// part: gkl_gemv_chunks(m) * (n + 1) float64 scratch
 template <typename T>
 cudaError_t gkl_gemv_t(const T *A, int64_t m, int n, int64_t lda, const T *u, const T *alpha, const T *vprev, T *z,
-                       double *part, cudaStream_t s);
+                       double *part, cudaStream_t s, const T *mu = nullptr);
 int64_t gkl_gemv_chunks(int64_t m);
 int64_t gkl_reorth_blocks(int64_t len);
 template <typename T>

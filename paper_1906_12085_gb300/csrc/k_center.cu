@@ -96,7 +96,7 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
 template <typename T, int VEC>
 __global__ void __launch_bounds__(kThreads) center_sq_kernel(T *__restrict__ A, int64_t m, int64_t n, int64_t lda,
                                                              int64_t rows_per_chunk, const double *__restrict__ mu,
-                                                             int subtract, double *__restrict__ sq) {
+                                                             int subtract, double *__restrict__ sq, int write = 1) {
     __shared__ double red[kThreads / 32];
     const int64_t r0 = (int64_t)blockIdx.x * rows_per_chunk;
     const int64_t r1 = min(m, r0 + rows_per_chunk);
@@ -117,10 +117,10 @@ __global__ void __launch_bounds__(kThreads) center_sq_kernel(T *__restrict__ A, 
                     unpack(*p, x);
 #pragma unroll
                     for (int v = 0; v < VEC; v++) x[v] -= mv[v];
-                    if (subtract) *p = pack<V>(x);
+                    if (subtract && write) *p = pack<V>(x);
                 } else {
                     x[0] = A[r * lda + c0] - mv[0];
-                    if (subtract) A[r * lda + c0] = x[0];
+                    if (subtract && write) A[r * lda + c0] = x[0];
                 }
 #pragma unroll
                 for (int v = 0; v < VEC; v++) sub += x[v] * x[v];
@@ -138,6 +138,33 @@ __global__ void sum_kernel(const double *__restrict__ x, int64_t count, double *
     for (int64_t i = threadIdx.x; i < count; i += blockDim.x) acc += x[i];
     const double t = block_sum(acc, red);
     if (threadIdx.x == 0) *out = t;
+}
+
+template <typename T>
+__global__ void mean_copy_kernel(const double *__restrict__ mu, int64_t n, int64_t npad, T *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < npad) out[i] = i < n ? (T)mu[i] : T(0);
+}
+
+// C[r][c] -= (x ? x[r] : 1) * y[c]
+template <typename T>
+__global__ void rank1_sub_kernel(T *__restrict__ C, int64_t rows, int64_t cols, int64_t ldc, const T *__restrict__ x,
+                                 const T *__restrict__ y) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * cols) return;
+    const int64_t r = idx / cols, c = idx % cols;
+    C[r * ldc + c] -= (x ? x[r] : T(1)) * y[c];
+}
+
+// c[j] = sum_k mu[k] B[k][j] (j < N), one thread per j
+template <typename T>
+__global__ void vecmat_kernel(const T *__restrict__ mu, const T *__restrict__ B, int64_t K, int64_t N, int64_t ldb,
+                              T *__restrict__ c) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    double s = 0.0;
+    for (int64_t k = 0; k < K; k++) s += (double)mu[k] * (double)B[k * ldb + j];
+    c[j] = (T)s;
 }
 
 int64_t chunk_rows(int64_t m) {
@@ -175,6 +202,86 @@ cudaError_t center_columns(T *A, int64_t m, int64_t n, int64_t lda, bool subtrac
     note_launch(2);
     return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t column_means(const T *A, int64_t m, int64_t n, int64_t lda, double *mu, T *mu_t, int64_t npad,
+                         double *part, cudaStream_t s) {
+    const int64_t rpc = chunk_rows(m);
+    const int64_t chunks = ceil_div(m, rpc);
+    constexpr int V = Vec<T>::n;
+    const bool vec = (n % V == 0) && (lda % V == 0) && ((uintptr_t)A % 16 == 0);
+    if (vec) colsum_kernel<T, V><<<(unsigned)chunks, kThreads, 0, s>>>(A, m, n, lda, rpc, part);
+    else colsum_kernel<T, 1><<<(unsigned)chunks, kThreads, 0, s>>>(A, m, n, lda, rpc, part);
+    colmean_kernel<<<(unsigned)ceil_div(n, 8), 256, 0, s>>>(part, chunks, n, m, mu);
+    mean_copy_kernel<T><<<(unsigned)ceil_div(npad, 256), 256, 0, s>>>(mu, n, npad, mu_t);
+    note_launch(3);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t column_sums(const T *X, int64_t rows, int64_t cols, int64_t ld, double *dsum, T *out, double *part,
+                        cudaStream_t s) {
+    const int64_t rpc = chunk_rows(rows);
+    const int64_t chunks = ceil_div(rows, rpc);
+    constexpr int V = Vec<T>::n;
+    const bool vec = (cols % V == 0) && (ld % V == 0) && ((uintptr_t)X % 16 == 0);
+    if (vec) colsum_kernel<T, V><<<(unsigned)chunks, kThreads, 0, s>>>(X, rows, cols, ld, rpc, part);
+    else colsum_kernel<T, 1><<<(unsigned)chunks, kThreads, 0, s>>>(X, rows, cols, ld, rpc, part);
+    colmean_kernel<<<(unsigned)ceil_div(cols, 8), 256, 0, s>>>(part, chunks, cols, 1, dsum);
+    mean_copy_kernel<T><<<(unsigned)ceil_div(cols, 256), 256, 0, s>>>(dsum, cols, cols, out);
+    note_launch(3);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t centered_fro2(const T *A, int64_t m, int64_t n, int64_t lda, const double *mu, double *fro2, double *part,
+                          cudaStream_t s) {
+    const int64_t rpc = chunk_rows(m);
+    const int64_t chunks = ceil_div(m, rpc);
+    double *sq = part + chunks * n;
+    constexpr int V = Vec<T>::n;
+    const bool vec = (n % V == 0) && (lda % V == 0) && ((uintptr_t)A % 16 == 0);
+    T *Aw = const_cast<T *>(A);  // read only: write = 0
+    if (vec) center_sq_kernel<T, V><<<(unsigned)chunks, kThreads, 0, s>>>(Aw, m, n, lda, rpc, mu, mu != nullptr, sq, 0);
+    else center_sq_kernel<T, 1><<<(unsigned)chunks, kThreads, 0, s>>>(Aw, m, n, lda, rpc, mu, mu != nullptr, sq, 0);
+    sum_kernel<<<1, 1024, 0, s>>>(sq, chunks, fro2);
+    note_launch(2);
+    return cudaGetLastError();
+}
+
+cudaError_t sum_f64(const double *x, int64_t count, double *out, cudaStream_t s) {
+    sum_kernel<<<1, 1024, 0, s>>>(x, count, out);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t rank1_sub(T *C, int64_t rows, int64_t cols, int64_t ldc, const T *x, const T *y, cudaStream_t s) {
+    const int64_t total = rows * cols;
+    if (total <= 0) return cudaSuccess;
+    rank1_sub_kernel<T><<<(unsigned)ceil_div(total, 256), 256, 0, s>>>(C, rows, cols, ldc, x, y);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t vecmat(const T *mu, const T *B, int64_t K, int64_t N, int64_t ldb, T *c, cudaStream_t s) {
+    vecmat_kernel<T><<<(unsigned)ceil_div(N, 128), 128, 0, s>>>(mu, B, K, N, ldb, c);
+    note_launch();
+    return cudaGetLastError();
+}
+
+#define INST_CENTER(T)                                                                                            \
+    template cudaError_t column_means<T>(const T *, int64_t, int64_t, int64_t, double *, T *, int64_t, double *,    \
+                                         cudaStream_t);                                                           \
+    template cudaError_t centered_fro2<T>(const T *, int64_t, int64_t, int64_t, const double *, double *, double *, \
+                                          cudaStream_t);                                                          \
+    template cudaError_t column_sums<T>(const T *, int64_t, int64_t, int64_t, double *, T *, double *,              \
+                                        cudaStream_t);                                                            \
+    template cudaError_t rank1_sub<T>(T *, int64_t, int64_t, int64_t, const T *, const T *, cudaStream_t);          \
+    template cudaError_t vecmat<T>(const T *, const T *, int64_t, int64_t, int64_t, T *, cudaStream_t);
+INST_CENTER(float)
+INST_CENTER(double)
 
 template cudaError_t center_columns<float>(float *, int64_t, int64_t, int64_t, bool, double *, double *, double *,
                                            cudaStream_t);

@@ -29,14 +29,27 @@ __device__ __forceinline__ T warp_red(T v) {
 }
 
 // y[r] = A[r] . v - (beta ? beta[0] : 0) * uprev[r]; one warp per row, v staged in shared memory.
+// With mu, the centred product (A - 1 mu^T) v = A v - (mu . v) is formed (each block
+// recomputes mu . v from shared memory).
 template <typename T, bool VEC>
 __global__ void __launch_bounds__(GT) gemv_n_kernel(const T *__restrict__ A, int64_t m, int n, int64_t lda,
                                                     const T *__restrict__ v, const T *__restrict__ beta,
-                                                    const T *__restrict__ uprev, T *__restrict__ y) {
+                                                    const T *__restrict__ uprev, T *__restrict__ y,
+                                                    const T *__restrict__ mu) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     T *vs = reinterpret_cast<T *>(sm_raw);
-    for (int c = threadIdx.x; c < n; c += GT) vs[c] = v[c];
+    __shared__ double mred[GT / 32];
+    double mv = 0.0;
+    for (int c = threadIdx.x; c < n; c += GT) {
+        vs[c] = v[c];
+        if (mu) mv += (double)mu[c] * (double)v[c];
+    }
+    mv = warp_red(mv);
+    if ((threadIdx.x & 31) == 0) mred[threadIdx.x >> 5] = mv;
     __syncthreads();
+    double mvt = 0.0;
+    for (int k = 0; k < GT / 32; k++) mvt += mred[k];
+    const T mdot = (T)mvt;
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (GT / 32);
     const T b = beta ? beta[0] : T(0);
@@ -56,7 +69,7 @@ __global__ void __launch_bounds__(GT) gemv_n_kernel(const T *__restrict__ A, int
         } else {
             for (int c = lane; c < n; c += 32) acc += row[c] * vs[c];
         }
-        acc = warp_red(acc);
+        acc = warp_red(acc) - mdot;
         if (lane == 0) y[r] = uprev ? acc - b * uprev[r] : acc;
     }
 }
@@ -67,11 +80,25 @@ __global__ void __launch_bounds__(GT) gemv_n_kernel(const T *__restrict__ A, int
 // cost of one float64 add per 32 rows.
 template <typename T, bool VEC>
 __global__ void __launch_bounds__(GT) gemv_t_kernel(const T *__restrict__ A, int64_t m, int n, int64_t lda,
-                                                    const T *__restrict__ u, int64_t rpc, double *__restrict__ part) {
+                                                    const T *__restrict__ u, int64_t rpc, double *__restrict__ part,
+                                                    double *__restrict__ usum) {
     constexpr int E = VEC ? V4<T>::n : 1;
     const int64_t r0 = (int64_t)blockIdx.x * rpc;
     const int64_t r1 = min(m, r0 + rpc);
     const int c0 = (blockIdx.y * GT + threadIdx.x) * E;
+    if (usum && blockIdx.y == 0) {  // sum of u over the chunk (for the mean correction), whole block
+        __shared__ double ured[GT / 32];
+        double su = 0.0;
+        for (int64_t r = r0 + threadIdx.x; r < r1; r += GT) su += (double)u[r];
+        su = warp_red(su);
+        if ((threadIdx.x & 31) == 0) ured[threadIdx.x >> 5] = su;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int k = 0; k < GT / 32; k++) t += ured[k];
+            usum[blockIdx.x] = t;
+        }
+    }
     if (c0 >= n) return;
     double acc[E];
 #pragma unroll
@@ -105,18 +132,30 @@ __global__ void __launch_bounds__(GT) gemv_t_kernel(const T *__restrict__ A, int
 // z[c] = sum_k part[k][c] - (alpha ? alpha[0] : 0) * vprev[c]; 8 row groups x 32 columns per block, fixed order
 template <typename T>
 __global__ void colsum_sub_kernel(const double *__restrict__ part, int64_t chunks, int n, const T *__restrict__ alpha,
-                                  const T *__restrict__ vprev, T *__restrict__ z) {
+                                  const T *__restrict__ vprev, T *__restrict__ z, const T *__restrict__ mu,
+                                  const double *__restrict__ usum) {
     __shared__ double red[8][33];
+    __shared__ double usr[8];
     const int cx = threadIdx.x & 31, gy = threadIdx.x >> 5;
     const int c = blockIdx.x * 32 + cx;
     double s = 0.0;
     if (c < n)
         for (int64_t k = gy; k < chunks; k += 8) s += part[k * n + c];
     red[gy][cx] = s;
+    if (mu && cx == 0) {
+        double su = 0.0;
+        for (int64_t k = gy; k < chunks; k += 8) su += usum[k];
+        usr[gy] = su;
+    }
     __syncthreads();
     if (gy == 0 && c < n) {
         double t = red[0][cx];
         for (int g = 1; g < 8; g++) t += red[g][cx];
+        if (mu) {
+            double su = usr[0];
+            for (int g = 1; g < 8; g++) su += usr[g];
+            t -= (double)mu[c] * su;
+        }
         z[c] = alpha ? (T)(t - (double)alpha[0] * (double)vprev[c]) : (T)t;
     }
 }
@@ -240,7 +279,7 @@ int64_t gkl_gemv_chunks(int64_t m) {
 
 template <typename T>
 cudaError_t gkl_gemv_n(const T *A, int64_t m, int n, int64_t lda, const T *v, const T *beta, const T *uprev, T *y,
-                       cudaStream_t s) {
+                       cudaStream_t s, const T *mu) {
     constexpr int E = V4<T>::n;
     const bool vec = (n % E == 0) && (lda % E == 0) && ((uintptr_t)A % 16 == 0);
     int64_t blocks = ceil_div(m, GT / 32);
@@ -250,24 +289,25 @@ cudaError_t gkl_gemv_n(const T *A, int64_t m, int n, int64_t lda, const T *v, co
         cudaFuncSetAttribute(gemv_n_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(gemv_n_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     }
-    if (vec) gemv_n_kernel<T, true><<<(unsigned)blocks, GT, smem, s>>>(A, m, n, lda, v, beta, uprev, y);
-    else gemv_n_kernel<T, false><<<(unsigned)blocks, GT, smem, s>>>(A, m, n, lda, v, beta, uprev, y);
+    if (vec) gemv_n_kernel<T, true><<<(unsigned)blocks, GT, smem, s>>>(A, m, n, lda, v, beta, uprev, y, mu);
+    else gemv_n_kernel<T, false><<<(unsigned)blocks, GT, smem, s>>>(A, m, n, lda, v, beta, uprev, y, mu);
     note_launch();
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t gkl_gemv_t(const T *A, int64_t m, int n, int64_t lda, const T *u, const T *alpha, const T *vprev, T *z,
-                       double *part, cudaStream_t s) {
+                       double *part, cudaStream_t s, const T *mu) {
     constexpr int E = V4<T>::n;
     const bool vec = (n % E == 0) && (lda % E == 0) && ((uintptr_t)A % 16 == 0);
     const int64_t rpc = m < 4096 ? 64 : 2048;
     const int64_t chunks = ceil_div(m, rpc);
     const int cols_per_block = GT * (vec ? E : 1);
     dim3 grid((unsigned)chunks, (unsigned)ceil_div(n, cols_per_block));
-    if (vec) gemv_t_kernel<T, true><<<grid, GT, 0, s>>>(A, m, n, lda, u, rpc, part);
-    else gemv_t_kernel<T, false><<<grid, GT, 0, s>>>(A, m, n, lda, u, rpc, part);
-    colsum_sub_kernel<T><<<(unsigned)ceil_div(n, 32), 256, 0, s>>>(part, chunks, n, alpha, vprev, z);
+    double *usum = mu ? part + chunks * n : nullptr;  // chunks extra entries after the column partials
+    if (vec) gemv_t_kernel<T, true><<<grid, GT, 0, s>>>(A, m, n, lda, u, rpc, part, usum);
+    else gemv_t_kernel<T, false><<<grid, GT, 0, s>>>(A, m, n, lda, u, rpc, part, usum);
+    colsum_sub_kernel<T><<<(unsigned)ceil_div(n, 32), 256, 0, s>>>(part, chunks, n, alpha, vprev, z, mu, usum);
     note_launch(2);
     return cudaGetLastError();
 }
@@ -310,10 +350,10 @@ cudaError_t gkl_bidiag(const T *alpha, const T *beta, int steps, double *B, cuda
 
 #define INST_GKL(T)                                                                                                  \
     template cudaError_t gkl_gemv_n<T>(const T *, int64_t, int, int64_t, const T *, const T *, const T *, T *,        \
-                                       cudaStream_t);                                                                \
+                                       cudaStream_t, const T *);                                                     \
     template cudaError_t gkl_gemv_t<T>(const T *, int64_t, int, int64_t, const T *, const T *, const T *, T *,       \
                                        double *,                                                                     \
-                                       cudaStream_t);                                                                \
+                                       cudaStream_t, const T *);                                                     \
     template cudaError_t gkl_reorth_normalize<T>(const T *, int64_t, int, T *, int64_t, T *, T *, T *, T *, T *,     \
                                                  int *, cudaStream_t);                                               \
     template cudaError_t gkl_bidiag<T>(const T *, const T *, int, double *, cudaStream_t);

@@ -79,6 +79,7 @@ struct Bars {
     uint64_t full[S], split[S], empty[S];
     uint64_t tempty[TS];  // TMEM A stage free (NN)
     uint64_t acc_full[2], acc_empty[2];
+    double ssq_w[NSPLIT / 32];
     uint32_t tmem;
     int abort_flag;
 };
@@ -150,7 +151,7 @@ template <int N>
 __global__ void __launch_bounds__(NTHR, 1)
     tc_nn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBh,
                  const __grid_constant__ CUtensorMap tmBl, int64_t m, int n, float *__restrict__ Y, int64_t ldy,
-                 int *__restrict__ status) {
+                 int *__restrict__ status, const float *__restrict__ mu, double *__restrict__ ssq) {
     using C = NNCfg<N>;
     constexpr int S = C::S;
     extern __shared__ uint8_t smem_raw[];
@@ -227,10 +228,18 @@ __global__ void __launch_bounds__(NTHR, 1)
             }
         }
     } else if (warp < EPI_WARP0) {
+        // split workers; with `mu` the column means are subtracted on the fly (A itself
+        // is never written), with `ssq` the squared centred entries of valid rows are summed
+        // Stage g's TMEM stores are waited for (and the stage signalled) only after the
+        // loads and split of stage g + 1, so the store latency overlaps useful work.
         const int q = warp & 3, h = (warp - 2) >> 2, r = q * 32 + lane;
         uint32_t g = 0;
         bool ok = true;
-        for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x)
+        int pend = -1;  // TMEM stage whose stores are still in flight
+        double acc64 = 0.0;
+        for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
+            const bool row_ok = t * TM + r < m;
+            float acc32 = 0.f;
             for (int kb = 0; kb < nkb; kb++, g++) {
                 const int s = g % S, ts = g % TS;
                 if (!(ok = wait_ok(&bar->full[s], (g / S) & 1, abort_flag))) break;
@@ -239,17 +248,37 @@ __global__ void __launch_bounds__(NTHR, 1)
                 uint32_t hi[16], lo[16];
 #pragma unroll
                 for (int c4 = 0; c4 < 4; c4++) {
-                    const float4 v = *reinterpret_cast<const float4 *>(raw + kmajor_off(r, h * 4 + c4));
+                    float4 v = *reinterpret_cast<const float4 *>(raw + kmajor_off(r, h * 4 + c4));
+                    if (mu) {
+                        const float4 mv = __ldg(reinterpret_cast<const float4 *>(mu + kb * TBK + h * 16 + c4 * 4));
+                        v.x -= mv.x; v.y -= mv.y; v.z -= mv.z; v.w -= mv.w;
+                    }
+                    if (ssq && row_ok) acc32 += v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w;
                     split_tr(v.x, hi[c4 * 4 + 0], lo[c4 * 4 + 0]);
                     split_tr(v.y, hi[c4 * 4 + 1], lo[c4 * 4 + 1]);
                     split_tr(v.z, hi[c4 * 4 + 2], lo[c4 * 4 + 2]);
                     split_tr(v.w, hi[c4 * 4 + 3], lo[c4 * 4 + 3]);
                 }
+                if (pend >= 0) {
+                    tmem_wait_st();
+                    tc_fence_before();
+                    mbar_arrive(&bar->split[pend]);
+                }
                 store_a(tmem, q, h, ts, hi, lo);
-                tmem_wait_st();
-                tc_fence_before();
-                mbar_arrive(&bar->split[ts]);
+                pend = ts;
             }
+            acc64 += (double)acc32;
+        }
+        if (pend >= 0) {
+            tmem_wait_st();
+            tc_fence_before();
+            mbar_arrive(&bar->split[pend]);
+        }
+        if (ssq) {  // per-warp partials; combined after the final barrier
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc64 += __shfl_xor_sync(0xffffffffu, acc64, o);
+            if (lane == 0) bar->ssq_w[warp - 2] = acc64;
+        }
     } else {
         const int q = warp & 3;
         uint32_t it = 0;
@@ -269,7 +298,14 @@ __global__ void __launch_bounds__(NTHR, 1)
         tc_fence_after();
         tmem_dealloc(tmem, TMEM_COLS);
     }
-    if (threadIdx.x == 0 && bar->abort_flag) atomicOr(status, (int)ST_TIMEOUT);
+    if (threadIdx.x == 0) {
+        if (bar->abort_flag) atomicOr(status, (int)ST_TIMEOUT);
+        if (ssq) {
+            double t = 0.0;
+            for (int w = 0; w < NSPLIT / 32; w++) t += bar->ssq_w[w];
+            ssq[blockIdx.x] = t;
+        }
+    }
 }
 
 // ======================================================================= TN
@@ -294,7 +330,8 @@ struct TNCfg {
 template <int N>
 __global__ void __launch_bounds__(NTHR, 1)
     tc_tn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmQ, int64_t rows,
-                 int ncols, int64_t rpc, int nchunks, float *__restrict__ part, int *__restrict__ status) {
+                 int ncols, int64_t rpc, int nchunks, float *__restrict__ part, int *__restrict__ status,
+                 const float *__restrict__ mu) {
     using C = TNCfg<N>;
     constexpr int SR = C::SR, SS = C::SS;
     extern __shared__ uint8_t smem_raw[];
@@ -387,10 +424,12 @@ __global__ void __launch_bounds__(NTHR, 1)
             }
         }
     } else if (warp < EPI_WARP0) {
+        // as in the NN kernel, stage g is signalled after the work of stage g + 1
         const int wt = threadIdx.x - 64;
         const int q = warp & 3, h = (warp - 2) >> 2, i = q * 32 + lane;
         uint32_t g = 0;
         bool ok = true;
+        int pend_sr = -1, pend_ss = -1;
         for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
             int64_t r0, r1;
             int c0;
@@ -404,12 +443,20 @@ __global__ void __launch_bounds__(NTHR, 1)
                 const float *rawQ = reinterpret_cast<const float *>(sRaw + sr * C::RAW + C::RAW_A);
                 uint8_t *sp = sSplit + ss * C::SPL;
                 const int valid = (int)(r1 - (r0 + (int64_t)kb * TBK));  // rows of this stage inside the chunk
-                {   // A column i, rows 16h..16h+15 -> TMEM lane i
+                {   // A column i, rows 16h..16h+15 -> TMEM lane i (column mean subtracted when given)
+                    const float mc = mu ? __ldg(mu + c0 + i) : 0.f;
                     uint32_t hi[16], lo[16];
 #pragma unroll
                     for (int e = 0; e < 16; e++) {
                         const int k = h * 16 + e;
-                        split_tr(k < valid ? rawA[k * TM + i] : 0.f, hi[e], lo[e]);
+                        split_tr(k < valid ? rawA[k * TM + i] - mc : 0.f, hi[e], lo[e]);
+                    }
+                    if (pend_ss >= 0) {
+                        fence_proxy_async_smem();
+                        tmem_wait_st();
+                        tc_fence_before();
+                        mbar_arrive(&bar->empty[pend_sr]);   // raw stage consumed
+                        mbar_arrive(&bar->split[pend_ss]);   // split stage ready
                     }
                     store_a(tmem, q, h, ss, hi, lo);
                 }
@@ -424,12 +471,16 @@ __global__ void __launch_bounds__(NTHR, 1)
                     *reinterpret_cast<float4 *>(sp + off) = hq;
                     *reinterpret_cast<float4 *>(sp + C::SPL_B + off) = lq;
                 }
-                fence_proxy_async_smem();
-                tmem_wait_st();
-                tc_fence_before();
-                mbar_arrive(&bar->empty[sr]);   // raw stage consumed
-                mbar_arrive(&bar->split[ss]);   // split stage ready
+                pend_sr = sr;
+                pend_ss = ss;
             }
+        }
+        if (pend_ss >= 0) {
+            fence_proxy_async_smem();
+            tmem_wait_st();
+            tc_fence_before();
+            mbar_arrive(&bar->empty[pend_sr]);
+            mbar_arrive(&bar->split[pend_ss]);
         }
     } else {
         const int q = warp & 3;
@@ -536,7 +587,7 @@ int num_sms() {
 
 template <int N>
 cudaError_t launch_nn(const CUtensorMap &a, const CUtensorMap &bh, const CUtensorMap &bl, int64_t m, int n, float *Y,
-                      int64_t ldy, int *status, cudaStream_t s) {
+                      int64_t ldy, int *status, const float *mu, double *ssq, cudaStream_t s) {
     using C = NNCfg<N>;
     static bool attr = false;
     if (!attr) {
@@ -545,14 +596,14 @@ cudaError_t launch_nn(const CUtensorMap &a, const CUtensorMap &bh, const CUtenso
     }
     const int64_t tiles = ceil_div(m, TM);
     const int grid = (int)(tiles < num_sms() ? tiles : num_sms());
-    tc_nn_kernel<N><<<grid, NTHR, C::SMEM, s>>>(a, bh, bl, m, n, Y, ldy, status);
+    tc_nn_kernel<N><<<grid, NTHR, C::SMEM, s>>>(a, bh, bl, m, n, Y, ldy, status, mu, ssq);
     note_launch();
     return cudaGetLastError();
 }
 
 template <int N>
 cudaError_t launch_tn(const CUtensorMap &a, const CUtensorMap &qm, int64_t rows, int ncols, int64_t rpc, int nchunks,
-                      float *part, int *status, cudaStream_t s) {
+                      float *part, int *status, const float *mu, cudaStream_t s) {
     using C = TNCfg<N>;
     static bool attr = false;
     if (!attr) {
@@ -561,7 +612,7 @@ cudaError_t launch_tn(const CUtensorMap &a, const CUtensorMap &qm, int64_t rows,
     }
     const int64_t tiles = ceil_div(ncols, TM) * nchunks;
     const int grid = (int)(tiles < num_sms() ? tiles : num_sms());
-    tc_tn_kernel<N><<<grid, NTHR, C::SMEM, s>>>(a, qm, rows, ncols, rpc, nchunks, part, status);
+    tc_tn_kernel<N><<<grid, NTHR, C::SMEM, s>>>(a, qm, rows, ncols, rpc, nchunks, part, status, mu);
     note_launch();
     return cudaGetLastError();
 }
@@ -594,22 +645,29 @@ cudaError_t tc_split_transpose(const float *Z, int64_t rows, int cols, int64_t l
     return cudaGetLastError();
 }
 
+int tc_gemm_nn_grid(int64_t m) {
+    const int64_t tiles = ceil_div(m, TM);
+    return (int)(tiles < num_sms() ? tiles : num_sms());
+}
+
 cudaError_t tc_gemm_nn(int64_t m, int n, int N, const float *A, int64_t lda, const float *Bth, const float *Btl,
-                       int64_t ldb, float *Y, int64_t ldy, int *status, cudaStream_t s) {
+                       int64_t ldb, float *Y, int64_t ldy, int *status, cudaStream_t s, const float *mu,
+                       double *ssq) {
     if (N % 16 || N < 16 || N > 128) return cudaErrorInvalidValue;
+    if (mu && (reinterpret_cast<uintptr_t>(mu) & 15)) return cudaErrorInvalidValue;
     CUtensorMap ma, mbh, mbl;
     if (!make_map(&ma, A, m, n, lda, TM, TBK, true) || !make_map(&mbh, Bth, N, n, ldb, N, TBK, true) ||
         !make_map(&mbl, Btl, N, n, ldb, N, TBK, true))
         return cudaErrorInvalidValue;
     switch (N) {
-        case 16: return launch_nn<16>(ma, mbh, mbl, m, n, Y, ldy, status, s);
-        case 32: return launch_nn<32>(ma, mbh, mbl, m, n, Y, ldy, status, s);
-        case 48: return launch_nn<48>(ma, mbh, mbl, m, n, Y, ldy, status, s);
-        case 64: return launch_nn<64>(ma, mbh, mbl, m, n, Y, ldy, status, s);
-        case 80: return launch_nn<80>(ma, mbh, mbl, m, n, Y, ldy, status, s);
-        case 96: return launch_nn<96>(ma, mbh, mbl, m, n, Y, ldy, status, s);
-        case 112: return launch_nn<112>(ma, mbh, mbl, m, n, Y, ldy, status, s);
-        case 128: return launch_nn<128>(ma, mbh, mbl, m, n, Y, ldy, status, s);
+        case 16: return launch_nn<16>(ma, mbh, mbl, m, n, Y, ldy, status, mu, ssq, s);
+        case 32: return launch_nn<32>(ma, mbh, mbl, m, n, Y, ldy, status, mu, ssq, s);
+        case 48: return launch_nn<48>(ma, mbh, mbl, m, n, Y, ldy, status, mu, ssq, s);
+        case 64: return launch_nn<64>(ma, mbh, mbl, m, n, Y, ldy, status, mu, ssq, s);
+        case 80: return launch_nn<80>(ma, mbh, mbl, m, n, Y, ldy, status, mu, ssq, s);
+        case 96: return launch_nn<96>(ma, mbh, mbl, m, n, Y, ldy, status, mu, ssq, s);
+        case 112: return launch_nn<112>(ma, mbh, mbl, m, n, Y, ldy, status, mu, ssq, s);
+        case 128: return launch_nn<128>(ma, mbh, mbl, m, n, Y, ldy, status, mu, ssq, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -620,7 +678,8 @@ int64_t tc_gemm_tn_partials(int64_t rows, int ncols, int N) {
 }
 
 cudaError_t tc_gemm_tn(int64_t rows, int ncols, int N, const float *A, int64_t lda, const float *Q, int64_t ldq,
-                       float *C, int64_t ldc, float *part, int64_t part_elems, int *status, cudaStream_t s) {
+                       float *C, int64_t ldc, float *part, int64_t part_elems, int *status, cudaStream_t s,
+                       const float *mu) {
     if (N % 16 || N < 16 || N > 128) return cudaErrorInvalidValue;
     const TNSplit sp = tn_split(rows, ncols);
     if (part == nullptr || part_elems < (int64_t)sp.chunks * ncols * N) return cudaErrorInvalidValue;
@@ -629,14 +688,14 @@ cudaError_t tc_gemm_tn(int64_t rows, int ncols, int N, const float *A, int64_t l
         return cudaErrorInvalidValue;
     cudaError_t e = cudaErrorInvalidValue;
     switch (N) {
-        case 16: e = launch_tn<16>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, s); break;
-        case 32: e = launch_tn<32>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, s); break;
-        case 48: e = launch_tn<48>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, s); break;
-        case 64: e = launch_tn<64>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, s); break;
-        case 80: e = launch_tn<80>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, s); break;
-        case 96: e = launch_tn<96>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, s); break;
-        case 112: e = launch_tn<112>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, s); break;
-        case 128: e = launch_tn<128>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, s); break;
+        case 16: e = launch_tn<16>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s); break;
+        case 32: e = launch_tn<32>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s); break;
+        case 48: e = launch_tn<48>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s); break;
+        case 64: e = launch_tn<64>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s); break;
+        case 80: e = launch_tn<80>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s); break;
+        case 96: e = launch_tn<96>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s); break;
+        case 112: e = launch_tn<112>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s); break;
+        case 128: e = launch_tn<128>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s); break;
     }
     if (e != cudaSuccess) return e;
     const int64_t total = (int64_t)ncols * N;

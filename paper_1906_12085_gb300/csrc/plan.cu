@@ -32,6 +32,11 @@ struct rsvd_plan {
     size_t ws_bytes = 0;
     // carved workspace
     double *mu = nullptr, *fro2 = nullptr, *cpart = nullptr;
+    void *mu_t = nullptr;        // column means in the element type, zero padded to npad
+    int64_t npad = 0;
+    double *ssq = nullptr;       // per-CTA partial sums of squares from the sketch product
+    void *cvec = nullptr;        // rank-1 correction vectors (CUDA-core fallback)
+    double *dsum = nullptr;
     void *Y = nullptr, *Qb = nullptr, *Tmp = nullptr;   // m x wide
     void *Ob = nullptr, *Z = nullptr, *Qz = nullptr, *Tn = nullptr, *Vt = nullptr, *Tmpn = nullptr;  // n x max(lp, nx)
     void *part = nullptr;
@@ -84,7 +89,16 @@ void carve(rsvd_plan *P, Carver &c) {
     const int64_t nw = sq;                               // width of the n-row buffers
     P->mu = (double *)c.take(sizeof(double) * n);
     P->fro2 = (double *)c.take(sizeof(double));
-    P->cpart = (double *)c.take(sizeof(double) * center_partials(m, n));
+    {
+        int64_t cp = center_partials(m, n);
+        const int64_t cq = center_partials(m, P->wide);
+        P->cpart = (double *)c.take(sizeof(double) * (cp > cq ? cp : cq));
+    }
+    P->npad = round_up(n, 128);
+    P->mu_t = c.take(es * P->npad);
+    P->ssq = (double *)c.take(sizeof(double) * 2048);
+    P->cvec = c.take(es * P->wide);
+    P->dsum = (double *)c.take(sizeof(double) * (P->wide > n ? P->wide : n));
     P->Y = c.take(es * m * P->wide);
     P->Qb = c.take(es * m * P->wide);
     P->Tmp = c.take(es * m * P->wide);
@@ -179,59 +193,84 @@ inline bool al16(const void *p, int64_t ld, size_t es) {
     return (reinterpret_cast<uintptr_t>(p) & 15) == 0 && ((ld * (int64_t)es) & 15) == 0;
 }
 
-// Y (rows x N) = X (rows x K) B, B row-major K x N (ldb), N = lp.
+// Y (rows x N) = (X - 1 mu^T) B, B row-major K x N (ldb), N = lp.  mu (element type,
+// padded) may be NULL.  When fro2 is given it receives ||X - 1 mu^T||_F^2.
 template <typename T>
 cudaError_t prod_nn(rsvd_plan *P, int64_t rows, int64_t K, const T *X, int64_t ldx, const T *B, int64_t ldb, T *Y,
-                    int64_t ldy) {
+                    int64_t ldy, const T *mu = nullptr, double *fro2 = nullptr) {
     if constexpr (sizeof(T) == 4) {
         if (P->tc && al16(X, ldx, 4) && (ldy % 4) == 0 && K <= P->ldt) {
             cudaError_t e = tc_split_transpose(B, K, P->lp, ldb, P->lp, P->Bth, P->Btl, P->ldt, P->stream);
             if (e == cudaSuccess)
-                e = tc_gemm_nn(rows, (int)K, P->lp, X, ldx, P->Bth, P->Btl, P->ldt, Y, ldy, P->status, P->stream);
+                e = tc_gemm_nn(rows, (int)K, P->lp, X, ldx, P->Bth, P->Btl, P->ldt, Y, ldy, P->status, P->stream, mu,
+                               fro2 ? P->ssq : nullptr);
+            if (e == cudaSuccess && fro2) e = sum_f64(P->ssq, tc_gemm_nn_grid(rows), fro2, P->stream);
             if (e != cudaErrorInvalidValue) return e;
             cudaGetLastError();
         }
     }
-    return gemm_nn<T>(rows, P->lp, K, X, ldx, B, ldb, Y, ldy, P->stream);
+    cudaError_t e = cudaSuccess;
+    if (fro2) e = centered_fro2<T>(X, rows, K, ldx, mu ? P->mu : nullptr, fro2, P->cpart, P->stream);
+    if (e == cudaSuccess) e = gemm_nn<T>(rows, P->lp, K, X, ldx, B, ldb, Y, ldy, P->stream);
+    if (e == cudaSuccess && mu) {  // exact rank-1 correction: Y -= 1 (mu^T B)
+        e = vecmat<T>(mu, B, K, P->lp, ldb, (T *)P->cvec, P->stream);
+        if (e == cudaSuccess) e = rank1_sub<T>(Y, rows, P->lp, ldy, nullptr, (T *)P->cvec, P->stream);
+    }
+    return e;
 }
 
-// C (ncols x N) = X^T Q with X rows x ncols (ldx), Q rows x N (ldq), N = lp.
+// C (ncols x N) = (X - 1 mu^T)^T Q with X rows x ncols (ldx), Q rows x N (ldq), N = lp.
 template <typename T>
 cudaError_t prod_tn(rsvd_plan *P, int64_t rows, int64_t ncols, const T *X, int64_t ldx, const T *Q, int64_t ldq,
-                    T *C, int64_t ldc) {
+                    T *C, int64_t ldc, const T *mu = nullptr) {
     if constexpr (sizeof(T) == 4) {
         if (P->tc && al16(X, ldx, 4) && al16(Q, ldq, 4) &&
             tc_gemm_tn_partials(rows, (int)ncols, P->lp) <= P->tcpart_elems) {
             cudaError_t e = tc_gemm_tn(rows, (int)ncols, P->lp, X, ldx, Q, ldq, C, ldc, P->tcpart, P->tcpart_elems,
-                                       P->status, P->stream);
+                                       P->status, P->stream, mu);
             if (e != cudaErrorInvalidValue) return e;
             cudaGetLastError();
         }
     }
-    return gemm_tn<T>(rows, ncols, P->lp, X, ldx, Q, ldq, C, ldc, (T *)P->part, P->part_elems, P->stream);
+    cudaError_t e = gemm_tn<T>(rows, ncols, P->lp, X, ldx, Q, ldq, C, ldc, (T *)P->part, P->part_elems, P->stream);
+    if (e == cudaSuccess && mu) {  // exact rank-1 correction: C -= mu (1^T Q)
+        e = column_sums<T>(Q, rows, P->lp, ldq, P->dsum, (T *)P->cvec, P->cpart, P->stream);
+        if (e == cudaSuccess) e = rank1_sub<T>(C, ncols, P->lp, ldc, mu, (T *)P->cvec, P->stream);
+    }
+    return e;
 }
 
-// CholeskyQR2 of X (rows x w, ld): Qo = X R^{-1} with R = R2 R1 (written to Rt
-// when want_r).  R1 from chol(X^T X); Q1 = X R1^{-1} into Tmp; R2 from
-// chol(Q1^T Q1); Qo = Q1 R2^{-1}.
+// CholeskyQR of X (rows x w, ld) with one or two passes: Qo = X R^{-1}.
+// Pass 1: R1 = chol(X^T X), Q1 = X R1^{-1}.  Pass 2 (CholeskyQR2): R2 = chol(Q1^T Q1),
+// Qo = Q1 R2^{-1}, and R = R2 R1 is written to Rt when want_r.  One pass leaves Qo
+// well conditioned (||Qo^T Qo - I|| ~ u cond(X)^2) with exactly the range of X, which
+// is all an intermediate power-iteration basis needs; the final basis and the
+// factorisation of T use two passes.
 template <typename T>
-rsvd_status cqr2(rsvd_plan *P, const T *X, int64_t rows, int w, int ld, T *Qo, T *Tmp, bool want_r) {
+rsvd_status cqr(rsvd_plan *P, const T *X, int64_t rows, int w, int ld, T *Qo, T *Tmp, bool want_r, int passes = 2) {
     cudaStream_t s = P->stream;
     T *G = (T *)P->G, *Ric = (T *)P->Rinv_c, *part = (T *)P->part;
     const double u = unit_roundoff<T>();
     const bool skinny = ld == P->lp;  // the l-wide blocks of the randomized solver
+    T *Q1 = passes == 2 ? Tmp : Qo;
     if (skinny) CK(prod_tn<T>(P, rows, ld, X, ld, X, ld, G, ld));
     else CK(gemm_tn<T>(rows, ld, ld, X, ld, X, ld, G, ld, part, P->part_elems, s));
     CK(chol_inv<T, T, T>(G, ld, w, rows, u, P->R1, P->R1i, Ric, ld, P->status, s));
-    if (skinny) CK(prod_nn<T>(P, rows, ld, X, ld, Ric, ld, Tmp, ld));
-    else CK(gemm_nn<T>(rows, ld, ld, X, ld, Ric, ld, Tmp, ld, s));
-    if (skinny) CK(prod_tn<T>(P, rows, ld, Tmp, ld, Tmp, ld, G, ld));
-    else CK(gemm_tn<T>(rows, ld, ld, Tmp, ld, Tmp, ld, G, ld, part, P->part_elems, s));
+    if (skinny) CK(prod_nn<T>(P, rows, ld, X, ld, Ric, ld, Q1, ld));
+    else CK(gemm_nn<T>(rows, ld, ld, X, ld, Ric, ld, Q1, ld, s));
+    if (passes == 1) return RSVD_OK;
+    if (skinny) CK(prod_tn<T>(P, rows, ld, Q1, ld, Q1, ld, G, ld));
+    else CK(gemm_tn<T>(rows, ld, ld, Q1, ld, Q1, ld, G, ld, part, P->part_elems, s));
     CK(chol_inv<T, T, T>(G, ld, w, rows, u, P->R2, P->R2i, Ric, ld, P->status, s));
-    if (skinny) CK(prod_nn<T>(P, rows, ld, Tmp, ld, Ric, ld, Qo, ld));
-    else CK(gemm_nn<T>(rows, ld, ld, Tmp, ld, Ric, ld, Qo, ld, s));
+    if (skinny) CK(prod_nn<T>(P, rows, ld, Q1, ld, Ric, ld, Qo, ld));
+    else CK(gemm_nn<T>(rows, ld, ld, Q1, ld, Ric, ld, Qo, ld, s));
     if (want_r) CK(trmm_upper(P->R2, P->R1, P->Rt, w, s));
     return RSVD_OK;
+}
+
+template <typename T>
+rsvd_status cqr2(rsvd_plan *P, const T *X, int64_t rows, int w, int ld, T *Qo, T *Tmp, bool want_r) {
+    return cqr<T>(P, X, rows, w, ld, Qo, Tmp, want_r, 2);
 }
 
 template <typename T>
@@ -250,40 +289,47 @@ rsvd_status run_rsvd(rsvd_plan *P, T *A, const T *Omega, double *S, T *U, T *V) 
     T *Y = (T *)P->Y, *Q = (T *)P->Qb, *Tmp = (T *)P->Tmp;
     T *Ob = (T *)P->Ob, *Z = (T *)P->Z, *Qz = (T *)P->Qz, *Tn = (T *)P->Tn, *Vt = (T *)P->Vt, *Tmpn = (T *)P->Tmpn;
     rsvd_status st;
+    // A is read only: its column means mu are subtracted inside every product with A
+    const bool centred = !(P->flags & RSVD_FLAG_NO_CENTER);
+    const T *mu = centred ? (const T *)P->mu_t : nullptr;
     {
         Span sp(P, RSVD_STAGE_CENTER);
-        if ((st = center<T>(P, A))) return st;                                // A <- A - 1 mu^T, ||A||_F^2
+        if (centred) CK(column_means<T>(A, m, n, n, P->mu, (T *)P->mu_t, P->npad, P->cpart, s));
+        else CK(cudaMemsetAsync(P->mu, 0, sizeof(double) * n, s));
     }
     CK(copy2d<T, T>(Omega, l, Ob, lp, n, l, lp, s));                          // G padded to lp columns
     {
         Span sp(P, RSVD_STAGE_AX);
-        CK(prod_nn<T>(P, m, n, A, n, Ob, lp, Y, lp));                          // H(0) = A G
+        CK(prod_nn<T>(P, m, n, A, n, Ob, lp, Y, lp, mu, P->fro2));             // H(0) = A G, ||A||_F^2
     }
+    // re-orthonormalisation after every half step; one CholeskyQR pass for the
+    // intermediate bases, two for the final one (see cqr)
     {
         Span sp(P, RSVD_STAGE_ORTH);
-        if ((st = cqr2<T>(P, Y, m, l, lp, Q, Tmp, false))) return st;         // Q = orth(H)
+        if ((st = cqr<T>(P, Y, m, l, lp, Q, Tmp, false, P->q > 0 ? 1 : 2))) return st;  // Q = orth(H)
     }
     for (int it = 0; it < P->q; it++) {                                      // H(i) = A (A^T H(i-1))
+        const bool last = it == P->q - 1;
         {
             Span sp(P, RSVD_STAGE_ATX);
-            CK(prod_tn<T>(P, m, n, A, n, Q, lp, Z, lp));
+            CK(prod_tn<T>(P, m, n, A, n, Q, lp, Z, lp, mu));
         }
         {
             Span sp(P, RSVD_STAGE_ORTH);
-            if ((st = cqr2<T>(P, Z, n, l, lp, Qz, Tmpn, false))) return st;
+            if ((st = cqr<T>(P, Z, n, l, lp, Qz, Tmpn, false, 1))) return st;
         }
         {
             Span sp(P, RSVD_STAGE_AX);
-            CK(prod_nn<T>(P, m, n, A, n, Qz, lp, Y, lp));
+            CK(prod_nn<T>(P, m, n, A, n, Qz, lp, Y, lp, mu));
         }
         {
             Span sp(P, RSVD_STAGE_ORTH);
-            if ((st = cqr2<T>(P, Y, m, l, lp, Q, Tmp, false))) return st;
+            if ((st = cqr<T>(P, Y, m, l, lp, Q, Tmp, false, last ? 2 : 1))) return st;
         }
     }
     {
         Span sp(P, RSVD_STAGE_ATX);
-        CK(prod_tn<T>(P, m, n, A, n, Q, lp, Tn, lp));                           // T = A^T Q  (= B^T)
+        CK(prod_tn<T>(P, m, n, A, n, Q, lp, Tn, lp, mu));                       // T = A^T Q  (= B^T)
     }
     T *UR = (T *)P->UR, *W = (T *)P->Wm;
     {
@@ -378,7 +424,7 @@ GklBufs gkl_carve(rsvd_plan *P, int steps, char *base, size_t *bytes) {
     b.w = c.take(es * m);
     b.z = c.take(es * n);
     b.part = c.take(es * nblk * (steps + 1));
-    b.gpart = (double *)c.take(sizeof(double) * gkl_gemv_chunks(m) * n);
+    b.gpart = (double *)c.take(sizeof(double) * gkl_gemv_chunks(m) * (n + 1));
     b.coef = c.take(es * (steps + 1));
     b.sq = c.take(es * nblk);
     b.alpha = c.take(es * steps);
@@ -414,10 +460,13 @@ rsvd_status run_gkl(rsvd_plan *P, T *A, const T *v1, int steps, double *S, T *U,
     GklBufs b = gkl_carve(P, steps, (char *)P->gkl_ws, &bytes);
     T *Ut = (T *)b.Ut, *Vt = (T *)b.Vt, *w = (T *)b.w, *z = (T *)b.z, *part = (T *)b.part, *coef = (T *)b.coef;
     T *sq = (T *)b.sq, *alpha = (T *)b.alpha, *beta = (T *)b.beta, *nrm = (T *)b.nrm;
-    rsvd_status st;
+    // A is read only: the column means are subtracted inside the products
+    const bool centred = !(P->flags & RSVD_FLAG_NO_CENTER);
+    const T *mu = centred ? (const T *)P->mu_t : nullptr;
     {
         Span sp_(P, RSVD_STAGE_CENTER);
-        if ((st = center<T>(P, A))) return st;
+        if (centred) CK(column_means<T>(A, m, n, n, P->mu, (T *)P->mu_t, P->npad, P->cpart, s));
+        CK(centered_fro2<T>(A, m, n, n, centred ? P->mu : nullptr, P->fro2, P->cpart, s));
     }
     {   // v_1 = v1 / ||v1||
         Span sp_(P, RSVD_STAGE_ORTH);
@@ -428,7 +477,7 @@ rsvd_status run_gkl(rsvd_plan *P, T *A, const T *v1, int steps, double *S, T *U,
         {
             Span sp_(P, RSVD_STAGE_AX);   // w = A v_j - beta_{j-1} u_{j-1}
             CK(gkl_gemv_n<T>(A, m, (int)n, n, Vt + (int64_t)j * n, j ? beta + j - 1 : nullptr,
-                             j ? Ut + (int64_t)(j - 1) * m : nullptr, w, s));
+                             j ? Ut + (int64_t)(j - 1) * m : nullptr, w, s, mu));
         }
         {
             Span sp_(P, RSVD_STAGE_ORTH);  // CGS2 against u_0..u_{j-1}; alpha_j = ||w||; u_j = w / alpha_j
@@ -436,7 +485,8 @@ rsvd_status run_gkl(rsvd_plan *P, T *A, const T *v1, int steps, double *S, T *U,
         }
         {
             Span sp_(P, RSVD_STAGE_ATX);  // z = A^T u_j - alpha_j v_j
-            CK(gkl_gemv_t<T>(A, m, (int)n, n, Ut + (int64_t)j * m, alpha + j, Vt + (int64_t)j * n, z, b.gpart, s));
+            CK(gkl_gemv_t<T>(A, m, (int)n, n, Ut + (int64_t)j * m, alpha + j, Vt + (int64_t)j * n, z, b.gpart, s,
+                             mu));
         }
         {
             Span sp_(P, RSVD_STAGE_ORTH);  // CGS2 against v_0..v_j; beta_j = ||z||; v_{j+1} = z / beta_j
