@@ -186,7 +186,7 @@ def run_ours(args):
     m, n, k, p, q = w["m"], w["n"], w["k"], w["p"], w["q"]
     l = k + p
     A64, sigma, extras = synth.workload(WORKLOAD, device=dev)
-    A0 = A64.float().contiguous()           # pristine copy (inputs are re-centred in place each step)
+    A0 = A64.float().contiguous()           # pristine copy (host source of the end-to-end leg)
     del A64
     Om = extras["omega"].to(dev).contiguous()
     A = A0.clone()

@@ -154,11 +154,11 @@ template <typename T>
 cudaError_t gkl_gemv_n(const T *A, int64_t m, int n, int64_t lda, const T *v, const T *beta, const T *uprev, T *y,
                        cudaStream_t s, const T *mu = nullptr);
 // z = (A - 1 mu^T)^T u - alpha[0] * vprev (alpha / vprev / mu may be NULL);
-// part: gkl_gemv_chunks(m) * (n + 1) float64 scratch
+// part: gkl_gemv_chunks(m, n) * (n + 1) float64 scratch
 template <typename T>
 cudaError_t gkl_gemv_t(const T *A, int64_t m, int n, int64_t lda, const T *u, const T *alpha, const T *vprev, T *z,
                        double *part, cudaStream_t s, const T *mu = nullptr);
-int64_t gkl_gemv_chunks(int64_t m);
+int64_t gkl_gemv_chunks(int64_t m, int n);
 int64_t gkl_reorth_blocks(int64_t len);
 template <typename T>
 cudaError_t gkl_reorth_normalize(const T *Bt, int64_t ld, int cnt, T *w, int64_t len, T *coef, T *part, T *sq,

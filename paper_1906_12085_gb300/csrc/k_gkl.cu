@@ -163,35 +163,59 @@ __global__ void colsum_sub_kernel(const double *__restrict__ part, int64_t chunk
 // part[b][i] = sum over rows of block b of Bt[i][r] w[r], i < cnt (Bt cnt x len, ld).
 // Four basis vectors per sweep (independent accumulators); warp sums land in
 // shared memory and are combined once at the end, in warp order.
-template <typename T>
+// part[b][i] = sum over block b's rows r of Bt[i][r] w[r].  VEC: warp k takes the
+// vectors i = k, k + 8, ... (two at a time), each lane a strided run of E-wide loads
+// over the block's rows, with w staged in shared memory; one warp reduction per
+// vector.  Scalar form for lengths or strides that are not multiples of E.
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(GT) multi_dot_kernel(const T *__restrict__ Bt, int64_t ld, int cnt,
                                                        const T *__restrict__ w, int64_t len, int64_t rpb,
                                                        T *__restrict__ part) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    T *red = reinterpret_cast<T *>(sm_raw);  // cnt x (GT / 32)
+    T *ws = reinterpret_cast<T *>(sm_raw);  // rpb entries of w
     const int64_t r0 = (int64_t)blockIdx.x * rpb;
-    const int64_t r1 = min(len, r0 + rpb);
+    const int nr = (int)(min(len, r0 + rpb) - r0);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int i0 = 0; i0 < cnt; i0 += 4) {
-        T acc[4] = {T(0), T(0), T(0), T(0)};
-        const int nq = cnt - i0 < 4 ? cnt - i0 : 4;
-        for (int64_t r = r0 + threadIdx.x; r < r1; r += GT) {
-            const T wr = w[r];
-#pragma unroll
-            for (int q = 0; q < 4; q++)
-                if (q < nq) acc[q] += Bt[(int64_t)(i0 + q) * ld + r] * wr;
-        }
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const T t = warp_red(acc[q]);
-            if (lane == 0 && q < nq) red[(i0 + q) * (GT / 32) + wid] = t;
-        }
-    }
+    for (int r = threadIdx.x; r < nr; r += GT) ws[r] = w[r0 + r];
     __syncthreads();
-    for (int i = threadIdx.x; i < cnt; i += GT) {
-        T t = red[i * (GT / 32)];
-        for (int k = 1; k < GT / 32; k++) t += red[i * (GT / 32) + k];
-        part[(int64_t)blockIdx.x * cnt + i] = t;
+    if constexpr (VEC) {
+        using V = typename V4<T>::type;
+        constexpr int E = V4<T>::n;
+        for (int i = wid; i < cnt; i += 2 * (GT / 32)) {
+            const int i2 = i + GT / 32;
+            const bool two = i2 < cnt;
+            const T *b1 = Bt + (int64_t)i * ld + r0;
+            const T *b2 = Bt + (int64_t)(two ? i2 : i) * ld + r0;
+            T a1 = T(0), a2 = T(0);
+#pragma unroll 8
+            for (int r = lane * E; r < nr; r += 32 * E) {
+                const V x = *reinterpret_cast<const V *>(ws + r);
+                const V u1 = *reinterpret_cast<const V *>(b1 + r);
+                const V u2 = *reinterpret_cast<const V *>(b2 + r);
+                const T *px = reinterpret_cast<const T *>(&x);
+                const T *p1 = reinterpret_cast<const T *>(&u1);
+                const T *p2 = reinterpret_cast<const T *>(&u2);
+#pragma unroll
+                for (int e = 0; e < E; e++) {
+                    a1 += p1[e] * px[e];
+                    a2 += p2[e] * px[e];
+                }
+            }
+            a1 = warp_red(a1);
+            a2 = warp_red(a2);
+            if (lane == 0) {
+                part[(int64_t)blockIdx.x * cnt + i] = a1;
+                if (two) part[(int64_t)blockIdx.x * cnt + i2] = a2;
+            }
+        }
+    } else {
+        for (int i = wid; i < cnt; i += GT / 32) {
+            const T *b1 = Bt + (int64_t)i * ld + r0;
+            T a1 = T(0);
+            for (int r = lane; r < nr; r += 32) a1 += b1[r] * ws[r];
+            a1 = warp_red(a1);
+            if (lane == 0) part[(int64_t)blockIdx.x * cnt + i] = a1;
+        }
     }
 }
 
@@ -207,8 +231,10 @@ __global__ void sum_parts_kernel(const T *__restrict__ part, int64_t nblk, int c
     if (lane == 0) coef[i] = s;
 }
 
-// w[r] -= sum_i coef[i] Bt[i][r]; sq[b] = sum over the block's rows of w[r]^2 (after the update)
-template <typename T>
+// w[r] -= sum_i coef[i] Bt[i][r]; sq[b] = sum over the block's rows of w[r]^2 (after the update).
+// VEC: a thread owns E consecutive rows, so the loop over i runs E independent chains
+// with its loads issued ahead.
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(GT) multi_axpy_kernel(const T *__restrict__ Bt, int64_t ld, int cnt,
                                                         const T *__restrict__ coef, T *__restrict__ w, int64_t len,
                                                         int64_t rpb, T *__restrict__ sq) {
@@ -220,11 +246,31 @@ __global__ void __launch_bounds__(GT) multi_axpy_kernel(const T *__restrict__ Bt
     const int64_t r0 = (int64_t)blockIdx.x * rpb;
     const int64_t r1 = min(len, r0 + rpb);
     T s2 = T(0);
-    for (int64_t r = r0 + threadIdx.x; r < r1; r += GT) {
-        T x = w[r];
-        for (int i = 0; i < cnt; i++) x -= cs[i] * Bt[(int64_t)i * ld + r];
-        w[r] = x;
-        s2 += x * x;
+    if constexpr (VEC) {
+        using V = typename V4<T>::type;
+        constexpr int E = V4<T>::n;
+        for (int64_t r = r0 + (int64_t)threadIdx.x * E; r < r1; r += (int64_t)GT * E) {
+            V xv = *reinterpret_cast<const V *>(w + r);
+            T *x = reinterpret_cast<T *>(&xv);
+#pragma unroll 8
+            for (int i = 0; i < cnt; i++) {
+                const V bv = *reinterpret_cast<const V *>(Bt + (int64_t)i * ld + r);
+                const T *pb = reinterpret_cast<const T *>(&bv);
+                const T c = cs[i];
+#pragma unroll
+                for (int e = 0; e < E; e++) x[e] -= c * pb[e];
+            }
+            *reinterpret_cast<V *>(w + r) = xv;
+#pragma unroll
+            for (int e = 0; e < E; e++) s2 += x[e] * x[e];
+        }
+    } else {
+        for (int64_t r = r0 + threadIdx.x; r < r1; r += GT) {
+            T x = w[r];
+            for (int i = 0; i < cnt; i++) x -= cs[i] * Bt[(int64_t)i * ld + r];
+            w[r] = x;
+            s2 += x * x;
+        }
     }
     s2 = warp_red(s2);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s2;
@@ -272,10 +318,18 @@ __global__ void bidiag_kernel(const T *__restrict__ alpha, const T *__restrict__
 
 }  // namespace
 
-int64_t gkl_gemv_chunks(int64_t m) {
-    const int64_t rpc = m < 4096 ? 64 : 2048;
-    return ceil_div(m, rpc);
+// Rows per chunk of A^T u: small enough that the (chunk, column block) grid fills
+// about two waves of 8 blocks on every SM, at least 256 rows so each thread keeps
+// a long run of independent loads.  Partials cost 8 (n + 1) bytes per chunk.
+static int64_t gemv_t_rpc(int64_t m, int n) {
+    if (m < 4096) return 64;
+    const int64_t colblocks = ceil_div(n, GT * 4);
+    const int64_t want = ceil_div(2 * 8 * 152, colblocks);
+    const int64_t rpc = round_up(ceil_div(m, want), 32);
+    return rpc < 256 ? 256 : rpc;
 }
+
+int64_t gkl_gemv_chunks(int64_t m, int n) { return ceil_div(m, gemv_t_rpc(m, n)); }
 
 template <typename T>
 cudaError_t gkl_gemv_n(const T *A, int64_t m, int n, int64_t lda, const T *v, const T *beta, const T *uprev, T *y,
@@ -300,7 +354,7 @@ cudaError_t gkl_gemv_t(const T *A, int64_t m, int n, int64_t lda, const T *u, co
                        double *part, cudaStream_t s, const T *mu) {
     constexpr int E = V4<T>::n;
     const bool vec = (n % E == 0) && (lda % E == 0) && ((uintptr_t)A % 16 == 0);
-    const int64_t rpc = m < 4096 ? 64 : 2048;
+    const int64_t rpc = gemv_t_rpc(m, n);
     const int64_t chunks = ceil_div(m, rpc);
     const int cols_per_block = GT * (vec ? E : 1);
     dim3 grid((unsigned)chunks, (unsigned)ceil_div(n, cols_per_block));
@@ -321,18 +375,25 @@ int64_t gkl_reorth_blocks(int64_t len) { return ceil_div(len, kReorthRows); }
 template <typename T>
 cudaError_t gkl_reorth_normalize(const T *Bt, int64_t ld, int cnt, T *w, int64_t len, T *coef, T *part, T *sq,
                                  T *nrm, T *out, int *status, cudaStream_t s) {
-    const int64_t rpb = kReorthRows;
+    constexpr int E = V4<T>::n;
+    const int64_t rpb = kReorthRows;  // a multiple of 32 E
     const int64_t nblk = ceil_div(len, rpb);
+    // E-wide loads need every vector (and w) to start on a 16-byte boundary and whole E-groups
+    const bool vec = ld % E == 0 && len % E == 0 && (reinterpret_cast<uintptr_t>(Bt) & 15) == 0 &&
+                     (reinterpret_cast<uintptr_t>(w) & 15) == 0;
     const size_t smem_c = sizeof(T) * (size_t)(cnt > 0 ? cnt : 1);
-    const size_t smem_d = sizeof(T) * (size_t)(cnt > 0 ? cnt : 1) * (GT / 32);
+    const size_t smem_d = sizeof(T) * (size_t)rpb;
     for (int pass = 0; pass < 2 && cnt > 0; pass++) {
-        multi_dot_kernel<T><<<(unsigned)nblk, GT, smem_d, s>>>(Bt, ld, cnt, w, len, rpb, part);
+        if (vec) multi_dot_kernel<T, true><<<(unsigned)nblk, GT, smem_d, s>>>(Bt, ld, cnt, w, len, rpb, part);
+        else multi_dot_kernel<T, false><<<(unsigned)nblk, GT, smem_d, s>>>(Bt, ld, cnt, w, len, rpb, part);
         sum_parts_kernel<T><<<(unsigned)ceil_div(cnt, 8), 256, 0, s>>>(part, nblk, cnt, coef);
-        multi_axpy_kernel<T><<<(unsigned)nblk, GT, smem_c, s>>>(Bt, ld, cnt, coef, w, len, rpb, sq);
+        if (vec) multi_axpy_kernel<T, true><<<(unsigned)nblk, GT, smem_c, s>>>(Bt, ld, cnt, coef, w, len, rpb, sq);
+        else multi_axpy_kernel<T, false><<<(unsigned)nblk, GT, smem_c, s>>>(Bt, ld, cnt, coef, w, len, rpb, sq);
         note_launch(3);
     }
     if (cnt == 0) {  // norm only
-        multi_axpy_kernel<T><<<(unsigned)nblk, GT, smem_c, s>>>(Bt, ld, 0, coef, w, len, rpb, sq);
+        if (vec) multi_axpy_kernel<T, true><<<(unsigned)nblk, GT, smem_c, s>>>(Bt, ld, 0, coef, w, len, rpb, sq);
+        else multi_axpy_kernel<T, false><<<(unsigned)nblk, GT, smem_c, s>>>(Bt, ld, 0, coef, w, len, rpb, sq);
         note_launch();
     }
     norm_kernel<T><<<1, 1024, 0, s>>>(sq, nblk, nrm);

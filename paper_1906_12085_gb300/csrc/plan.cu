@@ -424,7 +424,7 @@ GklBufs gkl_carve(rsvd_plan *P, int steps, char *base, size_t *bytes) {
     b.w = c.take(es * m);
     b.z = c.take(es * n);
     b.part = c.take(es * nblk * (steps + 1));
-    b.gpart = (double *)c.take(sizeof(double) * gkl_gemv_chunks(m) * (n + 1));
+    b.gpart = (double *)c.take(sizeof(double) * gkl_gemv_chunks(m, (int)n) * (n + 1));
     b.coef = c.take(es * (steps + 1));
     b.sq = c.take(es * nblk);
     b.alpha = c.take(es * steps);
