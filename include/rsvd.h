@@ -215,6 +215,87 @@ uint64_t rsvd_launch_count(void);
 /* Static description of a status code. */
 const char *rsvd_status_string(rsvd_status s);
 
+/* ====================================================================
+ * Batching and serving.  The paper has no counterpart: these run many
+ * independent randomized PCA problems (Sec. 3.1.2) at once.  Each problem
+ * executes exactly the kernels and arithmetic of a single rsvd() call, so its
+ * result does not depend on what it was batched or served with.
+ * ==================================================================== */
+
+/* Device workspace bytes a plan of these sizes needs, a multiple of 256 (no
+ * allocation, no GPU work).  Same argument rules and errors as rsvd_plan_create. */
+rsvd_status rsvd_workspace_query(int64_t m, int64_t n, int k, int p, int q, rsvd_dtype dtype, size_t *bytes);
+
+/* rsvd_plan_create on caller-owned device memory: `workspace` (256-byte
+ * aligned, at least rsvd_workspace_query bytes) is carved, not allocated, and
+ * is cleared with an asynchronous memset on `cuda_stream`; the call neither
+ * allocates device memory nor synchronises.  The caller keeps the workspace
+ * alive until rsvd_plan_destroy and frees it afterwards.  RSVD_ERR_ARG for a
+ * NULL, misaligned or short workspace. */
+rsvd_status rsvd_plan_create_in(rsvd_plan_t *plan, int64_t m, int64_t n, int k, int p, int q, rsvd_dtype dtype,
+                                void *cuda_stream, void *workspace, size_t bytes);
+
+/*
+ * Batched small solves: `count` (1..RSVD_BATCH_MAX) problems whose plans share
+ * dtype, l = k + p and q (m, n, k may differ; plans distinct).  A run solves
+ * every problem in lockstep: each problem's products run on its own plan's
+ * stream; each small dense step (Cholesky of the CholeskyQR2 Gram matrices,
+ * Jacobi SVD of R, the float64 refinement) is one launch over all problems on
+ * `cuda_stream`, which waits for the problems' streams and which they wait
+ * for.  On a non-legacy stream the whole run is captured into one CUDA graph
+ * on first use and replayed while the argument pointers and plan flags repeat
+ * (the plans' streams must then be non-legacy too).  rsvd_batch_run takes
+ * arrays of `count` device pointers with the meaning and layout of rsvd()'s
+ * arguments (col_scales NULL); it is asynchronous.  rsvd_batch_sync waits and
+ * returns the first failing status (statuses: `count` host ints or NULL).
+ * Afterwards pca_threshold works on each plan as after rsvd().  The batch
+ * object owns only its tables and events; the plans stay the caller's.
+ */
+#define RSVD_BATCH_MAX 256
+typedef struct rsvd_batch *rsvd_batch_t;
+rsvd_status rsvd_batch_create(rsvd_batch_t *batch, int count, rsvd_plan_t const *plans, void *cuda_stream);
+rsvd_status rsvd_batch_run(rsvd_batch_t batch, void *const *A, const void *const *Omega, double *const *S,
+                           void *const *U, void *const *V);
+rsvd_status rsvd_batch_sync(rsvd_batch_t batch, int *statuses);
+rsvd_status rsvd_batch_destroy(rsvd_batch_t batch);
+
+/*
+ * Serving loop: continuous batching of float32 randomized PCA requests.
+ *   rsvd_server_create: one device arena of `hbm_bytes` (cudaMalloc'd once)
+ *     holds every admitted request's plan workspace; at most `max_inflight`
+ *     batches run at once, each of at most `max_batch` requests, on streams
+ *     of the server's own.
+ *   rsvd_server_submit: queue request `id` (A m x n, Omega n x (k+p), S k
+ *     doubles, U m x k, V n x k: caller-owned device memory that must stay
+ *     valid until the request completes; t is the Sec. 2.4 threshold).
+ *     RSVD_ERR_OOM if its workspace can never fit the arena; argument errors
+ *     as rsvd_plan_create.  Does not block.
+ *   rsvd_server_poll: retire finished batches (frees their arena space),
+ *     admit queued requests in arrival order while the arena and the batch
+ *     slots allow (the oldest waiting request is never overtaken; consecutive
+ *     queued requests of the same l and q share a batch), launch them, and
+ *     write up to `max_out` completions to `out`.  Returns the number written,
+ *     or a negative rsvd_status on a CUDA error.  Does not block.
+ *   rsvd_server_pending: requests queued or running.
+ * Times are host milliseconds since rsvd_server_create: submit (the call),
+ * start (admission and launch), done (the device finished the request's
+ * batch, from CUDA events).  One host thread drives a server.
+ */
+typedef struct rsvd_server *rsvd_server_t;
+typedef struct {
+    int64_t id;
+    int status;  /* rsvd_status of the solve, RSVD_WARN_K_GT_k when t is not reached within k */
+    int K;       /* Sec. 2.4 K */
+    int batch;   /* requests in the batch it ran in */
+    double submit_ms, start_ms, done_ms;
+} rsvd_completion;
+rsvd_status rsvd_server_create(rsvd_server_t *server, size_t hbm_bytes, int max_batch, int max_inflight);
+rsvd_status rsvd_server_submit(rsvd_server_t server, int64_t id, int64_t m, int64_t n, int k, int p, int q,
+                               double t, const float *A, const float *Omega, double *S, float *U, float *V);
+int rsvd_server_poll(rsvd_server_t server, rsvd_completion *out, int max_out);
+int rsvd_server_pending(rsvd_server_t server);
+rsvd_status rsvd_server_destroy(rsvd_server_t server);
+
 #ifdef __cplusplus
 }
 #endif

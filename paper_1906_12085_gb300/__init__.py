@@ -22,7 +22,10 @@ __all__ = [
     "rsvd_plan_create", "rsvd_plan_destroy", "rsvd_plan_workspace_bytes", "rsvd_plan_set_flags",
     "rsvd_plan_sync", "rsvd", "svd_exact", "svd_truncated_krylov", "pca_threshold", "rsvd_plan_fro2",
     "rsvd_status_string", "check", "rsvd_plan_profile", "rsvd_plan_profile_read", "rsvd_launch_count",
-    "STAGES", "svd_exact_gram_static",
+    "STAGES", "svd_exact_gram_static", "RSVD_BATCH_MAX", "Completion", "rsvd_workspace_query",
+    "rsvd_plan_create_in", "Batch", "rsvd_batch_create", "rsvd_batch_run", "rsvd_batch_sync",
+    "rsvd_batch_destroy", "Server", "rsvd_server_create", "rsvd_server_submit", "rsvd_server_poll",
+    "rsvd_server_pending", "rsvd_server_destroy",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -34,8 +37,18 @@ RSVD_OK, RSVD_ERR_ARG, RSVD_ERR_OOM, RSVD_ERR_CHOL, RSVD_ERR_NOCONV = 0, -1, -2,
 RSVD_ERR_TIMEOUT, RSVD_ERR_CUDA, RSVD_ERR_UNSUPPORTED, RSVD_WARN_K_GT_k = -5, -6, -8, 1
 RSVD_EXACT_GRAM, RSVD_EXACT_QR_JACOBI = 0, 1
 RSVD_FLAG_NO_CENTER = 1
+RSVD_BATCH_MAX = 256
 # tracing stages (RSVD_STAGE_* in include/rsvd.h)
 STAGES = ("center", "ax", "atx", "orth", "small", "finish")
+
+
+class Completion(ctypes.Structure):
+    """rsvd_completion of include/rsvd.h."""
+    _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int), ("K", ctypes.c_int), ("batch", ctypes.c_int),
+                ("submit_ms", ctypes.c_double), ("start_ms", ctypes.c_double), ("done_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class RsvdError(RuntimeError):
@@ -80,9 +93,24 @@ def lib() -> ctypes.CDLL:
     L.svd_exact_gram_static.restype = i32
     L.rsvd_status_string.argtypes = [i32]
     L.rsvd_status_string.restype = ctypes.c_char_p
+    sz = ctypes.c_size_t
+    L.rsvd_workspace_query.argtypes = [i64, i64, i32, i32, i32, i32, ctypes.POINTER(sz)]
+    L.rsvd_plan_create_in.argtypes = [ctypes.POINTER(vp), i64, i64, i32, i32, i32, i32, vp, vp, sz]
+    L.rsvd_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp), vp]
+    L.rsvd_batch_run.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                 ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    L.rsvd_batch_sync.argtypes = [vp, ctypes.POINTER(i32)]
+    L.rsvd_batch_destroy.argtypes = [vp]
+    L.rsvd_server_create.argtypes = [ctypes.POINTER(vp), sz, i32, i32]
+    L.rsvd_server_submit.argtypes = [vp, i64, i64, i64, i32, i32, i32, ctypes.c_double, vp, vp, vp, vp, vp]
+    L.rsvd_server_poll.argtypes = [vp, ctypes.POINTER(Completion), i32]
+    L.rsvd_server_pending.argtypes = [vp]
+    L.rsvd_server_destroy.argtypes = [vp]
     for f in ("rsvd_plan_create", "rsvd_plan_destroy", "rsvd_plan_set_flags", "rsvd_plan_sync", "rsvd",
               "svd_exact", "svd_truncated_krylov", "pca_threshold", "rsvd_plan_fro2", "rsvd_plan_profile",
-              "rsvd_plan_profile_read"):
+              "rsvd_plan_profile_read", "rsvd_workspace_query", "rsvd_plan_create_in", "rsvd_batch_create",
+              "rsvd_batch_run", "rsvd_batch_sync", "rsvd_batch_destroy", "rsvd_server_create",
+              "rsvd_server_submit", "rsvd_server_poll", "rsvd_server_pending", "rsvd_server_destroy"):
         getattr(L, f).restype = i32
     _lib = L
     return L
@@ -230,3 +258,136 @@ def svd_exact_gram_static(A, dtype: int, S, U, V, stream=None) -> int:
     Synchronises the stream before returning."""
     m, n = A.shape
     return lib().svd_exact_gram_static(_ptr(A), m, n, int(dtype), _ptr(S), _ptr(U), _ptr(V), _stream(stream))
+
+
+# ------------------------------------------------------------- batching and serving
+def rsvd_workspace_query(m: int, n: int, k: int, p: int, q: int, dtype: int = RSVD_F32) -> tuple[int, int]:
+    """(status, bytes of device workspace a plan of these sizes needs)."""
+    b = ctypes.c_size_t(0)
+    st = lib().rsvd_workspace_query(m, n, k, p, q, dtype, ctypes.byref(b))
+    return st, int(b.value)
+
+
+class _PlanIn(Plan):
+    """A plan on caller-owned workspace; keeps the workspace tensor alive."""
+
+    def __init__(self, handle, m, n, k, p, q, dtype, workspace):
+        super().__init__(handle, m, n, k, p, q, dtype)
+        self.workspace = workspace
+
+
+def rsvd_plan_create_in(m: int, n: int, k: int, p: int, q: int, dtype: int, stream, workspace) -> Plan:
+    """rsvd_plan_create on `workspace` (a device tensor of at least rsvd_workspace_query bytes)."""
+    h = ctypes.c_void_p()
+    nbytes = workspace.numel() * workspace.element_size()
+    st = lib().rsvd_plan_create_in(ctypes.byref(h), m, n, k, p, q, dtype, _stream(stream), _ptr(workspace), nbytes)
+    check(st, "rsvd_plan_create_in")
+    return _PlanIn(h.value, m, n, k, p, q, dtype, workspace)
+
+
+def _ptrs(ts):
+    arr = (ctypes.c_void_p * len(ts))()
+    for i, t in enumerate(ts):
+        arr[i] = _ptr(t)
+    return arr
+
+
+class Batch:
+    """Owning handle of an rsvd_batch_t; keeps its plans alive."""
+
+    def __init__(self, handle, plans):
+        self.handle = handle
+        self.plans = list(plans)
+
+    def close(self):
+        if self.handle:
+            lib().rsvd_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def rsvd_batch_create(plans, stream=None) -> Batch:
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_void_p * len(plans))(*[p.handle for p in plans])
+    check(lib().rsvd_batch_create(ctypes.byref(h), len(plans), arr, _stream(stream)), "rsvd_batch_create")
+    return Batch(h.value, plans)
+
+
+def rsvd_batch_run(batch: Batch, A, Omega, S, U, V) -> int:
+    return lib().rsvd_batch_run(batch.handle, _ptrs(A), _ptrs(Omega), _ptrs(S), _ptrs(U), _ptrs(V))
+
+
+def rsvd_batch_sync(batch: Batch) -> tuple[int, list[int]]:
+    sts = (ctypes.c_int * len(batch.plans))()
+    st = lib().rsvd_batch_sync(batch.handle, sts)
+    return st, list(sts)
+
+
+def rsvd_batch_destroy(batch: Batch) -> int:
+    batch.close()
+    return RSVD_OK
+
+
+class Server:
+    """Owning handle of an rsvd_server_t."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def close(self):
+        if self.handle:
+            lib().rsvd_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def rsvd_server_create(hbm_bytes: int, max_batch: int = 16, max_inflight: int = 8) -> Server:
+    h = ctypes.c_void_p()
+    check(lib().rsvd_server_create(ctypes.byref(h), int(hbm_bytes), max_batch, max_inflight), "rsvd_server_create")
+    return Server(h.value)
+
+
+def rsvd_server_submit(server: Server, rid: int, k: int, p: int, q: int, t: float, A, Omega, S, U, V) -> int:
+    m, n = A.shape
+    return lib().rsvd_server_submit(server.handle, int(rid), m, n, k, p, q, float(t), _ptr(A), _ptr(Omega), _ptr(S),
+                                    _ptr(U), _ptr(V))
+
+
+def rsvd_server_poll(server: Server, max_out: int = 256) -> list[dict]:
+    """Progress the server; the completions it returns (dicts of rsvd_completion fields)."""
+    buf = (Completion * max_out)()
+    w = lib().rsvd_server_poll(server.handle, buf, max_out)
+    if w < 0:
+        raise RsvdError(w, "rsvd_server_poll")
+    return [buf[i].as_dict() for i in range(w)]
+
+
+def rsvd_server_pending(server: Server) -> int:
+    return int(lib().rsvd_server_pending(server.handle))
+
+
+def rsvd_server_destroy(server: Server) -> int:
+    server.close()
+    return RSVD_OK

@@ -96,6 +96,43 @@ cudaError_t jacobi_osvd(const double *R, int l, int lp, double *sig, To *UR, To 
 template <typename To>
 cudaError_t sv_refine(const double *R, int l, int lp, const To *UR, const To *W, double *sig, cudaStream_t s);
 
+// Serving interface of plan.cu (used by server.cu): a batch context on stream bs
+// for up to `cap` problems, and one launch of a float32 batch followed, per
+// problem, by the Sec. 2.4 K selection and an asynchronous copy of three ints
+// (status bits, K, reached) to host_out + 3 i (pinned memory).
+struct ServeBatch;
+ServeBatch *serve_batch_new(cudaStream_t bs, int cap);
+void serve_batch_free(ServeBatch *b);
+rsvd_status serve_batch_launch(ServeBatch *b, int count, rsvd_plan_t const *plans, const float *const *A,
+                               const float *const *Om, double *const *S, float *const *U, float *const *V,
+                               const double *t, int *host_out);
+rsvd_status serve_status(int bits, int reached);
+
+// Batched forms: one launch solves `count` independent problems of the same l, lp;
+// problem b takes its pointers from the device table entry b (one CTA per problem,
+// sv_refine one CTA per (value, problem)).  Same arithmetic as the single forms,
+// so a problem's result does not depend on the batch it is solved in.
+struct CholTab {
+    const void *G;     // TG, l x l (ldg)
+    double *R, *Rinv;  // l x l
+    void *Rc;          // Tc, lp x lp
+    int *status;
+    double coef;       // chol_shift_coef(rows, l, u)
+};
+struct JacTab {
+    const double *R;   // l x l
+    double *sig;       // l
+    void *UR, *W;      // To, lp x lp
+    int *status;
+};
+double chol_shift_coef(int64_t rows, int l, double unit_roundoff);
+template <typename TG, typename Tk, typename Tc>
+cudaError_t chol_inv_batched(const CholTab *tab, int count, int64_t ldg, int l, int lp, cudaStream_t s);
+template <typename Ta, typename To>
+cudaError_t jacobi_osvd_batched(const JacTab *tab, int count, int l, int lp, cudaStream_t s);
+template <typename To>
+cudaError_t sv_refine_batched(const JacTab *tab, int count, int l, int lp, cudaStream_t s);
+
 // Cyclic (parallel-ordered) two-sided Jacobi eigen-decomposition of the n x n
 // symmetric float64 matrix G (ld n): lam descending (n doubles), V (n x n, ld n).
 cudaError_t jacobi_eig(const double *G, int n, double *lam, double *V, int *status, cudaStream_t s);

@@ -67,10 +67,9 @@ template <> struct Eps<double> { static constexpr double v = DBL_EPSILON; };
 //     X[k][:] /= R[k][k],  X[i][:] -= R[i][k] X[k][:]  (i < k).
 // Arithmetic in Tk; l <= 16 * LB.
 template <typename TG, typename Tk, typename Tc, int LB>
-__global__ void __launch_bounds__(256) chol_inv_kernel(const TG *__restrict__ G, int64_t ldg, int l,
-                                                       double shift_coef, double *__restrict__ R,
-                                                       double *__restrict__ Rinv, Tc *__restrict__ Rinv_c, int lp,
-                                                       int *__restrict__ status) {
+__device__ __forceinline__ void chol_inv_body(const TG *__restrict__ G, int64_t ldg, int l, double shift_coef,
+                                              double *__restrict__ R, double *__restrict__ Rinv,
+                                              Tc *__restrict__ Rinv_c, int lp, int *__restrict__ status) {
     extern __shared__ __align__(16) unsigned char smraw[];
     Tk *Rs = reinterpret_cast<Tk *>(smraw);  // l x l factor R
     Tk *rowbuf = Rs + l * l;                 // 2 x 16 LB broadcast rows
@@ -207,6 +206,23 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(const TG *__restrict__ G,
         }
 }
 
+template <typename TG, typename Tk, typename Tc, int LB>
+__global__ void __launch_bounds__(256) chol_inv_kernel(const TG *__restrict__ G, int64_t ldg, int l,
+                                                       double shift_coef, double *__restrict__ R,
+                                                       double *__restrict__ Rinv, Tc *__restrict__ Rinv_c, int lp,
+                                                       int *__restrict__ status) {
+    chol_inv_body<TG, Tk, Tc, LB>(G, ldg, l, shift_coef, R, Rinv, Rinv_c, lp, status);
+}
+
+// One CTA per problem of a batch; problem b's pointers and shift are tab[b].
+template <typename TG, typename Tk, typename Tc, int LB>
+__global__ void __launch_bounds__(256) chol_inv_batch_kernel(const CholTab *__restrict__ tab, int64_t ldg, int l,
+                                                             int lp) {
+    const CholTab t = tab[blockIdx.x];
+    chol_inv_body<TG, Tk, Tc, LB>(static_cast<const TG *>(t.G), ldg, l, t.coef, t.R, t.Rinv,
+                                  static_cast<Tc *>(t.Rc), lp, t.status);
+}
+
 __global__ void trmm_upper_kernel(const double *__restrict__ R2, const double *__restrict__ R1, double *__restrict__ R,
                                   int l) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -219,10 +235,9 @@ __global__ void trmm_upper_kernel(const double *__restrict__ R2, const double *_
 
 // ------------------------------------------------------------ one-sided Jacobi
 template <typename Ta, typename To>
-__global__ void __launch_bounds__(1024) jacobi_osvd_kernel(const double *__restrict__ R, int l, int lp,
-                                                           double *__restrict__ sig, To *__restrict__ UR,
-                                                           To *__restrict__ W, int *__restrict__ status,
-                                                           int max_sweeps, int gsize) {
+__device__ __forceinline__ void jacobi_osvd_body(const double *__restrict__ R, int l, int lp, double *__restrict__ sig,
+                                                 To *__restrict__ UR, To *__restrict__ W, int *__restrict__ status,
+                                                 int max_sweeps, int gsize) {
     // gsize lanes (16 or 32) rotate one column pair; a warp holds 32 / gsize pairs
     extern __shared__ __align__(16) unsigned char smraw[];
     const int L = l + (l & 1);
@@ -340,14 +355,29 @@ __global__ void __launch_bounds__(1024) jacobi_osvd_kernel(const double *__restr
     }
 }
 
+template <typename Ta, typename To>
+__global__ void __launch_bounds__(1024) jacobi_osvd_kernel(const double *__restrict__ R, int l, int lp,
+                                                           double *__restrict__ sig, To *__restrict__ UR,
+                                                           To *__restrict__ W, int *__restrict__ status,
+                                                           int max_sweeps, int gsize) {
+    jacobi_osvd_body<Ta, To>(R, l, lp, sig, UR, W, status, max_sweeps, gsize);
+}
+
+template <typename Ta, typename To>
+__global__ void __launch_bounds__(1024) jacobi_osvd_batch_kernel(const JacTab *__restrict__ tab, int l, int lp,
+                                                                 int max_sweeps, int gsize) {
+    const JacTab t = tab[blockIdx.x];
+    jacobi_osvd_body<Ta, To>(t.R, l, lp, t.sig, static_cast<To *>(t.UR), static_cast<To *>(t.W), t.status,
+                             max_sweeps, gsize);
+}
+
 // sig[i] = x_i^T R w_i / (||x_i|| ||w_i||) in float64 for the columns x_i of UR and
 // w_i of W (ld lp): the Rayleigh quotient of the Jacobi singular vectors, whose
 // error is quadratic in the vectors' error.  One block per singular value.
 template <typename To>
-__global__ void sv_refine_kernel(const double *__restrict__ R, int l, int lp, const To *__restrict__ UR,
-                                 const To *__restrict__ W, double *__restrict__ sig) {
+__device__ __forceinline__ void sv_refine_body(const double *__restrict__ R, int l, int lp, const To *__restrict__ UR,
+                                               const To *__restrict__ W, double *__restrict__ sig, int i) {
     __shared__ double red[3][32];
-    const int i = blockIdx.x;
     double acc = 0.0, nx = 0.0, nw = 0.0;
     for (int r = threadIdx.x; r < l; r += blockDim.x) {
         double rw = 0.0;
@@ -369,6 +399,19 @@ __global__ void sv_refine_kernel(const double *__restrict__ R, int l, int lp, co
         for (int k = 0; k < (int)(blockDim.x >> 5); k++) { a += red[0][k]; x += red[1][k]; w += red[2][k]; }
         if (x > 0.0 && w > 0.0) sig[i] = fabs(a) / sqrt(x * w);
     }
+}
+
+template <typename To>
+__global__ void sv_refine_kernel(const double *__restrict__ R, int l, int lp, const To *__restrict__ UR,
+                                 const To *__restrict__ W, double *__restrict__ sig) {
+    sv_refine_body<To>(R, l, lp, UR, W, sig, blockIdx.x);
+}
+
+// blockIdx.x: singular value, blockIdx.y: problem of the batch
+template <typename To>
+__global__ void sv_refine_batch_kernel(const JacTab *__restrict__ tab, int l, int lp) {
+    const JacTab t = tab[blockIdx.y];
+    sv_refine_body<To>(t.R, l, lp, static_cast<const To *>(t.UR), static_cast<const To *>(t.W), t.sig, blockIdx.x);
 }
 
 // ------------------------------------------------------------ two-sided Jacobi
@@ -563,7 +606,7 @@ __global__ void pca_select_kernel(const double *__restrict__ sigma, int count, c
 template <typename TG, typename Tk, typename Tc>
 cudaError_t chol_inv(const TG *G, int64_t ldg, int l, int64_t rows, double u, double *R, double *Rinv, Tc *Rinv_c,
                      int lp, int *status, cudaStream_t s) {
-    const double coef = 11.0 * ((double)rows * l + (double)l * (l + 1)) * u;
+    const double coef = chol_shift_coef(rows, l, u);
     if (l <= 64) {
         const size_t smem = sizeof(Tk) * ((size_t)l * l + 2 * 64);
         chol_inv_kernel<TG, Tk, Tc, 4><<<1, 256, smem, s>>>(G, ldg, l, coef, R, Rinv, Rinv_c, lp, status);
@@ -575,6 +618,24 @@ cudaError_t chol_inv(const TG *G, int64_t ldg, int l, int64_t rows, double u, do
     note_launch();
     return cudaGetLastError();
 }
+
+template <typename TG, typename Tk, typename Tc>
+cudaError_t chol_inv_batched(const CholTab *tab, int count, int64_t ldg, int l, int lp, cudaStream_t s) {
+    if (count < 1) return cudaSuccess;
+    if (l <= 64) {
+        const size_t smem = sizeof(Tk) * ((size_t)l * l + 2 * 64);
+        chol_inv_batch_kernel<TG, Tk, Tc, 4><<<count, 256, smem, s>>>(tab, ldg, l, lp);
+    } else {
+        const size_t smem = sizeof(Tk) * ((size_t)l * l + 2 * 128);
+        cudaFuncSetAttribute(chol_inv_batch_kernel<TG, Tk, Tc, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        chol_inv_batch_kernel<TG, Tk, Tc, 8><<<count, 256, smem, s>>>(tab, ldg, l, lp);
+    }
+    note_launch();
+    return cudaGetLastError();
+}
+
+double chol_shift_coef(int64_t rows, int l, double u) { return 11.0 * ((double)rows * l + (double)l * (l + 1)) * u; }
 
 cudaError_t trmm_upper(const double *R2, const double *R1, double *R, int l, cudaStream_t s) {
     trmm_upper_kernel<<<(l * l + 255) / 256, 256, 0, s>>>(R2, R1, R, l);
@@ -597,6 +658,29 @@ cudaError_t jacobi_osvd(const double *R, int l, int lp, double *sig, To *UR, To 
     return cudaGetLastError();
 }
 
+template <typename Ta, typename To>
+cudaError_t jacobi_osvd_batched(const JacTab *tab, int count, int l, int lp, cudaStream_t s) {
+    if (count < 1) return cudaSuccess;
+    const int L = l + (l & 1);
+    const size_t smem = sizeof(Ta) * (2 * (size_t)L * L + 1) + sizeof(double) * L + sizeof(int) * L +
+                        sizeof(double) * L + 16;
+    cudaFuncSetAttribute(jacobi_osvd_batch_kernel<Ta, To>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int gsize = l <= 64 ? 16 : 32;
+    int threads = (L / 2) * gsize;
+    threads = threads < 64 ? 64 : threads > 1024 ? 1024 : (threads + 31) / 32 * 32;
+    jacobi_osvd_batch_kernel<Ta, To><<<count, threads, smem, s>>>(tab, l, lp, 40, gsize);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <typename To>
+cudaError_t sv_refine_batched(const JacTab *tab, int count, int l, int lp, cudaStream_t s) {
+    if (count < 1) return cudaSuccess;
+    sv_refine_batch_kernel<To><<<dim3(l, count), 128, 0, s>>>(tab, l, lp);
+    note_launch();
+    return cudaGetLastError();
+}
+
 template <typename To>
 cudaError_t sv_refine(const double *R, int l, int lp, const To *UR, const To *W, double *sig, cudaStream_t s) {
     sv_refine_kernel<To><<<l, 128, 0, s>>>(R, l, lp, UR, W, sig);
@@ -604,6 +688,12 @@ cudaError_t sv_refine(const double *R, int l, int lp, const To *UR, const To *W,
     return cudaGetLastError();
 }
 template cudaError_t sv_refine<float>(const double *, int, int, const float *, const float *, double *, cudaStream_t);
+template cudaError_t sv_refine_batched<float>(const JacTab *, int, int, int, cudaStream_t);
+template cudaError_t sv_refine_batched<double>(const JacTab *, int, int, int, cudaStream_t);
+template cudaError_t jacobi_osvd_batched<float, float>(const JacTab *, int, int, int, cudaStream_t);
+template cudaError_t jacobi_osvd_batched<double, double>(const JacTab *, int, int, int, cudaStream_t);
+template cudaError_t chol_inv_batched<float, float, float>(const CholTab *, int, int64_t, int, int, cudaStream_t);
+template cudaError_t chol_inv_batched<double, double, double>(const CholTab *, int, int64_t, int, int, cudaStream_t);
 template cudaError_t sv_refine<double>(const double *, int, int, const double *, const double *, double *,
                                        cudaStream_t);
 

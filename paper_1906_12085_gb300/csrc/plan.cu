@@ -30,6 +30,7 @@ struct rsvd_plan {
     unsigned flags = 0;
     void *ws = nullptr;
     size_t ws_bytes = 0;
+    bool ws_owned = true;     // false: the workspace belongs to the caller (rsvd_plan_create_in)
     // carved workspace
     double *mu = nullptr, *fro2 = nullptr, *cpart = nullptr;
     void *mu_t = nullptr;        // column means in the element type, zero padded to npad
@@ -523,20 +524,209 @@ void drop_graph(rsvd_plan *P) {
     P->graph = nullptr;
 }
 
-}  // namespace
+// ------------------------------------------------------------------ batching
+// Several independent randomized PCA problems of the same l, lp, q and dtype
+// solved in lockstep: each problem's products run on its own plan's stream, and
+// at every small dense step (Cholesky of a Gram matrix, Jacobi SVD of R, the
+// float64 refinement) the streams join on the batch stream, one batched launch
+// solves that step for every problem, and the streams fork again.  Every
+// problem runs exactly the kernels (and arithmetic) of a single solve.
+struct BatchCtx {
+    cudaStream_t bs = nullptr;
+    std::vector<cudaEvent_t> ev;  // cap join events + 1 fork event
+    cudaEvent_t up = nullptr;     // the last direct-mode table upload (the host table is reused)
+    bool up_pending = false;
+    void *dtab = nullptr, *htab = nullptr;
+    size_t tab_bytes = 0;
+    int cap = 0;
+    ~BatchCtx() {
+        if (up) cudaEventDestroy(up);
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        if (dtab) cudaFree(dtab);
+        if (htab) cudaFreeHost(htab);
+    }
+    // tables: 4 CholTab blocks (rows m / n x pass 1 / 2) and one JacTab block, `count` entries each
+    static size_t bytes_for(int count) { return (4 * sizeof(CholTab) + sizeof(JacTab)) * (size_t)count; }
+    cudaError_t reserve(int count) {
+        if (count <= cap) return cudaSuccess;
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        ev.clear();
+        if (dtab) cudaFree(dtab);
+        if (htab) cudaFreeHost(htab);
+        dtab = htab = nullptr;
+        cap = 0;
+        if (!up && cudaEventCreateWithFlags(&up, cudaEventDisableTiming) != cudaSuccess) return cudaErrorMemoryAllocation;
+        ev.resize(count + 1);
+        for (auto &e : ev)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return cudaErrorMemoryAllocation;
+        tab_bytes = bytes_for(count);
+        if (cudaMalloc(&dtab, tab_bytes) != cudaSuccess) return cudaErrorMemoryAllocation;
+        if (cudaMallocHost(&htab, tab_bytes) != cudaSuccess) return cudaErrorMemoryAllocation;
+        cap = count;
+        return cudaSuccess;
+    }
+    CholTab *chol(int variant, int count, bool dev) {
+        return reinterpret_cast<CholTab *>((char *)(dev ? dtab : htab)) + (size_t)variant * count;
+    }
+    JacTab *jac(int count, bool dev) {
+        return reinterpret_cast<JacTab *>((char *)(dev ? dtab : htab) + 4 * sizeof(CholTab) * (size_t)count);
+    }
+};
 
-extern "C" {
+cudaError_t join(BatchCtx &C, int count, rsvd_plan *const *Ps) {
+    for (int i = 0; i < count; i++) {
+        if (Ps[i]->stream == C.bs) continue;
+        if (cudaEventRecord(C.ev[i], Ps[i]->stream) != cudaSuccess) return cudaErrorUnknown;
+        if (cudaStreamWaitEvent(C.bs, C.ev[i], 0) != cudaSuccess) return cudaErrorUnknown;
+    }
+    return cudaSuccess;
+}
 
-rsvd_status rsvd_plan_create(rsvd_plan_t *plan, int64_t m, int64_t n, int k, int p, int q, rsvd_dtype dtype,
-                             void *cuda_stream) {
-    if (!plan) return RSVD_ERR_ARG;
-    *plan = nullptr;
+cudaError_t fork(BatchCtx &C, int count, rsvd_plan *const *Ps) {
+    if (cudaEventRecord(C.ev[count], C.bs) != cudaSuccess) return cudaErrorUnknown;
+    for (int i = 0; i < count; i++)
+        if (Ps[i]->stream != C.bs && cudaStreamWaitEvent(Ps[i]->stream, C.ev[count], 0) != cudaSuccess)
+            return cudaErrorUnknown;
+    return cudaSuccess;
+}
+
+enum { BQ_Y = 0, BQ_Z = 1, BQ_T = 2 };  // which l-wide block a batched CholeskyQR works on
+
+// Batched form of cqr(): the same products per problem, one batched Cholesky per pass.
+template <typename T>
+rsvd_status bcqr(BatchCtx &C, int count, rsvd_plan *const *Ps, int which, int passes, bool want_r) {
+    const int lp = Ps[0]->lp, l = Ps[0]->l;
+    auto bufs = [&](rsvd_plan *P, T *&X, T *&Qo, T *&Tmp, int64_t &rows) {
+        if (which == BQ_Y) { X = (T *)P->Y; Qo = (T *)P->Qb; Tmp = (T *)P->Tmp; rows = P->m; }
+        else { X = which == BQ_Z ? (T *)P->Z : (T *)P->Tn; Qo = (T *)P->Qz; Tmp = (T *)P->Tmpn; rows = P->n; }
+    };
+    const int rv = which == BQ_Y ? 0 : 2;  // table block: rows m (0, 1) or rows n (2, 3)
+    for (int pass = 0; pass < passes; pass++) {
+        for (int i = 0; i < count; i++) {
+            rsvd_plan *P = Ps[i];
+            T *X, *Qo, *Tmp;
+            int64_t rows;
+            bufs(P, X, Qo, Tmp, rows);
+            const T *src = pass == 0 ? X : Tmp;
+            CK(prod_tn<T>(P, rows, lp, src, lp, src, lp, (T *)P->G, lp));
+        }
+        CK(join(C, count, Ps));
+        CK(chol_inv_batched<T, T, T>(C.chol(rv + pass, count, true), count, lp, l, lp, C.bs));
+        CK(fork(C, count, Ps));
+        for (int i = 0; i < count; i++) {
+            rsvd_plan *P = Ps[i];
+            T *X, *Qo, *Tmp;
+            int64_t rows;
+            bufs(P, X, Qo, Tmp, rows);
+            const T *src = pass == 0 ? X : Tmp;
+            T *dst = (pass == passes - 1) ? Qo : Tmp;
+            CK(prod_nn<T>(P, rows, lp, src, lp, (const T *)P->Rinv_c, lp, dst, lp));
+            if (pass == 1 && want_r) CK(trmm_upper(P->R2, P->R1, P->Rt, l, P->stream));
+        }
+    }
+    return RSVD_OK;
+}
+
+// The steps of run_rsvd for `count` problems (see there for the step list).
+template <typename T>
+rsvd_status run_rsvd_batch(BatchCtx &C, int count, rsvd_plan *const *Ps, T *const *A, const T *const *Om,
+                           double *const *S, T *const *U, T *const *V, bool capturing) {
+    const int l = Ps[0]->l, lp = Ps[0]->lp, q = Ps[0]->q;
+    const double u = unit_roundoff<T>();
+    CK(C.reserve(count));
+    if (C.up_pending) {  // the previous upload must have read the host table before it is rewritten
+        CK(cudaEventSynchronize(C.up));
+        C.up_pending = false;
+    }
+    for (int i = 0; i < count; i++) {
+        rsvd_plan *P = Ps[i];
+        for (int pass = 0; pass < 2; pass++) {
+            double *R = pass ? P->R2 : P->R1, *Ri = pass ? P->R2i : P->R1i;
+            C.chol(pass, count, false)[i] = {P->G, R, Ri, P->Rinv_c, P->status, chol_shift_coef(P->m, l, u)};
+            C.chol(2 + pass, count, false)[i] = {P->G, R, Ri, P->Rinv_c, P->status, chol_shift_coef(P->n, l, u)};
+        }
+        C.jac(count, false)[i] = {P->Rt, P->sig, P->UR, P->Wm, P->status};
+    }
+    CK(cudaMemcpyAsync(C.dtab, C.htab, BatchCtx::bytes_for(count), cudaMemcpyHostToDevice, C.bs));
+    if (!capturing) {
+        CK(cudaEventRecord(C.up, C.bs));
+        C.up_pending = true;
+    }
+    CK(fork(C, count, Ps));
+    for (int i = 0; i < count; i++) {  // means, padded Omega, sketch H(0) = A G with ||A||_F^2
+        rsvd_plan *P = Ps[i];
+        const bool centred = !(P->flags & RSVD_FLAG_NO_CENTER);
+        if (centred) CK(column_means<T>(A[i], P->m, P->n, P->n, P->mu, (T *)P->mu_t, P->npad, P->cpart, P->stream));
+        else CK(cudaMemsetAsync(P->mu, 0, sizeof(double) * P->n, P->stream));
+        CK(copy2d<T, T>(Om[i], l, (T *)P->Ob, lp, P->n, l, lp, P->stream));
+        CK(prod_nn<T>(P, P->m, P->n, A[i], P->n, (T *)P->Ob, lp, (T *)P->Y, lp,
+                      centred ? (const T *)P->mu_t : nullptr, P->fro2));
+    }
+    rsvd_status st;
+    if ((st = bcqr<T>(C, count, Ps, BQ_Y, q > 0 ? 1 : 2, false))) return st;
+    for (int it = 0; it < q; it++) {
+        const bool last = it == q - 1;
+        for (int i = 0; i < count; i++) {
+            rsvd_plan *P = Ps[i];
+            const T *mu = (P->flags & RSVD_FLAG_NO_CENTER) ? nullptr : (const T *)P->mu_t;
+            CK(prod_tn<T>(P, P->m, P->n, A[i], P->n, (T *)P->Qb, lp, (T *)P->Z, lp, mu));
+        }
+        if ((st = bcqr<T>(C, count, Ps, BQ_Z, 1, false))) return st;
+        for (int i = 0; i < count; i++) {
+            rsvd_plan *P = Ps[i];
+            const T *mu = (P->flags & RSVD_FLAG_NO_CENTER) ? nullptr : (const T *)P->mu_t;
+            CK(prod_nn<T>(P, P->m, P->n, A[i], P->n, (T *)P->Qz, lp, (T *)P->Y, lp, mu));
+        }
+        if ((st = bcqr<T>(C, count, Ps, BQ_Y, last ? 2 : 1, false))) return st;
+    }
+    for (int i = 0; i < count; i++) {  // T = A^T Q
+        rsvd_plan *P = Ps[i];
+        const T *mu = (P->flags & RSVD_FLAG_NO_CENTER) ? nullptr : (const T *)P->mu_t;
+        CK(prod_tn<T>(P, P->m, P->n, A[i], P->n, (T *)P->Qb, lp, (T *)P->Tn, lp, mu));
+    }
+    if ((st = bcqr<T>(C, count, Ps, BQ_T, 2, true))) return st;  // T = Q_T R
+    CK(join(C, count, Ps));
+    CK(jacobi_osvd_batched<T, T>(C.jac(count, true), count, l, lp, C.bs));
+    CK(sv_refine_batched<T>(C.jac(count, true), count, l, lp, C.bs));
+    CK(fork(C, count, Ps));
+    for (int i = 0; i < count; i++) {
+        rsvd_plan *P = Ps[i];
+        const int k = P->k;
+        cudaStream_t s = P->stream;
+        CK(gemm_nn<T>(P->n, lp, lp, (T *)P->Qz, lp, (T *)P->UR, lp, (T *)P->Vt, lp, s));
+        CK(sign_normalize<T>((T *)P->Vt, P->n, l, lp, (T *)P->Wm, l, lp, s));
+        CK(gemm_nn<T>(P->m, k, lp, (T *)P->Qb, lp, (T *)P->Wm, lp, U[i], k, s));
+        CK(copy2d<T, T>((T *)P->Vt, lp, V[i], k, P->n, k, k, s));
+        CK(copy_f64(P->sig, S[i], k, s));
+        P->last_count = k;
+    }
+    CK(join(C, count, Ps));
+    return RSVD_OK;
+}
+
+rsvd_status batch_direct(BatchCtx &C, int count, rsvd_plan *const *Ps, void *const *A, const void *const *Om,
+                         double *const *S, void *const *U, void *const *V, bool capturing = false) {
+    if (Ps[0]->dtype == RSVD_F32)
+        return run_rsvd_batch<float>(C, count, Ps, (float *const *)A, (const float *const *)Om, S,
+                                     (float *const *)U, (float *const *)V, capturing);
+    return run_rsvd_batch<double>(C, count, Ps, (double *const *)A, (const double *const *)Om, S,
+                                  (double *const *)U, (double *const *)V, capturing);
+}
+
+// Maps the device status bits of a solve onto the ABI status.
+rsvd_status status_from_bits(int st) {
+    if (st & ST_CHOL) return RSVD_ERR_CHOL;
+    if (st & ST_NOCONV) return RSVD_ERR_NOCONV;
+    if (st & ST_TIMEOUT) return RSVD_ERR_TIMEOUT;
+    return RSVD_OK;
+}
+
+// Validates the sizes and fills the plan's shape fields and workspace size.
+rsvd_status plan_init(rsvd_plan *P, int64_t m, int64_t n, int k, int p, int q, rsvd_dtype dtype, void *cuda_stream) {
     if (m < 1 || n < 1 || m < n || k < 1 || p < 0 || q < 0) return RSVD_ERR_ARG;
     if ((int64_t)k + p > n) return RSVD_ERR_ARG;
     if (dtype != RSVD_F32 && dtype != RSVD_F64) return RSVD_ERR_UNSUPPORTED;
     if (k + p > kSmallMaxF64) return RSVD_ERR_UNSUPPORTED;
-    rsvd_plan *P = new (std::nothrow) rsvd_plan();
-    if (!P) return RSVD_ERR_OOM;
     P->m = m;
     P->n = n;
     P->k = k;
@@ -552,6 +742,102 @@ rsvd_status rsvd_plan_create(rsvd_plan_t *plan, int64_t m, int64_t n, int k, int
     Carver c;
     carve(P, c);
     P->ws_bytes = c.off;
+    return RSVD_OK;
+}
+
+}  // namespace
+
+namespace gbr {
+
+struct ServeBatch {
+    BatchCtx ctx;
+};
+
+ServeBatch *serve_batch_new(cudaStream_t bs, int cap) {
+    ServeBatch *b = new (std::nothrow) ServeBatch();
+    if (!b) return nullptr;
+    b->ctx.bs = bs;
+    if (b->ctx.reserve(cap) != cudaSuccess) {
+        delete b;
+        return nullptr;
+    }
+    return b;
+}
+
+void serve_batch_free(ServeBatch *b) { delete b; }
+
+rsvd_status serve_batch_launch(ServeBatch *b, int count, rsvd_plan *const *plans, const float *const *A,
+                               const float *const *Om, double *const *S, float *const *U, float *const *V,
+                               const double *t, int *host_out) {
+    const rsvd_status st = batch_direct(b->ctx, count, plans, (void *const *)A, (const void *const *)Om, S,
+                                        (void *const *)U, (void *const *)V);
+    if (st != RSVD_OK) return st;
+    cudaStream_t bs = b->ctx.bs;
+    for (int i = 0; i < count; i++) {  // K selection and the three result words per problem
+        rsvd_plan *P = plans[i];
+        CK(pca_select(P->sig, P->k, P->fro2, t[i], P->Kdev, P->Kdev + 1, bs));
+        CK(cudaMemcpyAsync(host_out + 3 * i, P->status, sizeof(int), cudaMemcpyDeviceToHost, bs));
+        CK(cudaMemcpyAsync(host_out + 3 * i + 1, P->Kdev, 2 * sizeof(int), cudaMemcpyDeviceToHost, bs));
+    }
+    return RSVD_OK;
+}
+
+rsvd_status serve_status(int bits, int reached) {
+    const rsvd_status st = status_from_bits(bits);
+    return st == RSVD_OK && !reached ? RSVD_WARN_K_GT_k : st;
+}
+
+}  // namespace gbr
+
+extern "C" {
+
+rsvd_status rsvd_workspace_query(int64_t m, int64_t n, int k, int p, int q, rsvd_dtype dtype, size_t *bytes) {
+    if (!bytes) return RSVD_ERR_ARG;
+    *bytes = 0;
+    rsvd_plan P;
+    const rsvd_status st = plan_init(&P, m, n, k, p, q, dtype, nullptr);
+    if (st != RSVD_OK) return st;
+    *bytes = (size_t)round_up((int64_t)P.ws_bytes, 256);
+    return RSVD_OK;
+}
+
+rsvd_status rsvd_plan_create_in(rsvd_plan_t *plan, int64_t m, int64_t n, int k, int p, int q, rsvd_dtype dtype,
+                                void *cuda_stream, void *workspace, size_t bytes) {
+    if (!plan) return RSVD_ERR_ARG;
+    *plan = nullptr;
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) return RSVD_ERR_ARG;
+    rsvd_plan *P = new (std::nothrow) rsvd_plan();
+    if (!P) return RSVD_ERR_OOM;
+    rsvd_status st = plan_init(P, m, n, k, p, q, dtype, cuda_stream);
+    if (st == RSVD_OK && bytes < P->ws_bytes) st = RSVD_ERR_ARG;
+    if (st != RSVD_OK) {
+        delete P;
+        return st;
+    }
+    P->ws = workspace;
+    P->ws_owned = false;
+    Carver c2;
+    c2.base = (char *)P->ws;
+    carve(P, c2);
+    if (cudaMemsetAsync(P->ws, 0, P->ws_bytes, P->stream) != cudaSuccess) {
+        delete P;
+        return RSVD_ERR_CUDA;
+    }
+    *plan = P;
+    return RSVD_OK;
+}
+
+rsvd_status rsvd_plan_create(rsvd_plan_t *plan, int64_t m, int64_t n, int k, int p, int q, rsvd_dtype dtype,
+                             void *cuda_stream) {
+    if (!plan) return RSVD_ERR_ARG;
+    *plan = nullptr;
+    rsvd_plan *P = new (std::nothrow) rsvd_plan();
+    if (!P) return RSVD_ERR_OOM;
+    const rsvd_status st = plan_init(P, m, n, k, p, q, dtype, cuda_stream);
+    if (st != RSVD_OK) {
+        delete P;
+        return st;
+    }
     if (cudaMalloc(&P->ws, P->ws_bytes) != cudaSuccess) {
         cudaGetLastError();
         delete P;
@@ -576,7 +862,7 @@ rsvd_status rsvd_plan_destroy(rsvd_plan_t P) {
     for (cudaEvent_t e : P->ev) cudaEventDestroy(e);
     drop_graph(P);
     if (P->gkl_ws) cudaFree(P->gkl_ws);
-    cudaFree(P->ws);
+    if (P->ws_owned) cudaFree(P->ws);
     delete P;
     return RSVD_OK;
 }
@@ -596,10 +882,7 @@ rsvd_status rsvd_plan_sync(rsvd_plan_t P) {
         return RSVD_ERR_CUDA;
     if (cudaStreamSynchronize(P->stream) != cudaSuccess) return RSVD_ERR_CUDA;
     if (cudaMemsetAsync(P->status, 0, sizeof(int), P->stream) != cudaSuccess) return RSVD_ERR_CUDA;
-    if (st & ST_CHOL) return RSVD_ERR_CHOL;
-    if (st & ST_NOCONV) return RSVD_ERR_NOCONV;
-    if (st & ST_TIMEOUT) return RSVD_ERR_TIMEOUT;
-    return RSVD_OK;
+    return status_from_bits(st);
 }
 
 rsvd_status rsvd(rsvd_plan_t P, void *A, const float *col_scales, const void *Omega, double *S, void *U, void *V) {
@@ -642,6 +925,119 @@ rsvd_status rsvd(rsvd_plan_t P, void *A, const float *col_scales, const void *Om
     if (cudaGraphLaunch(P->graph, P->stream) != cudaSuccess) return RSVD_ERR_CUDA;
     note_launch((int)P->glaunches);
     P->last_count = P->k;
+    return RSVD_OK;
+}
+
+}  // extern "C"
+
+struct rsvd_batch {
+    std::vector<rsvd_plan *> plans;
+    cudaStream_t stream = nullptr;
+    BatchCtx ctx;
+    cudaGraphExec_t graph = nullptr;
+    std::vector<const void *> key;
+    std::vector<unsigned> kflags;
+    uint64_t glaunches = 0;
+};
+
+extern "C" {
+
+rsvd_status rsvd_batch_create(rsvd_batch_t *batch, int count, rsvd_plan_t const *plans, void *cuda_stream) {
+    if (!batch) return RSVD_ERR_ARG;
+    *batch = nullptr;
+    if (count < 1 || count > RSVD_BATCH_MAX || !plans) return RSVD_ERR_ARG;
+    for (int i = 0; i < count; i++) {
+        const rsvd_plan *P = plans[i];
+        if (!P) return RSVD_ERR_ARG;
+        if (P->dtype != plans[0]->dtype || P->l != plans[0]->l || P->q != plans[0]->q) return RSVD_ERR_ARG;
+        for (int j = 0; j < i; j++)
+            if (plans[j] == P) return RSVD_ERR_ARG;
+    }
+    rsvd_batch *B = new (std::nothrow) rsvd_batch();
+    if (!B) return RSVD_ERR_OOM;
+    B->plans.assign(plans, plans + count);
+    B->stream = (cudaStream_t)cuda_stream;
+    B->ctx.bs = B->stream;
+    if (B->ctx.reserve(count) != cudaSuccess) {
+        delete B;
+        return RSVD_ERR_OOM;
+    }
+    *batch = B;
+    return RSVD_OK;
+}
+
+rsvd_status rsvd_batch_run(rsvd_batch_t B, void *const *A, const void *const *Omega, double *const *S,
+                           void *const *U, void *const *V) {
+    if (!B || !A || !Omega || !S || !U || !V) return RSVD_ERR_ARG;
+    const int count = (int)B->plans.size();
+    bool direct = B->stream == nullptr;
+    std::vector<const void *> key;
+    std::vector<unsigned> kflags;
+    for (int i = 0; i < count; i++) {
+        if (!A[i] || !Omega[i] || !S[i] || !U[i] || !V[i]) return RSVD_ERR_ARG;
+        rsvd_plan *P = B->plans[i];
+        if (P->stream == nullptr || P->prof) direct = true;
+        key.insert(key.end(), {A[i], Omega[i], S[i], U[i], V[i]});
+        kflags.push_back(P->flags);
+    }
+    rsvd_plan *const *Ps = B->plans.data();
+    if (direct) {
+        if (B->graph) cudaGraphExecDestroy(B->graph);
+        B->graph = nullptr;
+        return batch_direct(B->ctx, count, Ps, A, Omega, S, U, V);
+    }
+    if (!(B->graph && key == B->key && kflags == B->kflags)) {
+        if (B->graph) cudaGraphExecDestroy(B->graph);
+        B->graph = nullptr;
+        cudaGraph_t g = nullptr;
+        const uint64_t before = rsvd_launch_count();
+        if (cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+            cudaGetLastError();
+            return batch_direct(B->ctx, count, Ps, A, Omega, S, U, V);
+        }
+        const rsvd_status st = batch_direct(B->ctx, count, Ps, A, Omega, S, U, V, true);
+        const cudaError_t ce = cudaStreamEndCapture(B->stream, &g);
+        const uint64_t captured = rsvd_launch_count() - before;
+        g_launches.fetch_sub(captured, std::memory_order_relaxed);
+        if (st != RSVD_OK || ce != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return st != RSVD_OK ? st : RSVD_ERR_CUDA;
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&B->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            B->graph = nullptr;
+            cudaGetLastError();
+            return batch_direct(B->ctx, count, Ps, A, Omega, S, U, V);
+        }
+        B->key = key;
+        B->kflags = kflags;
+        B->glaunches = captured;
+    }
+    if (cudaGraphLaunch(B->graph, B->stream) != cudaSuccess) return RSVD_ERR_CUDA;
+    note_launch((int)B->glaunches);
+    for (rsvd_plan *P : B->plans) P->last_count = P->k;
+    return RSVD_OK;
+}
+
+rsvd_status rsvd_batch_sync(rsvd_batch_t B, int *statuses) {
+    if (!B) return RSVD_ERR_ARG;
+    if (cudaStreamSynchronize(B->stream) != cudaSuccess) return RSVD_ERR_CUDA;
+    rsvd_status worst = RSVD_OK;
+    for (size_t i = 0; i < B->plans.size(); i++) {
+        const rsvd_status st = rsvd_plan_sync(B->plans[i]);
+        if (statuses) statuses[i] = st;
+        if (st != RSVD_OK && worst == RSVD_OK) worst = st;
+    }
+    return worst;
+}
+
+rsvd_status rsvd_batch_destroy(rsvd_batch_t B) {
+    if (!B) return RSVD_OK;
+    cudaStreamSynchronize(B->stream);
+    if (B->graph) cudaGraphExecDestroy(B->graph);
+    delete B;
     return RSVD_OK;
 }
 

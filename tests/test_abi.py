@@ -65,3 +65,35 @@ def test_null_plan_arguments():
     assert L.pca_threshold(None, 0.9, ctypes.byref(K)) == g.RSVD_ERR_ARG
     assert L.rsvd_plan_sync(None) == g.RSVD_ERR_ARG
     assert g.rsvd_status_string(g.RSVD_ERR_CHOL) == "Cholesky breakdown"
+
+
+def test_workspace_query_and_create_in_argument_errors():
+    L = g.lib()
+    st, b = g.rsvd_workspace_query(10, 20, 1, 0, 0)          # m < n
+    assert st == g.RSVD_ERR_ARG and b == 0
+    st, b = g.rsvd_workspace_query(100, 20, 4, 2, 1, g.RSVD_BF16)
+    assert st == g.RSVD_ERR_UNSUPPORTED
+    st, b = g.rsvd_workspace_query(1000, 64, 8, 4, 1)
+    assert st == g.RSVD_OK and b > 0 and b % 256 == 0
+    h = ctypes.c_void_p()
+    assert L.rsvd_plan_create_in(ctypes.byref(h), 1000, 64, 8, 4, 1, g.RSVD_F32, None, None, b) == g.RSVD_ERR_ARG
+    assert L.rsvd_plan_create_in(ctypes.byref(h), 1000, 64, 8, 4, 1, g.RSVD_F32, None, 4096 + 16, b) == g.RSVD_ERR_ARG
+    assert L.rsvd_plan_create_in(None, 1000, 64, 8, 4, 1, g.RSVD_F32, None, 4096, b) == g.RSVD_ERR_ARG
+    assert h.value is None
+
+
+def test_batch_and_server_argument_errors():
+    L = g.lib()
+    h = ctypes.c_void_p()
+    assert L.rsvd_batch_create(ctypes.byref(h), 0, None, None) == g.RSVD_ERR_ARG
+    assert L.rsvd_batch_create(ctypes.byref(h), g.RSVD_BATCH_MAX + 1, None, None) == g.RSVD_ERR_ARG
+    assert L.rsvd_batch_run(None, None, None, None, None, None) == g.RSVD_ERR_ARG
+    assert L.rsvd_batch_sync(None, None) == g.RSVD_ERR_ARG
+    assert L.rsvd_batch_destroy(None) == g.RSVD_OK
+    assert L.rsvd_server_create(ctypes.byref(h), 0, 4, 2) == g.RSVD_ERR_ARG
+    assert L.rsvd_server_create(ctypes.byref(h), 1 << 20, 0, 2) == g.RSVD_ERR_ARG
+    assert L.rsvd_server_create(ctypes.byref(h), 1 << 20, 4, 0) == g.RSVD_ERR_ARG
+    assert L.rsvd_server_submit(None, 0, 100, 10, 2, 1, 1, 0.9, None, None, None, None, None) == g.RSVD_ERR_ARG
+    assert L.rsvd_server_poll(None, None, 0) == g.RSVD_ERR_ARG
+    assert L.rsvd_server_pending(None) == 0
+    assert L.rsvd_server_destroy(None) == g.RSVD_OK

@@ -1,0 +1,102 @@
+"""Serving loop (rsvd_server_*): continuous batching with HBM admission.
+
+A mixed stream of requests goes through a server whose arena holds only a few
+workspaces at a time, so requests queue, batch (consecutive requests of the
+same l) and overlap.  Every result must equal the same request solved alone,
+bit for bit (status, K, S, U, V): the split-K sums run in a fixed order and a
+batch runs each problem's own kernels.  Admission follows arrival order."""
+import numpy as np
+import pytest
+import torch
+
+import paper_1906_12085_gb300 as g
+import synth
+
+pytestmark = pytest.mark.gpu
+
+Q = 2
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1906_12085_gb300 import build
+    build.build()
+
+
+def _requests(count, seed):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(count):
+        n = int(rng.choice([64, 128, 256]))
+        m = int(rng.integers(max(1000, n), 20000))
+        k = int(rng.choice([8, 16, 24]))
+        p = 8
+        alpha = float(rng.uniform(0.5, 2.0))
+        sig = synth.spectrum_power(n, alpha)
+        A = synth.prescribed(m, n, sig, 1000 + i, 2000 + i).float()
+        Om = synth.gaussian(n, k + p, seed=3000 + i, dtype=torch.float32)
+        reqs.append(dict(id=i, m=m, n=n, k=k, p=p, A=A, Om=Om))
+    return reqs
+
+
+def _alone(r):
+    dev = torch.device("cuda")
+    S = torch.zeros(r["k"], dtype=torch.float64, device=dev)
+    U = torch.zeros(r["m"], r["k"], device=dev)
+    V = torch.zeros(r["n"], r["k"], device=dev)
+    with g.rsvd_plan_create(r["m"], r["n"], r["k"], r["p"], Q, g.RSVD_F32) as plan:
+        g.check(g.rsvd(plan, r["A"].to(dev), None, r["Om"].to(dev), S, U, V))
+        st = g.rsvd_plan_sync(plan)
+        stK, K = g.pca_threshold(plan, 0.9)
+    return (stK if st == g.RSVD_OK else st), K, S.cpu().numpy(), U.cpu().numpy(), V.cpu().numpy()
+
+
+def test_served_results_equal_alone_bitwise():
+    reqs = _requests(24, 7)
+    alone = {r["id"]: _alone(r) for r in reqs}
+    dev = torch.device("cuda")
+    for r in reqs:
+        r["Ad"], r["Od"] = r["A"].to(dev), r["Om"].to(dev)
+        r["S"] = torch.zeros(r["k"], dtype=torch.float64, device=dev)
+        r["U"] = torch.zeros(r["m"], r["k"], device=dev)
+        r["V"] = torch.zeros(r["n"], r["k"], device=dev)
+    ws = max(g.rsvd_workspace_query(r["m"], r["n"], r["k"], r["p"], Q)[1] for r in reqs)
+    torch.cuda.synchronize()
+    done = []
+    with g.rsvd_server_create(3 * ws, max_batch=4, max_inflight=3) as srv:
+        for i, r in enumerate(reqs):           # arrivals interleaved with progress
+            g.check(g.rsvd_server_submit(srv, r["id"], r["k"], r["p"], Q, 0.9, r["Ad"], r["Od"], r["S"], r["U"],
+                                         r["V"]), "submit")
+            if i % 3 == 2:
+                done += g.rsvd_server_poll(srv)
+        while g.rsvd_server_pending(srv) > 0:
+            done += g.rsvd_server_poll(srv)
+    torch.cuda.synchronize()
+    assert sorted(c["id"] for c in done) == [r["id"] for r in reqs]
+    assert any(c["batch"] > 1 for c in done)
+    starts = {c["id"]: c["start_ms"] for c in done}
+    assert all(starts[i] <= starts[i + 1] for i in range(len(reqs) - 1))   # arrival order kept
+    for c in done:
+        r = reqs[c["id"]]
+        a_st, a_K, a_S, a_U, a_V = alone[c["id"]]
+        assert c["submit_ms"] <= c["start_ms"] <= c["done_ms"] + 1e-3
+        assert c["status"] == a_st and c["K"] == a_K
+        assert np.array_equal(r["S"].cpu().numpy(), a_S)
+        assert np.array_equal(r["U"].cpu().numpy(), a_U)
+        assert np.array_equal(r["V"].cpu().numpy(), a_V)
+
+
+def test_server_rejects_request_larger_than_arena():
+    dev = torch.device("cuda")
+    m, n, k, p = 20000, 256, 16, 8
+    ws = g.rsvd_workspace_query(m, n, k, p, Q)[1]
+    with g.rsvd_server_create(ws // 2, max_batch=2, max_inflight=1) as srv:
+        A = torch.zeros(m, n, device=dev)
+        Om = torch.zeros(n, k + p, device=dev)
+        S = torch.zeros(k, dtype=torch.float64, device=dev)
+        U = torch.zeros(m, k, device=dev)
+        V = torch.zeros(n, k, device=dev)
+        assert g.rsvd_server_submit(srv, 0, k, p, Q, 0.9, A, Om, S, U, V) == g.RSVD_ERR_OOM
+        assert g.rsvd_server_pending(srv) == 0
