@@ -77,7 +77,7 @@ typedef struct rsvd_plan *rsvd_plan_t;
  * workspace once (cudaMalloc) and launches everything on `cuda_stream`
  * (a cudaStream_t, may be NULL).  For svd_exact the plan needs n <= 112 (the
  * n x n eigen / SVD problem is solved in one CTA's shared memory); for rsvd
- * l <= 112.  Returns RSVD_ERR_ARG on inconsistent sizes, RSVD_ERR_UNSUPPORTED
+ * l <= 128 (RSVD_F32) or l <= 112 (RSVD_F64).  Returns RSVD_ERR_ARG on inconsistent sizes, RSVD_ERR_UNSUPPORTED
  * for a dtype this build does not implement, RSVD_ERR_OOM if the workspace
  * cannot be allocated.  On error *plan is set to NULL.
  */

@@ -19,6 +19,9 @@ enum StatusBits : int {
 
 // Largest l (or n for svd_exact) whose l x l working set fits one CTA's shared memory.
 constexpr int kSmallMaxF64 = 112;
+// Largest l of a float32 randomized solve: the float32 Jacobi working set and the
+// 16 x 8 register blocks of the Cholesky kernel, and N <= 128 of the tensor-core products.
+constexpr int kSmallMaxF32 = 128;
 // Largest Lanczos step count whose bidiagonal SVD fits one CTA in float32.
 constexpr int kGklMaxStepsF32 = 160;
 

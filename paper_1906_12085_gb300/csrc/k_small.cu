@@ -255,8 +255,9 @@ __device__ __forceinline__ void jacobi_osvd_body(const double *__restrict__ R, i
         X[idx] = (p < l && i < l) ? (Ta)R[i * l + p] : Ta(0);
         V[idx] = (p == i) ? Ta(1) : Ta(0);
     }
-    // rotate when |x_p . x_q| > tol ||x_p|| ||x_q||
-    const Ta tol = (Ta)((double)l * Eps<Ta>::v);
+    // rotate when |x_p . x_q| > tol ||x_p|| ||x_q||, tol = sqrt(l) eps: the converged
+    // columns are then orthogonal to sqrt(l) eps (an l eps threshold leaves l eps)
+    const Ta tol = (Ta)(sqrt((double)l) * Eps<Ta>::v);
     int sweep = 0;
     bool converged = false;
     __syncthreads();

@@ -726,7 +726,7 @@ rsvd_status plan_init(rsvd_plan *P, int64_t m, int64_t n, int k, int p, int q, r
     if (m < 1 || n < 1 || m < n || k < 1 || p < 0 || q < 0) return RSVD_ERR_ARG;
     if ((int64_t)k + p > n) return RSVD_ERR_ARG;
     if (dtype != RSVD_F32 && dtype != RSVD_F64) return RSVD_ERR_UNSUPPORTED;
-    if (k + p > kSmallMaxF64) return RSVD_ERR_UNSUPPORTED;
+    if (k + p > (dtype == RSVD_F32 ? kSmallMaxF32 : kSmallMaxF64)) return RSVD_ERR_UNSUPPORTED;
     P->m = m;
     P->n = n;
     P->k = k;
