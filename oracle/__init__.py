@@ -15,6 +15,9 @@ Functions and the passages they follow:
 * ``gkl``           -- Golub-Kahan-Lanczos with full reorthogonalisation
 * ``pca_threshold`` -- Sec. 2.4 cumulative explained-variance criterion
 * ``qr``            -- Householder QR (orthonormalisation inside ``rsvd``)
+* ``quantize_bf16``, ``quantize_e4m3`` and the encoders / decoders -- the
+  storage formats of the precision form (bfloat16 round-to-nearest-even; OCP
+  e4m3 with per-column scales amax/448, round-to-nearest-even, saturating)
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py`` against
 closed forms, prescribed spectra, invariants, brute force on 4x3 integer
@@ -64,6 +67,16 @@ def lib():
         L.orc_gkl.argtypes = [i64, i64, P, P, ctypes.c_int, i64, P, P, P, P, P]
         L.orc_pca_threshold.argtypes = [i64, P, ctypes.c_double, ctypes.c_double, ctypes.POINTER(i64)]
         L.orc_sign_normalize.argtypes = [i64, i64, i64, P, P]
+        L.orc_bf16_encode.argtypes = [ctypes.c_float]
+        L.orc_bf16_encode.restype = ctypes.c_uint16
+        L.orc_bf16_decode.argtypes = [ctypes.c_uint16]
+        L.orc_bf16_decode.restype = ctypes.c_double
+        L.orc_e4m3_encode.argtypes = [ctypes.c_float]
+        L.orc_e4m3_encode.restype = ctypes.c_uint8
+        L.orc_e4m3_decode.argtypes = [ctypes.c_uint8]
+        L.orc_e4m3_decode.restype = ctypes.c_double
+        L.orc_quantize_bf16.argtypes = [i64, i64, ctypes.c_void_p, i64, ctypes.c_void_p]
+        L.orc_quantize_e4m3.argtypes = [i64, i64, ctypes.c_void_p, i64, ctypes.c_void_p, ctypes.c_void_p]
         for f in ("orc_center", "orc_qr", "orc_svd", "orc_eig_jacobi", "orc_svd_gram", "orc_rsvd",
                   "orc_gkl", "orc_pca_threshold"):
             getattr(L, f).restype = ctypes.c_int
@@ -180,3 +193,65 @@ def sign_normalize(U, V):
     v = _f64(V).copy()
     lib().orc_sign_normalize(u.shape[0], v.shape[0], v.shape[1], _p(u), _p(v))
     return u, v
+
+
+# ------------------------------------------------------------ storage formats
+def bf16_encode(x: float) -> int:
+    return int(lib().orc_bf16_encode(float(np.float32(x))))
+
+
+def bf16_decode(b: int) -> float:
+    return float(lib().orc_bf16_decode(int(b)))
+
+
+def e4m3_encode(x: float) -> int:
+    return int(lib().orc_e4m3_encode(float(np.float32(x))))
+
+
+def e4m3_decode(c: int) -> float:
+    return float(lib().orc_e4m3_decode(int(c)))
+
+
+def _f32(x) -> np.ndarray:
+    if hasattr(x, "detach"):
+        x = x.detach().cpu().numpy()
+    return np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+
+
+def quantize_bf16(A) -> np.ndarray:
+    """bfloat16 codes (uint16, m x n) of the float32 matrix A."""
+    a = _f32(A)
+    m, n = a.shape
+    out = np.empty((m, n), dtype=np.uint16)
+    lib().orc_quantize_bf16(m, n, a.ctypes.data, n, out.ctypes.data)
+    return out
+
+
+def quantize_e4m3(A):
+    """(e4m3 codes uint8 m x n, float32 column scales n) of the float32 matrix A."""
+    a = _f32(A)
+    m, n = a.shape
+    out = np.empty((m, n), dtype=np.uint8)
+    sc = np.empty(n, dtype=np.float32)
+    lib().orc_quantize_e4m3(m, n, a.ctypes.data, n, out.ctypes.data, sc.ctypes.data)
+    return out, sc
+
+
+_BF16_LUT = None
+_E4M3_LUT = None
+
+
+def dequantize_bf16(codes) -> np.ndarray:
+    """float64 values of bfloat16 codes (exact)."""
+    global _BF16_LUT
+    if _BF16_LUT is None:
+        _BF16_LUT = np.array([bf16_decode(i) for i in range(65536)], dtype=np.float64)
+    return _BF16_LUT[np.asarray(codes, dtype=np.uint16)]
+
+
+def dequantize_e4m3(codes, scales) -> np.ndarray:
+    """float64 values code * scale (exact: 4 significant bits times a float32)."""
+    global _E4M3_LUT
+    if _E4M3_LUT is None:
+        _E4M3_LUT = np.array([e4m3_decode(i) for i in range(256)], dtype=np.float64)
+    return _E4M3_LUT[np.asarray(codes, dtype=np.uint8)] * np.asarray(scales, dtype=np.float64)[None, :]

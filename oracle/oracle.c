@@ -552,3 +552,89 @@ void orc_sign_normalize(int64_t m, int64_t n, int64_t k, double *U, double *V) {
         }
     }
 }
+
+
+/* ------------------------------------------------ precision-form storage formats
+ * Written from the format definitions: every finite value of the target format
+ * is enumerated (or bracketed) and the nearest one is chosen by an exact
+ * comparison in float64, ties to the even code. */
+
+static double bf16_value(uint16_t b) {
+    uint32_t u = (uint32_t)b << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+double orc_bf16_decode(uint16_t b) { return bf16_value(b); }
+
+uint16_t orc_bf16_encode(float x) {
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    if (x != x) return (uint16_t)((u >> 16) | 0x0040u);  /* NaN stays NaN (quiet) */
+    /* the two bfloat16 values bracketing x: the truncation toward zero and the
+     * next one away from zero (same sign); both exact in float64 */
+    const uint16_t lo = (uint16_t)(u >> 16);
+    const uint16_t hi = (uint16_t)(lo + 1);
+    if ((u & 0xFFFFu) == 0) return lo;                    /* exactly representable */
+    const double v = (double)x, a = bf16_value(lo);
+    /* the upper neighbour as if the exponent range were unbounded (IEEE rounding:
+     * a value nearer 2^128 than the largest finite bfloat16 overflows to infinity) */
+    const double b = ((hi & 0x7FFFu) == 0x7F80u) ? (x < 0.f ? -ldexp(1.0, 128) : ldexp(1.0, 128)) : bf16_value(hi);
+    const double da = fabs(v - a), db = fabs(b - v);
+    if (da < db) return lo;
+    if (db < da) return hi;
+    return (lo & 1u) ? hi : lo;                           /* tie: even mantissa */
+}
+
+static double e4m3_value(uint8_t c) {
+    const int s = c >> 7, e = (c >> 3) & 15, mt = c & 7;
+    double v;
+    if (e == 0) v = ldexp((double)mt, -9);               /* subnormal: m * 2^-9 */
+    else v = ldexp(1.0 + mt / 8.0, e - 7);
+    return s ? -v : v;
+}
+
+double orc_e4m3_decode(uint8_t c) {
+    if ((c & 0x7F) == 0x7F) return NAN;
+    return e4m3_value(c);
+}
+
+uint8_t orc_e4m3_encode(float x) {
+    if (x != x) return 0x7F;
+    const double v = fabs((double)x);
+    const uint8_t sign = signbit(x) ? 0x80 : 0x00;   /* a zero result keeps the sign of x */
+    if (v >= 448.0) return (uint8_t)(sign | 0x7E);        /* saturate to the largest finite */
+    int best = 0;
+    double bd = v;                                        /* distance to code 0 (value 0) */
+    for (int c = 1; c <= 0x7E; c++) {                     /* every non-negative finite code */
+        const double d = fabs(e4m3_value((uint8_t)c) - v);
+        if (d < bd || (d == bd && (c & 1) == 0 && (best & 1) == 1)) {
+            bd = d;
+            best = c;
+        }
+    }
+    return (uint8_t)(sign | best);
+}
+
+void orc_quantize_bf16(int64_t m, int64_t n, const float *A, int64_t lda, uint16_t *out) {
+    for (int64_t i = 0; i < m; i++)
+        for (int64_t j = 0; j < n; j++) out[i * n + j] = orc_bf16_encode(A[i * lda + j]);
+}
+
+void orc_quantize_e4m3(int64_t m, int64_t n, const float *A, int64_t lda, uint8_t *out, float *scales) {
+    for (int64_t j = 0; j < n; j++) {
+        float amax = 0.f;
+        for (int64_t i = 0; i < m; i++) {
+            const float a = fabsf(A[i * lda + j]);
+            if (a > amax) amax = a;
+        }
+        volatile float s = amax > 0.f ? amax / 448.0f : 1.0f;   /* float32 division */
+        scales[j] = s;
+    }
+    for (int64_t i = 0; i < m; i++)
+        for (int64_t j = 0; j < n; j++) {
+            volatile float q = A[i * lda + j] / scales[j];        /* rounded to float32 */
+            out[i * n + j] = orc_e4m3_encode(q);
+        }
+}

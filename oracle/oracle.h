@@ -63,6 +63,22 @@ int orc_pca_threshold(int64_t count, const double *sigma, double fro2, double t,
  * the matching column of U (sign convention of all oracle outputs). */
 void orc_sign_normalize(int64_t m, int64_t n, int64_t k, double *U, double *V);
 
+/* ---- Storage formats of the precision form (reading c11 of the survey) ----
+ * bfloat16: the float32 value rounded to the nearest bfloat16 (8 exponent
+ * bits, 7 stored mantissa bits), ties to the even mantissa.
+ * e4m3 (OCP FP8 "E4M3FN": bias 7, 3 mantissa bits, no infinities, NaN =
+ * S.1111.111, largest finite 448): per column j the scale s_j = amax_j / 448
+ * computed in float32 (s_j = 1 for an all-zero column), the quotient
+ * a / s_j rounded to float32, then the nearest e4m3 value with ties to the
+ * even code, magnitudes above 448 saturated to 448. */
+uint16_t orc_bf16_encode(float x);
+double orc_bf16_decode(uint16_t b);
+uint8_t orc_e4m3_encode(float x);
+double orc_e4m3_decode(uint8_t c);
+/* A float32 m x n (lda) -> codes m x n (row-major) and n column scales. */
+void orc_quantize_bf16(int64_t m, int64_t n, const float *A, int64_t lda, uint16_t *out);
+void orc_quantize_e4m3(int64_t m, int64_t n, const float *A, int64_t lda, uint8_t *out, float *scales);
+
 #ifdef __cplusplus
 }
 #endif
