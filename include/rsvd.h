@@ -215,6 +215,25 @@ uint64_t rsvd_launch_count(void);
 /* Static description of a status code. */
 const char *rsvd_status_string(rsvd_status s);
 
+/*
+ * Storage of the precision form (BF16 / FP8 e4m3 matrices; the paper works in
+ * float64 throughout and has no counterpart).  A: m x n float32 (lda >= n,
+ * device).  Aq: m x n row-major codes (device; 2 bytes per entry for
+ * RSVD_BF16, 1 byte for RSVD_FP8_E4M3).
+ *   RSVD_BF16     : the nearest bfloat16 value, ties to even.
+ *   RSVD_FP8_E4M3 : col_scales (n floats, device) receive s_j = amax_j / 448
+ *                   (float32 division; 1 for an all-zero column) and Aq the
+ *                   nearest OCP e4m3 value (bias 7, 3 mantissa bits, no
+ *                   infinities) of the float32 quotient a_ij / s_j, ties to
+ *                   even, magnitudes above 448 saturated to 448.
+ * The stored matrix is then exactly Aq (bfloat16) or Aq diag(s) (e4m3).
+ * Asynchronous on cuda_stream; no workspace (col_scales also holds the
+ * column maxima while they are reduced).  RSVD_ERR_ARG for NULL pointers or
+ * bad sizes, RSVD_ERR_UNSUPPORTED for other dtypes.
+ */
+rsvd_status rsvd_quantize(const float *A, int64_t m, int64_t n, int64_t lda, rsvd_dtype dtype, void *Aq,
+                          float *col_scales, void *cuda_stream);
+
 /* ====================================================================
  * Batching and serving.  The paper has no counterpart: these run many
  * independent randomized PCA problems (Sec. 3.1.2) at once.  Each problem
@@ -258,6 +277,29 @@ rsvd_status rsvd_batch_run(rsvd_batch_t batch, void *const *A, const void *const
                            void *const *U, void *const *V);
 rsvd_status rsvd_batch_sync(rsvd_batch_t batch, int *statuses);
 rsvd_status rsvd_batch_destroy(rsvd_batch_t batch);
+
+/*
+ * Autotuner of the products' launch shape (float32 plans on the tensor-core
+ * path): the number of persistent CTAs of Y = A X and of Z = A^T X.  The tiles
+ * and their order of summation do not depend on it, so results are bitwise the
+ * same under every choice; only the sharing of the GPU between concurrent
+ * problems changes.  Runs `concurrency` (1..64) copies of the plan's problem on A and
+ * Omega (the caller's plan plus concurrency-1 temporary plans, as one lockstep
+ * batch like rsvd_batch_run) under each candidate decomposition, keeps the one
+ * with the smallest median batch time over three runs, and records it in a
+ * process-wide table keyed by (ceil(log2 m), n, l rounded up to 16): the plan
+ * and every plan created later in that bucket (rsvd_plan_create,
+ * rsvd_plan_create_in, the serving loop) use it.  Synchronises; allocates and
+ * frees temporary device memory; the plan's outputs of the last solve are not
+ * kept (solve again before pca_threshold).  nn_ctas / tn_ctas (host, may be
+ * NULL) receive the choice, 0 meaning the default (one CTA per SM).  Other plans: RSVD_OK with the current (default)
+ * choice.  rsvd_tune_lookup returns RSVD_OK and the recorded choice for a
+ * bucket, RSVD_ERR_ARG when there is none; rsvd_tune_clear empties the table.
+ */
+rsvd_status rsvd_autotune(rsvd_plan_t plan, void *A, const void *Omega, int concurrency, int *nn_ctas,
+                          int *tn_ctas);
+rsvd_status rsvd_tune_lookup(int64_t m, int64_t n, int k, int p, int *nn_ctas, int *tn_ctas);
+void rsvd_tune_clear(void);
 
 /*
  * Serving loop: continuous batching of float32 randomized PCA requests.

@@ -25,7 +25,8 @@ __all__ = [
     "STAGES", "svd_exact_gram_static", "RSVD_BATCH_MAX", "Completion", "rsvd_workspace_query",
     "rsvd_plan_create_in", "Batch", "rsvd_batch_create", "rsvd_batch_run", "rsvd_batch_sync",
     "rsvd_batch_destroy", "Server", "rsvd_server_create", "rsvd_server_submit", "rsvd_server_poll",
-    "rsvd_server_pending", "rsvd_server_destroy",
+    "rsvd_server_pending", "rsvd_server_destroy", "rsvd_autotune", "rsvd_tune_lookup", "rsvd_tune_clear",
+    "rsvd_quantize",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -106,11 +107,17 @@ def lib() -> ctypes.CDLL:
     L.rsvd_server_poll.argtypes = [vp, ctypes.POINTER(Completion), i32]
     L.rsvd_server_pending.argtypes = [vp]
     L.rsvd_server_destroy.argtypes = [vp]
+    L.rsvd_autotune.argtypes = [vp, vp, vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    L.rsvd_tune_lookup.argtypes = [i64, i64, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    L.rsvd_quantize.argtypes = [vp, i64, i64, i64, i32, vp, vp, vp]
+    L.rsvd_tune_clear.argtypes = []
+    L.rsvd_tune_clear.restype = None
     for f in ("rsvd_plan_create", "rsvd_plan_destroy", "rsvd_plan_set_flags", "rsvd_plan_sync", "rsvd",
               "svd_exact", "svd_truncated_krylov", "pca_threshold", "rsvd_plan_fro2", "rsvd_plan_profile",
               "rsvd_plan_profile_read", "rsvd_workspace_query", "rsvd_plan_create_in", "rsvd_batch_create",
               "rsvd_batch_run", "rsvd_batch_sync", "rsvd_batch_destroy", "rsvd_server_create",
-              "rsvd_server_submit", "rsvd_server_poll", "rsvd_server_pending", "rsvd_server_destroy"):
+              "rsvd_server_submit", "rsvd_server_poll", "rsvd_server_pending", "rsvd_server_destroy",
+              "rsvd_autotune", "rsvd_tune_lookup", "rsvd_quantize"):
         getattr(L, f).restype = i32
     _lib = L
     return L
@@ -391,3 +398,26 @@ def rsvd_server_pending(server: Server) -> int:
 def rsvd_server_destroy(server: Server) -> int:
     server.close()
     return RSVD_OK
+
+
+def rsvd_autotune(plan: Plan, A, Omega, concurrency: int = 1) -> tuple[int, int, int]:
+    """(status, nn_ctas, tn_ctas): tune the products' decomposition for the plan's bucket."""
+    a, b = ctypes.c_int(0), ctypes.c_int(0)
+    st = lib().rsvd_autotune(plan.handle, _ptr(A), _ptr(Omega), concurrency, ctypes.byref(a), ctypes.byref(b))
+    return st, a.value, b.value
+
+
+def rsvd_tune_lookup(m: int, n: int, k: int, p: int) -> tuple[int, int, int]:
+    a, b = ctypes.c_int(0), ctypes.c_int(0)
+    st = lib().rsvd_tune_lookup(m, n, k, p, ctypes.byref(a), ctypes.byref(b))
+    return st, a.value, b.value
+
+
+def rsvd_tune_clear() -> None:
+    lib().rsvd_tune_clear()
+
+
+def rsvd_quantize(A, dtype: int, Aq, col_scales=None, stream=None) -> int:
+    """Store the float32 matrix A (device) as bfloat16 or e4m3 codes in Aq (see include/rsvd.h)."""
+    m, n = A.shape
+    return lib().rsvd_quantize(_ptr(A), m, n, n, int(dtype), _ptr(Aq), _ptr(col_scales), _stream(stream))

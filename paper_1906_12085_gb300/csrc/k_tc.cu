@@ -114,9 +114,18 @@ __device__ __forceinline__ void store_a(uint32_t tmem, int q, int h, int s, cons
     tmem_st16(tmem + lane_base + col + 32, lo);
 }
 
-// Epilogue: one TMEM lane quarter of accumulator b -> N floats per row at dst (row stride ld).
+// K steps (stages) accumulated in one TMEM accumulator before it is drained: the
+// tensor core's float32 accumulation does not round to nearest, so its error grows
+// with the number of accumulation steps; sub-chunks of SUBK stages (256 rows or
+// columns of K) bound it, and the epilogue adds the sub-chunk results with IEEE
+// float32 additions in a fixed order.
+constexpr int SUBK = 8;
+
+// Epilogue: one TMEM lane quarter of accumulator b -> N floats per row at dst;
+// `add` accumulates into dst (written by the same thread for the previous sub-chunk).
 template <int N>
-__device__ __forceinline__ void drain_acc(uint32_t tmem, uint32_t b, int q, int lane, float *dst, bool valid) {
+__device__ __forceinline__ void drain_acc(uint32_t tmem, uint32_t b, int q, int lane, float *dst, bool valid,
+                                          bool add = false) {
 #pragma unroll
     for (int c0 = 0; c0 < N; c0 += 32) {
         float v[32];
@@ -125,14 +134,46 @@ __device__ __forceinline__ void drain_acc(uint32_t tmem, uint32_t b, int q, int 
             float *p = dst + c0;
             if (c0 + 32 <= N && ((reinterpret_cast<uintptr_t>(p) & 15) == 0)) {
 #pragma unroll
-                for (int j = 0; j < 32; j += 4)
-                    *reinterpret_cast<float4 *>(p + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                for (int j = 0; j < 32; j += 4) {
+                    float4 w = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    if (add) {
+                        const float4 o = *reinterpret_cast<const float4 *>(p + j);
+                        w.x += o.x; w.y += o.y; w.z += o.z; w.w += o.w;
+                    }
+                    *reinterpret_cast<float4 *>(p + j) = w;
+                }
             } else {
 #pragma unroll
                 for (int j = 0; j < 32; j++)
-                    if (c0 + j < N) p[j] = v[j];
+                    if (c0 + j < N) p[j] = add ? p[j] + v[j] : v[j];
             }
         }
+    }
+}
+
+// Sub-chunk results summed in registers (N <= 64: N floats per epilogue thread) and
+// written once per tile; wider tiles add into memory after every sub-chunk instead.
+template <int N>
+__device__ __forceinline__ void sum_acc(uint32_t tmem, uint32_t b, int q, float *acc, bool first) {
+#pragma unroll
+    for (int c0 = 0; c0 < N; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + b * ACC_STRIDE + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+        for (int j = 0; j < 16; j++) acc[c0 + j] = first ? v[j] : acc[c0 + j] + v[j];
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void store_acc(const float *acc, float *dst, bool valid) {
+    if (!valid) return;
+    if ((N % 4) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+#pragma unroll
+        for (int j = 0; j < N; j += 4)
+            *reinterpret_cast<float4 *>(dst + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < N; j++) dst[j] = acc[j];
     }
 }
 
@@ -210,22 +251,24 @@ __global__ void __launch_bounds__(NTHR, 1)
         if (lane == 0) {
             uint32_t g = 0, it = 0;
             bool ok = true;
-            for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x, it++) {
-                const uint32_t b = it & 1;
-                if (!(ok = wait_ok(&bar->acc_empty[b], ((it >> 1) & 1) ^ 1, abort_flag))) break;
-                tc_fence_after();
-                const uint32_t d = tmem + b * ACC_STRIDE;
-                for (int kb = 0; kb < nkb; kb++, g++) {
-                    const int s = g % S, ts = g % TS;
-                    if (!(ok = wait_ok(&bar->split[ts], (g / TS) & 1, abort_flag))) break;
+            for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x)
+                for (int k0 = 0; ok && k0 < nkb; k0 += SUBK, it++) {  // one accumulator per sub-chunk
+                    const int k1 = k0 + SUBK < nkb ? k0 + SUBK : nkb;
+                    const uint32_t b = it & 1;
+                    if (!(ok = wait_ok(&bar->acc_empty[b], ((it >> 1) & 1) ^ 1, abort_flag))) break;
                     tc_fence_after();
-                    const uint32_t a = tmem + A_COL0 + (uint32_t)ts * 64;
-                    mma_stage<N>(d, a, a + 32, sBh + s * C::B_STAGE, sBl + s * C::B_STAGE, kb == 0);
-                    mma_commit(&bar->empty[s]);
-                    mma_commit(&bar->tempty[ts]);
+                    const uint32_t d = tmem + b * ACC_STRIDE;
+                    for (int kb = k0; kb < k1; kb++, g++) {
+                        const int s = g % S, ts = g % TS;
+                        if (!(ok = wait_ok(&bar->split[ts], (g / TS) & 1, abort_flag))) break;
+                        tc_fence_after();
+                        const uint32_t a = tmem + A_COL0 + (uint32_t)ts * 64;
+                        mma_stage<N>(d, a, a + 32, sBh + s * C::B_STAGE, sBl + s * C::B_STAGE, kb == k0);
+                        mma_commit(&bar->empty[s]);
+                        mma_commit(&bar->tempty[ts]);
+                    }
+                    if (ok) mma_commit(&bar->acc_full[b]);
                 }
-                if (ok) mma_commit(&bar->acc_full[b]);
-            }
         }
     } else if (warp < EPI_WARP0) {
         // split workers; with `mu` the column means are subtracted on the fly (A itself
@@ -282,14 +325,21 @@ __global__ void __launch_bounds__(NTHR, 1)
     } else {
         const int q = warp & 3;
         uint32_t it = 0;
-        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, it++) {
-            const uint32_t b = it & 1;
-            if (!wait_ok(&bar->acc_full[b], (it >> 1) & 1, abort_flag)) break;
-            tc_fence_after();
+        bool ok = true;
+        for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
             const int64_t row = t * TM + q * 32 + lane;
-            drain_acc<N>(tmem, b, q, lane, Y + row * ldy, row < m);
-            tc_fence_before();
-            mbar_arrive(&bar->acc_empty[b]);
+            float acc[N <= 64 ? N : 1];
+            for (int k0 = 0; k0 < nkb; k0 += SUBK, it++) {
+                const uint32_t b = it & 1;
+                if (!(ok = wait_ok(&bar->acc_full[b], (it >> 1) & 1, abort_flag))) break;
+                tc_fence_after();
+                if constexpr (N <= 64) sum_acc<N>(tmem, b, q, acc, k0 == 0);
+                else drain_acc<N>(tmem, b, q, lane, Y + row * ldy, row < m, k0 > 0);
+                tc_fence_before();
+                mbar_arrive(&bar->acc_empty[b]);
+            }
+            if constexpr (N <= 64)
+                if (ok) store_acc<N>(acc, Y + row * ldy, row < m);
         }
     }
     tc_fence_before();
@@ -402,25 +452,28 @@ __global__ void __launch_bounds__(NTHR, 1)
         if (lane == 0) {
             uint32_t g = 0, it = 0;
             bool ok = true;
-            for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x, it++) {
+            for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
                 int64_t r0, r1;
                 int c0;
                 tile_rows(t, r0, r1, c0);
                 const int nkb = (int)((r1 - r0 + TBK - 1) / TBK);
-                const uint32_t b = it & 1;
-                if (!(ok = wait_ok(&bar->acc_empty[b], ((it >> 1) & 1) ^ 1, abort_flag))) break;
-                tc_fence_after();
-                const uint32_t d = tmem + b * ACC_STRIDE;
-                for (int kb = 0; kb < nkb; kb++, g++) {
-                    const int s = g % SS;
-                    if (!(ok = wait_ok(&bar->split[s], (g / SS) & 1, abort_flag))) break;
+                for (int k0 = 0; ok && k0 < nkb; k0 += SUBK, it++) {  // one accumulator per sub-chunk
+                    const int k1 = k0 + SUBK < nkb ? k0 + SUBK : nkb;
+                    const uint32_t b = it & 1;
+                    if (!(ok = wait_ok(&bar->acc_empty[b], ((it >> 1) & 1) ^ 1, abort_flag))) break;
                     tc_fence_after();
-                    uint8_t *sp = sSplit + s * C::SPL;
-                    const uint32_t a = tmem + A_COL0 + (uint32_t)s * 64;
-                    mma_stage<N>(d, a, a + 32, sp, sp + C::SPL_B, kb == 0);
-                    mma_commit(&bar->empty[SR + s]);
+                    const uint32_t d = tmem + b * ACC_STRIDE;
+                    for (int kb = k0; kb < k1; kb++, g++) {
+                        const int s = g % SS;
+                        if (!(ok = wait_ok(&bar->split[s], (g / SS) & 1, abort_flag))) break;
+                        tc_fence_after();
+                        uint8_t *sp = sSplit + s * C::SPL;
+                        const uint32_t a = tmem + A_COL0 + (uint32_t)s * 64;
+                        mma_stage<N>(d, a, a + 32, sp, sp + C::SPL_B, kb == k0);
+                        mma_commit(&bar->empty[SR + s]);
+                    }
+                    if (ok) mma_commit(&bar->acc_full[b]);
                 }
-                if (ok) mma_commit(&bar->acc_full[b]);
             }
         }
     } else if (warp < EPI_WARP0) {
@@ -485,18 +538,27 @@ __global__ void __launch_bounds__(NTHR, 1)
     } else {
         const int q = warp & 3;
         uint32_t it = 0;
-        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, it++) {
+        bool ok = true;
+        for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
             int64_t r0, r1;
             int c0;
             tile_rows(t, r0, r1, c0);
+            const int nkb = (int)((r1 - r0 + TBK - 1) / TBK);
             const int64_t chunk = t / ntn;
-            const uint32_t b = it & 1;
-            if (!wait_ok(&bar->acc_full[b], (it >> 1) & 1, abort_flag)) break;
-            tc_fence_after();
             const int c = c0 + q * 32 + lane;
-            drain_acc<N>(tmem, b, q, lane, part + (chunk * ncols + c) * (int64_t)N, c < ncols);
-            tc_fence_before();
-            mbar_arrive(&bar->acc_empty[b]);
+            float *dst = part + (chunk * ncols + c) * (int64_t)N;
+            float acc[N <= 64 ? N : 1];
+            for (int k0 = 0; k0 < nkb; k0 += SUBK, it++) {
+                const uint32_t b = it & 1;
+                if (!(ok = wait_ok(&bar->acc_full[b], (it >> 1) & 1, abort_flag))) break;
+                tc_fence_after();
+                if constexpr (N <= 64) sum_acc<N>(tmem, b, q, acc, k0 == 0);
+                else drain_acc<N>(tmem, b, q, lane, dst, c < ncols, k0 > 0);
+                tc_fence_before();
+                mbar_arrive(&bar->acc_empty[b]);
+            }
+            if constexpr (N <= 64)
+                if (ok) store_acc<N>(acc, dst, c < ncols);
         }
     }
     tc_fence_before();
@@ -587,15 +649,14 @@ int num_sms() {
 
 template <int N>
 cudaError_t launch_nn(const CUtensorMap &a, const CUtensorMap &bh, const CUtensorMap &bl, int64_t m, int n, float *Y,
-                      int64_t ldy, int *status, const float *mu, double *ssq, cudaStream_t s) {
+                      int64_t ldy, int *status, const float *mu, double *ssq, cudaStream_t s, int ctas) {
     using C = NNCfg<N>;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(tc_nn_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         attr = true;
     }
-    const int64_t tiles = ceil_div(m, TM);
-    const int grid = (int)(tiles < num_sms() ? tiles : num_sms());
+    const int grid = tc_gemm_nn_grid(m, ctas);
     tc_nn_kernel<N><<<grid, NTHR, C::SMEM, s>>>(a, bh, bl, m, n, Y, ldy, status, mu, ssq);
     note_launch();
     return cudaGetLastError();
@@ -603,7 +664,7 @@ cudaError_t launch_nn(const CUtensorMap &a, const CUtensorMap &bh, const CUtenso
 
 template <int N>
 cudaError_t launch_tn(const CUtensorMap &a, const CUtensorMap &qm, int64_t rows, int ncols, int64_t rpc, int nchunks,
-                      float *part, int *status, const float *mu, cudaStream_t s) {
+                      float *part, int *status, const float *mu, cudaStream_t s, int ctas) {
     using C = TNCfg<N>;
     static bool attr = false;
     if (!attr) {
@@ -611,7 +672,8 @@ cudaError_t launch_tn(const CUtensorMap &a, const CUtensorMap &qm, int64_t rows,
         attr = true;
     }
     const int64_t tiles = ceil_div(ncols, TM) * nchunks;
-    const int grid = (int)(tiles < num_sms() ? tiles : num_sms());
+    const int64_t cap = ctas > 0 && ctas < num_sms() ? ctas : num_sms();
+    const int grid = (int)(tiles < cap ? tiles : cap);
     tc_tn_kernel<N><<<grid, NTHR, C::SMEM, s>>>(a, qm, rows, ncols, rpc, nchunks, part, status, mu);
     note_launch();
     return cudaGetLastError();
@@ -622,6 +684,9 @@ struct TNSplit {
     int chunks;
 };
 
+// Row chunks of A^T Q: about 2 x SMs column-tile x chunk tiles, at least four stages
+// per tile.  The split does not depend on the grid size, so a capped grid (tuning)
+// computes every tile, and hence the result, exactly as the full one.
 TNSplit tn_split(int64_t rows, int ncols) {
     const int64_t ntn = ceil_div(ncols, TM);
     const int64_t target = 2 * (int64_t)num_sms();
@@ -637,6 +702,23 @@ TNSplit tn_split(int64_t rows, int ncols) {
 
 bool tc_available() { return encode_fn() != nullptr; }
 
+bool tc_make_map(CUtensorMap *map, const void *ptr, int esize, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                 int box_cols, bool swizzle) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    if ((reinterpret_cast<uintptr_t>(ptr) & 15) || ((ld * esize) & 15)) return false;
+    const CUtensorMapDataType dt = esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * esize)};
+    cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(map, dt, 2, const_cast<void *>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t tc_split_transpose(const float *Z, int64_t rows, int cols, int64_t ldz, int N, float *th, float *tl,
                                int64_t ldt, cudaStream_t s) {
     const int64_t total = (int64_t)N * ldt;
@@ -645,14 +727,15 @@ cudaError_t tc_split_transpose(const float *Z, int64_t rows, int cols, int64_t l
     return cudaGetLastError();
 }
 
-int tc_gemm_nn_grid(int64_t m) {
+int tc_gemm_nn_grid(int64_t m, int ctas) {
     const int64_t tiles = ceil_div(m, TM);
-    return (int)(tiles < num_sms() ? tiles : num_sms());
+    const int64_t cap = ctas > 0 && ctas < num_sms() ? ctas : num_sms();
+    return (int)(tiles < cap ? tiles : cap);
 }
 
 cudaError_t tc_gemm_nn(int64_t m, int n, int N, const float *A, int64_t lda, const float *Bth, const float *Btl,
                        int64_t ldb, float *Y, int64_t ldy, int *status, cudaStream_t s, const float *mu,
-                       double *ssq) {
+                       double *ssq, int ctas) {
     if (N % 16 || N < 16 || N > 128) return cudaErrorInvalidValue;
     if (mu && (reinterpret_cast<uintptr_t>(mu) & 15)) return cudaErrorInvalidValue;
     CUtensorMap ma, mbh, mbl;
@@ -660,14 +743,14 @@ cudaError_t tc_gemm_nn(int64_t m, int n, int N, const float *A, int64_t lda, con
         !make_map(&mbl, Btl, N, n, ldb, N, TBK, true))
         return cudaErrorInvalidValue;
     switch (N) {
-        case 16: return launch_nn<16>(ma, mbh, mbl, m, n, Y, ldy, status, mu, ssq, s);
-        case 32: return launch_nn<32>(ma, mbh, mbl, m, n, Y, ldy, status, mu, ssq, s);
-        case 48: return launch_nn<48>(ma, mbh, mbl, m, n, Y, ldy, status, mu, ssq, s);
-        case 64: return launch_nn<64>(ma, mbh, mbl, m, n, Y, ldy, status, mu, ssq, s);
-        case 80: return launch_nn<80>(ma, mbh, mbl, m, n, Y, ldy, status, mu, ssq, s);
-        case 96: return launch_nn<96>(ma, mbh, mbl, m, n, Y, ldy, status, mu, ssq, s);
-        case 112: return launch_nn<112>(ma, mbh, mbl, m, n, Y, ldy, status, mu, ssq, s);
-        case 128: return launch_nn<128>(ma, mbh, mbl, m, n, Y, ldy, status, mu, ssq, s);
+        case 16: return launch_nn<16>(ma, mbh, mbl, m, n, Y, ldy, status, mu, ssq, s, ctas);
+        case 32: return launch_nn<32>(ma, mbh, mbl, m, n, Y, ldy, status, mu, ssq, s, ctas);
+        case 48: return launch_nn<48>(ma, mbh, mbl, m, n, Y, ldy, status, mu, ssq, s, ctas);
+        case 64: return launch_nn<64>(ma, mbh, mbl, m, n, Y, ldy, status, mu, ssq, s, ctas);
+        case 80: return launch_nn<80>(ma, mbh, mbl, m, n, Y, ldy, status, mu, ssq, s, ctas);
+        case 96: return launch_nn<96>(ma, mbh, mbl, m, n, Y, ldy, status, mu, ssq, s, ctas);
+        case 112: return launch_nn<112>(ma, mbh, mbl, m, n, Y, ldy, status, mu, ssq, s, ctas);
+        case 128: return launch_nn<128>(ma, mbh, mbl, m, n, Y, ldy, status, mu, ssq, s, ctas);
     }
     return cudaErrorInvalidValue;
 }
@@ -679,7 +762,7 @@ int64_t tc_gemm_tn_partials(int64_t rows, int ncols, int N) {
 
 cudaError_t tc_gemm_tn(int64_t rows, int ncols, int N, const float *A, int64_t lda, const float *Q, int64_t ldq,
                        float *C, int64_t ldc, float *part, int64_t part_elems, int *status, cudaStream_t s,
-                       const float *mu) {
+                       const float *mu, int ctas) {
     if (N % 16 || N < 16 || N > 128) return cudaErrorInvalidValue;
     const TNSplit sp = tn_split(rows, ncols);
     if (part == nullptr || part_elems < (int64_t)sp.chunks * ncols * N) return cudaErrorInvalidValue;
@@ -688,14 +771,14 @@ cudaError_t tc_gemm_tn(int64_t rows, int ncols, int N, const float *A, int64_t l
         return cudaErrorInvalidValue;
     cudaError_t e = cudaErrorInvalidValue;
     switch (N) {
-        case 16: e = launch_tn<16>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s); break;
-        case 32: e = launch_tn<32>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s); break;
-        case 48: e = launch_tn<48>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s); break;
-        case 64: e = launch_tn<64>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s); break;
-        case 80: e = launch_tn<80>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s); break;
-        case 96: e = launch_tn<96>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s); break;
-        case 112: e = launch_tn<112>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s); break;
-        case 128: e = launch_tn<128>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s); break;
+        case 16: e = launch_tn<16>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s, ctas); break;
+        case 32: e = launch_tn<32>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s, ctas); break;
+        case 48: e = launch_tn<48>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s, ctas); break;
+        case 64: e = launch_tn<64>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s, ctas); break;
+        case 80: e = launch_tn<80>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s, ctas); break;
+        case 96: e = launch_tn<96>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s, ctas); break;
+        case 112: e = launch_tn<112>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s, ctas); break;
+        case 128: e = launch_tn<128>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s, ctas); break;
     }
     if (e != cudaSuccess) return e;
     const int64_t total = (int64_t)ncols * N;

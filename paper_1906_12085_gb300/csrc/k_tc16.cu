@@ -1,0 +1,468 @@
+// bfloat16 tall-skinny products of the precision form on tcgen05 (kind::f16,
+// float32 accumulation in tensor memory).  The stored bfloat16 matrix A is an
+// exact operand; the small operand is bfloat16 too: rounded from float32 for
+// the power-iteration products (only its span matters there), or split into
+// three bfloat16 terms whose sum carries the float32 value (the
+// Rayleigh-Ritz product, float32-accurate against the stored A).
+//
+//   tc16_gemm_nn : Y (m x N) = A (m x n) Z (n x N) - 1 c^T      (c: N floats or NULL)
+//                  A and Zt (Z transposed, N x n) are K-major: TMA boxes of 64
+//                  K elements (one 128-byte swizzled row) x rows.
+//   tc16_gemm_tn : C (n x N) = A^T (Q_1 + ... + Q_nb) - mu (1^T Q)  (mu, qsum optional)
+//                  A and Q are used as stored (row-major): both operands are
+//                  MN-major; split-K over row chunks into float32 partials that a
+//                  second kernel sums in chunk order.
+//
+// Both kernels are persistent and warp-specialised: warp 0 issues the TMA loads
+// of a ring of shared-memory stages, one thread of warp 1 issues the MMAs into
+// one of two TMEM accumulators, warps 2-5 drain the other accumulator.  Every
+// wait is bounded; a stalled pipeline sets ST_TIMEOUT instead of hanging.
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+#include "tc_ptx.cuh"
+
+namespace gbr {
+namespace {
+
+using namespace tc;
+
+constexpr int TM = 128;                  // MMA M
+constexpr int BK = 64;                   // bfloat16 K elements per stage (128 bytes)
+constexpr int THR = 192;                 // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int NEPI = 128;
+constexpr uint32_t A_ST = TM * 128;      // 16 KB: 128 rows (NN) or 2 MN atoms x 64 rows (TN)
+constexpr uint32_t TCOLS = 256;          // two accumulators of up to 128 float32 columns
+constexpr uint32_t ATOM_K = BK * 128;    // TN: bytes of one 64-element MN atom column over the stage's rows
+// TN: stages accumulated in one TMEM accumulator before it is drained and added (IEEE
+// float32) to the partial: the tensor core's accumulation error grows with the number of
+// accumulation steps, 4 stages (256 rows) bound it.
+constexpr int SUBK = 4;
+
+template <int S>
+struct Bars16 {
+    uint64_t full[S], empty[S];
+    uint64_t acc_full[2], acc_empty[2];
+    uint32_t tmem;
+    int abort_flag;
+};
+
+__device__ __forceinline__ bool wait16(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    if (*abort_flag) return false;
+    if (mbar_wait(bar, parity)) return true;
+    *abort_flag = 1;
+    return false;
+}
+
+constexpr int cmin(int a, int b) { return a < b ? a : b; }
+
+// ======================================================================= NN
+template <int N>
+struct NN16 {
+    static constexpr uint32_t B_ST = N * 128;
+    static constexpr uint32_t STAGE = A_ST + B_ST;
+    static constexpr int S = cmin(8, (int)((200 * 1024) / STAGE));
+    static constexpr uint32_t NEED = S * STAGE + 1024 + sizeof(Bars16<S>) + 64;
+    static constexpr uint32_t SMEM = NEED > 120 * 1024 ? NEED : 120 * 1024;  // one CTA per SM (owns TMEM)
+};
+
+template <int N>
+__global__ void __launch_bounds__(THR, 1)
+    tc16_nn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t m, int n,
+                   float *__restrict__ Y, int64_t ldy, const float *__restrict__ c, int *__restrict__ status) {
+    using C = NN16<N>;
+    constexpr int S = C::S;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *sA = base;
+    uint8_t *sB = sA + S * A_ST;
+    Bars16<S> *bar = reinterpret_cast<Bars16<S> *>(sB + S * C::B_ST);
+    volatile int *abort_flag = &bar->abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t ntiles = (m + TM - 1) / TM;
+    const int nkb = (n + BK - 1) / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; s++) {
+            mbar_init(&bar->full[s], 1);
+            mbar_init(&bar->empty[s], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&bar->acc_full[b], 1);
+            mbar_init(&bar->acc_empty[b], NEPI);
+        }
+        bar->abort_flag = 0;
+        mbar_fence_init();
+    }
+    if (warp == 1) tmem_alloc(&bar->tmem, TCOLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = bar->tmem;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            tma_prefetch_desc(&tmA);
+            tma_prefetch_desc(&tmB);
+            uint32_t g = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x)
+                for (int kb = 0; kb < nkb; kb++, g++) {
+                    const int s = g % S;
+                    if (!(ok = wait16(&bar->empty[s], ((g / S) & 1) ^ 1, abort_flag))) break;
+                    mbar_arrive_expect_tx(&bar->full[s], C::STAGE);
+                    tma_load_2d(sA + s * A_ST, &tmA, kb * BK, (int32_t)(t * TM), &bar->full[s]);
+                    tma_load_2d(sB + s * C::B_ST, &tmB, kb * BK, 0, &bar->full[s]);
+                }
+            for (uint32_t k = g > (uint32_t)S ? g - S : 0; k < g; k++) mbar_wait(&bar->full[k % S], (k / S) & 1);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(TM, N, false, false);
+            uint32_t g = 0, it = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x, it++) {
+                const uint32_t b = it & 1;
+                if (!(ok = wait16(&bar->acc_empty[b], ((it >> 1) & 1) ^ 1, abort_flag))) break;
+                tc_fence_after();
+                const uint32_t d = tmem + b * 128;
+                for (int kb = 0; kb < nkb; kb++, g++) {
+                    const int s = g % S;
+                    if (!(ok = wait16(&bar->full[s], (g / S) & 1, abort_flag))) break;
+                    tc_fence_after();
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; kk++)
+                        mma_bf16(d, sdesc_kmajor_sw128(sA + s * A_ST, kk * 32),
+                                 sdesc_kmajor_sw128(sB + s * C::B_ST, kk * 32), idesc, (kb | kk) ? 1u : 0u);
+                    mma_commit(&bar->empty[s]);
+                }
+                if (ok) mma_commit(&bar->acc_full[b]);
+            }
+        }
+    } else {
+        const int q = warp & 3;  // TMEM lane quarter of this warp
+        uint32_t it = 0;
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, it++) {
+            const uint32_t b = it & 1;
+            if (!wait16(&bar->acc_full[b], (it >> 1) & 1, abort_flag)) break;
+            tc_fence_after();
+            const int64_t row = t * TM + q * 32 + lane;
+#pragma unroll
+            for (int c0 = 0; c0 < N; c0 += 32) {
+                float v[32];
+                tmem_ld32(tmem + b * 128 + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+                if (row < m) {
+                    float *p = Y + row * ldy + c0;
+#pragma unroll
+                    for (int j = 0; j < 32; j++)
+                        if (c0 + j < N) p[j] = c ? v[j] - c[c0 + j] : v[j];
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&bar->acc_empty[b]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, TCOLS);
+    }
+    if (threadIdx.x == 0 && bar->abort_flag) atomicOr(status, (int)ST_TIMEOUT);
+}
+
+// ======================================================================= TN
+// Tile (chunk, column tile): D (128 columns of A x N) = sum over the chunk's rows
+// of A[r][c] Q_i[r][j].  Stage layout: A as two MN atoms (columns c0..c0+63 and
+// c0+64..c0+127) of 64 rows each; every Q_i as ceil(N/64) MN atoms of 64 rows.
+template <int N, int NB>
+struct TN16 {
+    static constexpr int NA = (N + 63) / 64;          // MN atoms of one Q operand loaded by TMA
+    // two atoms of room per operand whatever N: the MMA's reads of one operand then stay
+    // inside its own 16 KB under either assignment of the two descriptor strides
+    static constexpr uint32_t Q_ST = 2 * ATOM_K;
+    static constexpr uint32_t STAGE = A_ST + NB * Q_ST;
+    static constexpr int S = cmin(8, (int)((200 * 1024) / STAGE));
+    static constexpr uint32_t NEED = S * STAGE + 1024 + sizeof(Bars16<S>) + 64;
+    static constexpr uint32_t SMEM = NEED > 120 * 1024 ? NEED : 120 * 1024;
+};
+
+template <int N, int NB>
+__global__ void __launch_bounds__(THR, 1)
+    tc16_tn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmQ1,
+                   const __grid_constant__ CUtensorMap tmQ2, const __grid_constant__ CUtensorMap tmQ3, int64_t rows,
+                   int ncols, int64_t rpc, int nchunks, float *__restrict__ part, int *__restrict__ status) {
+    using C = TN16<N, NB>;
+    constexpr int S = C::S;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    Bars16<S> *bar = reinterpret_cast<Bars16<S> *>(base + S * C::STAGE);
+    volatile int *abort_flag = &bar->abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntn = (ncols + TM - 1) / TM;
+    const int64_t ntiles = (int64_t)ntn * nchunks;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; s++) {
+            mbar_init(&bar->full[s], 1);
+            mbar_init(&bar->empty[s], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&bar->acc_full[b], 1);
+            mbar_init(&bar->acc_empty[b], NEPI);
+        }
+        bar->abort_flag = 0;
+        mbar_fence_init();
+    }
+    if (warp == 1) tmem_alloc(&bar->tmem, TCOLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = bar->tmem;
+
+    auto tile = [&](int64_t t, int64_t &r0, int64_t &r1, int &c0) {
+        const int64_t chunk = t / ntn;
+        c0 = (int)(t % ntn) * TM;
+        r0 = chunk * rpc;
+        r1 = r0 + rpc < rows ? r0 + rpc : rows;
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            tma_prefetch_desc(&tmA);
+            tma_prefetch_desc(&tmQ1);
+            if (NB > 1) {
+                tma_prefetch_desc(&tmQ2);
+                tma_prefetch_desc(&tmQ3);
+            }
+            uint32_t g = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
+                int64_t r0, r1;
+                int c0;
+                tile(t, r0, r1, c0);
+                const int nkb = (int)((r1 - r0 + BK - 1) / BK);
+                for (int kb = 0; kb < nkb; kb++, g++) {
+                    const int s = g % S;
+                    if (!(ok = wait16(&bar->empty[s], ((g / S) & 1) ^ 1, abort_flag))) break;
+                    uint8_t *st = base + s * C::STAGE;
+                    const int32_t y = (int32_t)(r0 + kb * BK);
+                    mbar_arrive_expect_tx(&bar->full[s], A_ST + NB * C::NA * ATOM_K);  // bytes the boxes below bring
+                    tma_load_2d(st, &tmA, c0, y, &bar->full[s]);
+                    tma_load_2d(st + ATOM_K, &tmA, c0 + 64, y, &bar->full[s]);
+#pragma unroll
+                    for (int i = 0; i < NB; i++) {
+                        const CUtensorMap *mq = i == 0 ? &tmQ1 : i == 1 ? &tmQ2 : &tmQ3;
+#pragma unroll
+                        for (int a = 0; a < C::NA; a++)
+                            tma_load_2d(st + A_ST + i * C::Q_ST + a * ATOM_K, mq, a * 64, y, &bar->full[s]);
+                    }
+                }
+            }
+            for (uint32_t k = g > (uint32_t)S ? g - S : 0; k < g; k++) mbar_wait(&bar->full[k % S], (k / S) & 1);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(TM, N, true, true);
+            uint32_t g = 0, it = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
+                int64_t r0, r1;
+                int c0;
+                tile(t, r0, r1, c0);
+                const int nkb = (int)((r1 - r0 + BK - 1) / BK);
+                for (int k0 = 0; ok && k0 < nkb; k0 += SUBK, it++) {
+                    const int k1 = k0 + SUBK < nkb ? k0 + SUBK : nkb;
+                    const uint32_t b = it & 1;
+                    if (!(ok = wait16(&bar->acc_empty[b], ((it >> 1) & 1) ^ 1, abort_flag))) break;
+                    tc_fence_after();
+                    const uint32_t d = tmem + b * 128;
+                    for (int kb = k0; kb < k1; kb++, g++) {
+                        const int s = g % S;
+                        if (!(ok = wait16(&bar->full[s], (g / S) & 1, abort_flag))) break;
+                        tc_fence_after();
+                        const uint8_t *st = base + s * C::STAGE;
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; kk++) {  // 16 rows = two 8-row K atoms = 2048 bytes
+                            const uint64_t ad = sdesc_mn_sw128(st, kk * 2048, ATOM_K, 1024);
+#pragma unroll
+                            for (int i = 0; i < NB; i++)
+                                mma_bf16(d, ad, sdesc_mn_sw128(st + A_ST + i * C::Q_ST, kk * 2048, ATOM_K, 1024),
+                                         idesc, ((kb - k0) | kk | i) ? 1u : 0u);
+                        }
+                        mma_commit(&bar->empty[s]);
+                    }
+                    if (ok) mma_commit(&bar->acc_full[b]);
+                }
+            }
+        }
+    } else {
+        const int q = warp & 3;
+        uint32_t it = 0;
+        bool ok = true;
+        for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
+            int64_t r0, r1;
+            int c0;
+            tile(t, r0, r1, c0);
+            const int nkb = (int)((r1 - r0 + BK - 1) / BK);
+            const int64_t chunk = t / ntn;
+            const int cc = c0 + q * 32 + lane;
+            for (int k0 = 0; k0 < nkb; k0 += SUBK, it++) {
+                const uint32_t b = it & 1;
+                if (!(ok = wait16(&bar->acc_full[b], (it >> 1) & 1, abort_flag))) break;
+                tc_fence_after();
+#pragma unroll
+                for (int j0 = 0; j0 < N; j0 += 32) {
+                    float v[32];
+                    tmem_ld32(tmem + b * 128 + ((uint32_t)(q * 32) << 16) + (uint32_t)j0, v);
+                    if (cc < ncols) {
+                        float *p = part + (chunk * ncols + cc) * (int64_t)N + j0;
+#pragma unroll
+                        for (int j = 0; j < 32; j++)
+                            if (j0 + j < N) p[j] = k0 > 0 ? p[j] + v[j] : v[j];
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&bar->acc_empty[b]);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, TCOLS);
+    }
+    if (threadIdx.x == 0 && bar->abort_flag) atomicOr(status, (int)ST_TIMEOUT);
+}
+
+// out[c][j] = sum over chunks (in order) of part[chunk][c][j] - mu[c] qsum[j]; one thread per (c, j)
+__global__ void sum16_kernel(const float *__restrict__ part, int nchunks, int ncols, int N, float *__restrict__ out,
+                             int64_t ldo, const float *__restrict__ mu, const double *__restrict__ qsum) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)ncols * N) return;
+    const int c = (int)(idx / N), j = (int)(idx % N);
+    double s = 0.0;
+    for (int k = 0; k < nchunks; k++) s += (double)part[((int64_t)k * ncols + c) * N + j];
+    if (mu) s -= (double)mu[c] * qsum[j];
+    out[(int64_t)c * ldo + j] = (float)s;
+}
+
+int sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    }
+    return n;
+}
+
+struct Split16 {
+    int64_t rpc;
+    int chunks;
+};
+
+Split16 split16(int64_t rows, int ncols) {
+    const int64_t ntn = ceil_div(ncols, TM);
+    int64_t chunks = ceil_div(2 * (int64_t)sms(), ntn);
+    const int64_t maxc = ceil_div(rows, 4 * BK);
+    if (chunks > maxc) chunks = maxc;
+    if (chunks < 1) chunks = 1;
+    const int64_t rpc = round_up(ceil_div(rows, chunks), BK);
+    return {rpc, (int)ceil_div(rows, rpc)};
+}
+
+template <int N>
+cudaError_t launch16_nn(const CUtensorMap &a, const CUtensorMap &b, int64_t m, int n, float *Y, int64_t ldy,
+                        const float *c, int *status, cudaStream_t s) {
+    using C = NN16<N>;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(tc16_nn_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        attr = true;
+    }
+    const int64_t tiles = ceil_div(m, TM);
+    const int grid = (int)(tiles < sms() ? tiles : sms());
+    tc16_nn_kernel<N><<<grid, THR, C::SMEM, s>>>(a, b, m, n, Y, ldy, c, status);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <int N, int NB>
+cudaError_t launch16_tn(const CUtensorMap &a, const CUtensorMap *q, int64_t rows, int ncols, Split16 sp, float *part,
+                        int *status, cudaStream_t s) {
+    using C = TN16<N, NB>;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(tc16_tn_kernel<N, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        attr = true;
+    }
+    const int64_t tiles = ceil_div(ncols, TM) * sp.chunks;
+    const int grid = (int)(tiles < sms() ? tiles : sms());
+    tc16_tn_kernel<N, NB><<<grid, THR, C::SMEM, s>>>(a, q[0], q[1], q[2], rows, ncols, sp.rpc, sp.chunks, part, status);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t tc16_gemm_nn(int64_t m, int n, int N, const void *A, int64_t lda, const void *Zt, int64_t ldz, float *Y,
+                         int64_t ldy, const float *c, int *status, cudaStream_t s) {
+    if (N % 16 || N < 16 || N > 128) return cudaErrorInvalidValue;
+    CUtensorMap ma, mb;
+    if (!tc_make_map(&ma, A, 2, m, n, lda, TM, BK, true) || !tc_make_map(&mb, Zt, 2, N, n, ldz, N, BK, true))
+        return cudaErrorInvalidValue;
+    switch (N) {
+        case 16: return launch16_nn<16>(ma, mb, m, n, Y, ldy, c, status, s);
+        case 32: return launch16_nn<32>(ma, mb, m, n, Y, ldy, c, status, s);
+        case 48: return launch16_nn<48>(ma, mb, m, n, Y, ldy, c, status, s);
+        case 64: return launch16_nn<64>(ma, mb, m, n, Y, ldy, c, status, s);
+        case 80: return launch16_nn<80>(ma, mb, m, n, Y, ldy, c, status, s);
+        case 96: return launch16_nn<96>(ma, mb, m, n, Y, ldy, c, status, s);
+        case 112: return launch16_nn<112>(ma, mb, m, n, Y, ldy, c, status, s);
+        case 128: return launch16_nn<128>(ma, mb, m, n, Y, ldy, c, status, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+int64_t tc16_gemm_tn_partials(int64_t rows, int ncols, int N) {
+    const Split16 sp = split16(rows, ncols);
+    return (int64_t)sp.chunks * ncols * N;
+}
+
+cudaError_t tc16_gemm_tn(int64_t rows, int ncols, int N, const void *A, int64_t lda, const void *const *Q, int nq,
+                         int64_t ldq, float *C, int64_t ldc, float *part, int64_t part_elems, const float *mu,
+                         const double *qsum, int *status, cudaStream_t s) {
+    if (N % 16 || N < 16 || N > 128 || (nq != 1 && nq != 3)) return cudaErrorInvalidValue;
+    const Split16 sp = split16(rows, ncols);
+    if (!part || part_elems < (int64_t)sp.chunks * ncols * N) return cudaErrorInvalidValue;
+    CUtensorMap ma, mq[3];
+    if (!tc_make_map(&ma, A, 2, rows, ncols, lda, BK, 64, true)) return cudaErrorInvalidValue;
+    for (int i = 0; i < 3; i++)
+        if (!tc_make_map(&mq[i], Q[i < nq ? i : 0], 2, rows, N, ldq, BK, 64, true)) return cudaErrorInvalidValue;
+    cudaError_t e = cudaErrorInvalidValue;
+#define TN16_CASE(NN)                                                                                   \
+    case NN:                                                                                            \
+        e = nq == 1 ? launch16_tn<NN, 1>(ma, mq, rows, ncols, sp, part, status, s)                      \
+                    : launch16_tn<NN, 3>(ma, mq, rows, ncols, sp, part, status, s);                     \
+        break;
+    switch (N) {
+        TN16_CASE(16)
+        TN16_CASE(32)
+        TN16_CASE(48)
+        TN16_CASE(64)
+        TN16_CASE(80)
+        TN16_CASE(96)
+        TN16_CASE(112)
+        TN16_CASE(128)
+    }
+#undef TN16_CASE
+    if (e != cudaSuccess) return e;
+    const int64_t total = (int64_t)ncols * N;
+    sum16_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, s>>>(part, sp.chunks, ncols, N, C, ldc, mu, qsum);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace gbr

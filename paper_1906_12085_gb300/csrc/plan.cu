@@ -7,8 +7,12 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -49,6 +53,7 @@ struct rsvd_plan {
     int last_count = 0;
     // tensor-core path (float32): transposed tf32 split of the small operand, split-K partials
     bool tc = false;
+    int nn_ctas = 0, tn_ctas = 0;  // work decomposition of the products (0: defaults; see rsvd_autotune)
     int64_t ldt = 0;          // leading dimension of Bth / Btl (>= max(n, wide), multiple of 4)
     float *Bth = nullptr, *Btl = nullptr;
     float *tcpart = nullptr;
@@ -204,8 +209,8 @@ cudaError_t prod_nn(rsvd_plan *P, int64_t rows, int64_t K, const T *X, int64_t l
             cudaError_t e = tc_split_transpose(B, K, P->lp, ldb, P->lp, P->Bth, P->Btl, P->ldt, P->stream);
             if (e == cudaSuccess)
                 e = tc_gemm_nn(rows, (int)K, P->lp, X, ldx, P->Bth, P->Btl, P->ldt, Y, ldy, P->status, P->stream, mu,
-                               fro2 ? P->ssq : nullptr);
-            if (e == cudaSuccess && fro2) e = sum_f64(P->ssq, tc_gemm_nn_grid(rows), fro2, P->stream);
+                               fro2 ? P->ssq : nullptr, P->nn_ctas);
+            if (e == cudaSuccess && fro2) e = sum_f64(P->ssq, tc_gemm_nn_grid(rows, P->nn_ctas), fro2, P->stream);
             if (e != cudaErrorInvalidValue) return e;
             cudaGetLastError();
         }
@@ -228,7 +233,7 @@ cudaError_t prod_tn(rsvd_plan *P, int64_t rows, int64_t ncols, const T *X, int64
         if (P->tc && al16(X, ldx, 4) && al16(Q, ldq, 4) &&
             tc_gemm_tn_partials(rows, (int)ncols, P->lp) <= P->tcpart_elems) {
             cudaError_t e = tc_gemm_tn(rows, (int)ncols, P->lp, X, ldx, Q, ldq, C, ldc, P->tcpart, P->tcpart_elems,
-                                       P->status, P->stream, mu);
+                                       P->status, P->stream, mu, P->tn_ctas);
             if (e != cudaErrorInvalidValue) return e;
             cudaGetLastError();
         }
@@ -721,6 +726,23 @@ rsvd_status status_from_bits(int st) {
     return RSVD_OK;
 }
 
+// Process-wide table of tuned product decompositions (rsvd_autotune), keyed by
+// (ceil(log2 m), n, lp).
+struct TuneKey {
+    int lgm;
+    int64_t n;
+    int lp;
+    bool operator<(const TuneKey &o) const { return std::tie(lgm, n, lp) < std::tie(o.lgm, o.n, o.lp); }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune;
+
+TuneKey tune_key(int64_t m, int64_t n, int lp) {
+    int b = 0;
+    while (b < 62 && ((int64_t)1 << b) < m) b++;
+    return {b, n, lp};
+}
+
 // Validates the sizes and fills the plan's shape fields and workspace size.
 rsvd_status plan_init(rsvd_plan *P, int64_t m, int64_t n, int k, int p, int q, rsvd_dtype dtype, void *cuda_stream) {
     if (m < 1 || n < 1 || m < n || k < 1 || p < 0 || q < 0) return RSVD_ERR_ARG;
@@ -739,6 +761,14 @@ rsvd_status plan_init(rsvd_plan *P, int64_t m, int64_t n, int k, int p, int q, r
     P->dtype = dtype;
     P->stream = (cudaStream_t)cuda_stream;
     P->tc = dtype == RSVD_F32 && P->lp <= 128 && tc_available();
+    if (P->tc) {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune.find(tune_key(m, n, P->lp));
+        if (it != g_tune.end()) {
+            P->nn_ctas = it->second.first;
+            P->tn_ctas = it->second.second;
+        }
+    }
     Carver c;
     carve(P, c);
     P->ws_bytes = c.off;
@@ -1039,6 +1069,105 @@ rsvd_status rsvd_batch_destroy(rsvd_batch_t B) {
     if (B->graph) cudaGraphExecDestroy(B->graph);
     delete B;
     return RSVD_OK;
+}
+
+rsvd_status rsvd_autotune(rsvd_plan_t P, void *A, const void *Omega, int concurrency, int *nn_out, int *tn_out) {
+    if (!P || !A || !Omega || concurrency < 1 || concurrency > 64) return RSVD_ERR_ARG;
+    if (nn_out) *nn_out = P->nn_ctas;
+    if (tn_out) *tn_out = P->tn_ctas;
+    if (P->dtype != RSVD_F32 || !P->tc) return RSVD_OK;  // nothing to tune on the CUDA-core path
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return RSVD_ERR_CUDA;
+    const int cand[][2] = {{0, 0}, {sms / 2, sms / 2}, {sms / 4, sms / 4}, {sms / 2, 0}, {0, sms / 2}};
+    const int ncand = (int)(sizeof(cand) / sizeof(cand[0]));
+    rsvd_status st = RSVD_OK;
+    std::vector<rsvd_plan *> plans{P};
+    std::vector<cudaStream_t> streams;
+    cudaStream_t bs = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    char *out = nullptr;
+    const size_t sb = round_up(sizeof(double) * P->k, 256), ub = round_up(sizeof(float) * P->m * P->k, 256),
+                 vb = round_up(sizeof(float) * P->n * P->k, 256);
+    std::vector<void *> Av(concurrency, A), Ov(concurrency, const_cast<void *>(Omega)), Uv, Vv;
+    std::vector<double *> Sv;
+    float best_ms = 3.4e38f;
+    int best = 0;
+    {
+        BatchCtx ctx;
+        bool ok = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess &&
+                  cudaMalloc(&out, (sb + ub + vb) * concurrency) == cudaSuccess;
+        for (int i = 1; ok && i < concurrency; i++) {
+            cudaStream_t x = nullptr;
+            rsvd_plan_t Q = nullptr;
+            ok = cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) == cudaSuccess;
+            if (ok) streams.push_back(x);
+            ok = ok && rsvd_plan_create(&Q, P->m, P->n, P->k, P->p, P->q, P->dtype, x) == RSVD_OK;
+            if (ok) plans.push_back(Q);
+        }
+        ctx.bs = bs;
+        ok = ok && ctx.reserve(concurrency) == cudaSuccess;
+        for (int i = 0; ok && i < concurrency; i++) {
+            char *b = out + (sb + ub + vb) * i;
+            Sv.push_back((double *)b);
+            Uv.push_back(b + sb);
+            Vv.push_back(b + sb + ub);
+        }
+        for (int c = 0; ok && c < ncand; c++) {
+            for (rsvd_plan *X : plans) {
+                X->nn_ctas = cand[c][0];
+                X->tn_ctas = cand[c][1];
+            }
+            float ms[3];
+            for (int r = 0; ok && r < 4; r++) {  // one warm-up, three timed
+                ok = cudaEventRecord(e0, bs) == cudaSuccess &&
+                     batch_direct(ctx, concurrency, plans.data(), Av.data(), (const void *const *)Ov.data(),
+                                  Sv.data(), Uv.data(), Vv.data()) == RSVD_OK &&
+                     cudaEventRecord(e1, bs) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+                if (ok && r > 0) ok = cudaEventElapsedTime(&ms[r - 1], e0, e1) == cudaSuccess;
+            }
+            if (!ok) break;
+            std::sort(ms, ms + 3);
+            if (ms[1] < best_ms) {
+                best_ms = ms[1];
+                best = c;
+            }
+        }
+        if (!ok) st = RSVD_ERR_CUDA;
+        for (size_t i = 1; i < plans.size(); i++) rsvd_plan_destroy(plans[i]);
+    }
+    for (cudaStream_t x : streams) cudaStreamDestroy(x);
+    if (bs) cudaStreamDestroy(bs);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (out) cudaFree(out);
+    cudaMemsetAsync(P->status, 0, sizeof(int), P->stream);
+    P->nn_ctas = cand[best][0];
+    P->tn_ctas = cand[best][1];
+    if (st == RSVD_OK) {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune[tune_key(P->m, P->n, P->lp)] = {P->nn_ctas, P->tn_ctas};
+    }
+    if (nn_out) *nn_out = P->nn_ctas;
+    if (tn_out) *tn_out = P->tn_ctas;
+    P->last_count = 0;
+    return st;
+}
+
+rsvd_status rsvd_tune_lookup(int64_t m, int64_t n, int k, int p, int *nn_ctas, int *tn_ctas) {
+    if (m < 1 || n < 1 || k < 1 || p < 0) return RSVD_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(tune_key(m, n, (int)round_up(k + p, 16)));
+    if (it == g_tune.end()) return RSVD_ERR_ARG;
+    if (nn_ctas) *nn_ctas = it->second.first;
+    if (tn_ctas) *tn_ctas = it->second.second;
+    return RSVD_OK;
+}
+
+void rsvd_tune_clear(void) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune.clear();
 }
 
 rsvd_status svd_exact(rsvd_plan_t P, void *A, int method, double *S, void *U, void *V) {

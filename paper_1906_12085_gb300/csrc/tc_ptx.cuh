@@ -111,6 +111,43 @@ __device__ __forceinline__ uint64_t sdesc_kmajor_sw128(const void *base, uint32_
     return d;
 }
 
+// MN-major operand, 128-byte swizzle: each K row holds 64 consecutive 16-bit MN
+// elements (128 bytes), 8 K rows form a 1024-byte atom; sbo = bytes between
+// K-adjacent atoms, lbo = bytes between MN-adjacent atoms (64 elements apart).
+__device__ __forceinline__ uint64_t sdesc_mn_sw128(const void *base, uint32_t byte_off, uint32_t lbo, uint32_t sbo) {
+    const uint32_t a = smem_addr(base) + byte_off;
+    uint64_t d = 0;
+    d |= (uint64_t)((a & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor of kind::f16: D f32, A and B bf16, shape M x N; a_mn / b_mn
+// select MN-major (transposed) operands.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn, bool b_mn) {
+    return (1u << 4)                       // D format: f32
+           | (1u << 7)                     // A format: bf16
+           | (1u << 10)                    // B format: bf16
+           | (a_mn ? (1u << 15) : 0u)      // A MN-major
+           | (b_mn ? (1u << 16) : 0u)      // B MN-major
+           | ((uint32_t)(N >> 3) << 17)
+           | ((uint32_t)(M >> 4) << 24);
+}
+
+// D[tmem] (+)= A[smem] * B[smem]  (one MMA of shape M x N x 16, bf16 operands)
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 // Instruction descriptor: D f32, A and B tf32, both K-major, shape M x N.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
     return (1u << 4)                       // D format: f32
@@ -163,6 +200,21 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
 }
 
 // Load 32 consecutive fp32 columns of this warp's 32 TMEM lanes (one lane per thread).
+// 16 consecutive 32-bit columns of this warp's 32 TMEM lanes (one lane per thread).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
     uint32_t r[32];
     asm volatile(
@@ -185,4 +237,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
 }  // namespace tc
+
+// Row-major matrix rows x cols (ld elements of esize bytes: 4 float32, 2 bfloat16,
+// 1 byte) as a 2-D TMA map with a box of box_rows x box_cols, 128-byte swizzle or
+// none; out-of-range elements read as zero.  False when the pointer or the row
+// pitch is not 16-byte aligned or the encoder is unavailable.
+bool tc_make_map(CUtensorMap *map, const void *ptr, int esize, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                 int box_cols, bool swizzle);
 }  // namespace gbr

@@ -164,11 +164,26 @@ def main(argv=None) -> int:
     ap.add_argument("--max-batch", type=int, default=8)
     ap.add_argument("--max-inflight", type=int, default=8)
     ap.add_argument("--seed", type=int, default=7)
+    ap.add_argument("--autotune", action="store_true",
+                    help="tune the product decomposition of every (ceil log2 m, n, l) bucket the stream hits first")
     a = ap.parse_args(argv)
     dev = torch.device("cuda")
     from paper_1906_12085_gb300 import build
     build.build()
     mats, alphas, omegas = make_pool(a.pool, dev)
+    if a.autotune:
+        t0 = time.perf_counter()
+        seen = {}
+        for rate in [float(x) for x in a.rates.split(",")]:
+            for r in make_requests(a.requests, rate, a.pool, a.seed):
+                lgm = int(np.ceil(np.log2(r["m"])))
+                seen.setdefault((lgm, r["n"], -(-(r["k"] + r["p"]) // 16)), r)
+        for r in seen.values():
+            A = mats[r["n"]][r["j"]][: r["m"]]
+            Om = omegas[(r["n"], r["k"] + r["p"])]
+            with g.rsvd_plan_create(r["m"], r["n"], r["k"], r["p"], Q, g.RSVD_F32) as plan:
+                g.check(g.rsvd_autotune(plan, A, Om, concurrency=4)[0], "rsvd_autotune")
+        print(json.dumps({"autotuned_buckets": len(seen), "seconds": time.perf_counter() - t0}), flush=True)
     warm = make_requests(64, 1e6, a.pool, a.seed + 1)   # warm-up: kernels loaded, allocator primed
     if a.mode == "server":
         run_server(warm, mats, omegas, dev, int(a.budget_gb * 2**30), a.max_batch, a.max_inflight)

@@ -97,3 +97,12 @@ def test_batch_and_server_argument_errors():
     assert L.rsvd_server_poll(None, None, 0) == g.RSVD_ERR_ARG
     assert L.rsvd_server_pending(None) == 0
     assert L.rsvd_server_destroy(None) == g.RSVD_OK
+
+
+def test_autotune_argument_errors():
+    L = g.lib()
+    a, b = ctypes.c_int(7), ctypes.c_int(7)
+    assert L.rsvd_autotune(None, None, None, 1, ctypes.byref(a), ctypes.byref(b)) == g.RSVD_ERR_ARG
+    g.rsvd_tune_clear()
+    assert g.rsvd_tune_lookup(1000, 64, 8, 8)[0] == g.RSVD_ERR_ARG
+    assert g.rsvd_tune_lookup(0, 64, 8, 8)[0] == g.RSVD_ERR_ARG

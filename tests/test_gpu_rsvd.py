@@ -176,3 +176,39 @@ def test_rsvd_repeatable_bitwise():
     r1 = _run_rsvd(A0, Om, k, p, 2, g.RSVD_F32)
     r2 = _run_rsvd(A0, Om, k, p, 2, g.RSVD_F32)
     assert np.array_equal(r1["S"], r2["S"]) and np.array_equal(r1["U"], r2["U"])
+
+
+@pytest.mark.slow
+def test_rsvd_f32_full_workload_matches_oracle():
+    """The benchmark's workload at full size (200000 x 1000, k = 50, p = 10, q = 2),
+    solved as bench.py times it (captured graph on a user stream), against the FP64
+    oracle on the same stored float32 matrix and Omega."""
+    dev = torch.device("cuda")
+    A64, sigma, ex = synth.workload("rpca_fp32_200000x1000", device=dev)
+    A = A64.float().contiguous()
+    del A64
+    Om = ex["omega"].to(dev).contiguous()
+    m, n = A.shape
+    k, p, q = 50, 10, 2
+    S = torch.zeros(k, dtype=torch.float64, device=dev)
+    U = torch.zeros(m, k, device=dev)
+    V = torch.zeros(n, k, device=dev)
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()                       # inputs were made on the default stream
+    with torch.cuda.stream(stream):
+        with g.rsvd_plan_create(m, n, k, p, q, g.RSVD_F32, stream) as plan:
+            for _ in range(2):                     # capture, then replay
+                g.check(g.rsvd(plan, A, None, Om, S, U, V))
+            assert g.rsvd_plan_sync(plan) == g.RSVD_OK
+            stK, K = g.pca_threshold(plan, 0.9)
+    torch.cuda.synchronize()
+    Ah = A.cpu().double().numpy()
+    Ac, mu, fro2 = oracle.center(Ah)
+    s, Uo, Vo = oracle.rsvd(Ac, Om.cpu().double(), q=q, k=k)
+    Sg = S.cpu().numpy()
+    assert np.abs(Sg - s).max() <= 1e-5 * s[0]
+    Vg = V.cpu().double().numpy()
+    assert np.abs(Vg.T @ Vg - np.eye(k)).max() <= 1e-5
+    sep = _gaps(s) >= 2e-2
+    assert np.abs(Vg[:, sep] - Vo[:, sep]).max() <= 2e-3
+    assert K == oracle.pca_threshold(s, fro2, 0.9)[0]
