@@ -18,6 +18,8 @@
  * - Element types follow the plan's dtype:
  *     RSVD_F64 : A, Omega, U, V are double;
  *     RSVD_F32 : A, Omega, U, V are float;
+ *     RSVD_BF16: A holds bfloat16 codes (2 bytes, e.g. from rsvd_quantize);
+ *                Omega, U, V are float;
  *   singular values S are always double.
  * - Outputs are sorted by descending singular value.  Sign convention: the
  *   largest-magnitude entry of every right singular vector v_i is positive
@@ -43,7 +45,7 @@ extern "C" {
 typedef enum {
     RSVD_F64 = 0,      /* float64 storage and arithmetic                       */
     RSVD_F32 = 1,      /* float32 storage, float32 products with float32 sums   */
-    RSVD_BF16 = 2,     /* reserved: bfloat16 storage (precision form)           */
+    RSVD_BF16 = 2,     /* bfloat16 storage of A (precision form, rsvd only)     */
     RSVD_FP8_E4M3 = 3  /* reserved: e4m3 storage with per-column scales         */
 } rsvd_dtype;
 
@@ -106,7 +108,14 @@ rsvd_status rsvd_plan_sync(rsvd_plan_t plan);
  * orth() is CholeskyQR2 (R_ii > 0), which in exact arithmetic equals the
  * Householder QR the step list names.
  *   A      : m x n, row-major, read only (centred on the fly).
- *   col_scales : must be NULL for RSVD_F32 / RSVD_F64 (reserved for e4m3).
+ *   col_scales : must be NULL (reserved for e4m3).
+ * RSVD_BF16 plans (n a multiple of 8, l <= 112) solve for the stored bfloat16
+ * matrix exactly as given: the products with A run on the tensor cores with
+ * float32 accumulation, the small operand of the sketch and power products
+ * rounded to bfloat16 and the basis of T = A^T Q split into three bfloat16
+ * terms (float32-accurate); the column means enter as exact rank-1
+ * corrections; CholeskyQR's Cholesky and the SVD of R run in float64.
+ * svd_exact, svd_truncated_krylov and batches take RSVD_F32 / RSVD_F64 plans.
  *   Omega  : n x l Gaussian test matrix (caller-drawn), row-major.
  *   S      : k doubles; U : m x k; V : n x k (row-major).
  */

@@ -99,6 +99,30 @@ cudaError_t jacobi_osvd(const double *R, int l, int lp, double *sig, To *UR, To 
 template <typename To>
 cudaError_t sv_refine(const double *R, int l, int lp, const To *UR, const To *W, double *sig, cudaStream_t s);
 
+// ------------------------------------------------------ bfloat16 precision form
+// Y (m x N) = A Z - 1 c^T with A m x n bfloat16 (lda), Z given as Zt (N x n
+// bfloat16, ldz); c (N floats) may be NULL.  n, lda, ldz multiples of 8.
+cudaError_t tc16_gemm_nn(int64_t m, int n, int N, const void *A, int64_t lda, const void *Zt, int64_t ldz, float *Y,
+                         int64_t ldy, const float *c, int *status, cudaStream_t s);
+// C (ncols x N) = A^T (Q_1 + .. + Q_nq) - mu qsum^T with A rows x ncols bfloat16 and
+// nq (1 or 3) bfloat16 terms Q_i rows x N (ldq); mu (ncols floats) / qsum (N doubles)
+// optional.  part: tc16_gemm_tn_partials floats.
+int64_t tc16_gemm_tn_partials(int64_t rows, int ncols, int N);
+cudaError_t tc16_gemm_tn(int64_t rows, int ncols, int N, const void *A, int64_t lda, const void *const *Q, int nq,
+                         int64_t ldq, float *C, int64_t ldc, float *part, int64_t part_elems, const float *mu,
+                         const double *qsum, int *status, cudaStream_t s);
+// column statistics of a bfloat16 matrix (psum / psq: colstats16_chunks(m) x n doubles, colv: n doubles)
+int64_t colstats16_chunks(int64_t m);
+cudaError_t colstats16(const void *A, int64_t m, int64_t n, int64_t lda, bool center, double *mu, float *mu_f,
+                       double *fro2, double *psum, double *psq, double *colv, cudaStream_t s);
+// Zt = round(Z)^T padded to lp rows; c = mu^T Zt^T (when mu and c are given)
+cudaError_t to_bf16_t(const float *Z, int64_t n, int l, int64_t ldzin, int lp, void *Zt, int64_t ldz,
+                      const double *mu, float *c, cudaStream_t s);
+// Q -> nq (1 or 3) bfloat16 terms and their column sums qsum (part: split_bf16_chunks(rows) x lp doubles)
+int64_t split_bf16_chunks(int64_t rows);
+cudaError_t split_bf16(const float *Q, int64_t rows, int lp, int nq, void *Q1, void *Q2, void *Q3, double *part,
+                       double *qsum, cudaStream_t s);
+
 // Serving interface of plan.cu (used by server.cu): a batch context on stream bs
 // for up to `cap` problems, and one launch of a float32 batch followed, per
 // problem, by the Sec. 2.4 K selection and an asynchronous copy of three ints

@@ -1,0 +1,186 @@
+// Element-wise and reduction kernels of the bfloat16 precision form (the
+// products themselves are in k_tc16.cu):
+//   colstats16 : column means mu of the stored bfloat16 matrix and
+//                ||A - 1 mu^T||_F^2 = sum_j (sum_i a_ij^2 - m mu_j^2), float64
+//                accumulation in a fixed order;
+//   to_bf16_t  : Zt (lp x n bfloat16) = round(Z)^T, rows l..lp-1 zero, and the
+//                mean correction c = mu^T round(Z) of the sketch / power products;
+//   split_bf16 : Q (m x lp float32) -> one bfloat16 term, or three whose sum
+//                carries Q to float32 accuracy (hi = round(Q), mid = round(Q - hi),
+//                lo = round(Q - hi - mid), each difference exact in float32), and
+//                the column sums of the terms (float64) for the mean correction.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace gbr {
+namespace {
+
+__device__ __forceinline__ float bf(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
+__device__ __forceinline__ uint16_t rbf(float x) {
+    return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+
+// partial column sums / sums of squares over row chunks: 32 columns x 8 row groups per block
+__global__ void colstats16_kernel(const uint16_t *__restrict__ A, int64_t m, int64_t n, int64_t lda, int64_t rpb,
+                                  double *__restrict__ psum, double *__restrict__ psq) {
+    __shared__ double rs[8][33], rq[8][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t c = (int64_t)blockIdx.x * 32 + tx;
+    const int64_t r0 = (int64_t)blockIdx.y * rpb, r1 = min(m, r0 + rpb);
+    double s = 0.0, q = 0.0;
+    if (c < n) {
+        for (int64_t g = r0 + ty * 32; g < r1; g += 8 * 32) {  // 32-row groups in float32, then float64
+            float fs = 0.f, fq = 0.f;
+            const int64_t ge = min(r1, g + 32);
+            for (int64_t r = g; r < ge; r++) {
+                const float a = bf(A[r * lda + c]);
+                fs += a;
+                fq = fmaf(a, a, fq);
+            }
+            s += fs;
+            q += fq;
+        }
+    }
+    rs[ty][tx] = s;
+    rq[ty][tx] = q;
+    __syncthreads();
+    if (ty == 0 && c < n) {
+        for (int k = 1; k < 8; k++) {
+            s += rs[k][tx];
+            q += rq[k][tx];
+        }
+        psum[(int64_t)blockIdx.y * n + c] = s;
+        psq[(int64_t)blockIdx.y * n + c] = q;
+    }
+}
+
+// mu_j, float copy, and colv_j = sum_i a_ij^2 - m mu_j^2 (chunks summed in order)
+__global__ void colstats16_finish(const double *__restrict__ psum, const double *__restrict__ psq, int nch,
+                                  int64_t m, int64_t n, bool center, double *__restrict__ mu, float *__restrict__ mu_f,
+                                  double *__restrict__ colv) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    double s = 0.0, q = 0.0;
+    for (int k = 0; k < nch; k++) {
+        s += psum[(int64_t)k * n + c];
+        q += psq[(int64_t)k * n + c];
+    }
+    const double mj = center ? s / (double)m : 0.0;  // without centring: mu = 0, ||A||_F^2
+    mu[c] = mj;
+    mu_f[c] = (float)mj;
+    colv[c] = q - (double)m * mj * mj;
+}
+
+// Zt[j][i] = round(Z[i][j]) for j < l, 0 for l <= j < lp (i < n; ldz >= n)
+__global__ void to_bf16_t_kernel(const float *__restrict__ Z, int64_t n, int l, int64_t ldzin, int lp,
+                                 uint16_t *__restrict__ Zt, int64_t ldz) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)lp * n) return;
+    const int j = (int)(idx / n);
+    const int64_t i = idx % n;
+    Zt[(int64_t)j * ldz + i] = j < l ? rbf(Z[i * ldzin + j]) : (uint16_t)0;
+}
+
+// c[j] = sum_i mu_i Zt[j][i] (float64, fixed order), one warp per j
+__global__ void mean_corr_kernel(const double *__restrict__ mu, const uint16_t *__restrict__ Zt, int64_t n,
+                                 int64_t ldz, int lp, float *__restrict__ c) {
+    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (j >= lp) return;
+    double s = 0.0;
+    for (int64_t i = lane; i < n; i += 32) s += mu[i] * (double)bf(Zt[(int64_t)j * ldz + i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) c[j] = (float)s;
+}
+
+// Q (rows x lp) -> nq bfloat16 terms; per row chunk the column sums of the terms
+__global__ void split_bf16_kernel(const float *__restrict__ Q, int64_t rows, int lp, int nq, uint16_t *__restrict__ Q1,
+                                  uint16_t *__restrict__ Q2, uint16_t *__restrict__ Q3, int64_t rpb,
+                                  double *__restrict__ part) {
+    __shared__ double red[2][128];
+    const int j = threadIdx.x & 127, ry = threadIdx.x >> 7;  // 128 columns x 2 row groups (256 threads)
+    const int64_t r0 = (int64_t)blockIdx.x * rpb, r1 = min(rows, r0 + rpb);
+    double s = 0.0;
+    if (j < lp) {
+        for (int64_t r = r0 + ry; r < r1; r += 2) {
+            const float x = Q[r * lp + j];
+            const uint16_t h = rbf(x);
+            float sum = bf(h);
+            Q1[r * lp + j] = h;
+            if (nq == 3) {
+                const float d1 = x - bf(h);          // exact
+                const uint16_t mid = rbf(d1);
+                const float d2 = d1 - bf(mid);       // exact
+                const uint16_t lo = rbf(d2);
+                Q2[r * lp + j] = mid;
+                Q3[r * lp + j] = lo;
+                s += (double)sum + (double)bf(mid) + (double)bf(lo);
+            } else {
+                s += (double)sum;
+            }
+        }
+    }
+    red[ry][j] = s;
+    __syncthreads();
+    if (ry == 0 && j < lp) part[(int64_t)blockIdx.x * lp + j] = red[0][j] + red[1][j];
+}
+
+// qsum[j] = sum over chunks (in order)
+__global__ void sum_rows_kernel(const double *__restrict__ part, int nch, int lp, double *__restrict__ qsum) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= lp) return;
+    double s = 0.0;
+    for (int k = 0; k < nch; k++) s += part[(int64_t)k * lp + j];
+    qsum[j] = s;
+}
+
+}  // namespace
+
+int64_t colstats16_chunks(int64_t m) { return ceil_div(m, 4096) < 1024 ? ceil_div(m, 4096) : 1024; }
+
+cudaError_t colstats16(const void *A, int64_t m, int64_t n, int64_t lda, bool center, double *mu, float *mu_f,
+                       double *fro2, double *psum, double *psq, double *colv, cudaStream_t s) {
+    const int64_t nch = colstats16_chunks(m);
+    const int64_t rpb = round_up(ceil_div(m, nch), 32);
+    const int64_t ch = ceil_div(m, rpb);
+    colstats16_kernel<<<dim3((unsigned)ceil_div(n, 32), (unsigned)ch), 256, 0, s>>>(
+        static_cast<const uint16_t *>(A), m, n, lda, rpb, psum, psq);
+    colstats16_finish<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(psum, psq, (int)ch, m, n, center, mu, mu_f, colv);
+    note_launch(2);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return sum_f64(colv, n, fro2, s);
+}
+
+cudaError_t to_bf16_t(const float *Z, int64_t n, int l, int64_t ldzin, int lp, void *Zt, int64_t ldz,
+                      const double *mu, float *c, cudaStream_t s) {
+    const int64_t total = (int64_t)lp * n;
+    to_bf16_t_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, s>>>(Z, n, l, ldzin, lp, static_cast<uint16_t *>(Zt),
+                                                                    ldz);
+    note_launch();
+    if (mu && c) {
+        mean_corr_kernel<<<(unsigned)ceil_div(lp, 8), 256, 0, s>>>(mu, static_cast<const uint16_t *>(Zt), n, ldz, lp,
+                                                                    c);
+        note_launch();
+    }
+    return cudaGetLastError();
+}
+
+int64_t split_bf16_chunks(int64_t rows) { return ceil_div(rows, 2048); }
+
+cudaError_t split_bf16(const float *Q, int64_t rows, int lp, int nq, void *Q1, void *Q2, void *Q3, double *part,
+                       double *qsum, cudaStream_t s) {
+    if (lp > 128) return cudaErrorInvalidValue;
+    const int64_t rpb = 2048;
+    const int64_t nch = ceil_div(rows, rpb);
+    split_bf16_kernel<<<(unsigned)nch, 256, 0, s>>>(Q, rows, lp, nq, static_cast<uint16_t *>(Q1),
+                                                    static_cast<uint16_t *>(Q2), static_cast<uint16_t *>(Q3), rpb,
+                                                    part);
+    sum_rows_kernel<<<(unsigned)ceil_div(lp, 128), 128, 0, s>>>(part, (int)nch, lp, qsum);
+    note_launch(2);
+    return cudaGetLastError();
+}
+
+}  // namespace gbr

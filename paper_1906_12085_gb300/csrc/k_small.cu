@@ -752,6 +752,7 @@ cudaError_t pca_select(const double *sigma, int count, const double *fro2, doubl
     template cudaError_t chol_inv<TG, TK, TC>(const TG *, int64_t, int, int64_t, double, double *, double *, TC *, \
                                               int, int *, cudaStream_t);
 INST_CHOL(float, float, float)
+INST_CHOL(float, double, float)
 INST_CHOL(double, double, double)
 template cudaError_t jacobi_osvd<float, float>(const double *, int, int, double *, float *, float *, int *,
                                                cudaStream_t);

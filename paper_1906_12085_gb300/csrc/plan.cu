@@ -58,6 +58,16 @@ struct rsvd_plan {
     float *Bth = nullptr, *Btl = nullptr;
     float *tcpart = nullptr;
     int64_t tcpart_elems = 0;
+    // bfloat16 precision form (dtype RSVD_BF16): A is stored as bfloat16, the m-row and
+    // n-row work blocks stay float32; these hold the bfloat16 operands of the products
+    void *Ztb = nullptr;                       // lp x ldzb: the small operand of A X, transposed
+    int64_t ldzb = 0;
+    void *Qb1 = nullptr, *Qb2 = nullptr, *Qb3 = nullptr;   // m x lp: terms of Q for A^T Q
+    float *mu_f = nullptr, *c16 = nullptr;    // means (float), mean correction of A X
+    double *qsum = nullptr, *qpart = nullptr;  // column sums of the Q terms and their partials
+    double *psum = nullptr, *psq = nullptr, *colv = nullptr;  // column statistics scratch
+    float *part16 = nullptr;
+    int64_t part16_elems = 0;
     // Golub-Kahan-Lanczos workspace, allocated on the first Krylov solve and grown with `steps`
     void *gkl_ws = nullptr;
     int gkl_cap = 0;
@@ -143,6 +153,22 @@ void carve(rsvd_plan *P, Carver &c) {
     P->sig = (double *)c.take(sizeof(double) * (n > sq ? n : sq));
     P->status = (int *)c.take(sizeof(int));
     P->Kdev = (int *)c.take(2 * sizeof(int));
+    if (P->dtype == RSVD_BF16) {
+        P->ldzb = round_up(n, 8);
+        P->Ztb = c.take(2 * P->lp * P->ldzb);
+        P->Qb1 = c.take(2 * m * P->lp);
+        P->Qb2 = c.take(2 * m * P->lp);
+        P->Qb3 = c.take(2 * m * P->lp);
+        P->mu_f = (float *)c.take(sizeof(float) * n);
+        P->c16 = (float *)c.take(sizeof(float) * P->lp);
+        P->qsum = (double *)c.take(sizeof(double) * P->lp);
+        P->qpart = (double *)c.take(sizeof(double) * split_bf16_chunks(m) * P->lp);
+        P->psum = (double *)c.take(sizeof(double) * colstats16_chunks(m) * n);
+        P->psq = (double *)c.take(sizeof(double) * colstats16_chunks(m) * n);
+        P->colv = (double *)c.take(sizeof(double) * n);
+        P->part16_elems = tc16_gemm_tn_partials(m, (int)n, P->lp);
+        P->part16 = (float *)c.take(sizeof(float) * P->part16_elems);
+    }
     if (P->tc) {
         P->ldt = round_up(n > P->wide ? n : P->wide, 4);
         P->Bth = (float *)c.take(sizeof(float) * P->lp * P->ldt);
@@ -261,13 +287,15 @@ rsvd_status cqr(rsvd_plan *P, const T *X, int64_t rows, int w, int ld, T *Qo, T 
     T *Q1 = passes == 2 ? Tmp : Qo;
     if (skinny) CK(prod_tn<T>(P, rows, ld, X, ld, X, ld, G, ld));
     else CK(gemm_tn<T>(rows, ld, ld, X, ld, X, ld, G, ld, part, P->part_elems, s));
-    CK(chol_inv<T, T, T>(G, ld, w, rows, u, P->R1, P->R1i, Ric, ld, P->status, s));
+    if (P->dtype == RSVD_BF16) CK(chol_inv<T, double, T>(G, ld, w, rows, u, P->R1, P->R1i, Ric, ld, P->status, s));
+    else CK(chol_inv<T, T, T>(G, ld, w, rows, u, P->R1, P->R1i, Ric, ld, P->status, s));
     if (skinny) CK(prod_nn<T>(P, rows, ld, X, ld, Ric, ld, Q1, ld));
     else CK(gemm_nn<T>(rows, ld, ld, X, ld, Ric, ld, Q1, ld, s));
     if (passes == 1) return RSVD_OK;
     if (skinny) CK(prod_tn<T>(P, rows, ld, Q1, ld, Q1, ld, G, ld));
     else CK(gemm_tn<T>(rows, ld, ld, Q1, ld, Q1, ld, G, ld, part, P->part_elems, s));
-    CK(chol_inv<T, T, T>(G, ld, w, rows, u, P->R2, P->R2i, Ric, ld, P->status, s));
+    if (P->dtype == RSVD_BF16) CK(chol_inv<T, double, T>(G, ld, w, rows, u, P->R2, P->R2i, Ric, ld, P->status, s));
+    else CK(chol_inv<T, T, T>(G, ld, w, rows, u, P->R2, P->R2i, Ric, ld, P->status, s));
     if (skinny) CK(prod_nn<T>(P, rows, ld, Q1, ld, Ric, ld, Qo, ld));
     else CK(gemm_nn<T>(rows, ld, ld, Q1, ld, Ric, ld, Qo, ld, s));
     if (want_r) CK(trmm_upper(P->R2, P->R1, P->Rt, w, s));
@@ -350,6 +378,80 @@ rsvd_status run_rsvd(rsvd_plan *P, T *A, const T *Omega, double *S, T *U, T *V) 
         CK(sign_normalize<T>(Vt, n, l, lp, W, l, lp, s));
         CK(gemm_nn<T>(m, k, lp, Q, lp, W, lp, U, k, s));                      // U = Q W (leading k)
         CK(copy2d<T, T>(Vt, lp, V, k, n, k, k, s));
+        CK(copy_f64(P->sig, S, k, s));
+    }
+    P->last_count = k;
+    return RSVD_OK;
+}
+
+// Sec. 3.1.2 on a bfloat16-stored A (precision form).  The products with A take
+// bfloat16 operands on the tensor cores with float32 accumulation: the small operand
+// of the sketch and power products is rounded to bfloat16 (it only spans the
+// subspace), the basis Q of the Rayleigh-Ritz product T = A^T Q is split into three
+// bfloat16 terms (float32-accurate against the stored A); the column means enter as
+// exact rank-1 corrections of each product.  CholeskyQR runs its Cholesky in
+// float64 and the SVD of R is a float64 one-sided Jacobi.
+rsvd_status run_rsvd_bf16(rsvd_plan *P, const void *A, const float *Omega, double *S, float *U, float *V) {
+    cudaStream_t s = P->stream;
+    const int64_t m = P->m, n = P->n;
+    const int l = P->l, lp = P->lp, k = P->k;
+    float *Y = (float *)P->Y, *Q = (float *)P->Qb, *Tmp = (float *)P->Tmp;
+    float *Z = (float *)P->Z, *Qz = (float *)P->Qz, *Tn = (float *)P->Tn, *Vt = (float *)P->Vt;
+    float *Tmpn = (float *)P->Tmpn;
+    const bool centred = !(P->flags & RSVD_FLAG_NO_CENTER);
+    rsvd_status st;
+    {
+        Span sp(P, RSVD_STAGE_CENTER);
+        CK(colstats16(A, m, n, n, centred, P->mu, P->mu_f, P->fro2, P->psum, P->psq, P->colv, s));
+    }
+    const double *mu = centred ? P->mu : nullptr;
+    const float *muf = centred ? P->mu_f : nullptr;
+    const void *q1[3] = {P->Qb1, P->Qb2, P->Qb3};
+    auto ax = [&](const float *Zs, int64_t ldzs) -> rsvd_status {  // Y = (A - 1 mu^T) round(Zs)
+        Span sp(P, RSVD_STAGE_AX);
+        CK(to_bf16_t(Zs, n, l, ldzs, lp, P->Ztb, P->ldzb, mu, P->c16, s));
+        CK(tc16_gemm_nn(m, (int)n, lp, A, n, P->Ztb, P->ldzb, Y, lp, mu ? P->c16 : nullptr, P->status, s));
+        return RSVD_OK;
+    };
+    auto atx = [&](int nq, float *Out) -> rsvd_status {  // Out = (A - 1 mu^T)^T (sum of the nq terms of Q)
+        Span sp(P, RSVD_STAGE_ATX);
+        CK(split_bf16(Q, m, lp, nq, P->Qb1, P->Qb2, P->Qb3, P->qpart, P->qsum, s));
+        CK(tc16_gemm_tn(m, (int)n, lp, A, n, q1, nq, lp, Out, lp, P->part16, P->part16_elems, muf,
+                        muf ? P->qsum : nullptr, P->status, s));
+        return RSVD_OK;
+    };
+    if ((st = ax(Omega, l))) return st;
+    {
+        Span sp(P, RSVD_STAGE_ORTH);
+        if ((st = cqr<float>(P, Y, m, l, lp, Q, Tmp, false, P->q > 0 ? 1 : 2))) return st;
+    }
+    for (int it = 0; it < P->q; it++) {
+        const bool last = it == P->q - 1;
+        if ((st = atx(1, Z))) return st;
+        {
+            Span sp(P, RSVD_STAGE_ORTH);
+            if ((st = cqr<float>(P, Z, n, l, lp, Qz, Tmpn, false, 1))) return st;
+        }
+        if ((st = ax(Qz, lp))) return st;
+        {
+            Span sp(P, RSVD_STAGE_ORTH);
+            if ((st = cqr<float>(P, Y, m, l, lp, Q, Tmp, false, last ? 2 : 1))) return st;
+        }
+    }
+    if ((st = atx(3, Tn))) return st;  // T = A^T Q, float32-accurate
+    float *UR = (float *)P->UR, *W = (float *)P->Wm;
+    {
+        Span sp(P, RSVD_STAGE_SMALL);
+        if ((st = cqr2<float>(P, Tn, n, l, lp, Qz, Tmpn, true))) return st;
+        CK(jacobi_osvd<double, float>(P->Rt, l, lp, P->sig, UR, W, P->status, s));
+        CK(sv_refine<float>(P->Rt, l, lp, UR, W, P->sig, s));
+    }
+    {
+        Span sp(P, RSVD_STAGE_FINISH);
+        CK(gemm_nn<float>(n, lp, lp, Qz, lp, UR, lp, Vt, lp, s));
+        CK(sign_normalize<float>(Vt, n, l, lp, W, l, lp, s));
+        CK(gemm_nn<float>(m, k, lp, Q, lp, W, lp, U, k, s));
+        CK(copy2d<float, float>(Vt, lp, V, k, n, k, k, s));
         CK(copy_f64(P->sig, S, k, s));
     }
     P->last_count = k;
@@ -520,6 +622,7 @@ rsvd_status run_gkl(rsvd_plan *P, T *A, const T *v1, int steps, double *S, T *U,
 }
 
 rsvd_status rsvd_direct(rsvd_plan_t P, void *A, const void *Omega, double *S, void *U, void *V) {
+    if (P->dtype == RSVD_BF16) return run_rsvd_bf16(P, A, (const float *)Omega, S, (float *)U, (float *)V);
     if (P->dtype == RSVD_F32) return run_rsvd<float>(P, (float *)A, (const float *)Omega, S, (float *)U, (float *)V);
     return run_rsvd<double>(P, (double *)A, (const double *)Omega, S, (double *)U, (double *)V);
 }
@@ -747,8 +850,9 @@ TuneKey tune_key(int64_t m, int64_t n, int lp) {
 rsvd_status plan_init(rsvd_plan *P, int64_t m, int64_t n, int k, int p, int q, rsvd_dtype dtype, void *cuda_stream) {
     if (m < 1 || n < 1 || m < n || k < 1 || p < 0 || q < 0) return RSVD_ERR_ARG;
     if ((int64_t)k + p > n) return RSVD_ERR_ARG;
-    if (dtype != RSVD_F32 && dtype != RSVD_F64) return RSVD_ERR_UNSUPPORTED;
+    if (dtype != RSVD_F32 && dtype != RSVD_F64 && dtype != RSVD_BF16) return RSVD_ERR_UNSUPPORTED;
     if (k + p > (dtype == RSVD_F32 ? kSmallMaxF32 : kSmallMaxF64)) return RSVD_ERR_UNSUPPORTED;
+    if (dtype == RSVD_BF16 && (n % 8 || !tc_available())) return RSVD_ERR_UNSUPPORTED;  // TMA rows of 16-byte multiples
     P->m = m;
     P->n = n;
     P->k = k;
@@ -756,11 +860,11 @@ rsvd_status plan_init(rsvd_plan *P, int64_t m, int64_t n, int k, int p, int q, r
     P->q = q;
     P->l = k + p;
     P->lp = (int)round_up(P->l, 16);
-    P->nx = n <= kSmallMaxF64 ? (int)n : 0;
+    P->nx = n <= kSmallMaxF64 && dtype != RSVD_BF16 ? (int)n : 0;
     P->wide = P->lp > P->nx ? P->lp : P->nx;
     P->dtype = dtype;
     P->stream = (cudaStream_t)cuda_stream;
-    P->tc = dtype == RSVD_F32 && P->lp <= 128 && tc_available();
+    P->tc = (dtype == RSVD_F32 || dtype == RSVD_BF16) && P->lp <= 128 && tc_available();
     if (P->tc) {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune.find(tune_key(m, n, P->lp));
@@ -980,6 +1084,7 @@ rsvd_status rsvd_batch_create(rsvd_batch_t *batch, int count, rsvd_plan_t const 
         const rsvd_plan *P = plans[i];
         if (!P) return RSVD_ERR_ARG;
         if (P->dtype != plans[0]->dtype || P->l != plans[0]->l || P->q != plans[0]->q) return RSVD_ERR_ARG;
+        if (P->dtype != RSVD_F32 && P->dtype != RSVD_F64) return RSVD_ERR_UNSUPPORTED;
         for (int j = 0; j < i; j++)
             if (plans[j] == P) return RSVD_ERR_ARG;
     }
@@ -1181,6 +1286,7 @@ rsvd_status svd_exact(rsvd_plan_t P, void *A, int method, double *S, void *U, vo
 rsvd_status svd_truncated_krylov(rsvd_plan_t P, void *A, const void *v1, int steps, double *S, void *U, void *V) {
     if (!P || !A || !v1 || !S || !U || !V) return RSVD_ERR_ARG;
     if (steps < P->k || steps > P->n || steps < 1) return RSVD_ERR_ARG;
+    if (P->dtype == RSVD_BF16) return RSVD_ERR_UNSUPPORTED;
     if (steps > (P->dtype == RSVD_F64 ? kSmallMaxF64 : kGklMaxStepsF32)) return RSVD_ERR_UNSUPPORTED;
     if (P->dtype == RSVD_F32)
         return run_gkl<float>(P, (float *)A, (const float *)v1, steps, S, (float *)U, (float *)V);

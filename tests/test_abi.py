@@ -50,8 +50,12 @@ def test_plan_create_rejects_bad_sizes(args):
 
 def test_plan_create_rejects_unbuilt_dtypes():
     h = ctypes.c_void_p()
-    for dt in (g.RSVD_BF16, g.RSVD_FP8_E4M3, 7):
+    for dt in (g.RSVD_FP8_E4M3, 7):
         assert g.lib().rsvd_plan_create(ctypes.byref(h), 100, 20, 4, 2, 1, dt, None) == g.RSVD_ERR_UNSUPPORTED
+    # bfloat16 plans need rows of whole 16-byte units (n a multiple of 8) and l <= 112
+    assert g.lib().rsvd_plan_create(ctypes.byref(h), 100, 20, 4, 2, 1, g.RSVD_BF16, None) == g.RSVD_ERR_UNSUPPORTED
+    assert g.lib().rsvd_plan_create(ctypes.byref(h), 1000, 256, 100, 16, 1, g.RSVD_BF16, None) == \
+        g.RSVD_ERR_UNSUPPORTED
 
 
 def test_null_plan_arguments():
@@ -71,7 +75,7 @@ def test_workspace_query_and_create_in_argument_errors():
     L = g.lib()
     st, b = g.rsvd_workspace_query(10, 20, 1, 0, 0)          # m < n
     assert st == g.RSVD_ERR_ARG and b == 0
-    st, b = g.rsvd_workspace_query(100, 20, 4, 2, 1, g.RSVD_BF16)
+    st, b = g.rsvd_workspace_query(100, 20, 4, 2, 1, g.RSVD_FP8_E4M3)
     assert st == g.RSVD_ERR_UNSUPPORTED
     st, b = g.rsvd_workspace_query(1000, 64, 8, 4, 1)
     assert st == g.RSVD_OK and b > 0 and b % 256 == 0

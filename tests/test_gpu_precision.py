@@ -1,0 +1,93 @@
+"""Precision form: randomized PCA of a bfloat16-stored matrix (RSVD_BF16 plans)
+against the FP64 oracle run on the same stored matrix (the oracle's own
+bfloat16 encoding of the float32 matrix, dequantised exactly) and the same
+Omega.  The sketch and power products round their small operand to bfloat16,
+which perturbs only the basis; the Rayleigh-Ritz product is float32-accurate.
+Reported and bounded (tolerances stated here, derived in the design notes;
+||A - 1 mu^T||_F^2 to 1e-6 relative):
+  sigma: |s_i - s_i^O| <= 1e-4 sigma_1^O for i <= k;
+  gap:   (||A - U U^T A||_F - ||A - U^O U^O^T A||_F) / ||A||_F <= 1e-4;
+  U, V orthonormal to 1e-5."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1906_12085_gb300 as g
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1906_12085_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def _stored(m, n, seed, shift=True):
+    sig = synth.spectrum_power(n, 1.5)
+    A = synth.prescribed(m, n, sig, 40961 + seed, 40962 + seed)
+    if shift:
+        A = A + torch.linspace(-0.05, 0.1, n, dtype=torch.float64).unsqueeze(0)
+    A32 = A.float().numpy()
+    codes = oracle.quantize_bf16(A32)
+    return codes, oracle.dequantize_bf16(codes)
+
+
+def _proj_residual(A, U):
+    """||A - U U^T A||_F for orthonormal U (float64)."""
+    B = U.T @ A
+    return np.sqrt(max(np.sum(A * A) - np.sum(B * B), 0.0))
+
+
+@pytest.mark.parametrize("m,n,k,p,q,shift", [
+    (60000, 512, 48, 16, 3, True),
+    (20011, 256, 20, 12, 2, True),     # ragged m
+    (30000, 1024, 40, 8, 1, False),    # data centred, NO_CENTER
+])
+def test_bf16_rsvd_matches_oracle_on_stored_matrix(m, n, k, p, q, shift):
+    codes, Ad = _stored(m, n, m % 97, shift)
+    Om = synth.gaussian(n, k + p, seed=40964, dtype=torch.float32)
+    dev = torch.device("cuda")
+    A = torch.from_numpy(codes.view(np.int16)).to(dev)
+    S = torch.zeros(k, dtype=torch.float64, device=dev)
+    U = torch.zeros(m, k, device=dev)
+    V = torch.zeros(n, k, device=dev)
+    with g.rsvd_plan_create(m, n, k, p, q, g.RSVD_BF16) as plan:
+        if not shift:
+            g.check(g.rsvd_plan_set_flags(plan, g.RSVD_FLAG_NO_CENTER))
+        g.check(g.rsvd(plan, A, None, Om.to(dev), S, U, V), "rsvd bf16")
+        assert g.rsvd_plan_sync(plan) == g.RSVD_OK
+        fro2 = g.rsvd_plan_fro2(plan)
+        stK, K = g.pca_threshold(plan, 0.9)
+    torch.cuda.synchronize()
+    Ac, mu, fro2o = oracle.center(Ad) if shift else (Ad, None, float(np.sum(Ad * Ad)))
+    # squares summed in float32 over 32-row groups, then float64; sum a^2 - m mu^2 cancels by (mu / std)^2
+    assert abs(fro2 - fro2o) <= 1e-6 * fro2o
+    s, Uo, Vo = oracle.rsvd(Ac, Om.double(), q=q, k=k)
+    Sg, Ug, Vg = S.cpu().numpy(), U.cpu().double().numpy(), V.cpu().double().numpy()
+    err = np.abs(Sg - s).max() / s[0]
+    assert err <= 1e-4, err
+    assert np.abs(Ug.T @ Ug - np.eye(k)).max() <= 1e-5
+    assert np.abs(Vg.T @ Vg - np.eye(k)).max() <= 1e-5
+    gap = (_proj_residual(Ac, Ug) - _proj_residual(Ac, Uo)) / np.sqrt(np.sum(Ac * Ac))
+    assert gap <= 1e-4, gap
+    print(f"bf16 rsvd {m}x{n} k={k}: max sigma error {err:.2e} sigma_1, projection gap {gap:.2e} ||A||_F")
+    Ko, reached = oracle.pca_threshold(s, fro2o, 0.9)
+    assert K == Ko
+
+
+def test_bf16_plan_rejects_unsupported_paths():
+    dev = torch.device("cuda")
+    with g.rsvd_plan_create(1000, 64, 8, 8, 1, g.RSVD_BF16) as plan:
+        A = torch.zeros(1000, 64, dtype=torch.int16, device=dev)
+        S = torch.zeros(64, dtype=torch.float64, device=dev)
+        assert g.svd_exact(plan, A, g.RSVD_EXACT_GRAM, S, S, S) == g.RSVD_ERR_UNSUPPORTED
+        v1 = torch.ones(64, device=dev)
+        assert g.svd_truncated_krylov(plan, A, v1, 16, S, S, S) == g.RSVD_ERR_UNSUPPORTED
+        with pytest.raises(g.RsvdError):
+            g.rsvd_batch_create([plan])
