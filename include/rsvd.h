@@ -114,7 +114,8 @@ rsvd_status rsvd_plan_sync(rsvd_plan_t plan);
  * float32 accumulation, the small operand of the sketch and power products
  * rounded to bfloat16 and the basis of T = A^T Q split into three bfloat16
  * terms (float32-accurate); the column means enter as exact rank-1
- * corrections; CholeskyQR's Cholesky and the SVD of R run in float64.
+ * corrections; CholeskyQR's Cholesky runs in float64 and the singular values
+ * of R are float64 Rayleigh quotients of its float32 Jacobi vectors.
  * svd_exact, svd_truncated_krylov and batches take RSVD_F32 / RSVD_F64 plans.
  *   Omega  : n x l Gaussian test matrix (caller-drawn), row-major.
  *   S      : k doubles; U : m x k; V : n x k (row-major).

@@ -151,8 +151,9 @@ __device__ __forceinline__ void drain_acc(uint32_t tmem, uint32_t b, int q, int 
     }
 }
 
-// Sub-chunk results summed in registers (N <= 64: N floats per epilogue thread) and
-// written once per tile; wider tiles add into memory after every sub-chunk instead.
+// Sub-chunk results summed in registers (N floats per epilogue thread; beyond 64 the
+// 128-register budget of these 448-thread kernels spills part of them to local memory)
+// and written once per tile.
 template <int N>
 __device__ __forceinline__ void sum_acc(uint32_t tmem, uint32_t b, int q, float *acc, bool first) {
 #pragma unroll
@@ -328,18 +329,16 @@ __global__ void __launch_bounds__(NTHR, 1)
         bool ok = true;
         for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
             const int64_t row = t * TM + q * 32 + lane;
-            float acc[N <= 64 ? N : 1];
+            float acc[N];
             for (int k0 = 0; k0 < nkb; k0 += SUBK, it++) {
                 const uint32_t b = it & 1;
                 if (!(ok = wait_ok(&bar->acc_full[b], (it >> 1) & 1, abort_flag))) break;
                 tc_fence_after();
-                if constexpr (N <= 64) sum_acc<N>(tmem, b, q, acc, k0 == 0);
-                else drain_acc<N>(tmem, b, q, lane, Y + row * ldy, row < m, k0 > 0);
+                sum_acc<N>(tmem, b, q, acc, k0 == 0);
                 tc_fence_before();
                 mbar_arrive(&bar->acc_empty[b]);
             }
-            if constexpr (N <= 64)
-                if (ok) store_acc<N>(acc, Y + row * ldy, row < m);
+            if (ok) store_acc<N>(acc, Y + row * ldy, row < m);
         }
     }
     tc_fence_before();
@@ -547,18 +546,16 @@ __global__ void __launch_bounds__(NTHR, 1)
             const int64_t chunk = t / ntn;
             const int c = c0 + q * 32 + lane;
             float *dst = part + (chunk * ncols + c) * (int64_t)N;
-            float acc[N <= 64 ? N : 1];
+            float acc[N];
             for (int k0 = 0; k0 < nkb; k0 += SUBK, it++) {
                 const uint32_t b = it & 1;
                 if (!(ok = wait_ok(&bar->acc_full[b], (it >> 1) & 1, abort_flag))) break;
                 tc_fence_after();
-                if constexpr (N <= 64) sum_acc<N>(tmem, b, q, acc, k0 == 0);
-                else drain_acc<N>(tmem, b, q, lane, dst, c < ncols, k0 > 0);
+                sum_acc<N>(tmem, b, q, acc, k0 == 0);
                 tc_fence_before();
                 mbar_arrive(&bar->acc_empty[b]);
             }
-            if constexpr (N <= 64)
-                if (ok) store_acc<N>(acc, dst, c < ncols);
+            if (ok) store_acc<N>(acc, dst, c < ncols);
         }
     }
     tc_fence_before();

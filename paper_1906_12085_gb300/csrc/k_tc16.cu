@@ -307,23 +307,26 @@ __global__ void __launch_bounds__(THR, 1)
             const int nkb = (int)((r1 - r0 + BK - 1) / BK);
             const int64_t chunk = t / ntn;
             const int cc = c0 + q * 32 + lane;
+            float acc[N];  // the tile's sum over its sub-chunks (IEEE float32 adds, fixed order)
             for (int k0 = 0; k0 < nkb; k0 += SUBK, it++) {
                 const uint32_t b = it & 1;
                 if (!(ok = wait16(&bar->acc_full[b], (it >> 1) & 1, abort_flag))) break;
                 tc_fence_after();
 #pragma unroll
-                for (int j0 = 0; j0 < N; j0 += 32) {
-                    float v[32];
-                    tmem_ld32(tmem + b * 128 + ((uint32_t)(q * 32) << 16) + (uint32_t)j0, v);
-                    if (cc < ncols) {
-                        float *p = part + (chunk * ncols + cc) * (int64_t)N + j0;
+                for (int j0 = 0; j0 < N; j0 += 16) {
+                    float v[16];
+                    tmem_ld16(tmem + b * 128 + ((uint32_t)(q * 32) << 16) + (uint32_t)j0, v);
 #pragma unroll
-                        for (int j = 0; j < 32; j++)
-                            if (j0 + j < N) p[j] = k0 > 0 ? p[j] + v[j] : v[j];
-                    }
+                    for (int j = 0; j < 16; j++) acc[j0 + j] = k0 > 0 ? acc[j0 + j] + v[j] : v[j];
                 }
                 tc_fence_before();
                 mbar_arrive(&bar->acc_empty[b]);
+            }
+            if (ok && cc < ncols) {
+                float *p = part + (chunk * ncols + cc) * (int64_t)N;
+#pragma unroll
+                for (int j = 0; j < N; j += 4)
+                    *reinterpret_cast<float4 *>(p + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
             }
         }
     }

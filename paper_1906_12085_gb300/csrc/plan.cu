@@ -390,7 +390,7 @@ rsvd_status run_rsvd(rsvd_plan *P, T *A, const T *Omega, double *S, T *U, T *V) 
 // subspace), the basis Q of the Rayleigh-Ritz product T = A^T Q is split into three
 // bfloat16 terms (float32-accurate against the stored A); the column means enter as
 // exact rank-1 corrections of each product.  CholeskyQR runs its Cholesky in
-// float64 and the SVD of R is a float64 one-sided Jacobi.
+// float64; the SVD of R is a one-sided Jacobi whose values are recomputed in float64.
 rsvd_status run_rsvd_bf16(rsvd_plan *P, const void *A, const float *Omega, double *S, float *U, float *V) {
     cudaStream_t s = P->stream;
     const int64_t m = P->m, n = P->n;
@@ -443,7 +443,9 @@ rsvd_status run_rsvd_bf16(rsvd_plan *P, const void *A, const float *Omega, doubl
     {
         Span sp(P, RSVD_STAGE_SMALL);
         if ((st = cqr2<float>(P, Tn, n, l, lp, Qz, Tmpn, true))) return st;
-        CK(jacobi_osvd<double, float>(P->Rt, l, lp, P->sig, UR, W, P->status, s));
+        // float32 rotations, float64 Rayleigh-quotient values (the float64 rate of this
+        // GPU is 1/58 of float32: a float64 Jacobi of l = 112 takes ~50 ms)
+        CK(jacobi_osvd<float, float>(P->Rt, l, lp, P->sig, UR, W, P->status, s));
         CK(sv_refine<float>(P->Rt, l, lp, UR, W, P->sig, s));
     }
     {

@@ -3,6 +3,7 @@
     python -m paper_1906_12085_gb300.profile_case rsvd --m 200000 --n 1000 --k 50 --p 10 --q 2
     python -m paper_1906_12085_gb300.profile_case gkl  --m 262144 --n 2048 --k 100 --steps 150
     python -m paper_1906_12085_gb300.profile_case exact --m 2000 --n 100 --dtype f64
+    python -m paper_1906_12085_gb300.profile_case rsvd --m 1048576 --n 4096 --k 96 --p 16 --q 3 --dtype bf16
 
 The matrix is seeded Gaussian data made on the device (a kernel's DRAM traffic and
 its launch shape do not depend on the values), so few launches precede the
@@ -29,15 +30,21 @@ def main(argv=None) -> int:
     ap.add_argument("--p", type=int, default=10)
     ap.add_argument("--q", type=int, default=2)
     ap.add_argument("--steps", type=int, default=150)
-    ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--dtype", choices=["f32", "f64", "bf16"], default="f32")
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--timed", type=int, default=0, help="then time this many graph-replayed solves (rsvd)")
     a = ap.parse_args(argv)
     dev = torch.device("cuda")
-    dt = g.RSVD_F32 if a.dtype == "f32" else g.RSVD_F64
-    tdt = torch.float32 if a.dtype == "f32" else torch.float64
+    dt = {"f32": g.RSVD_F32, "f64": g.RSVD_F64, "bf16": g.RSVD_BF16}[a.dtype]
+    tdt = torch.float64 if a.dtype == "f64" else torch.float32   # element type of Omega, U, V
     gen = torch.Generator(device=dev)
     gen.manual_seed(12085)
     A = torch.randn(a.m, a.n, generator=gen, device=dev, dtype=tdt)
+    if a.dtype == "bf16":  # stored as bfloat16 codes by the library's quantiser
+        Aq = torch.empty(a.m, a.n, dtype=torch.int16, device=dev)
+        g.check(g.rsvd_quantize(A, g.RSVD_BF16, Aq), "rsvd_quantize")
+        del A
+        A = Aq
     k = a.k if a.path != "exact" else a.n
     S = torch.zeros(k, dtype=torch.float64, device=dev)
     if a.path == "exact":
@@ -60,6 +67,21 @@ def main(argv=None) -> int:
                 g.check(g.svd_exact(plan, A, g.RSVD_EXACT_QR_JACOBI, S, U, V), "svd_exact")
         g.check(g.rsvd_plan_sync(plan), "solve status")
         prof = g.rsvd_plan_profile_read(plan)
+        if a.timed and a.path == "rsvd":       # graph-replayed solves, CUDA events on the plan's stream
+            g.rsvd_plan_profile(plan, False)
+            s0 = torch.cuda.current_stream()
+            for _ in range(2):
+                g.check(g.rsvd(plan, A, None, Om, S, U, V))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s0)
+            for _ in range(a.timed):
+                g.check(g.rsvd(plan, A, None, Om, S, U, V))
+            e1.record(s0)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / a.timed
+            l = a.k + a.p
+            flops = 2.0 * a.m * a.n * l * (2 * a.q + 2) + 2.0 * a.m * l * l * (a.q + 2) + 2.0 * a.n * l * l
+            print(f"timed: {ms:.3f} ms per solve, {flops / ms / 1e9:.1f} GFLOP/s over {a.timed} solves")
     torch.cuda.synchronize()
     print({kk: round(v[0], 4) for kk, v in prof.items()}, "ms;", "sigma_1 =", float(S[0]))
     return 0
