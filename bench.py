@@ -116,6 +116,22 @@ def traffic_for(kernel_src: str, kernel: str):
         return None
 
 
+def slowest_rank_ms(ms: float, world: int, device) -> float:
+    """The timed region of the slowest rank (replicas: every rank solves its own matrix)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    return float(t.item())
+
+
+def job_gflops(world: int, flops_per_solve: float, steps: int, ms_max: float) -> float:
+    """Whole-job throughput: every rank's solves over the slowest rank's time (weak scaling)."""
+    return world * flops_per_solve * steps / (ms_max * 1e-3) / 1e9
+
+
 def oracle_sample(A_host32, Om32, k, q, rows):
     """Time the FP64 oracle on the first `rows` rows (centred) of the workload matrix."""
     import numpy as np
@@ -220,13 +236,9 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     clocks = sampler.stop()
     st = g.rsvd_plan_sync(plan)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.barrier()
-    ms_max = float(t.item())
+    ms_max = slowest_rank_ms(ms, world, dev)
     flops = alg_flops(m, n, k, p, q)
-    value = world * flops * args.steps / (ms_max * 1e-3) / 1e9
+    value = job_gflops(world, flops, args.steps, ms_max)
 
     # per-kernel durations: the same K steps again with CUDA events recorded on the plan's
     # stream around every kernel group (direct launches, identical kernels)

@@ -685,10 +685,20 @@ struct TNSplit {
 // per tile.  The split does not depend on the grid size, so a capped grid (tuning)
 // computes every tile, and hence the result, exactly as the full one.
 TNSplit tn_split(int64_t rows, int ncols) {
-    const int64_t ntn = ceil_div(ncols, TM);
-    const int64_t target = 2 * (int64_t)num_sms();
-    int64_t chunks = ceil_div(target, ntn);
+    const int64_t ntn = ceil_div(ncols, TM), nsm = num_sms();
     const int64_t maxc = ceil_div(rows, 4 * TBK);  // at least four stages per tile
+    // at least two waves of tiles; the chunk count (up to twice that) that fills the last wave best
+    const int64_t c0 = ceil_div(2 * nsm, ntn);
+    int64_t chunks = c0;
+    double best = -1.0;
+    for (int64_t c = c0; c <= 2 * c0 && c <= maxc; c++) {
+        const int64_t t = c * ntn;
+        const double eff = (double)t / (double)(ceil_div(t, nsm) * nsm);
+        if (eff > best + 1e-9) {
+            best = eff;
+            chunks = c;
+        }
+    }
     if (chunks > maxc) chunks = maxc;
     if (chunks < 1) chunks = 1;
     const int64_t rpc = round_up(ceil_div(rows, chunks), TBK);

@@ -366,10 +366,22 @@ struct Split16 {
     int chunks;
 };
 
+// Row chunks of A^T Q: at least two waves of (chunk, column tile) tiles, the count of
+// chunks chosen (up to twice that) so the last wave is as full as possible; at least
+// four stages per tile.
 Split16 split16(int64_t rows, int ncols) {
-    const int64_t ntn = ceil_div(ncols, TM);
-    int64_t chunks = ceil_div(2 * (int64_t)sms(), ntn);
+    const int64_t ntn = ceil_div(ncols, TM), nsm = sms();
     const int64_t maxc = ceil_div(rows, 4 * BK);
+    int64_t c0 = ceil_div(2 * nsm, ntn), chunks = c0;
+    double best = -1.0;
+    for (int64_t c = c0; c <= 2 * c0 && c <= maxc; c++) {
+        const int64_t t = c * ntn;
+        const double eff = (double)t / (double)(ceil_div(t, nsm) * nsm);
+        if (eff > best + 1e-9) {
+            best = eff;
+            chunks = c;
+        }
+    }
     if (chunks > maxc) chunks = maxc;
     if (chunks < 1) chunks = 1;
     const int64_t rpc = round_up(ceil_div(rows, chunks), BK);

@@ -81,7 +81,7 @@ def main(argv=None) -> int:
             ms = e0.elapsed_time(e1) / a.timed
             l = a.k + a.p
             flops = 2.0 * a.m * a.n * l * (2 * a.q + 2) + 2.0 * a.m * l * l * (a.q + 2) + 2.0 * a.n * l * l
-            print(f"timed: {ms:.3f} ms per solve, {flops / ms / 1e9:.1f} GFLOP/s over {a.timed} solves")
+            print(f"timed: {ms:.3f} ms per solve, {flops / (ms * 1e-3) / 1e12:.1f} TFLOP/s over {a.timed} solves")
     torch.cuda.synchronize()
     print({kk: round(v[0], 4) for kk, v in prof.items()}, "ms;", "sigma_1 =", float(S[0]))
     return 0
