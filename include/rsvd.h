@@ -20,6 +20,8 @@
  *     RSVD_F32 : A, Omega, U, V are float;
  *     RSVD_BF16: A holds bfloat16 codes (2 bytes, e.g. from rsvd_quantize);
  *                Omega, U, V are float;
+ *     RSVD_FP8_E4M3: A holds e4m3 codes (1 byte) and rsvd takes the column
+ *                scales s (the matrix is A diag(s)); Omega, U, V are float;
  *   singular values S are always double.
  * - Outputs are sorted by descending singular value.  Sign convention: the
  *   largest-magnitude entry of every right singular vector v_i is positive
@@ -46,7 +48,7 @@ typedef enum {
     RSVD_F64 = 0,      /* float64 storage and arithmetic                       */
     RSVD_F32 = 1,      /* float32 storage, float32 products with float32 sums   */
     RSVD_BF16 = 2,     /* bfloat16 storage of A (precision form, rsvd only)     */
-    RSVD_FP8_E4M3 = 3  /* reserved: e4m3 storage with per-column scales         */
+    RSVD_FP8_E4M3 = 3  /* e4m3 storage of A with per-column scales (rsvd only)  */
 } rsvd_dtype;
 
 typedef enum {
@@ -108,7 +110,7 @@ rsvd_status rsvd_plan_sync(rsvd_plan_t plan);
  * orth() is CholeskyQR2 (R_ii > 0), which in exact arithmetic equals the
  * Householder QR the step list names.
  *   A      : m x n, row-major, read only (centred on the fly).
- *   col_scales : must be NULL (reserved for e4m3).
+ *   col_scales : n floats (device) for RSVD_FP8_E4M3 plans, NULL otherwise.
  * RSVD_BF16 plans (n a multiple of 8, l <= 112) solve for the stored bfloat16
  * matrix exactly as given: the products with A run on the tensor cores with
  * float32 accumulation, the small operand of the sketch and power products
@@ -116,6 +118,12 @@ rsvd_status rsvd_plan_sync(rsvd_plan_t plan);
  * terms (float32-accurate); the column means enter as exact rank-1
  * corrections; CholeskyQR's Cholesky runs in float64 and the singular values
  * of R are float64 Rayleigh quotients of its float32 Jacobi vectors.
+ * RSVD_FP8_E4M3 plans (n a multiple of 16, l <= 112) solve for A diag(s): the
+ * sketch and power products run on e4m3 operands (the small operand diag(s) Z
+ * and the basis Q quantised per column with their own scales, which the
+ * epilogues multiply back); the Rayleigh-Ritz product runs on the exact
+ * bfloat16 copy of the codes with the three-term basis (float32-accurate), in
+ * 2mn bytes of extra workspace; the rest as for bfloat16.
  * svd_exact, svd_truncated_krylov and batches take RSVD_F32 / RSVD_F64 plans.
  *   Omega  : n x l Gaussian test matrix (caller-drawn), row-major.
  *   S      : k doubles; U : m x k; V : n x k (row-major).

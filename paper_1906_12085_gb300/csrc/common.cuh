@@ -110,7 +110,17 @@ cudaError_t tc16_gemm_nn(int64_t m, int n, int N, const void *A, int64_t lda, co
 int64_t tc16_gemm_tn_partials(int64_t rows, int ncols, int N);
 cudaError_t tc16_gemm_tn(int64_t rows, int ncols, int N, const void *A, int64_t lda, const void *const *Q, int nq,
                          int64_t ldq, float *C, int64_t ldc, float *part, int64_t part_elems, const float *mu,
-                         const double *qsum, int *status, cudaStream_t s);
+                         const double *qsum, int *status, cudaStream_t s, const float *cs = nullptr);
+// e4m3 forms (A and the small operand as e4m3 codes, float32 accumulation):
+//   Y = (A Zq) diag(ts) - 1 c^T                     (ts, c: N floats, optional)
+//   C = diag(cs) (A^T Qq) diag(qs) - mu qsum^T      (cs: ncols, qs: N floats; mu, qsum optional)
+// n and the leading dimensions multiples of 16.
+cudaError_t tc8_gemm_nn(int64_t m, int n, int N, const void *A, int64_t lda, const void *Zt, int64_t ldz, float *Y,
+                        int64_t ldy, const float *ts, const float *c, int *status, cudaStream_t s);
+int64_t tc8_gemm_tn_partials(int64_t rows, int ncols, int N);
+cudaError_t tc8_gemm_tn(int64_t rows, int ncols, int N, const void *A, int64_t lda, const void *Q, int64_t ldq,
+                        float *C, int64_t ldc, float *part, int64_t part_elems, const float *cs, const float *qs,
+                        const float *mu, const double *qsum, int *status, cudaStream_t s);
 // column statistics of a bfloat16 matrix (psum / psq: colstats16_chunks(m) x n doubles, colv: n doubles)
 int64_t colstats16_chunks(int64_t m);
 cudaError_t colstats16(const void *A, int64_t m, int64_t n, int64_t lda, bool center, double *mu, float *mu_f,
@@ -122,6 +132,16 @@ cudaError_t to_bf16_t(const float *Z, int64_t n, int l, int64_t ldzin, int lp, v
 int64_t split_bf16_chunks(int64_t rows);
 cudaError_t split_bf16(const float *Q, int64_t rows, int lp, int nq, void *Q1, void *Q2, void *Q3, double *part,
                        double *qsum, cudaStream_t s);
+
+// e4m3 counterparts (the stored matrix is A_q diag(scales); see k_prec.cu)
+cudaError_t colstats8(const void *A, int64_t m, int64_t n, int64_t lda, bool center, const float *scales, double *mu,
+                      float *mu_f, double *fro2, double *psum, double *psq, double *colv, cudaStream_t s);
+cudaError_t prep8_small(const float *Z, int64_t n, int l, int64_t ldzin, int lp, const float *scales,
+                        const double *mu, void *Zqt, int64_t ldz, float *t, float *c, cudaStream_t s);
+// mpart: split_bf16_chunks(rows) x lp floats, part: split_bf16_chunks(rows) x lp doubles
+cudaError_t prep8_q(const float *Q, int64_t rows, int lp, void *Qq, float *u, float *mpart, double *part,
+                    double *qsum, cudaStream_t s);
+cudaError_t e4m3_to_bf16(const void *A, int64_t count, void *B, cudaStream_t s);
 
 // Serving interface of plan.cu (used by server.cu): a batch context on stream bs
 // for up to `cap` problems, and one launch of a float32 batch followed, per

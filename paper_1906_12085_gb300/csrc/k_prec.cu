@@ -9,6 +9,14 @@
 //                carries Q to float32 accuracy (hi = round(Q), mid = round(Q - hi),
 //                lo = round(Q - hi - mid), each difference exact in float32), and
 //                the column sums of the terms (float64) for the mean correction.
+// and their e4m3 counterparts (the stored matrix is A_q diag(s)):
+//   colstats8  : means and ||A - 1 mu^T||_F^2 of A_q diag(s);
+//   prep8_small: Zq = e4m3(diag(s) Z diag(1/t)) transposed, t_j = amax_i |s_i Z_ij| / 448,
+//                and c_j = t_j sum_i (mu_i / s_i) Zq_ij (the product uses exactly
+//                Z_eff = diag(1/s) Zq diag(t), so c = mu^T Z_eff);
+//   prep8_q    : Qq = e4m3(Q diag(1/u)), u_j = amax_r |Q_rj| / 448, and
+//                qsum_j = u_j sum_r Qq_rj;
+//   e4m3_to_bf16: the codes as bfloat16 (exact: every e4m3 value is a bfloat16).
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -136,7 +144,205 @@ __global__ void sum_rows_kernel(const double *__restrict__ part, int nch, int lp
     qsum[j] = s;
 }
 
+// ------------------------------------------------------------------ e4m3
+// value of an e4m3 code (finite codes only): normal 2^(e-7) (1 + m/8), subnormal m 2^-9
+__device__ __forceinline__ float f8(uint8_t c) {
+    const uint32_t e = (c >> 3) & 15u, mt = c & 7u, sg = (uint32_t)(c & 0x80u) << 24;
+    if (e) return __uint_as_float(sg | ((e + 120u) << 23) | (mt << 20));
+    return __uint_as_float(sg | __float_as_uint((float)mt * 0.001953125f));  // m * 2^-9
+}
+
+__device__ __forceinline__ uint8_t e4m3(float x) {
+    unsigned short d;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(d) : "f"(0.f), "f"(x));
+    return (uint8_t)(d & 0xFF);
+}
+
+__global__ void colstats8_kernel(const uint8_t *__restrict__ A, int64_t m, int64_t n, int64_t lda, int64_t rpb,
+                                 double *__restrict__ psum, double *__restrict__ psq) {
+    __shared__ double rs[8][33], rq[8][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t c = (int64_t)blockIdx.x * 32 + tx;
+    const int64_t r0 = (int64_t)blockIdx.y * rpb, r1 = min(m, r0 + rpb);
+    double s = 0.0, q = 0.0;
+    if (c < n) {
+        for (int64_t g = r0 + ty * 32; g < r1; g += 8 * 32) {
+            float fs = 0.f, fq = 0.f;
+            const int64_t ge = min(r1, g + 32);
+            for (int64_t r = g; r < ge; r++) {
+                const float a = f8(A[r * lda + c]);
+                fs += a;
+                fq = fmaf(a, a, fq);
+            }
+            s += fs;
+            q += fq;
+        }
+    }
+    rs[ty][tx] = s;
+    rq[ty][tx] = q;
+    __syncthreads();
+    if (ty == 0 && c < n) {
+        for (int k = 1; k < 8; k++) {
+            s += rs[k][tx];
+            q += rq[k][tx];
+        }
+        psum[(int64_t)blockIdx.y * n + c] = s;
+        psq[(int64_t)blockIdx.y * n + c] = q;
+    }
+}
+
+// the statistics of column j scaled by s_j
+__global__ void colstats8_finish(const double *__restrict__ psum, const double *__restrict__ psq, int nch, int64_t m,
+                                 int64_t n, bool center, const float *__restrict__ sc, double *__restrict__ mu,
+                                 float *__restrict__ mu_f, double *__restrict__ colv) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    double s = 0.0, q = 0.0;
+    for (int k = 0; k < nch; k++) {
+        s += psum[(int64_t)k * n + c];
+        q += psq[(int64_t)k * n + c];
+    }
+    const double sj = (double)sc[c];
+    const double mq = center ? s / (double)m : 0.0;   // mean of the codes' values
+    mu[c] = sj * mq;
+    mu_f[c] = (float)(sj * mq);
+    colv[c] = sj * sj * (q - (double)m * mq * mq);
+}
+
+// one block per column j < lp: t_j, the codes of column j (row j of Zqt), c_j
+__global__ void prep8_small_kernel(const float *__restrict__ Z, int64_t n, int l, int64_t ldzin,
+                                   const float *__restrict__ sc, const double *__restrict__ mu,
+                                   uint8_t *__restrict__ Zqt, int64_t ldz, float *__restrict__ t, float *__restrict__ c) {
+    __shared__ float rmax[32];
+    __shared__ double rsum[32];
+    const int j = blockIdx.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint8_t *row = Zqt + (int64_t)j * ldz;
+    if (j >= l) {  // padding rows
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) row[i] = 0;
+        if (threadIdx.x == 0) {
+            t[j] = 1.f;
+            if (c) c[j] = 0.f;
+        }
+        return;
+    }
+    float mx = 0.f;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) mx = fmaxf(mx, fabsf(sc[i] * Z[i * ldzin + j]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) rmax[wid] = mx;
+    __syncthreads();
+    mx = 0.f;
+    for (int w = 0; w < nw; w++) mx = fmaxf(mx, rmax[w]);
+    const float tj = mx > 0.f ? __fdiv_rn(mx, 448.f) : 1.f;
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const uint8_t q = e4m3(__fdiv_rn(sc[i] * Z[i * ldzin + j], tj));
+        row[i] = q;
+        if (mu) acc += mu[i] / (double)sc[i] * (double)f8(q);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) rsum[wid] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        t[j] = tj;
+        if (c) {
+            double a = 0.0;
+            for (int w = 0; w < nw; w++) a += rsum[w];
+            c[j] = (float)(a * (double)tj);
+        }
+    }
+}
+
+// column maxima of Q (rows x lp), partial over row chunks (128 columns x 2 row groups per block)
+__global__ void colmax_q_kernel(const float *__restrict__ Q, int64_t rows, int lp, int64_t rpb,
+                                float *__restrict__ part) {
+    __shared__ float red[2][128];
+    const int j = threadIdx.x & 127, ry = threadIdx.x >> 7;
+    const int64_t r0 = (int64_t)blockIdx.x * rpb, r1 = min(rows, r0 + rpb);
+    float mx = 0.f;
+    if (j < lp)
+        for (int64_t r = r0 + ry; r < r1; r += 2) mx = fmaxf(mx, fabsf(Q[r * lp + j]));
+    red[ry][j] = mx;
+    __syncthreads();
+    if (ry == 0 && j < lp) part[(int64_t)blockIdx.x * lp + j] = fmaxf(red[0][j], red[1][j]);
+}
+
+__global__ void colmax_finish(const float *__restrict__ part, int nch, int lp, float *__restrict__ u) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= lp) return;
+    float mx = 0.f;
+    for (int k = 0; k < nch; k++) mx = fmaxf(mx, part[(int64_t)k * lp + j]);
+    u[j] = mx > 0.f ? __fdiv_rn(mx, 448.f) : 1.f;
+}
+
+// Qq = e4m3(Q / u) and per row chunk the column sums of u_j Qq_rj
+__global__ void quant_q_kernel(const float *__restrict__ Q, int64_t rows, int lp, const float *__restrict__ u,
+                               uint8_t *__restrict__ Qq, int64_t rpb, double *__restrict__ part) {
+    __shared__ double red[2][128];
+    const int j = threadIdx.x & 127, ry = threadIdx.x >> 7;
+    const int64_t r0 = (int64_t)blockIdx.x * rpb, r1 = min(rows, r0 + rpb);
+    double s = 0.0;
+    if (j < lp) {
+        const float uj = u[j];
+        for (int64_t r = r0 + ry; r < r1; r += 2) {
+            const uint8_t q = e4m3(__fdiv_rn(Q[r * lp + j], uj));
+            Qq[r * lp + j] = q;
+            s += (double)f8(q);
+        }
+        s *= (double)uj;
+    }
+    red[ry][j] = s;
+    __syncthreads();
+    if (ry == 0 && j < lp) part[(int64_t)blockIdx.x * lp + j] = red[0][j] + red[1][j];
+}
+
+__global__ void e4m3_to_bf16_kernel(const uint8_t *__restrict__ A, int64_t total, uint16_t *__restrict__ B) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < total) B[i] = rbf(f8(A[i]));
+}
+
 }  // namespace
+
+cudaError_t colstats8(const void *A, int64_t m, int64_t n, int64_t lda, bool center, const float *scales, double *mu,
+                      float *mu_f, double *fro2, double *psum, double *psq, double *colv, cudaStream_t s) {
+    const int64_t nch = colstats16_chunks(m);
+    const int64_t rpb = round_up(ceil_div(m, nch), 32);
+    const int64_t ch = ceil_div(m, rpb);
+    colstats8_kernel<<<dim3((unsigned)ceil_div(n, 32), (unsigned)ch), 256, 0, s>>>(static_cast<const uint8_t *>(A), m,
+                                                                                   n, lda, rpb, psum, psq);
+    colstats8_finish<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(psum, psq, (int)ch, m, n, center, scales, mu, mu_f,
+                                                                colv);
+    note_launch(2);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return sum_f64(colv, n, fro2, s);
+}
+
+cudaError_t prep8_small(const float *Z, int64_t n, int l, int64_t ldzin, int lp, const float *scales,
+                        const double *mu, void *Zqt, int64_t ldz, float *t, float *c, cudaStream_t s) {
+    prep8_small_kernel<<<lp, 256, 0, s>>>(Z, n, l, ldzin, scales, mu, static_cast<uint8_t *>(Zqt), ldz, t, c);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t prep8_q(const float *Q, int64_t rows, int lp, void *Qq, float *u, float *mpart, double *part,
+                    double *qsum, cudaStream_t s) {
+    if (lp > 128) return cudaErrorInvalidValue;
+    const int64_t rpb = 2048;
+    const int64_t nch = ceil_div(rows, rpb);
+    colmax_q_kernel<<<(unsigned)nch, 256, 0, s>>>(Q, rows, lp, rpb, mpart);
+    colmax_finish<<<(unsigned)ceil_div(lp, 128), 128, 0, s>>>(mpart, (int)nch, lp, u);
+    quant_q_kernel<<<(unsigned)nch, 256, 0, s>>>(Q, rows, lp, u, static_cast<uint8_t *>(Qq), rpb, part);
+    sum_rows_kernel<<<(unsigned)ceil_div(lp, 128), 128, 0, s>>>(part, (int)nch, lp, qsum);
+    note_launch(4);
+    return cudaGetLastError();
+}
+
+cudaError_t e4m3_to_bf16(const void *A, int64_t count, void *B, cudaStream_t s) {
+    e4m3_to_bf16_kernel<<<(unsigned)ceil_div(count, 256), 256, 0, s>>>(static_cast<const uint8_t *>(A), count,
+                                                                       static_cast<uint16_t *>(B));
+    note_launch();
+    return cudaGetLastError();
+}
 
 int64_t colstats16_chunks(int64_t m) { return ceil_div(m, 4096) < 1024 ? ceil_div(m, 4096) : 1024; }
 

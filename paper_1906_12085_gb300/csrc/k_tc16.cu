@@ -1,5 +1,5 @@
-// bfloat16 tall-skinny products of the precision form on tcgen05 (kind::f16,
-// float32 accumulation in tensor memory).  The stored bfloat16 matrix A is an
+// bfloat16 and e4m3 tall-skinny products of the precision form on tcgen05
+// (kind::f16 / kind::f8f6f4, float32 accumulation in tensor memory).  The stored bfloat16 matrix A is an
 // exact operand; the small operand is bfloat16 too: rounded from float32 for
 // the power-iteration products (only its span matters there), or split into
 // three bfloat16 terms whose sum carries the float32 value (the
@@ -28,12 +28,42 @@ namespace {
 using namespace tc;
 
 constexpr int TM = 128;                  // MMA M
-constexpr int BK = 64;                   // bfloat16 K elements per stage (128 bytes)
 constexpr int THR = 192;                 // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr int NEPI = 128;
-constexpr uint32_t A_ST = TM * 128;      // 16 KB: 128 rows (NN) or 2 MN atoms x 64 rows (TN)
+constexpr uint32_t A_ST = TM * 128;      // 16 KB of A per stage (NN: 128 rows; TN: 128 columns)
 constexpr uint32_t TCOLS = 256;          // two accumulators of up to 128 float32 columns
-constexpr uint32_t ATOM_K = BK * 128;    // TN: bytes of one 64-element MN atom column over the stage's rows
+
+// Element-size traits (ESZ bytes per element: 2 bfloat16, 1 e4m3).  A stage holds
+// 128 bytes of K per row in NN (one swizzled row), and in TN TN_BK rows of the
+// 128-column A tile as MN atoms of 128 bytes (QW elements); each MMA consumes KMMA
+// K elements (32 bytes of a K-major row, or KMMA rows of an MN-major atom).
+template <int ESZ>
+struct Elt;
+template <>
+struct Elt<2> {
+    static constexpr int NN_BK = 64, TN_BK = 64, KMMA = 16, QW = 64, A_ATOMS = 2;
+    static constexpr uint32_t ATOM = 64 * 128;       // one MN atom over the stage's 64 rows
+    static constexpr uint32_t LBO = ATOM;            // byte stride between MN-adjacent atoms
+    static constexpr uint32_t Q_ROOM = 2 * ATOM;     // two atoms of room per Q operand (see TN16)
+};
+template <>
+struct Elt<1> {
+    static constexpr int NN_BK = 128, TN_BK = 128, KMMA = 32, QW = 128, A_ATOMS = 1;
+    static constexpr uint32_t ATOM = 128 * 128;      // the single MN atom over the stage's 128 rows
+    static constexpr uint32_t LBO = 1024;            // unused with one atom; equal to SBO, so both stride readings agree
+    static constexpr uint32_t Q_ROOM = ATOM;
+};
+
+template <int ESZ>
+__host__ __device__ constexpr uint32_t idesc_e(int M, int N, bool a_mn, bool b_mn) {
+    return ESZ == 2 ? idesc_bf16(M, N, a_mn, b_mn) : idesc_e4m3(M, N, a_mn, b_mn);
+}
+
+template <int ESZ>
+__device__ __forceinline__ void mma_e(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if constexpr (ESZ == 2) mma_bf16(d, a, b, idesc, acc);
+    else mma_e4m3(d, a, b, idesc, acc);
+}
 // TN: stages accumulated in one TMEM accumulator before it is drained and added (IEEE
 // float32) to the partial: the tensor core's accumulation error grows with the number of
 // accumulation steps, 4 stages (256 rows) bound it.
@@ -57,7 +87,7 @@ __device__ __forceinline__ bool wait16(uint64_t *bar, uint32_t parity, volatile 
 constexpr int cmin(int a, int b) { return a < b ? a : b; }
 
 // ======================================================================= NN
-template <int N>
+template <int N, int ESZ>
 struct NN16 {
     static constexpr uint32_t B_ST = N * 128;
     static constexpr uint32_t STAGE = A_ST + B_ST;
@@ -66,11 +96,13 @@ struct NN16 {
     static constexpr uint32_t SMEM = NEED > 120 * 1024 ? NEED : 120 * 1024;  // one CTA per SM (owns TMEM)
 };
 
-template <int N>
+template <int N, int ESZ>
 __global__ void __launch_bounds__(THR, 1)
     tc16_nn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t m, int n,
-                   float *__restrict__ Y, int64_t ldy, const float *__restrict__ c, int *__restrict__ status) {
-    using C = NN16<N>;
+                   float *__restrict__ Y, int64_t ldy, const float *__restrict__ ts, const float *__restrict__ c,
+                   int *__restrict__ status) {
+    using C = NN16<N, ESZ>;
+    constexpr int BK = Elt<ESZ>::NN_BK;
     constexpr int S = C::S;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -118,7 +150,7 @@ __global__ void __launch_bounds__(THR, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16(TM, N, false, false);
+            constexpr uint32_t idesc = idesc_e<ESZ>(TM, N, false, false);
             uint32_t g = 0, it = 0;
             bool ok = true;
             for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x, it++) {
@@ -131,9 +163,9 @@ __global__ void __launch_bounds__(THR, 1)
                     if (!(ok = wait16(&bar->full[s], (g / S) & 1, abort_flag))) break;
                     tc_fence_after();
 #pragma unroll
-                    for (int kk = 0; kk < BK / 16; kk++)
-                        mma_bf16(d, sdesc_kmajor_sw128(sA + s * A_ST, kk * 32),
-                                 sdesc_kmajor_sw128(sB + s * C::B_ST, kk * 32), idesc, (kb | kk) ? 1u : 0u);
+                    for (int kk = 0; kk < 4; kk++)  // 32 bytes of K per MMA
+                        mma_e<ESZ>(d, sdesc_kmajor_sw128(sA + s * A_ST, kk * 32),
+                                   sdesc_kmajor_sw128(sB + s * C::B_ST, kk * 32), idesc, (kb | kk) ? 1u : 0u);
                     mma_commit(&bar->empty[s]);
                 }
                 if (ok) mma_commit(&bar->acc_full[b]);
@@ -155,7 +187,7 @@ __global__ void __launch_bounds__(THR, 1)
                     float *p = Y + row * ldy + c0;
 #pragma unroll
                     for (int j = 0; j < 32; j++)
-                        if (c0 + j < N) p[j] = c ? v[j] - c[c0 + j] : v[j];
+                        if (c0 + j < N) p[j] = (ts ? v[j] * ts[c0 + j] : v[j]) - (c ? c[c0 + j] : 0.f);
                 }
             }
             tc_fence_before();
@@ -175,24 +207,27 @@ __global__ void __launch_bounds__(THR, 1)
 // Tile (chunk, column tile): D (128 columns of A x N) = sum over the chunk's rows
 // of A[r][c] Q_i[r][j].  Stage layout: A as two MN atoms (columns c0..c0+63 and
 // c0+64..c0+127) of 64 rows each; every Q_i as ceil(N/64) MN atoms of 64 rows.
-template <int N, int NB>
+template <int N, int NB, int ESZ>
 struct TN16 {
-    static constexpr int NA = (N + 63) / 64;          // MN atoms of one Q operand loaded by TMA
-    // two atoms of room per operand whatever N: the MMA's reads of one operand then stay
-    // inside its own 16 KB under either assignment of the two descriptor strides
-    static constexpr uint32_t Q_ST = 2 * ATOM_K;
+    using E = Elt<ESZ>;
+    static constexpr int NA = (N + E::QW - 1) / E::QW;  // MN atoms of one Q operand loaded by TMA
+    // bfloat16: two atoms of room per operand whatever N, so the MMA's reads of one operand
+    // stay inside its own 16 KB under either assignment of the two descriptor strides
+    static constexpr uint32_t Q_ST = E::Q_ROOM;
     static constexpr uint32_t STAGE = A_ST + NB * Q_ST;
     static constexpr int S = cmin(8, (int)((200 * 1024) / STAGE));
     static constexpr uint32_t NEED = S * STAGE + 1024 + sizeof(Bars16<S>) + 64;
     static constexpr uint32_t SMEM = NEED > 120 * 1024 ? NEED : 120 * 1024;
 };
 
-template <int N, int NB>
+template <int N, int NB, int ESZ>
 __global__ void __launch_bounds__(THR, 1)
     tc16_tn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmQ1,
                    const __grid_constant__ CUtensorMap tmQ2, const __grid_constant__ CUtensorMap tmQ3, int64_t rows,
                    int ncols, int64_t rpc, int nchunks, float *__restrict__ part, int *__restrict__ status) {
-    using C = TN16<N, NB>;
+    using C = TN16<N, NB, ESZ>;
+    using E = Elt<ESZ>;
+    constexpr int BK = E::TN_BK;
     constexpr int S = C::S;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -247,15 +282,17 @@ __global__ void __launch_bounds__(THR, 1)
                     if (!(ok = wait16(&bar->empty[s], ((g / S) & 1) ^ 1, abort_flag))) break;
                     uint8_t *st = base + s * C::STAGE;
                     const int32_t y = (int32_t)(r0 + kb * BK);
-                    mbar_arrive_expect_tx(&bar->full[s], A_ST + NB * C::NA * ATOM_K);  // bytes the boxes below bring
-                    tma_load_2d(st, &tmA, c0, y, &bar->full[s]);
-                    tma_load_2d(st + ATOM_K, &tmA, c0 + 64, y, &bar->full[s]);
+                    // bytes the boxes below bring
+                    mbar_arrive_expect_tx(&bar->full[s], (E::A_ATOMS + NB * C::NA) * E::ATOM);
+#pragma unroll
+                    for (int a = 0; a < E::A_ATOMS; a++)
+                        tma_load_2d(st + a * E::ATOM, &tmA, c0 + a * E::QW, y, &bar->full[s]);
 #pragma unroll
                     for (int i = 0; i < NB; i++) {
                         const CUtensorMap *mq = i == 0 ? &tmQ1 : i == 1 ? &tmQ2 : &tmQ3;
 #pragma unroll
                         for (int a = 0; a < C::NA; a++)
-                            tma_load_2d(st + A_ST + i * C::Q_ST + a * ATOM_K, mq, a * 64, y, &bar->full[s]);
+                            tma_load_2d(st + A_ST + i * C::Q_ST + a * E::ATOM, mq, a * E::QW, y, &bar->full[s]);
                     }
                 }
             }
@@ -263,7 +300,7 @@ __global__ void __launch_bounds__(THR, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16(TM, N, true, true);
+            constexpr uint32_t idesc = idesc_e<ESZ>(TM, N, true, true);
             uint32_t g = 0, it = 0;
             bool ok = true;
             for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
@@ -283,12 +320,13 @@ __global__ void __launch_bounds__(THR, 1)
                         tc_fence_after();
                         const uint8_t *st = base + s * C::STAGE;
 #pragma unroll
-                        for (int kk = 0; kk < BK / 16; kk++) {  // 16 rows = two 8-row K atoms = 2048 bytes
-                            const uint64_t ad = sdesc_mn_sw128(st, kk * 2048, ATOM_K, 1024);
+                        for (int kk = 0; kk < BK / E::KMMA; kk++) {  // KMMA rows = KMMA / 8 K atoms of 1024 bytes
+                            const uint32_t off = kk * E::KMMA * 128;
+                            const uint64_t ad = sdesc_mn_sw128(st, off, E::LBO, 1024);
 #pragma unroll
                             for (int i = 0; i < NB; i++)
-                                mma_bf16(d, ad, sdesc_mn_sw128(st + A_ST + i * C::Q_ST, kk * 2048, ATOM_K, 1024),
-                                         idesc, ((kb - k0) | kk | i) ? 1u : 0u);
+                                mma_e<ESZ>(d, ad, sdesc_mn_sw128(st + A_ST + i * C::Q_ST, off, E::LBO, 1024), idesc,
+                                           ((kb - k0) | kk | i) ? 1u : 0u);
                         }
                         mma_commit(&bar->empty[s]);
                     }
@@ -339,14 +377,18 @@ __global__ void __launch_bounds__(THR, 1)
     if (threadIdx.x == 0 && bar->abort_flag) atomicOr(status, (int)ST_TIMEOUT);
 }
 
-// out[c][j] = sum over chunks (in order) of part[chunk][c][j] - mu[c] qsum[j]; one thread per (c, j)
+// out[c][j] = cs[c] qs[j] (sum over chunks, in order, of part[chunk][c][j]) - mu[c] qsum[j]
+// (cs, qs, mu optional); one thread per (c, j)
 __global__ void sum16_kernel(const float *__restrict__ part, int nchunks, int ncols, int N, float *__restrict__ out,
-                             int64_t ldo, const float *__restrict__ mu, const double *__restrict__ qsum) {
+                             int64_t ldo, const float *__restrict__ cs, const float *__restrict__ qs,
+                             const float *__restrict__ mu, const double *__restrict__ qsum) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)ncols * N) return;
     const int c = (int)(idx / N), j = (int)(idx % N);
     double s = 0.0;
     for (int k = 0; k < nchunks; k++) s += (double)part[((int64_t)k * ncols + c) * N + j];
+    if (cs) s *= (double)cs[c];
+    if (qs) s *= (double)qs[j];
     if (mu) s -= (double)mu[c] * qsum[j];
     out[(int64_t)c * ldo + j] = (float)s;
 }
@@ -369,9 +411,9 @@ struct Split16 {
 // Row chunks of A^T Q: at least two waves of (chunk, column tile) tiles, the count of
 // chunks chosen (up to twice that) so the last wave is as full as possible; at least
 // four stages per tile.
-Split16 split16(int64_t rows, int ncols) {
+Split16 split16(int64_t rows, int ncols, int bk) {
     const int64_t ntn = ceil_div(ncols, TM), nsm = sms();
-    const int64_t maxc = ceil_div(rows, 4 * BK);
+    const int64_t maxc = ceil_div(rows, 4 * bk);
     int64_t c0 = ceil_div(2 * nsm, ntn), chunks = c0;
     double best = -1.0;
     for (int64_t c = c0; c <= 2 * c0 && c <= maxc; c++) {
@@ -384,83 +426,82 @@ Split16 split16(int64_t rows, int ncols) {
     }
     if (chunks > maxc) chunks = maxc;
     if (chunks < 1) chunks = 1;
-    const int64_t rpc = round_up(ceil_div(rows, chunks), BK);
+    const int64_t rpc = round_up(ceil_div(rows, chunks), bk);
     return {rpc, (int)ceil_div(rows, rpc)};
 }
 
-template <int N>
+template <int N, int ESZ>
 cudaError_t launch16_nn(const CUtensorMap &a, const CUtensorMap &b, int64_t m, int n, float *Y, int64_t ldy,
-                        const float *c, int *status, cudaStream_t s) {
-    using C = NN16<N>;
+                        const float *ts, const float *c, int *status, cudaStream_t s) {
+    using C = NN16<N, ESZ>;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(tc16_nn_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        cudaFuncSetAttribute(tc16_nn_kernel<N, ESZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         attr = true;
     }
     const int64_t tiles = ceil_div(m, TM);
     const int grid = (int)(tiles < sms() ? tiles : sms());
-    tc16_nn_kernel<N><<<grid, THR, C::SMEM, s>>>(a, b, m, n, Y, ldy, c, status);
+    tc16_nn_kernel<N, ESZ><<<grid, THR, C::SMEM, s>>>(a, b, m, n, Y, ldy, ts, c, status);
     note_launch();
     return cudaGetLastError();
 }
 
-template <int N, int NB>
+template <int N, int NB, int ESZ>
 cudaError_t launch16_tn(const CUtensorMap &a, const CUtensorMap *q, int64_t rows, int ncols, Split16 sp, float *part,
                         int *status, cudaStream_t s) {
-    using C = TN16<N, NB>;
+    using C = TN16<N, NB, ESZ>;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(tc16_tn_kernel<N, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        cudaFuncSetAttribute(tc16_tn_kernel<N, NB, ESZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         attr = true;
     }
     const int64_t tiles = ceil_div(ncols, TM) * sp.chunks;
     const int grid = (int)(tiles < sms() ? tiles : sms());
-    tc16_tn_kernel<N, NB><<<grid, THR, C::SMEM, s>>>(a, q[0], q[1], q[2], rows, ncols, sp.rpc, sp.chunks, part, status);
+    tc16_tn_kernel<N, NB, ESZ><<<grid, THR, C::SMEM, s>>>(a, q[0], q[1], q[2], rows, ncols, sp.rpc, sp.chunks, part,
+                                                           status);
     note_launch();
     return cudaGetLastError();
 }
 
-}  // namespace
-
-cudaError_t tc16_gemm_nn(int64_t m, int n, int N, const void *A, int64_t lda, const void *Zt, int64_t ldz, float *Y,
-                         int64_t ldy, const float *c, int *status, cudaStream_t s) {
+template <int ESZ>
+cudaError_t gemm_nn_e(int64_t m, int n, int N, const void *A, int64_t lda, const void *Zt, int64_t ldz, float *Y,
+                      int64_t ldy, const float *ts, const float *c, int *status, cudaStream_t s) {
     if (N % 16 || N < 16 || N > 128) return cudaErrorInvalidValue;
+    constexpr int BK = Elt<ESZ>::NN_BK;
     CUtensorMap ma, mb;
-    if (!tc_make_map(&ma, A, 2, m, n, lda, TM, BK, true) || !tc_make_map(&mb, Zt, 2, N, n, ldz, N, BK, true))
+    if (!tc_make_map(&ma, A, ESZ, m, n, lda, TM, BK, true) || !tc_make_map(&mb, Zt, ESZ, N, n, ldz, N, BK, true))
         return cudaErrorInvalidValue;
     switch (N) {
-        case 16: return launch16_nn<16>(ma, mb, m, n, Y, ldy, c, status, s);
-        case 32: return launch16_nn<32>(ma, mb, m, n, Y, ldy, c, status, s);
-        case 48: return launch16_nn<48>(ma, mb, m, n, Y, ldy, c, status, s);
-        case 64: return launch16_nn<64>(ma, mb, m, n, Y, ldy, c, status, s);
-        case 80: return launch16_nn<80>(ma, mb, m, n, Y, ldy, c, status, s);
-        case 96: return launch16_nn<96>(ma, mb, m, n, Y, ldy, c, status, s);
-        case 112: return launch16_nn<112>(ma, mb, m, n, Y, ldy, c, status, s);
-        case 128: return launch16_nn<128>(ma, mb, m, n, Y, ldy, c, status, s);
+        case 16: return launch16_nn<16, ESZ>(ma, mb, m, n, Y, ldy, ts, c, status, s);
+        case 32: return launch16_nn<32, ESZ>(ma, mb, m, n, Y, ldy, ts, c, status, s);
+        case 48: return launch16_nn<48, ESZ>(ma, mb, m, n, Y, ldy, ts, c, status, s);
+        case 64: return launch16_nn<64, ESZ>(ma, mb, m, n, Y, ldy, ts, c, status, s);
+        case 80: return launch16_nn<80, ESZ>(ma, mb, m, n, Y, ldy, ts, c, status, s);
+        case 96: return launch16_nn<96, ESZ>(ma, mb, m, n, Y, ldy, ts, c, status, s);
+        case 112: return launch16_nn<112, ESZ>(ma, mb, m, n, Y, ldy, ts, c, status, s);
+        case 128: return launch16_nn<128, ESZ>(ma, mb, m, n, Y, ldy, ts, c, status, s);
     }
     return cudaErrorInvalidValue;
 }
 
-int64_t tc16_gemm_tn_partials(int64_t rows, int ncols, int N) {
-    const Split16 sp = split16(rows, ncols);
-    return (int64_t)sp.chunks * ncols * N;
-}
-
-cudaError_t tc16_gemm_tn(int64_t rows, int ncols, int N, const void *A, int64_t lda, const void *const *Q, int nq,
-                         int64_t ldq, float *C, int64_t ldc, float *part, int64_t part_elems, const float *mu,
-                         const double *qsum, int *status, cudaStream_t s) {
-    if (N % 16 || N < 16 || N > 128 || (nq != 1 && nq != 3)) return cudaErrorInvalidValue;
-    const Split16 sp = split16(rows, ncols);
+template <int ESZ>
+cudaError_t gemm_tn_e(int64_t rows, int ncols, int N, const void *A, int64_t lda, const void *const *Q, int nq,
+                      int64_t ldq, float *C, int64_t ldc, float *part, int64_t part_elems, const float *cs,
+                      const float *qs, const float *mu, const double *qsum, int *status, cudaStream_t s) {
+    using E = Elt<ESZ>;
+    if (N % 16 || N < 16 || N > 128 || (nq != 1 && nq != 3) || (ESZ == 1 && nq != 1)) return cudaErrorInvalidValue;
+    const Split16 sp = split16(rows, ncols, E::TN_BK);
     if (!part || part_elems < (int64_t)sp.chunks * ncols * N) return cudaErrorInvalidValue;
     CUtensorMap ma, mq[3];
-    if (!tc_make_map(&ma, A, 2, rows, ncols, lda, BK, 64, true)) return cudaErrorInvalidValue;
+    if (!tc_make_map(&ma, A, ESZ, rows, ncols, lda, E::TN_BK, E::QW, true)) return cudaErrorInvalidValue;
     for (int i = 0; i < 3; i++)
-        if (!tc_make_map(&mq[i], Q[i < nq ? i : 0], 2, rows, N, ldq, BK, 64, true)) return cudaErrorInvalidValue;
+        if (!tc_make_map(&mq[i], Q[i < nq ? i : 0], ESZ, rows, N, ldq, E::TN_BK, E::QW, true))
+            return cudaErrorInvalidValue;
     cudaError_t e = cudaErrorInvalidValue;
 #define TN16_CASE(NN)                                                                                   \
     case NN:                                                                                            \
-        e = nq == 1 ? launch16_tn<NN, 1>(ma, mq, rows, ncols, sp, part, status, s)                      \
-                    : launch16_tn<NN, 3>(ma, mq, rows, ncols, sp, part, status, s);                     \
+        e = nq == 1 ? launch16_tn<NN, 1, ESZ>(ma, mq, rows, ncols, sp, part, status, s)                 \
+                    : launch16_tn<NN, ESZ == 2 ? 3 : 1, ESZ>(ma, mq, rows, ncols, sp, part, status, s); \
         break;
     switch (N) {
         TN16_CASE(16)
@@ -475,9 +516,45 @@ cudaError_t tc16_gemm_tn(int64_t rows, int ncols, int N, const void *A, int64_t 
 #undef TN16_CASE
     if (e != cudaSuccess) return e;
     const int64_t total = (int64_t)ncols * N;
-    sum16_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, s>>>(part, sp.chunks, ncols, N, C, ldc, mu, qsum);
+    sum16_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, s>>>(part, sp.chunks, ncols, N, C, ldc, cs, qs, mu, qsum);
     note_launch();
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t tc16_gemm_nn(int64_t m, int n, int N, const void *A, int64_t lda, const void *Zt, int64_t ldz, float *Y,
+                         int64_t ldy, const float *c, int *status, cudaStream_t s) {
+    return gemm_nn_e<2>(m, n, N, A, lda, Zt, ldz, Y, ldy, nullptr, c, status, s);
+}
+
+cudaError_t tc8_gemm_nn(int64_t m, int n, int N, const void *A, int64_t lda, const void *Zt, int64_t ldz, float *Y,
+                        int64_t ldy, const float *ts, const float *c, int *status, cudaStream_t s) {
+    return gemm_nn_e<1>(m, n, N, A, lda, Zt, ldz, Y, ldy, ts, c, status, s);
+}
+
+int64_t tc16_gemm_tn_partials(int64_t rows, int ncols, int N) {
+    const Split16 sp = split16(rows, ncols, Elt<2>::TN_BK);
+    return (int64_t)sp.chunks * ncols * N;
+}
+
+int64_t tc8_gemm_tn_partials(int64_t rows, int ncols, int N) {
+    const Split16 sp = split16(rows, ncols, Elt<1>::TN_BK);
+    return (int64_t)sp.chunks * ncols * N;
+}
+
+cudaError_t tc16_gemm_tn(int64_t rows, int ncols, int N, const void *A, int64_t lda, const void *const *Q, int nq,
+                         int64_t ldq, float *C, int64_t ldc, float *part, int64_t part_elems, const float *mu,
+                         const double *qsum, int *status, cudaStream_t s, const float *cs) {
+    return gemm_tn_e<2>(rows, ncols, N, A, lda, Q, nq, ldq, C, ldc, part, part_elems, cs, nullptr, mu, qsum, status,
+                        s);
+}
+
+cudaError_t tc8_gemm_tn(int64_t rows, int ncols, int N, const void *A, int64_t lda, const void *Q, int64_t ldq,
+                        float *C, int64_t ldc, float *part, int64_t part_elems, const float *cs, const float *qs,
+                        const float *mu, const double *qsum, int *status, cudaStream_t s) {
+    const void *q3[3] = {Q, Q, Q};
+    return gemm_tn_e<1>(rows, ncols, N, A, lda, q3, 1, ldq, C, ldc, part, part_elems, cs, qs, mu, qsum, status, s);
 }
 
 }  // namespace gbr

@@ -68,12 +68,18 @@ struct rsvd_plan {
     double *psum = nullptr, *psq = nullptr, *colv = nullptr;  // column statistics scratch
     float *part16 = nullptr;
     int64_t part16_elems = 0;
+    // e4m3 form (dtype RSVD_FP8_E4M3): e4m3 operands of the sketch / power products and the
+    // bfloat16 copy of the stored codes for the float32-accurate Rayleigh-Ritz product
+    void *Zq8 = nullptr, *Qq8 = nullptr, *A16 = nullptr;
+    int64_t ldz8 = 0;
+    float *t8 = nullptr, *u8 = nullptr, *mpart8 = nullptr, *part8 = nullptr;
+    int64_t part8_elems = 0;
     // Golub-Kahan-Lanczos workspace, allocated on the first Krylov solve and grown with `steps`
     void *gkl_ws = nullptr;
     int gkl_cap = 0;
     // CUDA graph of the last rsvd solve, replayed while the caller's pointers and flags repeat
     cudaGraphExec_t graph = nullptr;
-    const void *gkey[6] = {};
+    const void *gkey[7] = {};
     unsigned gflags = 0;
     uint64_t glaunches = 0;
     // tracing: event pairs recorded around stage groups while profiling is on
@@ -153,7 +159,18 @@ void carve(rsvd_plan *P, Carver &c) {
     P->sig = (double *)c.take(sizeof(double) * (n > sq ? n : sq));
     P->status = (int *)c.take(sizeof(int));
     P->Kdev = (int *)c.take(2 * sizeof(int));
-    if (P->dtype == RSVD_BF16) {
+    if (P->dtype == RSVD_FP8_E4M3) {
+        P->ldz8 = round_up(n, 16);
+        P->Zq8 = c.take((size_t)P->lp * P->ldz8);
+        P->Qq8 = c.take((size_t)m * P->lp);
+        P->A16 = c.take(2 * (size_t)m * n);
+        P->t8 = (float *)c.take(sizeof(float) * P->lp);
+        P->u8 = (float *)c.take(sizeof(float) * P->lp);
+        P->mpart8 = (float *)c.take(sizeof(float) * split_bf16_chunks(m) * P->lp);
+        P->part8_elems = tc8_gemm_tn_partials(m, (int)n, P->lp);
+        P->part8 = (float *)c.take(sizeof(float) * P->part8_elems);
+    }
+    if (P->dtype == RSVD_BF16 || P->dtype == RSVD_FP8_E4M3) {
         P->ldzb = round_up(n, 8);
         P->Ztb = c.take(2 * P->lp * P->ldzb);
         P->Qb1 = c.take(2 * m * P->lp);
@@ -287,14 +304,16 @@ rsvd_status cqr(rsvd_plan *P, const T *X, int64_t rows, int w, int ld, T *Qo, T 
     T *Q1 = passes == 2 ? Tmp : Qo;
     if (skinny) CK(prod_tn<T>(P, rows, ld, X, ld, X, ld, G, ld));
     else CK(gemm_tn<T>(rows, ld, ld, X, ld, X, ld, G, ld, part, P->part_elems, s));
-    if (P->dtype == RSVD_BF16) CK(chol_inv<T, double, T>(G, ld, w, rows, u, P->R1, P->R1i, Ric, ld, P->status, s));
+    if (P->dtype == RSVD_BF16 || P->dtype == RSVD_FP8_E4M3)
+        CK(chol_inv<T, double, T>(G, ld, w, rows, u, P->R1, P->R1i, Ric, ld, P->status, s));
     else CK(chol_inv<T, T, T>(G, ld, w, rows, u, P->R1, P->R1i, Ric, ld, P->status, s));
     if (skinny) CK(prod_nn<T>(P, rows, ld, X, ld, Ric, ld, Q1, ld));
     else CK(gemm_nn<T>(rows, ld, ld, X, ld, Ric, ld, Q1, ld, s));
     if (passes == 1) return RSVD_OK;
     if (skinny) CK(prod_tn<T>(P, rows, ld, Q1, ld, Q1, ld, G, ld));
     else CK(gemm_tn<T>(rows, ld, ld, Q1, ld, Q1, ld, G, ld, part, P->part_elems, s));
-    if (P->dtype == RSVD_BF16) CK(chol_inv<T, double, T>(G, ld, w, rows, u, P->R2, P->R2i, Ric, ld, P->status, s));
+    if (P->dtype == RSVD_BF16 || P->dtype == RSVD_FP8_E4M3)
+        CK(chol_inv<T, double, T>(G, ld, w, rows, u, P->R2, P->R2i, Ric, ld, P->status, s));
     else CK(chol_inv<T, T, T>(G, ld, w, rows, u, P->R2, P->R2i, Ric, ld, P->status, s));
     if (skinny) CK(prod_nn<T>(P, rows, ld, Q1, ld, Ric, ld, Qo, ld));
     else CK(gemm_nn<T>(rows, ld, ld, Q1, ld, Ric, ld, Qo, ld, s));
@@ -445,6 +464,86 @@ rsvd_status run_rsvd_bf16(rsvd_plan *P, const void *A, const float *Omega, doubl
         if ((st = cqr2<float>(P, Tn, n, l, lp, Qz, Tmpn, true))) return st;
         // float32 rotations, float64 Rayleigh-quotient values (the float64 rate of this
         // GPU is 1/58 of float32: a float64 Jacobi of l = 112 takes ~50 ms)
+        CK(jacobi_osvd<float, float>(P->Rt, l, lp, P->sig, UR, W, P->status, s));
+        CK(sv_refine<float>(P->Rt, l, lp, UR, W, P->sig, s));
+    }
+    {
+        Span sp(P, RSVD_STAGE_FINISH);
+        CK(gemm_nn<float>(n, lp, lp, Qz, lp, UR, lp, Vt, lp, s));
+        CK(sign_normalize<float>(Vt, n, l, lp, W, l, lp, s));
+        CK(gemm_nn<float>(m, k, lp, Q, lp, W, lp, U, k, s));
+        CK(copy2d<float, float>(Vt, lp, V, k, n, k, k, s));
+        CK(copy_f64(P->sig, S, k, s));
+    }
+    P->last_count = k;
+    return RSVD_OK;
+}
+
+// Sec. 3.1.2 on an e4m3-stored A = A_q diag(s) (precision form).  The sketch and power
+// products take e4m3 operands (kind::f8f6f4, float32 accumulation): the small operand
+// diag(s) Z and the basis Q are quantised per column with their own scales, which the
+// epilogues multiply back; the Rayleigh-Ritz product T = A^T Q runs on the exact
+// bfloat16 copy of the codes with Q split into three bfloat16 terms and diag(s)
+// applied to the sum.  Means, CholeskyQR and the small SVD as for bfloat16.
+rsvd_status run_rsvd_fp8(rsvd_plan *P, const void *A, const float *sc, const float *Omega, double *S, float *U,
+                         float *V) {
+    cudaStream_t s = P->stream;
+    const int64_t m = P->m, n = P->n;
+    const int l = P->l, lp = P->lp, k = P->k;
+    float *Y = (float *)P->Y, *Q = (float *)P->Qb, *Tmp = (float *)P->Tmp;
+    float *Z = (float *)P->Z, *Qz = (float *)P->Qz, *Tn = (float *)P->Tn, *Vt = (float *)P->Vt;
+    float *Tmpn = (float *)P->Tmpn;
+    const bool centred = !(P->flags & RSVD_FLAG_NO_CENTER);
+    rsvd_status st;
+    {
+        Span sp(P, RSVD_STAGE_CENTER);
+        CK(colstats8(A, m, n, n, centred, sc, P->mu, P->mu_f, P->fro2, P->psum, P->psq, P->colv, s));
+    }
+    const double *mu = centred ? P->mu : nullptr;
+    const float *muf = centred ? P->mu_f : nullptr;
+    auto ax = [&](const float *Zs, int64_t ldzs) -> rsvd_status {  // Y = (A - 1 mu^T) Z_eff
+        Span sp(P, RSVD_STAGE_AX);
+        CK(prep8_small(Zs, n, l, ldzs, lp, sc, mu, P->Zq8, P->ldz8, P->t8, P->c16, s));
+        CK(tc8_gemm_nn(m, (int)n, lp, A, n, P->Zq8, P->ldz8, Y, lp, P->t8, mu ? P->c16 : nullptr, P->status, s));
+        return RSVD_OK;
+    };
+    auto atx = [&](float *Out) -> rsvd_status {  // Out = (A - 1 mu^T)^T Q_eff
+        Span sp(P, RSVD_STAGE_ATX);
+        CK(prep8_q(Q, m, lp, P->Qq8, P->u8, P->mpart8, P->qpart, P->qsum, s));
+        CK(tc8_gemm_tn(m, (int)n, lp, A, n, P->Qq8, lp, Out, lp, P->part8, P->part8_elems, sc, P->u8, muf,
+                       muf ? P->qsum : nullptr, P->status, s));
+        return RSVD_OK;
+    };
+    if ((st = ax(Omega, l))) return st;
+    {
+        Span sp(P, RSVD_STAGE_ORTH);
+        if ((st = cqr<float>(P, Y, m, l, lp, Q, Tmp, false, P->q > 0 ? 1 : 2))) return st;
+    }
+    for (int it = 0; it < P->q; it++) {
+        const bool last = it == P->q - 1;
+        if ((st = atx(Z))) return st;
+        {
+            Span sp(P, RSVD_STAGE_ORTH);
+            if ((st = cqr<float>(P, Z, n, l, lp, Qz, Tmpn, false, 1))) return st;
+        }
+        if ((st = ax(Qz, lp))) return st;
+        {
+            Span sp(P, RSVD_STAGE_ORTH);
+            if ((st = cqr<float>(P, Y, m, l, lp, Q, Tmp, false, last ? 2 : 1))) return st;
+        }
+    }
+    {
+        Span sp(P, RSVD_STAGE_ATX);  // T = A^T Q, float32-accurate, on the bfloat16 copy of the codes
+        const void *q3[3] = {P->Qb1, P->Qb2, P->Qb3};
+        CK(e4m3_to_bf16(A, m * n, P->A16, s));
+        CK(split_bf16(Q, m, lp, 3, P->Qb1, P->Qb2, P->Qb3, P->qpart, P->qsum, s));
+        CK(tc16_gemm_tn(m, (int)n, lp, P->A16, n, q3, 3, lp, Tn, lp, P->part16, P->part16_elems, muf,
+                        muf ? P->qsum : nullptr, P->status, s, sc));
+    }
+    float *UR = (float *)P->UR, *W = (float *)P->Wm;
+    {
+        Span sp(P, RSVD_STAGE_SMALL);
+        if ((st = cqr2<float>(P, Tn, n, l, lp, Qz, Tmpn, true))) return st;
         CK(jacobi_osvd<float, float>(P->Rt, l, lp, P->sig, UR, W, P->status, s));
         CK(sv_refine<float>(P->Rt, l, lp, UR, W, P->sig, s));
     }
@@ -623,7 +722,8 @@ rsvd_status run_gkl(rsvd_plan *P, T *A, const T *v1, int steps, double *S, T *U,
     return RSVD_OK;
 }
 
-rsvd_status rsvd_direct(rsvd_plan_t P, void *A, const void *Omega, double *S, void *U, void *V) {
+rsvd_status rsvd_direct(rsvd_plan_t P, void *A, const float *sc, const void *Omega, double *S, void *U, void *V) {
+    if (P->dtype == RSVD_FP8_E4M3) return run_rsvd_fp8(P, A, sc, (const float *)Omega, S, (float *)U, (float *)V);
     if (P->dtype == RSVD_BF16) return run_rsvd_bf16(P, A, (const float *)Omega, S, (float *)U, (float *)V);
     if (P->dtype == RSVD_F32) return run_rsvd<float>(P, (float *)A, (const float *)Omega, S, (float *)U, (float *)V);
     return run_rsvd<double>(P, (double *)A, (const double *)Omega, S, (double *)U, (double *)V);
@@ -852,9 +952,12 @@ TuneKey tune_key(int64_t m, int64_t n, int lp) {
 rsvd_status plan_init(rsvd_plan *P, int64_t m, int64_t n, int k, int p, int q, rsvd_dtype dtype, void *cuda_stream) {
     if (m < 1 || n < 1 || m < n || k < 1 || p < 0 || q < 0) return RSVD_ERR_ARG;
     if ((int64_t)k + p > n) return RSVD_ERR_ARG;
-    if (dtype != RSVD_F32 && dtype != RSVD_F64 && dtype != RSVD_BF16) return RSVD_ERR_UNSUPPORTED;
+    if (dtype != RSVD_F32 && dtype != RSVD_F64 && dtype != RSVD_BF16 && dtype != RSVD_FP8_E4M3)
+        return RSVD_ERR_UNSUPPORTED;
     if (k + p > (dtype == RSVD_F32 ? kSmallMaxF32 : kSmallMaxF64)) return RSVD_ERR_UNSUPPORTED;
-    if (dtype == RSVD_BF16 && (n % 8 || !tc_available())) return RSVD_ERR_UNSUPPORTED;  // TMA rows of 16-byte multiples
+    // TMA rows of 16-byte multiples: n % 8 (bfloat16), n % 16 (e4m3)
+    if (dtype == RSVD_BF16 && (n % 8 || !tc_available())) return RSVD_ERR_UNSUPPORTED;
+    if (dtype == RSVD_FP8_E4M3 && (n % 16 || !tc_available())) return RSVD_ERR_UNSUPPORTED;
     P->m = m;
     P->n = n;
     P->k = k;
@@ -862,11 +965,11 @@ rsvd_status plan_init(rsvd_plan *P, int64_t m, int64_t n, int k, int p, int q, r
     P->q = q;
     P->l = k + p;
     P->lp = (int)round_up(P->l, 16);
-    P->nx = n <= kSmallMaxF64 && dtype != RSVD_BF16 ? (int)n : 0;
+    P->nx = n <= kSmallMaxF64 && (dtype == RSVD_F32 || dtype == RSVD_F64) ? (int)n : 0;
     P->wide = P->lp > P->nx ? P->lp : P->nx;
     P->dtype = dtype;
     P->stream = (cudaStream_t)cuda_stream;
-    P->tc = (dtype == RSVD_F32 || dtype == RSVD_BF16) && P->lp <= 128 && tc_available();
+    P->tc = dtype != RSVD_F64 && P->lp <= 128 && tc_available();
     if (P->tc) {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune.find(tune_key(m, n, P->lp));
@@ -1023,22 +1126,22 @@ rsvd_status rsvd_plan_sync(rsvd_plan_t P) {
 
 rsvd_status rsvd(rsvd_plan_t P, void *A, const float *col_scales, const void *Omega, double *S, void *U, void *V) {
     if (!P || !A || !Omega || !S || !U || !V) return RSVD_ERR_ARG;
-    if (col_scales) return RSVD_ERR_ARG;
+    if ((col_scales != nullptr) != (P->dtype == RSVD_FP8_E4M3)) return RSVD_ERR_ARG;  // e4m3 needs its scales
     // Tracing records events between launches and the legacy stream cannot be captured:
     // both run the launches directly.
-    if (P->prof || P->stream == nullptr) return rsvd_direct(P, A, Omega, S, U, V);
-    const void *key[6] = {A, Omega, S, U, V, P};
+    if (P->prof || P->stream == nullptr) return rsvd_direct(P, A, col_scales, Omega, S, U, V);
+    const void *key[7] = {A, Omega, S, U, V, P, col_scales};
     bool hit = P->graph && P->gflags == P->flags;
-    for (int i = 0; hit && i < 6; i++) hit = P->gkey[i] == key[i];
+    for (int i = 0; hit && i < 7; i++) hit = P->gkey[i] == key[i];
     if (!hit) {
         drop_graph(P);
         cudaGraph_t g = nullptr;
         const uint64_t before = rsvd_launch_count();
         if (cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
             cudaGetLastError();
-            return rsvd_direct(P, A, Omega, S, U, V);
+            return rsvd_direct(P, A, col_scales, Omega, S, U, V);
         }
-        const rsvd_status st = rsvd_direct(P, A, Omega, S, U, V);
+        const rsvd_status st = rsvd_direct(P, A, col_scales, Omega, S, U, V);
         const cudaError_t ce = cudaStreamEndCapture(P->stream, &g);
         const uint64_t captured = rsvd_launch_count() - before;
         g_launches.fetch_sub(captured, std::memory_order_relaxed);  // captured, not yet executed
@@ -1052,9 +1155,9 @@ rsvd_status rsvd(rsvd_plan_t P, void *A, const float *col_scales, const void *Om
         if (ie != cudaSuccess) {
             P->graph = nullptr;
             cudaGetLastError();
-            return rsvd_direct(P, A, Omega, S, U, V);
+            return rsvd_direct(P, A, col_scales, Omega, S, U, V);
         }
-        for (int i = 0; i < 6; i++) P->gkey[i] = key[i];
+        for (int i = 0; i < 7; i++) P->gkey[i] = key[i];
         P->gflags = P->flags;
         P->glaunches = captured;
     }
@@ -1288,7 +1391,7 @@ rsvd_status svd_exact(rsvd_plan_t P, void *A, int method, double *S, void *U, vo
 rsvd_status svd_truncated_krylov(rsvd_plan_t P, void *A, const void *v1, int steps, double *S, void *U, void *V) {
     if (!P || !A || !v1 || !S || !U || !V) return RSVD_ERR_ARG;
     if (steps < P->k || steps > P->n || steps < 1) return RSVD_ERR_ARG;
-    if (P->dtype == RSVD_BF16) return RSVD_ERR_UNSUPPORTED;
+    if (P->dtype != RSVD_F32 && P->dtype != RSVD_F64) return RSVD_ERR_UNSUPPORTED;
     if (steps > (P->dtype == RSVD_F64 ? kSmallMaxF64 : kGklMaxStepsF32)) return RSVD_ERR_UNSUPPORTED;
     if (P->dtype == RSVD_F32)
         return run_gkl<float>(P, (float *)A, (const float *)v1, steps, S, (float *)U, (float *)V);

@@ -4,6 +4,7 @@
     python -m paper_1906_12085_gb300.profile_case gkl  --m 262144 --n 2048 --k 100 --steps 150
     python -m paper_1906_12085_gb300.profile_case exact --m 2000 --n 100 --dtype f64
     python -m paper_1906_12085_gb300.profile_case rsvd --m 1048576 --n 4096 --k 96 --p 16 --q 3 --dtype bf16
+    python -m paper_1906_12085_gb300.profile_case rsvd --m 1048576 --n 4096 --k 96 --p 16 --q 3 --dtype fp8
 
 The matrix is seeded Gaussian data made on the device (a kernel's DRAM traffic and
 its launch shape do not depend on the values), so few launches precede the
@@ -30,19 +31,26 @@ def main(argv=None) -> int:
     ap.add_argument("--p", type=int, default=10)
     ap.add_argument("--q", type=int, default=2)
     ap.add_argument("--steps", type=int, default=150)
-    ap.add_argument("--dtype", choices=["f32", "f64", "bf16"], default="f32")
+    ap.add_argument("--dtype", choices=["f32", "f64", "bf16", "fp8"], default="f32")
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--timed", type=int, default=0, help="then time this many graph-replayed solves (rsvd)")
     a = ap.parse_args(argv)
     dev = torch.device("cuda")
-    dt = {"f32": g.RSVD_F32, "f64": g.RSVD_F64, "bf16": g.RSVD_BF16}[a.dtype]
+    dt = {"f32": g.RSVD_F32, "f64": g.RSVD_F64, "bf16": g.RSVD_BF16, "fp8": g.RSVD_FP8_E4M3}[a.dtype]
     tdt = torch.float64 if a.dtype == "f64" else torch.float32   # element type of Omega, U, V
     gen = torch.Generator(device=dev)
     gen.manual_seed(12085)
     A = torch.randn(a.m, a.n, generator=gen, device=dev, dtype=tdt)
+    sc = None
     if a.dtype == "bf16":  # stored as bfloat16 codes by the library's quantiser
         Aq = torch.empty(a.m, a.n, dtype=torch.int16, device=dev)
         g.check(g.rsvd_quantize(A, g.RSVD_BF16, Aq), "rsvd_quantize")
+        del A
+        A = Aq
+    elif a.dtype == "fp8":  # e4m3 codes and column scales
+        Aq = torch.empty(a.m, a.n, dtype=torch.uint8, device=dev)
+        sc = torch.empty(a.n, dtype=torch.float32, device=dev)
+        g.check(g.rsvd_quantize(A, g.RSVD_FP8_E4M3, Aq, sc), "rsvd_quantize")
         del A
         A = Aq
     k = a.k if a.path != "exact" else a.n
@@ -58,7 +66,7 @@ def main(argv=None) -> int:
         for _ in range(a.repeat):
             if a.path == "rsvd":
                 Om = torch.randn(a.n, a.k + a.p, generator=gen, device=dev, dtype=tdt)
-                g.check(g.rsvd(plan, A, None, Om, S, U, V), "rsvd")
+                g.check(g.rsvd(plan, A, sc, Om, S, U, V), "rsvd")
             elif a.path == "gkl":
                 v1 = torch.randn(a.n, generator=gen, device=dev, dtype=tdt)
                 v1 /= v1.norm()
@@ -71,11 +79,11 @@ def main(argv=None) -> int:
             g.rsvd_plan_profile(plan, False)
             s0 = torch.cuda.current_stream()
             for _ in range(2):
-                g.check(g.rsvd(plan, A, None, Om, S, U, V))
+                g.check(g.rsvd(plan, A, sc, Om, S, U, V))
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(s0)
             for _ in range(a.timed):
-                g.check(g.rsvd(plan, A, None, Om, S, U, V))
+                g.check(g.rsvd(plan, A, sc, Om, S, U, V))
             e1.record(s0)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / a.timed

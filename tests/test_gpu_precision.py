@@ -1,4 +1,4 @@
-"""Precision form: randomized PCA of a bfloat16-stored matrix (RSVD_BF16 plans)
+"""Precision form: randomized PCA of a bfloat16- or e4m3-stored matrix
 against the FP64 oracle run on the same stored matrix (the oracle's own
 bfloat16 encoding of the float32 matrix, dequantised exactly) and the same
 Omega.  The sketch and power products round their small operand to bfloat16,
@@ -91,3 +91,52 @@ def test_bf16_plan_rejects_unsupported_paths():
         assert g.svd_truncated_krylov(plan, A, v1, 16, S, S, S) == g.RSVD_ERR_UNSUPPORTED
         with pytest.raises(g.RsvdError):
             g.rsvd_batch_create([plan])
+
+
+def _stored8(m, n, seed, shift=True):
+    sig = synth.spectrum_power(n, 1.5)
+    A = synth.prescribed(m, n, sig, 40963 + seed, 40964 + seed)
+    if shift:
+        A = A + torch.linspace(-0.05, 0.1, n, dtype=torch.float64).unsqueeze(0)
+    codes, scales = oracle.quantize_e4m3(A.float().numpy())
+    return codes, scales, oracle.dequantize_e4m3(codes, scales)
+
+
+@pytest.mark.parametrize("m,n,k,p,q,shift", [
+    (60000, 512, 48, 16, 3, True),
+    (20011, 256, 20, 12, 2, True),
+    (30000, 1024, 40, 8, 1, False),
+])
+def test_e4m3_rsvd_matches_oracle_on_stored_matrix(m, n, k, p, q, shift):
+    """e4m3 storage: the sketch and power operands are quantised to e4m3 (3 mantissa
+    bits), which perturbs the basis by up to 2^-4 relative per step; the
+    Rayleigh-Ritz product is float32-accurate.  Bounds: sigma within 1e-3 sigma_1,
+    projection gap within 1e-3 ||A||_F (both stated, not derived tight)."""
+    codes, scales, Ad = _stored8(m, n, m % 89, shift)
+    Om = synth.gaussian(n, k + p, seed=40965, dtype=torch.float32)
+    dev = torch.device("cuda")
+    A = torch.from_numpy(codes).to(dev)
+    sc = torch.from_numpy(scales).to(dev)
+    S = torch.zeros(k, dtype=torch.float64, device=dev)
+    U = torch.zeros(m, k, device=dev)
+    V = torch.zeros(n, k, device=dev)
+    with g.rsvd_plan_create(m, n, k, p, q, g.RSVD_FP8_E4M3) as plan:
+        if not shift:
+            g.check(g.rsvd_plan_set_flags(plan, g.RSVD_FLAG_NO_CENTER))
+        assert g.rsvd(plan, A, None, Om.to(dev), S, U, V) == g.RSVD_ERR_ARG    # the scales are required
+        g.check(g.rsvd(plan, A, sc, Om.to(dev), S, U, V), "rsvd e4m3")
+        assert g.rsvd_plan_sync(plan) == g.RSVD_OK
+        fro2 = g.rsvd_plan_fro2(plan)
+        stK, K = g.pca_threshold(plan, 0.9)
+    torch.cuda.synchronize()
+    Ac, mu, fro2o = oracle.center(Ad) if shift else (Ad, None, float(np.sum(Ad * Ad)))
+    assert abs(fro2 - fro2o) <= 1e-6 * fro2o
+    s, Uo, Vo = oracle.rsvd(Ac, Om.double(), q=q, k=k)
+    Sg, Ug, Vg = S.cpu().numpy(), U.cpu().double().numpy(), V.cpu().double().numpy()
+    err = np.abs(Sg - s).max() / s[0]
+    gap = (_proj_residual(Ac, Ug) - _proj_residual(Ac, Uo)) / np.sqrt(np.sum(Ac * Ac))
+    print(f"e4m3 rsvd {m}x{n} k={k}: max sigma error {err:.2e} sigma_1, projection gap {gap:.2e} ||A||_F")
+    assert err <= 1e-3, err
+    assert gap <= 1e-3, gap
+    assert np.abs(Ug.T @ Ug - np.eye(k)).max() <= 1e-5
+    assert np.abs(Vg.T @ Vg - np.eye(k)).max() <= 1e-5
