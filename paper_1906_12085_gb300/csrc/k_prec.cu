@@ -41,6 +41,7 @@ __global__ void colstats16_kernel(const uint16_t *__restrict__ A, int64_t m, int
         for (int64_t g = r0 + ty * 32; g < r1; g += 8 * 32) {  // 32-row groups in float32, then float64
             float fs = 0.f, fq = 0.f;
             const int64_t ge = min(r1, g + 32);
+#pragma unroll 8
             for (int64_t r = g; r < ge; r++) {
                 const float a = bf(A[r * lda + c]);
                 fs += a;
@@ -158,36 +159,52 @@ __device__ __forceinline__ uint8_t e4m3(float x) {
     return (uint8_t)(d & 0xFF);
 }
 
+// 4 consecutive columns per thread (one 4-byte load per row; n and lda multiples of 4)
 __global__ void colstats8_kernel(const uint8_t *__restrict__ A, int64_t m, int64_t n, int64_t lda, int64_t rpb,
                                  double *__restrict__ psum, double *__restrict__ psq) {
-    __shared__ double rs[8][33], rq[8][33];
+    __shared__ double rs[8][128], rq[8][128];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int64_t c = (int64_t)blockIdx.x * 32 + tx;
+    const int64_t c = (int64_t)blockIdx.x * 128 + 4 * tx;
     const int64_t r0 = (int64_t)blockIdx.y * rpb, r1 = min(m, r0 + rpb);
-    double s = 0.0, q = 0.0;
+    double s[4] = {0.0, 0.0, 0.0, 0.0}, q[4] = {0.0, 0.0, 0.0, 0.0};
     if (c < n) {
         for (int64_t g = r0 + ty * 32; g < r1; g += 8 * 32) {
-            float fs = 0.f, fq = 0.f;
+            float fs[4] = {0.f, 0.f, 0.f, 0.f}, fq[4] = {0.f, 0.f, 0.f, 0.f};
             const int64_t ge = min(r1, g + 32);
+#pragma unroll 8
             for (int64_t r = g; r < ge; r++) {
-                const float a = f8(A[r * lda + c]);
-                fs += a;
-                fq = fmaf(a, a, fq);
+                const uint32_t w = *reinterpret_cast<const uint32_t *>(A + r * lda + c);
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    const float a = f8((uint8_t)(w >> (8 * e)));
+                    fs[e] += a;
+                    fq[e] = fmaf(a, a, fq[e]);
+                }
             }
-            s += fs;
-            q += fq;
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                s[e] += fs[e];
+                q[e] += fq[e];
+            }
         }
     }
-    rs[ty][tx] = s;
-    rq[ty][tx] = q;
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        rs[ty][4 * tx + e] = s[e];
+        rq[ty][4 * tx + e] = q[e];
+    }
     __syncthreads();
     if (ty == 0 && c < n) {
-        for (int k = 1; k < 8; k++) {
-            s += rs[k][tx];
-            q += rq[k][tx];
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            double a = rs[0][4 * tx + e], b = rq[0][4 * tx + e];
+            for (int k = 1; k < 8; k++) {
+                a += rs[k][4 * tx + e];
+                b += rq[k][4 * tx + e];
+            }
+            psum[(int64_t)blockIdx.y * n + c + e] = a;
+            psq[(int64_t)blockIdx.y * n + c + e] = b;
         }
-        psum[(int64_t)blockIdx.y * n + c] = s;
-        psq[(int64_t)blockIdx.y * n + c] = q;
     }
 }
 
@@ -295,9 +312,20 @@ __global__ void quant_q_kernel(const float *__restrict__ Q, int64_t rows, int lp
     if (ry == 0 && j < lp) part[(int64_t)blockIdx.x * lp + j] = red[0][j] + red[1][j];
 }
 
+// 16 codes per thread (one 16-byte load, two 16-byte stores); a scalar tail
 __global__ void e4m3_to_bf16_kernel(const uint8_t *__restrict__ A, int64_t total, uint16_t *__restrict__ B) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < total) B[i] = rbf(f8(A[i]));
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 16;
+    if (i + 16 <= total) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(A + i);
+        const uint8_t *c = reinterpret_cast<const uint8_t *>(&v);
+        uint32_t o[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) o[k] = (uint32_t)rbf(f8(c[2 * k])) | ((uint32_t)rbf(f8(c[2 * k + 1])) << 16);
+        *reinterpret_cast<uint4 *>(B + i) = make_uint4(o[0], o[1], o[2], o[3]);
+        *reinterpret_cast<uint4 *>(B + i + 8) = make_uint4(o[4], o[5], o[6], o[7]);
+    } else {
+        for (int64_t j = i; j < total; j++) B[j] = rbf(f8(A[j]));
+    }
 }
 
 }  // namespace
@@ -307,8 +335,9 @@ cudaError_t colstats8(const void *A, int64_t m, int64_t n, int64_t lda, bool cen
     const int64_t nch = colstats16_chunks(m);
     const int64_t rpb = round_up(ceil_div(m, nch), 32);
     const int64_t ch = ceil_div(m, rpb);
-    colstats8_kernel<<<dim3((unsigned)ceil_div(n, 32), (unsigned)ch), 256, 0, s>>>(static_cast<const uint8_t *>(A), m,
-                                                                                   n, lda, rpb, psum, psq);
+    if (n % 4 || lda % 4 || (reinterpret_cast<uintptr_t>(A) & 3)) return cudaErrorInvalidValue;
+    colstats8_kernel<<<dim3((unsigned)ceil_div(n, 128), (unsigned)ch), 256, 0, s>>>(static_cast<const uint8_t *>(A),
+                                                                                    m, n, lda, rpb, psum, psq);
     colstats8_finish<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(psum, psq, (int)ch, m, n, center, scales, mu, mu_f,
                                                                 colv);
     note_launch(2);
@@ -338,8 +367,9 @@ cudaError_t prep8_q(const float *Q, int64_t rows, int lp, void *Qq, float *u, fl
 }
 
 cudaError_t e4m3_to_bf16(const void *A, int64_t count, void *B, cudaStream_t s) {
-    e4m3_to_bf16_kernel<<<(unsigned)ceil_div(count, 256), 256, 0, s>>>(static_cast<const uint8_t *>(A), count,
-                                                                       static_cast<uint16_t *>(B));
+    if ((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15)) return cudaErrorInvalidValue;
+    e4m3_to_bf16_kernel<<<(unsigned)ceil_div(ceil_div(count, 16), 256), 256, 0, s>>>(
+        static_cast<const uint8_t *>(A), count, static_cast<uint16_t *>(B));
     note_launch();
     return cudaGetLastError();
 }

@@ -602,19 +602,41 @@ __global__ void pca_select_kernel(const double *__restrict__ sigma, int count, c
     *reached = 0;
 }
 
+// Register blocks per thread side of the Cholesky kernel (l <= 16 LB): float64 takes
+// the smallest block that covers l (its 8 x 8 block spills), float32 4 or 8.
+int chol_lb(int l, size_t tk) {
+    if (l <= 64) return 4;
+    if (tk == 8 && l <= 96) return 6;
+    if (tk == 8 && l <= 112) return 7;
+    return 8;
+}
+
+// One problem (tab == nullptr) or a batch of `count` problems from a device table.
+template <typename TG, typename Tk, typename Tc, int LB>
+void launch_chol(const CholTab *tab, int count, const TG *G, int64_t ldg, int l, double coef, double *R, double *Rinv,
+                 Tc *Rinv_c, int lp, int *status, cudaStream_t s) {
+    const size_t smem = sizeof(Tk) * ((size_t)l * l + 2 * 16 * LB);
+    if (tab) {
+        cudaFuncSetAttribute(chol_inv_batch_kernel<TG, Tk, Tc, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        chol_inv_batch_kernel<TG, Tk, Tc, LB><<<count, 256, smem, s>>>(tab, ldg, l, lp);
+    } else {
+        cudaFuncSetAttribute(chol_inv_kernel<TG, Tk, Tc, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        chol_inv_kernel<TG, Tk, Tc, LB><<<1, 256, smem, s>>>(G, ldg, l, coef, R, Rinv, Rinv_c, lp, status);
+    }
+}
+
 }  // namespace
 
 template <typename TG, typename Tk, typename Tc>
 cudaError_t chol_inv(const TG *G, int64_t ldg, int l, int64_t rows, double u, double *R, double *Rinv, Tc *Rinv_c,
                      int lp, int *status, cudaStream_t s) {
     const double coef = chol_shift_coef(rows, l, u);
-    if (l <= 64) {
-        const size_t smem = sizeof(Tk) * ((size_t)l * l + 2 * 64);
-        chol_inv_kernel<TG, Tk, Tc, 4><<<1, 256, smem, s>>>(G, ldg, l, coef, R, Rinv, Rinv_c, lp, status);
-    } else {
-        const size_t smem = sizeof(Tk) * ((size_t)l * l + 2 * 128);
-        cudaFuncSetAttribute(chol_inv_kernel<TG, Tk, Tc, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        chol_inv_kernel<TG, Tk, Tc, 8><<<1, 256, smem, s>>>(G, ldg, l, coef, R, Rinv, Rinv_c, lp, status);
+    switch (chol_lb(l, sizeof(Tk))) {
+        case 4: launch_chol<TG, Tk, Tc, 4>(nullptr, 1, G, ldg, l, coef, R, Rinv, Rinv_c, lp, status, s); break;
+        case 6: launch_chol<TG, Tk, Tc, 6>(nullptr, 1, G, ldg, l, coef, R, Rinv, Rinv_c, lp, status, s); break;
+        case 7: launch_chol<TG, Tk, Tc, 7>(nullptr, 1, G, ldg, l, coef, R, Rinv, Rinv_c, lp, status, s); break;
+        default: launch_chol<TG, Tk, Tc, 8>(nullptr, 1, G, ldg, l, coef, R, Rinv, Rinv_c, lp, status, s); break;
     }
     note_launch();
     return cudaGetLastError();
@@ -623,14 +645,11 @@ cudaError_t chol_inv(const TG *G, int64_t ldg, int l, int64_t rows, double u, do
 template <typename TG, typename Tk, typename Tc>
 cudaError_t chol_inv_batched(const CholTab *tab, int count, int64_t ldg, int l, int lp, cudaStream_t s) {
     if (count < 1) return cudaSuccess;
-    if (l <= 64) {
-        const size_t smem = sizeof(Tk) * ((size_t)l * l + 2 * 64);
-        chol_inv_batch_kernel<TG, Tk, Tc, 4><<<count, 256, smem, s>>>(tab, ldg, l, lp);
-    } else {
-        const size_t smem = sizeof(Tk) * ((size_t)l * l + 2 * 128);
-        cudaFuncSetAttribute(chol_inv_batch_kernel<TG, Tk, Tc, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        chol_inv_batch_kernel<TG, Tk, Tc, 8><<<count, 256, smem, s>>>(tab, ldg, l, lp);
+    switch (chol_lb(l, sizeof(Tk))) {
+        case 4: launch_chol<TG, Tk, Tc, 4>(tab, count, nullptr, ldg, l, 0.0, nullptr, nullptr, nullptr, lp, nullptr, s); break;
+        case 6: launch_chol<TG, Tk, Tc, 6>(tab, count, nullptr, ldg, l, 0.0, nullptr, nullptr, nullptr, lp, nullptr, s); break;
+        case 7: launch_chol<TG, Tk, Tc, 7>(tab, count, nullptr, ldg, l, 0.0, nullptr, nullptr, nullptr, lp, nullptr, s); break;
+        default: launch_chol<TG, Tk, Tc, 8>(tab, count, nullptr, ldg, l, 0.0, nullptr, nullptr, nullptr, lp, nullptr, s); break;
     }
     note_launch();
     return cudaGetLastError();
