@@ -320,7 +320,7 @@ rsvd_status rsvd_tune_lookup(int64_t m, int64_t n, int k, int p, int *nn_ctas, i
 void rsvd_tune_clear(void);
 
 /*
- * Serving loop: continuous batching of float32 randomized PCA requests.
+ * Serving loop: continuous batching of randomized PCA requests.
  *   rsvd_server_create: one device arena of `hbm_bytes` (cudaMalloc'd once)
  *     holds every admitted request's plan workspace; at most `max_inflight`
  *     batches run at once, each of at most `max_batch` requests, on streams
@@ -352,6 +352,14 @@ typedef struct {
 rsvd_status rsvd_server_create(rsvd_server_t *server, size_t hbm_bytes, int max_batch, int max_inflight);
 rsvd_status rsvd_server_submit(rsvd_server_t server, int64_t id, int64_t m, int64_t n, int k, int p, int q,
                                double t, const float *A, const float *Omega, double *S, float *U, float *V);
+/* rsvd_server_submit for a stored matrix of any rsvd storage type: RSVD_F32,
+ * RSVD_BF16 or RSVD_FP8_E4M3 (with its n column scales; NULL otherwise).
+ * Omega, U, V are float.  Requests batch only with requests of the same type;
+ * the precision forms' batches run their solves concurrently (one stream per
+ * request) rather than in lockstep. */
+rsvd_status rsvd_server_submit_ex(rsvd_server_t server, int64_t id, int64_t m, int64_t n, int k, int p, int q,
+                                  rsvd_dtype dtype, double t, const void *A, const float *col_scales,
+                                  const float *Omega, double *S, float *U, float *V);
 int rsvd_server_poll(rsvd_server_t server, rsvd_completion *out, int max_out);
 int rsvd_server_pending(rsvd_server_t server);
 rsvd_status rsvd_server_destroy(rsvd_server_t server);

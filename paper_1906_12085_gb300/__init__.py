@@ -26,7 +26,7 @@ __all__ = [
     "rsvd_plan_create_in", "Batch", "rsvd_batch_create", "rsvd_batch_run", "rsvd_batch_sync",
     "rsvd_batch_destroy", "Server", "rsvd_server_create", "rsvd_server_submit", "rsvd_server_poll",
     "rsvd_server_pending", "rsvd_server_destroy", "rsvd_autotune", "rsvd_tune_lookup", "rsvd_tune_clear",
-    "rsvd_quantize",
+    "rsvd_quantize", "rsvd_server_submit_ex",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -105,6 +105,7 @@ def lib() -> ctypes.CDLL:
     L.rsvd_server_create.argtypes = [ctypes.POINTER(vp), sz, i32, i32]
     L.rsvd_server_submit.argtypes = [vp, i64, i64, i64, i32, i32, i32, ctypes.c_double, vp, vp, vp, vp, vp]
     L.rsvd_server_poll.argtypes = [vp, ctypes.POINTER(Completion), i32]
+    L.rsvd_server_submit_ex.argtypes = [vp, i64, i64, i64, i32, i32, i32, i32, ctypes.c_double, vp, vp, vp, vp, vp, vp]
     L.rsvd_server_pending.argtypes = [vp]
     L.rsvd_server_destroy.argtypes = [vp]
     L.rsvd_autotune.argtypes = [vp, vp, vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
@@ -117,7 +118,7 @@ def lib() -> ctypes.CDLL:
               "rsvd_plan_profile_read", "rsvd_workspace_query", "rsvd_plan_create_in", "rsvd_batch_create",
               "rsvd_batch_run", "rsvd_batch_sync", "rsvd_batch_destroy", "rsvd_server_create",
               "rsvd_server_submit", "rsvd_server_poll", "rsvd_server_pending", "rsvd_server_destroy",
-              "rsvd_autotune", "rsvd_tune_lookup", "rsvd_quantize"):
+              "rsvd_autotune", "rsvd_tune_lookup", "rsvd_quantize", "rsvd_server_submit_ex"):
         getattr(L, f).restype = i32
     _lib = L
     return L
@@ -380,6 +381,13 @@ def rsvd_server_submit(server: Server, rid: int, k: int, p: int, q: int, t: floa
     m, n = A.shape
     return lib().rsvd_server_submit(server.handle, int(rid), m, n, k, p, q, float(t), _ptr(A), _ptr(Omega), _ptr(S),
                                     _ptr(U), _ptr(V))
+
+
+def rsvd_server_submit_ex(server: Server, rid: int, k: int, p: int, q: int, dtype: int, t: float, A, col_scales,
+                          Omega, S, U, V) -> int:
+    m, n = A.shape
+    return lib().rsvd_server_submit_ex(server.handle, int(rid), m, n, k, p, q, int(dtype), float(t), _ptr(A),
+                                       _ptr(col_scales), _ptr(Omega), _ptr(S), _ptr(U), _ptr(V))
 
 
 def rsvd_server_poll(server: Server, max_out: int = 256) -> list[dict]:

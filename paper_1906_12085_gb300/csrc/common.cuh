@@ -144,15 +144,16 @@ cudaError_t prep8_q(const float *Q, int64_t rows, int lp, void *Qq, float *u, fl
 cudaError_t e4m3_to_bf16(const void *A, int64_t count, void *B, cudaStream_t s);
 
 // Serving interface of plan.cu (used by server.cu): a batch context on stream bs
-// for up to `cap` problems, and one launch of a float32 batch followed, per
+// for up to `cap` problems, and one launch of a batch (float32: lockstep; the
+// bfloat16 / e4m3 forms: concurrent solves on the problems' streams) followed, per
 // problem, by the Sec. 2.4 K selection and an asynchronous copy of three ints
 // (status bits, K, reached) to host_out + 3 i (pinned memory).
 struct ServeBatch;
 ServeBatch *serve_batch_new(cudaStream_t bs, int cap);
 void serve_batch_free(ServeBatch *b);
-rsvd_status serve_batch_launch(ServeBatch *b, int count, rsvd_plan_t const *plans, const float *const *A,
-                               const float *const *Om, double *const *S, float *const *U, float *const *V,
-                               const double *t, int *host_out);
+rsvd_status serve_batch_launch(ServeBatch *b, int count, rsvd_plan_t const *plans, const void *const *A,
+                               const float *const *sc, const float *const *Om, double *const *S, float *const *U,
+                               float *const *V, const double *t, int *host_out);
 rsvd_status serve_status(int bits, int reached);
 
 // Batched forms: one launch solves `count` independent problems of the same l, lp;

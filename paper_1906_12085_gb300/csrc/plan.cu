@@ -1005,12 +1005,24 @@ ServeBatch *serve_batch_new(cudaStream_t bs, int cap) {
 
 void serve_batch_free(ServeBatch *b) { delete b; }
 
-rsvd_status serve_batch_launch(ServeBatch *b, int count, rsvd_plan *const *plans, const float *const *A,
-                               const float *const *Om, double *const *S, float *const *U, float *const *V,
-                               const double *t, int *host_out) {
-    const rsvd_status st = batch_direct(b->ctx, count, plans, (void *const *)A, (const void *const *)Om, S,
-                                        (void *const *)U, (void *const *)V);
-    if (st != RSVD_OK) return st;
+rsvd_status serve_batch_launch(ServeBatch *b, int count, rsvd_plan *const *plans, const void *const *A,
+                               const float *const *sc, const float *const *Om, double *const *S, float *const *U,
+                               float *const *V, const double *t, int *host_out) {
+    const rsvd_dtype dt = plans[0]->dtype;
+    if (dt == RSVD_F32 || dt == RSVD_F64) {  // lockstep batch
+        const rsvd_status st = batch_direct(b->ctx, count, plans, (void *const *)A, (const void *const *)Om, S,
+                                            (void *const *)U, (void *const *)V);
+        if (st != RSVD_OK) return st;
+    } else {  // precision forms: every problem's solve on its own stream, then joined
+        CK(b->ctx.reserve(count));
+        CK(fork(b->ctx, count, plans));
+        for (int i = 0; i < count; i++) {
+            const rsvd_status st = rsvd_direct(plans[i], const_cast<void *>(A[i]), sc ? sc[i] : nullptr, Om[i], S[i],
+                                               U[i], V[i]);
+            if (st != RSVD_OK) return st;
+        }
+        CK(join(b->ctx, count, plans));
+    }
     cudaStream_t bs = b->ctx.bs;
     for (int i = 0; i < count; i++) {  // K selection and the three result words per problem
         rsvd_plan *P = plans[i];

@@ -1,13 +1,13 @@
-// Serving loop for float32 randomized PCA requests (include/rsvd.h,
-// rsvd_server_*): continuous batching with HBM admission.
+// Serving loop for randomized PCA requests (include/rsvd.h, rsvd_server_*):
+// continuous batching with HBM admission.
 //
 // One device arena (cudaMalloc'd once) holds the plan workspaces of admitted
 // requests; the first-fit Arena tracks it.  Requests wait in arrival order.
 // Every poll first retires batches whose completion event has fired (their
 // workspaces return to the arena), then admits from the head of the queue:
 // a batch takes the oldest waiting request and the requests queued directly
-// behind it that share its l and q, while their workspaces fit and the batch
-// is not full.  The head is never skipped (no starvation of large requests).
+// behind it that share its l, q and storage type, while their workspaces fit
+// and the batch is not full.  The head is never skipped (no starvation of large requests).
 // Each batch runs on a slot of its own (a batch stream, one stream per problem,
 // pinned result words, a completion event), so batches admitted while others
 // run overlap on the device.
@@ -28,8 +28,10 @@ using Clock = std::chrono::steady_clock;
 struct Request {
     int64_t id, m, n;
     int k, p, q;
+    rsvd_dtype dtype;
     double t;
-    const float *A, *Om;
+    const void *A;
+    const float *sc, *Om;
     double *S;
     float *U, *V;
     size_t ws;
@@ -124,9 +126,10 @@ bool admit_one(rsvd_server *S, rsvd_status *err) {
     run.slot = si;
     const Request &head = S->queue.front();
     const int l = head.k + head.p, q = head.q;
+    const rsvd_dtype dt = head.dtype;
     while (!S->queue.empty() && (int)run.reqs.size() < S->max_batch) {
         const Request &rq = S->queue.front();
-        if (rq.k + rq.p != l || rq.q != q) break;
+        if (rq.k + rq.p != l || rq.q != q || rq.dtype != dt) break;
         size_t off = 0;
         if (!S->arena.alloc(rq.ws, &off)) break;
         run.reqs.push_back(rq);
@@ -135,14 +138,15 @@ bool admit_one(rsvd_server *S, rsvd_status *err) {
     }
     if (run.reqs.empty()) return false;
     const int count = (int)run.reqs.size();
-    std::vector<const float *> A(count), Om(count);
+    std::vector<const void *> A(count);
+    std::vector<const float *> Om(count), Sc(count);
     std::vector<double *> Sg(count);
     std::vector<float *> U(count), V(count);
     std::vector<double> t(count);
     for (int i = 0; i < count; i++) {
         const Request &rq = run.reqs[i];
         rsvd_plan_t P = nullptr;
-        rsvd_status st = rsvd_plan_create_in(&P, rq.m, rq.n, rq.k, rq.p, rq.q, RSVD_F32, slot.ps[i],
+        rsvd_status st = rsvd_plan_create_in(&P, rq.m, rq.n, rq.k, rq.p, rq.q, rq.dtype, slot.ps[i],
                                              S->base + run.offs[i], rq.ws);
         if (st != RSVD_OK) {  // the whole batch fails with this status (nothing was launched)
             const double now = S->now_ms();
@@ -155,6 +159,7 @@ bool admit_one(rsvd_server *S, rsvd_status *err) {
         }
         run.plans.push_back(P);
         A[i] = rq.A;
+        Sc[i] = rq.sc;
         Om[i] = rq.Om;
         Sg[i] = rq.S;
         U[i] = rq.U;
@@ -162,8 +167,8 @@ bool admit_one(rsvd_server *S, rsvd_status *err) {
         t[i] = rq.t;
     }
     run.start_ms = S->now_ms();
-    rsvd_status st = gbr::serve_batch_launch(slot.sb, count, run.plans.data(), A.data(), Om.data(), Sg.data(),
-                                             U.data(), V.data(), t.data(), slot.host_out);
+    rsvd_status st = gbr::serve_batch_launch(slot.sb, count, run.plans.data(), A.data(), Sc.data(), Om.data(),
+                                             Sg.data(), U.data(), V.data(), t.data(), slot.host_out);
     if (st == RSVD_OK && cudaEventRecord(slot.done, slot.bs) != cudaSuccess) st = RSVD_ERR_CUDA;
     if (st != RSVD_OK) {
         *err = st;
@@ -215,15 +220,23 @@ rsvd_status rsvd_server_create(rsvd_server_t *server, size_t hbm_bytes, int max_
     return RSVD_OK;
 }
 
-rsvd_status rsvd_server_submit(rsvd_server_t S, int64_t id, int64_t m, int64_t n, int k, int p, int q, double t,
-                               const float *A, const float *Omega, double *Sg, float *U, float *V) {
+rsvd_status rsvd_server_submit_ex(rsvd_server_t S, int64_t id, int64_t m, int64_t n, int k, int p, int q,
+                                  rsvd_dtype dtype, double t, const void *A, const float *col_scales,
+                                  const float *Omega, double *Sg, float *U, float *V) {
     if (!S || !A || !Omega || !Sg || !U || !V || !(t > 0.0) || t > 1.0) return RSVD_ERR_ARG;
+    if (dtype == RSVD_F64) return RSVD_ERR_UNSUPPORTED;                   // float32 outputs only
+    if ((col_scales != nullptr) != (dtype == RSVD_FP8_E4M3)) return RSVD_ERR_ARG;
     size_t ws = 0;
-    const rsvd_status st = rsvd_workspace_query(m, n, k, p, q, RSVD_F32, &ws);
+    const rsvd_status st = rsvd_workspace_query(m, n, k, p, q, dtype, &ws);
     if (st != RSVD_OK) return st;
     if (gbr::Arena::round(ws) > S->arena.size()) return RSVD_ERR_OOM;
-    S->queue.push_back(Request{id, m, n, k, p, q, t, A, Omega, Sg, U, V, ws, S->now_ms()});
+    S->queue.push_back(Request{id, m, n, k, p, q, dtype, t, A, col_scales, Omega, Sg, U, V, ws, S->now_ms()});
     return RSVD_OK;
+}
+
+rsvd_status rsvd_server_submit(rsvd_server_t S, int64_t id, int64_t m, int64_t n, int k, int p, int q, double t,
+                               const float *A, const float *Omega, double *Sg, float *U, float *V) {
+    return rsvd_server_submit_ex(S, id, m, n, k, p, q, RSVD_F32, t, A, nullptr, Omega, Sg, U, V);
 }
 
 int rsvd_server_poll(rsvd_server_t S, rsvd_completion *out, int max_out) {

@@ -100,3 +100,83 @@ def test_server_rejects_request_larger_than_arena():
         V = torch.zeros(n, k, device=dev)
         assert g.rsvd_server_submit(srv, 0, k, p, Q, 0.9, A, Om, S, U, V) == g.RSVD_ERR_OOM
         assert g.rsvd_server_pending(srv) == 0
+
+
+def _quantized(r, dtype):
+    """The request's matrix stored in `dtype` by the library's quantiser (device)."""
+    dev = torch.device("cuda")
+    A = r["A"].to(dev)
+    if dtype == g.RSVD_F32:
+        return A, None
+    if dtype == g.RSVD_BF16:
+        Aq = torch.empty(r["m"], r["n"], dtype=torch.int16, device=dev)
+        g.check(g.rsvd_quantize(A, dtype, Aq), "quantize")
+        return Aq, None
+    Aq = torch.empty(r["m"], r["n"], dtype=torch.uint8, device=dev)
+    sc = torch.empty(r["n"], device=dev)
+    g.check(g.rsvd_quantize(A, dtype, Aq, sc), "quantize")
+    return Aq, sc
+
+
+def test_served_mixed_storage_types_equal_alone_bitwise():
+    """float32, bfloat16 and e4m3 requests interleaved: a batch holds one storage
+    type (consecutive requests of the same l, q and type); the precision forms'
+    batches run their solves concurrently, each bit-identical to a solve alone."""
+    reqs = _requests(18, 11)
+    types = [g.RSVD_BF16, g.RSVD_BF16, g.RSVD_FP8_E4M3, g.RSVD_FP8_E4M3, g.RSVD_F32, g.RSVD_BF16]
+    dev = torch.device("cuda")
+    alone = {}
+    for i, r in enumerate(reqs):
+        r["k"], r["p"] = 16, 8                      # one l: batches are cut by type alone
+        r["Om"] = synth.gaussian(r["n"], 24, seed=5000 + i, dtype=torch.float32)
+        r["dt"] = types[i % len(types)]
+        r["Aq"], r["sc"] = _quantized(r, r["dt"])
+        r["Od"] = r["Om"].to(dev)
+        S = torch.zeros(r["k"], dtype=torch.float64, device=dev)
+        U = torch.zeros(r["m"], r["k"], device=dev)
+        V = torch.zeros(r["n"], r["k"], device=dev)
+        with g.rsvd_plan_create(r["m"], r["n"], r["k"], r["p"], Q, r["dt"]) as plan:
+            g.check(g.rsvd(plan, r["Aq"], r["sc"], r["Od"], S, U, V))
+            st = g.rsvd_plan_sync(plan)
+            stK, K = g.pca_threshold(plan, 0.9)
+        alone[r["id"]] = ((stK if st == g.RSVD_OK else st), K, S.cpu().numpy(), U.cpu().numpy(), V.cpu().numpy())
+        r["S"] = torch.zeros(r["k"], dtype=torch.float64, device=dev)
+        r["U"] = torch.zeros(r["m"], r["k"], device=dev)
+        r["V"] = torch.zeros(r["n"], r["k"], device=dev)
+    ws = max(g.rsvd_workspace_query(r["m"], r["n"], r["k"], r["p"], Q, r["dt"])[1] for r in reqs)
+    torch.cuda.synchronize()
+    done = []
+    with g.rsvd_server_create(4 * ws, max_batch=4, max_inflight=3) as srv:
+        for i, r in enumerate(reqs):
+            g.check(g.rsvd_server_submit_ex(srv, r["id"], r["k"], r["p"], Q, r["dt"], 0.9, r["Aq"], r["sc"], r["Od"],
+                                            r["S"], r["U"], r["V"]), "submit")
+        while g.rsvd_server_pending(srv) > 0:
+            done += g.rsvd_server_poll(srv)
+    torch.cuda.synchronize()
+    assert sorted(c["id"] for c in done) == [r["id"] for r in reqs]
+    assert any(c["batch"] > 1 for c in done)
+    for c in done:
+        r = reqs[c["id"]]
+        a_st, a_K, a_S, a_U, a_V = alone[c["id"]]
+        assert c["status"] == a_st and c["K"] == a_K, (c, r["dt"])
+        assert np.array_equal(r["S"].cpu().numpy(), a_S), r["dt"]
+        assert np.array_equal(r["U"].cpu().numpy(), a_U), r["dt"]
+        assert np.array_equal(r["V"].cpu().numpy(), a_V), r["dt"]
+
+
+def test_server_submit_ex_checks_scales():
+    dev = torch.device("cuda")
+    m, n, k, p = 4000, 64, 8, 8
+    Aq = torch.zeros(m, n, dtype=torch.uint8, device=dev)
+    sc = torch.ones(n, device=dev)
+    Om = torch.zeros(n, k + p, device=dev)
+    S = torch.zeros(k, dtype=torch.float64, device=dev)
+    U = torch.zeros(m, k, device=dev)
+    V = torch.zeros(n, k, device=dev)
+    with g.rsvd_server_create(1 << 28, max_batch=2, max_inflight=1) as srv:
+        assert g.rsvd_server_submit_ex(srv, 0, k, p, Q, g.RSVD_FP8_E4M3, 0.9, Aq, None, Om, S, U, V) == g.RSVD_ERR_ARG
+        A16 = torch.zeros(m, n, dtype=torch.int16, device=dev)
+        assert g.rsvd_server_submit_ex(srv, 1, k, p, Q, g.RSVD_BF16, 0.9, A16, sc, Om, S, U, V) == g.RSVD_ERR_ARG
+        assert g.rsvd_server_submit_ex(srv, 2, k, p, Q, g.RSVD_F64, 0.9, Aq, None, Om, S, U, V) \
+            == g.RSVD_ERR_UNSUPPORTED
+        assert g.rsvd_server_pending(srv) == 0
