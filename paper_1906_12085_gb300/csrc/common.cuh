@@ -130,6 +130,7 @@ cudaError_t to_bf16_t(const float *Z, int64_t n, int l, int64_t ldzin, int lp, v
                       const double *mu, float *c, cudaStream_t s);
 // Q -> nq (1 or 3) bfloat16 terms and their column sums qsum (part: split_bf16_chunks(rows) x lp doubles)
 int64_t split_bf16_chunks(int64_t rows);
+int64_t q_chunk_rows(int64_t rows);
 cudaError_t split_bf16(const float *Q, int64_t rows, int lp, int nq, void *Q1, void *Q2, void *Q3, double *part,
                        double *qsum, cudaStream_t s);
 

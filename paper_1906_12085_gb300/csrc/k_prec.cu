@@ -8,16 +8,19 @@
 //   split_bf16 : Q (m x lp float32) -> one bfloat16 term, or three whose sum
 //                carries Q to float32 accuracy (hi = round(Q), mid = round(Q - hi),
 //                lo = round(Q - hi - mid), each difference exact in float32), and
-//                the column sums of the terms (float64) for the mean correction.
+//                the column sums of the terms (compensated float32 per thread, then
+//                float64) for the mean correction.
 // and their e4m3 counterparts (the stored matrix is A_q diag(s)):
 //   colstats8  : means and ||A - 1 mu^T||_F^2 of A_q diag(s);
 //   prep8_small: Zq = e4m3(diag(s) Z diag(1/t)) transposed, t_j = amax_i |s_i Z_ij| / 448,
 //                and c_j = t_j sum_i (mu_i / s_i) Zq_ij (the product uses exactly
 //                Z_eff = diag(1/s) Zq diag(t), so c = mu^T Z_eff);
 //   prep8_q    : Qq = e4m3(Q diag(1/u)), u_j = amax_r |Q_rj| / 448, and
-//                qsum_j = u_j sum_r Qq_rj;
+//                qsum_j = u_j sum_r Qq_rj (code sums exact in integers);
 //   e4m3_to_bf16: the codes as bfloat16 (exact: every e4m3 value is a bfloat16).
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 
@@ -104,20 +107,39 @@ __global__ void mean_corr_kernel(const double *__restrict__ mu, const uint16_t *
     if (lane == 0) c[j] = (float)s;
 }
 
+// The per-column passes over Q (rows x lp, lp <= 128) run 256 threads per row
+// chunk as G = 256 / CW row groups of CW = lp rounded up to 32 columns.
+__device__ __forceinline__ void q_layout(int lp, int &j, int &ry, int &G) {
+    const int cw = (lp + 31) & ~31;
+    G = 256 / cw;
+    j = threadIdx.x % cw;
+    ry = threadIdx.x / cw;
+}
+
+// s + c += x with the rounding error of every addition carried in c (Neumaier):
+// |s + c - sum x| stays at float32 rounding of the total, not of every step
+__device__ __forceinline__ void nsum(float &s, float &c, float x) {
+    const float t = s + x;
+    c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+}
+
 // Q (rows x lp) -> nq bfloat16 terms; per row chunk the column sums of the terms
+// (compensated float32 per thread, float64 across the row groups in a fixed order)
 __global__ void split_bf16_kernel(const float *__restrict__ Q, int64_t rows, int lp, int nq, uint16_t *__restrict__ Q1,
                                   uint16_t *__restrict__ Q2, uint16_t *__restrict__ Q3, int64_t rpb,
                                   double *__restrict__ part) {
-    __shared__ double red[2][128];
-    const int j = threadIdx.x & 127, ry = threadIdx.x >> 7;  // 128 columns x 2 row groups (256 threads)
+    __shared__ double red[256];
+    int j, ry, G;
+    q_layout(lp, j, ry, G);
     const int64_t r0 = (int64_t)blockIdx.x * rpb, r1 = min(rows, r0 + rpb);
-    double s = 0.0;
-    if (j < lp) {
-        for (int64_t r = r0 + ry; r < r1; r += 2) {
+    float s = 0.f, c = 0.f;
+    if (j < lp && ry < G) {
+        for (int64_t r = r0 + ry; r < r1; r += G) {
             const float x = Q[r * lp + j];
             const uint16_t h = rbf(x);
-            float sum = bf(h);
             Q1[r * lp + j] = h;
+            nsum(s, c, bf(h));
             if (nq == 3) {
                 const float d1 = x - bf(h);          // exact
                 const uint16_t mid = rbf(d1);
@@ -125,15 +147,19 @@ __global__ void split_bf16_kernel(const float *__restrict__ Q, int64_t rows, int
                 const uint16_t lo = rbf(d2);
                 Q2[r * lp + j] = mid;
                 Q3[r * lp + j] = lo;
-                s += (double)sum + (double)bf(mid) + (double)bf(lo);
-            } else {
-                s += (double)sum;
+                nsum(s, c, bf(mid));
+                nsum(s, c, bf(lo));
             }
         }
     }
-    red[ry][j] = s;
+    red[threadIdx.x] = (double)s + (double)c;
     __syncthreads();
-    if (ry == 0 && j < lp) part[(int64_t)blockIdx.x * lp + j] = red[0][j] + red[1][j];
+    if (ry == 0 && j < lp) {
+        const int cw = (lp + 31) & ~31;
+        double a = red[j];
+        for (int g = 1; g < G; g++) a += red[g * cw + j];
+        part[(int64_t)blockIdx.x * lp + j] = a;
+    }
 }
 
 // qsum[j] = sum over chunks (in order)
@@ -269,18 +295,23 @@ __global__ void prep8_small_kernel(const float *__restrict__ Z, int64_t n, int l
     }
 }
 
-// column maxima of Q (rows x lp), partial over row chunks (128 columns x 2 row groups per block)
+// column maxima of Q (rows x lp), partial over row chunks
 __global__ void colmax_q_kernel(const float *__restrict__ Q, int64_t rows, int lp, int64_t rpb,
                                 float *__restrict__ part) {
-    __shared__ float red[2][128];
-    const int j = threadIdx.x & 127, ry = threadIdx.x >> 7;
+    __shared__ float red[256];
+    int j, ry, G;
+    q_layout(lp, j, ry, G);
     const int64_t r0 = (int64_t)blockIdx.x * rpb, r1 = min(rows, r0 + rpb);
     float mx = 0.f;
-    if (j < lp)
-        for (int64_t r = r0 + ry; r < r1; r += 2) mx = fmaxf(mx, fabsf(Q[r * lp + j]));
-    red[ry][j] = mx;
+    if (j < lp && ry < G)
+        for (int64_t r = r0 + ry; r < r1; r += G) mx = fmaxf(mx, fabsf(Q[r * lp + j]));
+    red[threadIdx.x] = mx;
     __syncthreads();
-    if (ry == 0 && j < lp) part[(int64_t)blockIdx.x * lp + j] = fmaxf(red[0][j], red[1][j]);
+    if (ry == 0 && j < lp) {
+        const int cw = (lp + 31) & ~31;
+        for (int g = 1; g < G; g++) mx = fmaxf(mx, red[g * cw + j]);
+        part[(int64_t)blockIdx.x * lp + j] = mx;
+    }
 }
 
 __global__ void colmax_finish(const float *__restrict__ part, int nch, int lp, float *__restrict__ u) {
@@ -291,25 +322,38 @@ __global__ void colmax_finish(const float *__restrict__ part, int nch, int lp, f
     u[j] = mx > 0.f ? __fdiv_rn(mx, 448.f) : 1.f;
 }
 
-// Qq = e4m3(Q / u) and per row chunk the column sums of u_j Qq_rj
+// an e4m3 code's value in units of 2^-9 (every finite e4m3 value is an integer
+// multiple of 2^-9, at most 448 = 229376 units)
+__device__ __forceinline__ int f8_units(uint8_t q) {
+    const int e = (q >> 3) & 15, mt = q & 7;
+    const int v = e ? (8 + mt) << (e - 1) : mt;
+    return (q & 0x80) ? -v : v;
+}
+
+// Qq = e4m3(Q / u) and per row chunk the column sums of u_j Qq_rj (the code sums are
+// exact integers; one rounding, the product with u_j, in float64)
 __global__ void quant_q_kernel(const float *__restrict__ Q, int64_t rows, int lp, const float *__restrict__ u,
                                uint8_t *__restrict__ Qq, int64_t rpb, double *__restrict__ part) {
-    __shared__ double red[2][128];
-    const int j = threadIdx.x & 127, ry = threadIdx.x >> 7;
+    __shared__ long long red[256];
+    int j, ry, G;
+    q_layout(lp, j, ry, G);
     const int64_t r0 = (int64_t)blockIdx.x * rpb, r1 = min(rows, r0 + rpb);
-    double s = 0.0;
-    if (j < lp) {
+    long long s = 0;
+    if (j < lp && ry < G) {
         const float uj = u[j];
-        for (int64_t r = r0 + ry; r < r1; r += 2) {
+        for (int64_t r = r0 + ry; r < r1; r += G) {
             const uint8_t q = e4m3(__fdiv_rn(Q[r * lp + j], uj));
             Qq[r * lp + j] = q;
-            s += (double)f8(q);
+            s += f8_units(q);
         }
-        s *= (double)uj;
     }
-    red[ry][j] = s;
+    red[threadIdx.x] = s;
     __syncthreads();
-    if (ry == 0 && j < lp) part[(int64_t)blockIdx.x * lp + j] = red[0][j] + red[1][j];
+    if (ry == 0 && j < lp) {
+        const int cw = (lp + 31) & ~31;
+        for (int g = 1; g < G; g++) s += red[g * cw + j];
+        part[(int64_t)blockIdx.x * lp + j] = (double)s * 0.001953125 * (double)u[j];
+    }
 }
 
 // 16 codes per thread (one 16-byte load, two 16-byte stores); a scalar tail
@@ -356,7 +400,7 @@ cudaError_t prep8_small(const float *Z, int64_t n, int l, int64_t ldzin, int lp,
 cudaError_t prep8_q(const float *Q, int64_t rows, int lp, void *Qq, float *u, float *mpart, double *part,
                     double *qsum, cudaStream_t s) {
     if (lp > 128) return cudaErrorInvalidValue;
-    const int64_t rpb = 2048;
+    const int64_t rpb = q_chunk_rows(rows);
     const int64_t nch = ceil_div(rows, rpb);
     colmax_q_kernel<<<(unsigned)nch, 256, 0, s>>>(Q, rows, lp, rpb, mpart);
     colmax_finish<<<(unsigned)ceil_div(lp, 128), 128, 0, s>>>(mpart, (int)nch, lp, u);
@@ -404,12 +448,14 @@ cudaError_t to_bf16_t(const float *Z, int64_t n, int l, int64_t ldzin, int lp, v
     return cudaGetLastError();
 }
 
-int64_t split_bf16_chunks(int64_t rows) { return ceil_div(rows, 2048); }
+// rows per chunk of the passes over Q: about four chunks per SM, multiples of 32 rows
+int64_t q_chunk_rows(int64_t rows) { return round_up(std::max<int64_t>(ceil_div(rows, 4 * 152), 32), 32); }
+int64_t split_bf16_chunks(int64_t rows) { return ceil_div(rows, q_chunk_rows(rows)); }
 
 cudaError_t split_bf16(const float *Q, int64_t rows, int lp, int nq, void *Q1, void *Q2, void *Q3, double *part,
                        double *qsum, cudaStream_t s) {
     if (lp > 128) return cudaErrorInvalidValue;
-    const int64_t rpb = 2048;
+    const int64_t rpb = q_chunk_rows(rows);
     const int64_t nch = ceil_div(rows, rpb);
     split_bf16_kernel<<<(unsigned)nch, 256, 0, s>>>(Q, rows, lp, nq, static_cast<uint16_t *>(Q1),
                                                     static_cast<uint16_t *>(Q2), static_cast<uint16_t *>(Q3), rpb,

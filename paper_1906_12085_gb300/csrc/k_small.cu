@@ -13,6 +13,8 @@
 // rotates one pair without synchronising with the others.
 #include <float.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace gbr {
@@ -30,20 +32,25 @@ __device__ __forceinline__ int rr_pos(int k, int r, int L) {
 // Jacobi rotation (c, s) annihilating gamma for column norms^2 alpha, beta:
 // zeta = (beta - alpha) / (2 gamma), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
 // c = 1 / sqrt(1 + t^2), s = c t.
-__device__ __forceinline__ void jrot(float al, float be, float ga, float &c, float &s) {
-    // zeta and t only choose the angle (fast division is enough); c is computed
-    // with the IEEE square root and division so that c^2 + s^2 = 1 to rounding
+__device__ __forceinline__ void jrot(float al, float be, float ga, float &c, float &s, float &t) {
+    // zeta and t only choose the angle (fast division is enough); c comes from the
+    // reciprocal square root: a rotation scaled by (1 + O(eps)) keeps the two columns
+    // (and the two accumulated V columns) orthogonal, only their norms move, and the
+    // V columns are renormalised at the end
     const float zeta = __fdividef(be - al, 2.f * ga);
-    const float t = copysignf(1.f, zeta) * __frcp_rn(fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
-    c = 1.f / sqrtf(fmaf(t, t, 1.f));
+    t = copysignf(1.f, zeta) * __frcp_rn(fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+    c = rsqrtf(fmaf(t, t, 1.f));
     s = c * t;
 }
-__device__ __forceinline__ void jrot(double al, double be, double ga, double &c, double &s) {
+__device__ __forceinline__ void jrot(double al, double be, double ga, double &c, double &s, double &t) {
     const double zeta = (be - al) / (2.0 * ga);
-    const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+    t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
     c = 1.0 / sqrt(1.0 + t * t);
     s = c * t;
 }
+
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -57,6 +64,48 @@ template <> struct Eps<float> { static constexpr double v = FLT_EPSILON; };
 template <> struct Eps<double> { static constexpr double v = DBL_EPSILON; };
 
 // ------------------------------------------------------------ Cholesky + inverse
+// Trailing update of Cholesky step j for the register blocks a, b >= A0 = j / 16
+// (b >= a): M[a][b] -= (row[r] / d) row[c] with no test per element.  Every
+// upper-triangle entry with j < r <= c gets exactly the update of the textbook
+// step; the other entries touched (finished rows r <= j, entries left of the
+// diagonal) are never read again for R.
+template <int LB, int A0, typename Tk>
+__device__ __forceinline__ void chol_update(Tk (&M)[LB][LB], const Tk *row, Tk dinv, int a0, int tx, int ty) {
+    if constexpr (A0 < LB) {
+        if (a0 == A0) {
+#pragma unroll
+            for (int a = A0; a < LB; a++) {
+                const Tk f = row[ty + 16 * a] * dinv;
+#pragma unroll
+                for (int b = a; b < LB; b++) M[a][b] -= f * row[tx + 16 * b];
+            }
+        } else {
+            chol_update<LB, A0 + 1>(M, row, dinv, a0, tx, ty);
+        }
+    }
+}
+
+// Back-substitution step k of the inverse for rows i < k: X[i][:] -= R[i][k] X[k][:],
+// on the blocks a <= B0 = k / 16 (rows below k are left unchanged by a zero
+// factor) and b >= max(a, B0) (row k of X is zero left of column k).
+template <int LB, int B0, typename Tk>
+__device__ __forceinline__ void inv_update(Tk (&M)[LB][LB], const Tk *row, const Tk *Rs, int l, int k, int b0,
+                                           int tx, int ty) {
+    if constexpr (B0 < LB) {
+        if (b0 == B0) {
+#pragma unroll
+            for (int a = 0; a <= B0; a++) {
+                const int i = ty + 16 * a;
+                const Tk f = i < k ? Rs[i * l + k] : Tk(0);
+#pragma unroll
+                for (int b = a > B0 ? a : B0; b < LB; b++) M[a][b] -= f * row[tx + 16 * b];
+            }
+        } else {
+            inv_update<LB, B0 + 1>(M, row, Rs, l, k, b0, tx, ty);
+        }
+    }
+}
+
 // Upper Cholesky R^T R = G and the inverse of R in one CTA of 256 threads laid
 // out as a 16 x 16 grid.  Thread (ty, tx) keeps the entries (ty + 16a, tx + 16b),
 // a, b < LB, in registers; each elimination step only broadcasts one row through
@@ -73,6 +122,7 @@ __device__ __forceinline__ void chol_inv_body(const TG *__restrict__ G, int64_t 
     extern __shared__ __align__(16) unsigned char smraw[];
     Tk *Rs = reinterpret_cast<Tk *>(smraw);  // l x l factor R
     Tk *rowbuf = Rs + l * l;                 // 2 x 16 LB broadcast rows
+    Tk *rdiag = rowbuf + 2 * 16 * LB;        // 1 / R[j][j] (16 LB entries)
     __shared__ double trace;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     constexpr int W = 16 * LB;
@@ -114,25 +164,17 @@ __device__ __forceinline__ void chol_inv_body(const TG *__restrict__ G, int64_t 
             const Tk *row = rowbuf + (j & 1) * W;
             const Tk d = row[j];
             if (!(d > Tk(0)) || !(d < Tk(3.0e38))) { bad = true; break; }  // uniform: every thread reads d
-            const Tk dinv = Tk(1) / d, rinv = Tk(1) / sqrt(d);
+            // 1 / sqrt(d) from the reciprocal square root (no division in the step's
+            // dependency chain); 1 / d = rinv^2, and 1 / R[j][j] = rinv for the inverse
+            const Tk rinv = rsq(d), dinv = rinv * rinv;
+            if (tid == 0) rdiag[j] = rinv;
             if (ty == 0)
 #pragma unroll
                 for (int b = 0; b < LB; b++) {
                     const int c = tx + 16 * b;
                     if (c >= j && c < l) Rs[j * l + c] = row[c] * rinv;
                 }
-#pragma unroll
-            for (int a = 0; a < LB; a++) {
-                const int r = ty + 16 * a;
-                if (r > j && r < l) {
-                    const Tk f = row[r] * dinv;
-#pragma unroll
-                    for (int b = 0; b < LB; b++) {
-                        const int c = tx + 16 * b;
-                        if (c >= r && c < l) M[a][b] -= f * row[c];
-                    }
-                }
-            }
+            chol_update<LB, 0>(M, row, dinv, j >> 4, tx, ty);
             if (j + 1 < l) {
                 Tk *nxt = rowbuf + ((j + 1) & 1) * W;
 #pragma unroll
@@ -160,7 +202,7 @@ __device__ __forceinline__ void chol_inv_body(const TG *__restrict__ G, int64_t 
     {   // publish the scaled last row
         const int k = l - 1;
         Tk *buf = rowbuf + (k & 1) * W;
-        const Tk inv = Tk(1) / Rs[k * l + k];
+        const Tk inv = rdiag[k];
 #pragma unroll
         for (int a = 0; a < LB; a++)
             if (ty + 16 * a == k)
@@ -173,18 +215,10 @@ __device__ __forceinline__ void chol_inv_body(const TG *__restrict__ G, int64_t 
     __syncthreads();
     for (int k = l - 1; k >= 0; k--) {
         const Tk *row = rowbuf + (k & 1) * W;
-#pragma unroll
-        for (int a = 0; a < LB; a++) {
-            const int i = ty + 16 * a;
-            if (i < k) {
-                const Tk f = Rs[i * l + k];
-#pragma unroll
-                for (int b = 0; b < LB; b++) M[a][b] -= f * row[tx + 16 * b];
-            }
-        }
+        inv_update<LB, 0>(M, row, Rs, l, k, k >> 4, tx, ty);
         if (k > 0) {
             Tk *nxt = rowbuf + ((k - 1) & 1) * W;
-            const Tk inv = Tk(1) / Rs[(k - 1) * l + (k - 1)];
+            const Tk inv = rdiag[k - 1];
 #pragma unroll
             for (int a = 0; a < LB; a++)
                 if (ty + 16 * a == k - 1)
@@ -207,7 +241,7 @@ __device__ __forceinline__ void chol_inv_body(const TG *__restrict__ G, int64_t 
 }
 
 template <typename TG, typename Tk, typename Tc, int LB>
-__global__ void __launch_bounds__(256) chol_inv_kernel(const TG *__restrict__ G, int64_t ldg, int l,
+__global__ void __launch_bounds__(256, 1) chol_inv_kernel(const TG *__restrict__ G, int64_t ldg, int l,
                                                        double shift_coef, double *__restrict__ R,
                                                        double *__restrict__ Rinv, Tc *__restrict__ Rinv_c, int lp,
                                                        int *__restrict__ status) {
@@ -216,7 +250,7 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(const TG *__restrict__ G,
 
 // One CTA per problem of a batch; problem b's pointers and shift are tab[b].
 template <typename TG, typename Tk, typename Tc, int LB>
-__global__ void __launch_bounds__(256) chol_inv_batch_kernel(const CholTab *__restrict__ tab, int64_t ldg, int l,
+__global__ void __launch_bounds__(256, 1) chol_inv_batch_kernel(const CholTab *__restrict__ tab, int64_t ldg, int l,
                                                              int lp) {
     const CholTab t = tab[blockIdx.x];
     chol_inv_body<TG, Tk, Tc, LB>(static_cast<const TG *>(t.G), ldg, l, t.coef, t.R, t.Rinv,
@@ -234,84 +268,225 @@ __global__ void trmm_upper_kernel(const double *__restrict__ R2, const double *_
 }
 
 // ------------------------------------------------------------ one-sided Jacobi
-template <typename Ta, typename To>
+// Blocked one-sided (Hestenes) Jacobi.  The columns of X (= R at the start) and
+// of the accumulated rotation V are cut into nb blocks of BW columns.  A sweep
+// pairs the blocks in the round-robin order (nb - 1 block rounds, nb / 2 disjoint
+// block pairs each); warp w holds the 2 BW columns of its block pair, X and V,
+// in registers, NR rows per lane (row i = lane + 32 r), and rotates every
+// column pair between the two blocks (BW rounds of BW disjoint pairs; in the
+// first block round also the pairs inside each block, BW - 1 rounds) without
+// leaving the warp.  One round of BW pairs:
+//   gamma_j = x_p . x_q : per-lane partial sums, then a reduce-scatter over the
+//                         warp (lane group g ends with the total of pair g);
+//   each group computes its rotation from gamma and the tracked squared norms
+//   alpha = ||x_p||^2, beta = ||x_q||^2 (rotate when |gamma| > tol sqrt(alpha beta)),
+//   c, s and t gamma go to every lane, which rotates its rows of x_p, x_q, v_p,
+//   v_q and updates alpha -= t gamma, beta += t gamma (exact for the rotation
+//   that zeroes gamma).
+// The squared norms are recomputed from the columns whenever a block pair is
+// loaded.  The sweep order covers every column pair once; sweeps repeat until
+// one rotates nothing.
+template <int BW>
+__device__ __forceinline__ int rs_index(int lane) {  // pair held by this lane after the reduce-scatter
+    return BW == 8 ? ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1)
+                   : ((lane >> 4) & 1) * 2 + ((lane >> 3) & 1);
+}
+template <int BW>
+__device__ __forceinline__ int rs_owner(int j) {  // lowest lane holding pair j
+    return BW == 8 ? ((j >> 2) & 1) * 16 + ((j >> 1) & 1) * 8 + (j & 1) * 4 : ((j >> 1) & 1) * 16 + (j & 1) * 8;
+}
+
+// warp sums of BW per-lane values; lane ends with the total of value rs_index(lane)
+template <typename Ta, int BW>
+__device__ __forceinline__ Ta reduce_scatter(const Ta (&g)[BW], int lane) {
+    Ta h[BW / 2];
+    const bool b16 = lane & 16;
+#pragma unroll
+    for (int j = 0; j < BW / 2; j++) {
+        const Ta send = b16 ? g[j] : g[j + BW / 2];
+        const Ta keep = b16 ? g[j + BW / 2] : g[j];
+        h[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    Ta k[BW / 4];
+    const bool b8 = lane & 8;
+#pragma unroll
+    for (int j = 0; j < BW / 4; j++) {
+        const Ta send = b8 ? h[j] : h[j + BW / 4];
+        const Ta keep = b8 ? h[j + BW / 4] : h[j];
+        k[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    Ta v;
+    if constexpr (BW == 8) {
+        const bool b4 = lane & 4;
+        const Ta send = b4 ? k[0] : k[1];
+        v = (b4 ? k[1] : k[0]) + __shfl_xor_sync(0xffffffffu, send, 4);
+    } else {
+        v = k[0];
+        v += __shfl_xor_sync(0xffffffffu, v, 4);
+    }
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    return v;
+}
+
+// (c, s, t gamma) of the rotation annihilating gamma, or (1, 0, 0) below the threshold
+template <typename Ta>
+__device__ __forceinline__ void jrot_t(Ta al, Ta be, Ta ga, Ta tol, Ta &c, Ta &s, Ta &d, bool &rot) {
+    c = Ta(1);
+    s = Ta(0);
+    d = Ta(0);
+    if (ga != Ta(0) && fabs(ga) > tol * sqrt(al * be)) {
+        Ta t;
+        jrot(al, be, ga, c, s, t);
+        d = t * ga;
+        rot = true;
+    }
+}
+
+// Pair j of round rd: kind 0 crosses the blocks (column j of the first with
+// column (j + rd) mod BW of the second); kind 1 pairs columns inside each block
+// (circle method on BW columns, BW / 2 pairs per block).
+template <int BW>
+__device__ __forceinline__ void bj_pair(int kind, int rd, int j, int &p, int &q) {
+    if (kind == 0) {
+        p = j;
+        q = BW + (j + rd) % BW;
+    } else {
+        const int k = j % (BW / 2), off = j < BW / 2 ? 0 : BW;
+        const int a = rr_pos(k, rd, BW), b = rr_pos(BW - 1 - k, rd, BW);
+        p = off + min(a, b);
+        q = off + max(a, b);
+    }
+}
+
+template <typename Ta, int BW, int NR>
+__device__ __forceinline__ void bj_round(int kind, int rd, Ta (&x)[2 * BW][NR], Ta (&v)[2 * BW][NR],
+                                         Ta (&nr)[2 * BW], Ta tol, int lane, bool &rot) {
+    Ta g[BW];
+#pragma unroll
+    for (int j = 0; j < BW; j++) {
+        int p, q;
+        bj_pair<BW>(kind, rd, j, p, q);
+        Ta a = Ta(0);
+#pragma unroll
+        for (int r = 0; r < NR; r++) a = fma(x[p][r], x[q][r], a);
+        g[j] = a;
+    }
+    const Ta ga = reduce_scatter<Ta, BW>(g, lane);
+    const int mine = rs_index<BW>(lane);
+    Ta al = Ta(0), be = Ta(0);
+#pragma unroll
+    for (int j = 0; j < BW; j++) {
+        int p, q;
+        bj_pair<BW>(kind, rd, j, p, q);
+        if (j == mine) {
+            al = nr[p];
+            be = nr[q];
+        }
+    }
+    Ta c, s, d;
+    jrot_t(al, be, ga, tol, c, s, d, rot);
+#pragma unroll
+    for (int j = 0; j < BW; j++) {
+        int p, q;
+        bj_pair<BW>(kind, rd, j, p, q);
+        const int src = rs_owner<BW>(j);
+        const Ta cj = __shfl_sync(0xffffffffu, c, src), sj = __shfl_sync(0xffffffffu, s, src);
+        const Ta dj = __shfl_sync(0xffffffffu, d, src);
+#pragma unroll
+        for (int r = 0; r < NR; r++) {
+            const Ta xp = x[p][r], xq = x[q][r];
+            x[p][r] = cj * xp - sj * xq;
+            x[q][r] = sj * xp + cj * xq;
+            const Ta vp = v[p][r], vq = v[q][r];
+            v[p][r] = cj * vp - sj * vq;
+            v[q][r] = sj * vp + cj * vq;
+        }
+        nr[p] -= dj;
+        nr[q] += dj;
+    }
+}
+
+// X, V: Lc columns of L rows each (column c at X + c L); rows >= L of a lane are zero.
+// Warp w takes block pairs w, w + nwarps, ... of each block round.
+template <typename Ta, int BW, int NR>
+__device__ __forceinline__ bool bj_sweeps(Ta *X, Ta *V, int l, int L, int nb, int max_sweeps, int *rotated) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const Ta tol = (Ta)(sqrt((double)l) * Eps<Ta>::v);
+    Ta x[2 * BW][NR], v[2 * BW][NR], nr[2 * BW];
+    for (int sweep = 0; sweep < max_sweeps; sweep++) {
+        bool rot = false;
+        for (int br = 0; br < nb - 1; br++) {
+          for (int bp = warp; bp < nb / 2; bp += nwarps) {
+            const int A = rr_pos(bp, br, nb), B = rr_pos(nb - 1 - bp, br, nb);
+#pragma unroll
+            for (int c = 0; c < 2 * BW; c++) {
+                const int col = (c < BW ? A * BW + c : B * BW + c - BW);
+                Ta ss = Ta(0);
+#pragma unroll
+                for (int r = 0; r < NR; r++) {
+                    const int i = lane + 32 * r;
+                    x[c][r] = i < L ? X[col * L + i] : Ta(0);
+                    v[c][r] = i < L ? V[col * L + i] : Ta(0);
+                    ss = fma(x[c][r], x[c][r], ss);
+                }
+                nr[c] = warp_sum(ss);
+            }
+            if (br == 0) {
+#pragma unroll
+                for (int rd = 0; rd < BW - 1; rd++) bj_round<Ta, BW, NR>(1, rd, x, v, nr, tol, lane, rot);
+            }
+#pragma unroll
+            for (int rd = 0; rd < BW; rd++) bj_round<Ta, BW, NR>(0, rd, x, v, nr, tol, lane, rot);
+#pragma unroll
+            for (int c = 0; c < 2 * BW; c++) {
+                const int col = (c < BW ? A * BW + c : B * BW + c - BW);
+#pragma unroll
+                for (int r = 0; r < NR; r++) {
+                    const int i = lane + 32 * r;
+                    if (i < L) {
+                        X[col * L + i] = x[c][r];
+                        V[col * L + i] = v[c][r];
+                    }
+                }
+            }
+          }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) *rotated = 0;
+        __syncthreads();
+        if (__any_sync(0xffffffffu, rot) && lane == 0) *rotated = 1;
+        __syncthreads();
+        if (!*rotated) return true;
+    }
+    return false;
+}
+
+// Columns of the blocked sweep: nb blocks of BW (nb even, nb BW >= l).
+__host__ __device__ constexpr int bj_blocks(int l, int bw) { return 2 * ((l + 2 * bw - 1) / (2 * bw)); }
+
+template <typename Ta, typename To, int BW, int NR>
 __device__ __forceinline__ void jacobi_osvd_body(const double *__restrict__ R, int l, int lp, double *__restrict__ sig,
                                                  To *__restrict__ UR, To *__restrict__ W, int *__restrict__ status,
-                                                 int max_sweeps, int gsize) {
-    // gsize lanes (16 or 32) rotate one column pair; a warp holds 32 / gsize pairs
+                                                 int max_sweeps) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int L = l + (l & 1);
-    Ta *X = reinterpret_cast<Ta *>(smraw);  // X[p * L + i]: column p of the rotated matrix
-    Ta *V = X + L * L;                       // V[p * L + i]: column p of the accumulated rotation
-    double *nrm = reinterpret_cast<double *>(V + L * L + ((L * L) & 1));
+    const int nb = bj_blocks(l, BW), Lc = nb * BW;
+    Ta *X = reinterpret_cast<Ta *>(smraw);  // X[p * L + i]: column p of the rotated matrix (Lc columns)
+    Ta *V = X + (size_t)Lc * L;              // V[p * L + i]: column p of the accumulated rotation
+    double *nrm = reinterpret_cast<double *>(V + (size_t)Lc * L + (((size_t)Lc * L) & 1));
     int *perm = reinterpret_cast<int *>(nrm + L);
     __shared__ int rotated;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    const int gl = lane % gsize, gpw = 32 / gsize;               // lane in group, groups per warp
-    const int grp = warp * gpw + lane / gsize, ngrp = nw * gpw;
-    const unsigned gmask = gsize == 32 ? 0xffffffffu : (0xffffu << (lane & 16));
-    for (int idx = tid; idx < L * L; idx += nt) {
+    for (int idx = tid; idx < Lc * L; idx += nt) {
         const int p = idx / L, i = idx % L;
         X[idx] = (p < l && i < l) ? (Ta)R[i * l + p] : Ta(0);
         V[idx] = (p == i) ? Ta(1) : Ta(0);
     }
+    __syncthreads();
     // rotate when |x_p . x_q| > tol ||x_p|| ||x_q||, tol = sqrt(l) eps: the converged
     // columns are then orthogonal to sqrt(l) eps (an l eps threshold leaves l eps)
-    const Ta tol = (Ta)(sqrt((double)l) * Eps<Ta>::v);
-    int sweep = 0;
-    bool converged = false;
-    __syncthreads();
-    for (; sweep < max_sweeps; sweep++) {
-        if (tid == 0) rotated = 0;
-        __syncthreads();
-        for (int r = 0; r < L - 1; r++) {
-            for (int pr0 = 0; pr0 < L / 2; pr0 += ngrp) {
-                const int pr = pr0 + grp;
-                const bool act = pr < L / 2;
-                int p = 0, q = 1;
-                if (act) {
-                    const int a = rr_pos(pr, r, L), b = rr_pos(L - 1 - pr, r, L);
-                    p = min(a, b);
-                    q = max(a, b);
-                }
-                const bool live = act && q < l;
-                Ta al = 0, be = 0, ga = 0;
-                if (live)
-                    for (int i = gl; i < l; i += gsize) {
-                        const Ta xp = X[p * L + i], xq = X[q * L + i];
-                        al += xp * xp;
-                        be += xq * xq;
-                        ga += xp * xq;
-                    }
-                // three interleaved reductions inside the group
-                for (int o = gsize >> 1; o > 0; o >>= 1) {
-                    const Ta a1 = __shfl_xor_sync(gmask, al, o);
-                    const Ta b1 = __shfl_xor_sync(gmask, be, o);
-                    const Ta g1 = __shfl_xor_sync(gmask, ga, o);
-                    al += a1;
-                    be += b1;
-                    ga += g1;
-                }
-                if (live && ga != Ta(0) && fabs(ga) > tol * sqrt(al * be)) {
-                    Ta c, s;
-                    jrot(al, be, ga, c, s);
-                    for (int i = gl; i < L; i += gsize) {
-                        const Ta xp = X[p * L + i], xq = X[q * L + i];
-                        X[p * L + i] = c * xp - s * xq;
-                        X[q * L + i] = s * xp + c * xq;
-                        const Ta vp = V[p * L + i], vq = V[q * L + i];
-                        V[p * L + i] = c * vp - s * vq;
-                        V[q * L + i] = s * vp + c * vq;
-                    }
-                    if (gl == 0) rotated = 1;
-                }
-            }
-            __syncthreads();
-        }
-        const int any = rotated;
-        __syncthreads();
-        if (!any) { converged = true; break; }
-    }
+    const bool converged = bj_sweeps<Ta, BW, NR>(X, V, l, L, nb, max_sweeps, &rotated);
     if (!converged && tid == 0) atomicOr(status, (int)ST_NOCONV);
     Ta *nrm_t = reinterpret_cast<Ta *>(nrm);
     for (int p = warp; p < l; p += nw) {
@@ -356,20 +531,21 @@ __device__ __forceinline__ void jacobi_osvd_body(const double *__restrict__ R, i
     }
 }
 
-template <typename Ta, typename To>
-__global__ void __launch_bounds__(1024) jacobi_osvd_kernel(const double *__restrict__ R, int l, int lp,
+// MAXT threads at most (MAXT / 32 warps), so that the 4 BW NR column registers fit
+template <typename Ta, typename To, int BW, int NR, int MAXT>
+__global__ void __launch_bounds__(MAXT) jacobi_osvd_kernel(const double *__restrict__ R, int l, int lp,
                                                            double *__restrict__ sig, To *__restrict__ UR,
                                                            To *__restrict__ W, int *__restrict__ status,
-                                                           int max_sweeps, int gsize) {
-    jacobi_osvd_body<Ta, To>(R, l, lp, sig, UR, W, status, max_sweeps, gsize);
+                                                           int max_sweeps) {
+    jacobi_osvd_body<Ta, To, BW, NR>(R, l, lp, sig, UR, W, status, max_sweeps);
 }
 
-template <typename Ta, typename To>
-__global__ void __launch_bounds__(1024) jacobi_osvd_batch_kernel(const JacTab *__restrict__ tab, int l, int lp,
-                                                                 int max_sweeps, int gsize) {
+template <typename Ta, typename To, int BW, int NR, int MAXT>
+__global__ void __launch_bounds__(MAXT) jacobi_osvd_batch_kernel(const JacTab *__restrict__ tab, int l, int lp,
+                                                                 int max_sweeps) {
     const JacTab t = tab[blockIdx.x];
-    jacobi_osvd_body<Ta, To>(t.R, l, lp, t.sig, static_cast<To *>(t.UR), static_cast<To *>(t.W), t.status,
-                             max_sweeps, gsize);
+    jacobi_osvd_body<Ta, To, BW, NR>(t.R, l, lp, t.sig, static_cast<To *>(t.UR), static_cast<To *>(t.W), t.status,
+                                     max_sweeps);
 }
 
 // sig[i] = x_i^T R w_i / (||x_i|| ||w_i||) in float64 for the columns x_i of UR and
@@ -615,7 +791,7 @@ int chol_lb(int l, size_t tk) {
 template <typename TG, typename Tk, typename Tc, int LB>
 void launch_chol(const CholTab *tab, int count, const TG *G, int64_t ldg, int l, double coef, double *R, double *Rinv,
                  Tc *Rinv_c, int lp, int *status, cudaStream_t s) {
-    const size_t smem = sizeof(Tk) * ((size_t)l * l + 2 * 16 * LB);
+    const size_t smem = sizeof(Tk) * ((size_t)l * l + 3 * 16 * LB);
     if (tab) {
         cudaFuncSetAttribute(chol_inv_batch_kernel<TG, Tk, Tc, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
@@ -663,34 +839,80 @@ cudaError_t trmm_upper(const double *R2, const double *R1, double *R, int l, cud
     return cudaGetLastError();
 }
 
-template <typename Ta, typename To>
-cudaError_t jacobi_osvd(const double *R, int l, int lp, double *sig, To *UR, To *W, int *status, cudaStream_t s) {
+// Block width and rows per lane of the blocked Jacobi for an l x l factor:
+// 8-column blocks for float32 of 65..128 columns, else 4 (register budget);
+// rows per lane ceil(L / 32).
+template <typename Ta>
+void jacobi_shape(int l, int &bw, int &nr) {
     const int L = l + (l & 1);
-    // X, V (L x L each), norms (L doubles), permutation (L ints), column scales (L x Ta)
-    const size_t smem = sizeof(Ta) * (2 * (size_t)L * L + 1) + sizeof(double) * L + sizeof(int) * L +
-                        sizeof(double) * L + 16;
-    cudaFuncSetAttribute(jacobi_osvd_kernel<Ta, To>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int gsize = l <= 64 ? 16 : 32;
-    int threads = (L / 2) * gsize;
-    threads = threads < 64 ? 64 : threads > 1024 ? 1024 : (threads + 31) / 32 * 32;
-    jacobi_osvd_kernel<Ta, To><<<1, threads, smem, s>>>(R, l, lp, sig, UR, W, status, 40, gsize);
+    nr = (L + 31) / 32;
+    bw = (sizeof(Ta) == 4 && l > 64 && L <= 128) ? 8 : 4;
+}
+
+template <typename Ta>
+size_t jacobi_smem(int l, int bw) {
+    const int L = l + (l & 1);
+    const size_t cells = (size_t)bj_blocks(l, bw) * bw * L;
+    // X, V (cells each), norms (L doubles), permutation (L ints), column scales (L x Ta)
+    return sizeof(Ta) * (2 * cells + 1) + sizeof(double) * L + sizeof(int) * L + sizeof(double) * L + 16;
+}
+
+template <typename Ta, typename To, int BW, int NR>
+void launch_jacobi(const JacTab *tab, int count, const double *R, int l, int lp, double *sig, To *UR, To *W,
+                   int *status, cudaStream_t s) {
+    // float64, the 8-wide blocks and 5 rows per lane need up to 255 registers: 8 warps; else 16
+    constexpr int MAXT = (sizeof(Ta) == 8 || BW == 8 || NR == 5) ? 256 : 512;
+    const size_t smem = jacobi_smem<Ta>(l, BW);
+    const int threads = 32 * std::min(bj_blocks(l, BW) / 2, MAXT / 32);
+    if (tab) {
+        cudaFuncSetAttribute(jacobi_osvd_batch_kernel<Ta, To, BW, NR, MAXT>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        jacobi_osvd_batch_kernel<Ta, To, BW, NR, MAXT><<<count, threads, smem, s>>>(tab, l, lp, 40);
+    } else {
+        cudaFuncSetAttribute(jacobi_osvd_kernel<Ta, To, BW, NR, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        jacobi_osvd_kernel<Ta, To, BW, NR, MAXT><<<1, threads, smem, s>>>(R, l, lp, sig, UR, W, status, 40);
+    }
+}
+
+template <typename Ta, typename To>
+cudaError_t jacobi_dispatch(const JacTab *tab, int count, const double *R, int l, int lp, double *sig, To *UR,
+                            To *W, int *status, cudaStream_t s) {
+    int bw, nr;
+    jacobi_shape<Ta>(l, bw, nr);
+    if (nr > (sizeof(Ta) == 8 ? 4 : 5) || jacobi_smem<Ta>(l, bw) > 227 * 1024) return cudaErrorInvalidValue;
+    if constexpr (sizeof(Ta) == 4) {
+        if (bw == 8) {
+            switch (nr) {
+                case 3: launch_jacobi<Ta, To, 8, 3>(tab, count, R, l, lp, sig, UR, W, status, s); break;
+                default: launch_jacobi<Ta, To, 8, 4>(tab, count, R, l, lp, sig, UR, W, status, s); break;
+            }
+            note_launch();
+            return cudaGetLastError();
+        }
+    }
+    switch (nr) {
+        case 1: launch_jacobi<Ta, To, 4, 1>(tab, count, R, l, lp, sig, UR, W, status, s); break;
+        case 2: launch_jacobi<Ta, To, 4, 2>(tab, count, R, l, lp, sig, UR, W, status, s); break;
+        case 3: launch_jacobi<Ta, To, 4, 3>(tab, count, R, l, lp, sig, UR, W, status, s); break;
+        case 4: launch_jacobi<Ta, To, 4, 4>(tab, count, R, l, lp, sig, UR, W, status, s); break;
+        default:
+            if constexpr (sizeof(Ta) == 4) launch_jacobi<Ta, To, 4, 5>(tab, count, R, l, lp, sig, UR, W, status, s);
+            break;
+    }
     note_launch();
     return cudaGetLastError();
 }
 
 template <typename Ta, typename To>
+cudaError_t jacobi_osvd(const double *R, int l, int lp, double *sig, To *UR, To *W, int *status, cudaStream_t s) {
+    return jacobi_dispatch<Ta, To>(nullptr, 1, R, l, lp, sig, UR, W, status, s);
+}
+
+template <typename Ta, typename To>
 cudaError_t jacobi_osvd_batched(const JacTab *tab, int count, int l, int lp, cudaStream_t s) {
     if (count < 1) return cudaSuccess;
-    const int L = l + (l & 1);
-    const size_t smem = sizeof(Ta) * (2 * (size_t)L * L + 1) + sizeof(double) * L + sizeof(int) * L +
-                        sizeof(double) * L + 16;
-    cudaFuncSetAttribute(jacobi_osvd_batch_kernel<Ta, To>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int gsize = l <= 64 ? 16 : 32;
-    int threads = (L / 2) * gsize;
-    threads = threads < 64 ? 64 : threads > 1024 ? 1024 : (threads + 31) / 32 * 32;
-    jacobi_osvd_batch_kernel<Ta, To><<<count, threads, smem, s>>>(tab, l, lp, 40, gsize);
-    note_launch();
-    return cudaGetLastError();
+    return jacobi_dispatch<Ta, To>(tab, count, nullptr, l, lp, nullptr, nullptr, nullptr, nullptr, s);
 }
 
 template <typename To>
