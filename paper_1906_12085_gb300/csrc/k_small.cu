@@ -64,124 +64,122 @@ template <> struct Eps<float> { static constexpr double v = FLT_EPSILON; };
 template <> struct Eps<double> { static constexpr double v = DBL_EPSILON; };
 
 // ------------------------------------------------------------ Cholesky + inverse
-// Trailing update of Cholesky step j for the register blocks a, b >= A0 = j / 16
-// (b >= a): M[a][b] -= (row[r] / d) row[c] with no test per element.  Every
-// upper-triangle entry with j < r <= c gets exactly the update of the textbook
-// step; the other entries touched (finished rows r <= j, entries left of the
-// diagonal) are never read again for R.
-template <int LB, int A0, typename Tk>
-__device__ __forceinline__ void chol_update(Tk (&M)[LB][LB], const Tk *row, Tk dinv, int a0, int tx, int ty) {
-    if constexpr (A0 < LB) {
-        if (a0 == A0) {
-#pragma unroll
-            for (int a = A0; a < LB; a++) {
-                const Tk f = row[ty + 16 * a] * dinv;
-#pragma unroll
-                for (int b = a; b < LB; b++) M[a][b] -= f * row[tx + 16 * b];
-            }
-        } else {
-            chol_update<LB, A0 + 1>(M, row, dinv, a0, tx, ty);
-        }
-    }
+// Upper Cholesky R^T R = G and the inverse X = R^{-1} of an l x l matrix in one
+// CTA of 256 threads, blocked by 16-column panels (NP = ceil(l / 16) panels, the
+// matrix padded to 16 NP with the identity).  Arithmetic in Tk, in shared memory.
+//   Cholesky, panel p (rows / columns o = 16 p .. o + 15), right-looking:
+//     (1) one warp factors the diagonal block D = R_pp^T R_pp: for k = 0..15,
+//         R_kk = sqrt(D_kk), R_kc = D_kc / R_kk (c > k), D_ic -= R_ki R_kc (k < i <= c);
+//     (2) every column c right of the panel solves R_pp^T x = A[o..o+15][c]
+//         (forward substitution) for the panel rows of R;
+//     (3) rank-16 update of the trailing upper triangle:
+//         A[i][c] -= sum_k R[o+k][i] R[o+k][c].
+//   Inverse, row blocks p = NP-1 .. 0 (back substitution by blocks):
+//     T = delta_pb I - sum_{p<q<=b} R_pq X_qb for every column block b >= p, then
+//     X_pb = R_pp^{-1} T by back substitution inside the block (rows 15..0).
+// The reciprocal pivots 1 / R_kk come from the reciprocal square root, so no
+// step waits on a division.  Three barriers per panel for the factor, two per
+// row block for the inverse.
+template <typename Tk>
+struct CholSmem {
+    Tk *A, *X, *rdiag;
+    int S;  // row stride of A and X
+};
+
+template <typename Tk>
+__device__ __forceinline__ CholSmem<Tk> chol_smem(int LL) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    CholSmem<Tk> m;
+    m.S = LL + (sizeof(Tk) == 4 ? 16 : 1);
+    m.A = reinterpret_cast<Tk *>(smraw);
+    m.X = m.A + (size_t)LL * m.S;
+    m.rdiag = m.X + (size_t)LL * m.S;
+    return m;
 }
 
-// Back-substitution step k of the inverse for rows i < k: X[i][:] -= R[i][k] X[k][:],
-// on the blocks a <= B0 = k / 16 (rows below k are left unchanged by a zero
-// factor) and b >= max(a, B0) (row k of X is zero left of column k).
-template <int LB, int B0, typename Tk>
-__device__ __forceinline__ void inv_update(Tk (&M)[LB][LB], const Tk *row, const Tk *Rs, int l, int k, int b0,
-                                           int tx, int ty) {
-    if constexpr (B0 < LB) {
-        if (b0 == B0) {
-#pragma unroll
-            for (int a = 0; a <= B0; a++) {
-                const int i = ty + 16 * a;
-                const Tk f = i < k ? Rs[i * l + k] : Tk(0);
-#pragma unroll
-                for (int b = a > B0 ? a : B0; b < LB; b++) M[a][b] -= f * row[tx + 16 * b];
-            }
-        } else {
-            inv_update<LB, B0 + 1>(M, row, Rs, l, k, b0, tx, ty);
-        }
-    }
-}
-
-// Upper Cholesky R^T R = G and the inverse of R in one CTA of 256 threads laid
-// out as a 16 x 16 grid.  Thread (ty, tx) keeps the entries (ty + 16a, tx + 16b),
-// a, b < LB, in registers; each elimination step only broadcasts one row through
-// a double-buffered shared row, so a step costs one barrier.
-//   Cholesky (right-looking): with the current row j (unscaled) in the buffer,
-//     R[j][c] = M[j][c] / sqrt(M[j][j]),  M[r][c] -= M[j][r] M[j][c] / M[j][j]  (j < r <= c).
-//   Inverse (back substitution on R X = I from the bottom row up):
-//     X[k][:] /= R[k][k],  X[i][:] -= R[i][k] X[k][:]  (i < k).
-// Arithmetic in Tk; l <= 16 * LB.
-template <typename TG, typename Tk, typename Tc, int LB>
+template <typename TG, typename Tk, typename Tc>
 __device__ __forceinline__ void chol_inv_body(const TG *__restrict__ G, int64_t ldg, int l, double shift_coef,
                                               double *__restrict__ R, double *__restrict__ Rinv,
                                               Tc *__restrict__ Rinv_c, int lp, int *__restrict__ status) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    Tk *Rs = reinterpret_cast<Tk *>(smraw);  // l x l factor R
-    Tk *rowbuf = Rs + l * l;                 // 2 x 16 LB broadcast rows
-    Tk *rdiag = rowbuf + 2 * 16 * LB;        // 1 / R[j][j] (16 LB entries)
+    const int NP = (l + 15) >> 4, LL = 16 * NP;
+    const CholSmem<Tk> sm = chol_smem<Tk>(LL);
+    Tk *A = sm.A, *X = sm.X, *rdiag = sm.rdiag;
+    const int S = sm.S;
     __shared__ double trace;
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    constexpr int W = 16 * LB;
-    Tk M[LB][LB];
+    __shared__ int bad;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, tx = tid & 15, ty = tid >> 4;
     int used = 0;  // 0: plain, 1: shifted, 2: breakdown fallback (R = 0, R^{-1} = I)
     for (int attempt = 0; attempt < 3; attempt++) {
-#pragma unroll
-        for (int a = 0; a < LB; a++)
-#pragma unroll
-            for (int b = 0; b < LB; b++) {
-                const int r = ty + 16 * a, c = tx + 16 * b;
-                Tk v = Tk(0);
-                if (r < l && c < l) v = attempt == 2 ? Tk(r == c ? 1 : 0) : (Tk)G[(int64_t)min(r, c) * ldg + max(r, c)];
-                M[a][b] = v;
-            }
-        if (attempt == 1 && tid < 32) {  // trace for the shift (only after a breakdown)
+        if (attempt == 1 && warp == 0) {  // trace for the shift (only after a breakdown)
             double tr = 0.0;
-            for (int i = tid; i < l; i += 32) tr += (double)G[(int64_t)i * ldg + i];
+            for (int i = lane; i < l; i += 32) tr += (double)G[(int64_t)i * ldg + i];
             tr = warp_sum(tr);
-            if (tid == 0) trace = tr;
+            if (lane == 0) trace = tr;
         }
-        for (int i = tid; i < l * l; i += 256) Rs[i] = Tk(0);
+        if (tid == 0) bad = 0;
         __syncthreads();
-        if (attempt == 1) {  // shifted CholeskyQR: G + s I with s = 11 (rows l + l(l+1)) u tr(G)
-            const Tk sh = (Tk)(shift_coef * trace);
-#pragma unroll
-            for (int a = 0; a < LB; a++)
-#pragma unroll
-                for (int b = 0; b < LB; b++)
-                    if (ty + 16 * a == tx + 16 * b && ty + 16 * a < l) M[a][b] += sh;
+        const Tk sh = attempt == 1 ? (Tk)(shift_coef * trace) : Tk(0);
+        for (int idx = tid; idx < LL * LL; idx += 256) {  // upper triangle (the lower one is never read)
+            const int i = idx / LL, j = idx % LL;
+            if (j < i) continue;
+            Tk v;
+            if (i < l && j < l) v = attempt == 2 ? Tk(i == j ? 1 : 0) : (Tk)G[(int64_t)i * ldg + j];
+            else v = Tk(i == j ? 1 : 0);
+            if (i == j && i < l) v += sh;
+            A[i * S + j] = v;
         }
-        // publish row 0
-        if (ty == 0)
-#pragma unroll
-            for (int b = 0; b < LB; b++) rowbuf[tx + 16 * b] = M[0][b];
         __syncthreads();
-        bool bad = false;
-        for (int j = 0; j < l; j++) {
-            const Tk *row = rowbuf + (j & 1) * W;
-            const Tk d = row[j];
-            if (!(d > Tk(0)) || !(d < Tk(3.0e38))) { bad = true; break; }  // uniform: every thread reads d
-            // 1 / sqrt(d) from the reciprocal square root (no division in the step's
-            // dependency chain); 1 / d = rinv^2, and 1 / R[j][j] = rinv for the inverse
-            const Tk rinv = rsq(d), dinv = rinv * rinv;
-            if (tid == 0) rdiag[j] = rinv;
-            if (ty == 0)
-#pragma unroll
-                for (int b = 0; b < LB; b++) {
-                    const int c = tx + 16 * b;
-                    if (c >= j && c < l) Rs[j * l + c] = row[c] * rinv;
+        for (int p = 0; p < NP; p++) {
+            const int o = 16 * p;
+            if (warp == 0) {  // (1) diagonal block, lane c < 16 owns column o + c
+                for (int k = 0; k < 16; k++) {
+                    const Tk d = A[(o + k) * S + o + k];
+                    if (!(d > Tk(0)) || !(d < Tk(3.0e38))) {  // every lane reads the same d
+                        if (lane == 0) bad = 1;
+                        break;
+                    }
+                    const Tk rinv = rsq(d);
+                    __syncwarp();
+                    if (lane < 16 && lane >= k) A[(o + k) * S + o + lane] = lane == k ? d * rinv : A[(o + k) * S + o + lane] * rinv;
+                    if (lane == 0) rdiag[o + k] = rinv;
+                    __syncwarp();
+                    if (lane < 16 && lane > k) {
+                        const Tk rc = A[(o + k) * S + o + lane];
+                        for (int i = k + 1; i <= lane; i++) A[(o + i) * S + o + lane] -= A[(o + k) * S + o + i] * rc;
+                    }
+                    __syncwarp();
                 }
-            chol_update<LB, 0>(M, row, dinv, j >> 4, tx, ty);
-            if (j + 1 < l) {
-                Tk *nxt = rowbuf + ((j + 1) & 1) * W;
+            }
+            __syncthreads();
+            if (bad) break;
+            // (2) panel rows right of the block: R_pp^T x = a for every column c
+            for (int c = o + 16 + tid; c < LL; c += 256) {
+                Tk x[16];
 #pragma unroll
-                for (int a = 0; a < LB; a++)
-                    if (ty + 16 * a == j + 1)
+                for (int k = 0; k < 16; k++) x[k] = A[(o + k) * S + c];
 #pragma unroll
-                        for (int b = 0; b < LB; b++) nxt[tx + 16 * b] = M[a][b];
+                for (int k = 0; k < 16; k++) {
+                    x[k] *= rdiag[o + k];
+#pragma unroll
+                    for (int i = k + 1; i < 16; i++) x[i] -= A[(o + k) * S + o + i] * x[k];
+                }
+#pragma unroll
+                for (int k = 0; k < 16; k++) A[(o + k) * S + c] = x[k];
+            }
+            __syncthreads();
+            // (3) trailing update, blocks p < a <= b
+            for (int a = p + 1; a < NP; a++) {
+                const int i = 16 * a + ty;
+                Tk ri[16];
+#pragma unroll
+                for (int k = 0; k < 16; k++) ri[k] = A[(o + k) * S + i];
+                for (int b = a; b < NP; b++) {
+                    const int c = 16 * b + tx;
+                    Tk acc = A[i * S + c];
+#pragma unroll
+                    for (int k = 0; k < 16; k++) acc -= ri[k] * A[(o + k) * S + c];
+                    A[i * S + c] = acc;
+                }
             }
             __syncthreads();
         }
@@ -192,69 +190,65 @@ __device__ __forceinline__ void chol_inv_body(const TG *__restrict__ G, int64_t 
         }
         __syncthreads();
     }
-    for (int i = tid; i < l * l; i += 256) R[i] = used < 2 ? (double)Rs[i] : 0.0;
-    // inverse: X in registers (reusing M), identity to start
-#pragma unroll
-    for (int a = 0; a < LB; a++)
-#pragma unroll
-        for (int b = 0; b < LB; b++) M[a][b] = Tk((ty + 16 * a == tx + 16 * b) ? 1 : 0);
-    __syncthreads();
-    {   // publish the scaled last row
-        const int k = l - 1;
-        Tk *buf = rowbuf + (k & 1) * W;
-        const Tk inv = rdiag[k];
-#pragma unroll
-        for (int a = 0; a < LB; a++)
-            if (ty + 16 * a == k)
-#pragma unroll
-                for (int b = 0; b < LB; b++) {
-                    M[a][b] *= inv;
-                    buf[tx + 16 * b] = M[a][b];
-                }
+    for (int idx = tid; idx < l * l; idx += 256) {
+        const int i = idx / l, j = idx % l;
+        R[idx] = (used < 2 && j >= i) ? (double)A[i * S + j] : 0.0;
     }
-    __syncthreads();
-    for (int k = l - 1; k >= 0; k--) {
-        const Tk *row = rowbuf + (k & 1) * W;
-        inv_update<LB, 0>(M, row, Rs, l, k, k >> 4, tx, ty);
-        if (k > 0) {
-            Tk *nxt = rowbuf + ((k - 1) & 1) * W;
-            const Tk inv = rdiag[k - 1];
+    // inverse by row blocks, bottom up
+    for (int p = NP - 1; p >= 0; p--) {
+        const int o = 16 * p;
+        // T = delta I - sum_{p<q<=b} R_pq X_qb for column blocks b >= p (written into X)
+        for (int b = p; b < NP; b++) {
+            const int i = o + ty, c = 16 * b + tx;
+            Tk acc = (b == p && ty == tx) ? Tk(1) : Tk(0);
+            for (int q = p + 1; q <= b; q++) {
 #pragma unroll
-            for (int a = 0; a < LB; a++)
-                if (ty + 16 * a == k - 1)
+                for (int k = 0; k < 16; k++) acc -= A[i * S + 16 * q + k] * X[(16 * q + k) * S + c];
+            }
+            X[i * S + c] = acc;
+        }
+        __syncthreads();
+        // X_pb = R_pp^{-1} T: back substitution inside the block, one thread per column
+        for (int c = o + tid; c < LL; c += 256) {
+            Tk x[16];
 #pragma unroll
-                    for (int b = 0; b < LB; b++) {
-                        M[a][b] *= inv;
-                        nxt[tx + 16 * b] = M[a][b];
-                    }
+            for (int k = 0; k < 16; k++) x[k] = X[(o + k) * S + c];
+#pragma unroll
+            for (int k = 15; k >= 0; k--) {
+                x[k] *= rdiag[o + k];
+#pragma unroll
+                for (int i = 0; i < k; i++) x[i] -= A[(o + i) * S + o + k] * x[k];
+            }
+#pragma unroll
+            for (int k = 0; k < 16; k++) X[(o + k) * S + c] = x[k];
         }
         __syncthreads();
     }
-#pragma unroll
-    for (int a = 0; a < LB; a++)
-#pragma unroll
-        for (int b = 0; b < LB; b++) {
-            const int i = ty + 16 * a, j = tx + 16 * b;
-            if (i < l && j < l) Rinv[i * l + j] = j >= i ? (double)M[a][b] : 0.0;
-            if (i < lp && j < lp) Rinv_c[i * lp + j] = (i < l && j < l && j >= i) ? (Tc)M[a][b] : Tc(0);
-        }
+    for (int idx = tid; idx < l * l; idx += 256) {
+        const int i = idx / l, j = idx % l;
+        Rinv[idx] = j >= i ? (double)X[i * S + j] : 0.0;
+    }
+    for (int idx = tid; idx < lp * lp; idx += 256) {
+        const int i = idx / lp, j = idx % lp;
+        Rinv_c[idx] = (i < l && j < l && j >= i) ? (Tc)X[i * S + j] : Tc(0);
+    }
 }
 
-template <typename TG, typename Tk, typename Tc, int LB>
+template <typename TG, typename Tk, typename Tc>
 __global__ void __launch_bounds__(256, 1) chol_inv_kernel(const TG *__restrict__ G, int64_t ldg, int l,
-                                                       double shift_coef, double *__restrict__ R,
-                                                       double *__restrict__ Rinv, Tc *__restrict__ Rinv_c, int lp,
-                                                       int *__restrict__ status) {
-    chol_inv_body<TG, Tk, Tc, LB>(G, ldg, l, shift_coef, R, Rinv, Rinv_c, lp, status);
+                                                          double shift_coef, double *__restrict__ R,
+                                                          double *__restrict__ Rinv, Tc *__restrict__ Rinv_c, int lp,
+                                                          int *__restrict__ status) {
+    chol_inv_body<TG, Tk, Tc>(G, ldg, l, shift_coef, R, Rinv, Rinv_c, lp, status);
 }
 
 // One CTA per problem of a batch; problem b's pointers and shift are tab[b].
-template <typename TG, typename Tk, typename Tc, int LB>
+template <typename TG, typename Tk, typename Tc>
 __global__ void __launch_bounds__(256, 1) chol_inv_batch_kernel(const CholTab *__restrict__ tab, int64_t ldg, int l,
-                                                             int lp) {
+                                                                int lp) {
     const CholTab t = tab[blockIdx.x];
-    chol_inv_body<TG, Tk, Tc, LB>(static_cast<const TG *>(t.G), ldg, l, t.coef, t.R, t.Rinv,
-                                  static_cast<Tc *>(t.Rc), lp, t.status);
+    chol_inv_body<TG, Tk, Tc>(static_cast<const TG *>(t.G), ldg, l, t.coef, t.R, t.Rinv, static_cast<Tc *>(t.Rc), lp,
+                              t.status);
 }
 
 __global__ void trmm_upper_kernel(const double *__restrict__ R2, const double *__restrict__ R1, double *__restrict__ R,
@@ -778,28 +772,11 @@ __global__ void pca_select_kernel(const double *__restrict__ sigma, int count, c
     *reached = 0;
 }
 
-// Register blocks per thread side of the Cholesky kernel (l <= 16 LB): float64 takes
-// the smallest block that covers l (its 8 x 8 block spills), float32 4 or 8.
-int chol_lb(int l, size_t tk) {
-    if (l <= 64) return 4;
-    if (tk == 8 && l <= 96) return 6;
-    if (tk == 8 && l <= 112) return 7;
-    return 8;
-}
-
-// One problem (tab == nullptr) or a batch of `count` problems from a device table.
-template <typename TG, typename Tk, typename Tc, int LB>
-void launch_chol(const CholTab *tab, int count, const TG *G, int64_t ldg, int l, double coef, double *R, double *Rinv,
-                 Tc *Rinv_c, int lp, int *status, cudaStream_t s) {
-    const size_t smem = sizeof(Tk) * ((size_t)l * l + 3 * 16 * LB);
-    if (tab) {
-        cudaFuncSetAttribute(chol_inv_batch_kernel<TG, Tk, Tc, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        chol_inv_batch_kernel<TG, Tk, Tc, LB><<<count, 256, smem, s>>>(tab, ldg, l, lp);
-    } else {
-        cudaFuncSetAttribute(chol_inv_kernel<TG, Tk, Tc, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        chol_inv_kernel<TG, Tk, Tc, LB><<<1, 256, smem, s>>>(G, ldg, l, coef, R, Rinv, Rinv_c, lp, status);
-    }
+// shared memory of the blocked Cholesky: A and X (16 NP rows of stride S) and the pivots
+template <typename Tk>
+size_t chol_smem_bytes(int l) {
+    const int LL = 16 * ((l + 15) / 16), S = LL + (sizeof(Tk) == 4 ? 16 : 1);
+    return sizeof(Tk) * (2 * (size_t)LL * S + LL);
 }
 
 }  // namespace
@@ -808,12 +785,10 @@ template <typename TG, typename Tk, typename Tc>
 cudaError_t chol_inv(const TG *G, int64_t ldg, int l, int64_t rows, double u, double *R, double *Rinv, Tc *Rinv_c,
                      int lp, int *status, cudaStream_t s) {
     const double coef = chol_shift_coef(rows, l, u);
-    switch (chol_lb(l, sizeof(Tk))) {
-        case 4: launch_chol<TG, Tk, Tc, 4>(nullptr, 1, G, ldg, l, coef, R, Rinv, Rinv_c, lp, status, s); break;
-        case 6: launch_chol<TG, Tk, Tc, 6>(nullptr, 1, G, ldg, l, coef, R, Rinv, Rinv_c, lp, status, s); break;
-        case 7: launch_chol<TG, Tk, Tc, 7>(nullptr, 1, G, ldg, l, coef, R, Rinv, Rinv_c, lp, status, s); break;
-        default: launch_chol<TG, Tk, Tc, 8>(nullptr, 1, G, ldg, l, coef, R, Rinv, Rinv_c, lp, status, s); break;
-    }
+    const size_t smem = chol_smem_bytes<Tk>(l);
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    cudaFuncSetAttribute(chol_inv_kernel<TG, Tk, Tc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    chol_inv_kernel<TG, Tk, Tc><<<1, 256, smem, s>>>(G, ldg, l, coef, R, Rinv, Rinv_c, lp, status);
     note_launch();
     return cudaGetLastError();
 }
@@ -821,12 +796,10 @@ cudaError_t chol_inv(const TG *G, int64_t ldg, int l, int64_t rows, double u, do
 template <typename TG, typename Tk, typename Tc>
 cudaError_t chol_inv_batched(const CholTab *tab, int count, int64_t ldg, int l, int lp, cudaStream_t s) {
     if (count < 1) return cudaSuccess;
-    switch (chol_lb(l, sizeof(Tk))) {
-        case 4: launch_chol<TG, Tk, Tc, 4>(tab, count, nullptr, ldg, l, 0.0, nullptr, nullptr, nullptr, lp, nullptr, s); break;
-        case 6: launch_chol<TG, Tk, Tc, 6>(tab, count, nullptr, ldg, l, 0.0, nullptr, nullptr, nullptr, lp, nullptr, s); break;
-        case 7: launch_chol<TG, Tk, Tc, 7>(tab, count, nullptr, ldg, l, 0.0, nullptr, nullptr, nullptr, lp, nullptr, s); break;
-        default: launch_chol<TG, Tk, Tc, 8>(tab, count, nullptr, ldg, l, 0.0, nullptr, nullptr, nullptr, lp, nullptr, s); break;
-    }
+    const size_t smem = chol_smem_bytes<Tk>(l);
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    cudaFuncSetAttribute(chol_inv_batch_kernel<TG, Tk, Tc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    chol_inv_batch_kernel<TG, Tk, Tc><<<count, 256, smem, s>>>(tab, ldg, l, lp);
     note_launch();
     return cudaGetLastError();
 }

@@ -302,9 +302,13 @@ rsvd_status cqr(rsvd_plan *P, const T *X, int64_t rows, int w, int ld, T *Qo, T 
     const double u = unit_roundoff<T>();
     const bool skinny = ld == P->lp;  // the l-wide blocks of the randomized solver
     T *Q1 = passes == 2 ? Tmp : Qo;
+    // the precision forms factor the Gram matrices of CholeskyQR2 (the final basis and
+    // T) in float64; the single-pass re-orthonormalisations inside the power
+    // iteration, like the float32 path's, in float32
+    const bool f64 = (P->dtype == RSVD_BF16 || P->dtype == RSVD_FP8_E4M3) && passes == 2;
     if (skinny) CK(prod_tn<T>(P, rows, ld, X, ld, X, ld, G, ld));
     else CK(gemm_tn<T>(rows, ld, ld, X, ld, X, ld, G, ld, part, P->part_elems, s));
-    if (P->dtype == RSVD_BF16 || P->dtype == RSVD_FP8_E4M3)
+    if (f64)
         CK(chol_inv<T, double, T>(G, ld, w, rows, u, P->R1, P->R1i, Ric, ld, P->status, s));
     else CK(chol_inv<T, T, T>(G, ld, w, rows, u, P->R1, P->R1i, Ric, ld, P->status, s));
     if (skinny) CK(prod_nn<T>(P, rows, ld, X, ld, Ric, ld, Q1, ld));
@@ -312,7 +316,7 @@ rsvd_status cqr(rsvd_plan *P, const T *X, int64_t rows, int w, int ld, T *Qo, T 
     if (passes == 1) return RSVD_OK;
     if (skinny) CK(prod_tn<T>(P, rows, ld, Q1, ld, Q1, ld, G, ld));
     else CK(gemm_tn<T>(rows, ld, ld, Q1, ld, Q1, ld, G, ld, part, P->part_elems, s));
-    if (P->dtype == RSVD_BF16 || P->dtype == RSVD_FP8_E4M3)
+    if (f64)
         CK(chol_inv<T, double, T>(G, ld, w, rows, u, P->R2, P->R2i, Ric, ld, P->status, s));
     else CK(chol_inv<T, T, T>(G, ld, w, rows, u, P->R2, P->R2i, Ric, ld, P->status, s));
     if (skinny) CK(prod_nn<T>(P, rows, ld, Q1, ld, Ric, ld, Qo, ld));
