@@ -162,13 +162,16 @@ __global__ void split_bf16_kernel(const float *__restrict__ Q, int64_t rows, int
     }
 }
 
-// qsum[j] = sum over chunks (in order)
+// qsum[j] = sum over chunks: one warp per column, lane-strided partial sums in
+// chunk order, then a fixed shuffle tree
 __global__ void sum_rows_kernel(const double *__restrict__ part, int nch, int lp, double *__restrict__ qsum) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (j >= lp) return;
     double s = 0.0;
-    for (int k = 0; k < nch; k++) s += part[(int64_t)k * lp + j];
-    qsum[j] = s;
+    for (int k = lane; k < nch; k += 32) s += part[(int64_t)k * lp + j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) qsum[j] = s;
 }
 
 // ------------------------------------------------------------------ e4m3
@@ -405,7 +408,7 @@ cudaError_t prep8_q(const float *Q, int64_t rows, int lp, void *Qq, float *u, fl
     colmax_q_kernel<<<(unsigned)nch, 256, 0, s>>>(Q, rows, lp, rpb, mpart);
     colmax_finish<<<(unsigned)ceil_div(lp, 128), 128, 0, s>>>(mpart, (int)nch, lp, u);
     quant_q_kernel<<<(unsigned)nch, 256, 0, s>>>(Q, rows, lp, u, static_cast<uint8_t *>(Qq), rpb, part);
-    sum_rows_kernel<<<(unsigned)ceil_div(lp, 128), 128, 0, s>>>(part, (int)nch, lp, qsum);
+    sum_rows_kernel<<<(unsigned)ceil_div(lp, 8), 256, 0, s>>>(part, (int)nch, lp, qsum);
     note_launch(4);
     return cudaGetLastError();
 }
@@ -460,7 +463,7 @@ cudaError_t split_bf16(const float *Q, int64_t rows, int lp, int nq, void *Q1, v
     split_bf16_kernel<<<(unsigned)nch, 256, 0, s>>>(Q, rows, lp, nq, static_cast<uint16_t *>(Q1),
                                                     static_cast<uint16_t *>(Q2), static_cast<uint16_t *>(Q3), rpb,
                                                     part);
-    sum_rows_kernel<<<(unsigned)ceil_div(lp, 128), 128, 0, s>>>(part, (int)nch, lp, qsum);
+    sum_rows_kernel<<<(unsigned)ceil_div(lp, 8), 256, 0, s>>>(part, (int)nch, lp, qsum);
     note_launch(2);
     return cudaGetLastError();
 }
