@@ -38,7 +38,9 @@ __device__ __forceinline__ void jrot(float al, float be, float ga, float &c, flo
     // (and the two accumulated V columns) orthogonal, only their norms move, and the
     // V columns are renormalised at the end
     const float zeta = __fdividef(be - al, 2.f * ga);
-    t = copysignf(1.f, zeta) * __frcp_rn(fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+    const float z2 = fmaf(zeta, zeta, 1.f);
+    const float root = z2 < 1e30f ? z2 * rsqrtf(z2) : fabsf(zeta);  // sqrt(1 + zeta^2)
+    t = copysignf(1.f, zeta) * __fdividef(1.f, fabsf(zeta) + root);
     c = rsqrtf(fmaf(t, t, 1.f));
     s = c * t;
 }
@@ -68,8 +70,10 @@ template <> struct Eps<double> { static constexpr double v = DBL_EPSILON; };
 // CTA of 256 threads, blocked by 16-column panels (NP = ceil(l / 16) panels, the
 // matrix padded to 16 NP with the identity).  Arithmetic in Tk, in shared memory.
 //   Cholesky, panel p (rows / columns o = 16 p .. o + 15), right-looking:
-//     (1) one warp factors the diagonal block D = R_pp^T R_pp: for k = 0..15,
-//         R_kk = sqrt(D_kk), R_kc = D_kc / R_kk (c > k), D_ic -= R_ki R_kc (k < i <= c);
+//     (1) one warp factors the diagonal block D = R_pp^T R_pp with each column in
+//         the registers of one lane (row k of R broadcast through shared memory):
+//         for k = 0..15, R_kk = sqrt(D_kk), R_kc = D_kc / R_kk (c > k),
+//         D_ic -= R_ki R_kc (k < i <= c);
 //     (2) every column c right of the panel solves R_pp^T x = A[o..o+15][c]
 //         (forward substitution) for the panel rows of R;
 //     (3) rank-16 update of the trailing upper triangle:
@@ -131,23 +135,34 @@ __device__ __forceinline__ void chol_inv_body(const TG *__restrict__ G, int64_t 
         __syncthreads();
         for (int p = 0; p < NP; p++) {
             const int o = 16 * p;
-            if (warp == 0) {  // (1) diagonal block, lane c < 16 owns column o + c
+            if (warp == 0) {  // (1) diagonal block: lane c (and c + 16) holds column o + c in registers
+                const int c = lane & 15;
+                Tk col[16];
+#pragma unroll
+                for (int i = 0; i < 16; i++) col[i] = A[(o + i) * S + o + c];
+                Tk *rowk = X;  // row k of R_pp (X is free until the inverse)
+                bool ok = true;
+#pragma unroll
                 for (int k = 0; k < 16; k++) {
-                    const Tk d = A[(o + k) * S + o + k];
-                    if (!(d > Tk(0)) || !(d < Tk(3.0e38))) {  // every lane reads the same d
-                        if (lane == 0) bad = 1;
-                        break;
-                    }
-                    const Tk rinv = rsq(d);
-                    __syncwarp();
-                    if (lane < 16 && lane >= k) A[(o + k) * S + o + lane] = lane == k ? d * rinv : A[(o + k) * S + o + lane] * rinv;
+                    const Tk d = __shfl_sync(0xffffffffu, col[k], k);  // D_kk, the same in every lane
+                    ok = ok && d > Tk(0) && d < Tk(3.0e38);  // after a breakdown the remaining steps are discarded
+                    const Tk rinv = rsq(ok ? d : Tk(1));
+                    col[k] = c == k ? d * rinv : (c > k ? col[k] * rinv : col[k]);  // R_kc for c >= k
+                    if (lane < 16) rowk[c] = col[k];
                     if (lane == 0) rdiag[o + k] = rinv;
                     __syncwarp();
-                    if (lane < 16 && lane > k) {
-                        const Tk rc = A[(o + k) * S + o + lane];
-                        for (int i = k + 1; i <= lane; i++) A[(o + i) * S + o + lane] -= A[(o + k) * S + o + i] * rc;
+#pragma unroll
+                    for (int i = k + 1; i < 16; i++) {
+                        const Tk rki = rowk[i];
+                        if (c >= i) col[i] -= rki * col[k];
                     }
                     __syncwarp();
+                }
+                if (!ok) {
+                    if (lane == 0) bad = 1;
+                } else if (lane < 16) {
+#pragma unroll
+                    for (int i = 0; i < 16; i++) A[(o + i) * S + o + c] = col[i];
                 }
             }
             __syncthreads();
@@ -323,13 +338,14 @@ __device__ __forceinline__ Ta reduce_scatter(const Ta (&g)[BW], int lane) {
     return v;
 }
 
-// (c, s, t gamma) of the rotation annihilating gamma, or (1, 0, 0) below the threshold
+// (c, s, t gamma) of the rotation annihilating gamma, or (1, 0, 0) below the
+// threshold |gamma| > tol sqrt(alpha beta) (compared squared: tol2 = tol^2)
 template <typename Ta>
-__device__ __forceinline__ void jrot_t(Ta al, Ta be, Ta ga, Ta tol, Ta &c, Ta &s, Ta &d, bool &rot) {
+__device__ __forceinline__ void jrot_t(Ta al, Ta be, Ta ga, Ta tol2, Ta &c, Ta &s, Ta &d, bool &rot) {
     c = Ta(1);
     s = Ta(0);
     d = Ta(0);
-    if (ga != Ta(0) && fabs(ga) > tol * sqrt(al * be)) {
+    if (ga != Ta(0) && ga * ga > tol2 * (al * be)) {
         Ta t;
         jrot(al, be, ga, c, s, t);
         d = t * ga;
@@ -355,7 +371,7 @@ __device__ __forceinline__ void bj_pair(int kind, int rd, int j, int &p, int &q)
 
 template <typename Ta, int BW, int NR>
 __device__ __forceinline__ void bj_round(int kind, int rd, Ta (&x)[2 * BW][NR], Ta (&v)[2 * BW][NR],
-                                         Ta (&nr)[2 * BW], Ta tol, int lane, bool &rot) {
+                                         Ta (&nr)[2 * BW], Ta tol2, int lane, bool &rot) {
     Ta g[BW];
 #pragma unroll
     for (int j = 0; j < BW; j++) {
@@ -379,7 +395,7 @@ __device__ __forceinline__ void bj_round(int kind, int rd, Ta (&x)[2 * BW][NR], 
         }
     }
     Ta c, s, d;
-    jrot_t(al, be, ga, tol, c, s, d, rot);
+    jrot_t(al, be, ga, tol2, c, s, d, rot);
 #pragma unroll
     for (int j = 0; j < BW; j++) {
         int p, q;
@@ -403,35 +419,48 @@ __device__ __forceinline__ void bj_round(int kind, int rd, Ta (&x)[2 * BW][NR], 
 
 // X, V: Lc columns of L rows each (column c at X + c L); rows >= L of a lane are zero.
 // Warp w takes block pairs w, w + nwarps, ... of each block round.
+// trk: the squared column norms, recomputed from the columns at the start of
+// every sweep and carried (updated by the rotations) from block round to block round.
 template <typename Ta, int BW, int NR>
-__device__ __forceinline__ bool bj_sweeps(Ta *X, Ta *V, int l, int L, int nb, int max_sweeps, int *rotated) {
+__device__ __forceinline__ bool bj_sweeps(Ta *X, Ta *V, Ta *trk, int l, int L, int nb, int max_sweeps,
+                                          int *rotated) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const Ta tol = (Ta)(sqrt((double)l) * Eps<Ta>::v);
+    const Ta tol = (Ta)(sqrt((double)l) * Eps<Ta>::v), tol2 = tol * tol;
     Ta x[2 * BW][NR], v[2 * BW][NR], nr[2 * BW];
     for (int sweep = 0; sweep < max_sweeps; sweep++) {
         bool rot = false;
+        for (int p = warp; p < nb * BW; p += nwarps) {
+            Ta ss = Ta(0);
+#pragma unroll
+            for (int r = 0; r < NR; r++) {
+                const int i = lane + 32 * r;
+                const Ta xv = i < L ? X[p * L + i] : Ta(0);
+                ss = fma(xv, xv, ss);
+            }
+            ss = warp_sum(ss);
+            if (lane == 0) trk[p] = ss;
+        }
+        __syncthreads();
         for (int br = 0; br < nb - 1; br++) {
           for (int bp = warp; bp < nb / 2; bp += nwarps) {
             const int A = rr_pos(bp, br, nb), B = rr_pos(nb - 1 - bp, br, nb);
 #pragma unroll
             for (int c = 0; c < 2 * BW; c++) {
                 const int col = (c < BW ? A * BW + c : B * BW + c - BW);
-                Ta ss = Ta(0);
 #pragma unroll
                 for (int r = 0; r < NR; r++) {
                     const int i = lane + 32 * r;
                     x[c][r] = i < L ? X[col * L + i] : Ta(0);
                     v[c][r] = i < L ? V[col * L + i] : Ta(0);
-                    ss = fma(x[c][r], x[c][r], ss);
                 }
-                nr[c] = warp_sum(ss);
+                nr[c] = trk[col];
             }
             if (br == 0) {
 #pragma unroll
-                for (int rd = 0; rd < BW - 1; rd++) bj_round<Ta, BW, NR>(1, rd, x, v, nr, tol, lane, rot);
+                for (int rd = 0; rd < BW - 1; rd++) bj_round<Ta, BW, NR>(1, rd, x, v, nr, tol2, lane, rot);
             }
 #pragma unroll
-            for (int rd = 0; rd < BW; rd++) bj_round<Ta, BW, NR>(0, rd, x, v, nr, tol, lane, rot);
+            for (int rd = 0; rd < BW; rd++) bj_round<Ta, BW, NR>(0, rd, x, v, nr, tol2, lane, rot);
 #pragma unroll
             for (int c = 0; c < 2 * BW; c++) {
                 const int col = (c < BW ? A * BW + c : B * BW + c - BW);
@@ -443,6 +472,7 @@ __device__ __forceinline__ bool bj_sweeps(Ta *X, Ta *V, int l, int L, int nb, in
                         V[col * L + i] = v[c][r];
                     }
                 }
+                if (lane == 0) trk[col] = nr[c];
             }
           }
             __syncthreads();
@@ -480,7 +510,8 @@ __device__ __forceinline__ void jacobi_osvd_body(const double *__restrict__ R, i
     __syncthreads();
     // rotate when |x_p . x_q| > tol ||x_p|| ||x_q||, tol = sqrt(l) eps: the converged
     // columns are then orthogonal to sqrt(l) eps (an l eps threshold leaves l eps)
-    const bool converged = bj_sweeps<Ta, BW, NR>(X, V, l, L, nb, max_sweeps, &rotated);
+    Ta *trk = reinterpret_cast<Ta *>(perm + L) + L;  // after the column scales vn (see below)
+    const bool converged = bj_sweeps<Ta, BW, NR>(X, V, trk, l, L, nb, max_sweeps, &rotated);
     if (!converged && tid == 0) atomicOr(status, (int)ST_NOCONV);
     Ta *nrm_t = reinterpret_cast<Ta *>(nrm);
     for (int p = warp; p < l; p += nw) {
@@ -826,8 +857,10 @@ template <typename Ta>
 size_t jacobi_smem(int l, int bw) {
     const int L = l + (l & 1);
     const size_t cells = (size_t)bj_blocks(l, bw) * bw * L;
-    // X, V (cells each), norms (L doubles), permutation (L ints), column scales (L x Ta)
-    return sizeof(Ta) * (2 * cells + 1) + sizeof(double) * L + sizeof(int) * L + sizeof(double) * L + 16;
+    // X, V (cells each), norms (L doubles), permutation (L ints), column scales (L x Ta),
+    // tracked squared norms (nb bw x Ta)
+    return sizeof(Ta) * (2 * cells + 1) + sizeof(double) * L + sizeof(int) * L + sizeof(double) * L +
+           sizeof(double) * (size_t)bj_blocks(l, bw) * bw + 16;
 }
 
 template <typename Ta, typename To, int BW, int NR>
