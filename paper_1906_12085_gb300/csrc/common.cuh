@@ -19,9 +19,19 @@ enum StatusBits : int {
 
 // Largest l (or n for svd_exact) whose l x l working set fits one CTA's shared memory.
 constexpr int kSmallMaxF64 = 112;
-// Largest l of a float32 randomized solve: the float32 Jacobi working set and the
-// 16 x 8 register blocks of the Cholesky kernel, and N <= 128 of the tensor-core products.
+// Largest l of a float32 batched or lockstep-served solve (the batched small kernels
+// keep their l x l blocks in shared memory).
 constexpr int kSmallMaxF32 = 128;
+// Largest l of a single float32 / bfloat16 / e4m3 randomized solve: above the shared-
+// memory sizes the Cholesky and Jacobi keep their l x l blocks in a global scratch
+// (one CTA each), and the products run on column slices of N <= 128.
+constexpr int kRsvdMaxL = 288;
+// Tensor-core products take N <= 128 output columns per launch; wider products run
+// as ceil(N / 128) launches on column slices of this width (a multiple of 16).
+inline int column_slice(int N) {
+    const int k = (N + 127) / 128;
+    return ((N + k - 1) / k + 15) / 16 * 16;
+}
 // Largest Lanczos step count whose bidiagonal SVD fits one CTA in float32.
 constexpr int kGklMaxStepsF32 = 160;
 
@@ -79,9 +89,13 @@ int64_t gemm_tn_partials(int64_t rows, int64_t N, int64_t L);
 // Rinv_c (element type Tc, lp x lp, zero padded).  On a non-positive pivot
 // retries once with the shift 11 (rows*l + l(l+1)) u tr(G) (shifted
 // CholeskyQR); on a second breakdown sets ST_CHOL and returns R = 0, R^{-1} = I.
+// Matrices whose two l x l blocks exceed one SM's shared memory (l > 112 in float64,
+// l > 128 in float32) live in `scratch` (chol_scratch_bytes(l, sizeof(Tk)) bytes of
+// device memory), which may be NULL otherwise.
 template <typename TG, typename Tk, typename Tc>
 cudaError_t chol_inv(const TG *G, int64_t ldg, int l, int64_t rows, double unit_roundoff, double *R,
-                     double *Rinv, Tc *Rinv_c, int lp, int *status, cudaStream_t s);
+                     double *Rinv, Tc *Rinv_c, int lp, int *status, cudaStream_t s, void *scratch = nullptr);
+size_t chol_scratch_bytes(int l, size_t tk);
 
 // R = R2 * R1 for upper-triangular l x l float64 matrices (ld l).
 cudaError_t trmm_upper(const double *R2, const double *R1, double *R, int l, cudaStream_t s);
@@ -89,9 +103,12 @@ cudaError_t trmm_upper(const double *R2, const double *R1, double *R, int l, cud
 // One-sided Jacobi SVD of the l x l float64 matrix R (ld l), arithmetic in Ta:
 // R W = U_R diag(sig).  Outputs sorted descending: sig (l doubles), U_R and W
 // in element type To (lp x lp, zero padded, ld lp).
+// Above one SM's shared memory (float32: l > 160; float64: l > 112) X and V live in
+// `scratch` (jacobi_scratch_bytes(l, sizeof(Ta)) bytes), l <= 288 (float32).
 template <typename Ta, typename To>
 cudaError_t jacobi_osvd(const double *R, int l, int lp, double *sig, To *UR, To *W, int *status,
-                        cudaStream_t s);
+                        cudaStream_t s, void *scratch = nullptr);
+size_t jacobi_scratch_bytes(int l, size_t ta);
 
 // Float64 Rayleigh-quotient refinement of the singular values returned by
 // jacobi_osvd: sig[i] = u_i^T R w_i / (||u_i|| ||w_i||) (R upper triangular or

@@ -107,13 +107,23 @@ __global__ void mean_corr_kernel(const double *__restrict__ mu, const uint16_t *
     if (lane == 0) c[j] = (float)s;
 }
 
-// The per-column passes over Q (rows x lp, lp <= 128) run 256 threads per row
-// chunk as G = 256 / CW row groups of CW = lp rounded up to 32 columns.
-__device__ __forceinline__ void q_layout(int lp, int &j, int &ry, int &G) {
-    const int cw = (lp + 31) & ~31;
-    G = 256 / cw;
-    j = threadIdx.x % cw;
-    ry = threadIdx.x / cw;
+// The per-column passes over Q (rows x lp) run 256 threads per (row chunk, group of
+// up to 128 columns: blockIdx.y) as G = 256 / CW row groups of CW = the group's
+// width rounded up to 32 columns.  jj: column within the group, j: column of Q.
+struct QLayout {
+    int j, jj, ry, G, cw;
+    bool ok;
+};
+__device__ __forceinline__ QLayout q_layout(int lp) {
+    QLayout q;
+    const int j0 = blockIdx.y * 128, wid = min(128, lp - j0);
+    q.cw = (wid + 31) & ~31;
+    q.G = 256 / q.cw;
+    q.jj = threadIdx.x % q.cw;
+    q.ry = threadIdx.x / q.cw;
+    q.j = j0 + q.jj;
+    q.ok = q.jj < wid && q.ry < q.G;
+    return q;
 }
 
 // s + c += x with the rounding error of every addition carried in c (Neumaier):
@@ -130,11 +140,11 @@ __global__ void split_bf16_kernel(const float *__restrict__ Q, int64_t rows, int
                                   uint16_t *__restrict__ Q2, uint16_t *__restrict__ Q3, int64_t rpb,
                                   double *__restrict__ part) {
     __shared__ double red[256];
-    int j, ry, G;
-    q_layout(lp, j, ry, G);
+    const QLayout ql = q_layout(lp);
+    const int j = ql.j, ry = ql.ry, G = ql.G;
     const int64_t r0 = (int64_t)blockIdx.x * rpb, r1 = min(rows, r0 + rpb);
     float s = 0.f, c = 0.f;
-    if (j < lp && ry < G) {
+    if (ql.ok) {
         for (int64_t r = r0 + ry; r < r1; r += G) {
             const float x = Q[r * lp + j];
             const uint16_t h = rbf(x);
@@ -154,10 +164,9 @@ __global__ void split_bf16_kernel(const float *__restrict__ Q, int64_t rows, int
     }
     red[threadIdx.x] = (double)s + (double)c;
     __syncthreads();
-    if (ry == 0 && j < lp) {
-        const int cw = (lp + 31) & ~31;
-        double a = red[j];
-        for (int g = 1; g < G; g++) a += red[g * cw + j];
+    if (ry == 0 && ql.ok) {
+        double a = red[ql.jj];
+        for (int g = 1; g < G; g++) a += red[g * ql.cw + ql.jj];
         part[(int64_t)blockIdx.x * lp + j] = a;
     }
 }
@@ -302,17 +311,16 @@ __global__ void prep8_small_kernel(const float *__restrict__ Z, int64_t n, int l
 __global__ void colmax_q_kernel(const float *__restrict__ Q, int64_t rows, int lp, int64_t rpb,
                                 float *__restrict__ part) {
     __shared__ float red[256];
-    int j, ry, G;
-    q_layout(lp, j, ry, G);
+    const QLayout ql = q_layout(lp);
+    const int j = ql.j, ry = ql.ry, G = ql.G;
     const int64_t r0 = (int64_t)blockIdx.x * rpb, r1 = min(rows, r0 + rpb);
     float mx = 0.f;
-    if (j < lp && ry < G)
+    if (ql.ok)
         for (int64_t r = r0 + ry; r < r1; r += G) mx = fmaxf(mx, fabsf(Q[r * lp + j]));
     red[threadIdx.x] = mx;
     __syncthreads();
-    if (ry == 0 && j < lp) {
-        const int cw = (lp + 31) & ~31;
-        for (int g = 1; g < G; g++) mx = fmaxf(mx, red[g * cw + j]);
+    if (ry == 0 && ql.ok) {
+        for (int g = 1; g < G; g++) mx = fmaxf(mx, red[g * ql.cw + ql.jj]);
         part[(int64_t)blockIdx.x * lp + j] = mx;
     }
 }
@@ -338,11 +346,11 @@ __device__ __forceinline__ int f8_units(uint8_t q) {
 __global__ void quant_q_kernel(const float *__restrict__ Q, int64_t rows, int lp, const float *__restrict__ u,
                                uint8_t *__restrict__ Qq, int64_t rpb, double *__restrict__ part) {
     __shared__ long long red[256];
-    int j, ry, G;
-    q_layout(lp, j, ry, G);
+    const QLayout ql = q_layout(lp);
+    const int j = ql.j, ry = ql.ry, G = ql.G;
     const int64_t r0 = (int64_t)blockIdx.x * rpb, r1 = min(rows, r0 + rpb);
     long long s = 0;
-    if (j < lp && ry < G) {
+    if (ql.ok) {
         const float uj = u[j];
         for (int64_t r = r0 + ry; r < r1; r += G) {
             const uint8_t q = e4m3(__fdiv_rn(Q[r * lp + j], uj));
@@ -352,9 +360,8 @@ __global__ void quant_q_kernel(const float *__restrict__ Q, int64_t rows, int lp
     }
     red[threadIdx.x] = s;
     __syncthreads();
-    if (ry == 0 && j < lp) {
-        const int cw = (lp + 31) & ~31;
-        for (int g = 1; g < G; g++) s += red[g * cw + j];
+    if (ry == 0 && ql.ok) {
+        for (int g = 1; g < G; g++) s += red[g * ql.cw + ql.jj];
         part[(int64_t)blockIdx.x * lp + j] = (double)s * 0.001953125 * (double)u[j];
     }
 }
@@ -402,12 +409,12 @@ cudaError_t prep8_small(const float *Z, int64_t n, int l, int64_t ldzin, int lp,
 
 cudaError_t prep8_q(const float *Q, int64_t rows, int lp, void *Qq, float *u, float *mpart, double *part,
                     double *qsum, cudaStream_t s) {
-    if (lp > 128) return cudaErrorInvalidValue;
     const int64_t rpb = q_chunk_rows(rows);
     const int64_t nch = ceil_div(rows, rpb);
-    colmax_q_kernel<<<(unsigned)nch, 256, 0, s>>>(Q, rows, lp, rpb, mpart);
+    const dim3 grid((unsigned)nch, (unsigned)ceil_div(lp, 128));
+    colmax_q_kernel<<<grid, 256, 0, s>>>(Q, rows, lp, rpb, mpart);
     colmax_finish<<<(unsigned)ceil_div(lp, 128), 128, 0, s>>>(mpart, (int)nch, lp, u);
-    quant_q_kernel<<<(unsigned)nch, 256, 0, s>>>(Q, rows, lp, u, static_cast<uint8_t *>(Qq), rpb, part);
+    quant_q_kernel<<<grid, 256, 0, s>>>(Q, rows, lp, u, static_cast<uint8_t *>(Qq), rpb, part);
     sum_rows_kernel<<<(unsigned)ceil_div(lp, 8), 256, 0, s>>>(part, (int)nch, lp, qsum);
     note_launch(4);
     return cudaGetLastError();
@@ -457,10 +464,10 @@ int64_t split_bf16_chunks(int64_t rows) { return ceil_div(rows, q_chunk_rows(row
 
 cudaError_t split_bf16(const float *Q, int64_t rows, int lp, int nq, void *Q1, void *Q2, void *Q3, double *part,
                        double *qsum, cudaStream_t s) {
-    if (lp > 128) return cudaErrorInvalidValue;
     const int64_t rpb = q_chunk_rows(rows);
     const int64_t nch = ceil_div(rows, rpb);
-    split_bf16_kernel<<<(unsigned)nch, 256, 0, s>>>(Q, rows, lp, nq, static_cast<uint16_t *>(Q1),
+    split_bf16_kernel<<<dim3((unsigned)nch, (unsigned)ceil_div(lp, 128)), 256, 0, s>>>(Q, rows, lp, nq,
+                                                                                    static_cast<uint16_t *>(Q1),
                                                     static_cast<uint16_t *>(Q2), static_cast<uint16_t *>(Q3), rpb,
                                                     part);
     sum_rows_kernel<<<(unsigned)ceil_div(lp, 8), 256, 0, s>>>(part, (int)nch, lp, qsum);

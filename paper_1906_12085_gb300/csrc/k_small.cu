@@ -90,23 +90,32 @@ struct CholSmem {
     int S;  // row stride of A and X
 };
 
-template <typename Tk>
-__device__ __forceinline__ CholSmem<Tk> chol_smem(int LL) {
+// A and X in shared memory, or (gws != NULL, matrices too large for one SM) in the
+// global scratch gws (2 LL S elements; L2-resident); the pivots always in shared memory.
+template <typename Tk, bool GM>
+__device__ __forceinline__ CholSmem<Tk> chol_smem(int LL, Tk *gws) {
     extern __shared__ __align__(16) unsigned char smraw[];
     CholSmem<Tk> m;
     m.S = LL + (sizeof(Tk) == 4 ? 16 : 1);
-    m.A = reinterpret_cast<Tk *>(smraw);
-    m.X = m.A + (size_t)LL * m.S;
-    m.rdiag = m.X + (size_t)LL * m.S;
+    if constexpr (GM) {
+        m.A = gws;
+        m.X = gws + (size_t)LL * m.S;
+        m.rdiag = reinterpret_cast<Tk *>(smraw);
+    } else {
+        m.A = reinterpret_cast<Tk *>(smraw);
+        m.X = m.A + (size_t)LL * m.S;
+        m.rdiag = m.X + (size_t)LL * m.S;
+    }
     return m;
 }
 
-template <typename TG, typename Tk, typename Tc>
+template <typename TG, typename Tk, typename Tc, bool GM = false>
 __device__ __forceinline__ void chol_inv_body(const TG *__restrict__ G, int64_t ldg, int l, double shift_coef,
                                               double *__restrict__ R, double *__restrict__ Rinv,
-                                              Tc *__restrict__ Rinv_c, int lp, int *__restrict__ status) {
+                                              Tc *__restrict__ Rinv_c, int lp, int *__restrict__ status,
+                                              Tk *gws = nullptr) {
     const int NP = (l + 15) >> 4, LL = 16 * NP;
-    const CholSmem<Tk> sm = chol_smem<Tk>(LL);
+    const CholSmem<Tk> sm = chol_smem<Tk, GM>(LL, gws);
     Tk *A = sm.A, *X = sm.X, *rdiag = sm.rdiag;
     const int S = sm.S;
     __shared__ double trace;
@@ -249,12 +258,12 @@ __device__ __forceinline__ void chol_inv_body(const TG *__restrict__ G, int64_t 
     }
 }
 
-template <typename TG, typename Tk, typename Tc>
+template <typename TG, typename Tk, typename Tc, bool GM>
 __global__ void __launch_bounds__(256, 1) chol_inv_kernel(const TG *__restrict__ G, int64_t ldg, int l,
                                                           double shift_coef, double *__restrict__ R,
                                                           double *__restrict__ Rinv, Tc *__restrict__ Rinv_c, int lp,
-                                                          int *__restrict__ status) {
-    chol_inv_body<TG, Tk, Tc>(G, ldg, l, shift_coef, R, Rinv, Rinv_c, lp, status);
+                                                          int *__restrict__ status, Tk *__restrict__ gws) {
+    chol_inv_body<TG, Tk, Tc, GM>(G, ldg, l, shift_coef, R, Rinv, Rinv_c, lp, status, gws);
 }
 
 // One CTA per problem of a batch; problem b's pointers and shift are tab[b].
@@ -489,16 +498,21 @@ __device__ __forceinline__ bool bj_sweeps(Ta *X, Ta *V, Ta *trk, int l, int L, i
 // Columns of the blocked sweep: nb blocks of BW (nb even, nb BW >= l).
 __host__ __device__ constexpr int bj_blocks(int l, int bw) { return 2 * ((l + 2 * bw - 1) / (2 * bw)); }
 
+// X and V in shared memory, or (gws != NULL: too large for one SM) in the global
+// scratch gws (2 Lc L elements, L2-resident); the per-column arrays in shared memory.
 template <typename Ta, typename To, int BW, int NR>
 __device__ __forceinline__ void jacobi_osvd_body(const double *__restrict__ R, int l, int lp, double *__restrict__ sig,
                                                  To *__restrict__ UR, To *__restrict__ W, int *__restrict__ status,
-                                                 int max_sweeps) {
+                                                 int max_sweeps, Ta *gws) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int L = l + (l & 1);
     const int nb = bj_blocks(l, BW), Lc = nb * BW;
-    Ta *X = reinterpret_cast<Ta *>(smraw);  // X[p * L + i]: column p of the rotated matrix (Lc columns)
-    Ta *V = X + (size_t)Lc * L;              // V[p * L + i]: column p of the accumulated rotation
-    double *nrm = reinterpret_cast<double *>(V + (size_t)Lc * L + (((size_t)Lc * L) & 1));
+    // NR >= 6 (more than 160 rows) is only used with the global scratch
+    constexpr bool GM = NR >= 6;
+    Ta *X = GM ? gws : reinterpret_cast<Ta *>(smraw);  // X[p * L + i]: column p of the rotated matrix (Lc columns)
+    Ta *V = X + (size_t)Lc * L;                        // V[p * L + i]: column p of the accumulated rotation
+    double *nrm = GM ? reinterpret_cast<double *>(smraw)
+                     : reinterpret_cast<double *>(V + (size_t)Lc * L + (((size_t)Lc * L) & 1));
     int *perm = reinterpret_cast<int *>(nrm + L);
     __shared__ int rotated;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
@@ -561,8 +575,8 @@ template <typename Ta, typename To, int BW, int NR, int MAXT>
 __global__ void __launch_bounds__(MAXT) jacobi_osvd_kernel(const double *__restrict__ R, int l, int lp,
                                                            double *__restrict__ sig, To *__restrict__ UR,
                                                            To *__restrict__ W, int *__restrict__ status,
-                                                           int max_sweeps) {
-    jacobi_osvd_body<Ta, To, BW, NR>(R, l, lp, sig, UR, W, status, max_sweeps);
+                                                           int max_sweeps, Ta *gws) {
+    jacobi_osvd_body<Ta, To, BW, NR>(R, l, lp, sig, UR, W, status, max_sweeps, gws);
 }
 
 template <typename Ta, typename To, int BW, int NR, int MAXT>
@@ -570,7 +584,7 @@ __global__ void __launch_bounds__(MAXT) jacobi_osvd_batch_kernel(const JacTab *_
                                                                  int max_sweeps) {
     const JacTab t = tab[blockIdx.x];
     jacobi_osvd_body<Ta, To, BW, NR>(t.R, l, lp, t.sig, static_cast<To *>(t.UR), static_cast<To *>(t.W), t.status,
-                                     max_sweeps);
+                                     max_sweeps, nullptr);
 }
 
 // sig[i] = x_i^T R w_i / (||x_i|| ||w_i||) in float64 for the columns x_i of UR and
@@ -812,14 +826,30 @@ size_t chol_smem_bytes(int l) {
 
 }  // namespace
 
+size_t chol_scratch_bytes(int l, size_t tk) {
+    const int LL = 16 * ((l + 15) / 16), S = LL + (tk == 4 ? 16 : 1);
+    return tk * 2 * (size_t)LL * S;
+}
+
 template <typename TG, typename Tk, typename Tc>
 cudaError_t chol_inv(const TG *G, int64_t ldg, int l, int64_t rows, double u, double *R, double *Rinv, Tc *Rinv_c,
-                     int lp, int *status, cudaStream_t s) {
+                     int lp, int *status, cudaStream_t s, void *scratch) {
     const double coef = chol_shift_coef(rows, l, u);
-    const size_t smem = chol_smem_bytes<Tk>(l);
-    if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    cudaFuncSetAttribute(chol_inv_kernel<TG, Tk, Tc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    chol_inv_kernel<TG, Tk, Tc><<<1, 256, smem, s>>>(G, ldg, l, coef, R, Rinv, Rinv_c, lp, status);
+    size_t smem = chol_smem_bytes<Tk>(l);
+    Tk *gws = nullptr;
+    if (smem > 227 * 1024) {  // matrices in the global scratch, pivots in shared memory
+        if (!scratch) return cudaErrorInvalidValue;
+        gws = static_cast<Tk *>(scratch);
+        smem = sizeof(Tk) * 16 * (size_t)((l + 15) / 16);
+    }
+    if (gws) {
+        cudaFuncSetAttribute(chol_inv_kernel<TG, Tk, Tc, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        chol_inv_kernel<TG, Tk, Tc, true><<<1, 256, smem, s>>>(G, ldg, l, coef, R, Rinv, Rinv_c, lp, status, gws);
+    } else {
+        cudaFuncSetAttribute(chol_inv_kernel<TG, Tk, Tc, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        chol_inv_kernel<TG, Tk, Tc, false><<<1, 256, smem, s>>>(G, ldg, l, coef, R, Rinv, Rinv_c, lp, status, nullptr);
+    }
     note_launch();
     return cudaGetLastError();
 }
@@ -863,12 +893,20 @@ size_t jacobi_smem(int l, int bw) {
            sizeof(double) * (size_t)bj_blocks(l, bw) * bw + 16;
 }
 
+// the per-column arrays only (X and V in the global scratch)
+template <typename Ta>
+size_t jacobi_smem_small(int l, int bw) {
+    const int L = l + (l & 1);
+    return sizeof(double) * L + sizeof(int) * L + sizeof(double) * L + sizeof(double) * (size_t)bj_blocks(l, bw) * bw +
+           16;
+}
+
 template <typename Ta, typename To, int BW, int NR>
 void launch_jacobi(const JacTab *tab, int count, const double *R, int l, int lp, double *sig, To *UR, To *W,
-                   int *status, cudaStream_t s) {
-    // float64, the 8-wide blocks and 5 rows per lane need up to 255 registers: 8 warps; else 16
-    constexpr int MAXT = (sizeof(Ta) == 8 || BW == 8 || NR == 5) ? 256 : 512;
-    const size_t smem = jacobi_smem<Ta>(l, BW);
+                   int *status, cudaStream_t s, Ta *gws) {
+    // float64, the 8-wide blocks and 5 or more rows per lane need up to 255 registers: 8 warps; else 16
+    constexpr int MAXT = (sizeof(Ta) == 8 || BW == 8 || NR >= 5) ? 256 : 512;
+    const size_t smem = gws ? jacobi_smem_small<Ta>(l, BW) : jacobi_smem<Ta>(l, BW);
     const int threads = 32 * std::min(bj_blocks(l, BW) / 2, MAXT / 32);
     if (tab) {
         cudaFuncSetAttribute(jacobi_osvd_batch_kernel<Ta, To, BW, NR, MAXT>,
@@ -877,48 +915,68 @@ void launch_jacobi(const JacTab *tab, int count, const double *R, int l, int lp,
     } else {
         cudaFuncSetAttribute(jacobi_osvd_kernel<Ta, To, BW, NR, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
-        jacobi_osvd_kernel<Ta, To, BW, NR, MAXT><<<1, threads, smem, s>>>(R, l, lp, sig, UR, W, status, 40);
+        jacobi_osvd_kernel<Ta, To, BW, NR, MAXT><<<1, threads, smem, s>>>(R, l, lp, sig, UR, W, status, 40, gws);
     }
 }
 
 template <typename Ta, typename To>
 cudaError_t jacobi_dispatch(const JacTab *tab, int count, const double *R, int l, int lp, double *sig, To *UR,
-                            To *W, int *status, cudaStream_t s) {
+                            To *W, int *status, cudaStream_t s, void *scratch) {
     int bw, nr;
     jacobi_shape<Ta>(l, bw, nr);
-    if (nr > (sizeof(Ta) == 8 ? 4 : 5) || jacobi_smem<Ta>(l, bw) > 227 * 1024) return cudaErrorInvalidValue;
+    Ta *gws = nullptr;
+    if (nr >= 6) {  // X and V in the global scratch (single problems only)
+        if (tab || !scratch) return cudaErrorInvalidValue;
+        gws = static_cast<Ta *>(scratch);
+    }
+    if (nr > (sizeof(Ta) == 8 ? 4 : 9) || (!gws && jacobi_smem<Ta>(l, bw) > 227 * 1024)) return cudaErrorInvalidValue;
     if constexpr (sizeof(Ta) == 4) {
         if (bw == 8) {
             switch (nr) {
-                case 3: launch_jacobi<Ta, To, 8, 3>(tab, count, R, l, lp, sig, UR, W, status, s); break;
-                default: launch_jacobi<Ta, To, 8, 4>(tab, count, R, l, lp, sig, UR, W, status, s); break;
+                case 3: launch_jacobi<Ta, To, 8, 3>(tab, count, R, l, lp, sig, UR, W, status, s, gws); break;
+                default: launch_jacobi<Ta, To, 8, 4>(tab, count, R, l, lp, sig, UR, W, status, s, gws); break;
             }
             note_launch();
             return cudaGetLastError();
         }
     }
     switch (nr) {
-        case 1: launch_jacobi<Ta, To, 4, 1>(tab, count, R, l, lp, sig, UR, W, status, s); break;
-        case 2: launch_jacobi<Ta, To, 4, 2>(tab, count, R, l, lp, sig, UR, W, status, s); break;
-        case 3: launch_jacobi<Ta, To, 4, 3>(tab, count, R, l, lp, sig, UR, W, status, s); break;
-        case 4: launch_jacobi<Ta, To, 4, 4>(tab, count, R, l, lp, sig, UR, W, status, s); break;
+        case 1: launch_jacobi<Ta, To, 4, 1>(tab, count, R, l, lp, sig, UR, W, status, s, gws); break;
+        case 2: launch_jacobi<Ta, To, 4, 2>(tab, count, R, l, lp, sig, UR, W, status, s, gws); break;
+        case 3: launch_jacobi<Ta, To, 4, 3>(tab, count, R, l, lp, sig, UR, W, status, s, gws); break;
+        case 4: launch_jacobi<Ta, To, 4, 4>(tab, count, R, l, lp, sig, UR, W, status, s, gws); break;
         default:
-            if constexpr (sizeof(Ta) == 4) launch_jacobi<Ta, To, 4, 5>(tab, count, R, l, lp, sig, UR, W, status, s);
+            if constexpr (sizeof(Ta) == 4) {
+                switch (nr) {
+                    case 5: launch_jacobi<Ta, To, 4, 5>(tab, count, R, l, lp, sig, UR, W, status, s, gws); break;
+                    case 6: launch_jacobi<Ta, To, 4, 6>(tab, count, R, l, lp, sig, UR, W, status, s, gws); break;
+                    case 7: launch_jacobi<Ta, To, 4, 7>(tab, count, R, l, lp, sig, UR, W, status, s, gws); break;
+                    case 8: launch_jacobi<Ta, To, 4, 8>(tab, count, R, l, lp, sig, UR, W, status, s, gws); break;
+                    default: launch_jacobi<Ta, To, 4, 9>(tab, count, R, l, lp, sig, UR, W, status, s, gws); break;
+                }
+            }
             break;
     }
     note_launch();
     return cudaGetLastError();
 }
 
+size_t jacobi_scratch_bytes(int l, size_t ta) {
+    const int L = l + (l & 1);
+    const int bw = (ta == 4 && l > 64 && L <= 128) ? 8 : 4;
+    return ta * 2 * (size_t)bj_blocks(l, bw) * bw * L;
+}
+
 template <typename Ta, typename To>
-cudaError_t jacobi_osvd(const double *R, int l, int lp, double *sig, To *UR, To *W, int *status, cudaStream_t s) {
-    return jacobi_dispatch<Ta, To>(nullptr, 1, R, l, lp, sig, UR, W, status, s);
+cudaError_t jacobi_osvd(const double *R, int l, int lp, double *sig, To *UR, To *W, int *status, cudaStream_t s,
+                        void *scratch) {
+    return jacobi_dispatch<Ta, To>(nullptr, 1, R, l, lp, sig, UR, W, status, s, scratch);
 }
 
 template <typename Ta, typename To>
 cudaError_t jacobi_osvd_batched(const JacTab *tab, int count, int l, int lp, cudaStream_t s) {
     if (count < 1) return cudaSuccess;
-    return jacobi_dispatch<Ta, To>(tab, count, nullptr, l, lp, nullptr, nullptr, nullptr, nullptr, s);
+    return jacobi_dispatch<Ta, To>(tab, count, nullptr, l, lp, nullptr, nullptr, nullptr, nullptr, s, nullptr);
 }
 
 template <typename To>
@@ -997,16 +1055,16 @@ cudaError_t pca_select(const double *sigma, int count, const double *fro2, doubl
 
 #define INST_CHOL(TG, TK, TC)                                                                                   \
     template cudaError_t chol_inv<TG, TK, TC>(const TG *, int64_t, int, int64_t, double, double *, double *, TC *, \
-                                              int, int *, cudaStream_t);
+                                              int, int *, cudaStream_t, void *);
 INST_CHOL(float, float, float)
 INST_CHOL(float, double, float)
 INST_CHOL(double, double, double)
 template cudaError_t jacobi_osvd<float, float>(const double *, int, int, double *, float *, float *, int *,
-                                               cudaStream_t);
+                                               cudaStream_t, void *);
 template cudaError_t jacobi_osvd<double, float>(const double *, int, int, double *, float *, float *, int *,
-                                                cudaStream_t);
+                                                cudaStream_t, void *);
 template cudaError_t jacobi_osvd<double, double>(const double *, int, int, double *, double *, double *, int *,
-                                                 cudaStream_t);
+                                                 cudaStream_t, void *);
 template cudaError_t gram_finish<float>(const double *, const double *, int, double *, float *, int *, cudaStream_t);
 template cudaError_t gram_finish<double>(const double *, const double *, int, double *, double *, int *,
                                          cudaStream_t);

@@ -466,6 +466,16 @@ cudaError_t launch16_tn(const CUtensorMap &a, const CUtensorMap *q, int64_t rows
 template <int ESZ>
 cudaError_t gemm_nn_e(int64_t m, int n, int N, const void *A, int64_t lda, const void *Zt, int64_t ldz, float *Y,
                       int64_t ldy, const float *ts, const float *c, int *status, cudaStream_t s) {
+    if (N > 128 && N % 16 == 0) {  // column slices (A read once per slice)
+        const int w = column_slice(N);
+        for (int c0 = 0; c0 < N; c0 += w) {
+            const cudaError_t e =
+                gemm_nn_e<ESZ>(m, n, w < N - c0 ? w : N - c0, A, lda, static_cast<const uint8_t *>(Zt) + c0 * ldz * ESZ,
+                               ldz, Y + c0, ldy, ts ? ts + c0 : nullptr, c ? c + c0 : nullptr, status, s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     if (N % 16 || N < 16 || N > 128) return cudaErrorInvalidValue;
     constexpr int BK = Elt<ESZ>::NN_BK;
     CUtensorMap ma, mb;
@@ -489,6 +499,18 @@ cudaError_t gemm_tn_e(int64_t rows, int ncols, int N, const void *A, int64_t lda
                       int64_t ldq, float *C, int64_t ldc, float *part, int64_t part_elems, const float *cs,
                       const float *qs, const float *mu, const double *qsum, int *status, cudaStream_t s) {
     using E = Elt<ESZ>;
+    if (N > 128 && N % 16 == 0) {  // column slices of the Q terms and C (A read once per slice)
+        const int w = column_slice(N);
+        for (int c0 = 0; c0 < N; c0 += w) {
+            const void *qs_[3];
+            for (int i = 0; i < nq && i < 3; i++) qs_[i] = static_cast<const uint8_t *>(Q[i]) + c0 * ESZ;
+            const cudaError_t e = gemm_tn_e<ESZ>(rows, ncols, w < N - c0 ? w : N - c0, A, lda, qs_, nq, ldq, C + c0,
+                                                 ldc, part, part_elems, cs, qs ? qs + c0 : nullptr, mu,
+                                                 qsum ? qsum + c0 : nullptr, status, s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     if (N % 16 || N < 16 || N > 128 || (nq != 1 && nq != 3) || (ESZ == 1 && nq != 1)) return cudaErrorInvalidValue;
     const Split16 sp = split16(rows, ncols, E::TN_BK);
     if (!part || part_elems < (int64_t)sp.chunks * ncols * N) return cudaErrorInvalidValue;

@@ -50,6 +50,7 @@ struct rsvd_plan {
     double *G64 = nullptr, *R1 = nullptr, *R1i = nullptr, *R2 = nullptr, *R2i = nullptr, *Rt = nullptr;
     double *lam = nullptr, *Vfull = nullptr, *sig = nullptr;
     int *status = nullptr, *Kdev = nullptr;
+    void *chol_ws = nullptr, *jac_ws = nullptr;  // global l x l blocks of the small solvers (large l only)
     int last_count = 0;
     // tensor-core path (float32): transposed tf32 split of the small operand, split-K partials
     bool tc = false;
@@ -159,6 +160,10 @@ void carve(rsvd_plan *P, Carver &c) {
     P->sig = (double *)c.take(sizeof(double) * (n > sq ? n : sq));
     P->status = (int *)c.take(sizeof(int));
     P->Kdev = (int *)c.take(2 * sizeof(int));
+    if (P->lp > kSmallMaxF64)  // l x l blocks of the Cholesky beyond one SM's shared memory (float64 sizing)
+        P->chol_ws = c.take(chol_scratch_bytes(P->lp, sizeof(double)));
+    if (P->lp > 160)           // and of the float32 Jacobi
+        P->jac_ws = c.take(jacobi_scratch_bytes(P->lp, sizeof(float)));
     if (P->dtype == RSVD_FP8_E4M3) {
         P->ldz8 = round_up(n, 16);
         P->Zq8 = c.take((size_t)P->lp * P->ldz8);
@@ -309,16 +314,16 @@ rsvd_status cqr(rsvd_plan *P, const T *X, int64_t rows, int w, int ld, T *Qo, T 
     if (skinny) CK(prod_tn<T>(P, rows, ld, X, ld, X, ld, G, ld));
     else CK(gemm_tn<T>(rows, ld, ld, X, ld, X, ld, G, ld, part, P->part_elems, s));
     if (f64)
-        CK(chol_inv<T, double, T>(G, ld, w, rows, u, P->R1, P->R1i, Ric, ld, P->status, s));
-    else CK(chol_inv<T, T, T>(G, ld, w, rows, u, P->R1, P->R1i, Ric, ld, P->status, s));
+        CK(chol_inv<T, double, T>(G, ld, w, rows, u, P->R1, P->R1i, Ric, ld, P->status, s, P->chol_ws));
+    else CK(chol_inv<T, T, T>(G, ld, w, rows, u, P->R1, P->R1i, Ric, ld, P->status, s, P->chol_ws));
     if (skinny) CK(prod_nn<T>(P, rows, ld, X, ld, Ric, ld, Q1, ld));
     else CK(gemm_nn<T>(rows, ld, ld, X, ld, Ric, ld, Q1, ld, s));
     if (passes == 1) return RSVD_OK;
     if (skinny) CK(prod_tn<T>(P, rows, ld, Q1, ld, Q1, ld, G, ld));
     else CK(gemm_tn<T>(rows, ld, ld, Q1, ld, Q1, ld, G, ld, part, P->part_elems, s));
     if (f64)
-        CK(chol_inv<T, double, T>(G, ld, w, rows, u, P->R2, P->R2i, Ric, ld, P->status, s));
-    else CK(chol_inv<T, T, T>(G, ld, w, rows, u, P->R2, P->R2i, Ric, ld, P->status, s));
+        CK(chol_inv<T, double, T>(G, ld, w, rows, u, P->R2, P->R2i, Ric, ld, P->status, s, P->chol_ws));
+    else CK(chol_inv<T, T, T>(G, ld, w, rows, u, P->R2, P->R2i, Ric, ld, P->status, s, P->chol_ws));
     if (skinny) CK(prod_nn<T>(P, rows, ld, Q1, ld, Ric, ld, Qo, ld));
     else CK(gemm_nn<T>(rows, ld, ld, Q1, ld, Ric, ld, Qo, ld, s));
     if (want_r) CK(trmm_upper(P->R2, P->R1, P->Rt, w, s));
@@ -392,7 +397,7 @@ rsvd_status run_rsvd(rsvd_plan *P, T *A, const T *Omega, double *S, T *U, T *V) 
     {
         Span sp(P, RSVD_STAGE_SMALL);
         if ((st = cqr2<T>(P, Tn, n, l, lp, Qz, Tmpn, true))) return st;       // T = Q_T R
-        CK(jacobi_osvd<T, T>(P->Rt, l, lp, P->sig, UR, W, P->status, s));     // R = U_R Sigma W^T
+        CK(jacobi_osvd<T, T>(P->Rt, l, lp, P->sig, UR, W, P->status, s, P->jac_ws));     // R = U_R Sigma W^T
         CK(sv_refine<T>(P->Rt, l, lp, UR, W, P->sig, s));                     // sigma_i = u_i^T R w_i (float64)
     }
     {
@@ -468,7 +473,7 @@ rsvd_status run_rsvd_bf16(rsvd_plan *P, const void *A, const float *Omega, doubl
         if ((st = cqr2<float>(P, Tn, n, l, lp, Qz, Tmpn, true))) return st;
         // float32 rotations, float64 Rayleigh-quotient values (the float64 rate of this
         // GPU is 1/58 of float32: a float64 Jacobi of l = 112 takes ~50 ms)
-        CK(jacobi_osvd<float, float>(P->Rt, l, lp, P->sig, UR, W, P->status, s));
+        CK(jacobi_osvd<float, float>(P->Rt, l, lp, P->sig, UR, W, P->status, s, P->jac_ws));
         CK(sv_refine<float>(P->Rt, l, lp, UR, W, P->sig, s));
     }
     {
@@ -548,7 +553,7 @@ rsvd_status run_rsvd_fp8(rsvd_plan *P, const void *A, const float *sc, const flo
     {
         Span sp(P, RSVD_STAGE_SMALL);
         if ((st = cqr2<float>(P, Tn, n, l, lp, Qz, Tmpn, true))) return st;
-        CK(jacobi_osvd<float, float>(P->Rt, l, lp, P->sig, UR, W, P->status, s));
+        CK(jacobi_osvd<float, float>(P->Rt, l, lp, P->sig, UR, W, P->status, s, P->jac_ws));
         CK(sv_refine<float>(P->Rt, l, lp, UR, W, P->sig, s));
     }
     {
@@ -958,7 +963,7 @@ rsvd_status plan_init(rsvd_plan *P, int64_t m, int64_t n, int k, int p, int q, r
     if ((int64_t)k + p > n) return RSVD_ERR_ARG;
     if (dtype != RSVD_F32 && dtype != RSVD_F64 && dtype != RSVD_BF16 && dtype != RSVD_FP8_E4M3)
         return RSVD_ERR_UNSUPPORTED;
-    if (k + p > (dtype == RSVD_F32 ? kSmallMaxF32 : kSmallMaxF64)) return RSVD_ERR_UNSUPPORTED;
+    if (k + p > (dtype == RSVD_F64 ? kSmallMaxF64 : kRsvdMaxL)) return RSVD_ERR_UNSUPPORTED;
     // TMA rows of 16-byte multiples: n % 8 (bfloat16), n % 16 (e4m3)
     if (dtype == RSVD_BF16 && (n % 8 || !tc_available())) return RSVD_ERR_UNSUPPORTED;
     if (dtype == RSVD_FP8_E4M3 && (n % 16 || !tc_available())) return RSVD_ERR_UNSUPPORTED;
@@ -973,7 +978,7 @@ rsvd_status plan_init(rsvd_plan *P, int64_t m, int64_t n, int k, int p, int q, r
     P->wide = P->lp > P->nx ? P->lp : P->nx;
     P->dtype = dtype;
     P->stream = (cudaStream_t)cuda_stream;
-    P->tc = dtype != RSVD_F64 && P->lp <= 128 && tc_available();
+    P->tc = dtype != RSVD_F64 && tc_available();
     if (P->tc) {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune.find(tune_key(m, n, P->lp));
@@ -1013,11 +1018,11 @@ rsvd_status serve_batch_launch(ServeBatch *b, int count, rsvd_plan *const *plans
                                const float *const *sc, const float *const *Om, double *const *S, float *const *U,
                                float *const *V, const double *t, int *host_out) {
     const rsvd_dtype dt = plans[0]->dtype;
-    if (dt == RSVD_F32 || dt == RSVD_F64) {  // lockstep batch
+    if ((dt == RSVD_F32 || dt == RSVD_F64) && plans[0]->l <= kSmallMaxF32) {  // lockstep batch
         const rsvd_status st = batch_direct(b->ctx, count, plans, (void *const *)A, (const void *const *)Om, S,
                                             (void *const *)U, (void *const *)V);
         if (st != RSVD_OK) return st;
-    } else {  // precision forms: every problem's solve on its own stream, then joined
+    } else {  // precision forms and large l: every problem's solve on its own stream, then joined
         CK(b->ctx.reserve(count));
         CK(fork(b->ctx, count, plans));
         for (int i = 0; i < count; i++) {
@@ -1206,6 +1211,7 @@ rsvd_status rsvd_batch_create(rsvd_batch_t *batch, int count, rsvd_plan_t const 
         if (!P) return RSVD_ERR_ARG;
         if (P->dtype != plans[0]->dtype || P->l != plans[0]->l || P->q != plans[0]->q) return RSVD_ERR_ARG;
         if (P->dtype != RSVD_F32 && P->dtype != RSVD_F64) return RSVD_ERR_UNSUPPORTED;
+        if (P->l > kSmallMaxF32) return RSVD_ERR_UNSUPPORTED;  // batched small kernels: l x l in shared memory
         for (int j = 0; j < i; j++)
             if (plans[j] == P) return RSVD_ERR_ARG;
     }
@@ -1301,7 +1307,7 @@ rsvd_status rsvd_autotune(rsvd_plan_t P, void *A, const void *Omega, int concurr
     if (!P || !A || !Omega || concurrency < 1 || concurrency > 64) return RSVD_ERR_ARG;
     if (nn_out) *nn_out = P->nn_ctas;
     if (tn_out) *tn_out = P->tn_ctas;
-    if (P->dtype != RSVD_F32 || !P->tc) return RSVD_OK;  // nothing to tune on the CUDA-core path
+    if (P->dtype != RSVD_F32 || !P->tc || P->l > kSmallMaxF32) return RSVD_OK;  // tunes through lockstep batches (l <= 128)
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return RSVD_ERR_CUDA;

@@ -52,9 +52,14 @@ def test_plan_create_rejects_unbuilt_dtypes():
     h = ctypes.c_void_p()
     for dt in (g.RSVD_FP8_E4M3, 7):
         assert g.lib().rsvd_plan_create(ctypes.byref(h), 100, 20, 4, 2, 1, dt, None) == g.RSVD_ERR_UNSUPPORTED
-    # bfloat16 plans need rows of whole 16-byte units (n a multiple of 8) and l <= 112
+    # bfloat16 plans need rows of whole 16-byte units (n a multiple of 8) and l <= 288
     assert g.lib().rsvd_plan_create(ctypes.byref(h), 100, 20, 4, 2, 1, g.RSVD_BF16, None) == g.RSVD_ERR_UNSUPPORTED
-    assert g.lib().rsvd_plan_create(ctypes.byref(h), 1000, 256, 100, 16, 1, g.RSVD_BF16, None) == \
+    assert g.lib().rsvd_plan_create(ctypes.byref(h), 1000, 512, 280, 16, 1, g.RSVD_BF16, None) == \
+        g.RSVD_ERR_UNSUPPORTED
+    # float32 randomized solves up to l = 288, float64 up to 112
+    assert g.lib().rsvd_plan_create(ctypes.byref(h), 1000, 512, 280, 16, 1, g.RSVD_F32, None) == \
+        g.RSVD_ERR_UNSUPPORTED
+    assert g.lib().rsvd_plan_create(ctypes.byref(h), 1000, 512, 100, 16, 1, g.RSVD_F64, None) == \
         g.RSVD_ERR_UNSUPPORTED
 
 

@@ -67,7 +67,10 @@ def _run_rsvd(A_host, Om_host, k, p, q, dtype):
     (4096, 256, 50, 10, 2),    # the workload's k, p, q at reduced size
     (777, 64, 10, 6, 0),       # no power iteration
     (3000, 40, 30, 10, 1),     # l = n (full width)
-    (6000, 300, 120, 8, 1),    # l = 128, the largest float32 sketch
+    (6000, 300, 120, 8, 1),    # l = 128, the largest float32 batched / lockstep-served sketch
+    (6000, 300, 136, 8, 1),    # l = 144: products on two column slices
+    (6000, 300, 160, 16, 1),   # l = 176: Cholesky and Jacobi blocks in the global scratch
+    (8000, 400, 256, 32, 1),   # l = 288, the largest single solve
 ])
 def test_rsvd_f32_matches_oracle(m, n, k, p, q):
     A0 = _matrix(m, n)
