@@ -14,6 +14,7 @@
 #include <float.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -428,17 +429,47 @@ __device__ __forceinline__ void bj_round(int kind, int rd, Ta (&x)[2 * BW][NR], 
 
 // X, V: Lc columns of L rows each (column c at X + c L); rows >= L of a lane are zero.
 // Warp w takes block pairs w, w + nwarps, ... of each block round.
+// Synchronisation of the sweep: one CTA (__syncthreads), or the CTAs of a thread-block
+// cluster (hardware cluster barrier with release / acquire, which also orders the
+// global-memory columns between the CTAs).
+struct CtaSync {
+    static constexpr bool size_is_one = true;
+    static __device__ __forceinline__ void sync() { __syncthreads(); }
+    static __device__ __forceinline__ int rank() { return 0; }
+    static __device__ __forceinline__ int size() { return 1; }
+};
+struct ClusterSync {
+    static constexpr bool size_is_one = false;
+    static __device__ __forceinline__ void sync() {
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    }
+    static __device__ __forceinline__ int rank() {
+        unsigned r;
+        asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+        return (int)r;
+    }
+    static __device__ __forceinline__ int size() {
+        unsigned r;
+        asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+        return (int)r;
+    }
+};
+
 // trk: the squared column norms, recomputed from the columns at the start of
 // every sweep and carried (updated by the rotations) from block round to block round.
-template <typename Ta, int BW, int NR>
+// The block pairs of a round go to the warps of all CTAs of the group (warp w of CTA
+// r is warp r * nwarps + w).  rotated: one int in shared memory (CtaSync) or
+// max_sweeps zeroed counters in global memory (ClusterSync).
+template <typename Ta, int BW, int NR, typename Sync>
 __device__ __forceinline__ bool bj_sweeps(Ta *X, Ta *V, Ta *trk, int l, int L, int nb, int max_sweeps,
                                           int *rotated) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int warp = Sync::rank() * nwarps + (threadIdx.x >> 5), gwarps = Sync::size() * nwarps;
     const Ta tol = (Ta)(sqrt((double)l) * Eps<Ta>::v), tol2 = tol * tol;
     Ta x[2 * BW][NR], v[2 * BW][NR], nr[2 * BW];
     for (int sweep = 0; sweep < max_sweeps; sweep++) {
         bool rot = false;
-        for (int p = warp; p < nb * BW; p += nwarps) {
+        for (int p = warp; p < nb * BW; p += gwarps) {
             Ta ss = Ta(0);
 #pragma unroll
             for (int r = 0; r < NR; r++) {
@@ -449,9 +480,9 @@ __device__ __forceinline__ bool bj_sweeps(Ta *X, Ta *V, Ta *trk, int l, int L, i
             ss = warp_sum(ss);
             if (lane == 0) trk[p] = ss;
         }
-        __syncthreads();
+        Sync::sync();
         for (int br = 0; br < nb - 1; br++) {
-          for (int bp = warp; bp < nb / 2; bp += nwarps) {
+          for (int bp = warp; bp < nb / 2; bp += gwarps) {
             const int A = rr_pos(bp, br, nb), B = rr_pos(nb - 1 - bp, br, nb);
 #pragma unroll
             for (int c = 0; c < 2 * BW; c++) {
@@ -484,13 +515,19 @@ __device__ __forceinline__ bool bj_sweeps(Ta *X, Ta *V, Ta *trk, int l, int L, i
                 if (lane == 0) trk[col] = nr[c];
             }
           }
-            __syncthreads();
+            Sync::sync();
         }
-        if (threadIdx.x == 0) *rotated = 0;
-        __syncthreads();
-        if (__any_sync(0xffffffffu, rot) && lane == 0) *rotated = 1;
-        __syncthreads();
-        if (!*rotated) return true;
+        if constexpr (Sync::size_is_one) {
+            if (threadIdx.x == 0) *rotated = 0;
+            __syncthreads();
+            if (__any_sync(0xffffffffu, rot) && lane == 0) *rotated = 1;
+            __syncthreads();
+            if (!*rotated) return true;
+        } else {
+            if (__any_sync(0xffffffffu, rot) && lane == 0) atomicAdd(rotated + sweep, 1);
+            Sync::sync();
+            if (*reinterpret_cast<volatile int *>(rotated + sweep) == 0) return true;
+        }
     }
     return false;
 }
@@ -507,8 +544,10 @@ __device__ __forceinline__ void jacobi_osvd_body(const double *__restrict__ R, i
     extern __shared__ __align__(16) unsigned char smraw[];
     const int L = l + (l & 1);
     const int nb = bj_blocks(l, BW), Lc = nb * BW;
-    // NR >= 6 (more than 160 rows) is only used with the global scratch
+    // NR >= 6 (more than 160 rows) is only used with the global scratch, by the CTAs of
+    // a cluster: X, V, the tracked norms and the per-sweep rotation counters in gws
     constexpr bool GM = NR >= 6;
+    using Sync = typename std::conditional<GM, ClusterSync, CtaSync>::type;
     Ta *X = GM ? gws : reinterpret_cast<Ta *>(smraw);  // X[p * L + i]: column p of the rotated matrix (Lc columns)
     Ta *V = X + (size_t)Lc * L;                        // V[p * L + i]: column p of the accumulated rotation
     double *nrm = GM ? reinterpret_cast<double *>(smraw)
@@ -516,16 +555,20 @@ __device__ __forceinline__ void jacobi_osvd_body(const double *__restrict__ R, i
     int *perm = reinterpret_cast<int *>(nrm + L);
     __shared__ int rotated;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    for (int idx = tid; idx < Lc * L; idx += nt) {
+    const int gt = Sync::rank() * nt + tid, gnt = Sync::size() * nt;
+    for (int idx = gt; idx < Lc * L; idx += gnt) {
         const int p = idx / L, i = idx % L;
         X[idx] = (p < l && i < l) ? (Ta)R[i * l + p] : Ta(0);
         V[idx] = (p == i) ? Ta(1) : Ta(0);
     }
-    __syncthreads();
+    Ta *trk = GM ? V + (size_t)Lc * L : reinterpret_cast<Ta *>(perm + L) + L;  // (shared: after vn)
+    int *rotcnt = GM ? reinterpret_cast<int *>(trk + Lc) : &rotated;
+    if (GM && Sync::rank() == 0 && tid < max_sweeps) rotcnt[tid] = 0;
+    Sync::sync();
     // rotate when |x_p . x_q| > tol ||x_p|| ||x_q||, tol = sqrt(l) eps: the converged
     // columns are then orthogonal to sqrt(l) eps (an l eps threshold leaves l eps)
-    Ta *trk = reinterpret_cast<Ta *>(perm + L) + L;  // after the column scales vn (see below)
-    const bool converged = bj_sweeps<Ta, BW, NR>(X, V, trk, l, L, nb, max_sweeps, &rotated);
+    const bool converged = bj_sweeps<Ta, BW, NR, Sync>(X, V, trk, l, L, nb, max_sweeps, rotcnt);
+    if (GM && Sync::rank() != 0) return;  // the first CTA sorts and writes the results
     if (!converged && tid == 0) atomicOr(status, (int)ST_NOCONV);
     Ta *nrm_t = reinterpret_cast<Ta *>(nrm);
     for (int p = warp; p < l; p += nw) {
@@ -912,6 +955,24 @@ void launch_jacobi(const JacTab *tab, int count, const double *R, int l, int lp,
         cudaFuncSetAttribute(jacobi_osvd_batch_kernel<Ta, To, BW, NR, MAXT>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         jacobi_osvd_batch_kernel<Ta, To, BW, NR, MAXT><<<count, threads, smem, s>>>(tab, l, lp, 40);
+    } else if (gws) {  // a cluster of up to 8 CTAs (one warp per block pair where possible)
+        auto kern = jacobi_osvd_kernel<Ta, To, BW, NR, MAXT>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const int pairs = bj_blocks(l, BW) / 2;
+        const int csize = std::max(1, std::min(8, (pairs + MAXT / 32 - 1) / (MAXT / 32)));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)csize);
+        cfg.blockDim = dim3((unsigned)threads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)csize;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, kern, R, l, lp, sig, UR, W, status, 40, gws);
     } else {
         cudaFuncSetAttribute(jacobi_osvd_kernel<Ta, To, BW, NR, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
@@ -964,7 +1025,8 @@ cudaError_t jacobi_dispatch(const JacTab *tab, int count, const double *R, int l
 size_t jacobi_scratch_bytes(int l, size_t ta) {
     const int L = l + (l & 1);
     const int bw = (ta == 4 && l > 64 && L <= 128) ? 8 : 4;
-    return ta * 2 * (size_t)bj_blocks(l, bw) * bw * L;
+    const size_t lc = (size_t)bj_blocks(l, bw) * bw;
+    return ta * (2 * lc * L + lc) + 64 * sizeof(int);  // X, V, tracked norms, rotation counters
 }
 
 template <typename Ta, typename To>
