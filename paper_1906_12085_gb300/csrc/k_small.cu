@@ -66,6 +66,32 @@ template <typename T> struct Eps;
 template <> struct Eps<float> { static constexpr double v = FLT_EPSILON; };
 template <> struct Eps<double> { static constexpr double v = DBL_EPSILON; };
 
+// Synchronisation of the small solvers: one CTA (__syncthreads), or the CTAs of a
+// thread-block cluster (hardware cluster barrier with release / acquire, which also orders the
+// global-memory columns between the CTAs).
+struct CtaSync {
+    static constexpr bool size_is_one = true;
+    static __device__ __forceinline__ void sync() { __syncthreads(); }
+    static __device__ __forceinline__ int rank() { return 0; }
+    static __device__ __forceinline__ int size() { return 1; }
+};
+struct ClusterSync {
+    static constexpr bool size_is_one = false;
+    static __device__ __forceinline__ void sync() {
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    }
+    static __device__ __forceinline__ int rank() {
+        unsigned r;
+        asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+        return (int)r;
+    }
+    static __device__ __forceinline__ int size() {
+        unsigned r;
+        asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+        return (int)r;
+    }
+};
+
 // ------------------------------------------------------------ Cholesky + inverse
 // Upper Cholesky R^T R = G and the inverse X = R^{-1} of an l x l matrix in one
 // CTA of 256 threads, blocked by 16-column panels (NP = ceil(l / 16) panels, the
@@ -91,8 +117,8 @@ struct CholSmem {
     int S;  // row stride of A and X
 };
 
-// A and X in shared memory, or (gws != NULL, matrices too large for one SM) in the
-// global scratch gws (2 LL S elements; L2-resident); the pivots always in shared memory.
+// A and X in shared memory, or (GM: matrices too large for one SM) with the pivots in
+// the global scratch gws (2 LL S + LL elements, then the trace and breakdown flag).
 template <typename Tk, bool GM>
 __device__ __forceinline__ CholSmem<Tk> chol_smem(int LL, Tk *gws) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -101,7 +127,7 @@ __device__ __forceinline__ CholSmem<Tk> chol_smem(int LL, Tk *gws) {
     if constexpr (GM) {
         m.A = gws;
         m.X = gws + (size_t)LL * m.S;
-        m.rdiag = reinterpret_cast<Tk *>(smraw);
+        m.rdiag = gws + 2 * (size_t)LL * m.S;
     } else {
         m.A = reinterpret_cast<Tk *>(smraw);
         m.X = m.A + (size_t)LL * m.S;
@@ -115,25 +141,37 @@ __device__ __forceinline__ void chol_inv_body(const TG *__restrict__ G, int64_t 
                                               double *__restrict__ R, double *__restrict__ Rinv,
                                               Tc *__restrict__ Rinv_c, int lp, int *__restrict__ status,
                                               Tk *gws = nullptr) {
+    // GM: the matrices, the pivots and the breakdown flag in the global scratch, the work
+    // shared by the CTAs of a cluster (cluster barriers between the phases)
+    using Sync = typename std::conditional<GM, ClusterSync, CtaSync>::type;
     const int NP = (l + 15) >> 4, LL = 16 * NP;
     const CholSmem<Tk> sm = chol_smem<Tk, GM>(LL, gws);
     Tk *A = sm.A, *X = sm.X, *rdiag = sm.rdiag;
     const int S = sm.S;
-    __shared__ double trace;
-    __shared__ int bad;
+    __shared__ double trace_s;
+    __shared__ int bad_s;
+    double *tracep = &trace_s;
+    int *badp = &bad_s;
+    if constexpr (GM) {
+        tracep = reinterpret_cast<double *>(gws + 2 * (size_t)LL * S + ((LL + 1) & ~1));
+        badp = reinterpret_cast<int *>(tracep + 1);
+    }
+    volatile int *bad = badp;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, tx = tid & 15, ty = tid >> 4;
+    const int rank = Sync::rank(), nct = Sync::size();
+    const int gt = rank * 256 + tid, gnt = nct * 256;
     int used = 0;  // 0: plain, 1: shifted, 2: breakdown fallback (R = 0, R^{-1} = I)
     for (int attempt = 0; attempt < 3; attempt++) {
-        if (attempt == 1 && warp == 0) {  // trace for the shift (only after a breakdown)
+        if (attempt == 1 && rank == 0 && warp == 0) {  // trace for the shift (only after a breakdown)
             double tr = 0.0;
             for (int i = lane; i < l; i += 32) tr += (double)G[(int64_t)i * ldg + i];
             tr = warp_sum(tr);
-            if (lane == 0) trace = tr;
+            if (lane == 0) *tracep = tr;
         }
-        if (tid == 0) bad = 0;
-        __syncthreads();
-        const Tk sh = attempt == 1 ? (Tk)(shift_coef * trace) : Tk(0);
-        for (int idx = tid; idx < LL * LL; idx += 256) {  // upper triangle (the lower one is never read)
+        if (rank == 0 && tid == 0) *bad = 0;
+        Sync::sync();
+        const Tk sh = attempt == 1 ? (Tk)(shift_coef * *reinterpret_cast<volatile double *>(tracep)) : Tk(0);
+        for (int idx = gt; idx < LL * LL; idx += gnt) {  // upper triangle (the lower one is never read)
             const int i = idx / LL, j = idx % LL;
             if (j < i) continue;
             Tk v;
@@ -142,10 +180,10 @@ __device__ __forceinline__ void chol_inv_body(const TG *__restrict__ G, int64_t 
             if (i == j && i < l) v += sh;
             A[i * S + j] = v;
         }
-        __syncthreads();
+        Sync::sync();
         for (int p = 0; p < NP; p++) {
             const int o = 16 * p;
-            if (warp == 0) {  // (1) diagonal block: lane c (and c + 16) holds column o + c in registers
+            if (rank == 0 && warp == 0) {  // (1) diagonal block: lane c (and c + 16) holds column o + c in registers
                 const int c = lane & 15;
                 Tk col[16];
 #pragma unroll
@@ -169,16 +207,16 @@ __device__ __forceinline__ void chol_inv_body(const TG *__restrict__ G, int64_t 
                     __syncwarp();
                 }
                 if (!ok) {
-                    if (lane == 0) bad = 1;
+                    if (lane == 0) *bad = 1;
                 } else if (lane < 16) {
 #pragma unroll
                     for (int i = 0; i < 16; i++) A[(o + i) * S + o + c] = col[i];
                 }
             }
-            __syncthreads();
-            if (bad) break;
+            Sync::sync();
+            if (*bad) break;
             // (2) panel rows right of the block: R_pp^T x = a for every column c
-            for (int c = o + 16 + tid; c < LL; c += 256) {
+            for (int c = o + 16 + gt; c < LL; c += gnt) {
                 Tk x[16];
 #pragma unroll
                 for (int k = 0; k < 16; k++) x[k] = A[(o + k) * S + c];
@@ -191,31 +229,47 @@ __device__ __forceinline__ void chol_inv_body(const TG *__restrict__ G, int64_t 
 #pragma unroll
                 for (int k = 0; k < 16; k++) A[(o + k) * S + c] = x[k];
             }
-            __syncthreads();
+            Sync::sync();
             // (3) trailing update, blocks p < a <= b
-            for (int a = p + 1; a < NP; a++) {
-                const int i = 16 * a + ty;
-                Tk ri[16];
+            if constexpr (!GM) {
+                for (int a = p + 1; a < NP; a++) {
+                    const int i = 16 * a + ty;
+                    Tk ri[16];
 #pragma unroll
-                for (int k = 0; k < 16; k++) ri[k] = A[(o + k) * S + i];
-                for (int b = a; b < NP; b++) {
-                    const int c = 16 * b + tx;
+                    for (int k = 0; k < 16; k++) ri[k] = A[(o + k) * S + i];
+                    for (int b = a; b < NP; b++) {
+                        const int c = 16 * b + tx;
+                        Tk acc = A[i * S + c];
+#pragma unroll
+                        for (int k = 0; k < 16; k++) acc -= ri[k] * A[(o + k) * S + c];
+                        A[i * S + c] = acc;
+                    }
+                }
+            } else {  // the triangle of blocks dealt round-robin to the CTAs
+                const int na = NP - p - 1, ntri = na * (na + 1) / 2;
+                for (int t = rank; t < ntri; t += nct) {
+                    int a = p + 1, rem = t;
+                    while (rem >= NP - a) {
+                        rem -= NP - a;
+                        a++;
+                    }
+                    const int i = 16 * a + ty, c = 16 * (a + rem) + tx;
                     Tk acc = A[i * S + c];
 #pragma unroll
-                    for (int k = 0; k < 16; k++) acc -= ri[k] * A[(o + k) * S + c];
+                    for (int k = 0; k < 16; k++) acc -= A[(o + k) * S + i] * A[(o + k) * S + c];
                     A[i * S + c] = acc;
                 }
             }
-            __syncthreads();
+            Sync::sync();
         }
-        if (!bad) {
-            if (attempt > 0 && tid == 0) atomicOr(status, attempt == 1 ? (int)ST_SHIFT : (int)ST_CHOL);
+        if (!*bad) {
+            if (attempt > 0 && rank == 0 && tid == 0) atomicOr(status, attempt == 1 ? (int)ST_SHIFT : (int)ST_CHOL);
             used = attempt;
             break;
         }
-        __syncthreads();
+        Sync::sync();
     }
-    for (int idx = tid; idx < l * l; idx += 256) {
+    for (int idx = gt; idx < l * l; idx += gnt) {
         const int i = idx / l, j = idx % l;
         R[idx] = (used < 2 && j >= i) ? (double)A[i * S + j] : 0.0;
     }
@@ -223,7 +277,7 @@ __device__ __forceinline__ void chol_inv_body(const TG *__restrict__ G, int64_t 
     for (int p = NP - 1; p >= 0; p--) {
         const int o = 16 * p;
         // T = delta I - sum_{p<q<=b} R_pq X_qb for column blocks b >= p (written into X)
-        for (int b = p; b < NP; b++) {
+        for (int b = p + rank; b < NP; b += nct) {
             const int i = o + ty, c = 16 * b + tx;
             Tk acc = (b == p && ty == tx) ? Tk(1) : Tk(0);
             for (int q = p + 1; q <= b; q++) {
@@ -232,9 +286,9 @@ __device__ __forceinline__ void chol_inv_body(const TG *__restrict__ G, int64_t 
             }
             X[i * S + c] = acc;
         }
-        __syncthreads();
+        Sync::sync();
         // X_pb = R_pp^{-1} T: back substitution inside the block, one thread per column
-        for (int c = o + tid; c < LL; c += 256) {
+        for (int c = o + gt; c < LL; c += gnt) {
             Tk x[16];
 #pragma unroll
             for (int k = 0; k < 16; k++) x[k] = X[(o + k) * S + c];
@@ -247,13 +301,13 @@ __device__ __forceinline__ void chol_inv_body(const TG *__restrict__ G, int64_t 
 #pragma unroll
             for (int k = 0; k < 16; k++) X[(o + k) * S + c] = x[k];
         }
-        __syncthreads();
+        Sync::sync();
     }
-    for (int idx = tid; idx < l * l; idx += 256) {
+    for (int idx = gt; idx < l * l; idx += gnt) {
         const int i = idx / l, j = idx % l;
         Rinv[idx] = j >= i ? (double)X[i * S + j] : 0.0;
     }
-    for (int idx = tid; idx < lp * lp; idx += 256) {
+    for (int idx = gt; idx < lp * lp; idx += gnt) {
         const int i = idx / lp, j = idx % lp;
         Rinv_c[idx] = (i < l && j < l && j >= i) ? (Tc)X[i * S + j] : Tc(0);
     }
@@ -429,32 +483,6 @@ __device__ __forceinline__ void bj_round(int kind, int rd, Ta (&x)[2 * BW][NR], 
 
 // X, V: Lc columns of L rows each (column c at X + c L); rows >= L of a lane are zero.
 // Warp w takes block pairs w, w + nwarps, ... of each block round.
-// Synchronisation of the sweep: one CTA (__syncthreads), or the CTAs of a thread-block
-// cluster (hardware cluster barrier with release / acquire, which also orders the
-// global-memory columns between the CTAs).
-struct CtaSync {
-    static constexpr bool size_is_one = true;
-    static __device__ __forceinline__ void sync() { __syncthreads(); }
-    static __device__ __forceinline__ int rank() { return 0; }
-    static __device__ __forceinline__ int size() { return 1; }
-};
-struct ClusterSync {
-    static constexpr bool size_is_one = false;
-    static __device__ __forceinline__ void sync() {
-        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-    }
-    static __device__ __forceinline__ int rank() {
-        unsigned r;
-        asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-        return (int)r;
-    }
-    static __device__ __forceinline__ int size() {
-        unsigned r;
-        asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
-        return (int)r;
-    }
-};
-
 // trk: the squared column norms, recomputed from the columns at the start of
 // every sweep and carried (updated by the rotations) from block round to block round.
 // The block pairs of a round go to the warps of all CTAs of the group (warp w of CTA
@@ -871,7 +899,7 @@ size_t chol_smem_bytes(int l) {
 
 size_t chol_scratch_bytes(int l, size_t tk) {
     const int LL = 16 * ((l + 15) / 16), S = LL + (tk == 4 ? 16 : 1);
-    return tk * 2 * (size_t)LL * S;
+    return tk * (2 * (size_t)LL * S + ((LL + 1) & ~1)) + 2 * sizeof(double);  // A, X, pivots, trace, flag
 }
 
 template <typename TG, typename Tk, typename Tc>
@@ -880,14 +908,25 @@ cudaError_t chol_inv(const TG *G, int64_t ldg, int l, int64_t rows, double u, do
     const double coef = chol_shift_coef(rows, l, u);
     size_t smem = chol_smem_bytes<Tk>(l);
     Tk *gws = nullptr;
-    if (smem > 227 * 1024) {  // matrices in the global scratch, pivots in shared memory
+    if (smem > 227 * 1024) {  // matrices and pivots in the global scratch
         if (!scratch) return cudaErrorInvalidValue;
         gws = static_cast<Tk *>(scratch);
-        smem = sizeof(Tk) * 16 * (size_t)((l + 15) / 16);
+        smem = 0;
     }
-    if (gws) {
-        cudaFuncSetAttribute(chol_inv_kernel<TG, Tk, Tc, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        chol_inv_kernel<TG, Tk, Tc, true><<<1, 256, smem, s>>>(G, ldg, l, coef, R, Rinv, Rinv_c, lp, status, gws);
+    if (gws) {  // a cluster of 8 CTAs
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(8);
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 8;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, chol_inv_kernel<TG, Tk, Tc, true>, G, ldg, l, coef, R, Rinv, Rinv_c, lp, status, gws);
     } else {
         cudaFuncSetAttribute(chol_inv_kernel<TG, Tk, Tc, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
