@@ -81,7 +81,10 @@ typedef struct rsvd_plan *rsvd_plan_t;
  * workspace once (cudaMalloc) and launches everything on `cuda_stream`
  * (a cudaStream_t, may be NULL).  For svd_exact the plan needs n <= 112 (the
  * n x n eigen / SVD problem is solved in one CTA's shared memory); for rsvd
- * l <= 128 (RSVD_F32) or l <= 112 (RSVD_F64).  Returns RSVD_ERR_ARG on inconsistent sizes, RSVD_ERR_UNSUPPORTED
+ * l <= 288 (RSVD_F32, RSVD_BF16, RSVD_FP8_E4M3) or l <= 112 (RSVD_F64).  Above
+ * l = 128 the tensor-core products run on column slices of at most 128 and the
+ * l x l Cholesky and Jacobi blocks live in the plan's workspace, solved by an
+ * 8-CTA thread-block cluster once they exceed one SM's shared memory.  Returns RSVD_ERR_ARG on inconsistent sizes, RSVD_ERR_UNSUPPORTED
  * for a dtype this build does not implement, RSVD_ERR_OOM if the workspace
  * cannot be allocated.  On error *plan is set to NULL.
  */
@@ -111,14 +114,16 @@ rsvd_status rsvd_plan_sync(rsvd_plan_t plan);
  * Householder QR the step list names.
  *   A      : m x n, row-major, read only (centred on the fly).
  *   col_scales : n floats (device) for RSVD_FP8_E4M3 plans, NULL otherwise.
- * RSVD_BF16 plans (n a multiple of 8, l <= 112) solve for the stored bfloat16
+ * RSVD_BF16 plans (n a multiple of 8, l <= 288) solve for the stored bfloat16
  * matrix exactly as given: the products with A run on the tensor cores with
  * float32 accumulation, the small operand of the sketch and power products
  * rounded to bfloat16 and the basis of T = A^T Q split into three bfloat16
  * terms (float32-accurate); the column means enter as exact rank-1
- * corrections; CholeskyQR's Cholesky runs in float64 and the singular values
- * of R are float64 Rayleigh quotients of its float32 Jacobi vectors.
- * RSVD_FP8_E4M3 plans (n a multiple of 16, l <= 112) solve for A diag(s): the
+ * corrections; the Cholesky of CholeskyQR2 (final basis and T) runs in
+ * float64, the single-pass re-orthonormalisations of the power steps in
+ * float32, and the singular values of R are float64 Rayleigh quotients of its
+ * float32 Jacobi vectors.
+ * RSVD_FP8_E4M3 plans (n a multiple of 16, l <= 288) solve for A diag(s): the
  * sketch and power products run on e4m3 operands (the small operand diag(s) Z
  * and the basis Q quantised per column with their own scales, which the
  * epilogues multiply back); the Rayleigh-Ritz product runs on the exact
@@ -274,7 +279,8 @@ rsvd_status rsvd_plan_create_in(rsvd_plan_t *plan, int64_t m, int64_t n, int k, 
 
 /*
  * Batched small solves: `count` (1..RSVD_BATCH_MAX) problems whose plans share
- * dtype, l = k + p and q (m, n, k may differ; plans distinct).  A run solves
+ * dtype (RSVD_F32 or RSVD_F64), l = k + p <= 128 and q (m, n, k may differ;
+ * plans distinct); RSVD_ERR_UNSUPPORTED otherwise.  A run solves
  * every problem in lockstep: each problem's products run on its own plan's
  * stream; each small dense step (Cholesky of the CholeskyQR2 Gram matrices,
  * Jacobi SVD of R, the float64 refinement) is one launch over all problems on
@@ -355,8 +361,8 @@ rsvd_status rsvd_server_submit(rsvd_server_t server, int64_t id, int64_t m, int6
 /* rsvd_server_submit for a stored matrix of any rsvd storage type: RSVD_F32,
  * RSVD_BF16 or RSVD_FP8_E4M3 (with its n column scales; NULL otherwise).
  * Omega, U, V are float.  Requests batch only with requests of the same type;
- * the precision forms' batches run their solves concurrently (one stream per
- * request) rather than in lockstep. */
+ * the precision forms' batches (and float32 batches with l > 128) run their
+ * solves concurrently (one stream per request) rather than in lockstep. */
 rsvd_status rsvd_server_submit_ex(rsvd_server_t server, int64_t id, int64_t m, int64_t n, int k, int p, int q,
                                   rsvd_dtype dtype, double t, const void *A, const float *col_scales,
                                   const float *Omega, double *S, float *U, float *V);
