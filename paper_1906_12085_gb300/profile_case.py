@@ -35,6 +35,7 @@ def main(argv=None) -> int:
     ap.add_argument("--dtype", choices=["f32", "f64", "bf16", "fp8"], default="f32")
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--timed", type=int, default=0, help="then time this many graph-replayed solves (rsvd)")
+    ap.add_argument("--save", default="", help="write the singular values (float64, .npy) to this path")
     a = ap.parse_args(argv)
     dev = torch.device("cuda")
     dt = {"f32": g.RSVD_F32, "f64": g.RSVD_F64, "bf16": g.RSVD_BF16, "fp8": g.RSVD_FP8_E4M3}[a.dtype]
@@ -95,6 +96,9 @@ def main(argv=None) -> int:
             flops = 2.0 * a.m * a.n * l * (2 * a.q + 2) + 2.0 * a.m * l * l * (a.q + 2) + 2.0 * a.n * l * l
             print(f"timed: {ms:.3f} ms per solve, {flops / (ms * 1e-3) / 1e12:.1f} TFLOP/s over {a.timed} solves")
     torch.cuda.synchronize()
+    if a.save:
+        import numpy as np
+        np.save(a.save, S.cpu().numpy())
     traced = max(a.repeat - 1, 1)
     print({kk: round(v[0] / traced, 4) for kk, v in prof.items()}, "ms per traced solve;", "sigma_1 =", float(S[0]))
     return 0
