@@ -131,4 +131,10 @@ def test_batch_rejects_mixed_l_and_duplicates():
         g.rsvd_batch_create([p1, p1])
     p1.close()
     p2.close()
+    # l > 128: the batched small kernels keep l x l blocks in shared memory
+    p3 = g.rsvd_plan_create(2000, 300, 136, 8, Q, g.RSVD_F32)
+    with pytest.raises(g.RsvdError) as e:
+        g.rsvd_batch_create([p3])
+    assert e.value.status == g.RSVD_ERR_UNSUPPORTED
+    p3.close()
     del dev

@@ -180,3 +180,40 @@ def test_server_submit_ex_checks_scales():
         assert g.rsvd_server_submit_ex(srv, 2, k, p, Q, g.RSVD_F64, 0.9, Aq, None, Om, S, U, V) \
             == g.RSVD_ERR_UNSUPPORTED
         assert g.rsvd_server_pending(srv) == 0
+
+
+def test_served_wide_float32_requests_equal_alone_bitwise():
+    """float32 requests with l > 128 (beyond the lockstep batch's shared-memory small
+    kernels) are served as concurrent solves; each equals the same request alone."""
+    dev = torch.device("cuda")
+    reqs = []
+    for i in range(4):
+        m, n, k, p = 6000 + 500 * i, 300, 136, 8      # l = 144
+        sig = synth.spectrum_power(n, 1.0)
+        A = synth.prescribed(m, n, sig, 7000 + i, 7100 + i).float()
+        Om = synth.gaussian(n, k + p, seed=7200 + i, dtype=torch.float32)
+        reqs.append(dict(id=i, m=m, n=n, k=k, p=p, A=A, Om=Om))
+    alone = {r["id"]: _alone(r) for r in reqs}
+    for r in reqs:
+        r["Ad"], r["Od"] = r["A"].to(dev), r["Om"].to(dev)
+        r["S"] = torch.zeros(r["k"], dtype=torch.float64, device=dev)
+        r["U"] = torch.zeros(r["m"], r["k"], device=dev)
+        r["V"] = torch.zeros(r["n"], r["k"], device=dev)
+    ws = max(g.rsvd_workspace_query(r["m"], r["n"], r["k"], r["p"], Q)[1] for r in reqs)
+    torch.cuda.synchronize()
+    done = []
+    with g.rsvd_server_create(4 * ws, max_batch=4, max_inflight=2) as srv:
+        for r in reqs:
+            g.check(g.rsvd_server_submit(srv, r["id"], r["k"], r["p"], Q, 0.9, r["Ad"], r["Od"], r["S"], r["U"],
+                                         r["V"]), "submit")
+        while g.rsvd_server_pending(srv) > 0:
+            done += g.rsvd_server_poll(srv)
+    torch.cuda.synchronize()
+    assert sorted(c["id"] for c in done) == [r["id"] for r in reqs]
+    for c in done:
+        r = reqs[c["id"]]
+        a_st, a_K, a_S, a_U, a_V = alone[c["id"]]
+        assert c["status"] == a_st and c["K"] == a_K
+        assert np.array_equal(r["S"].cpu().numpy(), a_S)
+        assert np.array_equal(r["U"].cpu().numpy(), a_U)
+        assert np.array_equal(r["V"].cpu().numpy(), a_V)
