@@ -237,19 +237,23 @@ cudaError_t tc_split_transpose(const float *Z, int64_t rows, int cols, int64_t l
 // 3xTF32 on tcgen05.  N in {16, 32, ..., 128}; A, lda*4 and ldb*4 16-byte aligned.
 // mu (optional, 16-byte aligned, zero padded to a multiple of 32): column means
 // subtracted on the fly.  ctas > 0 caps the persistent grid (tuning; 0 = one CTA per SM).
+// upper_b: B is upper triangular (K = N), so a column slice of Y needs only the first
+// (end of the slice) columns of A and rows of B.
 // ssq (optional, tc_gemm_nn_grid(m, ctas) doubles): per-CTA
 // sums of the squared centred entries, i.e. ||A - 1 mu^T||_F^2 in parts.
 cudaError_t tc_gemm_nn(int64_t m, int n, int N, const float *A, int64_t lda, const float *Bth, const float *Btl,
                        int64_t ldb, float *Y, int64_t ldy, int *status, cudaStream_t s, const float *mu = nullptr,
-                       double *ssq = nullptr, int ctas = 0);
+                       double *ssq = nullptr, int ctas = 0, bool upper_b = false);
 int tc_gemm_nn_grid(int64_t m, int ctas = 0);
 // C (ncols x N, ldc) = (A - 1 mu^T)^T Q for A rows x ncols (lda) and Q rows x N (ldq), 3xTF32 on
 // tcgen05, split over row chunks into `part` (tc_gemm_tn_partials elements) and
 // summed in chunk order.  N in {16, ..., 128}; pointers and leading dimensions 16-byte
-// aligned; mu optional (zero padded to a multiple of 128).
+// aligned; mu optional (zero padded to a multiple of 128).  upper_c: only the upper
+// triangle of C is wanted (a Gram matrix, A = Q, ncols = N): a column slice of C is
+// computed for the rows up to its end.
 cudaError_t tc_gemm_tn(int64_t rows, int ncols, int N, const float *A, int64_t lda, const float *Q, int64_t ldq,
                        float *C, int64_t ldc, float *part, int64_t part_elems, int *status, cudaStream_t s,
-                       const float *mu = nullptr, int ctas = 0);
+                       const float *mu = nullptr, int ctas = 0, bool upper_c = false);
 int64_t tc_gemm_tn_partials(int64_t rows, int ncols, int N);
 
 // ------------------------------------------------------ Golub-Kahan-Lanczos

@@ -742,12 +742,14 @@ int tc_gemm_nn_grid(int64_t m, int ctas) {
 
 cudaError_t tc_gemm_nn(int64_t m, int n, int N, const float *A, int64_t lda, const float *Bth, const float *Btl,
                        int64_t ldb, float *Y, int64_t ldy, int *status, cudaStream_t s, const float *mu,
-                       double *ssq, int ctas) {
+                       double *ssq, int ctas, bool upper_b) {
     if (N > 128 && N % 16 == 0) {  // column slices (A read once per slice)
         const int w = column_slice(N);
         for (int c0 = 0; c0 < N; c0 += w) {
-            const cudaError_t e = tc_gemm_nn(m, n, w < N - c0 ? w : N - c0, A, lda, Bth + c0 * ldb, Btl + c0 * ldb,
-                                             ldb, Y + c0, ldy, status, s, mu, c0 == 0 ? ssq : nullptr, ctas);
+            const int wn = w < N - c0 ? w : N - c0;
+            const int kn = upper_b && c0 + wn < n ? c0 + wn : n;  // rows of a triangular B below the slice are zero
+            const cudaError_t e = tc_gemm_nn(m, kn, wn, A, lda, Bth + c0 * ldb, Btl + c0 * ldb, ldb, Y + c0, ldy,
+                                             status, s, mu, c0 == 0 ? ssq : nullptr, ctas);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
@@ -778,12 +780,14 @@ int64_t tc_gemm_tn_partials(int64_t rows, int ncols, int N) {
 
 cudaError_t tc_gemm_tn(int64_t rows, int ncols, int N, const float *A, int64_t lda, const float *Q, int64_t ldq,
                        float *C, int64_t ldc, float *part, int64_t part_elems, int *status, cudaStream_t s,
-                       const float *mu, int ctas) {
+                       const float *mu, int ctas, bool upper_c) {
     if (N > 128 && N % 16 == 0) {  // column slices of Q and C (A read once per slice)
         const int w = column_slice(N);
         for (int c0 = 0; c0 < N; c0 += w) {
-            const cudaError_t e = tc_gemm_tn(rows, ncols, w < N - c0 ? w : N - c0, A, lda, Q + c0, ldq, C + c0, ldc,
-                                             part, part_elems, status, s, mu, ctas);
+            const int wn = w < N - c0 ? w : N - c0;
+            const int nc = upper_c && c0 + wn < ncols ? c0 + wn : ncols;  // upper triangle: rows up to the slice end
+            const cudaError_t e = tc_gemm_tn(rows, nc, wn, A, lda, Q + c0, ldq, C + c0, ldc, part, part_elems, status,
+                                             s, mu, ctas);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;

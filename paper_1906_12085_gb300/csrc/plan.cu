@@ -249,15 +249,16 @@ inline bool al16(const void *p, int64_t ld, size_t es) {
 
 // Y (rows x N) = (X - 1 mu^T) B, B row-major K x N (ldb), N = lp.  mu (element type,
 // padded) may be NULL.  When fro2 is given it receives ||X - 1 mu^T||_F^2.
+// upper_b: B is upper triangular (the inverse Cholesky factor of CholeskyQR; K = lp).
 template <typename T>
 cudaError_t prod_nn(rsvd_plan *P, int64_t rows, int64_t K, const T *X, int64_t ldx, const T *B, int64_t ldb, T *Y,
-                    int64_t ldy, const T *mu = nullptr, double *fro2 = nullptr) {
+                    int64_t ldy, const T *mu = nullptr, double *fro2 = nullptr, bool upper_b = false) {
     if constexpr (sizeof(T) == 4) {
         if (P->tc && al16(X, ldx, 4) && (ldy % 4) == 0 && K <= P->ldt) {
             cudaError_t e = tc_split_transpose(B, K, P->lp, ldb, P->lp, P->Bth, P->Btl, P->ldt, P->stream);
             if (e == cudaSuccess)
                 e = tc_gemm_nn(rows, (int)K, P->lp, X, ldx, P->Bth, P->Btl, P->ldt, Y, ldy, P->status, P->stream, mu,
-                               fro2 ? P->ssq : nullptr, P->nn_ctas);
+                               fro2 ? P->ssq : nullptr, P->nn_ctas, upper_b && K == P->lp);
             if (e == cudaSuccess && fro2) e = sum_f64(P->ssq, tc_gemm_nn_grid(rows, P->nn_ctas), fro2, P->stream);
             if (e != cudaErrorInvalidValue) return e;
             cudaGetLastError();
@@ -274,14 +275,15 @@ cudaError_t prod_nn(rsvd_plan *P, int64_t rows, int64_t K, const T *X, int64_t l
 }
 
 // C (ncols x N) = (X - 1 mu^T)^T Q with X rows x ncols (ldx), Q rows x N (ldq), N = lp.
+// gram: X = Q and only the upper triangle of C is wanted (CholeskyQR's Gram matrix).
 template <typename T>
 cudaError_t prod_tn(rsvd_plan *P, int64_t rows, int64_t ncols, const T *X, int64_t ldx, const T *Q, int64_t ldq,
-                    T *C, int64_t ldc, const T *mu = nullptr) {
+                    T *C, int64_t ldc, const T *mu = nullptr, bool gram = false) {
     if constexpr (sizeof(T) == 4) {
         if (P->tc && al16(X, ldx, 4) && al16(Q, ldq, 4) &&
             tc_gemm_tn_partials(rows, (int)ncols, P->lp) <= P->tcpart_elems) {
             cudaError_t e = tc_gemm_tn(rows, (int)ncols, P->lp, X, ldx, Q, ldq, C, ldc, P->tcpart, P->tcpart_elems,
-                                       P->status, P->stream, mu, P->tn_ctas);
+                                       P->status, P->stream, mu, P->tn_ctas, gram && X == Q && ncols == P->lp);
             if (e != cudaErrorInvalidValue) return e;
             cudaGetLastError();
         }
@@ -311,20 +313,20 @@ rsvd_status cqr(rsvd_plan *P, const T *X, int64_t rows, int w, int ld, T *Qo, T 
     // T) in float64; the single-pass re-orthonormalisations inside the power
     // iteration, like the float32 path's, in float32
     const bool f64 = (P->dtype == RSVD_BF16 || P->dtype == RSVD_FP8_E4M3) && passes == 2;
-    if (skinny) CK(prod_tn<T>(P, rows, ld, X, ld, X, ld, G, ld));
+    if (skinny) CK(prod_tn<T>(P, rows, ld, X, ld, X, ld, G, ld, nullptr, true));
     else CK(gemm_tn<T>(rows, ld, ld, X, ld, X, ld, G, ld, part, P->part_elems, s));
     if (f64)
         CK(chol_inv<T, double, T>(G, ld, w, rows, u, P->R1, P->R1i, Ric, ld, P->status, s, P->chol_ws));
     else CK(chol_inv<T, T, T>(G, ld, w, rows, u, P->R1, P->R1i, Ric, ld, P->status, s, P->chol_ws));
-    if (skinny) CK(prod_nn<T>(P, rows, ld, X, ld, Ric, ld, Q1, ld));
+    if (skinny) CK(prod_nn<T>(P, rows, ld, X, ld, Ric, ld, Q1, ld, nullptr, nullptr, true));
     else CK(gemm_nn<T>(rows, ld, ld, X, ld, Ric, ld, Q1, ld, s));
     if (passes == 1) return RSVD_OK;
-    if (skinny) CK(prod_tn<T>(P, rows, ld, Q1, ld, Q1, ld, G, ld));
+    if (skinny) CK(prod_tn<T>(P, rows, ld, Q1, ld, Q1, ld, G, ld, nullptr, true));
     else CK(gemm_tn<T>(rows, ld, ld, Q1, ld, Q1, ld, G, ld, part, P->part_elems, s));
     if (f64)
         CK(chol_inv<T, double, T>(G, ld, w, rows, u, P->R2, P->R2i, Ric, ld, P->status, s, P->chol_ws));
     else CK(chol_inv<T, T, T>(G, ld, w, rows, u, P->R2, P->R2i, Ric, ld, P->status, s, P->chol_ws));
-    if (skinny) CK(prod_nn<T>(P, rows, ld, Q1, ld, Ric, ld, Qo, ld));
+    if (skinny) CK(prod_nn<T>(P, rows, ld, Q1, ld, Ric, ld, Qo, ld, nullptr, nullptr, true));
     else CK(gemm_nn<T>(rows, ld, ld, Q1, ld, Ric, ld, Qo, ld, s));
     if (want_r) CK(trmm_upper(P->R2, P->R1, P->Rt, w, s));
     return RSVD_OK;
