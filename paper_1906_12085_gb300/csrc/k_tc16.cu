@@ -89,6 +89,9 @@ constexpr int cmin(int a, int b) { return a < b ? a : b; }
 // ======================================================================= NN
 template <int N, int ESZ>
 struct NN16 {
+    // two accumulators of N float32 columns: 256 TMEM columns up to N = 128, 512 above
+    static constexpr uint32_t ACS = N > 128 ? 256 : 128;  // column stride of the accumulators
+    static constexpr uint32_t TC = 2 * ACS;
     static constexpr uint32_t B_ST = N * 128;
     static constexpr uint32_t STAGE = A_ST + B_ST;
     static constexpr int S = cmin(8, (int)((200 * 1024) / STAGE));
@@ -126,7 +129,7 @@ __global__ void __launch_bounds__(THR, 1)
         bar->abort_flag = 0;
         mbar_fence_init();
     }
-    if (warp == 1) tmem_alloc(&bar->tmem, TCOLS);
+    if (warp == 1) tmem_alloc(&bar->tmem, C::TC);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -157,7 +160,7 @@ __global__ void __launch_bounds__(THR, 1)
                 const uint32_t b = it & 1;
                 if (!(ok = wait16(&bar->acc_empty[b], ((it >> 1) & 1) ^ 1, abort_flag))) break;
                 tc_fence_after();
-                const uint32_t d = tmem + b * 128;
+                const uint32_t d = tmem + b * C::ACS;
                 for (int kb = 0; kb < nkb; kb++, g++) {
                     const int s = g % S;
                     if (!(ok = wait16(&bar->full[s], (g / S) & 1, abort_flag))) break;
@@ -182,7 +185,7 @@ __global__ void __launch_bounds__(THR, 1)
 #pragma unroll
             for (int c0 = 0; c0 < N; c0 += 32) {
                 float v[32];
-                tmem_ld32(tmem + b * 128 + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+                tmem_ld32(tmem + b * C::ACS + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
                 if (row < m) {
                     float *p = Y + row * ldy + c0;
 #pragma unroll
@@ -198,7 +201,7 @@ __global__ void __launch_bounds__(THR, 1)
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, TCOLS);
+        tmem_dealloc(tmem, C::TC);
     }
     if (threadIdx.x == 0 && bar->abort_flag) atomicOr(status, (int)ST_TIMEOUT);
 }
@@ -466,8 +469,8 @@ cudaError_t launch16_tn(const CUtensorMap &a, const CUtensorMap *q, int64_t rows
 template <int ESZ>
 cudaError_t gemm_nn_e(int64_t m, int n, int N, const void *A, int64_t lda, const void *Zt, int64_t ldz, float *Y,
                       int64_t ldy, const float *ts, const float *c, int *status, cudaStream_t s) {
-    if (N > 128 && N % 16 == 0) {  // column slices (A read once per slice)
-        const int w = column_slice(N);
+    if (N > 256 && N % 16 == 0) {  // column slices of up to 256 (A read once per slice)
+        const int k = (N + 255) / 256, w = ((N + k - 1) / k + 15) / 16 * 16;
         for (int c0 = 0; c0 < N; c0 += w) {
             const cudaError_t e =
                 gemm_nn_e<ESZ>(m, n, w < N - c0 ? w : N - c0, A, lda, static_cast<const uint8_t *>(Zt) + c0 * ldz * ESZ,
@@ -476,7 +479,7 @@ cudaError_t gemm_nn_e(int64_t m, int n, int N, const void *A, int64_t lda, const
         }
         return cudaSuccess;
     }
-    if (N % 16 || N < 16 || N > 128) return cudaErrorInvalidValue;
+    if (N % 16 || N < 16 || N > 256) return cudaErrorInvalidValue;
     constexpr int BK = Elt<ESZ>::NN_BK;
     CUtensorMap ma, mb;
     if (!tc_make_map(&ma, A, ESZ, m, n, lda, TM, BK, true) || !tc_make_map(&mb, Zt, ESZ, N, n, ldz, N, BK, true))
@@ -490,6 +493,14 @@ cudaError_t gemm_nn_e(int64_t m, int n, int N, const void *A, int64_t lda, const
         case 96: return launch16_nn<96, ESZ>(ma, mb, m, n, Y, ldy, ts, c, status, s);
         case 112: return launch16_nn<112, ESZ>(ma, mb, m, n, Y, ldy, ts, c, status, s);
         case 128: return launch16_nn<128, ESZ>(ma, mb, m, n, Y, ldy, ts, c, status, s);
+        case 144: return launch16_nn<144, ESZ>(ma, mb, m, n, Y, ldy, ts, c, status, s);
+        case 160: return launch16_nn<160, ESZ>(ma, mb, m, n, Y, ldy, ts, c, status, s);
+        case 176: return launch16_nn<176, ESZ>(ma, mb, m, n, Y, ldy, ts, c, status, s);
+        case 192: return launch16_nn<192, ESZ>(ma, mb, m, n, Y, ldy, ts, c, status, s);
+        case 208: return launch16_nn<208, ESZ>(ma, mb, m, n, Y, ldy, ts, c, status, s);
+        case 224: return launch16_nn<224, ESZ>(ma, mb, m, n, Y, ldy, ts, c, status, s);
+        case 240: return launch16_nn<240, ESZ>(ma, mb, m, n, Y, ldy, ts, c, status, s);
+        case 256: return launch16_nn<256, ESZ>(ma, mb, m, n, Y, ldy, ts, c, status, s);
     }
     return cudaErrorInvalidValue;
 }
