@@ -31,7 +31,6 @@ constexpr int TM = 128;                  // MMA M
 constexpr int THR = 192;                 // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr int NEPI = 128;
 constexpr uint32_t A_ST = TM * 128;      // 16 KB of A per stage (NN: 128 rows; TN: 128 columns)
-constexpr uint32_t TCOLS = 256;          // two accumulators of up to 128 float32 columns
 
 // Element-size traits (ESZ bytes per element: 2 bfloat16, 1 e4m3).  A stage holds
 // 128 bytes of K per row in NN (one swizzled row), and in TN TN_BK rows of the
@@ -214,9 +213,13 @@ template <int N, int NB, int ESZ>
 struct TN16 {
     using E = Elt<ESZ>;
     static constexpr int NA = (N + E::QW - 1) / E::QW;  // MN atoms of one Q operand loaded by TMA
-    // bfloat16: two atoms of room per operand whatever N, so the MMA's reads of one operand
-    // stay inside its own 16 KB under either assignment of the two descriptor strides
-    static constexpr uint32_t Q_ST = E::Q_ROOM;
+    // bfloat16: two atoms of room per operand up to N = 128, so the MMA's reads of one operand
+    // stay inside its own 16 KB under either assignment of the two descriptor strides; wider
+    // operands (N > 128, one term) take NA atoms at the atom stride the A operand already uses
+    static constexpr uint32_t Q_ST = NA * E::ATOM > E::Q_ROOM ? NA * E::ATOM : E::Q_ROOM;
+    // two accumulators of N float32 columns: 256 TMEM columns up to N = 128, 512 above
+    static constexpr uint32_t ACS = N > 128 ? 256 : 128;
+    static constexpr uint32_t TC = 2 * ACS;
     static constexpr uint32_t STAGE = A_ST + NB * Q_ST;
     static constexpr int S = cmin(8, (int)((200 * 1024) / STAGE));
     static constexpr uint32_t NEED = S * STAGE + 1024 + sizeof(Bars16<S>) + 64;
@@ -252,7 +255,7 @@ __global__ void __launch_bounds__(THR, 1)
         bar->abort_flag = 0;
         mbar_fence_init();
     }
-    if (warp == 1) tmem_alloc(&bar->tmem, TCOLS);
+    if (warp == 1) tmem_alloc(&bar->tmem, C::TC);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -316,7 +319,7 @@ __global__ void __launch_bounds__(THR, 1)
                     const uint32_t b = it & 1;
                     if (!(ok = wait16(&bar->acc_empty[b], ((it >> 1) & 1) ^ 1, abort_flag))) break;
                     tc_fence_after();
-                    const uint32_t d = tmem + b * 128;
+                    const uint32_t d = tmem + b * C::ACS;
                     for (int kb = k0; kb < k1; kb++, g++) {
                         const int s = g % S;
                         if (!(ok = wait16(&bar->full[s], (g / S) & 1, abort_flag))) break;
@@ -356,7 +359,7 @@ __global__ void __launch_bounds__(THR, 1)
 #pragma unroll
                 for (int j0 = 0; j0 < N; j0 += 16) {
                     float v[16];
-                    tmem_ld16(tmem + b * 128 + ((uint32_t)(q * 32) << 16) + (uint32_t)j0, v);
+                    tmem_ld16(tmem + b * C::ACS + ((uint32_t)(q * 32) << 16) + (uint32_t)j0, v);
 #pragma unroll
                     for (int j = 0; j < 16; j++) acc[j0 + j] = k0 > 0 ? acc[j0 + j] + v[j] : v[j];
                 }
@@ -375,7 +378,7 @@ __global__ void __launch_bounds__(THR, 1)
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, TCOLS);
+        tmem_dealloc(tmem, C::TC);
     }
     if (threadIdx.x == 0 && bar->abort_flag) atomicOr(status, (int)ST_TIMEOUT);
 }
@@ -510,8 +513,10 @@ cudaError_t gemm_tn_e(int64_t rows, int ncols, int N, const void *A, int64_t lda
                       int64_t ldq, float *C, int64_t ldc, float *part, int64_t part_elems, const float *cs,
                       const float *qs, const float *mu, const double *qsum, int *status, cudaStream_t s) {
     using E = Elt<ESZ>;
-    if (N > 128 && N % 16 == 0) {  // column slices of the Q terms and C (A read once per slice)
-        const int w = column_slice(N);
+    // one bfloat16 term: up to 192 columns per launch (the epilogue holds N sums per thread)
+    const int wmax = (ESZ == 2 && nq == 1) ? 192 : 128;
+    if (N > wmax && N % 16 == 0) {  // column slices of the Q terms and C (A read once per slice)
+        const int kq = (N + wmax - 1) / wmax, w = ((N + kq - 1) / kq + 15) / 16 * 16;
         for (int c0 = 0; c0 < N; c0 += w) {
             const void *qs_[3];
             for (int i = 0; i < nq && i < 3; i++) qs_[i] = static_cast<const uint8_t *>(Q[i]) + c0 * ESZ;
@@ -522,7 +527,7 @@ cudaError_t gemm_tn_e(int64_t rows, int ncols, int N, const void *A, int64_t lda
         }
         return cudaSuccess;
     }
-    if (N % 16 || N < 16 || N > 128 || (nq != 1 && nq != 3) || (ESZ == 1 && nq != 1)) return cudaErrorInvalidValue;
+    if (N % 16 || N < 16 || N > wmax || (nq != 1 && nq != 3) || (ESZ == 1 && nq != 1)) return cudaErrorInvalidValue;
     const Split16 sp = split16(rows, ncols, E::TN_BK);
     if (!part || part_elems < (int64_t)sp.chunks * ncols * N) return cudaErrorInvalidValue;
     CUtensorMap ma, mq[3];
@@ -547,6 +552,14 @@ cudaError_t gemm_tn_e(int64_t rows, int ncols, int N, const void *A, int64_t lda
         TN16_CASE(128)
     }
 #undef TN16_CASE
+    if constexpr (ESZ == 2) {  // one term, N > 128
+        switch (N) {
+            case 144: e = launch16_tn<144, 1, 2>(ma, mq, rows, ncols, sp, part, status, s); break;
+            case 160: e = launch16_tn<160, 1, 2>(ma, mq, rows, ncols, sp, part, status, s); break;
+            case 176: e = launch16_tn<176, 1, 2>(ma, mq, rows, ncols, sp, part, status, s); break;
+            case 192: e = launch16_tn<192, 1, 2>(ma, mq, rows, ncols, sp, part, status, s); break;
+        }
+    }
     if (e != cudaSuccess) return e;
     const int64_t total = (int64_t)ncols * N;
     sum16_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, s>>>(part, sp.chunks, ncols, N, C, ldc, cs, qs, mu, qsum);
