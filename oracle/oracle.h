@@ -63,7 +63,7 @@ int orc_pca_threshold(int64_t count, const double *sigma, double fro2, double t,
  * the matching column of U (sign convention of all oracle outputs). */
 void orc_sign_normalize(int64_t m, int64_t n, int64_t k, double *U, double *V);
 
-/* ---- Storage formats of the precision form (reading c11 of the survey) ----
+/* ---- Storage formats of the precision form ----
  * bfloat16: the float32 value rounded to the nearest bfloat16 (8 exponent
  * bits, 7 stored mantissa bits), ties to the even mantissa.
  * e4m3 (OCP FP8 "E4M3FN": bias 7, 3 mantissa bits, no infinities, NaN =

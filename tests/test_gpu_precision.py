@@ -48,7 +48,7 @@ def _proj_residual(A, U):
     (60000, 512, 48, 16, 3, True),
     (20011, 256, 20, 12, 2, True),     # ragged m
     (30000, 1024, 40, 8, 1, False),    # data centred, NO_CENTER
-    (20011, 512, 256, 32, 2, True),    # l = 288 (k = 256, p = 32: the survey's precision-form sizes)
+    (20011, 512, 256, 32, 2, True),    # l = 288 (k = 256, p = 32: the precision form's widest sketch)
 ])
 def test_bf16_rsvd_matches_oracle_on_stored_matrix(m, n, k, p, q, shift):
     codes, Ad = _stored(m, n, m % 97, shift)

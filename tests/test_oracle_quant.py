@@ -1,5 +1,5 @@
-"""Pins of the oracle's storage-format encoders (precision form, survey
-reading c11): values fixed by the format definitions (bfloat16: 8 exponent
+"""Pins of the oracle's storage-format encoders (precision form: BF16
+round-to-nearest-even, e4m3 with per-column scales): values fixed by the format definitions (bfloat16: 8 exponent
 and 7 mantissa bits; OCP e4m3: bias 7, 3 mantissa bits, largest finite 448,
 no infinities), exact ties resolved to the even code, saturation, subnormals,
 round trips over every code, and torch's own converters as an independent
