@@ -12,6 +12,7 @@ Functions and the passages they follow:
 * ``eig_jacobi``    -- eigen-decomposition used by the Gram route
 * ``svd_gram``      -- Sec. 2.3 / Sec. 3.1.3 "Truncated SVD" (A^T A, eig, sqrt, A v / sigma)
 * ``rsvd``          -- Sec. 3.1.2 randomized PCA with a given Gaussian test matrix
+* ``block_krylov``  -- Sec. 3.1.1 block Krylov method with a given Gaussian test matrix
 * ``gkl``           -- Golub-Kahan-Lanczos with full reorthogonalisation
 * ``pca_threshold`` -- Sec. 2.4 cumulative explained-variance criterion
 * ``qr``            -- Householder QR (orthonormalisation inside ``rsvd``)
@@ -65,6 +66,7 @@ def lib():
         L.orc_svd_gram.argtypes = [i64, i64, P, P, P, P]
         L.orc_rsvd.argtypes = [i64, i64, P, i64, ctypes.c_int, P, i64, P, P, P]
         L.orc_gkl.argtypes = [i64, i64, P, P, ctypes.c_int, i64, P, P, P, P, P]
+        L.orc_block_krylov.argtypes = [i64, i64, P, i64, ctypes.c_int, P, i64, P, P, P]
         L.orc_pca_threshold.argtypes = [i64, P, ctypes.c_double, ctypes.c_double, ctypes.POINTER(i64)]
         L.orc_sign_normalize.argtypes = [i64, i64, i64, P, P]
         L.orc_bf16_encode.argtypes = [ctypes.c_float]
@@ -78,7 +80,7 @@ def lib():
         L.orc_quantize_bf16.argtypes = [i64, i64, ctypes.c_void_p, i64, ctypes.c_void_p]
         L.orc_quantize_e4m3.argtypes = [i64, i64, ctypes.c_void_p, i64, ctypes.c_void_p, ctypes.c_void_p]
         for f in ("orc_center", "orc_qr", "orc_svd", "orc_eig_jacobi", "orc_svd_gram", "orc_rsvd",
-                  "orc_gkl", "orc_pca_threshold"):
+                  "orc_gkl", "orc_pca_threshold", "orc_block_krylov"):
             getattr(L, f).restype = ctypes.c_int
         L.orc_sign_normalize.restype = None
         _lib = L
@@ -163,6 +165,21 @@ def rsvd(A, Omega, q: int, k: int):
     u = np.zeros((m, k))
     v = np.zeros((n, k))
     _check(lib().orc_rsvd(m, n, _p(a), l, int(q), _p(om), k, _p(s), _p(u), _p(v)), "orc_rsvd")
+    return s, u, v
+
+
+def block_krylov(A, Omega, iters: int, k: int):
+    """Sec. 3.1.1 block Krylov method with the given Omega (n x l): (S, U, V) of the
+    leading k triplets from the basis of [H(0) | ... | H(iters)]."""
+    a = _f64(A)
+    om = _f64(Omega)
+    m, n = a.shape
+    l = om.shape[1]
+    s = np.zeros(k)
+    u = np.zeros((m, k))
+    v = np.zeros((n, k))
+    _check(lib().orc_block_krylov(m, n, _p(a), l, int(iters), _p(om), k, _p(s), _p(u), _p(v)),
+           "orc_block_krylov")
     return s, u, v
 
 

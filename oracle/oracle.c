@@ -441,6 +441,50 @@ done:
     return st;
 }
 
+/* Sec. 3.1.1 (block Krylov): H(0) = A G, H(j) = A (A^T H(j-1)) for j = 1..iters,
+ * H = [H(0) | ... | H(iters)], Q = qr(H), T = A^T Q = Vt Sigma W^T, U = Q W.  Each
+ * block is re-orthonormalised before it feeds the next (its span, and so the span
+ * of H, is that of the printed chain in exact arithmetic); the blocks are kept as
+ * the columns of H, whose Householder QR then gives the basis. */
+int orc_block_krylov(int64_t m, int64_t n, const double *A, int64_t l, int iters,
+                     const double *Omega, int64_t k, double *S, double *U, double *V) {
+    const int64_t w = (int64_t)(iters + 1) * l;
+    if (l <= 0 || iters < 0 || w > n || n > m || k <= 0 || k > w || !A || !Omega || !S) return ORC_ERR_ARG;
+    double *Y = dalloc((size_t)m * l), *Qb = dalloc((size_t)m * l), *Z = dalloc((size_t)n * l);
+    double *Qz = dalloc((size_t)n * l), *H = dalloc((size_t)m * w), *Q = dalloc((size_t)m * w);
+    double *T = dalloc((size_t)n * w), *sg = dalloc((size_t)w), *Vt = dalloc((size_t)n * w);
+    double *W = dalloc((size_t)w * w), *Ut = dalloc((size_t)m * w);
+    int st = ORC_ERR_OOM;
+    if (!Y || !Qb || !Z || !Qz || !H || !Q || !T || !sg || !Vt || !W || !Ut) goto done;
+    mm_nn(m, n, l, A, n, Omega, l, Y, l);                      /* H(0) = A G */
+    if ((st = orc_qr(m, l, Y, Qb, NULL))) goto done;
+    for (int j = 0; j <= iters; j++) {
+        if (j > 0) {                                           /* H(j) = A (A^T H(j-1)) */
+            mm_tn(m, n, l, A, n, Qb, l, Z, l);
+            if ((st = orc_qr(n, l, Z, Qz, NULL))) goto done;
+            mm_nn(m, n, l, A, n, Qz, l, Y, l);
+            if ((st = orc_qr(m, l, Y, Qb, NULL))) goto done;
+        }
+        for (int64_t r = 0; r < m; r++)                        /* block j of H */
+            for (int64_t c = 0; c < l; c++) AT(H, r, (int64_t)j * l + c, w) = AT(Qb, r, c, l);
+    }
+    if ((st = orc_qr(m, w, H, Q, NULL))) goto done;            /* Q = qr(H) */
+    mm_tn(m, n, w, A, n, Q, w, T, w);                          /* T = A^T Q */
+    if ((st = orc_svd(n, w, T, sg, Vt, W)) < 0) goto done;     /* T = Vt Sigma W^T */
+    mm_nn(m, w, w, Q, w, W, w, Ut, w);                         /* U = Q W */
+    orc_sign_normalize(m, n, w, Ut, Vt);
+    for (int64_t i = 0; i < k; i++) S[i] = sg[i];
+    if (U)
+        for (int64_t r = 0; r < m; r++)
+            for (int64_t j = 0; j < k; j++) AT(U, r, j, k) = AT(Ut, r, j, w);
+    if (V)
+        for (int64_t r = 0; r < n; r++)
+            for (int64_t j = 0; j < k; j++) AT(V, r, j, k) = AT(Vt, r, j, w);
+done:
+    free(Y); free(Qb); free(Z); free(Qz); free(H); free(Q); free(T); free(sg); free(Vt); free(W); free(Ut);
+    return st;
+}
+
 /* ------------------------------------------------------ Golub-Kahan-Lanczos */
 
 /* w <- w - B (B^T w), twice (classical Gram-Schmidt applied twice), B rows x cnt, ld */

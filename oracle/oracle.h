@@ -46,6 +46,14 @@ int orc_svd_gram(int64_t m, int64_t n, const double *A, double *S, double *U, do
 int orc_rsvd(int64_t m, int64_t n, const double *A, int64_t l, int q,
              const double *Omega, int64_t k, double *S, double *U, double *V);
 
+/* Sec. 3.1.1 block Krylov method with the given Gaussian test matrix Omega (n x l):
+ * H(0) = A Omega, H(j) = A (A^T H(j-1)) (j = 1..iters, every block re-orthonormalised
+ * before it feeds the next), H = [H(0) | ... | H(iters)] (m x (iters+1) l),
+ * Q = qr(H), T = A^T Q = Vt Sigma W^T, U = Q W.  Requires (iters+1) l <= n.
+ * Outputs the leading k triplets: S k, U m x k, V n x k. */
+int orc_block_krylov(int64_t m, int64_t n, const double *A, int64_t l, int iters,
+                     const double *Omega, int64_t k, double *S, double *U, double *V);
+
 /* Golub-Kahan-Lanczos bidiagonalisation with full reorthogonalisation
  * (classical Gram-Schmidt applied twice), `steps` steps from the start
  * vector v1 (length n), followed by the SVD of the steps x steps bidiagonal.
