@@ -24,10 +24,12 @@ constexpr int kSmallMaxF64 = 112;
 constexpr int kSmallMaxF32 = 128;
 // Largest l of a single float32 / bfloat16 / e4m3 randomized solve: above the shared-
 // memory sizes the Cholesky and Jacobi keep their l x l blocks in a global scratch
-// (one CTA each), and the products run on column slices of N <= 128.
+// (on an 8-CTA cluster), and the products run on column slices (N <= 128 per launch;
+// the bfloat16 / e4m3 A Z product up to 256, the one-term bfloat16 A^T Q up to 192).
 constexpr int kRsvdMaxL = 288;
-// Tensor-core products take N <= 128 output columns per launch; wider products run
-// as ceil(N / 128) launches on column slices of this width (a multiple of 16).
+// The float32 tensor-core products take N <= 128 output columns per launch; wider
+// products run as ceil(N / 128) launches on column slices of this width (a multiple
+// of 16).
 inline int column_slice(int N) {
     const int k = (N + 127) / 128;
     return ((N + k - 1) / k + 15) / 16 * 16;

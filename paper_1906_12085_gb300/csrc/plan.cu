@@ -419,8 +419,9 @@ rsvd_status run_rsvd(rsvd_plan *P, T *A, const T *Omega, double *S, T *U, T *V) 
 // of the sketch and power products is rounded to bfloat16 (it only spans the
 // subspace), the basis Q of the Rayleigh-Ritz product T = A^T Q is split into three
 // bfloat16 terms (float32-accurate against the stored A); the column means enter as
-// exact rank-1 corrections of each product.  CholeskyQR runs its Cholesky in
-// float64; the SVD of R is a one-sided Jacobi whose values are recomputed in float64.
+// exact rank-1 corrections of each product.  The Cholesky of CholeskyQR2 (final basis
+// and T) runs in float64, that of the single-pass power-step bases in float32; the SVD
+// of R is a one-sided Jacobi whose values are recomputed in float64.
 rsvd_status run_rsvd_bf16(rsvd_plan *P, const void *A, const float *Omega, double *S, float *U, float *V) {
     cudaStream_t s = P->stream;
     const int64_t m = P->m, n = P->n;
