@@ -16,6 +16,13 @@ with the FLOP count of the paper's randomized PCA step list (Sec. 3.1.2) in the
 
 ``--impl reference`` times the FP64 CPU oracle (the only reference this
 project has) on the host cores on a bounded row sample of the same workload.
+
+``--method block_krylov`` measures the paper's block Krylov method (Sec. 3.1.1)
+instead: A 1048576 x 4096 float32 with seeded N(0,1) entries (the Gaussian
+matrices of the paper's experiments), blocks of b = 96 columns, i = 2 (W = 288),
+k = 256, one step = one rsvd_block_krylov() solve; FLOPs per solve
+    F = 2mnb(2i+1) + 2mnW + 2mW^2 + 2nW^2
+(the products with A, the QR of the m x W basis, the SVD of T).
 """
 from __future__ import annotations
 
@@ -33,6 +40,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "rpca_fp32_200000x1000"
+BK_WORKLOAD = "block_krylov_fp32_gaussian_1048576x4096"
+BK = dict(m=1048576, n=4096, k=256, b=96, iters=2, seed_a=40971, seed_omega=40972)
 
 
 def alg_flops(m, n, k, p, q):
@@ -143,6 +152,155 @@ def oracle_sample(A_host32, Om32, k, q, rows):
     ac, mu, fro2 = oracle.center(a)
     oracle.rsvd(ac, om, q=q, k=k)
     return time.perf_counter() - t0
+
+
+def bk_flops(m, n, b, iters):
+    W = (iters + 1) * b
+    return 2.0 * m * n * b * (2 * iters + 1) + 2.0 * m * n * W + 2.0 * m * W * W + 2.0 * n * W * W
+
+
+def run_block_krylov(args):
+    """One JSON line for the block Krylov workload (replicas over ranks, like the default)."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_1906_12085_gb300 as g
+    import synth
+    from paper_1906_12085_gb300 import build as gbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    gbuild.build()
+    m, n, k, b, iters = BK["m"], BK["n"], BK["k"], BK["b"], BK["iters"]
+    W = (iters + 1) * b
+    A = synth.gaussian(m, n, BK["seed_a"], device=dev, dtype=torch.float32)
+    Om = synth.gaussian(n, b, BK["seed_omega"], device=dev, dtype=torch.float32)
+    S = torch.zeros(k, dtype=torch.float64, device=dev)
+    U = torch.zeros(m, k, dtype=torch.float32, device=dev)
+    V = torch.zeros(n, k, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    plan = g.rsvd_plan_create_block_krylov(m, n, k, b, iters, g.RSVD_F32, stream)
+
+    def step():
+        g.check(g.rsvd_block_krylov(plan, A, Om, S, U, V), "rsvd_block_krylov")
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    g.check(g.rsvd_plan_sync(plan), "warm-up solve status")
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    sampler.start()
+    launches0 = g.rsvd_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    launches = g.rsvd_launch_count() - launches0
+    ms = e0.elapsed_time(e1)
+    clocks = sampler.stop()
+    st = g.rsvd_plan_sync(plan)
+    ms_max = slowest_rank_ms(ms, world, dev)
+    flops = bk_flops(m, n, b, iters)
+    value = job_gflops(world, flops, args.steps, ms_max)
+
+    # per-stage durations (CUDA events on the plan's stream) over the same K steps
+    g.rsvd_plan_profile(plan, True)
+    g.rsvd_plan_profile_read(plan)
+    for _ in range(args.steps):
+        step()
+    prof = g.rsvd_plan_profile_read(plan)
+    g.rsvd_plan_profile(plan, False)
+    # The products with A are HBM-bound 3xTF32 passes over A (4mn bytes each): the A X
+    # stage makes i + 1 of them (N = b), the A^T X stage i (N = b) plus the Rayleigh-Ritz
+    # product at N = W, which runs as ceil(W / 128) column slices, one pass each.
+    pk, src = peaks()
+    hbm = float(pk.get("hbm_gbs", 6800.0))
+    Wp = -(-W // 16) * 16
+    passes = {"ax": iters + 1, "atx": iters + -(-Wp // 128)}
+    dom = "ax" if prof["ax"][0] >= prof["atx"][0] else "atx"
+    per_pass_ms = prof[dom][0] / args.steps / passes[dom]
+    achieved = 4.0 * m * n / (per_pass_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm",
+                "kernel": "tc_nn_kernel (A X, 3xTF32 tcgen05)" if dom == "ax" else
+                          "tc_tn_kernel + sum_chunks_kernel (A^T X, 3xTF32 tcgen05)",
+                "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "algorithmic_bytes_per_launch": 4.0 * m * n,
+                "passes_over_A_per_step": passes,
+                "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback 6800 GB/s",
+                "stage_ms_per_step": {kk: vv[0] / args.steps for kk, vv in prof.items()},
+                "timing": "stage durations from CUDA events around each kernel group over an instrumented "
+                          "pass of the same K steps; per pass over A = stage time / passes"}
+
+    e2e = None
+    if rank == 0 or world > 1:   # host buffers (pinned), copies inside the timed region
+        Ah = A.cpu().pin_memory()
+        Omh = Om.cpu().pin_memory()
+        Sh = torch.empty_like(S, device="cpu").pin_memory()
+        Uh = torch.empty_like(U, device="cpu").pin_memory()
+        Vh = torch.empty_like(V, device="cpu").pin_memory()
+        n_e2e = max(1, min(args.steps, 3))
+        torch.cuda.synchronize(dev)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(n_e2e):
+            A.copy_(Ah, non_blocking=True)
+            Om.copy_(Omh, non_blocking=True)
+            step()
+            Sh.copy_(S, non_blocking=True)
+            Uh.copy_(U, non_blocking=True)
+            Vh.copy_(V, non_blocking=True)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        ems = f0.elapsed_time(f1)
+        e2e = {"value": flops * n_e2e / (ems * 1e-3) / 1e9, "unit": "GFLOP/s",
+               "h2d_bytes_per_step": Ah.numel() * 4 + Omh.numel() * 4,
+               "d2h_bytes_per_step": Sh.numel() * 8 + Uh.numel() * 4 + Vh.numel() * 4,
+               "ms_per_step": ems / n_e2e}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import numpy as np
+
+        import oracle
+        rows = args.bk_cpu_rows
+        a = np.ascontiguousarray(A[:rows].cpu().numpy().astype(np.float64))
+        om = Om.cpu().numpy().astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.block_krylov(oracle.center(a)[0], om, iters, k)
+        tsec = time.perf_counter() - t0
+        cpu = {"value": bk_flops(rows, n, b, iters) / tsec / 1e9, "unit": "GFLOP/s", "cores": os.cpu_count(),
+               "kind": "oracle",
+               "sample": f"first {rows} of {m} rows (same n, b, i, k, Omega); FP64 C oracle, OpenMP, one solve"}
+
+    if rank == 0:
+        line = {
+            "metric": "block Krylov GFLOP/s", "value": value, "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": BK_WORKLOAD, "method": "block_krylov", "m": m, "n": n, "k": k, "b": b,
+                       "iters": iters, "W": W, "l2": "inputs larger than L2 (A is 17.2 GB), no flush",
+                       "parallelism": f"replicas{world}"},
+            "solves_per_s": world * args.steps / (ms_max * 1e-3), "status": st,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clocks, "peaks_source": src,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
 
 
 def run_reference(args):
@@ -339,11 +497,16 @@ def main():
     ap.add_argument("--sample-rows", type=int, default=40000, help="rows per reference-arm step")
     ap.add_argument("--cpu-baseline-rows", type=int, default=100000, help="rows of the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--method", default="rsvd", choices=["rsvd", "block_krylov"],
+                    help="rsvd: the default workload; block_krylov: the Sec. 3.1.1 workload")
+    ap.add_argument("--bk-cpu-rows", type=int, default=16384, help="rows of the block Krylov cpu_baseline sample")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.method == "block_krylov":
+        return run_block_krylov(args)
     return run_ours(args)
 
 

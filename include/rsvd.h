@@ -170,6 +170,42 @@ rsvd_status svd_truncated_krylov(rsvd_plan_t plan, void *A, const void *v1, int 
                                  double *S, void *U, void *V);
 
 /*
+ * Block Krylov method (Sec. 3.1.1): the Rayleigh-Ritz approximation of the
+ * leading k singular triplets from the block Krylov space
+ *   span [H(0) | H(1) | ... | H(i)],  H(0) = A Omega,  H(j) = A (A^T H(j-1)),
+ * of W = (i + 1) b columns (Omega n x b Gaussian, caller-drawn):
+ *   Q = orth([H(0) | ... | H(i)]);  T = A^T Q (= B^T);  T = Vt Sigma W^T;  U = Q W.
+ * The plan comes from rsvd_plan_create_block_krylov (block width b, i =
+ * `iters`); rsvd() and batches reject such plans, and rsvd_block_krylov
+ * rejects the others (RSVD_ERR_ARG).
+ * The basis is built block by block and never from the power blocks
+ * themselves, which become nearly dependent as they converge: block j is the
+ * part of A A^T (block j-1) orthogonal to the blocks before it (block classical
+ * Gram-Schmidt, applied twice), orthonormalised by SVQB -- the eigen-
+ * decomposition G = V diag(lam) V^T of its Gram matrix, X V diag(lam)^{-1/2}
+ * -- then projected once more and finished by CholeskyQR2.  In exact arithmetic
+ * this spans the same space as the step list; directions of a block whose
+ * eigenvalue lam is below 2u lam_1 (u the unit roundoff of the element type)
+ * are not resolved by the block's rounding and are replaced by pseudo-random
+ * ones (SplitMix64, fixed seed), which keeps Q orthonormal on rank-deficient
+ * or fast-decaying spectra and only enlarges the space searched.  The products
+ * with A and Omega are those of rsvd(); the Rayleigh-Ritz steps are rsvd()'s
+ * at width W, except that an RSVD_F32 plan factors T by CholeskyQR2 in float64
+ * (its Gram matrices accumulated in float64 from the float32 T): T's Ritz
+ * values span the whole Krylov space, far below what a float32 Gram resolves.
+ *   A     : m x n row-major, read only (centred on the fly unless RSVD_FLAG_NO_CENTER).
+ *   Omega : n x b; S : k doubles; U : m x k; V : n x k.
+ * Element types as for rsvd() with RSVD_F32 / RSVD_F64 (the only dtypes).
+ * Limits: k <= W <= n, b <= 112 (the block's Gram eigen-decomposition runs in
+ * one CTA), W <= 288 (RSVD_F32) or 112 (RSVD_F64); RSVD_ERR_UNSUPPORTED
+ * beyond them, RSVD_ERR_ARG for inconsistent sizes.  Launches run directly on
+ * the plan's stream (no graph capture); statuses as for rsvd().
+ */
+rsvd_status rsvd_plan_create_block_krylov(rsvd_plan_t *plan, int64_t m, int64_t n, int k, int b, int iters,
+                                          rsvd_dtype dtype, void *cuda_stream);
+rsvd_status rsvd_block_krylov(rsvd_plan_t plan, void *A, const void *Omega, double *S, void *U, void *V);
+
+/*
  * Sec. 2.4 cumulative explained variance: the minimal K with
  *   sum_{i<=K} sigma_i^2 >= t * ||A||_F^2
  * over the singular values of the plan's last solve, with the denominator

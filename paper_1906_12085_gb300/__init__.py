@@ -26,7 +26,7 @@ __all__ = [
     "rsvd_plan_create_in", "Batch", "rsvd_batch_create", "rsvd_batch_run", "rsvd_batch_sync",
     "rsvd_batch_destroy", "Server", "rsvd_server_create", "rsvd_server_submit", "rsvd_server_poll",
     "rsvd_server_pending", "rsvd_server_destroy", "rsvd_autotune", "rsvd_tune_lookup", "rsvd_tune_clear",
-    "rsvd_quantize", "rsvd_server_submit_ex",
+    "rsvd_quantize", "rsvd_server_submit_ex", "rsvd_plan_create_block_krylov", "rsvd_block_krylov",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -112,13 +112,16 @@ def lib() -> ctypes.CDLL:
     L.rsvd_tune_lookup.argtypes = [i64, i64, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     L.rsvd_quantize.argtypes = [vp, i64, i64, i64, i32, vp, vp, vp]
     L.rsvd_tune_clear.argtypes = []
+    L.rsvd_plan_create_block_krylov.argtypes = [ctypes.POINTER(vp), i64, i64, i32, i32, i32, i32, vp]
+    L.rsvd_block_krylov.argtypes = [vp, vp, vp, vp, vp, vp]
     L.rsvd_tune_clear.restype = None
     for f in ("rsvd_plan_create", "rsvd_plan_destroy", "rsvd_plan_set_flags", "rsvd_plan_sync", "rsvd",
               "svd_exact", "svd_truncated_krylov", "pca_threshold", "rsvd_plan_fro2", "rsvd_plan_profile",
               "rsvd_plan_profile_read", "rsvd_workspace_query", "rsvd_plan_create_in", "rsvd_batch_create",
               "rsvd_batch_run", "rsvd_batch_sync", "rsvd_batch_destroy", "rsvd_server_create",
               "rsvd_server_submit", "rsvd_server_poll", "rsvd_server_pending", "rsvd_server_destroy",
-              "rsvd_autotune", "rsvd_tune_lookup", "rsvd_quantize", "rsvd_server_submit_ex"):
+              "rsvd_autotune", "rsvd_tune_lookup", "rsvd_quantize", "rsvd_server_submit_ex",
+              "rsvd_plan_create_block_krylov", "rsvd_block_krylov"):
         getattr(L, f).restype = i32
     _lib = L
     return L
@@ -220,6 +223,21 @@ def rsvd_plan_sync(plan: Plan) -> int:
 
 def rsvd(plan: Plan, A, col_scales, Omega, S, U, V) -> int:
     return lib().rsvd(plan.handle, _ptr(A), _ptr(col_scales), _ptr(Omega), _ptr(S), _ptr(U), _ptr(V))
+
+
+def rsvd_plan_create_block_krylov(m: int, n: int, k: int, b: int, iters: int, dtype: int = RSVD_F32,
+                                  stream=None) -> Plan:
+    """Plan of the block Krylov method: blocks of b columns, iters + 1 of them."""
+    h = ctypes.c_void_p()
+    st = lib().rsvd_plan_create_block_krylov(ctypes.byref(h), m, n, k, b, iters, dtype, _stream(stream))
+    check(st, "rsvd_plan_create_block_krylov")
+    plan = Plan(h.value, m, n, k, 0, iters, dtype)
+    plan.b, plan.iters = b, iters
+    return plan
+
+
+def rsvd_block_krylov(plan: Plan, A, Omega, S, U, V) -> int:
+    return lib().rsvd_block_krylov(plan.handle, _ptr(A), _ptr(Omega), _ptr(S), _ptr(U), _ptr(V))
 
 
 def svd_exact(plan: Plan, A, method: int, S, U, V) -> int:

@@ -258,6 +258,23 @@ cudaError_t tc_gemm_tn(int64_t rows, int ncols, int N, const float *A, int64_t l
                        const float *mu = nullptr, int ctas = 0, bool upper_c = false);
 int64_t tc_gemm_tn_partials(int64_t rows, int ncols, int N);
 
+// ------------------------------------------------------ block Krylov (Sec. 3.1.1)
+// B ((jl + l) x lp, ld lp): rows below jl negated in place (they hold C = H^T Y),
+// rows jl..jl+l-1 set to [I_l 0]; then H[:, :jl+l] B = Y - H[:, :jl] C when
+// H[:, jl:jl+l] holds Y.
+template <typename T>
+cudaError_t bk_proj_matrix(T *B, int jl, int l, int lp, cudaStream_t s);
+// SVQB scaling of a block's Gram eigen-decomposition (lam descending, V l x l,
+// column i = eigenvector i): M (lp x lp) = V diag(lam)^{-1/2} on the columns with
+// lam_c > tau lam_0, zero columns elsewhere, flag[c] = 1 for those (lp ints).
+template <typename T>
+cudaError_t svqb_scale(const double *lam, const double *V, int l, int lp, double tau, T *M, int *flag,
+                       cudaStream_t s);
+// The flagged columns c < l of X (m x lp, ld lp) <- uniform entries in
+// [-sqrt(3/m), sqrt(3/m)) from a counter-based generator (SplitMix64) and `seed`.
+template <typename T>
+cudaError_t bk_fill(T *X, int64_t m, int l, int lp, const int *flag, uint64_t seed, cudaStream_t s);
+
 // ------------------------------------------------------ Golub-Kahan-Lanczos
 // y = (A - 1 mu^T) v - beta[0] * uprev (beta / uprev / mu may be NULL)
 template <typename T>

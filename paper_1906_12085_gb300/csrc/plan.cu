@@ -27,6 +27,10 @@ void gbr::note_launch(int count) { g_launches.fetch_add((uint64_t)count, std::me
 struct rsvd_plan {
     int64_t m = 0, n = 0;
     int k = 0, p = 0, q = 0, l = 0, lp = 0;  // lp: l padded to a multiple of 16 (zero columns)
+    int lpc = 0;                             // widest basis the workspace is sized for (lp, or Wp below)
+    // block Krylov plans (Sec. 3.1.1): bk_blocks = i + 1 blocks of l = b columns, W = bk_blocks * l
+    // columns in all, Wp = lpc = W padded to a multiple of 16; 0 for the other plans
+    int bk_blocks = 0;
     int nx = 0;                              // n if svd_exact is supported (n <= kSmallMaxF64), else 0
     int wide = 0;                            // width of the m-row work buffers
     rsvd_dtype dtype = RSVD_F32;
@@ -51,6 +55,12 @@ struct rsvd_plan {
     double *lam = nullptr, *Vfull = nullptr, *sig = nullptr;
     int *status = nullptr, *Kdev = nullptr;
     void *chol_ws = nullptr, *jac_ws = nullptr;  // global l x l blocks of the small solvers (large l only)
+    void *Hk = nullptr;                          // block Krylov basis, m x Wp
+    int *bk_flag = nullptr;                      // block Krylov: directions of a block to refill (lp ints)
+    // float32 block Krylov plans: float64 copies of T and its CholeskyQR2 bases (n x Wp) and
+    // the split-K partials of their float64 Gram products
+    double *t64 = nullptr, *q64a = nullptr, *q64b = nullptr, *part64 = nullptr;
+    int64_t part64_elems = 0;
     int last_count = 0;
     // tensor-core path (float32): transposed tf32 split of the small operand, split-K partials
     bool tc = false;
@@ -108,7 +118,7 @@ struct Carver {
 void carve(rsvd_plan *P, Carver &c) {
     const size_t es = esize(P->dtype);
     const int64_t m = P->m, n = P->n;
-    const int64_t sq = P->lp > P->nx ? P->lp : P->nx;   // small square side
+    const int64_t sq = P->lpc > P->nx ? P->lpc : P->nx;  // small square side
     const int64_t nw = sq;                               // width of the n-row buffers
     P->mu = (double *)c.take(sizeof(double) * n);
     P->fro2 = (double *)c.take(sizeof(double));
@@ -137,9 +147,11 @@ void carve(rsvd_plan *P, Carver &c) {
         const int64_t e = gemm_tn_partials(rows, N, L);
         if (e > pe) pe = e;
     };
-    upd(m, n, P->lp);          // Z = A^T Q, T = A^T Q
-    upd(m, P->lp, P->lp);      // Gram of Y
-    upd(n, P->lp, P->lp);      // Gram of Z, T
+    upd(m, n, P->lpc);         // Z = A^T Q, T = A^T Q
+    upd(m, P->lpc, P->lpc);    // Gram of Y
+    upd(n, P->lpc, P->lpc);    // Gram of Z, T
+    upd(m, P->lp, P->lp);
+    for (int j = 1; j < P->bk_blocks; j++) upd(m, (int64_t)j * P->l, P->lp);  // block Krylov projections
     if (P->nx) {
         upd(m, P->nx, P->nx);  // A^T A and Gram of A
     }
@@ -160,10 +172,21 @@ void carve(rsvd_plan *P, Carver &c) {
     P->sig = (double *)c.take(sizeof(double) * (n > sq ? n : sq));
     P->status = (int *)c.take(sizeof(int));
     P->Kdev = (int *)c.take(2 * sizeof(int));
-    if (P->lp > kSmallMaxF64)  // l x l blocks of the Cholesky beyond one SM's shared memory (float64 sizing)
-        P->chol_ws = c.take(chol_scratch_bytes(P->lp, sizeof(double)));
-    if (P->lp > 160)           // and of the float32 Jacobi
-        P->jac_ws = c.take(jacobi_scratch_bytes(P->lp, sizeof(float)));
+    if (P->lpc > kSmallMaxF64)  // l x l blocks of the Cholesky beyond one SM's shared memory (float64 sizing)
+        P->chol_ws = c.take(chol_scratch_bytes(P->lpc, sizeof(double)));
+    if (P->lpc > 160)           // and of the float32 Jacobi
+        P->jac_ws = c.take(jacobi_scratch_bytes(P->lpc, sizeof(float)));
+    if (P->bk_blocks) {
+        P->Hk = c.take(es * m * P->lpc);
+        P->bk_flag = (int *)c.take(sizeof(int) * P->lpc);
+        if (P->dtype == RSVD_F32) {
+            P->t64 = (double *)c.take(sizeof(double) * n * P->lpc);
+            P->q64a = (double *)c.take(sizeof(double) * n * P->lpc);
+            P->q64b = (double *)c.take(sizeof(double) * n * P->lpc);
+            P->part64_elems = gemm_tn_partials(n, P->lpc, P->lpc);
+            P->part64 = (double *)c.take(sizeof(double) * (P->part64_elems > 0 ? P->part64_elems : 1));
+        }
+    }
     if (P->dtype == RSVD_FP8_E4M3) {
         P->ldz8 = round_up(n, 16);
         P->Zq8 = c.take((size_t)P->lp * P->ldz8);
@@ -193,11 +216,17 @@ void carve(rsvd_plan *P, Carver &c) {
     }
     if (P->tc) {
         P->ldt = round_up(n > P->wide ? n : P->wide, 4);
-        P->Bth = (float *)c.take(sizeof(float) * P->lp * P->ldt);
-        P->Btl = (float *)c.take(sizeof(float) * P->lp * P->ldt);
-        int64_t te = tc_gemm_tn_partials(m, (int)n, P->lp);
-        const int64_t t2 = tc_gemm_tn_partials(m, P->lp, P->lp);
-        if (t2 > te) te = t2;
+        P->Bth = (float *)c.take(sizeof(float) * P->lpc * P->ldt);
+        P->Btl = (float *)c.take(sizeof(float) * P->lpc * P->ldt);
+        int64_t te = 0;
+        auto tupd = [&](int64_t rows, int64_t ncols, int N) {
+            const int64_t e = tc_gemm_tn_partials(rows, (int)ncols, N);
+            if (e > te) te = e;
+        };
+        tupd(m, n, P->lpc);
+        tupd(m, P->lpc, P->lpc);
+        tupd(m, P->lp, P->lp);
+        for (int j = 1; j < P->bk_blocks; j++) tupd(m, (int64_t)j * P->l, P->lp);
         P->tcpart_elems = te;
         P->tcpart = (float *)c.take(sizeof(float) * te);
     }
@@ -344,14 +373,80 @@ rsvd_status center(rsvd_plan *P, T *A) {
     return RSVD_OK;
 }
 
+// CholeskyQR2 of the float32 T (rows x w, ld) in float64: the Gram matrices are
+// accumulated in float64 from the float32 entries (every product exact), so they
+// stay positive semidefinite to float64 rounding and the factorisation holds up
+// to cond(T) ~ 1e8 (with the breakdown shift beyond).  Qo = float32 Q_T, Rt = R.
+rsvd_status cqr2_f64(rsvd_plan *P, const float *X, int64_t rows, int w, int ld, float *Qo) {
+    cudaStream_t s = P->stream;
+    const double u = DBL_EPSILON / 2;
+    double *T = P->t64, *Q1 = P->q64a, *Q2 = P->q64b;
+    CK(copy2d<float, double>(X, ld, T, ld, rows, ld, ld, s));
+    CK(gemm_tn<double>(rows, ld, ld, T, ld, T, ld, P->G64, ld, P->part64, P->part64_elems, s));
+    CK(chol_inv<double, double, double>(P->G64, ld, w, rows, u, P->R1, P->R1i, P->Vfull, ld, P->status, s,
+                                        P->chol_ws));
+    CK(gemm_nn<double>(rows, ld, ld, T, ld, P->Vfull, ld, Q1, ld, s));
+    CK(gemm_tn<double>(rows, ld, ld, Q1, ld, Q1, ld, P->G64, ld, P->part64, P->part64_elems, s));
+    CK(chol_inv<double, double, double>(P->G64, ld, w, rows, u, P->R2, P->R2i, P->Vfull, ld, P->status, s,
+                                        P->chol_ws));
+    CK(gemm_nn<double>(rows, ld, ld, Q1, ld, P->Vfull, ld, Q2, ld, s));
+    CK(trmm_upper(P->R2, P->R1, P->Rt, w, s));
+    CK(copy2d<double, float>(Q2, ld, Qo, ld, rows, ld, ld, s));
+    return RSVD_OK;
+}
+
+// The Rayleigh-Ritz steps shared by Sec. 3.1.1 and Sec. 3.1.2 for an orthonormal
+// basis Q (m x lp, the plan's current l and lp): T = (A - 1 mu^T)^T Q (= B^T),
+// T = Q_T R (CholeskyQR2), R = U_R Sigma W^T (one-sided Jacobi, singular values
+// refined in float64), V = Q_T U_R, U = Q W; the leading k triplets.  The float32
+// block Krylov solve factors T in float64 (cqr2_f64): its Ritz values span the
+// whole Krylov space, far below what a float32 Gram matrix of T resolves.
+template <typename T>
+rsvd_status ritz(rsvd_plan *P, const T *A, const T *mu, const T *Q, double *S, T *U, T *V) {
+    cudaStream_t s = P->stream;
+    const int64_t m = P->m, n = P->n;
+    const int l = P->l, lp = P->lp, k = P->k;
+    T *Qz = (T *)P->Qz, *Tn = (T *)P->Tn, *Vt = (T *)P->Vt, *Tmpn = (T *)P->Tmpn;
+    rsvd_status st;
+    {
+        Span sp(P, RSVD_STAGE_ATX);
+        CK(prod_tn<T>(P, m, n, A, n, Q, lp, Tn, lp, mu));                       // T = A^T Q  (= B^T)
+    }
+    T *UR = (T *)P->UR, *W = (T *)P->Wm;
+    {
+        Span sp(P, RSVD_STAGE_SMALL);
+        if constexpr (sizeof(T) == 4) {
+            if (P->bk_blocks) {
+                if ((st = cqr2_f64(P, (const float *)Tn, n, l, lp, (float *)Qz))) return st;   // T = Q_T R
+            } else if ((st = cqr2<T>(P, Tn, n, l, lp, Qz, Tmpn, true))) {
+                return st;
+            }
+        } else if ((st = cqr2<T>(P, Tn, n, l, lp, Qz, Tmpn, true))) {
+            return st;
+        }
+        CK(jacobi_osvd<T, T>(P->Rt, l, lp, P->sig, UR, W, P->status, s, P->jac_ws));     // R = U_R Sigma W^T
+        CK(sv_refine<T>(P->Rt, l, lp, UR, W, P->sig, s));                     // sigma_i = u_i^T R w_i (float64)
+    }
+    {
+        Span sp(P, RSVD_STAGE_FINISH);
+        CK(gemm_nn<T>(n, lp, lp, Qz, lp, UR, lp, Vt, lp, s));                 // Vt = Q_T U_R
+        CK(sign_normalize<T>(Vt, n, l, lp, W, l, lp, s));
+        CK(gemm_nn<T>(m, k, lp, Q, lp, W, lp, U, k, s));                      // U = Q W (leading k)
+        CK(copy2d<T, T>(Vt, lp, V, k, n, k, k, s));
+        CK(copy_f64(P->sig, S, k, s));
+    }
+    P->last_count = k;
+    return RSVD_OK;
+}
+
 // Sec. 3.1.2 with re-orthonormalised power steps; see rsvd() in include/rsvd.h.
 template <typename T>
 rsvd_status run_rsvd(rsvd_plan *P, T *A, const T *Omega, double *S, T *U, T *V) {
     cudaStream_t s = P->stream;
     const int64_t m = P->m, n = P->n;
-    const int l = P->l, lp = P->lp, k = P->k;
+    const int l = P->l, lp = P->lp;
     T *Y = (T *)P->Y, *Q = (T *)P->Qb, *Tmp = (T *)P->Tmp;
-    T *Ob = (T *)P->Ob, *Z = (T *)P->Z, *Qz = (T *)P->Qz, *Tn = (T *)P->Tn, *Vt = (T *)P->Vt, *Tmpn = (T *)P->Tmpn;
+    T *Ob = (T *)P->Ob, *Z = (T *)P->Z, *Qz = (T *)P->Qz, *Tmpn = (T *)P->Tmpn;
     rsvd_status st;
     // A is read only: its column means mu are subtracted inside every product with A
     const bool centred = !(P->flags & RSVD_FLAG_NO_CENTER);
@@ -391,27 +486,105 @@ rsvd_status run_rsvd(rsvd_plan *P, T *A, const T *Omega, double *S, T *U, T *V) 
             if ((st = cqr<T>(P, Y, m, l, lp, Q, Tmp, false, last ? 2 : 1))) return st;
         }
     }
-    {
-        Span sp(P, RSVD_STAGE_ATX);
-        CK(prod_tn<T>(P, m, n, A, n, Q, lp, Tn, lp, mu));                       // T = A^T Q  (= B^T)
+    return ritz<T>(P, A, mu, Q, S, U, V);
+}
+
+// The plan's basis width switched for the Rayleigh-Ritz steps of a block Krylov solve.
+struct Width {
+    rsvd_plan *P;
+    int l0, lp0;
+    Width(rsvd_plan *P_, int l, int lp) : P(P_), l0(P_->l), lp0(P_->lp) {
+        P->l = l;
+        P->lp = lp;
     }
-    T *UR = (T *)P->UR, *W = (T *)P->Wm;
+    ~Width() {
+        P->l = l0;
+        P->lp = lp0;
+    }
+};
+
+// Sec. 3.1.1 block Krylov method; see rsvd_block_krylov() in include/rsvd.h.  The basis
+// of the Krylov space [H(0) | ... | H(i)] is built block by block (block classical
+// Gram-Schmidt applied twice, each block orthonormalised by SVQB and CholeskyQR2), so
+// it is never formed from nearly dependent power blocks; the Rayleigh-Ritz steps are
+// those of the randomized method at width W = (i + 1) b.
+template <typename T>
+rsvd_status run_block_krylov(rsvd_plan *P, T *A, const T *Omega, double *S, T *U, T *V) {
+    cudaStream_t s = P->stream;
+    const int64_t m = P->m, n = P->n;
+    const int b = P->l, lp = P->lp, nb = P->bk_blocks, Wp = P->lpc;
+    T *Y = (T *)P->Y, *Qb = (T *)P->Qb, *Tmp = (T *)P->Tmp, *H = (T *)P->Hk;
+    T *Ob = (T *)P->Ob, *Z = (T *)P->Z, *Qz = (T *)P->Qz, *Tmpn = (T *)P->Tmpn;
+    T *Bp = (T *)P->UR, *M = (T *)P->Wm, *G = (T *)P->G;
+    rsvd_status st;
+    const bool centred = !(P->flags & RSVD_FLAG_NO_CENTER);
+    const T *mu = centred ? (const T *)P->mu_t : nullptr;
+    // eigenvalues of a block's Gram matrix below tau lam_1 are not resolved by its
+    // rounding (float32: 2^-23); their directions are replaced by random ones
+    const double tau = 2.0 * unit_roundoff<T>();
+    const uint64_t seed = 0x190612085ull;
     {
-        Span sp(P, RSVD_STAGE_SMALL);
-        if ((st = cqr2<T>(P, Tn, n, l, lp, Qz, Tmpn, true))) return st;       // T = Q_T R
-        CK(jacobi_osvd<T, T>(P->Rt, l, lp, P->sig, UR, W, P->status, s, P->jac_ws));     // R = U_R Sigma W^T
-        CK(sv_refine<T>(P->Rt, l, lp, UR, W, P->sig, s));                     // sigma_i = u_i^T R w_i (float64)
+        Span sp(P, RSVD_STAGE_CENTER);
+        if (centred) CK(column_means<T>(A, m, n, n, P->mu, (T *)P->mu_t, P->npad, P->cpart, s));
+        else CK(cudaMemsetAsync(P->mu, 0, sizeof(double) * n, s));
+    }
+    // Out = X - H_j (H_j^T X) for the first jl columns H_j of the basis: X is copied into
+    // the next b columns of H so that one product H[:, :jl+b] [-C; I] applies it
+    auto project = [&](const T *X, int jl, T *Out) -> cudaError_t {
+        cudaError_t e = copy2d<T, T>(X, lp, H + jl, Wp, m, b, b, s);
+        if (e == cudaSuccess) e = prod_tn<T>(P, m, jl, H, Wp, X, lp, Bp, lp);        // C = H_j^T X
+        if (e == cudaSuccess) e = bk_proj_matrix<T>(Bp, jl, b, lp, s);               // [-C; I]
+        if (e == cudaSuccess) e = prod_nn<T>(P, m, jl + b, H, Wp, Bp, lp, Out, lp);  // X - H_j C
+        return e;
+    };
+    // SVQB (Stathopoulos and Wu, 2002): X^T X = V diag(lam) V^T, Out = X V diag(lam)^{-1/2}
+    // on the resolved directions, random columns on the others
+    auto svqb = [&](const T *X, T *Out, uint64_t sd) -> cudaError_t {
+        cudaError_t e = prod_tn<T>(P, m, lp, X, lp, X, lp, G, lp);                   // the full Gram matrix
+        if (e == cudaSuccess) e = copy2d<T, double>(G, lp, P->G64, b, b, b, b, s);
+        if (e == cudaSuccess) e = jacobi_eig(P->G64, b, P->lam, P->Vfull, P->status, s);
+        if (e == cudaSuccess) e = svqb_scale<T>(P->lam, P->Vfull, b, lp, tau, M, P->bk_flag, s);
+        if (e == cudaSuccess) e = prod_nn<T>(P, m, lp, X, lp, M, lp, Out, lp);
+        if (e == cudaSuccess) e = bk_fill<T>(Out, m, b, lp, P->bk_flag, sd, s);
+        return e;
+    };
+    CK(copy2d<T, T>(Omega, b, Ob, lp, n, b, lp, s));                          // G padded to lp columns
+    {
+        Span sp(P, RSVD_STAGE_AX);
+        CK(prod_nn<T>(P, m, n, A, n, Ob, lp, Y, lp, mu, P->fro2));             // H(0) = A G, ||A||_F^2
     }
     {
-        Span sp(P, RSVD_STAGE_FINISH);
-        CK(gemm_nn<T>(n, lp, lp, Qz, lp, UR, lp, Vt, lp, s));                 // Vt = Q_T U_R
-        CK(sign_normalize<T>(Vt, n, l, lp, W, l, lp, s));
-        CK(gemm_nn<T>(m, k, lp, Q, lp, W, lp, U, k, s));                      // U = Q W (leading k)
-        CK(copy2d<T, T>(Vt, lp, V, k, n, k, k, s));
-        CK(copy_f64(P->sig, S, k, s));
+        Span sp(P, RSVD_STAGE_ORTH);
+        CK(svqb(Y, Tmp, seed));
+        if ((st = cqr<T>(P, Tmp, m, b, lp, Qb, Y, false, 2))) return st;
+        CK(copy2d<T, T>(Qb, lp, H, Wp, m, b, b, s));
     }
-    P->last_count = k;
-    return RSVD_OK;
+    for (int j = 1; j < nb; j++) {                // block j spans the new directions of A A^T (block j-1)
+        const int jl = j * b;
+        {
+            Span sp(P, RSVD_STAGE_ATX);
+            CK(prod_tn<T>(P, m, n, A, n, Qb, lp, Z, lp, mu));
+        }
+        {
+            Span sp(P, RSVD_STAGE_ORTH);
+            if ((st = cqr<T>(P, Z, n, b, lp, Qz, Tmpn, false, 1))) return st;
+        }
+        {
+            Span sp(P, RSVD_STAGE_AX);
+            CK(prod_nn<T>(P, m, n, A, n, Qz, lp, Y, lp, mu));
+        }
+        {
+            Span sp(P, RSVD_STAGE_ORTH);
+            CK(project(Y, jl, Tmp));
+            CK(project(Tmp, jl, Y));
+            CK(svqb(Y, Tmp, seed + (uint64_t)j));
+            CK(project(Tmp, jl, Y));
+            if ((st = cqr<T>(P, Y, m, b, lp, Qb, Tmp, false, 2))) return st;
+            CK(copy2d<T, T>(Qb, lp, H + jl, Wp, m, b, b, s));
+        }
+    }
+    Width wd(P, nb * b, Wp);
+    return ritz<T>(P, A, mu, H, S, U, V);
 }
 
 // Sec. 3.1.2 on a bfloat16-stored A (precision form).  The products with A take
@@ -977,6 +1150,7 @@ rsvd_status plan_init(rsvd_plan *P, int64_t m, int64_t n, int k, int p, int q, r
     P->q = q;
     P->l = k + p;
     P->lp = (int)round_up(P->l, 16);
+    P->lpc = P->lp;
     P->nx = n <= kSmallMaxF64 && (dtype == RSVD_F32 || dtype == RSVD_F64) ? (int)n : 0;
     P->wide = P->lp > P->nx ? P->lp : P->nx;
     P->dtype = dtype;
@@ -993,6 +1167,55 @@ rsvd_status plan_init(rsvd_plan *P, int64_t m, int64_t n, int k, int p, int q, r
     Carver c;
     carve(P, c);
     P->ws_bytes = c.off;
+    return RSVD_OK;
+}
+
+// Block Krylov plan: blocks of b columns, iters + 1 of them (W = (iters + 1) b).
+rsvd_status bk_plan_init(rsvd_plan *P, int64_t m, int64_t n, int k, int b, int iters, rsvd_dtype dtype,
+                         void *cuda_stream) {
+    if (m < 1 || n < 1 || m < n || k < 1 || b < 1 || iters < 0) return RSVD_ERR_ARG;
+    const int64_t W = (int64_t)(iters + 1) * b;
+    if (k > W || W > n) return RSVD_ERR_ARG;
+    if (dtype != RSVD_F32 && dtype != RSVD_F64) return RSVD_ERR_UNSUPPORTED;
+    // a block's Gram eigen-decomposition runs in one CTA's shared memory; the Rayleigh-Ritz
+    // steps at width W have the randomized method's limits
+    if (round_up(b, 16) > kSmallMaxF64) return RSVD_ERR_UNSUPPORTED;
+    if (W > (dtype == RSVD_F64 ? kSmallMaxF64 : kRsvdMaxL)) return RSVD_ERR_UNSUPPORTED;
+    P->m = m;
+    P->n = n;
+    P->k = k;
+    P->p = 0;
+    P->q = iters;
+    P->l = b;
+    P->lp = (int)round_up(b, 16);
+    P->bk_blocks = iters + 1;
+    P->lpc = (int)round_up(W, 16);
+    P->nx = n <= kSmallMaxF64 ? (int)n : 0;
+    P->wide = P->lpc > P->nx ? P->lpc : P->nx;
+    P->dtype = dtype;
+    P->stream = (cudaStream_t)cuda_stream;
+    P->tc = dtype == RSVD_F32 && tc_available();
+    Carver c;
+    carve(P, c);
+    P->ws_bytes = c.off;
+    return RSVD_OK;
+}
+
+// Allocates, carves and clears the workspace of an initialised plan.
+rsvd_status plan_alloc(rsvd_plan *P) {
+    if (cudaMalloc(&P->ws, P->ws_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return RSVD_ERR_OOM;
+    }
+    Carver c2;
+    c2.base = (char *)P->ws;
+    carve(P, c2);
+    if (cudaMemsetAsync(P->ws, 0, P->ws_bytes, P->stream) != cudaSuccess ||
+        cudaStreamSynchronize(P->stream) != cudaSuccess) {
+        cudaFree(P->ws);
+        P->ws = nullptr;
+        return RSVD_ERR_CUDA;
+    }
     return RSVD_OK;
 }
 
@@ -1096,27 +1319,37 @@ rsvd_status rsvd_plan_create(rsvd_plan_t *plan, int64_t m, int64_t n, int k, int
     *plan = nullptr;
     rsvd_plan *P = new (std::nothrow) rsvd_plan();
     if (!P) return RSVD_ERR_OOM;
-    const rsvd_status st = plan_init(P, m, n, k, p, q, dtype, cuda_stream);
+    rsvd_status st = plan_init(P, m, n, k, p, q, dtype, cuda_stream);
+    if (st == RSVD_OK) st = plan_alloc(P);
     if (st != RSVD_OK) {
         delete P;
         return st;
     }
-    if (cudaMalloc(&P->ws, P->ws_bytes) != cudaSuccess) {
-        cudaGetLastError();
+    *plan = P;
+    return RSVD_OK;
+}
+
+rsvd_status rsvd_plan_create_block_krylov(rsvd_plan_t *plan, int64_t m, int64_t n, int k, int b, int iters,
+                                          rsvd_dtype dtype, void *cuda_stream) {
+    if (!plan) return RSVD_ERR_ARG;
+    *plan = nullptr;
+    rsvd_plan *P = new (std::nothrow) rsvd_plan();
+    if (!P) return RSVD_ERR_OOM;
+    rsvd_status st = bk_plan_init(P, m, n, k, b, iters, dtype, cuda_stream);
+    if (st == RSVD_OK) st = plan_alloc(P);
+    if (st != RSVD_OK) {
         delete P;
-        return RSVD_ERR_OOM;
-    }
-    Carver c2;
-    c2.base = (char *)P->ws;
-    carve(P, c2);
-    if (cudaMemsetAsync(P->ws, 0, P->ws_bytes, P->stream) != cudaSuccess ||
-        cudaStreamSynchronize(P->stream) != cudaSuccess) {
-        cudaFree(P->ws);
-        delete P;
-        return RSVD_ERR_CUDA;
+        return st;
     }
     *plan = P;
     return RSVD_OK;
+}
+
+rsvd_status rsvd_block_krylov(rsvd_plan_t P, void *A, const void *Omega, double *S, void *U, void *V) {
+    if (!P || !A || !Omega || !S || !U || !V || !P->bk_blocks) return RSVD_ERR_ARG;
+    if (P->dtype == RSVD_F32)
+        return run_block_krylov<float>(P, (float *)A, (const float *)Omega, S, (float *)U, (float *)V);
+    return run_block_krylov<double>(P, (double *)A, (const double *)Omega, S, (double *)U, (double *)V);
 }
 
 rsvd_status rsvd_plan_destroy(rsvd_plan_t P) {
@@ -1149,7 +1382,7 @@ rsvd_status rsvd_plan_sync(rsvd_plan_t P) {
 }
 
 rsvd_status rsvd(rsvd_plan_t P, void *A, const float *col_scales, const void *Omega, double *S, void *U, void *V) {
-    if (!P || !A || !Omega || !S || !U || !V) return RSVD_ERR_ARG;
+    if (!P || !A || !Omega || !S || !U || !V || P->bk_blocks) return RSVD_ERR_ARG;
     if ((col_scales != nullptr) != (P->dtype == RSVD_FP8_E4M3)) return RSVD_ERR_ARG;  // e4m3 needs its scales
     // Tracing records events between launches and the legacy stream cannot be captured:
     // both run the launches directly.
@@ -1211,7 +1444,7 @@ rsvd_status rsvd_batch_create(rsvd_batch_t *batch, int count, rsvd_plan_t const 
     if (count < 1 || count > RSVD_BATCH_MAX || !plans) return RSVD_ERR_ARG;
     for (int i = 0; i < count; i++) {
         const rsvd_plan *P = plans[i];
-        if (!P) return RSVD_ERR_ARG;
+        if (!P || P->bk_blocks) return RSVD_ERR_ARG;
         if (P->dtype != plans[0]->dtype || P->l != plans[0]->l || P->q != plans[0]->q) return RSVD_ERR_ARG;
         if (P->dtype != RSVD_F32 && P->dtype != RSVD_F64) return RSVD_ERR_UNSUPPORTED;
         if (P->l > kSmallMaxF32) return RSVD_ERR_UNSUPPORTED;  // batched small kernels: l x l in shared memory
@@ -1307,7 +1540,7 @@ rsvd_status rsvd_batch_destroy(rsvd_batch_t B) {
 }
 
 rsvd_status rsvd_autotune(rsvd_plan_t P, void *A, const void *Omega, int concurrency, int *nn_out, int *tn_out) {
-    if (!P || !A || !Omega || concurrency < 1 || concurrency > 64) return RSVD_ERR_ARG;
+    if (!P || !A || !Omega || concurrency < 1 || concurrency > 64 || P->bk_blocks) return RSVD_ERR_ARG;
     if (nn_out) *nn_out = P->nn_ctas;
     if (tn_out) *tn_out = P->tn_ctas;
     if (P->dtype != RSVD_F32 || !P->tc || P->l > kSmallMaxF32) return RSVD_OK;  // tunes through lockstep batches (l <= 128)

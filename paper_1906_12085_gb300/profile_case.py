@@ -5,7 +5,9 @@
     python -m paper_1906_12085_gb300.profile_case exact --m 2000 --n 100 --dtype f64
     python -m paper_1906_12085_gb300.profile_case rsvd --m 1048576 --n 4096 --k 96 --p 16 --q 3 --dtype bf16
     python -m paper_1906_12085_gb300.profile_case rsvd --m 1048576 --n 4096 --k 96 --p 16 --q 3 --dtype fp8
+    python -m paper_1906_12085_gb300.profile_case bk --m 1048576 --n 4096 --k 256 --b 96 --iters 2 --repeat 2 --timed 3
 
+`bk` is the block Krylov method (blocks of --b columns, --iters + 1 of them).
 The matrix is seeded Gaussian data made on the device (a kernel's DRAM traffic and
 its launch shape do not depend on the values), so few launches precede the
 library's own.  The solve runs `--repeat` times as direct launches (tracing on,
@@ -25,16 +27,19 @@ import paper_1906_12085_gb300 as g
 
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
-    ap.add_argument("path", choices=["rsvd", "gkl", "exact"])
+    ap.add_argument("path", choices=["rsvd", "gkl", "exact", "bk"])
     ap.add_argument("--m", type=int, default=200000)
     ap.add_argument("--n", type=int, default=1000)
     ap.add_argument("--k", type=int, default=50)
     ap.add_argument("--p", type=int, default=10)
     ap.add_argument("--q", type=int, default=2)
     ap.add_argument("--steps", type=int, default=150)
+    ap.add_argument("--b", type=int, default=96, help="block width (bk)")
+    ap.add_argument("--iters", type=int, default=2, help="Krylov iterations (bk)")
     ap.add_argument("--dtype", choices=["f32", "f64", "bf16", "fp8"], default="f32")
     ap.add_argument("--repeat", type=int, default=1)
-    ap.add_argument("--timed", type=int, default=0, help="then time this many graph-replayed solves (rsvd)")
+    ap.add_argument("--timed", type=int, default=0,
+                    help="then time this many solves (rsvd: graph replays; bk: direct launches)")
     ap.add_argument("--save", default="", help="write the singular values (float64, .npy) to this path")
     a = ap.parse_args(argv)
     dev = torch.device("cuda")
@@ -63,7 +68,11 @@ def main(argv=None) -> int:
     else:
         U = torch.zeros(a.m, k, dtype=tdt, device=dev)
         V = torch.zeros(a.n, k, dtype=tdt, device=dev)
-    with g.rsvd_plan_create(a.m, a.n, k, a.p if a.path == "rsvd" else 0, a.q, dt) as plan:
+    if a.path == "bk":
+        plan = g.rsvd_plan_create_block_krylov(a.m, a.n, k, a.b, a.iters, dt)
+    else:
+        plan = g.rsvd_plan_create(a.m, a.n, k, a.p if a.path == "rsvd" else 0, a.q, dt)
+    with plan:
         g.rsvd_plan_profile(plan, True)
         for rep in range(a.repeat):
             if rep == 1:  # with --repeat > 1 the first solve is a warm-up (module loading, first touch)
@@ -72,6 +81,9 @@ def main(argv=None) -> int:
             if a.path == "rsvd":
                 Om = torch.randn(a.n, a.k + a.p, generator=gen, device=dev, dtype=tdt)
                 g.check(g.rsvd(plan, A, sc, Om, S, U, V), "rsvd")
+            elif a.path == "bk":
+                Om = torch.randn(a.n, a.b, generator=gen, device=dev, dtype=tdt)
+                g.check(g.rsvd_block_krylov(plan, A, Om, S, U, V), "rsvd_block_krylov")
             elif a.path == "gkl":
                 v1 = torch.randn(a.n, generator=gen, device=dev, dtype=tdt)
                 v1 /= v1.norm()
@@ -80,20 +92,31 @@ def main(argv=None) -> int:
                 g.check(g.svd_exact(plan, A, g.RSVD_EXACT_QR_JACOBI, S, U, V), "svd_exact")
         g.check(g.rsvd_plan_sync(plan), "solve status")
         prof = g.rsvd_plan_profile_read(plan)
-        if a.timed and a.path == "rsvd":       # graph-replayed solves, CUDA events on the plan's stream
+        if a.timed and a.path in ("rsvd", "bk"):   # CUDA events on the plan's stream (torch's current one)
             g.rsvd_plan_profile(plan, False)
             s0 = torch.cuda.current_stream()
+
+            def solve():
+                if a.path == "rsvd":
+                    return g.rsvd(plan, A, sc, Om, S, U, V)
+                return g.rsvd_block_krylov(plan, A, Om, S, U, V)
             for _ in range(2):
-                g.check(g.rsvd(plan, A, sc, Om, S, U, V))
+                g.check(solve())
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(s0)
             for _ in range(a.timed):
-                g.check(g.rsvd(plan, A, sc, Om, S, U, V))
+                g.check(solve())
             e1.record(s0)
             torch.cuda.synchronize()
+            g.check(g.rsvd_plan_sync(plan), "timed solves status")
             ms = e0.elapsed_time(e1) / a.timed
-            l = a.k + a.p
-            flops = 2.0 * a.m * a.n * l * (2 * a.q + 2) + 2.0 * a.m * l * l * (a.q + 2) + 2.0 * a.n * l * l
+            if a.path == "rsvd":
+                l = a.k + a.p
+                flops = 2.0 * a.m * a.n * l * (2 * a.q + 2) + 2.0 * a.m * l * l * (a.q + 2) + 2.0 * a.n * l * l
+            else:  # products with A (2 i + 1 of width b, T = A^T Q of width W), QR of the W basis, SVD of T
+                W = (a.iters + 1) * a.b
+                flops = 2.0 * a.m * a.n * a.b * (2 * a.iters + 1) + 2.0 * a.m * a.n * W + 2.0 * a.m * W * W \
+                    + 2.0 * a.n * W * W
             print(f"timed: {ms:.3f} ms per solve, {flops / (ms * 1e-3) / 1e12:.1f} TFLOP/s over {a.timed} solves")
     torch.cuda.synchronize()
     if a.save:

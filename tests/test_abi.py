@@ -63,6 +63,25 @@ def test_plan_create_rejects_unbuilt_dtypes():
         g.RSVD_ERR_UNSUPPORTED
 
 
+@pytest.mark.parametrize("args,want", [
+    ((10, 20, 1, 4, 0, g.RSVD_F32), g.RSVD_ERR_ARG),        # m < n
+    ((100, 20, 0, 4, 1, g.RSVD_F32), g.RSVD_ERR_ARG),       # k < 1
+    ((100, 20, 4, 0, 1, g.RSVD_F32), g.RSVD_ERR_ARG),       # b < 1
+    ((100, 20, 4, 4, -1, g.RSVD_F32), g.RSVD_ERR_ARG),      # iters < 0
+    ((100, 20, 13, 4, 2, g.RSVD_F32), g.RSVD_ERR_ARG),      # k > W = (iters + 1) b
+    ((100, 20, 4, 8, 2, g.RSVD_F32), g.RSVD_ERR_ARG),       # W > n
+    ((1000, 512, 8, 120, 0, g.RSVD_F32), g.RSVD_ERR_UNSUPPORTED),   # block Gram beyond one CTA (b > 112)
+    ((1000, 512, 100, 100, 2, g.RSVD_F32), g.RSVD_ERR_UNSUPPORTED),  # W = 300 > 288
+    ((1000, 512, 8, 60, 1, g.RSVD_F64), g.RSVD_ERR_UNSUPPORTED),    # float64: W = 120 > 112
+    ((1000, 512, 8, 16, 1, g.RSVD_BF16), g.RSVD_ERR_UNSUPPORTED),   # float32 / float64 only
+])
+def test_block_krylov_plan_rejects_bad_sizes(args, want):
+    h = ctypes.c_void_p(12345)
+    assert g.lib().rsvd_plan_create_block_krylov(ctypes.byref(h), *args, None) == want
+    assert h.value is None
+    assert g.lib().rsvd_block_krylov(None, None, None, None, None, None) == g.RSVD_ERR_ARG
+
+
 def test_null_plan_arguments():
     L = g.lib()
     assert L.rsvd_plan_destroy(None) == g.RSVD_OK
