@@ -176,3 +176,15 @@ def test_block_krylov_plan_rules():
         assert g.rsvd_autotune(plan, A, Om, 1)[0] == g.RSVD_ERR_ARG
         g.check(g.rsvd_block_krylov(plan, A, Om, S, U, V), "rsvd_block_krylov")
         assert g.rsvd_plan_sync(plan) == g.RSVD_OK
+
+
+def test_block_krylov_f32_power15_spectrum_w288():
+    """sigma_i = i^-1.5 (the survey's precision-form spectrum), b = 96, i = 2, k = 256."""
+    m, n, k, b, iters = 20000, 2048, 256, 96, 2
+    A32 = synth.prescribed(m, n, synth.spectrum_power(n, 1.5), 40961, 40962).float()
+    Om = synth.gaussian(n, b, seed=40965, dtype=torch.float32)
+    r = _run_bk(A32, Om, k, b, iters, g.RSVD_F32)
+    assert r["status"] == g.RSVD_OK
+    Ac, _, _ = oracle.center(A32.double())
+    s, _, _ = oracle.block_krylov(Ac, Om.double(), iters, k)
+    assert np.abs(r["S"] - s).max() <= 1e-5 * s[0]

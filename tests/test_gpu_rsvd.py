@@ -215,3 +215,17 @@ def test_rsvd_f32_full_workload_matches_oracle():
     sep = _gaps(s) >= 2e-2
     assert np.abs(Vg[:, sep] - Vo[:, sep]).max() <= 2e-3
     assert K == oracle.pca_threshold(s, fro2, 0.9)[0]
+
+
+@pytest.mark.parametrize("q", [1, 3])
+def test_rsvd_f32_power15_spectrum_l288(q):
+    """The survey's precision-form spectrum sigma_i = i^-1.5 at l = 288 (reduced m, n): the
+    float32 path's CholeskyQR2 of T still resolves it (cond(T) ~ 288^1.5)."""
+    m, n, k, p = 20000, 2048, 256, 32
+    A32 = synth.prescribed(m, n, synth.spectrum_power(n, 1.5), 40961, 40962).float()
+    Om = synth.gaussian(n, k + p, seed=40964, dtype=torch.float32)
+    r = _run_rsvd(A32, Om, k, p, q, g.RSVD_F32)
+    assert r["status"] == g.RSVD_OK
+    Ac, _, _ = oracle.center(A32.double())
+    s, _, _ = oracle.rsvd(Ac, Om.double(), q=q, k=k)
+    assert np.abs(r["S"] - s).max() <= 1e-5 * s[0]
