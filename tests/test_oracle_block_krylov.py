@@ -12,7 +12,11 @@ Each check is fixed by mathematics, not by re-running the oracle's own steps:
     triplets, and U, V have orthonormal columns;
   * the paper's chain printed without re-orthonormalisation spans the same space
     (numpy, small i where it is still well conditioned);
-  * a prescribed spectrum is recovered with few iterations."""
+  * a prescribed spectrum is recovered with few iterations;
+  * the block-by-block basis the library builds (each block A A^T applied to the
+    previous orthonormalised block, projected against the earlier blocks, then
+    orthonormalised) spans the same Krylov space, so its Ritz values agree with
+    the step list's (float64 restatement, well-conditioned sizes)."""
 import numpy as np
 import pytest
 
@@ -97,3 +101,27 @@ def test_argument_checks():
         oracle.block_krylov(A, np.zeros((20, 8)), iters=2, k=4)   # (iters + 1) l = 24 > n
     with pytest.raises(oracle.OracleError):
         oracle.block_krylov(A, np.zeros((20, 4)), iters=1, k=9)   # k > (iters + 1) l
+
+
+@pytest.mark.parametrize("iters,b", [(1, 6), (2, 8), (3, 5)])
+def test_block_by_block_basis_spans_the_same_space(iters, b):
+    """span{Q_0, ..., Q_j} = span{H(0), ..., H(j)} with Q_j the part of A A^T Q_{j-1}
+    orthogonal to Q_0..Q_{j-1}: by induction, since A A^T maps the first j blocks'
+    span into the first j + 1 blocks' span.  The Ritz values of the two bases agree."""
+    rng = np.random.default_rng(40 + iters)
+    m, n = 400, 60
+    A = _matrix(m, n, 1.0 / np.arange(1, n + 1) ** 0.7, seed=31 + iters)
+    Om = rng.standard_normal((n, b))
+    k = (iters + 1) * b
+    s_or, _, _ = oracle.block_krylov(A, Om, iters, k)
+    Q = [np.linalg.qr(A @ Om)[0]]
+    for _ in range(iters):
+        H = np.concatenate(Q, axis=1)
+        X = A @ (A.T @ Q[-1])
+        for _ in range(2):                       # block classical Gram-Schmidt, twice
+            X = X - H @ (H.T @ X)
+        Q.append(np.linalg.qr(X)[0])
+    H = np.concatenate(Q, axis=1)
+    assert np.abs(H.T @ H - np.eye(k)).max() < 1e-12
+    s_bb = np.linalg.svd(A.T @ H, compute_uv=False)
+    assert np.abs(s_bb - s_or).max() < 1e-10 * s_or[0]
