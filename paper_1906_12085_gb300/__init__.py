@@ -197,6 +197,22 @@ class Plan:
         self.close()
 
 
+class BlockKrylovPlan(Plan):
+    """Plan of the block Krylov method: blocks of b columns, iters + 1 of them (W = (iters + 1) b)."""
+
+    def __init__(self, handle: int, m, n, k, b, iters, dtype):
+        super().__init__(handle, m, n, k, 0, iters, dtype)
+        self.b, self.iters = b, iters
+
+    @property
+    def l(self):
+        return self.b
+
+    @property
+    def W(self):
+        return (self.iters + 1) * self.b
+
+
 def rsvd_plan_create(m: int, n: int, k: int, p: int, q: int, dtype: int = RSVD_F32, stream=None) -> Plan:
     h = ctypes.c_void_p()
     st = lib().rsvd_plan_create(ctypes.byref(h), m, n, k, p, q, dtype, _stream(stream))
@@ -231,9 +247,7 @@ def rsvd_plan_create_block_krylov(m: int, n: int, k: int, b: int, iters: int, dt
     h = ctypes.c_void_p()
     st = lib().rsvd_plan_create_block_krylov(ctypes.byref(h), m, n, k, b, iters, dtype, _stream(stream))
     check(st, "rsvd_plan_create_block_krylov")
-    plan = Plan(h.value, m, n, k, 0, iters, dtype)
-    plan.b, plan.iters = b, iters
-    return plan
+    return BlockKrylovPlan(h.value, m, n, k, b, iters, dtype)
 
 
 def rsvd_block_krylov(plan: Plan, A, Omega, S, U, V) -> int:
