@@ -25,6 +25,16 @@ def test_library_exports_every_header_function():
     assert set(names) <= exported
 
 
+def test_binding_covers_every_header_function():
+    """The Python layer keeps the C names: one callable per declared function, and every
+    library symbol has its argument types declared (no implicit int conversions)."""
+    names = g.header_functions()
+    assert [n for n in names if not callable(getattr(g, n, None))] == []
+    L = g.lib()
+    assert [n for n in names if getattr(getattr(L, n), "argtypes", None) is None] == []
+    assert set(names) <= set(g.__all__)
+
+
 def test_library_has_no_oracle_dependency():
     """The product library links neither the oracle library nor any of its symbols."""
     out = subprocess.run(["nm", "-D", g.library_path()], capture_output=True, text=True).stdout
