@@ -179,7 +179,7 @@ def test_block_krylov_plan_rules():
 
 
 def test_block_krylov_f32_power15_spectrum_w288():
-    """sigma_i = i^-1.5 (the survey's precision-form spectrum), b = 96, i = 2, k = 256."""
+    """sigma_i = i^-1.5 (the precision-form workload's spectrum), b = 96, i = 2, k = 256."""
     m, n, k, b, iters = 20000, 2048, 256, 96, 2
     A32 = synth.prescribed(m, n, synth.spectrum_power(n, 1.5), 40961, 40962).float()
     Om = synth.gaussian(n, b, seed=40965, dtype=torch.float32)

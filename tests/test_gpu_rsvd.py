@@ -219,7 +219,7 @@ def test_rsvd_f32_full_workload_matches_oracle():
 
 @pytest.mark.parametrize("q", [1, 3])
 def test_rsvd_f32_power15_spectrum_l288(q):
-    """The survey's precision-form spectrum sigma_i = i^-1.5 at l = 288 (reduced m, n): the
+    """The precision-form workload's spectrum sigma_i = i^-1.5 at l = 288 (reduced m, n): the
     float32 path's CholeskyQR2 of T still resolves it (cond(T) ~ 288^1.5)."""
     m, n, k, p = 20000, 2048, 256, 32
     A32 = synth.prescribed(m, n, synth.spectrum_power(n, 1.5), 40961, 40962).float()
