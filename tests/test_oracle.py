@@ -281,3 +281,18 @@ def test_pca_threshold_closed_forms():
     # equality counts as reached (>= in Sec. 2.4)
     K, ok = oracle.pca_threshold(np.array([1.0, 1.0]), 2.0, 0.5)
     assert ok and K == 1
+
+
+@pytest.mark.parametrize("m,n", [(2000, 100), (4000, 300)])
+def test_gram_route_on_the_papers_gaussian_matrices(m, n):
+    """Sec. 4's experiment: A with N(0,1) entries, all n triplets by the Gram route
+    ("truncated SVD" at k = n).  The residual delta = ||A - U S V^T||_F / ||A||_F is at
+    rounding level (cond(A) is about (sqrt m + sqrt n) / (sqrt m - sqrt n) < 2, so forming
+    A^T A loses nothing), and the extreme singular values sit at the Marchenko-Pastur
+    edges sqrt(m) +- sqrt(n) (to a few percent at these sizes)."""
+    A = synth.gaussian(m, n, seed=1906 + n).numpy()
+    s, U, V = oracle.svd_gram(A)
+    delta = np.linalg.norm(A - (U * s) @ V.T) / np.linalg.norm(A)
+    assert delta < 1e-13
+    assert 0.97 < s[0] / (math.sqrt(m) + math.sqrt(n)) < 1.03
+    assert 0.95 < s[-1] / (math.sqrt(m) - math.sqrt(n)) < 1.05
