@@ -204,6 +204,10 @@ cudaError_t sv_refine_batched(const JacTab *tab, int count, int l, int lp, cudaS
 // Cyclic (parallel-ordered) two-sided Jacobi eigen-decomposition of the n x n
 // symmetric float64 matrix G (ld n): lam descending (n doubles), V (n x n, ld n).
 cudaError_t jacobi_eig(const double *G, int n, double *lam, double *V, int *status, cudaStream_t s);
+// The same in float32 arithmetic (inputs and outputs float64), rotating a pair only when
+// |g_pq| also exceeds floor_rel * max_i g_ii (n <= 112).
+cudaError_t jacobi_eig_f32(const double *G, int n, double *lam, double *V, int *status, cudaStream_t s,
+                           double floor_rel);
 
 // Vs[:, i] = V[:, i] / sigma_i (zero column when sigma_i <= n eps sigma_1), sigma_i = sqrt(max(lam_i,0)).
 template <typename T>

@@ -702,25 +702,38 @@ __global__ void sv_refine_batch_kernel(const JacTab *__restrict__ tab, int l, in
 }
 
 // ------------------------------------------------------------ two-sided Jacobi
+// Arithmetic in Tm (float64 for the Gram route; float32 for the block Gram matrices of
+// SVQB).  A pair is rotated when |g_pq| > rel sqrt(|g_pp g_qq|) and |g_pq| > floor_rel *
+// max_i g_ii: the floor (0 for the Gram route) stops rotations among directions far
+// below what the caller resolves, which a relative test alone never finishes in float32.
+template <typename Tm>
 __global__ void __launch_bounds__(1024) jacobi_eig_kernel(const double *__restrict__ G, int n,
                                                           double *__restrict__ lam, double *__restrict__ Vout,
-                                                          int *__restrict__ status, int max_sweeps) {
+                                                          int *__restrict__ status, int max_sweeps,
+                                                          double floor_rel) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int L = n + (n & 1);
-    double *M = reinterpret_cast<double *>(smraw);  // n x n, row-major
-    double *Vt = M + n * n;                         // Vt[p * n + i] = V[i][p]
-    double *cs = Vt + n * n;                        // per pair: c, s
-    int *pq = reinterpret_cast<int *>(cs + L);      // per pair: p, q (or -1)
+    Tm *M = reinterpret_cast<Tm *>(smraw);  // n x n, row-major
+    Tm *Vt = M + n * n;                     // Vt[p * n + i] = V[i][p]
+    Tm *cs = Vt + n * n;                    // per pair: c, s
+    int *pq = reinterpret_cast<int *>(cs + L + (L & 1));  // per pair: p, q (or -1)
     int *perm = pq + L;
     __shared__ int rotated;
+    __shared__ Tm floor_s;
     const int tid = threadIdx.x, nt = blockDim.x, np = L / 2;
     for (int idx = tid; idx < n * n; idx += nt) {
-        M[idx] = G[idx];
-        Vt[idx] = (idx / n == idx % n) ? 1.0 : 0.0;
+        M[idx] = (Tm)G[idx];
+        Vt[idx] = (idx / n == idx % n) ? Tm(1) : Tm(0);
     }
-    const double rel = 1e-15;
+    const Tm rel = sizeof(Tm) == 8 ? Tm(1e-15) : (Tm)(sqrt((double)n) * FLT_EPSILON);
+    if (tid == 0) {
+        double dmax = 0.0;
+        for (int i = 0; i < n; i++) dmax = fmax(dmax, G[(int64_t)i * n + i]);
+        floor_s = (Tm)(floor_rel * dmax);
+    }
     bool converged = false;
     __syncthreads();
+    const Tm floor_v = floor_s;
     for (int sweep = 0; sweep < max_sweeps; sweep++) {
         if (tid == 0) rotated = 0;
         __syncthreads();
@@ -728,13 +741,13 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(const double *__restri
             for (int pr = tid; pr < np; pr += nt) {
                 const int a = rr_pos(pr, r, L), b = rr_pos(L - 1 - pr, r, L);
                 int p = min(a, b), q = max(a, b);
-                double c = 1.0, s = 0.0;
+                Tm c = 1, s = 0;
                 if (q < n) {
-                    const double apq = M[p * n + q], app = M[p * n + p], aqq = M[q * n + q];
-                    if (apq != 0.0 && fabs(apq) > rel * sqrt(fabs(app * aqq))) {
-                        const double theta = (aqq - app) / (2.0 * apq);
-                        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(1.0 + theta * theta));
-                        c = 1.0 / sqrt(1.0 + t * t);
+                    const Tm apq = M[p * n + q], app = M[p * n + p], aqq = M[q * n + q];
+                    if (apq != Tm(0) && fabs(apq) > rel * sqrt(fabs(app * aqq)) && fabs(apq) > floor_v) {
+                        const Tm theta = (aqq - app) / (Tm(2) * apq);
+                        const Tm t = (theta >= Tm(0) ? Tm(1) : Tm(-1)) / (fabs(theta) + sqrt(Tm(1) + theta * theta));
+                        c = Tm(1) / sqrt(Tm(1) + t * t);
                         s = t * c;
                         rotated = 1;
                     } else {
@@ -754,11 +767,11 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(const double *__restri
                 const int pr = idx / n, i = idx % n, p = pq[2 * pr];
                 if (p < 0) continue;
                 const int q = pq[2 * pr + 1];
-                const double c = cs[2 * pr], s = cs[2 * pr + 1];
-                const double x = M[i * n + p], y = M[i * n + q];
+                const Tm c = cs[2 * pr], s = cs[2 * pr + 1];
+                const Tm x = M[i * n + p], y = M[i * n + q];
                 M[i * n + p] = c * x - s * y;
                 M[i * n + q] = s * x + c * y;
-                const double vx = Vt[p * n + i], vy = Vt[q * n + i];
+                const Tm vx = Vt[p * n + i], vy = Vt[q * n + i];
                 Vt[p * n + i] = c * vx - s * vy;
                 Vt[q * n + i] = s * vx + c * vy;
             }
@@ -768,8 +781,8 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(const double *__restri
                 const int pr = idx / n, j = idx % n, p = pq[2 * pr];
                 if (p < 0) continue;
                 const int q = pq[2 * pr + 1];
-                const double c = cs[2 * pr], s = cs[2 * pr + 1];
-                const double x = M[p * n + j], y = M[q * n + j];
+                const Tm c = cs[2 * pr], s = cs[2 * pr + 1];
+                const Tm x = M[p * n + j], y = M[q * n + j];
                 M[p * n + j] = c * x - s * y;
                 M[q * n + j] = s * x + c * y;
             }
@@ -778,8 +791,8 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(const double *__restri
                 const int p = pq[2 * pr];
                 if (p < 0) continue;
                 const int q = pq[2 * pr + 1];
-                M[p * n + q] = 0.0;
-                M[q * n + p] = 0.0;
+                M[p * n + q] = Tm(0);
+                M[q * n + p] = Tm(0);
             }
             __syncthreads();
         }
@@ -798,10 +811,10 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(const double *__restri
         }
     }
     __syncthreads();
-    for (int o = tid; o < n; o += nt) lam[o] = M[perm[o] * n + perm[o]];
+    for (int o = tid; o < n; o += nt) lam[o] = (double)M[perm[o] * n + perm[o]];
     for (int idx = tid; idx < n * n; idx += nt) {
         const int i = idx / n, o = idx % n;
-        Vout[idx] = Vt[perm[o] * n + i];
+        Vout[idx] = (double)Vt[perm[o] * n + i];
     }
 }
 
@@ -1104,13 +1117,24 @@ template cudaError_t chol_inv_batched<double, double, double>(const CholTab *, i
 template cudaError_t sv_refine<double>(const double *, int, int, const double *, const double *, double *,
                                        cudaStream_t);
 
-cudaError_t jacobi_eig(const double *G, int n, double *lam, double *V, int *status, cudaStream_t s) {
+template <typename Tm>
+cudaError_t jacobi_eig_t(const double *G, int n, double *lam, double *V, int *status, cudaStream_t s,
+                         double floor_rel) {
     const int L = n + (n & 1);
-    const size_t smem = sizeof(double) * (2 * (size_t)n * n + L) + sizeof(int) * (2 * L) + 16;
-    cudaFuncSetAttribute(jacobi_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    jacobi_eig_kernel<<<1, 1024, smem, s>>>(G, n, lam, V, status, 50);
+    const size_t smem = sizeof(Tm) * (2 * (size_t)n * n + L + (L & 1)) + sizeof(int) * (2 * L) + 16;
+    cudaFuncSetAttribute(jacobi_eig_kernel<Tm>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    jacobi_eig_kernel<Tm><<<1, 1024, smem, s>>>(G, n, lam, V, status, 50, floor_rel);
     note_launch();
     return cudaGetLastError();
+}
+
+cudaError_t jacobi_eig(const double *G, int n, double *lam, double *V, int *status, cudaStream_t s) {
+    return jacobi_eig_t<double>(G, n, lam, V, status, s, 0.0);
+}
+
+cudaError_t jacobi_eig_f32(const double *G, int n, double *lam, double *V, int *status, cudaStream_t s,
+                           double floor_rel) {
+    return jacobi_eig_t<float>(G, n, lam, V, status, s, floor_rel);
 }
 
 template <typename T>

@@ -542,7 +542,11 @@ rsvd_status run_block_krylov(rsvd_plan *P, T *A, const T *Omega, double *S, T *U
     auto svqb = [&](const T *X, T *Out, uint64_t sd) -> cudaError_t {
         cudaError_t e = prod_tn<T>(P, m, lp, X, lp, X, lp, G, lp);                   // the full Gram matrix
         if (e == cudaSuccess) e = copy2d<T, double>(G, lp, P->G64, b, b, b, b, s);
-        if (e == cudaSuccess) e = jacobi_eig(P->G64, b, P->lam, P->Vfull, P->status, s);
+        // float32 plans: float32 Jacobi that leaves pairs below 2^-30 max_i g_ii alone, far below
+        // the 2u lam_1 refill threshold (the float64 one in one CTA took ~14 ms per 96 x 96 block)
+        if (e == cudaSuccess)
+            e = sizeof(T) == 4 ? jacobi_eig_f32(P->G64, b, P->lam, P->Vfull, P->status, s, 0x1.0p-30)
+                               : jacobi_eig(P->G64, b, P->lam, P->Vfull, P->status, s);
         if (e == cudaSuccess) e = svqb_scale<T>(P->lam, P->Vfull, b, lp, tau, M, P->bk_flag, s);
         if (e == cudaSuccess) e = prod_nn<T>(P, m, lp, X, lp, M, lp, Out, lp);
         if (e == cudaSuccess) e = bk_fill<T>(Out, m, b, lp, P->bk_flag, sd, s);
