@@ -55,12 +55,17 @@ typedef enum {
     RSVD_OK = 0,
     RSVD_ERR_ARG = -1,          /* invalid argument (sizes, NULL pointers, method)     */
     RSVD_ERR_OOM = -2,          /* device workspace allocation failed                  */
-    RSVD_ERR_CHOL = -3,         /* Cholesky breakdown even after the shifted retry     */
+    RSVD_ERR_CHOL = -3,         /* Cholesky breakdown even after the shifted retry, or a
+                                   final basis that failed its orthonormality check     */
     RSVD_ERR_NOCONV = -4,       /* a Jacobi solver hit its sweep cap                   */
-    RSVD_ERR_TIMEOUT = -5,      /* reserved for bounded device waits                   */
+    RSVD_ERR_TIMEOUT = -5,      /* a bounded device wait gave up (a product pipeline)  */
     RSVD_ERR_CUDA = -6,         /* a CUDA runtime call or kernel launch failed         */
     RSVD_ERR_UNSUPPORTED = -8,  /* size or dtype outside what this build implements    */
-    RSVD_WARN_K_GT_k = 1        /* the threshold t is not reached within the k values  */
+    RSVD_WARN_K_GT_k = 1,       /* the threshold t is not reached within the k values  */
+    RSVD_WARN_RANK_DEFICIENT = 2 /* numerically rank-deficient input: a basis Cholesky
+                                   needed its shift or removed dependent columns, or a
+                                   Gram-route sigma_i fell to ~0; results are valid and
+                                   the bases passed their orthonormality check          */
 } rsvd_status;
 
 /* svd_exact methods */
@@ -101,7 +106,8 @@ size_t rsvd_plan_workspace_bytes(rsvd_plan_t plan);
 rsvd_status rsvd_plan_set_flags(rsvd_plan_t plan, unsigned flags);
 
 /* Wait for the plan's stream; return the device status of the last solve
- * (RSVD_OK, RSVD_ERR_CHOL, RSVD_ERR_NOCONV, or RSVD_ERR_CUDA) and clear it. */
+ * (RSVD_OK, RSVD_WARN_RANK_DEFICIENT, RSVD_ERR_CHOL, RSVD_ERR_NOCONV, RSVD_ERR_TIMEOUT or
+ * RSVD_ERR_CUDA; errors take precedence over the warning) and clear it. */
 rsvd_status rsvd_plan_sync(rsvd_plan_t plan);
 
 /*
@@ -111,7 +117,20 @@ rsvd_status rsvd_plan_sync(rsvd_plan_t plan);
  *   repeat q times: Z = A^T Q, Q_Z = orth(Z), Y = A Q_Z, Q = orth(Y);
  *   T = A^T Q (= B^T with B = Q^T A);  T = Vt Sigma W^T;  U = Q W.
  * orth() is CholeskyQR2 (R_ii > 0), which in exact arithmetic equals the
- * Householder QR the step list names.
+ * Householder QR the step list names.  Bases stored in float32 (every dtype but
+ * RSVD_F64) factor their float32 Gram matrix first; when that Cholesky breaks
+ * down (a basis with condition number beyond ~1e4, as steep spectra and power
+ * steps produce), the Gram matrix is formed again from the float32 basis with
+ * float64 products and sums and factored in float64, so every direction the
+ * float32 basis resolves is kept; exactly dependent columns (rank(A) < l) then
+ * take the shift 11 (rows l + l(l+1)) u tr(G) of shifted CholeskyQR in float64.
+ * Float64 bases remove a column whose Cholesky pivot is below l u of its squared
+ * norm (it lies in the span of the columns before it) and replace it by a
+ * pseudo-random column that the next pass orthonormalises.  Both are reported as
+ * RSVD_WARN_RANK_DEFICIENT.  After the last CholeskyQR2 of Q and of T's factor
+ * Q_T, max |Q^T Q - I| is checked on the device against 2e-5 (float32 bases) or
+ * 1e-12 (float64); a basis beyond it makes the solve RSVD_ERR_CHOL, never a
+ * silent result.
  *   A      : m x n, row-major, read only (centred on the fly).
  *   col_scales : n floats (device) for RSVD_FP8_E4M3 plans, NULL otherwise.
  * RSVD_BF16 plans (n a multiple of 8, l <= 288) solve for the stored bfloat16
@@ -245,6 +264,16 @@ rsvd_status pca_threshold(rsvd_plan_t plan, double t, int *K);
  */
 rsvd_status svd_exact_gram_static(void *A, int64_t m, int64_t n, rsvd_dtype dtype, double *S, void *U, void *V,
                                   void *cuda_stream);
+
+/*
+ * Process-wide cap on the sweeps of the Jacobi solvers (the one-sided SVD of R and
+ * of the Lanczos bidiagonal, the two-sided eigen-decompositions of the Gram route
+ * and of block Krylov's SVQB); cap 0 restores the defaults (40 and 50 sweeps).  A
+ * solver that reaches the cap before a sweep without rotations sets
+ * RSVD_ERR_NOCONV.  Applies to launches issued afterwards: a CUDA graph a plan
+ * captured earlier keeps the cap it was captured with.  RSVD_ERR_ARG for cap < 0.
+ */
+rsvd_status rsvd_set_jacobi_sweep_cap(int cap);
 
 /* Host copy of ||A||_F^2 (after centring) recorded by the last solve; synchronises. */
 rsvd_status rsvd_plan_fro2(rsvd_plan_t plan, double *fro2);

@@ -17,7 +17,7 @@ import re
 __all__ = [
     "RSVD_F64", "RSVD_F32", "RSVD_BF16", "RSVD_FP8_E4M3",
     "RSVD_OK", "RSVD_ERR_ARG", "RSVD_ERR_OOM", "RSVD_ERR_CHOL", "RSVD_ERR_NOCONV", "RSVD_ERR_TIMEOUT",
-    "RSVD_ERR_CUDA", "RSVD_ERR_UNSUPPORTED", "RSVD_WARN_K_GT_k", "RSVD_EXACT_GRAM", "RSVD_EXACT_QR_JACOBI",
+    "RSVD_ERR_CUDA", "RSVD_ERR_UNSUPPORTED", "RSVD_WARN_K_GT_k", "RSVD_WARN_RANK_DEFICIENT", "RSVD_EXACT_GRAM", "RSVD_EXACT_QR_JACOBI",
     "RSVD_FLAG_NO_CENTER", "RsvdError", "lib", "library_path", "header_functions",
     "rsvd_plan_create", "rsvd_plan_destroy", "rsvd_plan_workspace_bytes", "rsvd_plan_set_flags",
     "rsvd_plan_sync", "rsvd", "svd_exact", "svd_truncated_krylov", "pca_threshold", "rsvd_plan_fro2",
@@ -27,6 +27,7 @@ __all__ = [
     "rsvd_batch_destroy", "Server", "rsvd_server_create", "rsvd_server_submit", "rsvd_server_poll",
     "rsvd_server_pending", "rsvd_server_destroy", "rsvd_autotune", "rsvd_tune_lookup", "rsvd_tune_clear",
     "rsvd_quantize", "rsvd_server_submit_ex", "rsvd_plan_create_block_krylov", "rsvd_block_krylov",
+    "rsvd_set_jacobi_sweep_cap",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -36,6 +37,7 @@ HEADER = os.path.join(ROOT, "include", "rsvd.h")
 RSVD_F64, RSVD_F32, RSVD_BF16, RSVD_FP8_E4M3 = 0, 1, 2, 3
 RSVD_OK, RSVD_ERR_ARG, RSVD_ERR_OOM, RSVD_ERR_CHOL, RSVD_ERR_NOCONV = 0, -1, -2, -3, -4
 RSVD_ERR_TIMEOUT, RSVD_ERR_CUDA, RSVD_ERR_UNSUPPORTED, RSVD_WARN_K_GT_k = -5, -6, -8, 1
+RSVD_WARN_RANK_DEFICIENT = 2
 RSVD_EXACT_GRAM, RSVD_EXACT_QR_JACOBI = 0, 1
 RSVD_FLAG_NO_CENTER = 1
 RSVD_BATCH_MAX = 256
@@ -115,13 +117,14 @@ def lib() -> ctypes.CDLL:
     L.rsvd_plan_create_block_krylov.argtypes = [ctypes.POINTER(vp), i64, i64, i32, i32, i32, i32, vp]
     L.rsvd_block_krylov.argtypes = [vp, vp, vp, vp, vp, vp]
     L.rsvd_tune_clear.restype = None
+    L.rsvd_set_jacobi_sweep_cap.argtypes = [i32]
     for f in ("rsvd_plan_create", "rsvd_plan_destroy", "rsvd_plan_set_flags", "rsvd_plan_sync", "rsvd",
               "svd_exact", "svd_truncated_krylov", "pca_threshold", "rsvd_plan_fro2", "rsvd_plan_profile",
               "rsvd_plan_profile_read", "rsvd_workspace_query", "rsvd_plan_create_in", "rsvd_batch_create",
               "rsvd_batch_run", "rsvd_batch_sync", "rsvd_batch_destroy", "rsvd_server_create",
               "rsvd_server_submit", "rsvd_server_poll", "rsvd_server_pending", "rsvd_server_destroy",
               "rsvd_autotune", "rsvd_tune_lookup", "rsvd_quantize", "rsvd_server_submit_ex",
-              "rsvd_plan_create_block_krylov", "rsvd_block_krylov"):
+              "rsvd_plan_create_block_krylov", "rsvd_block_krylov", "rsvd_set_jacobi_sweep_cap"):
         getattr(L, f).restype = i32
     _lib = L
     return L
@@ -134,6 +137,11 @@ def header_functions() -> list[str]:
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b([a-z_][a-z0-9_]*)\s*\(", text)) -
                   {"if", "while", "for", "sizeof", "return", "defined"})
+
+
+def rsvd_set_jacobi_sweep_cap(cap: int) -> int:
+    """Process-wide Jacobi sweep cap (0 restores the defaults)."""
+    return lib().rsvd_set_jacobi_sweep_cap(int(cap))
 
 
 def rsvd_status_string(status: int) -> str:

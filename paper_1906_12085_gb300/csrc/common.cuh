@@ -12,10 +12,18 @@ namespace gbr {
 enum StatusBits : int {
     ST_CHOL = 1,      // Cholesky breakdown after the shifted retry
     ST_NOCONV = 2,    // Jacobi sweep cap reached
-    ST_SHIFT = 4,     // shifted Cholesky was needed (informational)
-    ST_RANKDEF = 8,   // a singular value fell below n*eps*sigma_1 (informational)
+    ST_SHIFT = 4,     // shifted Cholesky was needed (warning: rank deficient)
+    ST_RANKDEF = 8,   // a singular value fell below n*eps*sigma_1, or a float64 basis column
+                      // was removed and refilled (warning: rank deficient)
     ST_TIMEOUT = 16,  // a bounded device wait gave up (pipeline stalled)
+    ST_ORTH = 32,     // a final basis failed the orthonormality check max|Q^T Q - I| <= tol
 };
+
+// Orthonormality bound of the final bases (max |Q^T Q - I|, checked on the device after the
+// last CholeskyQR2): float32 bases 2e-5 (a basis this close to orthonormal moves no Ritz
+// value by more than ~1e-5 relative), float64 bases 1e-12.
+constexpr double kOrthTolF32 = 2e-5;
+constexpr double kOrthTolF64 = 1e-12;
 
 // Largest l (or n for svd_exact) whose l x l working set fits one CTA's shared memory.
 constexpr int kSmallMaxF64 = 112;
@@ -88,16 +96,76 @@ int64_t gemm_tn_partials(int64_t rows, int64_t N, int64_t L);
 // ---------------------------------------------------------- small dense
 // Upper Cholesky R^T R = G (+ shift) of the leading l x l block of G (ldg), then
 // R^{-1}, arithmetic in Tk.  Writes R, Rinv (float64, l x l dense, ld l) and
-// Rinv_c (element type Tc, lp x lp, zero padded).  On a non-positive pivot
-// retries once with the shift 11 (rows*l + l(l+1)) u tr(G) (shifted
-// CholeskyQR); on a second breakdown sets ST_CHOL and returns R = 0, R^{-1} = I.
+// Rinv_c (element type Tc, lp x lp, zero padded).  The role selects what a
+// breakdown (a pivot that is not positive and finite) does:
+//   kCholPlain    : retry once with the shift 11 (rows*l + l(l+1)) u tr(G) (shifted
+//                   CholeskyQR, ST_SHIFT); on a second breakdown set ST_CHOL and return
+//                   R = 0, R^{-1} = I;
+//   kCholFirst    : a float64 fallback follows: write *fb = 1 and leave R, Rinv and
+//                   Rinv_c to it; on success write *fb = 0;
+//   kCholFallback : return at once unless *fb is set; otherwise as kCholPlain (G is then
+//                   the float64 Gram matrix of gram64_fb);
+//   kCholDeflate  : never shift: a pivot <= kDeflateRel l G_kk (G_kk the diagonal of G)
+//                   removes column k -- R_kk = 1, the rest of row and column k of R zero --
+//                   and sets fb[k] = 1 (fb: l ints, cleared first); X R^{-1} then keeps
+//                   column k of X, which the caller replaces (float64 bases).
 // Matrices whose two l x l blocks exceed one SM's shared memory (l > 112 in float64,
 // l > 128 in float32) live in `scratch` (chol_scratch_bytes(l, sizeof(Tk)) bytes of
 // device memory), which may be NULL otherwise.
+enum CholRole : int { kCholPlain = 0, kCholFirst = 1, kCholFallback = 2, kCholDeflate = 3 };
+// relative pivot below which kCholDeflate removes a column, per column of the block: the
+// float64 unit roundoff, i.e. a column whose squared distance from the span of the previous
+// ones is below l u of its squared norm, the rounding level of its float64 Gram matrix
+constexpr double kDeflateRel = 0x1.0p-53;
 template <typename TG, typename Tk, typename Tc>
 cudaError_t chol_inv(const TG *G, int64_t ldg, int l, int64_t rows, double unit_roundoff, double *R,
-                     double *Rinv, Tc *Rinv_c, int lp, int *status, cudaStream_t s, void *scratch = nullptr);
+                     double *Rinv, Tc *Rinv_c, int lp, int *status, cudaStream_t s, void *scratch = nullptr,
+                     int *fb = nullptr, int role = kCholPlain);
 size_t chol_scratch_bytes(int l, size_t tk);
+
+// The fallback of CholeskyQR after a breakdown of the float32 Gram matrix, one launch: the
+// float64 Gram matrix G (l x l upper triangle, ldg) = X^T X of X rows x l (ld, float32), every
+// product and sum in float64 (CUDA cores), split over row chunks into `part`
+// (gram64_partials(rows, l) doubles) and summed in chunk order by the last CTA (`count`: a
+// zeroed counter of the job, left zero), which then factors G as chol_inv does with role
+// kCholFallback (R, Rinv, Rc, lp, status, shift coefficient `coef`), its matrices in the
+// global scratch gws (chol_scratch_bytes(l, 8) bytes).  Returns at once unless *fb is set.
+struct G64Job {
+    const float *X;
+    int64_t rows, ld;
+    double *part, *G;
+    const int *fb;
+    unsigned *count;
+    double coef;
+    double *R, *Rinv;
+    float *Rc;
+    int lp;
+    int *status;
+    double *gws;
+};
+int64_t gram64_partials(int64_t rows, int l);
+cudaError_t gram64_fb(const G64Job &job, int l, int64_t ldg, cudaStream_t s);
+// the same for `count` jobs of one l (device table, one launch)
+cudaError_t gram64_fb_batched(const G64Job *tab, int count, int64_t max_rows, int l, int64_t ldg, cudaStream_t s);
+// The basis of a fallback pass: Q (rows x l, ld, float32) = X R^{-1} with float64 products and
+// sums (Rinv: float64 l x l upper triangular, ld l), rounded once; returns at once unless
+// *fb is set.  X and Q must not overlap.
+struct Rinv64Job {
+    const float *X;
+    int64_t rows, ld;
+    const double *Rinv;
+    float *Q;
+    const int *fb;
+};
+cudaError_t rinv64_fb(const Rinv64Job &job, int l, cudaStream_t s);
+
+// ST_ORTH into *status when max_{i<=j<l} |G_ij - delta_ij| > tol (or is not a number), G the
+// upper triangle of the Gram matrix Q^T Q of a basis (ldg).
+template <typename T>
+cudaError_t orth_check(const T *G, int l, int64_t ldg, double tol, int *status, cudaStream_t s);
+
+// Process-wide sweep cap of the Jacobi solvers (0: the defaults).
+void set_sweep_cap(int cap);
 
 // R = R2 * R1 for upper-triangular l x l float64 matrices (ld l).
 cudaError_t trmm_upper(const double *R2, const double *R1, double *R, int l, cudaStream_t s);
@@ -185,7 +253,9 @@ struct CholTab {
     double *R, *Rinv;  // l x l
     void *Rc;          // Tc, lp x lp
     int *status;
-    double coef;       // chol_shift_coef(rows, l, u)
+    double coef;       // chol_shift_coef(rows, l, u) of the arithmetic that may shift
+    const double *G64; // float64 Gram matrix of the fallback (kCholFallback), or NULL
+    int *fb;           // fallback flag (kCholFirst / kCholFallback), or NULL
 };
 struct JacTab {
     const double *R;   // l x l
@@ -195,7 +265,8 @@ struct JacTab {
 };
 double chol_shift_coef(int64_t rows, int l, double unit_roundoff);
 template <typename TG, typename Tk, typename Tc>
-cudaError_t chol_inv_batched(const CholTab *tab, int count, int64_t ldg, int l, int lp, cudaStream_t s);
+cudaError_t chol_inv_batched(const CholTab *tab, int count, int64_t ldg, int l, int lp, cudaStream_t s,
+                             int role = kCholPlain);
 template <typename Ta, typename To>
 cudaError_t jacobi_osvd_batched(const JacTab *tab, int count, int l, int lp, cudaStream_t s);
 template <typename To>
@@ -257,9 +328,13 @@ int tc_gemm_nn_grid(int64_t m, int ctas = 0);
 // aligned; mu optional (zero padded to a multiple of 128).  upper_c: only the upper
 // triangle of C is wanted (a Gram matrix, A = Q, ncols = N): a column slice of C is
 // computed for the rows up to its end.
+// chk (optional): C is the Gram matrix of a basis of chk_l columns; ST_ORTH goes into *chk when
+// an entry of its upper triangle differs from the identity's by more than chk_tol (col0: the
+// global index of this call's first column, for column slices).
 cudaError_t tc_gemm_tn(int64_t rows, int ncols, int N, const float *A, int64_t lda, const float *Q, int64_t ldq,
                        float *C, int64_t ldc, float *part, int64_t part_elems, int *status, cudaStream_t s,
-                       const float *mu = nullptr, int ctas = 0, bool upper_c = false);
+                       const float *mu = nullptr, int ctas = 0, bool upper_c = false, int *chk = nullptr,
+                       int chk_l = 0, double chk_tol = 0.0, int col0 = 0);
 int64_t tc_gemm_tn_partials(int64_t rows, int ncols, int N);
 
 // ------------------------------------------------------ block Krylov (Sec. 3.1.1)

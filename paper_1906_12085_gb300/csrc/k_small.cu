@@ -14,12 +14,21 @@
 #include <float.h>
 
 #include <algorithm>
+#include <atomic>
 #include <type_traits>
 
 #include "common.cuh"
 
 namespace gbr {
 namespace {
+
+// Sweep caps of the Jacobi solvers (rsvd_set_jacobi_sweep_cap): 0 means the defaults, 40
+// sweeps for the one-sided SVD and 50 for the two-sided eigen-decomposition.
+std::atomic<int> g_sweep_cap{0};
+int sweep_cap(int dflt) {
+    const int c = g_sweep_cap.load(std::memory_order_relaxed);
+    return c > 0 ? c : dflt;
+}
 
 __device__ __forceinline__ int rr_pos(int k, int r, int L) {
     // position k of round r in the circle method: player 0 fixed, the rest rotate
@@ -140,10 +149,17 @@ template <typename TG, typename Tk, typename Tc, bool GM = false>
 __device__ __forceinline__ void chol_inv_body(const TG *__restrict__ G, int64_t ldg, int l, double shift_coef,
                                               double *__restrict__ R, double *__restrict__ Rinv,
                                               Tc *__restrict__ Rinv_c, int lp, int *__restrict__ status,
-                                              Tk *gws = nullptr) {
+                                              Tk *gws = nullptr, int *fb = nullptr, int role = kCholPlain) {
     // GM: the matrices, the pivots and the breakdown flag in the global scratch, the work
     // shared by the CTAs of a cluster (cluster barriers between the phases)
     using Sync = typename std::conditional<GM, ClusterSync, CtaSync>::type;
+    // the fallback runs only after a breakdown of the first attempt (every thread reads the flag)
+    if (role == kCholFallback && *reinterpret_cast<volatile int *>(fb) == 0) return;
+    // kCholDeflate (float64 only, compiled out of the other forms): pivots <= tau G_kk remove
+    // their column (flags in fb[0..l-1])
+    constexpr bool kCanDeflate = std::is_same<Tk, double>::value && std::is_same<Tc, double>::value;
+    const bool deflate = kCanDeflate && role == kCholDeflate;
+    const double tau = deflate ? kDeflateRel * l : 0.0;
     const int NP = (l + 15) >> 4, LL = 16 * NP;
     const CholSmem<Tk> sm = chol_smem<Tk, GM>(LL, gws);
     Tk *A = sm.A, *X = sm.X, *rdiag = sm.rdiag;
@@ -161,6 +177,8 @@ __device__ __forceinline__ void chol_inv_body(const TG *__restrict__ G, int64_t 
     const int rank = Sync::rank(), nct = Sync::size();
     const int gt = rank * 256 + tid, gnt = nct * 256;
     int used = 0;  // 0: plain, 1: shifted, 2: breakdown fallback (R = 0, R^{-1} = I)
+    if (deflate)
+        for (int i = gt; i < l; i += gnt) fb[i] = 0;
     for (int attempt = 0; attempt < 3; attempt++) {
         if (attempt == 1 && rank == 0 && warp == 0) {  // trace for the shift (only after a breakdown)
             double tr = 0.0;
@@ -193,6 +211,28 @@ __device__ __forceinline__ void chol_inv_body(const TG *__restrict__ G, int64_t 
 #pragma unroll
                 for (int k = 0; k < 16; k++) {
                     const Tk d = __shfl_sync(0xffffffffu, col[k], k);  // D_kk, the same in every lane
+                    if (kCanDeflate && deflate) {  // a dependent column: R_kk = 1, R_kc = 0, panel row k zero
+                        const double g0 = o + k < l ? (double)G[(int64_t)(o + k) * ldg + o + k] : 1.0;
+                        const bool dep = !((double)d > tau * g0 && d < Tk(3.0e38));
+                        const Tk rinv = dep ? Tk(0) : rsq(d);
+                        col[k] = c == k ? (dep ? Tk(1) : d * rinv) : (c > k ? col[k] * rinv : col[k]);
+                        if (lane < 16) rowk[c] = col[k];
+                        if (lane == 0) {
+                            rdiag[o + k] = rinv;
+                            if (dep && o + k < l) {
+                                fb[o + k] = 1;
+                                atomicOr(status, (int)ST_RANKDEF);
+                            }
+                        }
+                        __syncwarp();
+#pragma unroll
+                        for (int i = k + 1; i < 16; i++) {
+                            const Tk rki = rowk[i];
+                            if (c >= i) col[i] -= rki * col[k];
+                        }
+                        __syncwarp();
+                        continue;
+                    }
                     ok = ok && d > Tk(0) && d < Tk(3.0e38);  // after a breakdown the remaining steps are discarded
                     const Tk rinv = rsq(ok ? d : Tk(1));
                     col[k] = c == k ? d * rinv : (c > k ? col[k] * rinv : col[k]);  // R_kc for c >= k
@@ -267,6 +307,21 @@ __device__ __forceinline__ void chol_inv_body(const TG *__restrict__ G, int64_t 
             used = attempt;
             break;
         }
+        if (role == kCholFirst) {  // breakdown: the float64 Gram matrix and Cholesky take over
+            if (rank == 0 && tid == 0) *fb = 1;
+            return;
+        }
+        Sync::sync();
+    }
+    if (role == kCholFirst && rank == 0 && tid == 0) *fb = 0;
+    if (kCanDeflate && deflate) {  // a removed column: zero above the diagonal, unit pivot for the inverse
+        for (int idx = gt; idx < LL * LL; idx += gnt) {
+            const int i = idx / LL, j = idx % LL;
+            if (j < l && i < j && reinterpret_cast<volatile int *>(fb)[j]) A[i * S + j] = Tk(0);
+        }
+        Sync::sync();
+        for (int i = gt; i < l; i += gnt)
+            if (reinterpret_cast<volatile int *>(fb)[i]) rdiag[i] = Tk(1);
         Sync::sync();
     }
     for (int idx = gt; idx < l * l; idx += gnt) {
@@ -313,22 +368,213 @@ __device__ __forceinline__ void chol_inv_body(const TG *__restrict__ G, int64_t 
     }
 }
 
+// ------------------------------------------------ float64 Gram of a float32 block
+// 64 x 64 output tiles of the upper triangle (tile pairs ti <= tj), row chunks split over
+// gridDim.y; each CTA stages 32 rows of both column tiles in shared memory as float64
+// and accumulates 4 x 4 outputs per thread in row order.
+constexpr int G64_TILE = 64, G64_ROWS = 32;
+
+struct G64Split {
+    int nt;            // column tiles
+    int pairs;         // tile pairs ti <= tj
+    int64_t chunks;    // row chunks
+    int64_t rpc;       // rows per chunk
+    int64_t cap;       // bound of `chunks` that grows with the rows (buffer and grid sizes)
+};
+
+__host__ __device__ inline G64Split g64_split(int64_t rows, int l) {
+    G64Split sp;
+    sp.nt = (l + G64_TILE - 1) / G64_TILE;
+    sp.pairs = sp.nt * (sp.nt + 1) / 2;
+    int64_t chunks = (304 + sp.pairs - 1) / sp.pairs;
+    const int64_t maxc = (rows + 255) / 256;
+    if (chunks > maxc) chunks = maxc;
+    if (chunks < 1) chunks = 1;
+    sp.cap = chunks;
+    const int64_t rpc = ((rows + chunks - 1) / chunks + G64_ROWS - 1) / G64_ROWS * G64_ROWS;
+    sp.rpc = rpc;
+    sp.chunks = (rows + rpc - 1) / rpc;
+    return sp;
+}
+
+// The CTAs of one job count themselves out on J.count; the last one sums the partials in
+// chunk order into G (deterministic), resets the counter and factors G in float64 (the
+// Cholesky body with its matrices in the global scratch J.gws, one CTA).
+template <bool TAB>
+__global__ void __launch_bounds__(256) gram64_kernel(G64Job job, const G64Job *__restrict__ tab, int l, int64_t ldg) {
+    const G64Job J = TAB ? tab[blockIdx.z] : job;
+    if (*reinterpret_cast<const volatile int *>(J.fb) == 0) return;
+    const G64Split sp = g64_split(J.rows, l);
+    const int64_t chunk = blockIdx.y;
+    if (chunk >= sp.chunks || (int)blockIdx.x >= sp.pairs) return;
+    const unsigned total = (unsigned)(sp.chunks * sp.pairs);
+    int ti = 0, p = blockIdx.x;
+    while (p >= sp.nt - ti) {
+        p -= sp.nt - ti;
+        ti++;
+    }
+    const int tj = ti + p;
+    __shared__ double xa[G64_ROWS][G64_TILE + 1], xb[G64_ROWS][G64_TILE + 1];
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+    const int64_t rb = chunk * sp.rpc, re = min(J.rows, rb + sp.rpc);
+    for (int64_t r0 = rb; r0 < re; r0 += G64_ROWS) {
+#pragma unroll
+        for (int v = 0; v < G64_ROWS * G64_TILE / 256; v++) {
+            const int e = tid + 256 * v, rr = e / G64_TILE, cc = e % G64_TILE;
+            const int64_t gr = r0 + rr;
+            const int ca = G64_TILE * ti + cc, cb = G64_TILE * tj + cc;
+            xa[rr][cc] = (gr < re && ca < l) ? (double)J.X[gr * J.ld + ca] : 0.0;
+            xb[rr][cc] = (gr < re && cb < l) ? (double)J.X[gr * J.ld + cb] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < G64_ROWS; k++) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) a[i] = xa[k][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; j++) b[j] = xb[k][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[i][j] = __fma_rn(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    const int LT = G64_TILE * sp.nt;
+    double *out = J.part + chunk * (int64_t)LT * LT;
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            out[(int64_t)(G64_TILE * ti + ty * 4 + i) * LT + G64_TILE * tj + tx * 4 + j] = acc[i][j];
+    // G[i][j] (i <= j < l) = sum of the chunk partials in chunk order, by the last CTA
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(J.count, 1u) == total - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int idx = tid; idx < l * l; idx += 256) {
+        const int i = idx / l, j = idx % l;
+        if (j < i) continue;
+        double sum = 0.0;
+        for (int64_t c = 0; c < sp.chunks; c++)
+            sum += reinterpret_cast<const volatile double *>(J.part)[c * LT * LT + (int64_t)i * LT + j];
+        J.G[(int64_t)i * ldg + j] = sum;
+    }
+    if (tid == 0) *J.count = 0u;
+    __threadfence();
+    __syncthreads();
+    chol_inv_body<double, double, float, true>(J.G, ldg, l, J.coef, J.R, J.Rinv, J.Rc, J.lp, J.status, J.gws,
+                                               const_cast<int *>(J.fb), kCholFallback);
+}
+
+// Q (rows x l, ld) = X R^{-1} in float64 products and sums, rounded once to float32; Rinv the
+// float64 l x l upper-triangular inverse (ld l).  64 x 64 output tiles over a fixed grid;
+// the K range of a tile stops at its last column (Rinv is upper triangular).
+template <bool TAB>
+__global__ void __launch_bounds__(256) rinv64_kernel(Rinv64Job job, const Rinv64Job *__restrict__ tab, int l) {
+    const Rinv64Job J = TAB ? tab[blockIdx.z] : job;
+    if (*reinterpret_cast<const volatile int *>(J.fb) == 0) return;
+    __shared__ double xs[G64_TILE][G64_ROWS + 1], rs[G64_ROWS][G64_TILE + 1];
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    const int ct = (l + G64_TILE - 1) / G64_TILE;
+    const int64_t rt = (J.rows + G64_TILE - 1) / G64_TILE;
+    for (int64_t t = blockIdx.x; t < rt * ct; t += gridDim.x) {
+        const int64_t r0 = (t / ct) * G64_TILE;
+        const int c0 = (int)(t % ct) * G64_TILE;
+        const int kend = min(l, c0 + G64_TILE);
+        double acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+        for (int k0 = 0; k0 < kend; k0 += G64_ROWS) {
+#pragma unroll
+            for (int v = 0; v < G64_TILE * G64_ROWS / 256; v++) {
+                const int e = tid + 256 * v;
+                const int xr = e / G64_ROWS, xk = e % G64_ROWS;  // X tile: 64 rows x 32 k
+                const int64_t gr = r0 + xr;
+                xs[xr][xk] = (gr < J.rows && k0 + xk < l) ? (double)J.X[gr * J.ld + k0 + xk] : 0.0;
+                const int rk = e / G64_TILE, rc = e % G64_TILE;  // Rinv tile: 32 k x 64 cols
+                rs[rk][rc] = (k0 + rk < l && c0 + rc < l) ? J.Rinv[(int64_t)(k0 + rk) * l + c0 + rc] : 0.0;
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int k = 0; k < G64_ROWS; k++) {
+                double a[4], b[4];
+#pragma unroll
+                for (int i = 0; i < 4; i++) a[i] = xs[ty * 4 + i][k];
+#pragma unroll
+                for (int j = 0; j < 4; j++) b[j] = rs[k][tx * 4 + j];
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+#pragma unroll
+                    for (int j = 0; j < 4; j++) acc[i][j] = __fma_rn(a[i], b[j], acc[i][j]);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int64_t r = r0 + ty * 4 + i;
+            if (r >= J.rows) break;
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int c = c0 + tx * 4 + j;
+                if (c < l) J.Q[r * J.ld + c] = (float)acc[i][j];
+            }
+        }
+    }
+}
+
+
 template <typename TG, typename Tk, typename Tc, bool GM>
 __global__ void __launch_bounds__(256, 1) chol_inv_kernel(const TG *__restrict__ G, int64_t ldg, int l,
                                                           double shift_coef, double *__restrict__ R,
                                                           double *__restrict__ Rinv, Tc *__restrict__ Rinv_c, int lp,
-                                                          int *__restrict__ status, Tk *__restrict__ gws) {
-    chol_inv_body<TG, Tk, Tc, GM>(G, ldg, l, shift_coef, R, Rinv, Rinv_c, lp, status, gws);
+                                                          int *__restrict__ status, Tk *__restrict__ gws, int *fb,
+                                                          int role) {
+    chol_inv_body<TG, Tk, Tc, GM>(G, ldg, l, shift_coef, R, Rinv, Rinv_c, lp, status, gws, fb, role);
 }
 
-// One CTA per problem of a batch; problem b's pointers and shift are tab[b].
+// One CTA per problem of a batch; problem b's pointers and shift are tab[b] (the fallback
+// role factors tab[b].G64).
 template <typename TG, typename Tk, typename Tc>
 __global__ void __launch_bounds__(256, 1) chol_inv_batch_kernel(const CholTab *__restrict__ tab, int64_t ldg, int l,
-                                                                int lp) {
+                                                                int lp, int role) {
     const CholTab t = tab[blockIdx.x];
-    chol_inv_body<TG, Tk, Tc>(static_cast<const TG *>(t.G), ldg, l, t.coef, t.R, t.Rinv, static_cast<Tc *>(t.Rc), lp,
-                              t.status);
+    const TG *G = static_cast<const TG *>(role == kCholFallback ? static_cast<const void *>(t.G64) : t.G);
+    chol_inv_body<TG, Tk, Tc>(G, ldg, l, t.coef, t.R, t.Rinv, static_cast<Tc *>(t.Rc), lp, t.status, nullptr, t.fb,
+                              role);
 }
+
+// ST_ORTH when max_{i <= j < l} |G_ij - delta_ij| > tol (or not a number): one CTA.
+template <typename T>
+__device__ __forceinline__ void orth_check_body(const T *__restrict__ G, int l, int64_t ldg, double tol,
+                                                int *__restrict__ status) {
+    bool bad = false;
+    for (int idx = threadIdx.x; idx < l * l; idx += blockDim.x) {
+        const int i = idx / l, j = idx % l;
+        if (j < i) continue;
+        const double e = fabs((double)G[(int64_t)i * ldg + j] - (i == j ? 1.0 : 0.0));
+        bad = bad || !(e <= tol);  // also catches NaN
+    }
+    bad = __syncthreads_or(bad);
+    if (bad && threadIdx.x == 0) atomicOr(status, (int)ST_ORTH);
+}
+
+template <typename T>
+__global__ void orth_check_kernel(const T *__restrict__ G, int l, int64_t ldg, double tol, int *__restrict__ status) {
+    orth_check_body<T>(G, l, ldg, tol, status);
+}
+
 
 __global__ void trmm_upper_kernel(const double *__restrict__ R2, const double *__restrict__ R1, double *__restrict__ R,
                                   int l) {
@@ -910,6 +1156,38 @@ size_t chol_smem_bytes(int l) {
 
 }  // namespace
 
+int64_t gram64_partials(int64_t rows, int l) {
+    const G64Split sp = g64_split(rows, l);
+    return sp.cap * (int64_t)(G64_TILE * sp.nt) * (G64_TILE * sp.nt);
+}
+
+cudaError_t gram64_fb(const G64Job &job, int l, int64_t ldg, cudaStream_t s) {
+    if (l < 1 || !job.fb || !job.count || !job.gws) return cudaErrorInvalidValue;
+    const G64Split sp = g64_split(job.rows, l);
+    gram64_kernel<false><<<dim3(sp.pairs, (unsigned)sp.chunks, 1), 256, 0, s>>>(job, nullptr, l, ldg);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t gram64_fb_batched(const G64Job *tab, int count, int64_t max_rows, int l, int64_t ldg, cudaStream_t s) {
+    if (count < 1) return cudaSuccess;
+    const G64Split sp = g64_split(max_rows, l);  // the chunk bound grows with the rows: enough for every job
+    G64Job none = {};
+    // a job's CTAs beyond its own chunk count return before counting themselves out
+    gram64_kernel<true><<<dim3(sp.pairs, (unsigned)sp.cap, count), 256, 0, s>>>(none, tab, l, ldg);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t rinv64_fb(const Rinv64Job &job, int l, cudaStream_t s) {
+    if (l < 1 || !job.fb) return cudaErrorInvalidValue;
+    rinv64_kernel<false><<<dim3(304, 1, 1), 256, 0, s>>>(job, nullptr, l);
+    note_launch();
+    return cudaGetLastError();
+}
+
+void set_sweep_cap(int cap) { g_sweep_cap.store(cap > 0 ? cap : 0, std::memory_order_relaxed); }
+
 size_t chol_scratch_bytes(int l, size_t tk) {
     const int LL = 16 * ((l + 15) / 16), S = LL + (tk == 4 ? 16 : 1);
     return tk * (2 * (size_t)LL * S + ((LL + 1) & ~1)) + 2 * sizeof(double);  // A, X, pivots, trace, flag
@@ -917,7 +1195,8 @@ size_t chol_scratch_bytes(int l, size_t tk) {
 
 template <typename TG, typename Tk, typename Tc>
 cudaError_t chol_inv(const TG *G, int64_t ldg, int l, int64_t rows, double u, double *R, double *Rinv, Tc *Rinv_c,
-                     int lp, int *status, cudaStream_t s, void *scratch) {
+                     int lp, int *status, cudaStream_t s, void *scratch, int *fb, int role) {
+    if (role != kCholPlain && !fb) return cudaErrorInvalidValue;
     const double coef = chol_shift_coef(rows, l, u);
     size_t smem = chol_smem_bytes<Tk>(l);
     Tk *gws = nullptr;
@@ -939,26 +1218,38 @@ cudaError_t chol_inv(const TG *G, int64_t ldg, int l, int64_t rows, double u, do
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        cudaLaunchKernelEx(&cfg, chol_inv_kernel<TG, Tk, Tc, true>, G, ldg, l, coef, R, Rinv, Rinv_c, lp, status, gws);
+        cudaLaunchKernelEx(&cfg, chol_inv_kernel<TG, Tk, Tc, true>, G, ldg, l, coef, R, Rinv, Rinv_c, lp, status, gws,
+                           fb, role);
     } else {
         cudaFuncSetAttribute(chol_inv_kernel<TG, Tk, Tc, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
-        chol_inv_kernel<TG, Tk, Tc, false><<<1, 256, smem, s>>>(G, ldg, l, coef, R, Rinv, Rinv_c, lp, status, nullptr);
+        chol_inv_kernel<TG, Tk, Tc, false><<<1, 256, smem, s>>>(G, ldg, l, coef, R, Rinv, Rinv_c, lp, status, nullptr,
+                                                                fb, role);
     }
     note_launch();
     return cudaGetLastError();
 }
 
 template <typename TG, typename Tk, typename Tc>
-cudaError_t chol_inv_batched(const CholTab *tab, int count, int64_t ldg, int l, int lp, cudaStream_t s) {
+cudaError_t chol_inv_batched(const CholTab *tab, int count, int64_t ldg, int l, int lp, cudaStream_t s, int role) {
     if (count < 1) return cudaSuccess;
     const size_t smem = chol_smem_bytes<Tk>(l);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     cudaFuncSetAttribute(chol_inv_batch_kernel<TG, Tk, Tc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    chol_inv_batch_kernel<TG, Tk, Tc><<<count, 256, smem, s>>>(tab, ldg, l, lp);
+    chol_inv_batch_kernel<TG, Tk, Tc><<<count, 256, smem, s>>>(tab, ldg, l, lp, role);
     note_launch();
     return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t orth_check(const T *G, int l, int64_t ldg, double tol, int *status, cudaStream_t s) {
+    orth_check_kernel<T><<<1, 256, 0, s>>>(G, l, ldg, tol, status);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template cudaError_t orth_check<float>(const float *, int, int64_t, double, int *, cudaStream_t);
+template cudaError_t orth_check<double>(const double *, int, int64_t, double, int *, cudaStream_t);
 
 double chol_shift_coef(int64_t rows, int l, double u) { return 11.0 * ((double)rows * l + (double)l * (l + 1)) * u; }
 
@@ -1006,7 +1297,7 @@ void launch_jacobi(const JacTab *tab, int count, const double *R, int l, int lp,
     if (tab) {
         cudaFuncSetAttribute(jacobi_osvd_batch_kernel<Ta, To, BW, NR, MAXT>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        jacobi_osvd_batch_kernel<Ta, To, BW, NR, MAXT><<<count, threads, smem, s>>>(tab, l, lp, 40);
+        jacobi_osvd_batch_kernel<Ta, To, BW, NR, MAXT><<<count, threads, smem, s>>>(tab, l, lp, sweep_cap(40));
     } else if (gws) {  // a cluster of up to 8 CTAs (one warp per block pair where possible)
         auto kern = jacobi_osvd_kernel<Ta, To, BW, NR, MAXT>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1024,11 +1315,12 @@ void launch_jacobi(const JacTab *tab, int count, const double *R, int l, int lp,
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        cudaLaunchKernelEx(&cfg, kern, R, l, lp, sig, UR, W, status, 40, gws);
+        cudaLaunchKernelEx(&cfg, kern, R, l, lp, sig, UR, W, status, sweep_cap(40), gws);
     } else {
         cudaFuncSetAttribute(jacobi_osvd_kernel<Ta, To, BW, NR, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
-        jacobi_osvd_kernel<Ta, To, BW, NR, MAXT><<<1, threads, smem, s>>>(R, l, lp, sig, UR, W, status, 40, gws);
+        jacobi_osvd_kernel<Ta, To, BW, NR, MAXT><<<1, threads, smem, s>>>(R, l, lp, sig, UR, W, status,
+                                                                          sweep_cap(40), gws);
     }
 }
 
@@ -1112,8 +1404,11 @@ template cudaError_t sv_refine_batched<float>(const JacTab *, int, int, int, cud
 template cudaError_t sv_refine_batched<double>(const JacTab *, int, int, int, cudaStream_t);
 template cudaError_t jacobi_osvd_batched<float, float>(const JacTab *, int, int, int, cudaStream_t);
 template cudaError_t jacobi_osvd_batched<double, double>(const JacTab *, int, int, int, cudaStream_t);
-template cudaError_t chol_inv_batched<float, float, float>(const CholTab *, int, int64_t, int, int, cudaStream_t);
-template cudaError_t chol_inv_batched<double, double, double>(const CholTab *, int, int64_t, int, int, cudaStream_t);
+template cudaError_t chol_inv_batched<float, float, float>(const CholTab *, int, int64_t, int, int, cudaStream_t, int);
+template cudaError_t chol_inv_batched<double, double, double>(const CholTab *, int, int64_t, int, int, cudaStream_t,
+                                                              int);
+template cudaError_t chol_inv_batched<double, double, float>(const CholTab *, int, int64_t, int, int, cudaStream_t,
+                                                             int);
 template cudaError_t sv_refine<double>(const double *, int, int, const double *, const double *, double *,
                                        cudaStream_t);
 
@@ -1123,7 +1418,7 @@ cudaError_t jacobi_eig_t(const double *G, int n, double *lam, double *V, int *st
     const int L = n + (n & 1);
     const size_t smem = sizeof(Tm) * (2 * (size_t)n * n + L + (L & 1)) + sizeof(int) * (2 * L) + 16;
     cudaFuncSetAttribute(jacobi_eig_kernel<Tm>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    jacobi_eig_kernel<Tm><<<1, 1024, smem, s>>>(G, n, lam, V, status, 50, floor_rel);
+    jacobi_eig_kernel<Tm><<<1, 1024, smem, s>>>(G, n, lam, V, status, sweep_cap(50), floor_rel);
     note_launch();
     return cudaGetLastError();
 }
@@ -1180,10 +1475,11 @@ cudaError_t pca_select(const double *sigma, int count, const double *fro2, doubl
 
 #define INST_CHOL(TG, TK, TC)                                                                                   \
     template cudaError_t chol_inv<TG, TK, TC>(const TG *, int64_t, int, int64_t, double, double *, double *, TC *, \
-                                              int, int *, cudaStream_t, void *);
+                                              int, int *, cudaStream_t, void *, int *, int);
 INST_CHOL(float, float, float)
 INST_CHOL(float, double, float)
 INST_CHOL(double, double, double)
+INST_CHOL(double, double, float)
 template cudaError_t jacobi_osvd<float, float>(const double *, int, int, double *, float *, float *, int *,
                                                cudaStream_t, void *);
 template cudaError_t jacobi_osvd<double, float>(const double *, int, int, double *, float *, float *, int *,

@@ -582,9 +582,11 @@ __global__ void split_transpose_kernel(const float *__restrict__ Z, int64_t rows
 
 // C[i * ldc + j] = sum_{s < chunks} part[s][i][j] (N x L per chunk).  A block covers 32
 // consecutive outputs with 8 row groups taking interleaved chunks; the groups are
-// combined in a fixed order, so the sum is deterministic.
+// combined in a fixed order, so the sum is deterministic.  With chk (C the Gram matrix Q^T Q
+// of a basis of chk_l columns, this launch's columns starting at col0): ST_ORTH when an entry
+// of its upper triangle differs from the identity's by more than tol.
 __global__ void sum_chunks_kernel(const float *__restrict__ part, int64_t chunks, int64_t N, int64_t L,
-                                  float *__restrict__ C, int64_t ldc) {
+                                  float *__restrict__ C, int64_t ldc, int *chk, int chk_l, int col0, float tol) {
     __shared__ float red[8][33];
     const int cx = threadIdx.x & 31, gy = threadIdx.x >> 5;
     const int64_t idx = (int64_t)blockIdx.x * 32 + cx;
@@ -598,6 +600,11 @@ __global__ void sum_chunks_kernel(const float *__restrict__ part, int64_t chunks
         float t = red[0][cx];
         for (int g = 1; g < 8; g++) t += red[g][cx];
         C[(idx / L) * ldc + idx % L] = t;
+        if (chk) {
+            const int64_t i = idx / L, j = col0 + idx % L;
+            if (i < chk_l && j < chk_l && j >= i && !(fabsf(t - (i == j ? 1.f : 0.f)) <= tol))
+                atomicOr(chk, (int)ST_ORTH);
+        }
     }
 }
 
@@ -780,14 +787,14 @@ int64_t tc_gemm_tn_partials(int64_t rows, int ncols, int N) {
 
 cudaError_t tc_gemm_tn(int64_t rows, int ncols, int N, const float *A, int64_t lda, const float *Q, int64_t ldq,
                        float *C, int64_t ldc, float *part, int64_t part_elems, int *status, cudaStream_t s,
-                       const float *mu, int ctas, bool upper_c) {
+                       const float *mu, int ctas, bool upper_c, int *chk, int chk_l, double chk_tol, int col0) {
     if (N > 128 && N % 16 == 0) {  // column slices of Q and C (A read once per slice)
         const int w = column_slice(N);
         for (int c0 = 0; c0 < N; c0 += w) {
             const int wn = w < N - c0 ? w : N - c0;
             const int nc = upper_c && c0 + wn < ncols ? c0 + wn : ncols;  // upper triangle: rows up to the slice end
             const cudaError_t e = tc_gemm_tn(rows, nc, wn, A, lda, Q + c0, ldq, C + c0, ldc, part, part_elems, status,
-                                             s, mu, ctas);
+                                             s, mu, ctas, false, chk, chk_l, chk_tol, col0 + c0);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
@@ -811,7 +818,8 @@ cudaError_t tc_gemm_tn(int64_t rows, int ncols, int N, const float *A, int64_t l
     }
     if (e != cudaSuccess) return e;
     const int64_t total = (int64_t)ncols * N;
-    sum_chunks_kernel<<<(unsigned)ceil_div(total, 32), 256, 0, s>>>(part, sp.chunks, ncols, N, C, ldc);
+    sum_chunks_kernel<<<(unsigned)ceil_div(total, 32), 256, 0, s>>>(part, sp.chunks, ncols, N, C, ldc, chk, chk_l,
+                                                                     col0, (float)chk_tol);
     note_launch();
     return cudaGetLastError();
 }

@@ -54,6 +54,12 @@ struct rsvd_plan {
     double *G64 = nullptr, *R1 = nullptr, *R1i = nullptr, *R2 = nullptr, *R2i = nullptr, *Rt = nullptr;
     double *lam = nullptr, *Vfull = nullptr, *sig = nullptr;
     int *status = nullptr, *Kdev = nullptr;
+    // CholeskyQR fallback of the float32 bases: breakdown flag of the current factorisation and
+    // the split-K partials of the float64 Gram matrix (not used by float64 plans)
+    int *fb = nullptr;             // float64 plans: the removed-column flags of kCholDeflate (lpc ints)
+    double *g64part = nullptr;
+    unsigned *g64count = nullptr;  // CTA counter of the float64 Gram reduction (kept zero between uses)
+    uint64_t nfact = 0;            // factorisations of the current solve (seeds of the column refills)
     void *chol_ws = nullptr, *jac_ws = nullptr;  // global l x l blocks of the small solvers (large l only)
     void *Hk = nullptr;                          // block Krylov basis, m x Wp
     int *bk_flag = nullptr;                      // block Krylov: directions of a block to refill (lp ints)
@@ -172,8 +178,21 @@ void carve(rsvd_plan *P, Carver &c) {
     P->sig = (double *)c.take(sizeof(double) * (n > sq ? n : sq));
     P->status = (int *)c.take(sizeof(int));
     P->Kdev = (int *)c.take(2 * sizeof(int));
-    if (P->lpc > kSmallMaxF64)  // l x l blocks of the Cholesky beyond one SM's shared memory (float64 sizing)
-        P->chol_ws = c.take(chol_scratch_bytes(P->lpc, sizeof(double)));
+    P->fb = (int *)c.take(sizeof(int) * sq);
+    if (P->dtype != RSVD_F64) {  // float64 Gram partials of the widest block the factorisations see
+        const int wmax = (int)sq;
+        int64_t ge = 0;
+        for (int w = 64; w < wmax + 64; w += 64) {  // the partials depend on w through its 64-column tiles
+            const int64_t e = gram64_partials(m > n ? m : n, w < wmax ? w : wmax);
+            if (e > ge) ge = e;
+        }
+        P->g64part = (double *)c.take(sizeof(double) * ge);
+        P->g64count = (unsigned *)c.take(sizeof(unsigned));
+    }
+    // l x l blocks of the Cholesky beyond one SM's shared memory (float64 sizing); float32 bases
+    // always: the float64 fallback factorisation runs in this scratch
+    if (P->lpc > kSmallMaxF64 || P->dtype != RSVD_F64)
+        P->chol_ws = c.take(chol_scratch_bytes((int)sq, sizeof(double)));
     if (P->lpc > 160)           // and of the float32 Jacobi
         P->jac_ws = c.take(jacobi_scratch_bytes(P->lpc, sizeof(float)));
     if (P->bk_blocks) {
@@ -305,24 +324,90 @@ cudaError_t prod_nn(rsvd_plan *P, int64_t rows, int64_t K, const T *X, int64_t l
 
 // C (ncols x N) = (X - 1 mu^T)^T Q with X rows x ncols (ldx), Q rows x N (ldq), N = lp.
 // gram: X = Q and only the upper triangle of C is wanted (CholeskyQR's Gram matrix).
+// chk_l > 0 (with gram): C = Q^T Q of a basis of chk_l columns, checked against the identity
+// (ST_ORTH beyond the element type's bound; fused into the product's reduction when it runs
+// on the tensor cores).
 template <typename T>
 cudaError_t prod_tn(rsvd_plan *P, int64_t rows, int64_t ncols, const T *X, int64_t ldx, const T *Q, int64_t ldq,
-                    T *C, int64_t ldc, const T *mu = nullptr, bool gram = false) {
+                    T *C, int64_t ldc, const T *mu = nullptr, bool gram = false, int chk_l = 0) {
+    const double tol = sizeof(T) == 4 ? kOrthTolF32 : kOrthTolF64;
     if constexpr (sizeof(T) == 4) {
         if (P->tc && al16(X, ldx, 4) && al16(Q, ldq, 4) &&
             tc_gemm_tn_partials(rows, (int)ncols, P->lp) <= P->tcpart_elems) {
             cudaError_t e = tc_gemm_tn(rows, (int)ncols, P->lp, X, ldx, Q, ldq, C, ldc, P->tcpart, P->tcpart_elems,
-                                       P->status, P->stream, mu, P->tn_ctas, gram && X == Q && ncols == P->lp);
+                                       P->status, P->stream, mu, P->tn_ctas, gram && X == Q && ncols == P->lp,
+                                       chk_l ? P->status : nullptr, chk_l, tol);
             if (e != cudaErrorInvalidValue) return e;
             cudaGetLastError();
         }
     }
     cudaError_t e = gemm_tn<T>(rows, ncols, P->lp, X, ldx, Q, ldq, C, ldc, (T *)P->part, P->part_elems, P->stream);
+    if (e == cudaSuccess && chk_l) e = orth_check<T>(C, chk_l, ldc, tol, P->status, P->stream);
     if (e == cudaSuccess && mu) {  // exact rank-1 correction: C -= mu (1^T Q)
         e = column_sums<T>(Q, rows, P->lp, ldq, P->dsum, (T *)P->cvec, P->cpart, P->stream);
         if (e == cudaSuccess) e = rank1_sub<T>(C, ncols, P->lp, ldc, mu, (T *)P->cvec, P->stream);
     }
     return e;
+}
+
+// The Cholesky of one CholeskyQR pass, R^T R = G with G the Gram matrix of X (rows x w, ld)
+// already in P->G.  Float32 bases (every dtype but float64): the float32 factorisation
+// (float64 arithmetic when f64) of the float32 Gram matrix; when it breaks down (a basis
+// with cond(X) beyond ~1e4, whose float32 Gram matrix is no longer positive definite) the
+// Gram matrix is formed again from the float32 X with float64 products and sums and
+// factored in float64 (mixed-precision CholeskyQR: it resolves every direction the float32
+// data carries; its shift, 11 (rows w + w(w+1)) u64 tr(G), only for exactly dependent
+// columns).  The basis of such a pass is then formed as X R^{-1} in float64 too (rinv64_fb in
+// cqr), so its error no longer grows with cond(X) times the product's rounding.  The
+// fallback launches return at once when the first factorisation succeeded.
+// Float64 bases whose R is not kept (deflate): columns with a pivot below l u64 of their
+// squared norm are removed (kCholDeflate) and refilled by the caller; a factorisation whose R
+// is kept (T, and A in svd_exact) shifts instead.
+template <typename T>
+rsvd_status chol_pass(rsvd_plan *P, const T *X, int64_t rows, int w, int ld, bool f64, double *R, double *Ri,
+                      T *Ric, bool deflate) {
+    cudaStream_t s = P->stream;
+    const double u64 = DBL_EPSILON / 2;
+    if constexpr (sizeof(T) == 4) {
+        const float *G = (const float *)P->G;
+        if (f64)
+            CK(chol_inv<float, double, float>(G, ld, w, rows, u64, R, Ri, Ric, ld, P->status, s, P->chol_ws, P->fb,
+                                              kCholFirst));
+        else CK(chol_inv<float, float, float>(G, ld, w, rows, u64, R, Ri, Ric, ld, P->status, s, P->chol_ws, P->fb,
+                                              kCholFirst));
+        const G64Job job = {X,  rows, ld,  P->g64part, P->G64,    P->fb, P->g64count, chol_shift_coef(rows, w, u64),
+                            R,  Ri,   Ric, ld,         P->status, (double *)P->chol_ws};
+        CK(gram64_fb(job, w, ld, s));  // float64 Gram matrix and Cholesky, after a breakdown only
+    } else {
+        CK(chol_inv<double, double, double>((const double *)P->G, ld, w, rows, u64, R, Ri, Ric, ld, P->status, s,
+                                            P->chol_ws, deflate ? P->fb : nullptr,
+                                            deflate ? kCholDeflate : kCholPlain));
+    }
+    return RSVD_OK;
+}
+
+// The columns of a float64 basis that kCholDeflate removed (P->fb) are replaced by pseudo-
+// random ones (SplitMix64 from a per-factorisation seed), which the next CholeskyQR pass
+// orthonormalises against the rest.
+template <typename T>
+rsvd_status refill(rsvd_plan *P, T *Q, int64_t rows, int w, int ld) {
+    if constexpr (sizeof(T) == 8) CK(bk_fill<T>(Q, rows, w, ld, P->fb, 0x2D0C4A5E1ull + 0x9E3779B97F4A7C15ull * ++P->nfact,
+                                                P->stream));
+    return RSVD_OK;
+}
+
+// Orthonormality check of a final basis Q (rows x w, ld): G = Q^T Q (upper triangle) and
+// ST_ORTH when max |G - I| exceeds the bound of the element type (kOrthTolF32 / F64).
+template <typename T>
+rsvd_status check_basis(rsvd_plan *P, const T *Q, int64_t rows, int w, int ld) {
+    T *G = (T *)P->G;
+    if (ld == P->lp) {
+        CK(prod_tn<T>(P, rows, ld, Q, ld, Q, ld, G, ld, nullptr, true, w));
+    } else {
+        CK(gemm_tn<T>(rows, ld, ld, Q, ld, Q, ld, G, ld, (T *)P->part, P->part_elems, P->stream));
+        CK(orth_check<T>(G, w, ld, sizeof(T) == 4 ? kOrthTolF32 : kOrthTolF64, P->status, P->stream));
+    }
+    return RSVD_OK;
 }
 
 // CholeskyQR of X (rows x w, ld) with one or two passes: Qo = X R^{-1}.
@@ -335,8 +420,8 @@ template <typename T>
 rsvd_status cqr(rsvd_plan *P, const T *X, int64_t rows, int w, int ld, T *Qo, T *Tmp, bool want_r, int passes = 2) {
     cudaStream_t s = P->stream;
     T *G = (T *)P->G, *Ric = (T *)P->Rinv_c, *part = (T *)P->part;
-    const double u = unit_roundoff<T>();
     const bool skinny = ld == P->lp;  // the l-wide blocks of the randomized solver
+    rsvd_status st;
     T *Q1 = passes == 2 ? Tmp : Qo;
     // the precision forms factor the Gram matrices of CholeskyQR2 (the final basis and
     // T) in float64; the single-pass re-orthonormalisations inside the power
@@ -344,19 +429,21 @@ rsvd_status cqr(rsvd_plan *P, const T *X, int64_t rows, int w, int ld, T *Qo, T 
     const bool f64 = (P->dtype == RSVD_BF16 || P->dtype == RSVD_FP8_E4M3) && passes == 2;
     if (skinny) CK(prod_tn<T>(P, rows, ld, X, ld, X, ld, G, ld, nullptr, true));
     else CK(gemm_tn<T>(rows, ld, ld, X, ld, X, ld, G, ld, part, P->part_elems, s));
-    if (f64)
-        CK(chol_inv<T, double, T>(G, ld, w, rows, u, P->R1, P->R1i, Ric, ld, P->status, s, P->chol_ws));
-    else CK(chol_inv<T, T, T>(G, ld, w, rows, u, P->R1, P->R1i, Ric, ld, P->status, s, P->chol_ws));
+    const bool defl = sizeof(T) == 8 && !want_r;  // float64 bases: remove and refill dependent columns
+    if ((st = chol_pass<T>(P, X, rows, w, ld, f64, P->R1, P->R1i, Ric, defl))) return st;
     if (skinny) CK(prod_nn<T>(P, rows, ld, X, ld, Ric, ld, Q1, ld, nullptr, nullptr, true));
     else CK(gemm_nn<T>(rows, ld, ld, X, ld, Ric, ld, Q1, ld, s));
+    // the final bases after a fallback: X R^{-1} in float64 (an intermediate basis only carries a range)
+    if (sizeof(T) == 4 && passes == 2) CK(rinv64_fb({(const float *)X, rows, ld, P->R1i, (float *)Q1, P->fb}, w, s));
+    if (defl && (st = refill<T>(P, Q1, rows, w, ld))) return st;
     if (passes == 1) return RSVD_OK;
     if (skinny) CK(prod_tn<T>(P, rows, ld, Q1, ld, Q1, ld, G, ld, nullptr, true));
     else CK(gemm_tn<T>(rows, ld, ld, Q1, ld, Q1, ld, G, ld, part, P->part_elems, s));
-    if (f64)
-        CK(chol_inv<T, double, T>(G, ld, w, rows, u, P->R2, P->R2i, Ric, ld, P->status, s, P->chol_ws));
-    else CK(chol_inv<T, T, T>(G, ld, w, rows, u, P->R2, P->R2i, Ric, ld, P->status, s, P->chol_ws));
+    if ((st = chol_pass<T>(P, Q1, rows, w, ld, f64, P->R2, P->R2i, Ric, defl))) return st;
     if (skinny) CK(prod_nn<T>(P, rows, ld, Q1, ld, Ric, ld, Qo, ld, nullptr, nullptr, true));
     else CK(gemm_nn<T>(rows, ld, ld, Q1, ld, Ric, ld, Qo, ld, s));
+    if (sizeof(T) == 4) CK(rinv64_fb({(const float *)Q1, rows, ld, P->R2i, (float *)Qo, P->fb}, w, s));
+    if (defl && (st = refill<T>(P, Qo, rows, w, ld))) return st;
     if (want_r) CK(trmm_upper(P->R2, P->R1, P->Rt, w, s));
     return RSVD_OK;
 }
@@ -409,6 +496,10 @@ rsvd_status ritz(rsvd_plan *P, const T *A, const T *mu, const T *Q, double *S, T
     T *Qz = (T *)P->Qz, *Tn = (T *)P->Tn, *Vt = (T *)P->Vt, *Tmpn = (T *)P->Tmpn;
     rsvd_status st;
     {
+        Span sp(P, RSVD_STAGE_ORTH);
+        if ((st = check_basis<T>(P, Q, m, l, lp))) return st;                  // Q^T Q = I
+    }
+    {
         Span sp(P, RSVD_STAGE_ATX);
         CK(prod_tn<T>(P, m, n, A, n, Q, lp, Tn, lp, mu));                       // T = A^T Q  (= B^T)
     }
@@ -424,6 +515,7 @@ rsvd_status ritz(rsvd_plan *P, const T *A, const T *mu, const T *Q, double *S, T
         } else if ((st = cqr2<T>(P, Tn, n, l, lp, Qz, Tmpn, true))) {
             return st;
         }
+        if ((st = check_basis<T>(P, Qz, n, l, lp))) return st;                // Q_T^T Q_T = I
         CK(jacobi_osvd<T, T>(P->Rt, l, lp, P->sig, UR, W, P->status, s, P->jac_ws));     // R = U_R Sigma W^T
         CK(sv_refine<T>(P->Rt, l, lp, UR, W, P->sig, s));                     // sigma_i = u_i^T R w_i (float64)
     }
@@ -443,6 +535,7 @@ rsvd_status ritz(rsvd_plan *P, const T *A, const T *mu, const T *Q, double *S, T
 template <typename T>
 rsvd_status run_rsvd(rsvd_plan *P, T *A, const T *Omega, double *S, T *U, T *V) {
     cudaStream_t s = P->stream;
+    P->nfact = 0;
     const int64_t m = P->m, n = P->n;
     const int l = P->l, lp = P->lp;
     T *Y = (T *)P->Y, *Q = (T *)P->Qb, *Tmp = (T *)P->Tmp;
@@ -511,6 +604,7 @@ struct Width {
 template <typename T>
 rsvd_status run_block_krylov(rsvd_plan *P, T *A, const T *Omega, double *S, T *U, T *V) {
     cudaStream_t s = P->stream;
+    P->nfact = 0;
     const int64_t m = P->m, n = P->n;
     const int b = P->l, lp = P->lp, nb = P->bk_blocks, Wp = P->lpc;
     T *Y = (T *)P->Y, *Qb = (T *)P->Qb, *Tmp = (T *)P->Tmp, *H = (T *)P->Hk;
@@ -646,11 +740,16 @@ rsvd_status run_rsvd_bf16(rsvd_plan *P, const void *A, const float *Omega, doubl
             if ((st = cqr<float>(P, Y, m, l, lp, Q, Tmp, false, last ? 2 : 1))) return st;
         }
     }
+    {
+        Span sp(P, RSVD_STAGE_ORTH);
+        if ((st = check_basis<float>(P, Q, m, l, lp))) return st;
+    }
     if ((st = atx(3, Tn))) return st;  // T = A^T Q, float32-accurate
     float *UR = (float *)P->UR, *W = (float *)P->Wm;
     {
         Span sp(P, RSVD_STAGE_SMALL);
         if ((st = cqr2<float>(P, Tn, n, l, lp, Qz, Tmpn, true))) return st;
+        if ((st = check_basis<float>(P, Qz, n, l, lp))) return st;
         // float32 rotations, float64 Rayleigh-quotient values (the float64 rate of this
         // GPU is 1/58 of float32: a float64 Jacobi of l = 112 takes ~50 ms)
         CK(jacobi_osvd<float, float>(P->Rt, l, lp, P->sig, UR, W, P->status, s, P->jac_ws));
@@ -722,6 +821,10 @@ rsvd_status run_rsvd_fp8(rsvd_plan *P, const void *A, const float *sc, const flo
         }
     }
     {
+        Span sp(P, RSVD_STAGE_ORTH);
+        if ((st = check_basis<float>(P, Q, m, l, lp))) return st;
+    }
+    {
         Span sp(P, RSVD_STAGE_ATX);  // T = A^T Q, float32-accurate, on the bfloat16 copy of the codes
         const void *q3[3] = {P->Qb1, P->Qb2, P->Qb3};
         CK(e4m3_to_bf16(A, m * n, P->A16, s));
@@ -733,6 +836,7 @@ rsvd_status run_rsvd_fp8(rsvd_plan *P, const void *A, const float *sc, const flo
     {
         Span sp(P, RSVD_STAGE_SMALL);
         if ((st = cqr2<float>(P, Tn, n, l, lp, Qz, Tmpn, true))) return st;
+        if ((st = check_basis<float>(P, Qz, n, l, lp))) return st;
         CK(jacobi_osvd<float, float>(P->Rt, l, lp, P->sig, UR, W, P->status, s, P->jac_ws));
         CK(sv_refine<float>(P->Rt, l, lp, UR, W, P->sig, s));
     }
@@ -782,6 +886,7 @@ rsvd_status run_exact(rsvd_plan *P, T *A, int method, double *S, T *U, T *V) {
         {
             Span sp(P, RSVD_STAGE_ORTH);
             if ((st = cqr2<T>(P, A, m, nn, nn, Qw, Tmp, true))) return st;           // A = Q R
+            if ((st = check_basis<T>(P, Qw, m, nn, nn))) return st;
         }
         {
             Span sp(P, RSVD_STAGE_SMALL);
@@ -944,8 +1049,11 @@ struct BatchCtx {
         if (dtab) cudaFree(dtab);
         if (htab) cudaFreeHost(htab);
     }
-    // tables: 4 CholTab blocks (rows m / n x pass 1 / 2) and one JacTab block, `count` entries each
-    static size_t bytes_for(int count) { return (4 * sizeof(CholTab) + sizeof(JacTab)) * (size_t)count; }
+    // tables: 4 CholTab blocks (rows m / n x pass 1 / 2), one JacTab block and 6 G64Job blocks
+    // (which block x pass 1 / 2: the float64 Gram fallback), `count` entries each
+    static size_t bytes_for(int count) {
+        return (4 * sizeof(CholTab) + sizeof(JacTab) + 6 * sizeof(G64Job)) * (size_t)count;
+    }
     cudaError_t reserve(int count) {
         if (count <= cap) return cudaSuccess;
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
@@ -969,6 +1077,11 @@ struct BatchCtx {
     }
     JacTab *jac(int count, bool dev) {
         return reinterpret_cast<JacTab *>((char *)(dev ? dtab : htab) + 4 * sizeof(CholTab) * (size_t)count);
+    }
+    G64Job *g64(int variant, int count, bool dev) {
+        return reinterpret_cast<G64Job *>((char *)(dev ? dtab : htab) +
+                                          (4 * sizeof(CholTab) + sizeof(JacTab)) * (size_t)count) +
+               (size_t)variant * count;
     }
 };
 
@@ -1000,6 +1113,8 @@ rsvd_status bcqr(BatchCtx &C, int count, rsvd_plan *const *Ps, int which, int pa
         else { X = which == BQ_Z ? (T *)P->Z : (T *)P->Tn; Qo = (T *)P->Qz; Tmp = (T *)P->Tmpn; rows = P->n; }
     };
     const int rv = which == BQ_Y ? 0 : 2;  // table block: rows m (0, 1) or rows n (2, 3)
+    int64_t max_rows = 0;
+    for (int i = 0; i < count; i++) max_rows = std::max(max_rows, which == BQ_Y ? Ps[i]->m : Ps[i]->n);
     for (int pass = 0; pass < passes; pass++) {
         for (int i = 0; i < count; i++) {
             rsvd_plan *P = Ps[i];
@@ -1010,7 +1125,13 @@ rsvd_status bcqr(BatchCtx &C, int count, rsvd_plan *const *Ps, int which, int pa
             CK(prod_tn<T>(P, rows, lp, src, lp, src, lp, (T *)P->G, lp));
         }
         CK(join(C, count, Ps));
-        CK(chol_inv_batched<T, T, T>(C.chol(rv + pass, count, true), count, lp, l, lp, C.bs));
+        const CholTab *tab = C.chol(rv + pass, count, true);
+        if constexpr (sizeof(T) == 4) {  // the float32 factorisation, and on a breakdown the float64 one (chol_pass)
+            CK(chol_inv_batched<float, float, float>(tab, count, lp, l, lp, C.bs, kCholFirst));
+            CK(gram64_fb_batched(C.g64(2 * which + pass, count, true), count, max_rows, l, lp, C.bs));
+        } else {  // float64: bases remove dependent columns (refilled below), T shifts (chol_pass)
+            CK(chol_inv_batched<T, T, T>(tab, count, lp, l, lp, C.bs, want_r ? kCholPlain : kCholDeflate));
+        }
         CK(fork(C, count, Ps));
         for (int i = 0; i < count; i++) {
             rsvd_plan *P = Ps[i];
@@ -1020,6 +1141,13 @@ rsvd_status bcqr(BatchCtx &C, int count, rsvd_plan *const *Ps, int which, int pa
             const T *src = pass == 0 ? X : Tmp;
             T *dst = (pass == passes - 1) ? Qo : Tmp;
             CK(prod_nn<T>(P, rows, lp, src, lp, (const T *)P->Rinv_c, lp, dst, lp));
+            if (sizeof(T) == 4 && passes == 2)
+                CK(rinv64_fb({(const float *)src, rows, lp, pass ? P->R2i : P->R1i, (float *)dst, P->fb}, l,
+                             P->stream));
+            if (sizeof(T) == 8 && !want_r) {
+                const rsvd_status rs = refill<T>(P, dst, rows, l, lp);
+                if (rs) return rs;
+            }
             if (pass == 1 && want_r) CK(trmm_upper(P->R2, P->R1, P->Rt, l, P->stream));
         }
     }
@@ -1031,7 +1159,7 @@ template <typename T>
 rsvd_status run_rsvd_batch(BatchCtx &C, int count, rsvd_plan *const *Ps, T *const *A, const T *const *Om,
                            double *const *S, T *const *U, T *const *V, bool capturing) {
     const int l = Ps[0]->l, lp = Ps[0]->lp, q = Ps[0]->q;
-    const double u = unit_roundoff<T>();
+    const double u = DBL_EPSILON / 2;  // shifts are applied in float64 only (chol_pass)
     CK(C.reserve(count));
     if (C.up_pending) {  // the previous upload must have read the host table before it is rewritten
         CK(cudaEventSynchronize(C.up));
@@ -1041,8 +1169,22 @@ rsvd_status run_rsvd_batch(BatchCtx &C, int count, rsvd_plan *const *Ps, T *cons
         rsvd_plan *P = Ps[i];
         for (int pass = 0; pass < 2; pass++) {
             double *R = pass ? P->R2 : P->R1, *Ri = pass ? P->R2i : P->R1i;
-            C.chol(pass, count, false)[i] = {P->G, R, Ri, P->Rinv_c, P->status, chol_shift_coef(P->m, l, u)};
-            C.chol(2 + pass, count, false)[i] = {P->G, R, Ri, P->Rinv_c, P->status, chol_shift_coef(P->n, l, u)};
+            C.chol(pass, count, false)[i] = {P->G, R, Ri, P->Rinv_c, P->status, chol_shift_coef(P->m, l, u),
+                                              P->G64, P->fb};
+            C.chol(2 + pass, count, false)[i] = {P->G, R, Ri, P->Rinv_c, P->status, chol_shift_coef(P->n, l, u),
+                                                  P->G64, P->fb};
+        }
+        if constexpr (sizeof(T) == 4) {  // the float64 Gram fallback of each (block, pass): its source block
+            const float *src[6] = {(const float *)P->Y, (const float *)P->Tmp, (const float *)P->Z,
+                                   (const float *)P->Tmpn, (const float *)P->Tn, (const float *)P->Tmpn};
+            for (int v = 0; v < 6; v++) {
+                const int64_t rows = v < 2 ? P->m : P->n;
+                const int pass = v & 1;
+                C.g64(v, count, false)[i] = {src[v],      rows,          lp,        P->g64part,
+                                             P->G64,      P->fb,         P->g64count, chol_shift_coef(rows, l, u),
+                                             pass ? P->R2 : P->R1, pass ? P->R2i : P->R1i, (float *)P->Rinv_c, lp,
+                                             P->status,   (double *)P->chol_ws};
+            }
         }
         C.jac(count, false)[i] = {P->Rt, P->sig, P->UR, P->Wm, P->status};
     }
@@ -1054,6 +1196,7 @@ rsvd_status run_rsvd_batch(BatchCtx &C, int count, rsvd_plan *const *Ps, T *cons
     CK(fork(C, count, Ps));
     for (int i = 0; i < count; i++) {  // means, padded Omega, sketch H(0) = A G with ||A||_F^2
         rsvd_plan *P = Ps[i];
+        P->nfact = 0;
         const bool centred = !(P->flags & RSVD_FLAG_NO_CENTER);
         if (centred) CK(column_means<T>(A[i], P->m, P->n, P->n, P->mu, (T *)P->mu_t, P->npad, P->cpart, P->stream));
         else CK(cudaMemsetAsync(P->mu, 0, sizeof(double) * P->n, P->stream));
@@ -1078,12 +1221,24 @@ rsvd_status run_rsvd_batch(BatchCtx &C, int count, rsvd_plan *const *Ps, T *cons
         }
         if ((st = bcqr<T>(C, count, Ps, BQ_Y, last ? 2 : 1, false))) return st;
     }
+    // orthonormality checks of the final bases (check_basis), per problem on its own stream
+    auto bcheck = [&](int which) -> rsvd_status {
+        for (int i = 0; i < count; i++) {
+            rsvd_plan *P = Ps[i];
+            const rsvd_status st = check_basis<T>(P, which == BQ_Y ? (const T *)P->Qb : (const T *)P->Qz,
+                                                  which == BQ_Y ? P->m : P->n, l, lp);
+            if (st) return st;
+        }
+        return RSVD_OK;
+    };
+    if ((st = bcheck(BQ_Y))) return st;
     for (int i = 0; i < count; i++) {  // T = A^T Q
         rsvd_plan *P = Ps[i];
         const T *mu = (P->flags & RSVD_FLAG_NO_CENTER) ? nullptr : (const T *)P->mu_t;
         CK(prod_tn<T>(P, P->m, P->n, A[i], P->n, (T *)P->Qb, lp, (T *)P->Tn, lp, mu));
     }
     if ((st = bcqr<T>(C, count, Ps, BQ_T, 2, true))) return st;  // T = Q_T R
+    if ((st = bcheck(BQ_T))) return st;
     CK(join(C, count, Ps));
     CK(jacobi_osvd_batched<T, T>(C.jac(count, true), count, l, lp, C.bs));
     CK(sv_refine_batched<T>(C.jac(count, true), count, l, lp, C.bs));
@@ -1114,9 +1269,10 @@ rsvd_status batch_direct(BatchCtx &C, int count, rsvd_plan *const *Ps, void *con
 
 // Maps the device status bits of a solve onto the ABI status.
 rsvd_status status_from_bits(int st) {
-    if (st & ST_CHOL) return RSVD_ERR_CHOL;
+    if (st & (ST_CHOL | ST_ORTH)) return RSVD_ERR_CHOL;
     if (st & ST_NOCONV) return RSVD_ERR_NOCONV;
     if (st & ST_TIMEOUT) return RSVD_ERR_TIMEOUT;
+    if (st & (ST_SHIFT | ST_RANKDEF)) return RSVD_WARN_RANK_DEFICIENT;
     return RSVD_OK;
 }
 
@@ -1274,7 +1430,7 @@ rsvd_status serve_batch_launch(ServeBatch *b, int count, rsvd_plan *const *plans
 
 rsvd_status serve_status(int bits, int reached) {
     const rsvd_status st = status_from_bits(bits);
-    return st == RSVD_OK && !reached ? RSVD_WARN_K_GT_k : st;
+    return st >= RSVD_OK && !reached ? RSVD_WARN_K_GT_k : st;  // errors first, then the K warning
 }
 
 }  // namespace gbr
@@ -1368,6 +1524,12 @@ rsvd_status rsvd_plan_destroy(rsvd_plan_t P) {
 }
 
 size_t rsvd_plan_workspace_bytes(rsvd_plan_t P) { return P ? P->ws_bytes : 0; }
+
+rsvd_status rsvd_set_jacobi_sweep_cap(int cap) {
+    if (cap < 0) return RSVD_ERR_ARG;
+    set_sweep_cap(cap);
+    return RSVD_OK;
+}
 
 rsvd_status rsvd_plan_set_flags(rsvd_plan_t P, unsigned flags) {
     if (!P || (flags & ~(unsigned)RSVD_FLAG_NO_CENTER)) return RSVD_ERR_ARG;
@@ -1530,7 +1692,7 @@ rsvd_status rsvd_batch_sync(rsvd_batch_t B, int *statuses) {
     for (size_t i = 0; i < B->plans.size(); i++) {
         const rsvd_status st = rsvd_plan_sync(B->plans[i]);
         if (statuses) statuses[i] = st;
-        if (st != RSVD_OK && worst == RSVD_OK) worst = st;
+        if ((st < RSVD_OK && worst >= RSVD_OK) || (st > RSVD_OK && worst == RSVD_OK)) worst = st;  // errors first
     }
     return worst;
 }
@@ -1714,6 +1876,7 @@ const char *rsvd_status_string(rsvd_status s) {
         case RSVD_ERR_CUDA: return "CUDA error";
         case RSVD_ERR_UNSUPPORTED: return "unsupported size or dtype";
         case RSVD_WARN_K_GT_k: return "threshold not reached within the returned values";
+        case RSVD_WARN_RANK_DEFICIENT: return "numerically rank-deficient input or basis (handled; bases checked)";
     }
     return "unknown status";
 }

@@ -118,7 +118,7 @@ def test_block_krylov_f32_hard_spectra(name):
     Om = synth.gaussian(n, b, seed=19065, dtype=torch.float32)
     k = 32
     r = _run_bk(A32, Om, k, b, iters, g.RSVD_F32, flags=g.RSVD_FLAG_NO_CENTER)
-    assert r["status"] == g.RSVD_OK
+    assert r["status"] in ((g.RSVD_OK, g.RSVD_WARN_RANK_DEFICIENT) if name == "rank20" else (g.RSVD_OK,))
     A64 = A32.double().numpy()
     s, _, _ = oracle.block_krylov(A64, Om.double(), iters, k)
     assert np.abs(r["S"] - s).max() <= 1e-5 * s[0]
