@@ -23,6 +23,17 @@ matrices of the paper's experiments), blocks of b = 96 columns, i = 2 (W = 288),
 k = 256, one step = one rsvd_block_krylov() solve; FLOPs per solve
     F = 2mnb(2i+1) + 2mnW + 2mW^2 + 2nW^2
 (the products with A, the QR of the m x W basis, the SVD of T).
+
+``--method gkl`` measures the Golub-Kahan-Lanczos path (HBM-bound): A 1048576 x
+2048 float32, sigma_i = exp(-i/200), 150 steps with full reorthogonalisation from
+a seeded unit v1, k = 100; metric: algorithmic HBM GB/s of the solve, bytes per
+solve = steps (8mn) + 8(m+n) steps (steps - 1) (two reads of A per step and the
+classical Gram-Schmidt passes over the growing bases, applied twice).
+
+``--method precision --dtype bf16|fp8`` measures the precision form: A 1048576 x
+4096 with sigma_i = i^-1.5 (Haar factors built in float32 on the device, a timing
+input) stored as bfloat16 or e4m3 with column scales by the library's quantiser;
+k = 256, p = 32, q = 3; metric: rSVD GFLOP/s as for the default workload.
 """
 from __future__ import annotations
 
@@ -40,6 +51,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "rpca_fp32_200000x1000"
+GKL_WORKLOAD = "gkl_fp32_1048576x2048"
+PREC_WORKLOAD = "mixed_rsvd_1048576x4096"
 BK_WORKLOAD = "block_krylov_fp32_gaussian_1048576x4096"
 BK = dict(m=1048576, n=4096, k=256, b=96, iters=2, seed_a=40971, seed_omega=40972)
 
@@ -303,6 +316,257 @@ def run_block_krylov(args):
     return 0
 
 
+def _timed_solves(step, args, dev, stream, world):
+    """Warm-up, then K timed solves between CUDA events with clock sampling (one rank's view)."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_1906_12085_gb300 as g
+    for _ in range(max(args.warmup, 0)):
+        step()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    launches0 = g.rsvd_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    launches = g.rsvd_launch_count() - launches0
+    clocks = sampler.stop()
+    return slowest_rank_ms(e0.elapsed_time(e1), world, dev), launches, clocks
+
+
+def _stage_profile(plan, step, steps):
+    """Per-stage CUDA-event durations over `steps` more solves (direct launches)."""
+    import paper_1906_12085_gb300 as g
+    g.rsvd_plan_profile(plan, True)
+    g.rsvd_plan_profile_read(plan)
+    for _ in range(steps):
+        step()
+    prof = g.rsvd_plan_profile_read(plan)
+    g.rsvd_plan_profile(plan, False)
+    return prof
+
+
+def _e2e(step, dev, stream, h2d, d2h, reps, work, unit):
+    """The same solve through the public API from pinned host buffers, copies inside the timed region."""
+    import torch
+    pins = [(d, d.cpu().pin_memory()) for d in h2d]
+    outs = [(d, torch.empty_like(d, device="cpu").pin_memory()) for d in d2h]
+    torch.cuda.synchronize(dev)
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(reps):
+        for d, h in pins:
+            d.copy_(h, non_blocking=True)
+        step()
+        for d, h in outs:
+            h.copy_(d, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize(dev)
+    ems = f0.elapsed_time(f1)
+    return {"value": work * reps / (ems * 1e-3) / 1e9, "unit": unit,
+            "h2d_bytes_per_step": sum(h.numel() * h.element_size() for _, h in pins),
+            "d2h_bytes_per_step": sum(h.numel() * h.element_size() for _, h in outs), "ms_per_step": ems / reps}
+
+
+def gkl_bytes(m, n, steps):
+    return steps * 8.0 * m * n + 8.0 * (m + n) * steps * (steps - 1)
+
+
+def run_gkl(args):
+    """One JSON line for the Golub-Kahan-Lanczos workload (HBM GB/s)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1906_12085_gb300 as g
+    import synth
+    from paper_1906_12085_gb300 import build as gbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    gbuild.build()
+    w = synth.WORKLOADS[GKL_WORKLOAD]
+    m, n, k, steps = w["m"], w["n"], w["k"], w["steps"]
+    A64, sigma, extras = synth.workload(GKL_WORKLOAD, device=dev)
+    A = A64.float().contiguous()
+    del A64
+    v1 = extras["v1"].to(dev)
+    S = torch.zeros(k, dtype=torch.float64, device=dev)
+    U = torch.zeros(m, k, dtype=torch.float32, device=dev)
+    V = torch.zeros(n, k, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    plan = g.rsvd_plan_create(m, n, k, 0, 0, g.RSVD_F32, stream)
+
+    def step():
+        g.check(g.svd_truncated_krylov(plan, A, v1, steps, S, U, V), "svd_truncated_krylov")
+
+    ms_max, launches, clocks = _timed_solves(step, args, dev, stream, world)
+    st = g.rsvd_plan_sync(plan)
+    nbytes = gkl_bytes(m, n, steps)
+    value = world * nbytes * args.steps / (ms_max * 1e-3) / 1e9
+    prof = _stage_profile(plan, step, args.steps)
+    pk, src = peaks()
+    hbm = float(pk.get("hbm_gbs", 6800.0))
+    # dominant GEMV of the step pair: A v (ax stage) or A^T u (atx stage), one launch per step each
+    dom = "ax" if prof["ax"][0] >= prof["atx"][0] else "atx"
+    per_launch_ms = prof[dom][0] / prof[dom][1]
+    achieved = 4.0 * m * n / (per_launch_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "gemv_n_kernel (A v)" if dom == "ax" else "gemv_t_kernel (A^T u)",
+                "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                "algorithmic_bytes_per_launch": 4.0 * m * n,
+                "solve_algorithmic_bytes": nbytes, "solve_frac": value / world / hbm,
+                "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback 6800 GB/s",
+                "stage_ms_per_step": {kk: vv[0] / args.steps for kk, vv in prof.items()},
+                "timing": "stage durations from CUDA events around each kernel group over an instrumented pass"}
+    e2e = _e2e(step, dev, stream, [A, v1], [S, U, V], 1, nbytes, "GB/s") if rank == 0 or world > 1 else None
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        rows = args.gkl_cpu_rows
+        a = np.ascontiguousarray(A[:rows].cpu().numpy().astype(np.float64))
+        t0 = time.perf_counter()
+        oracle.gkl(oracle.center(a)[0], v1.cpu().numpy().astype(np.float64), steps, k)
+        tsec = time.perf_counter() - t0
+        cpu = {"value": gkl_bytes(rows, n, steps) / tsec / 1e9, "unit": "GB/s", "cores": os.cpu_count(),
+               "kind": "oracle",
+               "sample": f"first {rows} of {m} rows (same n, steps, k, v1); FP64 C oracle, OpenMP, one solve"}
+    if rank == 0:
+        line = {"metric": "GKL HBM GB/s (algorithmic)", "value": value, "unit": "GB/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": GKL_WORKLOAD, "method": "gkl", "m": m, "n": n, "k": k, "lanczos_steps": steps,
+                           "l2": "inputs larger than L2 (A is 8.6 GB), no flush", "parallelism": f"replicas{world}"},
+                "solves_per_s": world * args.steps / (ms_max * 1e-3), "status": st,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks, "peaks_source": src}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_precision(args):
+    """One JSON line for the precision form (bfloat16 or e4m3 storage of A)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1906_12085_gb300 as g
+    import synth
+    from paper_1906_12085_gb300 import build as gbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    gbuild.build()
+    w = synth.WORKLOADS[PREC_WORKLOAD]
+    m, n, k, p, q = w["m"], w["n"], w["k"], w["p"], w["q"]
+    l = k + p
+    lp = -(-l // 16) * 16
+    dt = g.RSVD_BF16 if args.dtype == "bf16" else g.RSVD_FP8_E4M3
+    A32, sigma, extras = synth.workload(PREC_WORKLOAD, device=dev, dtype=torch.float32)
+    Om = extras["omega"].to(dev).contiguous()
+    sc = None
+    if dt == g.RSVD_BF16:
+        Aq = torch.empty(m, n, dtype=torch.int16, device=dev)
+        g.check(g.rsvd_quantize(A32, dt, Aq), "rsvd_quantize")
+    else:
+        Aq = torch.empty(m, n, dtype=torch.uint8, device=dev)
+        sc = torch.empty(n, dtype=torch.float32, device=dev)
+        g.check(g.rsvd_quantize(A32, dt, Aq, sc), "rsvd_quantize")
+    del A32
+    torch.cuda.empty_cache()
+    S = torch.zeros(k, dtype=torch.float64, device=dev)
+    U = torch.zeros(m, k, dtype=torch.float32, device=dev)
+    V = torch.zeros(n, k, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    plan = g.rsvd_plan_create(m, n, k, p, q, dt, stream)
+
+    def step():
+        g.check(g.rsvd(plan, Aq, sc, Om, S, U, V), "rsvd")
+
+    ms_max, launches, clocks = _timed_solves(step, args, dev, stream, world)
+    st = g.rsvd_plan_sync(plan)
+    flops = alg_flops(m, n, k, p, q)
+    value = job_gflops(world, flops, args.steps, ms_max)
+    prof = _stage_profile(plan, step, args.steps)
+    pk, src = peaks()
+    hbm = float(pk.get("hbm_gbs", 6800.0))
+    # the sketch and power products A Z (ax stage): q + 1 of them, each ceil(lp / 256) column
+    # slices of one pass over the stored A (2mn bytes bfloat16, mn e4m3)
+    esz = 2 if dt == g.RSVD_BF16 else 1
+    passes = (q + 1) * -(-lp // 256)
+    per_pass_ms = prof["ax"][0] / args.steps / passes
+    achieved = esz * m * n / (per_pass_ms * 1e-3) / 1e9
+    nslices = -(-lp // 256)
+    slice_n = -(-(-(-lp // nslices)) // 16) * 16   # width of one column slice
+    roofline = {"bound": "hbm", "kernel": "tc16_nn_kernel (A Z, kind::f16)" if esz == 2 else
+                "tc16_nn_kernel<e4m3> (A Z, kind::f8f6f4)",
+                "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                "algorithmic_bytes_per_launch": esz * float(m) * n, "passes_over_A_per_step_ax": passes,
+                "arithmetic_intensity_flop_per_byte": 2.0 * slice_n / esz,
+                "tensor": {"achieved_tflops": 2.0 * m * n * slice_n / (per_pass_ms * 1e-3) / 1e12,
+                           "peak_bf16_tflops": float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1900.0)))},
+                "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback 6800 GB/s",
+                "stage_ms_per_step": {kk: vv[0] / args.steps for kk, vv in prof.items()},
+                "timing": "stage durations from CUDA events around each kernel group over an instrumented pass; "
+                          "per pass over A = ax stage time / passes"}
+    e2e = None
+    if rank == 0 or world > 1:
+        e2e = _e2e(step, dev, stream, [Aq, Om] + ([sc] if sc is not None else []), [S, U, V], 1, flops,
+                   "GFLOP/s")
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        rows = args.prec_cpu_rows
+        codes = Aq[:rows].cpu().numpy()
+        a = (oracle.dequantize_bf16(codes.view(np.uint16)) if esz == 2
+             else oracle.dequantize_e4m3(codes, sc.cpu().numpy()))
+        om = Om.cpu().numpy().astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.rsvd(oracle.center(a)[0], om, q=q, k=k)
+        tsec = time.perf_counter() - t0
+        cpu = {"value": alg_flops(rows, n, k, p, q) / tsec / 1e9, "unit": "GFLOP/s", "cores": os.cpu_count(),
+               "kind": "oracle",
+               "sample": f"first {rows} of {m} rows of the stored matrix, dequantised (same n, k, p, q, Omega); "
+                         f"FP64 C oracle, OpenMP, one solve"}
+    if rank == 0:
+        line = {"metric": "rSVD GFLOP/s", "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+                "config": {"workload": PREC_WORKLOAD, "method": "precision", "storage": args.dtype, "m": m, "n": n,
+                           "k": k, "p": p, "q": q, "l2": f"inputs larger than L2 (A is {esz * m * n / 1e9:.1f} GB), "
+                                                          f"no flush", "parallelism": f"replicas{world}"},
+                "solves_per_s": world * args.steps / (ms_max * 1e-3), "status": st,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks, "peaks_source": src}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -497,9 +761,13 @@ def main():
     ap.add_argument("--sample-rows", type=int, default=40000, help="rows per reference-arm step")
     ap.add_argument("--cpu-baseline-rows", type=int, default=100000, help="rows of the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--method", default="rsvd", choices=["rsvd", "block_krylov"],
-                    help="rsvd: the default workload; block_krylov: the Sec. 3.1.1 workload")
+    ap.add_argument("--method", default="rsvd", choices=["rsvd", "block_krylov", "gkl", "precision"],
+                    help="rsvd: the default workload; block_krylov: the Sec. 3.1.1 workload; gkl: the Lanczos "
+                         "workload; precision: the bfloat16 / e4m3 precision form (--dtype)")
+    ap.add_argument("--dtype", default="bf16", choices=["bf16", "fp8"], help="storage of --method precision")
     ap.add_argument("--bk-cpu-rows", type=int, default=16384, help="rows of the block Krylov cpu_baseline sample")
+    ap.add_argument("--gkl-cpu-rows", type=int, default=16384, help="rows of the Lanczos cpu_baseline sample")
+    ap.add_argument("--prec-cpu-rows", type=int, default=8192, help="rows of the precision-form cpu_baseline sample")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -507,6 +775,10 @@ def main():
         return run_reference(args)
     if args.method == "block_krylov":
         return run_block_krylov(args)
+    if args.method == "gkl":
+        return run_gkl(args)
+    if args.method == "precision":
+        return run_precision(args)
     return run_ours(args)
 
 

@@ -49,6 +49,16 @@ constexpr int kGklMaxStepsF32 = 160;
 void note_launch(int count = 1);
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+// generators", OOPSLA 2014): the finaliser applied to seed + (i + 1) * gamma.  The
+// counter-based source of the columns that replace removed basis directions.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
 inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
 
 // ---------------------------------------------------------------- centring
@@ -102,17 +112,20 @@ int64_t gemm_tn_partials(int64_t rows, int64_t N, int64_t L);
 //                   CholeskyQR, ST_SHIFT); on a second breakdown set ST_CHOL and return
 //                   R = 0, R^{-1} = I;
 //   kCholFirst    : a float64 fallback follows: write *fb = 1 and leave R, Rinv and
-//                   Rinv_c to it; on success write *fb = 0;
+//                   Rinv_c to it; on success write *fb = 0.  With float32 arithmetic and a
+//                   scratch of chol_scratch_bytes(l, 8) bytes, a breakdown is first retried
+//                   in float64 on the same G (kCholRetry, in the scratch), and *fb = 1 only
+//                   when that breaks down too;
 //   kCholFallback : return at once unless *fb is set; otherwise as kCholPlain (G is then
 //                   the float64 Gram matrix of gram64_fb);
 //   kCholDeflate  : never shift: a pivot <= kDeflateRel l G_kk (G_kk the diagonal of G)
 //                   removes column k -- R_kk = 1, the rest of row and column k of R zero --
-//                   and sets fb[k] = 1 (fb: l ints, cleared first); X R^{-1} then keeps
-//                   column k of X, which the caller replaces (float64 bases).
+//                   and sets fb[k] = 1 and fb[l] = 1 (fb: l + 1 ints, cleared first); X R^{-1}
+//                   then keeps column k of X, which the caller replaces.
 // Matrices whose two l x l blocks exceed one SM's shared memory (l > 112 in float64,
 // l > 128 in float32) live in `scratch` (chol_scratch_bytes(l, sizeof(Tk)) bytes of
 // device memory), which may be NULL otherwise.
-enum CholRole : int { kCholPlain = 0, kCholFirst = 1, kCholFallback = 2, kCholDeflate = 3 };
+enum CholRole : int { kCholPlain = 0, kCholFirst = 1, kCholFallback = 2, kCholDeflate = 3, kCholRetry = 4 };
 // relative pivot below which kCholDeflate removes a column, per column of the block: the
 // float64 unit roundoff, i.e. a column whose squared distance from the span of the previous
 // ones is below l u of its squared norm, the rounding level of its float64 Gram matrix
@@ -127,9 +140,10 @@ size_t chol_scratch_bytes(int l, size_t tk);
 // float64 Gram matrix G (l x l upper triangle, ldg) = X^T X of X rows x l (ld, float32), every
 // product and sum in float64 (CUDA cores), split over row chunks into `part`
 // (gram64_partials(rows, l) doubles) and summed in chunk order by the last CTA (`count`: a
-// zeroed counter of the job, left zero), which then factors G as chol_inv does with role
-// kCholFallback (R, Rinv, Rc, lp, status, shift coefficient `coef`), its matrices in the
-// global scratch gws (chol_scratch_bytes(l, 8) bytes).  Returns at once unless *fb is set.
+// zeroed counter of the job, left zero), which then factors G as chol_inv does with `role`
+// kCholFallback (shift; R, Rinv, Rc, lp, status, shift coefficient `coef`) or kCholDeflate
+// (removed columns flagged in dflag, l ints), its matrices in the global scratch gws
+// (chol_scratch_bytes(l, 8) bytes).  Returns at once unless *fb is set.
 struct G64Job {
     const float *X;
     int64_t rows, ld;
@@ -142,20 +156,28 @@ struct G64Job {
     int lp;
     int *status;
     double *gws;
+    int role;
+    int *dflag;
 };
 int64_t gram64_partials(int64_t rows, int l);
 cudaError_t gram64_fb(const G64Job &job, int l, int64_t ldg, cudaStream_t s);
 // the same for `count` jobs of one l (device table, one launch)
 cudaError_t gram64_fb_batched(const G64Job *tab, int count, int64_t max_rows, int l, int64_t ldg, cudaStream_t s);
-// The basis of a fallback pass: Q (rows x l, ld, float32) = X R^{-1} with float64 products and
-// sums (Rinv: float64 l x l upper triangular, ld l), rounded once; returns at once unless
-// *fb is set.  X and Q must not overlap.
+// The basis of a fallback pass: Q (rows x l, ld, float32) = X R^{-1} to ~2^-48 relative
+// (Rinv: float64 l x l upper triangular, ld l), rounded once; the columns flagged in dflag
+// (may be NULL) are replaced by uniform entries in [-sqrt(3/rows), sqrt(3/rows)) from
+// SplitMix64 with `seed` (as bk_fill).  Returns at once unless *fb is set and, when `need`
+// is given, *need too (an intermediate basis: only when a column was removed).  X and Q
+// must not overlap.
 struct Rinv64Job {
     const float *X;
     int64_t rows, ld;
     const double *Rinv;
     float *Q;
     const int *fb;
+    const int *dflag;
+    uint64_t seed;
+    const int *need;
 };
 cudaError_t rinv64_fb(const Rinv64Job &job, int l, cudaStream_t s);
 
@@ -256,6 +278,7 @@ struct CholTab {
     double coef;       // chol_shift_coef(rows, l, u) of the arithmetic that may shift
     const double *G64; // float64 Gram matrix of the fallback (kCholFallback), or NULL
     int *fb;           // fallback flag (kCholFirst / kCholFallback), or NULL
+    double *ws64;      // scratch of the float64 retry of kCholFirst (chol_scratch_bytes(l, 8)), or NULL
 };
 struct JacTab {
     const double *R;   // l x l

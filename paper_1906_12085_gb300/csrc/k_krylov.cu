@@ -35,15 +35,6 @@ __global__ void svqb_scale_kernel(const double *__restrict__ lam, const double *
     }
 }
 
-// SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
-// generators", OOPSLA 2014): the finaliser applied to seed + (i + 1) * gamma.
-__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t i) {
-    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
 // X[r, c] = scale * (2 u - 1), u uniform in [0, 1) from counter r * lp + c, for
 // the flagged columns c < l of X (m x lp, ld lp).
 template <typename T>

@@ -145,11 +145,18 @@ __device__ __forceinline__ CholSmem<Tk> chol_smem(int LL, Tk *gws) {
     return m;
 }
 
+// The float64 retry of a float32 first attempt (kCholRetry), kept out of line so that the
+// float32 kernels' own code is generated as if it were absent.
+template <typename TG, typename Tc>
+__device__ __noinline__ void chol_retry64(const TG *G, int64_t ldg, int l, double shift_coef, double *R, double *Rinv,
+                                          Tc *Rinv_c, int lp, int *status, double *ws64, int *fb);
+
 template <typename TG, typename Tk, typename Tc, bool GM = false>
 __device__ __forceinline__ void chol_inv_body(const TG *__restrict__ G, int64_t ldg, int l, double shift_coef,
                                               double *__restrict__ R, double *__restrict__ Rinv,
                                               Tc *__restrict__ Rinv_c, int lp, int *__restrict__ status,
-                                              Tk *gws = nullptr, int *fb = nullptr, int role = kCholPlain) {
+                                              Tk *gws = nullptr, int *fb = nullptr, int role = kCholPlain,
+                                              double *ws64 = nullptr) {
     // GM: the matrices, the pivots and the breakdown flag in the global scratch, the work
     // shared by the CTAs of a cluster (cluster barriers between the phases)
     using Sync = typename std::conditional<GM, ClusterSync, CtaSync>::type;
@@ -157,7 +164,7 @@ __device__ __forceinline__ void chol_inv_body(const TG *__restrict__ G, int64_t 
     if (role == kCholFallback && *reinterpret_cast<volatile int *>(fb) == 0) return;
     // kCholDeflate (float64 only, compiled out of the other forms): pivots <= tau G_kk remove
     // their column (flags in fb[0..l-1])
-    constexpr bool kCanDeflate = std::is_same<Tk, double>::value && std::is_same<Tc, double>::value;
+    constexpr bool kCanDeflate = std::is_same<Tk, double>::value;
     const bool deflate = kCanDeflate && role == kCholDeflate;
     const double tau = deflate ? kDeflateRel * l : 0.0;
     const int NP = (l + 15) >> 4, LL = 16 * NP;
@@ -177,8 +184,8 @@ __device__ __forceinline__ void chol_inv_body(const TG *__restrict__ G, int64_t 
     const int rank = Sync::rank(), nct = Sync::size();
     const int gt = rank * 256 + tid, gnt = nct * 256;
     int used = 0;  // 0: plain, 1: shifted, 2: breakdown fallback (R = 0, R^{-1} = I)
-    if (deflate)
-        for (int i = gt; i < l; i += gnt) fb[i] = 0;
+    if (deflate)  // the flags and, after them, the word that says whether any column was removed
+        for (int i = gt; i <= l; i += gnt) fb[i] = 0;
     for (int attempt = 0; attempt < 3; attempt++) {
         if (attempt == 1 && rank == 0 && warp == 0) {  // trace for the shift (only after a breakdown)
             double tr = 0.0;
@@ -221,6 +228,7 @@ __device__ __forceinline__ void chol_inv_body(const TG *__restrict__ G, int64_t 
                             rdiag[o + k] = rinv;
                             if (dep && o + k < l) {
                                 fb[o + k] = 1;
+                                fb[l] = 1;
                                 atomicOr(status, (int)ST_RANKDEF);
                             }
                         }
@@ -307,13 +315,24 @@ __device__ __forceinline__ void chol_inv_body(const TG *__restrict__ G, int64_t 
             used = attempt;
             break;
         }
-        if (role == kCholFirst) {  // breakdown: the float64 Gram matrix and Cholesky take over
+        if (role == kCholFirst || role == kCholRetry) {
+            if constexpr (!std::is_same<Tk, double>::value) {
+                // the float32 arithmetic broke down (its rounding, ~l u of the pivots, can exceed a
+                // small positive pivot): factor the same Gram matrix again in float64, in the
+                // global scratch, with the CTAs of this launch
+                if (ws64) {
+                    Sync::sync();
+                    chol_retry64<TG, Tc>(G, ldg, l, shift_coef, R, Rinv, Rinv_c, lp, status, ws64, fb);
+                    return;
+                }
+            }
+            // breakdown: the float64 Gram matrix and Cholesky take over
             if (rank == 0 && tid == 0) *fb = 1;
             return;
         }
         Sync::sync();
     }
-    if (role == kCholFirst && rank == 0 && tid == 0) *fb = 0;
+    if ((role == kCholFirst || role == kCholRetry) && rank == 0 && tid == 0) *fb = 0;
     if (kCanDeflate && deflate) {  // a removed column: zero above the diagonal, unit pivot for the inverse
         for (int idx = gt; idx < LL * LL; idx += gnt) {
             const int i = idx / LL, j = idx % LL;
@@ -368,10 +387,21 @@ __device__ __forceinline__ void chol_inv_body(const TG *__restrict__ G, int64_t 
     }
 }
 
+template <typename TG, typename Tc>
+__device__ __noinline__ void chol_retry64(const TG *G, int64_t ldg, int l, double shift_coef, double *R, double *Rinv,
+                                          Tc *Rinv_c, int lp, int *status, double *ws64, int *fb) {
+    chol_inv_body<TG, double, Tc, true>(G, ldg, l, shift_coef, R, Rinv, Rinv_c, lp, status, ws64, fb, kCholRetry);
+}
+
 // ------------------------------------------------ float64 Gram of a float32 block
 // 64 x 64 output tiles of the upper triangle (tile pairs ti <= tj), row chunks split over
-// gridDim.y; each CTA stages 32 rows of both column tiles in shared memory as float64
-// and accumulates 4 x 4 outputs per thread in row order.
+// gridDim.y; each CTA stages 32 rows of both column tiles in shared memory and accumulates
+// 4 x 4 outputs per thread in row order.  The sums are float-float pairs on the FP32 units
+// (GB300's float64 rate is ~1/58 of its float32 rate): every product of two float32 values
+// is split exactly into p + e (p = fl(ab), e = fma(a, b, -p)), p is added to the running
+// sum by an error-free two-sum (Knuth) and the errors are gathered in a second float32
+// word: ~2^-48 relative per sum, like a float64 accumulation.  Intrinsics with explicit
+// rounding keep the compiler from fusing the steps.
 constexpr int G64_TILE = 64, G64_ROWS = 32;
 
 struct G64Split {
@@ -400,6 +430,18 @@ __host__ __device__ inline G64Split g64_split(int64_t rows, int l) {
 // The CTAs of one job count themselves out on J.count; the last one sums the partials in
 // chunk order into G (deterministic), resets the counter and factors G in float64 (the
 // Cholesky body with its matrices in the global scratch J.gws, one CTA).
+// (hi, lo) += a b: the product split exactly (p + e), p added by an error-free two-sum, the
+// rounding errors gathered in lo (explicit rounding intrinsics: no contraction)
+__device__ __forceinline__ void ff_madd(float &hi, float &lo, float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);
+    const float t = __fadd_rn(hi, p);
+    const float bp = __fsub_rn(t, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    hi = t;
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
+
 template <bool TAB>
 __global__ void __launch_bounds__(256) gram64_kernel(G64Job job, const G64Job *__restrict__ tab, int l, int64_t ldg) {
     const G64Job J = TAB ? tab[blockIdx.z] : job;
@@ -414,13 +456,13 @@ __global__ void __launch_bounds__(256) gram64_kernel(G64Job job, const G64Job *_
         ti++;
     }
     const int tj = ti + p;
-    __shared__ double xa[G64_ROWS][G64_TILE + 1], xb[G64_ROWS][G64_TILE + 1];
+    __shared__ float xa[G64_ROWS][G64_TILE + 1], xb[G64_ROWS][G64_TILE + 1];
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-    double acc[4][4];
+    float sh[4][4], sl[4][4];  // float-float sums: value sh + sl
 #pragma unroll
     for (int i = 0; i < 4; i++)
 #pragma unroll
-        for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+        for (int j = 0; j < 4; j++) sh[i][j] = sl[i][j] = 0.f;
     const int64_t rb = chunk * sp.rpc, re = min(J.rows, rb + sp.rpc);
     for (int64_t r0 = rb; r0 < re; r0 += G64_ROWS) {
 #pragma unroll
@@ -428,13 +470,13 @@ __global__ void __launch_bounds__(256) gram64_kernel(G64Job job, const G64Job *_
             const int e = tid + 256 * v, rr = e / G64_TILE, cc = e % G64_TILE;
             const int64_t gr = r0 + rr;
             const int ca = G64_TILE * ti + cc, cb = G64_TILE * tj + cc;
-            xa[rr][cc] = (gr < re && ca < l) ? (double)J.X[gr * J.ld + ca] : 0.0;
-            xb[rr][cc] = (gr < re && cb < l) ? (double)J.X[gr * J.ld + cb] : 0.0;
+            xa[rr][cc] = (gr < re && ca < l) ? J.X[gr * J.ld + ca] : 0.f;
+            xb[rr][cc] = (gr < re && cb < l) ? J.X[gr * J.ld + cb] : 0.f;
         }
         __syncthreads();
-#pragma unroll 4
+#pragma unroll 2
         for (int k = 0; k < G64_ROWS; k++) {
-            double a[4], b[4];
+            float a[4], b[4];
 #pragma unroll
             for (int i = 0; i < 4; i++) a[i] = xa[k][ty * 4 + i];
 #pragma unroll
@@ -442,7 +484,7 @@ __global__ void __launch_bounds__(256) gram64_kernel(G64Job job, const G64Job *_
 #pragma unroll
             for (int i = 0; i < 4; i++)
 #pragma unroll
-                for (int j = 0; j < 4; j++) acc[i][j] = __fma_rn(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < 4; j++) ff_madd(sh[i][j], sl[i][j], a[i], b[j]);
         }
         __syncthreads();
     }
@@ -452,7 +494,8 @@ __global__ void __launch_bounds__(256) gram64_kernel(G64Job job, const G64Job *_
     for (int i = 0; i < 4; i++)
 #pragma unroll
         for (int j = 0; j < 4; j++)
-            out[(int64_t)(G64_TILE * ti + ty * 4 + i) * LT + G64_TILE * tj + tx * 4 + j] = acc[i][j];
+            out[(int64_t)(G64_TILE * ti + ty * 4 + i) * LT + G64_TILE * tj + tx * 4 + j] =
+                (double)sh[i][j] + (double)sl[i][j];
     // G[i][j] (i <= j < l) = sum of the chunk partials in chunk order, by the last CTA
     __shared__ bool last;
     __threadfence();
@@ -473,17 +516,20 @@ __global__ void __launch_bounds__(256) gram64_kernel(G64Job job, const G64Job *_
     __threadfence();
     __syncthreads();
     chol_inv_body<double, double, float, true>(J.G, ldg, l, J.coef, J.R, J.Rinv, J.Rc, J.lp, J.status, J.gws,
-                                               const_cast<int *>(J.fb), kCholFallback);
+                                               J.role == kCholDeflate ? J.dflag : const_cast<int *>(J.fb), J.role);
 }
 
-// Q (rows x l, ld) = X R^{-1} in float64 products and sums, rounded once to float32; Rinv the
-// float64 l x l upper-triangular inverse (ld l).  64 x 64 output tiles over a fixed grid;
-// the K range of a tile stops at its last column (Rinv is upper triangular).
+// Q (rows x l, ld) = X R^{-1} to ~2^-48 relative, rounded once to float32; Rinv the float64
+// l x l upper-triangular inverse (ld l), split into float32 words rh + rl.  Float-float sums
+// as in gram64_kernel: x rh exactly as p + e, x rl rounded (its error is 2^-48 of the
+// term).  64 x 64 output tiles over a fixed grid; the K range of a tile stops at its last
+// column (Rinv is upper triangular).
 template <bool TAB>
 __global__ void __launch_bounds__(256) rinv64_kernel(Rinv64Job job, const Rinv64Job *__restrict__ tab, int l) {
     const Rinv64Job J = TAB ? tab[blockIdx.z] : job;
     if (*reinterpret_cast<const volatile int *>(J.fb) == 0) return;
-    __shared__ double xs[G64_TILE][G64_ROWS + 1], rs[G64_ROWS][G64_TILE + 1];
+    if (J.need && *reinterpret_cast<const volatile int *>(J.need) == 0) return;
+    __shared__ float xs[G64_TILE][G64_ROWS + 1], rsh[G64_ROWS][G64_TILE + 1], rsl[G64_ROWS][G64_TILE + 1];
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
     const int ct = (l + G64_TILE - 1) / G64_TILE;
     const int64_t rt = (J.rows + G64_TILE - 1) / G64_TILE;
@@ -491,33 +537,42 @@ __global__ void __launch_bounds__(256) rinv64_kernel(Rinv64Job job, const Rinv64
         const int64_t r0 = (t / ct) * G64_TILE;
         const int c0 = (int)(t % ct) * G64_TILE;
         const int kend = min(l, c0 + G64_TILE);
-        double acc[4][4];
+        float sh[4][4], sl[4][4];
 #pragma unroll
         for (int i = 0; i < 4; i++)
 #pragma unroll
-            for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+            for (int j = 0; j < 4; j++) sh[i][j] = sl[i][j] = 0.f;
         for (int k0 = 0; k0 < kend; k0 += G64_ROWS) {
 #pragma unroll
             for (int v = 0; v < G64_TILE * G64_ROWS / 256; v++) {
                 const int e = tid + 256 * v;
                 const int xr = e / G64_ROWS, xk = e % G64_ROWS;  // X tile: 64 rows x 32 k
                 const int64_t gr = r0 + xr;
-                xs[xr][xk] = (gr < J.rows && k0 + xk < l) ? (double)J.X[gr * J.ld + k0 + xk] : 0.0;
+                xs[xr][xk] = (gr < J.rows && k0 + xk < l) ? J.X[gr * J.ld + k0 + xk] : 0.f;
                 const int rk = e / G64_TILE, rc = e % G64_TILE;  // Rinv tile: 32 k x 64 cols
-                rs[rk][rc] = (k0 + rk < l && c0 + rc < l) ? J.Rinv[(int64_t)(k0 + rk) * l + c0 + rc] : 0.0;
+                const double r = (k0 + rk < l && c0 + rc < l) ? J.Rinv[(int64_t)(k0 + rk) * l + c0 + rc] : 0.0;
+                const float rh = __double2float_rn(r);
+                rsh[rk][rc] = rh;
+                rsl[rk][rc] = __double2float_rn(r - (double)rh);
             }
             __syncthreads();
-#pragma unroll 4
+#pragma unroll 2
             for (int k = 0; k < G64_ROWS; k++) {
-                double a[4], b[4];
+                float a[4], bh[4], bl[4];
 #pragma unroll
                 for (int i = 0; i < 4; i++) a[i] = xs[ty * 4 + i][k];
 #pragma unroll
-                for (int j = 0; j < 4; j++) b[j] = rs[k][tx * 4 + j];
+                for (int j = 0; j < 4; j++) {
+                    bh[j] = rsh[k][tx * 4 + j];
+                    bl[j] = rsl[k][tx * 4 + j];
+                }
 #pragma unroll
                 for (int i = 0; i < 4; i++)
 #pragma unroll
-                    for (int j = 0; j < 4; j++) acc[i][j] = __fma_rn(a[i], b[j], acc[i][j]);
+                    for (int j = 0; j < 4; j++) {
+                        ff_madd(sh[i][j], sl[i][j], a[i], bh[j]);
+                        sl[i][j] = __fmaf_rn(a[i], bl[j], sl[i][j]);
+                    }
             }
             __syncthreads();
         }
@@ -528,7 +583,13 @@ __global__ void __launch_bounds__(256) rinv64_kernel(Rinv64Job job, const Rinv64
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 const int c = c0 + tx * 4 + j;
-                if (c < l) J.Q[r * J.ld + c] = (float)acc[i][j];
+                if (c >= l) continue;
+                if (J.dflag && J.dflag[c]) {  // a removed column: pseudo-random entries (as bk_fill)
+                    const double u01 = (double)(splitmix64(J.seed, (uint64_t)(r * J.ld + c)) >> 11) * 0x1.0p-53;
+                    J.Q[r * J.ld + c] = (float)(sqrt(3.0 / (double)J.rows) * (2.0 * u01 - 1.0));
+                } else {
+                    J.Q[r * J.ld + c] = __double2float_rn((double)sh[i][j] + (double)sl[i][j]);
+                }
             }
         }
     }
@@ -540,8 +601,8 @@ __global__ void __launch_bounds__(256, 1) chol_inv_kernel(const TG *__restrict__
                                                           double shift_coef, double *__restrict__ R,
                                                           double *__restrict__ Rinv, Tc *__restrict__ Rinv_c, int lp,
                                                           int *__restrict__ status, Tk *__restrict__ gws, int *fb,
-                                                          int role) {
-    chol_inv_body<TG, Tk, Tc, GM>(G, ldg, l, shift_coef, R, Rinv, Rinv_c, lp, status, gws, fb, role);
+                                                          int role, double *ws64) {
+    chol_inv_body<TG, Tk, Tc, GM>(G, ldg, l, shift_coef, R, Rinv, Rinv_c, lp, status, gws, fb, role, ws64);
 }
 
 // One CTA per problem of a batch; problem b's pointers and shift are tab[b] (the fallback
@@ -552,7 +613,7 @@ __global__ void __launch_bounds__(256, 1) chol_inv_batch_kernel(const CholTab *_
     const CholTab t = tab[blockIdx.x];
     const TG *G = static_cast<const TG *>(role == kCholFallback ? static_cast<const void *>(t.G64) : t.G);
     chol_inv_body<TG, Tk, Tc>(G, ldg, l, t.coef, t.R, t.Rinv, static_cast<Tc *>(t.Rc), lp, t.status, nullptr, t.fb,
-                              role);
+                              role, t.ws64);
 }
 
 // ST_ORTH when max_{i <= j < l} |G_ij - delta_ij| > tol (or not a number): one CTA.
@@ -1197,6 +1258,8 @@ template <typename TG, typename Tk, typename Tc>
 cudaError_t chol_inv(const TG *G, int64_t ldg, int l, int64_t rows, double u, double *R, double *Rinv, Tc *Rinv_c,
                      int lp, int *status, cudaStream_t s, void *scratch, int *fb, int role) {
     if (role != kCholPlain && !fb) return cudaErrorInvalidValue;
+    // the float64 retry of a float32 first attempt: the scratch holds a float64 l x l pair
+    double *ws64 = (role == kCholFirst && sizeof(Tk) == 4) ? static_cast<double *>(scratch) : nullptr;
     const double coef = chol_shift_coef(rows, l, u);
     size_t smem = chol_smem_bytes<Tk>(l);
     Tk *gws = nullptr;
@@ -1219,12 +1282,12 @@ cudaError_t chol_inv(const TG *G, int64_t ldg, int l, int64_t rows, double u, do
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         cudaLaunchKernelEx(&cfg, chol_inv_kernel<TG, Tk, Tc, true>, G, ldg, l, coef, R, Rinv, Rinv_c, lp, status, gws,
-                           fb, role);
+                           fb, role, ws64);
     } else {
         cudaFuncSetAttribute(chol_inv_kernel<TG, Tk, Tc, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
         chol_inv_kernel<TG, Tk, Tc, false><<<1, 256, smem, s>>>(G, ldg, l, coef, R, Rinv, Rinv_c, lp, status, nullptr,
-                                                                fb, role);
+                                                                fb, role, ws64);
     }
     note_launch();
     return cudaGetLastError();

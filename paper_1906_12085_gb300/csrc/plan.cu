@@ -56,7 +56,8 @@ struct rsvd_plan {
     int *status = nullptr, *Kdev = nullptr;
     // CholeskyQR fallback of the float32 bases: breakdown flag of the current factorisation and
     // the split-K partials of the float64 Gram matrix (not used by float64 plans)
-    int *fb = nullptr;             // float64 plans: the removed-column flags of kCholDeflate (lpc ints)
+    int *fb = nullptr;             // fallback flag of the current factorisation (float32 bases)
+    int *dflag = nullptr;          // columns removed by kCholDeflate in the current factorisation (sq ints)
     double *g64part = nullptr;
     unsigned *g64count = nullptr;  // CTA counter of the float64 Gram reduction (kept zero between uses)
     uint64_t nfact = 0;            // factorisations of the current solve (seeds of the column refills)
@@ -178,7 +179,8 @@ void carve(rsvd_plan *P, Carver &c) {
     P->sig = (double *)c.take(sizeof(double) * (n > sq ? n : sq));
     P->status = (int *)c.take(sizeof(int));
     P->Kdev = (int *)c.take(2 * sizeof(int));
-    P->fb = (int *)c.take(sizeof(int) * sq);
+    P->fb = (int *)c.take(sizeof(int));
+    P->dflag = (int *)c.take(sizeof(int) * (sq + 1));
     if (P->dtype != RSVD_F64) {  // float64 Gram partials of the widest block the factorisations see
         const int wmax = (int)sq;
         int64_t ge = 0;
@@ -360,12 +362,19 @@ cudaError_t prod_tn(rsvd_plan *P, int64_t rows, int64_t ncols, const T *X, int64
 // columns).  The basis of such a pass is then formed as X R^{-1} in float64 too (rinv64_fb in
 // cqr), so its error no longer grows with cond(X) times the product's rounding.  The
 // fallback launches return at once when the first factorisation succeeded.
+// A float32 Cholesky that breaks down is first retried in float64 arithmetic on the same
+// float32 Gram matrix (inside the same launch): its rounding, ~l u32 relative to the pivots,
+// exceeds the small positive pivots of moderately conditioned bases at large l (measured:
+// pivot 263 of 288 at -2.2e-5 G_kk on the 1048576 x 4096 i^-1.5 sketch), which the float64
+// arithmetic resolves; only a Gram matrix that is itself indefinite reaches the float64 Gram.
 // Float64 bases whose R is not kept (deflate): columns with a pivot below l u64 of their
 // squared norm are removed (kCholDeflate) and refilled by the caller; a factorisation whose R
 // is kept (T, and A in svd_exact) shifts instead.
 template <typename T>
 rsvd_status chol_pass(rsvd_plan *P, const T *X, int64_t rows, int w, int ld, bool f64, double *R, double *Ri,
                       T *Ric, bool deflate) {
+    // float32 bases whose R is not kept: the float64 fallback removes dependent columns
+    // (kCholDeflate; rinv64_fb refills them) instead of shifting
     cudaStream_t s = P->stream;
     const double u64 = DBL_EPSILON / 2;
     if constexpr (sizeof(T) == 4) {
@@ -376,23 +385,25 @@ rsvd_status chol_pass(rsvd_plan *P, const T *X, int64_t rows, int w, int ld, boo
         else CK(chol_inv<float, float, float>(G, ld, w, rows, u64, R, Ri, Ric, ld, P->status, s, P->chol_ws, P->fb,
                                               kCholFirst));
         const G64Job job = {X,  rows, ld,  P->g64part, P->G64,    P->fb, P->g64count, chol_shift_coef(rows, w, u64),
-                            R,  Ri,   Ric, ld,         P->status, (double *)P->chol_ws};
+                            R,  Ri,   Ric, ld,         P->status, (double *)P->chol_ws, deflate ? kCholDeflate : kCholFallback,
+                            P->dflag};
         CK(gram64_fb(job, w, ld, s));  // float64 Gram matrix and Cholesky, after a breakdown only
     } else {
         CK(chol_inv<double, double, double>((const double *)P->G, ld, w, rows, u64, R, Ri, Ric, ld, P->status, s,
-                                            P->chol_ws, deflate ? P->fb : nullptr,
+                                            P->chol_ws, deflate ? P->dflag : nullptr,
                                             deflate ? kCholDeflate : kCholPlain));
     }
     return RSVD_OK;
 }
 
-// The columns of a float64 basis that kCholDeflate removed (P->fb) are replaced by pseudo-
+uint64_t refill_seed(rsvd_plan *P) { return 0x2D0C4A5E1ull + 0x9E3779B97F4A7C15ull * ++P->nfact; }
+
+// The columns of a float64 basis that kCholDeflate removed (P->dflag) are replaced by pseudo-
 // random ones (SplitMix64 from a per-factorisation seed), which the next CholeskyQR pass
 // orthonormalises against the rest.
 template <typename T>
 rsvd_status refill(rsvd_plan *P, T *Q, int64_t rows, int w, int ld) {
-    if constexpr (sizeof(T) == 8) CK(bk_fill<T>(Q, rows, w, ld, P->fb, 0x2D0C4A5E1ull + 0x9E3779B97F4A7C15ull * ++P->nfact,
-                                                P->stream));
+    if constexpr (sizeof(T) == 8) CK(bk_fill<T>(Q, rows, w, ld, P->dflag, refill_seed(P), P->stream));
     return RSVD_OK;
 }
 
@@ -429,21 +440,26 @@ rsvd_status cqr(rsvd_plan *P, const T *X, int64_t rows, int w, int ld, T *Qo, T 
     const bool f64 = (P->dtype == RSVD_BF16 || P->dtype == RSVD_FP8_E4M3) && passes == 2;
     if (skinny) CK(prod_tn<T>(P, rows, ld, X, ld, X, ld, G, ld, nullptr, true));
     else CK(gemm_tn<T>(rows, ld, ld, X, ld, X, ld, G, ld, part, P->part_elems, s));
-    const bool defl = sizeof(T) == 8 && !want_r;  // float64 bases: remove and refill dependent columns
+    const bool defl = !want_r;  // bases: remove and refill dependent columns (float32: in the fallback only)
     if ((st = chol_pass<T>(P, X, rows, w, ld, f64, P->R1, P->R1i, Ric, defl))) return st;
     if (skinny) CK(prod_nn<T>(P, rows, ld, X, ld, Ric, ld, Q1, ld, nullptr, nullptr, true));
     else CK(gemm_nn<T>(rows, ld, ld, X, ld, Ric, ld, Q1, ld, s));
-    // the final bases after a fallback: X R^{-1} in float64 (an intermediate basis only carries a range)
-    if (sizeof(T) == 4 && passes == 2) CK(rinv64_fb({(const float *)X, rows, ld, P->R1i, (float *)Q1, P->fb}, w, s));
-    if (defl && (st = refill<T>(P, Q1, rows, w, ld))) return st;
+    // after a fallback: the basis X R^{-1} to float64 accuracy, removed columns refilled (an
+    // intermediate basis only carries a range: there only when a column was removed)
+    if (sizeof(T) == 4)
+        CK(rinv64_fb({(const float *)X, rows, ld, P->R1i, (float *)Q1, P->fb, defl ? P->dflag : nullptr,
+                      refill_seed(P), passes == 2 ? nullptr : P->dflag + w}, w, s));
+    else if (defl && (st = refill<T>(P, Q1, rows, w, ld))) return st;
     if (passes == 1) return RSVD_OK;
     if (skinny) CK(prod_tn<T>(P, rows, ld, Q1, ld, Q1, ld, G, ld, nullptr, true));
     else CK(gemm_tn<T>(rows, ld, ld, Q1, ld, Q1, ld, G, ld, part, P->part_elems, s));
     if ((st = chol_pass<T>(P, Q1, rows, w, ld, f64, P->R2, P->R2i, Ric, defl))) return st;
     if (skinny) CK(prod_nn<T>(P, rows, ld, Q1, ld, Ric, ld, Qo, ld, nullptr, nullptr, true));
     else CK(gemm_nn<T>(rows, ld, ld, Q1, ld, Ric, ld, Qo, ld, s));
-    if (sizeof(T) == 4) CK(rinv64_fb({(const float *)Q1, rows, ld, P->R2i, (float *)Qo, P->fb}, w, s));
-    if (defl && (st = refill<T>(P, Qo, rows, w, ld))) return st;
+    if (sizeof(T) == 4)
+        CK(rinv64_fb({(const float *)Q1, rows, ld, P->R2i, (float *)Qo, P->fb, defl ? P->dflag : nullptr,
+                      refill_seed(P), nullptr}, w, s));
+    else if (defl && (st = refill<T>(P, Qo, rows, w, ld))) return st;
     if (want_r) CK(trmm_upper(P->R2, P->R1, P->Rt, w, s));
     return RSVD_OK;
 }
@@ -1131,6 +1147,7 @@ rsvd_status bcqr(BatchCtx &C, int count, rsvd_plan *const *Ps, int which, int pa
             CK(gram64_fb_batched(C.g64(2 * which + pass, count, true), count, max_rows, l, lp, C.bs));
         } else {  // float64: bases remove dependent columns (refilled below), T shifts (chol_pass)
             CK(chol_inv_batched<T, T, T>(tab, count, lp, l, lp, C.bs, want_r ? kCholPlain : kCholDeflate));
+            // (the float64 deflation flags are each problem's dflag: table field fb, see the table fill)
         }
         CK(fork(C, count, Ps));
         for (int i = 0; i < count; i++) {
@@ -1141,9 +1158,10 @@ rsvd_status bcqr(BatchCtx &C, int count, rsvd_plan *const *Ps, int which, int pa
             const T *src = pass == 0 ? X : Tmp;
             T *dst = (pass == passes - 1) ? Qo : Tmp;
             CK(prod_nn<T>(P, rows, lp, src, lp, (const T *)P->Rinv_c, lp, dst, lp));
-            if (sizeof(T) == 4 && passes == 2)
-                CK(rinv64_fb({(const float *)src, rows, lp, pass ? P->R2i : P->R1i, (float *)dst, P->fb}, l,
-                             P->stream));
+            if (sizeof(T) == 4)
+                CK(rinv64_fb({(const float *)src, rows, lp, pass ? P->R2i : P->R1i, (float *)dst, P->fb,
+                              want_r ? nullptr : P->dflag, refill_seed(P), passes == 2 ? nullptr : P->dflag + l},
+                             l, P->stream));
             if (sizeof(T) == 8 && !want_r) {
                 const rsvd_status rs = refill<T>(P, dst, rows, l, lp);
                 if (rs) return rs;
@@ -1169,10 +1187,12 @@ rsvd_status run_rsvd_batch(BatchCtx &C, int count, rsvd_plan *const *Ps, T *cons
         rsvd_plan *P = Ps[i];
         for (int pass = 0; pass < 2; pass++) {
             double *R = pass ? P->R2 : P->R1, *Ri = pass ? P->R2i : P->R1i;
+            // fb: the fallback flag (float32 plans) or the deflation flags (float64 plans)
+            int *fbt = sizeof(T) == 8 ? P->dflag : P->fb;
             C.chol(pass, count, false)[i] = {P->G, R, Ri, P->Rinv_c, P->status, chol_shift_coef(P->m, l, u),
-                                              P->G64, P->fb};
+                                              P->G64, fbt, (double *)P->chol_ws};
             C.chol(2 + pass, count, false)[i] = {P->G, R, Ri, P->Rinv_c, P->status, chol_shift_coef(P->n, l, u),
-                                                  P->G64, P->fb};
+                                                  P->G64, fbt, (double *)P->chol_ws};
         }
         if constexpr (sizeof(T) == 4) {  // the float64 Gram fallback of each (block, pass): its source block
             const float *src[6] = {(const float *)P->Y, (const float *)P->Tmp, (const float *)P->Z,
@@ -1183,7 +1203,8 @@ rsvd_status run_rsvd_batch(BatchCtx &C, int count, rsvd_plan *const *Ps, T *cons
                 C.g64(v, count, false)[i] = {src[v],      rows,          lp,        P->g64part,
                                              P->G64,      P->fb,         P->g64count, chol_shift_coef(rows, l, u),
                                              pass ? P->R2 : P->R1, pass ? P->R2i : P->R1i, (float *)P->Rinv_c, lp,
-                                             P->status,   (double *)P->chol_ws};
+                                             P->status,   (double *)P->chol_ws, v >= 4 ? kCholFallback : kCholDeflate,
+                                             P->dflag};
             }
         }
         C.jac(count, false)[i] = {P->Rt, P->sig, P->UR, P->Wm, P->status};

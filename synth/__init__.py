@@ -20,7 +20,9 @@ of arXiv:1906.12085):
 
 Generation runs in float64 with torch on the requested device (CPU for the
 small cases, CUDA for the multi-GB ones); results are deterministic for a
-given (seed, device).
+given (seed, device).  ``prescribed(..., dtype=torch.float32)`` draws and
+factors in float32 (orthonormal to ~1e-6): a timing input of the largest
+workloads, whose float64 QR would take minutes of float64 arithmetic.
 """
 from __future__ import annotations
 
@@ -58,10 +60,11 @@ def unit_vector(n: int, seed: int, device="cpu", dtype=torch.float64) -> torch.T
     return v.to(dtype)
 
 
-def haar(rows: int, cols: int, seed: int, center: bool = False, device="cpu") -> torch.Tensor:
-    """rows x cols matrix with orthonormal columns, Haar distributed (float64)."""
+def haar(rows: int, cols: int, seed: int, center: bool = False, device="cpu",
+         dtype=torch.float64) -> torch.Tensor:
+    """rows x cols matrix with orthonormal columns, Haar distributed (float64 unless dtype says)."""
     assert rows >= cols
-    g = gaussian(rows, cols, seed, device)
+    g = gaussian(rows, cols, seed, device, dtype)
     if center:
         g = g - g.mean(dim=0, keepdim=True)
     q, r = torch.linalg.qr(g, mode="reduced")
@@ -71,12 +74,12 @@ def haar(rows: int, cols: int, seed: int, center: bool = False, device="cpu") ->
 
 
 def prescribed(m: int, n: int, sigma: torch.Tensor, seed_u: int, seed_v: int,
-               center: bool = True, device="cpu") -> torch.Tensor:
+               center: bool = True, device="cpu", dtype=torch.float64) -> torch.Tensor:
     """A = U diag(sigma) V^T with Haar U (m x r, orthogonal to 1 if center) and V (n x r)."""
-    sigma = sigma.to(device=device, dtype=torch.float64)
+    sigma = sigma.to(device=device, dtype=dtype)
     r = sigma.numel()
-    u = haar(m, r, seed_u, center=center, device=device)
-    v = haar(n, r, seed_v, center=False, device=device)
+    u = haar(m, r, seed_u, center=center, device=device, dtype=dtype)
+    v = haar(n, r, seed_v, center=False, device=device, dtype=dtype)
     return (u * sigma.unsqueeze(0)) @ v.T
 
 
@@ -118,8 +121,9 @@ WORKLOADS = {
 }
 
 
-def workload(name: str, m: int | None = None, n: int | None = None, device="cpu"):
-    """Build (A float64, sigma, extras) for a named workload, optionally at a reduced size.
+def workload(name: str, m: int | None = None, n: int | None = None, device="cpu", dtype=torch.float64):
+    """Build (A, sigma, extras) for a named workload, optionally at a reduced size (A in
+    float64 unless dtype says otherwise; see prescribed).
 
     The spectrum is always evaluated at the (possibly reduced) n; the
     recipe is otherwise the one of the named workload.
@@ -139,7 +143,7 @@ def workload(name: str, m: int | None = None, n: int | None = None, device="cpu"
         sigma = spectrum_power(n, 1.5)
     else:
         raise ValueError(sp)
-    a = prescribed(m, n, sigma, seeds[0], seeds[1], center=True, device=device)
+    a = prescribed(m, n, sigma, seeds[0], seeds[1], center=True, device=device, dtype=dtype)
     extras = {}
     if "p" in w:
         l = w["k"] + w["p"]

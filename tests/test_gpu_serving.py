@@ -4,17 +4,60 @@ A mixed stream of requests goes through a server whose arena holds only a few
 workspaces at a time, so requests queue, batch (consecutive requests of the
 same l) and overlap.  Every result must equal the same request solved alone,
 bit for bit (status, K, S, U, V): the split-K sums run in a fixed order and a
-batch runs each problem's own kernels.  Admission follows arrival order."""
+batch runs each problem's own kernels.  Admission follows arrival order.
+
+Every served result is also compared with the FP64 oracle (Sec. 3.1.2 with the
+same Omega) on the stored matrix -- the float32 values, or the bfloat16 / e4m3
+codes the library's quantiser wrote, dequantised exactly -- at the tolerance of
+its storage type: |sigma_hat_i - sigma_i^O| <= 1e-5 (float32), 1e-4 (bfloat16),
+1e-3 (e4m3) times sigma_1^O; the projection gap (||A - U U^T A||_F - ||A - U^O
+U^O^T A||_F) / ||A||_F within the same bound; U and V orthonormal to 1e-5.  The
+request mix draws sigma_i = i^-alpha with alpha in [0.5, 2], whose power-step
+bases at q = 2 reach condition numbers far beyond a float32 Gram matrix."""
 import numpy as np
 import pytest
 import torch
 
+import oracle
 import paper_1906_12085_gb300 as g
 import synth
 
 pytestmark = pytest.mark.gpu
 
 Q = 2
+TOL = {g.RSVD_F32: 1e-5, g.RSVD_BF16: 1e-4, g.RSVD_FP8_E4M3: 1e-3}
+
+
+def _proj_residual(A, U):
+    """||A - U U^T A||_F for orthonormal U (float64)."""
+    B = U.T @ A
+    return np.sqrt(max(np.sum(A * A) - np.sum(B * B), 0.0))
+
+
+def _stored64(A_dev, sc_dev, dtype):
+    """The stored matrix in float64: float32 values, or the codes dequantised by the oracle."""
+    if dtype == g.RSVD_F32:
+        return A_dev.cpu().double().numpy()
+    if dtype == g.RSVD_BF16:
+        return oracle.dequantize_bf16(A_dev.cpu().numpy().view(np.uint16))
+    return oracle.dequantize_e4m3(A_dev.cpu().numpy(), sc_dev.cpu().numpy())
+
+
+def _check_oracle(A64, Om, k, S, U, V, dtype, status):
+    """A served result against the oracle on the stored matrix (tolerances in the module doc)."""
+    assert status in (g.RSVD_OK, g.RSVD_WARN_K_GT_k, g.RSVD_WARN_RANK_DEFICIENT), status
+    Ac, _, _ = oracle.center(A64)
+    s, Uo, _ = oracle.rsvd(Ac, Om.double(), q=Q, k=k)
+    tol = TOL[dtype]
+    err = np.abs(S - s).max() / s[0]
+    Ug = U.astype(np.float64)
+    gap = (_proj_residual(Ac, Ug) - _proj_residual(Ac, Uo)) / np.sqrt(np.sum(Ac * Ac))
+    assert err <= tol, (dtype, err)
+    assert gap <= tol, (dtype, gap)
+    assert np.abs(Ug.T @ Ug - np.eye(k)).max() <= 1e-5
+    Vg = V.astype(np.float64)
+    assert np.abs(Vg.T @ Vg - np.eye(k)).max() <= 1e-5
+    return err
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -86,6 +129,10 @@ def test_served_results_equal_alone_bitwise():
         assert np.array_equal(r["S"].cpu().numpy(), a_S)
         assert np.array_equal(r["U"].cpu().numpy(), a_U)
         assert np.array_equal(r["V"].cpu().numpy(), a_V)
+    errs = [_check_oracle(r["A"].double().numpy(), r["Om"], r["k"], r["S"].cpu().numpy(), r["U"].cpu().numpy(),
+                          r["V"].cpu().numpy(), g.RSVD_F32, c["status"])
+            for c in done for r in [reqs[c["id"]]]]
+    print(f"served float32 requests: max sigma error {max(errs):.2e} sigma_1")
 
 
 def test_server_rejects_request_larger_than_arena():
@@ -162,6 +209,9 @@ def test_served_mixed_storage_types_equal_alone_bitwise():
         assert np.array_equal(r["S"].cpu().numpy(), a_S), r["dt"]
         assert np.array_equal(r["U"].cpu().numpy(), a_U), r["dt"]
         assert np.array_equal(r["V"].cpu().numpy(), a_V), r["dt"]
+        err = _check_oracle(_stored64(r["Aq"], r["sc"], r["dt"]), r["Om"], r["k"], r["S"].cpu().numpy(),
+                            r["U"].cpu().numpy(), r["V"].cpu().numpy(), r["dt"], c["status"])
+        print(f"served request {c['id']} (dtype {r['dt']}): sigma error {err:.2e} sigma_1")
 
 
 def test_server_submit_ex_checks_scales():
@@ -217,3 +267,5 @@ def test_served_wide_float32_requests_equal_alone_bitwise():
         assert np.array_equal(r["S"].cpu().numpy(), a_S)
         assert np.array_equal(r["U"].cpu().numpy(), a_U)
         assert np.array_equal(r["V"].cpu().numpy(), a_V)
+        _check_oracle(r["A"].double().numpy(), r["Om"], r["k"], r["S"].cpu().numpy(), r["U"].cpu().numpy(),
+                      r["V"].cpu().numpy(), g.RSVD_F32, c["status"])
