@@ -34,6 +34,13 @@ classical Gram-Schmidt passes over the growing bases, applied twice).
 4096 with sigma_i = i^-1.5 (Haar factors built in float32 on the device, a timing
 input) stored as bfloat16 or e4m3 with column scales by the library's quantiser;
 k = 256, p = 32, q = 3; metric: rSVD GFLOP/s as for the default workload.
+
+``--method gram_grid`` runs the paper's experiment grid (Sec. 4) through the Gram route
+(svd_exact, RSVD_EXACT_GRAM, all n triplets, k = n): N(0,1) matrices with 5 row sizes
+{2000, ..., 10000} x 12 column sizes {100, ..., 2000}, plus a 60000 x 784 MNIST-shaped
+N(0,1) matrix (the dataset is not available); float64 by default (--dtype f32 for the
+float32 form).  Metric: solves/s over the grid; every point's time and the paper's
+residual delta = ||A - U Sigma V^T||_F / ||A||_F are listed.
 """
 from __future__ import annotations
 
@@ -567,6 +574,90 @@ def run_precision(args):
     return 0
 
 
+GRID_ROWS = [2000, 4000, 6000, 8000, 10000]
+GRID_COLS = [100, 200, 300, 400, 500, 600, 800, 900, 1000, 1200, 1500, 2000]
+
+
+def run_gram_grid(args):
+    """One JSON line for the paper's experiment grid through the Gram route (k = n)."""
+    import numpy as np
+    import torch
+
+    import paper_1906_12085_gb300 as g
+    import synth
+    from paper_1906_12085_gb300 import build as gbuild
+
+    if int(os.environ.get("RANK", "0")) != 0:   # replicas are not meaningful for a sweep: rank 0 runs it
+        return 0
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    gbuild.build()
+    f64 = args.dtype != "f32"
+    dt, tdt = (g.RSVD_F64, torch.float64) if f64 else (g.RSVD_F32, torch.float32)
+    stream = torch.cuda.current_stream(dev)
+    points = [(m, n) for m in GRID_ROWS for n in GRID_COLS] + [(60000, 784)]
+    reps = max(1, args.steps)
+    out, total_ms, total = [], 0.0, 0
+    launches0 = g.rsvd_launch_count()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    for idx, (m, n) in enumerate(points):
+        A0 = synth.gaussian(m, n, 40000 + idx, device=dev, dtype=tdt)
+        A = A0.clone()
+        S = torch.zeros(n, dtype=torch.float64, device=dev)
+        U = torch.zeros(m, n, dtype=tdt, device=dev)
+        V = torch.zeros(n, n, dtype=tdt, device=dev)
+        plan = g.rsvd_plan_create(m, n, 1, 0, 0, dt, stream)
+        for _ in range(max(args.warmup, 1)):     # the first call allocates the solver's workspace
+            g.check(g.svd_exact(plan, A, g.RSVD_EXACT_GRAM, S, U, V), "svd_exact")
+        st = g.rsvd_plan_sync(plan)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            g.check(g.svd_exact(plan, A, g.RSVD_EXACT_GRAM, S, U, V), "svd_exact")
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        st = g.rsvd_plan_sync(plan) if st == g.RSVD_OK else st
+        Ac = A0.double() - A0.double().mean(dim=0, keepdim=True)
+        delta = float(torch.linalg.norm(Ac - (U.double() * S) @ V.double().T) / torch.linalg.norm(Ac))
+        out.append({"m": m, "n": n, "ms": round(ms, 4), "delta": delta, "status": st})
+        total_ms += ms * reps
+        total += reps
+        plan.close()
+        del A0, A, U, V
+    clocks = sampler.stop()
+    launches = g.rsvd_launch_count() - launches0
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        sample = [(2000, 100), (2000, 200), (4000, 300), (4000, 500)]
+        t0 = time.perf_counter()
+        for idx, (m, n) in enumerate(sample):
+            a = synth.gaussian(m, n, 50000 + idx).numpy()
+            oracle.svd_gram(oracle.center(a)[0])
+        tsec = time.perf_counter() - t0
+        cpu = {"value": len(sample) / tsec, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "the grid points " + ", ".join(f"{m}x{n}" for m, n in sample) +
+                         " (float64 C oracle: A^T A, cyclic Jacobi, u_i = A v_i / sigma_i), one solve each"}
+    big = [p_ for p_ in out if p_["m"] == 10000 and p_["n"] == 2000][0]
+    mn = [p_ for p_ in out if p_["m"] == 60000][0]
+    line = {"metric": "Gram route (k = n) solves/s over the paper's grid", "value": total / (total_ms * 1e-3),
+            "unit": "solves/s", "n_gpus": 1, "steps": reps, "warmup": args.warmup,
+            "ms_per_step": total_ms / total, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if f64 else "f32", "data": "synthetic",
+            "config": {"workload": "paper_grid_gaussian", "method": "gram_grid", "rows": GRID_ROWS, "cols": GRID_COLS,
+                       "extra": "60000x784 N(0,1) (MNIST-shaped)",
+                       "l2": "each point solved back to back on the same buffers (A up to 160 MB)"},
+            "status": max((p_["status"] for p_ in out), key=abs),
+            "max_delta": max(p_["delta"] for p_ in out),
+            "point_10000x2000_ms": big["ms"], "point_60000x784_ms": mn["ms"],
+            "points": out, "cpu_baseline": cpu, "e2e": None, "gpu_launches": launches, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -761,10 +852,11 @@ def main():
     ap.add_argument("--sample-rows", type=int, default=40000, help="rows per reference-arm step")
     ap.add_argument("--cpu-baseline-rows", type=int, default=100000, help="rows of the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--method", default="rsvd", choices=["rsvd", "block_krylov", "gkl", "precision"],
+    ap.add_argument("--method", default="rsvd", choices=["rsvd", "block_krylov", "gkl", "precision", "gram_grid"],
                     help="rsvd: the default workload; block_krylov: the Sec. 3.1.1 workload; gkl: the Lanczos "
                          "workload; precision: the bfloat16 / e4m3 precision form (--dtype)")
-    ap.add_argument("--dtype", default="bf16", choices=["bf16", "fp8"], help="storage of --method precision")
+    ap.add_argument("--dtype", default=None, choices=["bf16", "fp8", "f32", "f64"],
+                    help="storage of --method precision (bf16 | fp8) or gram_grid (f64 | f32)")
     ap.add_argument("--bk-cpu-rows", type=int, default=16384, help="rows of the block Krylov cpu_baseline sample")
     ap.add_argument("--gkl-cpu-rows", type=int, default=16384, help="rows of the Lanczos cpu_baseline sample")
     ap.add_argument("--prec-cpu-rows", type=int, default=8192, help="rows of the precision-form cpu_baseline sample")
@@ -778,7 +870,13 @@ def main():
     if args.method == "gkl":
         return run_gkl(args)
     if args.method == "precision":
+        args.dtype = args.dtype or "bf16"
+        if args.dtype not in ("bf16", "fp8"):
+            ap.error("--method precision takes --dtype bf16 or fp8")
         return run_precision(args)
+    if args.method == "gram_grid":
+        args.dtype = args.dtype or "f64"
+        return run_gram_grid(args)
     return run_ours(args)
 
 

@@ -85,7 +85,8 @@ typedef struct rsvd_plan *rsvd_plan_t;
  * width of G, q plays the role of i).  The plan allocates its device
  * workspace once (cudaMalloc) and launches everything on `cuda_stream`
  * (a cudaStream_t, may be NULL).  For svd_exact the plan needs n <= 112 (the
- * n x n eigen / SVD problem is solved in one CTA's shared memory); for rsvd
+ * n x n eigen / SVD problem is solved in one CTA's shared memory), or n <= 4096
+ * for its Gram route (see svd_exact); for rsvd
  * l <= 288 (RSVD_F32, RSVD_BF16, RSVD_FP8_E4M3) or l <= 112 (RSVD_F64).  Above
  * l = 128 the tensor-core products run on column slices of at most 128 and the
  * l x l Cholesky and Jacobi blocks live in the plan's workspace, solved by an
@@ -163,8 +164,16 @@ rsvd_status rsvd(rsvd_plan_t plan, void *A, const float *col_scales, const void 
  *     sigma_i <= n * eps * sigma_1 are returned as zero vectors).
  *   method RSVD_EXACT_QR_JACOBI: A = Q R by CholeskyQR2, R = U_R Sigma V^T by
  *     one-sided Jacobi, U = Q U_R (backward stable; no squaring of cond(A)).
- *   S : n doubles; U : m x n; V : n x n.  Requires n <= 112 and dtype RSVD_F64
- *   or RSVD_F32.
+ *   S : n doubles; U : m x n; V : n x n.  dtype RSVD_F64 or RSVD_F32.
+ * Sizes: n <= 112 for both methods (the n x n problem in one CTA's shared memory);
+ * the Gram route also takes 112 < n <= 4096 (the k = n regime of the paper's
+ * experiments, Sec. 4): G = A^T A (float32 plans on the tensor cores when n is a
+ * multiple of 16), then a float64 eigen-decomposition on the whole GPU --
+ * Householder tridiagonalisation, bisection, inverse iteration (Gram-Schmidt
+ * inside clusters of eigenvalues closer than 1e-8 max|lambda|, at most 512 of
+ * them, else RSVD_ERR_NOCONV) and back-transformation.  Its first call on a plan
+ * allocates ~6 n^2 doubles of workspace with cudaMalloc.  RSVD_ERR_UNSUPPORTED
+ * beyond these sizes.
  */
 rsvd_status svd_exact(rsvd_plan_t plan, void *A, int method, double *S, void *U, void *V);
 

@@ -303,6 +303,22 @@ cudaError_t jacobi_eig(const double *G, int n, double *lam, double *V, int *stat
 cudaError_t jacobi_eig_f32(const double *G, int n, double *lam, double *V, int *status, cudaStream_t s,
                            double floor_rel);
 
+// Symmetric eigen-decomposition of the n x n float64 matrix A (row-major, both triangles;
+// overwritten) beyond one CTA (n <= kGramMaxN): lam descending (n doubles), V (n x n, column
+// i = eigenvector i).  Householder tridiagonalisation (a cooperative persistent launch with
+// bounded grid barriers: ST_TIMEOUT if one gives up), bisection, inverse iteration,
+// Gram-Schmidt inside clusters of eigenvalues closer than 1e-8 max|lam| (ST_NOCONV for a
+// cluster of more than 512), back-transformation.  ws: eigh_workspace_bytes(n) bytes.
+constexpr int kGramMaxN = 4096;
+size_t eigh_workspace_bytes(int n);
+cudaError_t eigh_large(double *A, int n, double *lam, double *V, int *status, void *ws, cudaStream_t s);
+// G64 (n x n, both triangles) = the upper triangle of Gs (ldg) in float64
+template <typename T>
+cudaError_t symmetrize(const T *Gs, int64_t ldg, int n, double *G64, cudaStream_t s);
+// gram_finish for any n (a multi-CTA grid)
+template <typename T>
+cudaError_t gram_scale(const double *lam, const double *V, int n, double *sig, T *Vs, int *status, cudaStream_t s);
+
 // Vs[:, i] = V[:, i] / sigma_i (zero column when sigma_i <= n eps sigma_1), sigma_i = sqrt(max(lam_i,0)).
 template <typename T>
 cudaError_t gram_finish(const double *lam, const double *V, int n, double *sig, T *Vs, int *status,

@@ -95,6 +95,8 @@ struct rsvd_plan {
     // Golub-Kahan-Lanczos workspace, allocated on the first Krylov solve and grown with `steps`
     void *gkl_ws = nullptr;
     int gkl_cap = 0;
+    // Gram route beyond one CTA (n > kSmallMaxF64), allocated on the first such svd_exact
+    void *gram_ws = nullptr;
     // CUDA graph of the last rsvd solve, replayed while the caller's pointers and flags repeat
     cudaGraphExec_t graph = nullptr;
     const void *gkey[7] = {};
@@ -923,6 +925,98 @@ rsvd_status run_exact(rsvd_plan *P, T *A, int method, double *S, T *U, T *V) {
     return RSVD_OK;
 }
 
+// The Gram route (Sec. 2.3, Sec. 3.1.3) for n beyond one CTA, the k = n regime of the
+// paper's experiments (Sec. 4): G = A^T A (float32 plans on the tensor cores when TMA can
+// address A, else CUDA cores), eigen-decomposition in float64 (eigh_large),
+// sigma = sqrt(lambda), U = A V Sigma^{-1}.  The workspace (G and V in float64, V Sigma^{-1}
+// in the element type, the solver's scratch, the Gram product's partials) is allocated on
+// the first call.
+struct GramBufs {
+    double *G64, *V64, *lam;
+    void *Vs, *eig, *part;
+    int64_t part_elems;
+};
+
+GramBufs gram_carve(rsvd_plan *P, char *base, size_t *bytes) {
+    const int64_t n = P->n, m = P->m;
+    const size_t es = esize(P->dtype);
+    Carver c;
+    c.base = base;
+    GramBufs b;
+    b.G64 = (double *)c.take(sizeof(double) * n * n);
+    b.V64 = (double *)c.take(sizeof(double) * n * n);
+    b.lam = (double *)c.take(sizeof(double) * n);
+    b.Vs = c.take(es * n * n);
+    b.eig = c.take(eigh_workspace_bytes((int)n));
+    int64_t pe = gemm_tn_partials(m, n, n);
+    if (P->dtype == RSVD_F32 && n % 16 == 0) {  // the tensor-core Gram: column slices up to the diagonal
+        const int w = column_slice((int)n);
+        for (int64_t c0 = 0; c0 < n; c0 += w) {
+            const int wn = (int)std::min<int64_t>(w, n - c0);
+            pe = std::max(pe, tc_gemm_tn_partials(m, (int)std::min<int64_t>(c0 + wn, n), wn));
+        }
+    }
+    b.part_elems = pe;
+    b.part = c.take(es * (pe > 0 ? pe : 1));
+    *bytes = c.off;
+    return b;
+}
+
+template <typename T>
+rsvd_status run_exact_large(rsvd_plan *P, T *A, double *S, T *U, T *V) {
+    cudaStream_t s = P->stream;
+    const int64_t m = P->m, n = P->n;
+    const int nn = (int)n;
+    size_t bytes = 0;
+    gram_carve(P, nullptr, &bytes);
+    if (!P->gram_ws) {
+        if (cudaMalloc(&P->gram_ws, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            P->gram_ws = nullptr;
+            return RSVD_ERR_OOM;
+        }
+    }
+    const GramBufs b = gram_carve(P, (char *)P->gram_ws, &bytes);
+    rsvd_status st;
+    {
+        Span sp(P, RSVD_STAGE_CENTER);
+        if ((st = center<T>(P, A))) return st;
+    }
+    {
+        Span sp(P, RSVD_STAGE_ATX);  // step 1: G = A^T A (upper triangle), widened to float64, both triangles
+        T *Gs = (T *)b.Vs;           // the n x n buffer of V Sigma^{-1}, free until step 3
+        bool done = false;
+        if constexpr (sizeof(T) == 4) {
+            if (P->tc && n % 16 == 0 && al16(A, n, 4)) {
+                const cudaError_t e = tc_gemm_tn(m, nn, nn, A, n, A, n, Gs, n, (float *)b.part, b.part_elems,
+                                                 P->status, s, nullptr, 0, true);
+                if (e == cudaSuccess) done = true;
+                else if (e != cudaErrorInvalidValue) return RSVD_ERR_CUDA;
+                else cudaGetLastError();
+            }
+        }
+        if (!done) CK(gemm_tn<T>(m, n, n, A, n, A, n, Gs, n, (T *)b.part, b.part_elems, s));
+        CK(symmetrize<T>(Gs, n, nn, b.G64, s));
+    }
+    {
+        Span sp(P, RSVD_STAGE_SMALL);  // step 2: eigen-decomposition; step 3: sigma = sqrt(lambda)
+        CK(eigh_large(b.G64, nn, b.lam, b.V64, P->status, b.eig, s));
+        CK(gram_scale<T>(b.lam, b.V64, nn, P->sig, (T *)b.Vs, P->status, s));
+    }
+    {
+        Span sp(P, RSVD_STAGE_AX);  // step 4: u_i = A v_i / sigma_i
+        CK(gemm_nn<T>(m, n, n, A, n, (const T *)b.Vs, n, U, n, s));
+    }
+    {
+        Span sp(P, RSVD_STAGE_FINISH);
+        CK(copy2d<double, T>(b.V64, n, V, n, n, n, n, s));
+        CK(sign_normalize<T>(V, n, nn, n, U, m, n, s));
+        CK(copy_f64(P->sig, S, n, s));
+    }
+    P->last_count = nn;
+    return RSVD_OK;
+}
+
 // Golub-Kahan-Lanczos with full reorthogonalisation (CGS2), then the SVD of the
 // steps x steps bidiagonal and the Ritz vectors; see svd_truncated_krylov().
 struct GklBufs {
@@ -1539,6 +1633,7 @@ rsvd_status rsvd_plan_destroy(rsvd_plan_t P) {
     for (cudaEvent_t e : P->ev) cudaEventDestroy(e);
     drop_graph(P);
     if (P->gkl_ws) cudaFree(P->gkl_ws);
+    if (P->gram_ws) cudaFree(P->gram_ws);
     if (P->ws_owned) cudaFree(P->ws);
     delete P;
     return RSVD_OK;
@@ -1828,7 +1923,12 @@ void rsvd_tune_clear(void) {
 rsvd_status svd_exact(rsvd_plan_t P, void *A, int method, double *S, void *U, void *V) {
     if (!P || !A || !S || !U || !V) return RSVD_ERR_ARG;
     if (method != RSVD_EXACT_GRAM && method != RSVD_EXACT_QR_JACOBI) return RSVD_ERR_ARG;
-    if (!P->nx) return RSVD_ERR_UNSUPPORTED;
+    if (P->dtype != RSVD_F32 && P->dtype != RSVD_F64) return RSVD_ERR_UNSUPPORTED;
+    if (!P->nx) {  // beyond one CTA: the Gram route's float64 eigensolver on the whole GPU
+        if (method != RSVD_EXACT_GRAM || P->n > kGramMaxN) return RSVD_ERR_UNSUPPORTED;
+        if (P->dtype == RSVD_F32) return run_exact_large<float>(P, (float *)A, S, (float *)U, (float *)V);
+        return run_exact_large<double>(P, (double *)A, S, (double *)U, (double *)V);
+    }
     if (P->dtype == RSVD_F32) return run_exact<float>(P, (float *)A, method, S, (float *)U, (float *)V);
     return run_exact<double>(P, (double *)A, method, S, (double *)U, (double *)V);
 }

@@ -3,6 +3,7 @@
     python -m paper_1906_12085_gb300.profile_case rsvd --m 200000 --n 1000 --k 50 --p 10 --q 2
     python -m paper_1906_12085_gb300.profile_case gkl  --m 262144 --n 2048 --k 100 --steps 150
     python -m paper_1906_12085_gb300.profile_case exact --m 2000 --n 100 --dtype f64
+    python -m paper_1906_12085_gb300.profile_case gram --m 10000 --n 2000 --dtype f32
     python -m paper_1906_12085_gb300.profile_case rsvd --m 1048576 --n 4096 --k 96 --p 16 --q 3 --dtype bf16
     python -m paper_1906_12085_gb300.profile_case rsvd --m 1048576 --n 4096 --k 96 --p 16 --q 3 --dtype fp8
     python -m paper_1906_12085_gb300.profile_case bk --m 1048576 --n 4096 --k 256 --b 96 --iters 2 --repeat 2 --timed 3
@@ -27,7 +28,7 @@ import paper_1906_12085_gb300 as g
 
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
-    ap.add_argument("path", choices=["rsvd", "gkl", "exact", "bk"])
+    ap.add_argument("path", choices=["rsvd", "gkl", "exact", "gram", "bk"])
     ap.add_argument("--m", type=int, default=200000)
     ap.add_argument("--n", type=int, default=1000)
     ap.add_argument("--k", type=int, default=50)
@@ -60,9 +61,9 @@ def main(argv=None) -> int:
         g.check(g.rsvd_quantize(A, g.RSVD_FP8_E4M3, Aq, sc), "rsvd_quantize")
         del A
         A = Aq
-    k = a.k if a.path != "exact" else a.n
+    k = a.k if a.path not in ("exact", "gram") else a.n
     S = torch.zeros(k, dtype=torch.float64, device=dev)
-    if a.path == "exact":
+    if a.path in ("exact", "gram"):
         U = torch.zeros(a.m, a.n, dtype=tdt, device=dev)
         V = torch.zeros(a.n, a.n, dtype=tdt, device=dev)
     else:
@@ -71,7 +72,7 @@ def main(argv=None) -> int:
     if a.path == "bk":
         plan = g.rsvd_plan_create_block_krylov(a.m, a.n, k, a.b, a.iters, dt)
     else:
-        plan = g.rsvd_plan_create(a.m, a.n, k, a.p if a.path == "rsvd" else 0, a.q, dt)
+        plan = g.rsvd_plan_create(a.m, a.n, 1 if a.path == "gram" else k, a.p if a.path == "rsvd" else 0, a.q, dt)
     with plan:
         g.rsvd_plan_profile(plan, True)
         for rep in range(a.repeat):
@@ -88,6 +89,8 @@ def main(argv=None) -> int:
                 v1 = torch.randn(a.n, generator=gen, device=dev, dtype=tdt)
                 v1 /= v1.norm()
                 g.check(g.svd_truncated_krylov(plan, A, v1, a.steps, S, U, V), "svd_truncated_krylov")
+            elif a.path == "gram":
+                g.check(g.svd_exact(plan, A, g.RSVD_EXACT_GRAM, S, U, V), "svd_exact")
             else:
                 g.check(g.svd_exact(plan, A, g.RSVD_EXACT_QR_JACOBI, S, U, V), "svd_exact")
         g.check(g.rsvd_plan_sync(plan), "solve status")

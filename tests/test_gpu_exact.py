@@ -100,13 +100,19 @@ def test_exact_small_and_square(m, n):
         assert np.abs(Ac @ V - U * S).max() <= 1e-8 * s[0]
 
 
-def test_exact_rejects_wide_plans():
-    m, n = 5000, 200   # n above the one-CTA limit of svd_exact
+def test_exact_size_limits():
+    """Beyond the one-CTA limit (n > 112) only the Gram route runs (up to n = 4096)."""
+    m, n = 5000, 200
     dev = torch.device("cuda")
     A = torch.zeros(m, n, dtype=torch.float64, device=dev)
     with g.rsvd_plan_create(m, n, 4, 2, 0, g.RSVD_F64) as plan:
         S = torch.zeros(n, dtype=torch.float64, device=dev)
-        st = g.svd_exact(plan, A, g.RSVD_EXACT_GRAM, S, torch.zeros(m, n, dtype=torch.float64, device=dev),
+        st = g.svd_exact(plan, A, g.RSVD_EXACT_QR_JACOBI, S, torch.zeros(m, n, dtype=torch.float64, device=dev),
                          torch.zeros(n, n, dtype=torch.float64, device=dev))
         assert st == g.RSVD_ERR_UNSUPPORTED
         assert g.svd_exact(plan, A, 7, S, A, A) == g.RSVD_ERR_ARG
+    m, n = 4200, 4097
+    A = torch.zeros(m, n, dtype=torch.float32, device=dev)
+    with g.rsvd_plan_create(m, n, 4, 2, 0, g.RSVD_F32) as plan:
+        S = torch.zeros(n, dtype=torch.float64, device=dev)
+        assert g.svd_exact(plan, A, g.RSVD_EXACT_GRAM, S, A, A) == g.RSVD_ERR_UNSUPPORTED
