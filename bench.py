@@ -27,8 +27,9 @@ k = 256, one step = one rsvd_block_krylov() solve; FLOPs per solve
 ``--method gkl`` measures the Golub-Kahan-Lanczos path (HBM-bound): A 1048576 x
 2048 float32, sigma_i = exp(-i/200), 150 steps with full reorthogonalisation from
 a seeded unit v1, k = 100; metric: algorithmic HBM GB/s of the solve, bytes per
-solve = steps (8mn) + 8(m+n) steps (steps - 1) (two reads of A per step and the
-classical Gram-Schmidt passes over the growing bases, applied twice).
+solve = steps r (4mn) + 8(m+n) steps (steps - 1): r reads of A per step (1 for the
+float32 one-pass form, 2 with --gkl-two-pass) and the classical Gram-Schmidt
+passes over the growing bases, applied twice.
 
 ``--method precision --dtype bf16|fp8`` measures the precision form: A 1048576 x
 4096 with sigma_i = i^-1.5 (Haar factors built in float32 on the device, a timing
@@ -129,8 +130,9 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def traffic_for(kernel_src: str, kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel source."""
+def traffic_for(kernel_src: str, kernel: str, workload: str = None):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel source
+    (captures on a smaller case are stored scaled to a full launch by the rows processed)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
@@ -138,7 +140,7 @@ def traffic_for(kernel_src: str, kernel: str):
         e = rec[kernel]
         with open(os.path.join(ROOT, "paper_1906_12085_gb300", "csrc", kernel_src), "rb") as f:
             h = hashlib.sha256(f.read()).hexdigest()[:16]
-        if e.get("source_sha256_16") != h or e.get("workload") != WORKLOAD:
+        if e.get("source_sha256_16") != h or e.get("workload") != (workload or WORKLOAD):
             return None
         return float(e["dram_bytes_per_launch"])
     except Exception:
@@ -384,8 +386,8 @@ def _e2e(step, dev, stream, h2d, d2h, reps, work, unit):
             "d2h_bytes_per_step": sum(h.numel() * h.element_size() for _, h in outs), "ms_per_step": ems / reps}
 
 
-def gkl_bytes(m, n, steps):
-    return steps * 8.0 * m * n + 8.0 * (m + n) * steps * (steps - 1)
+def gkl_bytes(m, n, steps, reads=2):
+    return steps * reads * 4.0 * m * n + 8.0 * (m + n) * steps * (steps - 1)
 
 
 def run_gkl(args):
@@ -417,23 +419,30 @@ def run_gkl(args):
     V = torch.zeros(n, k, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     plan = g.rsvd_plan_create(m, n, k, 0, 0, g.RSVD_F32, stream)
+    reads = 2 if args.gkl_two_pass else 1
+    if args.gkl_two_pass:
+        g.check(g.rsvd_plan_set_flags(plan, g.RSVD_FLAG_GKL_TWO_PASS), "flags")
 
     def step():
         g.check(g.svd_truncated_krylov(plan, A, v1, steps, S, U, V), "svd_truncated_krylov")
 
     ms_max, launches, clocks = _timed_solves(step, args, dev, stream, world)
     st = g.rsvd_plan_sync(plan)
-    nbytes = gkl_bytes(m, n, steps)
+    nbytes = gkl_bytes(m, n, steps, reads)
     value = world * nbytes * args.steps / (ms_max * 1e-3) / 1e9
     prof = _stage_profile(plan, step, args.steps)
     pk, src = peaks()
     hbm = float(pk.get("hbm_gbs", 6800.0))
-    # dominant GEMV of the step pair: A v (ax stage) or A^T u (atx stage), one launch per step each
+    # dominant GEMV of the step: the one-pass A v and A^T (A v) (ax stage), or with two passes
+    # A v (ax) or A^T u (atx); one launch group per step each
     dom = "ax" if prof["ax"][0] >= prof["atx"][0] else "atx"
     per_launch_ms = prof[dom][0] / prof[dom][1]
     achieved = 4.0 * m * n / (per_launch_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "gemv_n_kernel (A v)" if dom == "ax" else "gemv_t_kernel (A^T u)",
-                "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+    kname = ("gemv_nt_kernel (A v and A^T (A v), one read of A)" if reads == 1 else "gemv_n_kernel (A v)") \
+        if dom == "ax" else "gemv_t_kernel (A^T u)"
+    traffic = traffic_for("k_gkl.cu", "gemv_nt_kernel", GKL_WORKLOAD) if reads == 1 and dom == "ax" else None
+    roofline = {"bound": "hbm", "kernel": kname,
+                "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
                 "algorithmic_bytes_per_launch": 4.0 * m * n,
                 "solve_algorithmic_bytes": nbytes, "solve_frac": value / world / hbm,
                 "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback 6800 GB/s",
@@ -448,7 +457,7 @@ def run_gkl(args):
         t0 = time.perf_counter()
         oracle.gkl(oracle.center(a)[0], v1.cpu().numpy().astype(np.float64), steps, k)
         tsec = time.perf_counter() - t0
-        cpu = {"value": gkl_bytes(rows, n, steps) / tsec / 1e9, "unit": "GB/s", "cores": os.cpu_count(),
+        cpu = {"value": gkl_bytes(rows, n, steps, reads) / tsec / 1e9, "unit": "GB/s", "cores": os.cpu_count(),
                "kind": "oracle",
                "sample": f"first {rows} of {m} rows (same n, steps, k, v1); FP64 C oracle, OpenMP, one solve"}
     if rank == 0:
@@ -457,6 +466,7 @@ def run_gkl(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
                 "config": {"workload": GKL_WORKLOAD, "method": "gkl", "m": m, "n": n, "k": k, "lanczos_steps": steps,
+                           "a_reads_per_step": reads,
                            "l2": "inputs larger than L2 (A is 8.6 GB), no flush", "parallelism": f"replicas{world}"},
                 "solves_per_s": world * args.steps / (ms_max * 1e-3), "status": st,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
@@ -859,6 +869,7 @@ def main():
                     help="storage of --method precision (bf16 | fp8) or gram_grid (f64 | f32)")
     ap.add_argument("--bk-cpu-rows", type=int, default=16384, help="rows of the block Krylov cpu_baseline sample")
     ap.add_argument("--gkl-cpu-rows", type=int, default=16384, help="rows of the Lanczos cpu_baseline sample")
+    ap.add_argument("--gkl-two-pass", action="store_true", help="--method gkl: read A twice per step")
     ap.add_argument("--prec-cpu-rows", type=int, default=8192, help="rows of the precision-form cpu_baseline sample")
     args = ap.parse_args()
     if args.warmup < 3:

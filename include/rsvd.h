@@ -75,7 +75,10 @@ enum {
 };
 
 /* plan flags */
-enum { RSVD_FLAG_NO_CENTER = 1 };
+enum {
+    RSVD_FLAG_NO_CENTER = 1,     /* A is already centred (mu = 0)                                     */
+    RSVD_FLAG_GKL_TWO_PASS = 2   /* svd_truncated_krylov reads A twice per step (see there)           */
+};
 
 typedef struct rsvd_plan *rsvd_plan_t;
 
@@ -189,6 +192,12 @@ rsvd_status svd_exact(rsvd_plan_t plan, void *A, int method, double *S, void *U,
  * k Ritz triplets: S k doubles, U = U_s X (m x k), V = V_s Y (n x k).
  * This is the Krylov route of the library; the paper's own Krylov method
  * (Sec. 3.1.1, a block power basis) is a different algorithm.
+ * Float32 plans read A once per step: g = (A - 1 mu^T) v_j and x = (A - 1 mu^T)^T g
+ * come from the same rows, and A^T u_j is recovered by linearity from the stored
+ * A^T u_i (i < j) and the summed reorthogonalisation coefficients; the recovery
+ * multiplies the rounding of x by ||x|| / alpha_j, so a step whose ||x|| exceeds
+ * 16 alpha_j max_i alpha_i also reads A a second time (decided on the device).
+ * RSVD_FLAG_GKL_TWO_PASS (and float64 plans) always read A twice per step.
  * Requires k <= steps <= n and steps <= 160 (RSVD_F32) / 112 (RSVD_F64)
  * (RSVD_ERR_UNSUPPORTED otherwise).  The first call on a plan allocates the
  * Lanczos workspace (steps x m + (steps+1) x n elements and small buffers)

@@ -400,14 +400,27 @@ cudaError_t gkl_gemv_n(const T *A, int64_t m, int n, int64_t lda, const T *v, co
                        cudaStream_t s, const T *mu = nullptr);
 // z = (A - 1 mu^T)^T u - alpha[0] * vprev (alpha / vprev / mu may be NULL);
 // part: gkl_gemv_chunks(m, n) * (n + 1) float64 scratch
+// (y, when given, also receives (A - 1 mu^T)^T u; gate, when given, must be non-zero for the launches to run)
 template <typename T>
 cudaError_t gkl_gemv_t(const T *A, int64_t m, int n, int64_t lda, const T *u, const T *alpha, const T *vprev, T *z,
-                       double *part, cudaStream_t s, const T *mu = nullptr);
+                       double *part, cudaStream_t s, const T *mu = nullptr, T *y = nullptr, const int *gate = nullptr);
+// The one-pass step (float32): w = g - beta uprev and x = (A - 1 mu^T)^T g for g = (A - 1 mu^T) v,
+// one read of A; part: gkl_gemv_nt_chunks(m) * (n + 1) doubles.  cudaErrorInvalidValue when
+// gkl_one_pass_ok fails (n % 4, n > 4096, alignment).
+bool gkl_one_pass_ok(int64_t m, int n, int64_t lda, const void *A);
+int64_t gkl_gemv_nt_chunks(int64_t m);
+cudaError_t gkl_gemv_nt(const float *A, int64_t m, int n, int64_t lda, const float *v, const float *beta,
+                        const float *uprev, float *w, float *x, double *part, cudaStream_t s, const float *mu);
+// y_j = (x - beta_{j-1} y_{j-1} - sum_{i<j} coef_i y_i) / alpha_j into row j of Y (ld n),
+// z = y_j - alpha_j v_j, flag = whether gemv_t must recompute them (j <= 1024).
+cudaError_t gkl_recover(const float *x, float *Y, int j, int n, const float *beta, const float *coef,
+                        const float *alpha, const float *vj, float *z, int *flag, cudaStream_t s);
 int64_t gkl_gemv_chunks(int64_t m, int n);
 int64_t gkl_reorth_blocks(int64_t len);
+// (ctot, when given, receives the sum of the two passes' coefficients)
 template <typename T>
 cudaError_t gkl_reorth_normalize(const T *Bt, int64_t ld, int cnt, T *w, int64_t len, T *coef, T *part, T *sq,
-                                 T *nrm, T *out, int *status, cudaStream_t s);
+                                 T *nrm, T *out, int *status, cudaStream_t s, T *ctot = nullptr);
 template <typename T>
 cudaError_t gkl_bidiag(const T *alpha, const T *beta, int steps, double *B, cudaStream_t s);
 

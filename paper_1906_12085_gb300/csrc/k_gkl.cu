@@ -8,6 +8,13 @@
 //   alpha_j = ||w||, u_j = w / alpha_j       multi_axpy (norm fused) + scale_store
 //   z  = A^T u_j - alpha_j v_j               gemv_t + colsum_sub (one read of A)
 //   z -= V (V^T z), twice; beta_j = ||z||; v_{j+1} = z / beta_j
+// The one-pass form (float32) reads A once per step: gemv_nt forms g = A v_j and
+// x = A^T g from the same rows, and A^T u_j is recovered by linearity,
+//   y_j = A^T u_j = (x - beta_{j-1} y_{j-1} - sum_i c_i y_i) / alpha_j,
+// from the stored y_i = A^T u_i and the summed CGS2 coefficients c_i; the recovery
+// multiplies the rounding of x by ||x|| / alpha_j, so a step whose
+// ||x|| / (alpha_j max_i alpha_i) exceeds kRecoverBound runs gemv_t after all (gated on a
+// device flag).
 // The Krylov bases are stored transposed (U^T: steps x m, V^T: (steps+1) x n)
 // so every basis vector is contiguous.
 #include "common.cuh"
@@ -81,7 +88,8 @@ __global__ void __launch_bounds__(GT) gemv_n_kernel(const T *__restrict__ A, int
 template <typename T, bool VEC>
 __global__ void __launch_bounds__(GT) gemv_t_kernel(const T *__restrict__ A, int64_t m, int n, int64_t lda,
                                                     const T *__restrict__ u, int64_t rpc, double *__restrict__ part,
-                                                    double *__restrict__ usum) {
+                                                    double *__restrict__ usum, const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
     constexpr int E = VEC ? V4<T>::n : 1;
     const int64_t r0 = (int64_t)blockIdx.x * rpc;
     const int64_t r1 = min(m, r0 + rpc);
@@ -130,10 +138,12 @@ __global__ void __launch_bounds__(GT) gemv_t_kernel(const T *__restrict__ A, int
 }
 
 // z[c] = sum_k part[k][c] - (alpha ? alpha[0] : 0) * vprev[c]; 8 row groups x 32 columns per block, fixed order
+// (y, when given, receives the sum itself; gate, when given, must be set for the kernel to run)
 template <typename T>
 __global__ void colsum_sub_kernel(const double *__restrict__ part, int64_t chunks, int n, const T *__restrict__ alpha,
                                   const T *__restrict__ vprev, T *__restrict__ z, const T *__restrict__ mu,
-                                  const double *__restrict__ usum) {
+                                  const double *__restrict__ usum, T *__restrict__ y, const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
     __shared__ double red[8][33];
     __shared__ double usr[8];
     const int cx = threadIdx.x & 31, gy = threadIdx.x >> 5;
@@ -157,6 +167,167 @@ __global__ void colsum_sub_kernel(const double *__restrict__ part, int64_t chunk
             t -= (double)mu[c] * su;
         }
         z[c] = alpha ? (T)(t - (double)alpha[0] * (double)vprev[c]) : (T)t;
+        if (y) y[c] = (T)t;
+    }
+}
+
+// ---------------------------------------------------------------- one pass over A
+// A CTA takes a chunk of rows R at a time: every thread loads NV float4 of each row (its
+// columns c = 4 (tid + GT k)), forms its share of the R row dots with v, one CTA-wide
+// reduction gives g_r = (a_r - mu) . v, w_r = g_r - beta uprev_r is stored, and the same
+// registers accumulate a_rc g_r into the column partials (float32 over 32 rows, float64
+// beyond), with sum_r g_r kept for the mean correction of x = (A - 1 mu^T)^T g.
+template <int NV, int R>
+__global__ void __launch_bounds__(GT) gemv_nt_kernel(const float *__restrict__ A, int64_t m, int n, int64_t lda,
+                                                     const float *__restrict__ v, const float *__restrict__ beta,
+                                                     const float *__restrict__ uprev, float *__restrict__ w,
+                                                     const float *__restrict__ mu, int64_t rpc,
+                                                     double *__restrict__ part, double *__restrict__ gsum) {
+    __shared__ float red[GT / 32][R];
+    __shared__ float gr[R];
+    __shared__ double mred[GT / 32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    float4 vr[NV];
+    bool on[NV];
+    double mv = 0.0;
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        const int c = 4 * (tid + GT * k);
+        on[k] = c < n;
+        vr[k] = on[k] ? *reinterpret_cast<const float4 *>(v + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (mu && on[k]) {
+            const float4 mk = *reinterpret_cast<const float4 *>(mu + c);
+            mv += (double)mk.x * vr[k].x + (double)mk.y * vr[k].y + (double)mk.z * vr[k].z + (double)mk.w * vr[k].w;
+        }
+    }
+    mv = warp_red(mv);
+    if (lane == 0) mred[wid] = mv;
+    __syncthreads();
+    double mvt = 0.0;
+#pragma unroll
+    for (int k = 0; k < GT / 32; k++) mvt += mred[k];
+    const float mdot = (float)mvt;
+    const float b = beta ? beta[0] : 0.f;
+    const int64_t r0 = (int64_t)blockIdx.x * rpc, r1 = min(m, r0 + rpc);
+    float4 sub[NV];
+    double acc[NV][4];
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        sub[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0.0;
+    }
+    double gs = 0.0;
+    int since = 0;
+    for (int64_t rb = r0; rb < r1; rb += R) {
+        float4 a[R][NV];
+        float d[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const bool rin = rb + r < r1;
+            d[r] = 0.f;
+#pragma unroll
+            for (int k = 0; k < NV; k++) {
+                a[r][k] = (rin && on[k]) ? *reinterpret_cast<const float4 *>(A + (rb + r) * lda + 4 * (tid + GT * k))
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+                d[r] += a[r][k].x * vr[k].x + a[r][k].y * vr[k].y + a[r][k].z * vr[k].z + a[r][k].w * vr[k].w;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const float t = warp_red(d[r]);
+            if (lane == 0) red[wid][r] = t;
+        }
+        __syncthreads();
+        if (tid < R) {
+            float t = 0.f;
+#pragma unroll
+            for (int k = 0; k < GT / 32; k++) t += red[k][tid];
+            t -= mdot;
+            gr[tid] = t;
+            if (rb + tid < r1) {
+                w[rb + tid] = uprev ? t - b * uprev[rb + tid] : t;
+                gs += (double)t;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const float g = rb + r < r1 ? gr[r] : 0.f;
+#pragma unroll
+            for (int k = 0; k < NV; k++) {
+                sub[k].x += a[r][k].x * g;
+                sub[k].y += a[r][k].y * g;
+                sub[k].z += a[r][k].z * g;
+                sub[k].w += a[r][k].w * g;
+            }
+        }
+        since += R;
+        if (since >= 32) {
+#pragma unroll
+            for (int k = 0; k < NV; k++) {
+                acc[k][0] += sub[k].x;
+                acc[k][1] += sub[k].y;
+                acc[k][2] += sub[k].z;
+                acc[k][3] += sub[k].w;
+                sub[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            since = 0;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        acc[k][0] += sub[k].x;
+        acc[k][1] += sub[k].y;
+        acc[k][2] += sub[k].z;
+        acc[k][3] += sub[k].w;
+        if (on[k]) {
+            double *pp = part + (int64_t)blockIdx.x * n + 4 * (tid + GT * k);
+            pp[0] = acc[k][0];
+            pp[1] = acc[k][1];
+            pp[2] = acc[k][2];
+            pp[3] = acc[k][3];
+        }
+    }
+    // sum of g over the chunk (threads 0 .. R-1 hold their rows' shares)
+    gs = warp_red(gs);
+    if (tid == 0) gsum[blockIdx.x] = gs;
+}
+
+// The recovery of y_j = A^T u_j (one CTA): ||x||, y_j = (x - beta y_{j-1} - sum_{i<j} c_i y_i) / alpha_j
+// (Y: rows of the stored y_i, ld n), z = y_j - alpha_j v_j; flag = 1 when
+// ||x|| / (alpha_j max_{i<=j} alpha_i) > kRecoverBound (or alpha_j is not positive): the
+// caller's gated gemv_t then recomputes z and y_j from A.
+constexpr double kRecoverBound = 16.0;
+__global__ void __launch_bounds__(1024) recover_kernel(const float *__restrict__ x, float *__restrict__ Y, int j, int n,
+                                                       const float *__restrict__ beta, const float *__restrict__ coef,
+                                                       const float *__restrict__ alpha, const float *__restrict__ vj,
+                                                       float *__restrict__ z, int *__restrict__ flag) {
+    __shared__ double red[32];
+    __shared__ float cs[1024];
+    const float aj = alpha[j];
+    for (int i = threadIdx.x; i < j; i += blockDim.x) cs[i] = coef[i];
+    double x2 = 0.0;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) x2 += (double)x[c] * x[c];
+    x2 = warp_red(x2);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += red[k];
+        float amax = 0.f;
+        for (int i = 0; i <= j; i++) amax = fmaxf(amax, alpha[i]);
+        const bool bad = !(aj > 0.f) || sqrt(t) > kRecoverBound * (double)aj * (double)amax;
+        *flag = bad ? 1 : 0;
+    }
+    const float b = j > 0 ? beta[j - 1] : 0.f;
+    const float inv = aj > 0.f ? 1.f / aj : 0.f;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        float t = x[c];
+        if (j > 0) t -= b * Y[(int64_t)(j - 1) * n + c];
+        for (int i = 0; i < j; i++) t -= cs[i] * Y[(int64_t)i * n + c];
+        const float y = t * inv;
+        Y[(int64_t)j * n + c] = y;
+        z[c] = y - aj * vj[c];
     }
 }
 
@@ -351,7 +522,7 @@ cudaError_t gkl_gemv_n(const T *A, int64_t m, int n, int64_t lda, const T *v, co
 
 template <typename T>
 cudaError_t gkl_gemv_t(const T *A, int64_t m, int n, int64_t lda, const T *u, const T *alpha, const T *vprev, T *z,
-                       double *part, cudaStream_t s, const T *mu) {
+                       double *part, cudaStream_t s, const T *mu, T *y, const int *gate) {
     constexpr int E = V4<T>::n;
     const bool vec = (n % E == 0) && (lda % E == 0) && ((uintptr_t)A % 16 == 0);
     const int64_t rpc = gemv_t_rpc(m, n);
@@ -359,10 +530,49 @@ cudaError_t gkl_gemv_t(const T *A, int64_t m, int n, int64_t lda, const T *u, co
     const int cols_per_block = GT * (vec ? E : 1);
     dim3 grid((unsigned)chunks, (unsigned)ceil_div(n, cols_per_block));
     double *usum = mu ? part + chunks * n : nullptr;  // chunks extra entries after the column partials
-    if (vec) gemv_t_kernel<T, true><<<grid, GT, 0, s>>>(A, m, n, lda, u, rpc, part, usum);
-    else gemv_t_kernel<T, false><<<grid, GT, 0, s>>>(A, m, n, lda, u, rpc, part, usum);
-    colsum_sub_kernel<T><<<(unsigned)ceil_div(n, 32), 256, 0, s>>>(part, chunks, n, alpha, vprev, z, mu, usum);
+    if (vec) gemv_t_kernel<T, true><<<grid, GT, 0, s>>>(A, m, n, lda, u, rpc, part, usum, gate);
+    else gemv_t_kernel<T, false><<<grid, GT, 0, s>>>(A, m, n, lda, u, rpc, part, usum, gate);
+    colsum_sub_kernel<T><<<(unsigned)ceil_div(n, 32), 256, 0, s>>>(part, chunks, n, alpha, vprev, z, mu, usum, y,
+                                                                  gate);
     note_launch(2);
+    return cudaGetLastError();
+}
+
+// Rows per chunk of the one-pass product: two CTAs per SM, whole groups of 32 rows.
+static int64_t gemv_nt_rpc(int64_t m) { return round_up(ceil_div(m, 2 * 152), 32); }
+int64_t gkl_gemv_nt_chunks(int64_t m) { return ceil_div(m, gemv_nt_rpc(m)); }
+
+bool gkl_one_pass_ok(int64_t m, int n, int64_t lda, const void *A) {
+    return n % 4 == 0 && lda % 4 == 0 && n <= 4 * GT * 4 && (reinterpret_cast<uintptr_t>(A) & 15) == 0 && m >= 1;
+}
+
+cudaError_t gkl_gemv_nt(const float *A, int64_t m, int n, int64_t lda, const float *v, const float *beta,
+                        const float *uprev, float *w, float *x, double *part, cudaStream_t s, const float *mu) {
+    if (!gkl_one_pass_ok(m, n, lda, A) || (reinterpret_cast<uintptr_t>(v) & 15) ||
+        (mu && (reinterpret_cast<uintptr_t>(mu) & 15)))
+        return cudaErrorInvalidValue;
+    const int64_t rpc = gemv_nt_rpc(m);
+    const int64_t chunks = ceil_div(m, rpc);
+    double *gsum = part + chunks * n;
+    const int nv = (n + 4 * GT - 1) / (4 * GT);
+    const dim3 grid((unsigned)chunks);
+    switch (nv) {
+        case 1: gemv_nt_kernel<1, 8><<<grid, GT, 0, s>>>(A, m, n, lda, v, beta, uprev, w, mu, rpc, part, gsum); break;
+        case 2: gemv_nt_kernel<2, 8><<<grid, GT, 0, s>>>(A, m, n, lda, v, beta, uprev, w, mu, rpc, part, gsum); break;
+        case 3: gemv_nt_kernel<3, 4><<<grid, GT, 0, s>>>(A, m, n, lda, v, beta, uprev, w, mu, rpc, part, gsum); break;
+        default: gemv_nt_kernel<4, 4><<<grid, GT, 0, s>>>(A, m, n, lda, v, beta, uprev, w, mu, rpc, part, gsum); break;
+    }
+    colsum_sub_kernel<float><<<(unsigned)ceil_div(n, 32), 256, 0, s>>>(part, chunks, n, nullptr, nullptr, x, mu, gsum,
+                                                                       nullptr, nullptr);
+    note_launch(2);
+    return cudaGetLastError();
+}
+
+cudaError_t gkl_recover(const float *x, float *Y, int j, int n, const float *beta, const float *coef,
+                        const float *alpha, const float *vj, float *z, int *flag, cudaStream_t s) {
+    if (j > 1024) return cudaErrorInvalidValue;
+    recover_kernel<<<1, 1024, 0, s>>>(x, Y, j, n, beta, coef, alpha, vj, z, flag);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -372,9 +582,16 @@ int64_t gkl_reorth_blocks(int64_t len) { return ceil_div(len, kReorthRows); }
 // w <- w - B (B^T w) twice (classical Gram-Schmidt, twice) against the first cnt rows of
 // Bt (cnt x len, ld); then nrm[0] = ||w|| and out = w / nrm[0].  coef: cnt scratch,
 // part: blocks * max(cnt, 1) scratch, sq: blocks scratch (blocks = gkl_reorth_blocks(len)).
+// (elementwise sum of two coefficient vectors: the total CGS2 coefficient of each basis vector)
+template <typename T>
+__global__ void coef_add_kernel(const T *__restrict__ c, int cnt, T *__restrict__ tot, bool first) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < cnt) tot[i] = first ? c[i] : tot[i] + c[i];
+}
+
 template <typename T>
 cudaError_t gkl_reorth_normalize(const T *Bt, int64_t ld, int cnt, T *w, int64_t len, T *coef, T *part, T *sq,
-                                 T *nrm, T *out, int *status, cudaStream_t s) {
+                                 T *nrm, T *out, int *status, cudaStream_t s, T *ctot) {
     constexpr int E = V4<T>::n;
     const int64_t rpb = kReorthRows;  // a multiple of 32 E
     const int64_t nblk = ceil_div(len, rpb);
@@ -387,6 +604,10 @@ cudaError_t gkl_reorth_normalize(const T *Bt, int64_t ld, int cnt, T *w, int64_t
         if (vec) multi_dot_kernel<T, true><<<(unsigned)nblk, GT, smem_d, s>>>(Bt, ld, cnt, w, len, rpb, part);
         else multi_dot_kernel<T, false><<<(unsigned)nblk, GT, smem_d, s>>>(Bt, ld, cnt, w, len, rpb, part);
         sum_parts_kernel<T><<<(unsigned)ceil_div(cnt, 8), 256, 0, s>>>(part, nblk, cnt, coef);
+        if (ctot) {
+            coef_add_kernel<T><<<(unsigned)ceil_div(cnt, 256), 256, 0, s>>>(coef, cnt, ctot, pass == 0);
+            note_launch();
+        }
         if (vec) multi_axpy_kernel<T, true><<<(unsigned)nblk, GT, smem_c, s>>>(Bt, ld, cnt, coef, w, len, rpb, sq);
         else multi_axpy_kernel<T, false><<<(unsigned)nblk, GT, smem_c, s>>>(Bt, ld, cnt, coef, w, len, rpb, sq);
         note_launch(3);
@@ -413,10 +634,9 @@ cudaError_t gkl_bidiag(const T *alpha, const T *beta, int steps, double *B, cuda
     template cudaError_t gkl_gemv_n<T>(const T *, int64_t, int, int64_t, const T *, const T *, const T *, T *,        \
                                        cudaStream_t, const T *);                                                     \
     template cudaError_t gkl_gemv_t<T>(const T *, int64_t, int, int64_t, const T *, const T *, const T *, T *,       \
-                                       double *,                                                                     \
-                                       cudaStream_t, const T *);                                                     \
+                                       double *, cudaStream_t, const T *, T *, const int *);                         \
     template cudaError_t gkl_reorth_normalize<T>(const T *, int64_t, int, T *, int64_t, T *, T *, T *, T *, T *,     \
-                                                 int *, cudaStream_t);                                               \
+                                                 int *, cudaStream_t, T *);                                          \
     template cudaError_t gkl_bidiag<T>(const T *, const T *, int, double *, cudaStream_t);
 INST_GKL(float)
 INST_GKL(double)

@@ -1022,6 +1022,11 @@ rsvd_status run_exact_large(rsvd_plan *P, T *A, double *S, T *U, T *V) {
 struct GklBufs {
     void *Ut, *Vt, *w, *z, *part, *coef, *sq, *alpha, *beta, *nrm, *X, *Y;
     double *B, *gpart;
+    // the one-pass form (float32): x = A^T A v, the stored y_i = A^T u_i, the summed CGS2
+    // coefficients, the second-pass flag and the fused product's partials
+    float *x1, *Yr, *ctot;
+    int *flag;
+    double *ntpart;
 };
 
 GklBufs gkl_carve(rsvd_plan *P, int steps, char *base, size_t *bytes) {
@@ -1046,6 +1051,11 @@ GklBufs gkl_carve(rsvd_plan *P, int steps, char *base, size_t *bytes) {
     b.X = c.take(es * sp * sp);
     b.Y = c.take(es * sp * sp);
     b.B = (double *)c.take(sizeof(double) * steps * steps);
+    b.x1 = (float *)c.take(sizeof(float) * n);
+    b.Yr = (float *)c.take(sizeof(float) * steps * n);
+    b.ctot = (float *)c.take(sizeof(float) * (steps + 1));
+    b.flag = (int *)c.take(sizeof(int));
+    b.ntpart = (double *)c.take(sizeof(double) * gkl_gemv_nt_chunks(m) * (n + 1));
     *bytes = c.off;
     return b;
 }
@@ -1086,20 +1096,42 @@ rsvd_status run_gkl(rsvd_plan *P, T *A, const T *v1, int steps, double *S, T *U,
         CK(copy2d<T, T>(v1, 1, z, 1, n, 1, 1, s));
         CK(gkl_reorth_normalize<T>(Vt, n, 0, z, n, coef, part, sq, nrm, Vt, P->status, s));
     }
+    // float32: one read of A per step (A^T u_j recovered by linearity, a gated second pass
+    // where the recovery would lose accuracy), unless RSVD_FLAG_GKL_TWO_PASS
+    bool one = false;
+    if constexpr (sizeof(T) == 4)
+        one = !(P->flags & RSVD_FLAG_GKL_TWO_PASS) && gkl_one_pass_ok(m, (int)n, n, A) &&
+              (reinterpret_cast<uintptr_t>(Vt) & 15) == 0 && n % 4 == 0 &&
+              (!mu || (reinterpret_cast<uintptr_t>(mu) & 15) == 0) && steps <= 1024;
     for (int j = 0; j < steps; j++) {
         {
-            Span sp_(P, RSVD_STAGE_AX);   // w = A v_j - beta_{j-1} u_{j-1}
-            CK(gkl_gemv_n<T>(A, m, (int)n, n, Vt + (int64_t)j * n, j ? beta + j - 1 : nullptr,
-                             j ? Ut + (int64_t)(j - 1) * m : nullptr, w, s, mu));
+            Span sp_(P, RSVD_STAGE_AX);   // w = A v_j - beta_{j-1} u_{j-1}  (and x = A^T (A v_j) in one pass)
+            if constexpr (sizeof(T) == 4) {
+                if (one)
+                    CK(gkl_gemv_nt(A, m, (int)n, n, Vt + (int64_t)j * n, j ? beta + j - 1 : nullptr,
+                                   j ? Ut + (int64_t)(j - 1) * m : nullptr, w, b.x1, b.ntpart, s, mu));
+            }
+            if (!one)
+                CK(gkl_gemv_n<T>(A, m, (int)n, n, Vt + (int64_t)j * n, j ? beta + j - 1 : nullptr,
+                                 j ? Ut + (int64_t)(j - 1) * m : nullptr, w, s, mu));
         }
         {
             Span sp_(P, RSVD_STAGE_ORTH);  // CGS2 against u_0..u_{j-1}; alpha_j = ||w||; u_j = w / alpha_j
-            CK(gkl_reorth_normalize<T>(Ut, m, j, w, m, coef, part, sq, alpha + j, Ut + (int64_t)j * m, P->status, s));
+            CK(gkl_reorth_normalize<T>(Ut, m, j, w, m, coef, part, sq, alpha + j, Ut + (int64_t)j * m, P->status, s,
+                                       one ? (T *)b.ctot : nullptr));
         }
         {
             Span sp_(P, RSVD_STAGE_ATX);  // z = A^T u_j - alpha_j v_j
-            CK(gkl_gemv_t<T>(A, m, (int)n, n, Ut + (int64_t)j * m, alpha + j, Vt + (int64_t)j * n, z, b.gpart, s,
-                             mu));
+            if constexpr (sizeof(T) == 4) {
+                if (one) {
+                    CK(gkl_recover(b.x1, b.Yr, j, (int)n, beta, b.ctot, alpha, Vt + (int64_t)j * n, z, b.flag, s));
+                    CK(gkl_gemv_t<T>(A, m, (int)n, n, Ut + (int64_t)j * m, alpha + j, Vt + (int64_t)j * n, z, b.gpart,
+                                     s, mu, b.Yr + (int64_t)j * n, b.flag));
+                }
+            }
+            if (!one)
+                CK(gkl_gemv_t<T>(A, m, (int)n, n, Ut + (int64_t)j * m, alpha + j, Vt + (int64_t)j * n, z, b.gpart, s,
+                                 mu));
         }
         {
             Span sp_(P, RSVD_STAGE_ORTH);  // CGS2 against v_0..v_j; beta_j = ||z||; v_{j+1} = z / beta_j
@@ -1648,7 +1680,7 @@ rsvd_status rsvd_set_jacobi_sweep_cap(int cap) {
 }
 
 rsvd_status rsvd_plan_set_flags(rsvd_plan_t P, unsigned flags) {
-    if (!P || (flags & ~(unsigned)RSVD_FLAG_NO_CENTER)) return RSVD_ERR_ARG;
+    if (!P || (flags & ~(unsigned)(RSVD_FLAG_NO_CENTER | RSVD_FLAG_GKL_TWO_PASS))) return RSVD_ERR_ARG;
     P->flags = flags;
     return RSVD_OK;
 }

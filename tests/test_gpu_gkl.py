@@ -25,15 +25,60 @@ def built():
     build.build()
 
 
-def _run(A_dev, v1_dev, k, steps, dtype):
+def _run(A_dev, v1_dev, k, steps, dtype, flags=0):
     m, n = A_dev.shape
     S = torch.zeros(k, dtype=torch.float64, device=A_dev.device)
     U = torch.zeros(m, k, dtype=A_dev.dtype, device=A_dev.device)
     V = torch.zeros(n, k, dtype=A_dev.dtype, device=A_dev.device)
     with g.rsvd_plan_create(m, n, k, 0, 0, dtype) as plan:
+        g.check(g.rsvd_plan_set_flags(plan, flags), "flags")
         g.check(g.svd_truncated_krylov(plan, A_dev, v1_dev, steps, S, U, V), "svd_truncated_krylov")
         st = g.rsvd_plan_sync(plan)
     return st, S, U, V
+
+
+def _check_f32(A32, v1, k, steps, S, U, V, tag=""):
+    Ac, _, _ = oracle.center(A32.double())
+    s, Uo, Vo, al, be = oracle.gkl(Ac, v1.double(), steps=steps, k=k)
+    S = S.cpu().numpy()
+    err = np.abs(S - s).max() / s[0]
+    print(f"{tag}: max sigma error {err:.2e} sigma_1")
+    assert err <= 1e-5
+    Ud, Vd = U.cpu().double().numpy(), V.cpu().double().numpy()
+    assert np.abs(Ud.T @ Ud - np.eye(k)).max() <= 1e-5
+    assert np.abs(Vd.T @ Vd - np.eye(k)).max() <= 1e-5
+    assert np.abs(Ac @ Vd - Ud * S).max() <= 1e-5 * s[0]
+
+
+@pytest.mark.parametrize("scale", [200.0, 10.0])
+def test_gkl_f32_one_pass_and_two_pass_match_oracle(scale):
+    """float32 plans read A once per step (A^T u_j recovered by linearity); on the steep
+    exp(-i/10) spectrum the recovery's bound sends steps to the second read of A.  Both
+    forms and the forced two-pass form agree with the oracle from the same v1."""
+    m, n, k, steps = 20011, 512, 40, 120
+    i = torch.arange(1, n + 1, dtype=torch.float64)
+    A = synth.prescribed(m, n, torch.exp(-i / scale), 20481, 20482)
+    A32 = A.float()
+    v1 = synth.unit_vector(n, 20483, dtype=torch.float32)
+    dev = torch.device("cuda")
+    for flags, tag in [(0, "one pass"), (g.RSVD_FLAG_GKL_TWO_PASS, "two passes")]:
+        st, S, U, V = _run(A32.to(dev), v1.to(dev), k, steps, g.RSVD_F32, flags)
+        assert st == g.RSVD_OK
+        _check_f32(A32, v1, k, steps, S, U, V, f"exp(-i/{scale:g}) {tag}")
+
+
+@pytest.mark.slow
+def test_gkl_f32_lanczos_width_matches_oracle():
+    """The Lanczos workload's columns, steps and k (2048, 150, 100) at 262144 rows, from its v1."""
+    m, n, k, steps = 262144, 2048, 100, 150
+    dev = torch.device("cuda")
+    A, sigma, ex = synth.workload("gkl_fp32_1048576x2048", m=m, device=dev)
+    A32 = A.float()
+    del A
+    v1 = ex["v1"]
+    st, S, U, V = _run(A32, v1.to(dev), k, steps, g.RSVD_F32)
+    assert st == g.RSVD_OK
+    _check_f32(A32.cpu(), v1.cpu(), k, steps, S, U, V, "262144 x 2048, 150 steps")
 
 
 @pytest.mark.parametrize("m,n,k,steps", [(20011, 301, 20, 60), (5000, 130, 10, 40)])
