@@ -77,7 +77,11 @@ enum {
 /* plan flags */
 enum {
     RSVD_FLAG_NO_CENTER = 1,     /* A is already centred (mu = 0)                                     */
-    RSVD_FLAG_GKL_TWO_PASS = 2   /* svd_truncated_krylov reads A twice per step (see there)           */
+    RSVD_FLAG_GKL_TWO_PASS = 2,  /* svd_truncated_krylov reads A twice per step (see there)           */
+    RSVD_FLAG_SMALL_F32 = 4,     /* RSVD_BF16 / RSVD_FP8_E4M3: small SVD of B without the float64
+                                    refinement (float32 rotations, float64 Rayleigh quotients)       */
+    RSVD_FLAG_SMALL_FP64 = 8     /* RSVD_F32 rsvd / block Krylov: add the float64 refinement of the
+                                    small SVD of B (default for BF16 / e4m3; see rsvd)               */
 };
 
 typedef struct rsvd_plan *rsvd_plan_t;
@@ -144,8 +148,15 @@ rsvd_status rsvd_plan_sync(rsvd_plan_t plan);
  * terms (float32-accurate); the column means enter as exact rank-1
  * corrections; the Cholesky of CholeskyQR2 (final basis and T) runs in
  * float64, the single-pass re-orthonormalisations of the power steps in
- * float32, and the singular values of R are float64 Rayleigh quotients of its
- * float32 Jacobi vectors.
+ * float32.  The small SVD of B (the SVD of T's factor R, Sec. 3.1.2 step 6) is
+ * taken in float64: a float32 one-sided Jacobi start, then two Newton-type
+ * float64 refinement steps (Ogita and Aishima's refinement of the SVD by matrix
+ * products) that make U_R, W and sigma float64-accurate for the singular values
+ * above 1e-5 sigma_1 (smaller ones lie beneath the float32 accuracy of T and keep
+ * the start's absolute accuracy); about 0.5 ms at l = 288.  RSVD_FLAG_SMALL_F32
+ * skips the refinement (float32 rotations, float64 Rayleigh-quotient values);
+ * RSVD_FLAG_SMALL_FP64 adds it to RSVD_F32 single solves, which otherwise use
+ * that float32 form (their stated tolerance, 1e-5 sigma_1, needs no more).
  * RSVD_FP8_E4M3 plans (n a multiple of 16, l <= 288) solve for A diag(s): the
  * sketch and power products run on e4m3 operands (the small operand diag(s) Z
  * and the basis Q quantised per column with their own scales, which the

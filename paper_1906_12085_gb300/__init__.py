@@ -18,7 +18,7 @@ __all__ = [
     "RSVD_F64", "RSVD_F32", "RSVD_BF16", "RSVD_FP8_E4M3",
     "RSVD_OK", "RSVD_ERR_ARG", "RSVD_ERR_OOM", "RSVD_ERR_CHOL", "RSVD_ERR_NOCONV", "RSVD_ERR_TIMEOUT",
     "RSVD_ERR_CUDA", "RSVD_ERR_UNSUPPORTED", "RSVD_WARN_K_GT_k", "RSVD_WARN_RANK_DEFICIENT", "RSVD_EXACT_GRAM", "RSVD_EXACT_QR_JACOBI",
-    "RSVD_FLAG_NO_CENTER", "RSVD_FLAG_GKL_TWO_PASS", "RsvdError", "lib", "library_path", "header_functions",
+    "RSVD_FLAG_NO_CENTER", "RSVD_FLAG_GKL_TWO_PASS", "RSVD_FLAG_SMALL_F32", "RSVD_FLAG_SMALL_FP64", "RsvdError", "lib", "library_path", "header_functions",
     "rsvd_plan_create", "rsvd_plan_destroy", "rsvd_plan_workspace_bytes", "rsvd_plan_set_flags",
     "rsvd_plan_sync", "rsvd", "svd_exact", "svd_truncated_krylov", "pca_threshold", "rsvd_plan_fro2",
     "rsvd_status_string", "check", "rsvd_plan_profile", "rsvd_plan_profile_read", "rsvd_launch_count",
@@ -41,6 +41,8 @@ RSVD_WARN_RANK_DEFICIENT = 2
 RSVD_EXACT_GRAM, RSVD_EXACT_QR_JACOBI = 0, 1
 RSVD_FLAG_NO_CENTER = 1
 RSVD_FLAG_GKL_TWO_PASS = 2
+RSVD_FLAG_SMALL_F32 = 4
+RSVD_FLAG_SMALL_FP64 = 8
 RSVD_BATCH_MAX = 256
 # tracing stages (RSVD_STAGE_* in include/rsvd.h)
 STAGES = ("center", "ax", "atx", "orth", "small", "finish")

@@ -208,6 +208,14 @@ size_t jacobi_scratch_bytes(int l, size_t ta);
 template <typename To>
 cudaError_t sv_refine(const double *R, int l, int lp, const To *UR, const To *W, double *sig, cudaStream_t s);
 
+// Float64 SVD of R from the float32 jacobi_osvd result: two Newton-type refinement steps
+// (Ogita-Aishima) built from l x l float64 products update U_R and W (lp x lp float32,
+// in place: rounded back at the end) and give sig, the float64 singular values,
+// descending.  ws: svd_refine64_bytes(l) bytes; l <= 4096.
+size_t svd_refine64_bytes(int l);
+cudaError_t svd_refine64(const double *R, int l, int lp, float *UR, float *W, double *sig, double *ws,
+                         cudaStream_t s);
+
 // ------------------------------------------------------ bfloat16 precision form
 // Y (m x N) = A Z - 1 c^T with A m x n bfloat16 (lda), Z given as Zt (N x n
 // bfloat16, ldz); c (N floats) may be NULL.  n, lda, ldz multiples of 8.

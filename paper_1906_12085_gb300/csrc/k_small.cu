@@ -1051,7 +1051,10 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(const double *__restri
                 Tm c = 1, s = 0;
                 if (q < n) {
                     const Tm apq = M[p * n + q], app = M[p * n + p], aqq = M[q * n + q];
-                    if (apq != Tm(0) && fabs(apq) > rel * sqrt(fabs(app * aqq)) && fabs(apq) > floor_v) {
+                    // sqrt of each diagonal entry: their product overflows float32 for column
+                    // norms above ~4e9, which would stop every rotation
+                    if (apq != Tm(0) && fabs(apq) > rel * (sqrt(fabs(app)) * sqrt(fabs(aqq))) &&
+                        fabs(apq) > floor_v) {
                         const Tm theta = (aqq - app) / (Tm(2) * apq);
                         const Tm t = (theta >= Tm(0) ? Tm(1) : Tm(-1)) / (fabs(theta) + sqrt(Tm(1) + theta * theta));
                         c = Tm(1) / sqrt(Tm(1) + t * t);
@@ -1480,7 +1483,10 @@ cudaError_t jacobi_eig_t(const double *G, int n, double *lam, double *V, int *st
                          double floor_rel) {
     const int L = n + (n & 1);
     const size_t smem = sizeof(Tm) * (2 * (size_t)n * n + L + (L & 1)) + sizeof(int) * (2 * L) + 16;
-    cudaFuncSetAttribute(jacobi_eig_kernel<Tm>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (n < 1 || smem > 227 * 1024) return cudaErrorInvalidValue;  // one CTA holds M and V
+    const cudaError_t e = cudaFuncSetAttribute(jacobi_eig_kernel<Tm>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+    if (e != cudaSuccess) return e;
     jacobi_eig_kernel<Tm><<<1, 1024, smem, s>>>(G, n, lam, V, status, sweep_cap(50), floor_rel);
     note_launch();
     return cudaGetLastError();

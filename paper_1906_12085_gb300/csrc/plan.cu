@@ -62,6 +62,7 @@ struct rsvd_plan {
     unsigned *g64count = nullptr;  // CTA counter of the float64 Gram reduction (kept zero between uses)
     uint64_t nfact = 0;            // factorisations of the current solve (seeds of the column refills)
     void *chol_ws = nullptr, *jac_ws = nullptr;  // global l x l blocks of the small solvers (large l only)
+    double *ref64 = nullptr;                     // float64 refinement of the small SVD (float32 storage types)
     void *Hk = nullptr;                          // block Krylov basis, m x Wp
     int *bk_flag = nullptr;                      // block Krylov: directions of a block to refill (lp ints)
     // float32 block Krylov plans: float64 copies of T and its CholeskyQR2 bases (n x Wp) and
@@ -199,6 +200,7 @@ void carve(rsvd_plan *P, Carver &c) {
         P->chol_ws = c.take(chol_scratch_bytes((int)sq, sizeof(double)));
     if (P->lpc > 160)           // and of the float32 Jacobi
         P->jac_ws = c.take(jacobi_scratch_bytes(P->lpc, sizeof(float)));
+    if (P->dtype != RSVD_F64) P->ref64 = (double *)c.take(svd_refine64_bytes((int)P->lpc));
     if (P->bk_blocks) {
         P->Hk = c.take(es * m * P->lpc);
         P->bk_flag = (int *)c.take(sizeof(int) * P->lpc);
@@ -253,6 +255,13 @@ void carve(rsvd_plan *P, Carver &c) {
         P->tcpart_elems = te;
         P->tcpart = (float *)c.take(sizeof(float) * te);
     }
+}
+
+// The small SVD of B in float64 (refinement of the float32 Jacobi start): BF16 / e4m3
+// plans unless RSVD_FLAG_SMALL_F32, float32 plans when RSVD_FLAG_SMALL_FP64.
+bool small_fp64(const rsvd_plan *P) {
+    if (P->dtype == RSVD_BF16 || P->dtype == RSVD_FP8_E4M3) return !(P->flags & RSVD_FLAG_SMALL_F32);
+    return P->dtype == RSVD_F32 && (P->flags & RSVD_FLAG_SMALL_FP64) && P->ref64;
 }
 
 // Records a pair of events around a stage group when tracing is enabled.
@@ -535,7 +544,12 @@ rsvd_status ritz(rsvd_plan *P, const T *A, const T *mu, const T *Q, double *S, T
         }
         if ((st = check_basis<T>(P, Qz, n, l, lp))) return st;                // Q_T^T Q_T = I
         CK(jacobi_osvd<T, T>(P->Rt, l, lp, P->sig, UR, W, P->status, s, P->jac_ws));     // R = U_R Sigma W^T
-        CK(sv_refine<T>(P->Rt, l, lp, UR, W, P->sig, s));                     // sigma_i = u_i^T R w_i (float64)
+        if constexpr (sizeof(T) == 4) {
+            if (small_fp64(P)) CK(svd_refine64(P->Rt, l, lp, (float *)UR, (float *)W, P->sig, P->ref64, s));
+            else CK(sv_refine<T>(P->Rt, l, lp, UR, W, P->sig, s));                 // sigma_i = u_i^T R w_i (float64)
+        } else {
+            CK(sv_refine<T>(P->Rt, l, lp, UR, W, P->sig, s));
+        }
     }
     {
         Span sp(P, RSVD_STAGE_FINISH);
@@ -768,10 +782,12 @@ rsvd_status run_rsvd_bf16(rsvd_plan *P, const void *A, const float *Omega, doubl
         Span sp(P, RSVD_STAGE_SMALL);
         if ((st = cqr2<float>(P, Tn, n, l, lp, Qz, Tmpn, true))) return st;
         if ((st = check_basis<float>(P, Qz, n, l, lp))) return st;
-        // float32 rotations, float64 Rayleigh-quotient values (the float64 rate of this
-        // GPU is 1/58 of float32: a float64 Jacobi of l = 112 takes ~50 ms)
+        // float32 rotations (the float64 rate of this GPU is 1/58 of float32: a float64
+        // Jacobi of l = 112 takes ~50 ms), then the float64 refinement built from l x l
+        // products over all SMs (or float64 Rayleigh-quotient values only)
         CK(jacobi_osvd<float, float>(P->Rt, l, lp, P->sig, UR, W, P->status, s, P->jac_ws));
-        CK(sv_refine<float>(P->Rt, l, lp, UR, W, P->sig, s));
+        if (small_fp64(P)) CK(svd_refine64(P->Rt, l, lp, UR, W, P->sig, P->ref64, s));
+        else CK(sv_refine<float>(P->Rt, l, lp, UR, W, P->sig, s));
     }
     {
         Span sp(P, RSVD_STAGE_FINISH);
@@ -856,7 +872,8 @@ rsvd_status run_rsvd_fp8(rsvd_plan *P, const void *A, const float *sc, const flo
         if ((st = cqr2<float>(P, Tn, n, l, lp, Qz, Tmpn, true))) return st;
         if ((st = check_basis<float>(P, Qz, n, l, lp))) return st;
         CK(jacobi_osvd<float, float>(P->Rt, l, lp, P->sig, UR, W, P->status, s, P->jac_ws));
-        CK(sv_refine<float>(P->Rt, l, lp, UR, W, P->sig, s));
+        if (small_fp64(P)) CK(svd_refine64(P->Rt, l, lp, UR, W, P->sig, P->ref64, s));
+        else CK(sv_refine<float>(P->Rt, l, lp, UR, W, P->sig, s));
     }
     {
         Span sp(P, RSVD_STAGE_FINISH);
@@ -1680,7 +1697,9 @@ rsvd_status rsvd_set_jacobi_sweep_cap(int cap) {
 }
 
 rsvd_status rsvd_plan_set_flags(rsvd_plan_t P, unsigned flags) {
-    if (!P || (flags & ~(unsigned)(RSVD_FLAG_NO_CENTER | RSVD_FLAG_GKL_TWO_PASS))) return RSVD_ERR_ARG;
+    if (!P || (flags & ~(unsigned)(RSVD_FLAG_NO_CENTER | RSVD_FLAG_GKL_TWO_PASS | RSVD_FLAG_SMALL_F32 |
+                                   RSVD_FLAG_SMALL_FP64)))
+        return RSVD_ERR_ARG;
     P->flags = flags;
     return RSVD_OK;
 }

@@ -8,6 +8,8 @@ Reported and bounded (tolerances stated here, derived in the design notes;
   sigma: |s_i - s_i^O| <= 1e-4 sigma_1^O for i <= k;
   gap:   (||A - U U^T A||_F - ||A - U^O U^O^T A||_F) / ||A||_F <= 1e-4;
   U, V orthonormal to 1e-5."""
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -140,5 +142,61 @@ def test_e4m3_rsvd_matches_oracle_on_stored_matrix(m, n, k, p, q, shift):
     print(f"e4m3 rsvd {m}x{n} k={k}: max sigma error {err:.2e} sigma_1, projection gap {gap:.2e} ||A||_F")
     assert err <= 1e-3, err
     assert gap <= 1e-3, gap
+    assert np.abs(Ug.T @ Ug - np.eye(k)).max() <= 1e-5
+    assert np.abs(Vg.T @ Vg - np.eye(k)).max() <= 1e-5
+
+
+@pytest.fixture(scope="module")
+def mixed_262144x4096():
+    """The precision form's workload with a quarter of its rows: 262144 x 4096, sigma_i = i^-1.5,
+    Haar factors (built in float64 on the device), rounded to float32; Omega 4096 x 288."""
+    A, sig, ex = synth.workload("mixed_rsvd_1048576x4096", m=262144, device="cuda")
+    A32 = A.float().cpu().numpy()
+    del A
+    torch.cuda.empty_cache()
+    return A32, ex["omega"].cpu()
+
+
+@pytest.mark.slow
+@pytest.mark.skipif(os.environ.get("RSVD_TEST_FULL") != "1",
+                    reason="about 6 minutes of float64 oracle time per case; set RSVD_TEST_FULL=1")
+@pytest.mark.parametrize("dtype", ["bf16", "fp8"])
+def test_precision_form_at_262144x4096_l288_matches_oracle(mixed_262144x4096, dtype):
+    """k = 256, p = 32, q = 3 on the stored matrix; the oracle runs in float64 on the decoded
+    matrix.  Bounds as in the smaller cases: sigma within 1e-4 (BF16) / 1e-3 (e4m3) of
+    sigma_1, the same for the projection gap relative to ||A||_F; U, V orthonormal to 1e-5."""
+    A32, Om = mixed_262144x4096
+    m, n = A32.shape
+    k, p, q = 256, 32, 3
+    dev = torch.device("cuda")
+    if dtype == "bf16":
+        codes = oracle.quantize_bf16(A32)
+        Ad = oracle.dequantize_bf16(codes)
+        A, sc, dt, tol = torch.from_numpy(codes.view(np.int16)).to(dev), None, g.RSVD_BF16, 1e-4
+    else:
+        codes, scales = oracle.quantize_e4m3(A32)
+        Ad = oracle.dequantize_e4m3(codes, scales)
+        A, sc, dt, tol = torch.from_numpy(codes).to(dev), torch.from_numpy(scales).to(dev), g.RSVD_FP8_E4M3, 1e-3
+    del codes
+    S = torch.zeros(k, dtype=torch.float64, device=dev)
+    U = torch.zeros(m, k, device=dev)
+    V = torch.zeros(n, k, device=dev)
+    with g.rsvd_plan_create(m, n, k, p, q, dt) as plan:
+        g.check(g.rsvd(plan, A, sc, Om.to(dev), S, U, V), "rsvd " + dtype)
+        assert g.rsvd_plan_sync(plan) == g.RSVD_OK
+        fro2 = g.rsvd_plan_fro2(plan)
+    torch.cuda.synchronize()
+    del A
+    Ac, mu, fro2o = oracle.center(Ad)
+    del Ad
+    assert abs(fro2 - fro2o) <= 1e-6 * fro2o
+    s, Uo, Vo = oracle.rsvd(Ac, Om.double(), q=q, k=k)
+    Sg, Ug, Vg = S.cpu().numpy(), U.cpu().double().numpy(), V.cpu().double().numpy()
+    err = np.abs(Sg - s).max() / s[0]
+    gap = (_proj_residual(Ac, Ug) - _proj_residual(Ac, Uo)) / np.sqrt(fro2o)
+    print(f"{dtype} rsvd {m}x{n} k={k} p={p} q={q}: max sigma error {err:.2e} sigma_1, "
+          f"projection gap {gap:.2e} ||A||_F")
+    assert err <= tol, err
+    assert gap <= tol, gap
     assert np.abs(Ug.T @ Ug - np.eye(k)).max() <= 1e-5
     assert np.abs(Vg.T @ Vg - np.eye(k)).max() <= 1e-5

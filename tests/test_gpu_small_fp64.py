@@ -1,0 +1,91 @@
+"""GPU: the small SVD of B in float64 (Sec. 3.1.2 step 6) -- the float32 one-sided Jacobi
+start refined by two Newton-type float64 steps built from l x l products.
+
+* float32 plans with RSVD_FLAG_SMALL_FP64 on an exactly rank-40 matrix (l = 48 > rank,
+  so the sketch captures the range exactly): sigma within the float32 path's 1e-5 sigma_1
+  of the prescribed values and the Ritz pairs satisfy ||A v_i - sigma_i u_i|| <= 1e-6 sigma_1, no worse
+  than without the flag (the float32 Jacobi's rotations leave ~sqrt(l) u32 between the
+  vectors of R's SVD; the float64 ones leave only the float32 rounding of the output).
+* BF16 plans (refinement on by default) against RSVD_FLAG_SMALL_F32: both within the
+  form's 1e-4 sigma_1 of the float64 oracle on the stored matrix, and within 1e-5
+  sigma_1 of each other.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1906_12085_gb300 as g
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1906_12085_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def _solve(A, dt, k, p, q, Om, flags=0, sc=None):
+    dev = A.device
+    m, n = A.shape
+    S = torch.zeros(k, dtype=torch.float64, device=dev)
+    U = torch.zeros(m, k, device=dev)
+    V = torch.zeros(n, k, device=dev)
+    with g.rsvd_plan_create(m, n, k, p, q, dt) as plan:
+        g.check(g.rsvd_plan_set_flags(plan, flags))
+        g.check(g.rsvd(plan, A, sc, Om, S, U, V), "rsvd")
+        st = g.rsvd_plan_sync(plan)
+    torch.cuda.synchronize()
+    return st, S, U, V
+
+
+@pytest.mark.parametrize("q", [0, 2])
+def test_f32_small_fp64_on_exact_rank(q):
+    m, n, r, k, p = 30011, 384, 40, 40, 8
+    sig = torch.pow(2.0, -torch.arange(r, dtype=torch.float64) / 6.0)
+    A64 = synth.prescribed(m, n, sig, 51001, 51002).to("cuda")
+    A = A64.float().contiguous()
+    Om = synth.gaussian(n, k + p, seed=51003, dtype=torch.float32).to("cuda")
+    res = {}
+    for flags in (0, g.RSVD_FLAG_SMALL_FP64):
+        st, S, U, V = _solve(A.clone(), g.RSVD_F32, k, p, q, Om, flags)
+        assert st == g.RSVD_OK
+        err = (S.cpu() - sig).abs().max().item()
+        assert err <= 1e-5, (flags, err)
+        A32 = A.double()
+        Ac = A32 - A32.mean(dim=0, keepdim=True)
+        R = Ac @ V.double() - U.double() * S.unsqueeze(0)
+        res[flags] = R.norm(dim=0).max().item()
+        assert torch.allclose(U.double().T @ U.double(), torch.eye(k, dtype=torch.float64, device="cuda"), atol=1e-5)
+    print(f"q={q}: max ||A v - sigma u|| float32 small SVD {res[0]:.2e}, float64 {res[g.RSVD_FLAG_SMALL_FP64]:.2e}")
+    assert res[g.RSVD_FLAG_SMALL_FP64] <= 1e-6
+    assert res[g.RSVD_FLAG_SMALL_FP64] <= 1.5 * res[0] + 1e-7
+
+
+def test_bf16_small_svd_float64_default_and_float32_flag():
+    m, n, k, p, q = 20011, 512, 256, 32, 2
+    sig = synth.spectrum_power(n, 1.5)
+    A64 = synth.prescribed(m, n, sig, 51011, 51012)
+    codes = oracle.quantize_bf16(A64.float().numpy())
+    Ad = oracle.dequantize_bf16(codes)
+    Om = synth.gaussian(n, k + p, seed=51013, dtype=torch.float32)
+    A = torch.from_numpy(codes.view(np.int16)).to("cuda")
+    Ac, mu, fro2o = oracle.center(Ad)
+    s, Uo, Vo = oracle.rsvd(Ac, Om.double(), q=q, k=k)
+    out = {}
+    for flags in (0, g.RSVD_FLAG_SMALL_F32):
+        st, S, U, V = _solve(A, g.RSVD_BF16, k, p, q, Om.to("cuda"), flags)
+        assert st == g.RSVD_OK
+        Sg = S.cpu().numpy()
+        err = np.abs(Sg - s).max() / s[0]
+        assert err <= 1e-4, (flags, err)
+        Vg = V.cpu().double().numpy()
+        assert np.abs(Vg.T @ Vg - np.eye(k)).max() <= 1e-5
+        out[flags] = Sg
+        print(f"bf16 flags={flags}: max sigma error {err:.2e} sigma_1")
+    assert np.abs(out[0] - out[g.RSVD_FLAG_SMALL_F32]).max() <= 1e-5 * s[0]
