@@ -61,6 +61,7 @@ typedef enum {
     RSVD_ERR_TIMEOUT = -5,      /* a bounded device wait gave up (a product pipeline)  */
     RSVD_ERR_CUDA = -6,         /* a CUDA runtime call or kernel launch failed         */
     RSVD_ERR_UNSUPPORTED = -8,  /* size or dtype outside what this build implements    */
+    RSVD_ERR_REDUCE = -9,       /* rsvd_sharded: the caller's reduction reported failure */
     RSVD_WARN_K_GT_k = 1,       /* the threshold t is not reached within the k values  */
     RSVD_WARN_RANK_DEFICIENT = 2 /* numerically rank-deficient input: a basis Cholesky
                                    needed its shift or removed dependent columns, or a
@@ -169,6 +170,35 @@ rsvd_status rsvd_plan_sync(rsvd_plan_t plan);
  */
 rsvd_status rsvd(rsvd_plan_t plan, void *A, const float *col_scales, const void *Omega,
                  double *S, void *U, void *V);
+
+/*
+ * Row-sharded randomized PCA (Sec. 3.1.2 over a row-block partition of A; the
+ * paper runs one process).  Rank r of N holds the rows A_r of A = [A_1; ...; A_N]
+ * (m_total rows in all) and calls rsvd_sharded with its own plan, created with
+ * m = its row count (m >= n), the same n, k, p, q and dtype (RSVD_F32 or RSVD_F64)
+ * on every rank, and the same Omega.  Every product with A stays on the rank;
+ * what the method sums over rows is reduced across ranks by `allreduce`, a host
+ * function that must replace values[0 .. count) by their elementwise sum over all
+ * ranks (in rank-independent order, so that every rank receives the same numbers)
+ * and return 0 (anything else ends the solve with RSVD_ERR_REDUCE):
+ *   the column sums (n; the means follow), ||A - 1 mu^T||_F^2 (1), the Gram
+ *   matrix of every CholeskyQR pass and of the final basis (lp x lp, lp = l
+ *   rounded up to 16), Z = A^T Q of every power step and T = A^T Q (n x lp).
+ * The small steps after a reduction (CholeskyQR of Z and T, the SVD of R, V) run
+ * on every rank from the same numbers.  The reduced Gram matrices are factored in
+ * float64 with the breakdown shift; the fallback tiers of rsvd's CholeskyQR (which
+ * re-read the whole basis) are not used, so steep spectra that need them return
+ * RSVD_WARN_RANK_DEFICIENT or RSVD_ERR_CHOL here.
+ *   A     : this rank's m x n rows, read only.   Omega : n x l, as for rsvd.
+ *   S     : k doubles and V : n x k, the same on every rank.
+ *   U     : this rank's m x k rows of U.
+ * Direct launches with a stream synchronisation at every reduction (no graph).
+ * The first call allocates max(n, lp) x lp doubles of staging with cudaMalloc.
+ * Status as for rsvd (read with rsvd_plan_sync).
+ */
+typedef int (*rsvd_allreduce_fn)(double *values, int64_t count, void *ctx);
+rsvd_status rsvd_sharded(rsvd_plan_t plan, int64_t m_total, void *A, const void *Omega, double *S, void *U,
+                         void *V, rsvd_allreduce_fn allreduce, void *ctx);
 
 /*
  * All n singular triplets of A (Sec. 2.1 definition).

@@ -14,11 +14,14 @@ import ctypes
 import os
 import re
 
+import numpy as np
+
 __all__ = [
     "RSVD_F64", "RSVD_F32", "RSVD_BF16", "RSVD_FP8_E4M3",
     "RSVD_OK", "RSVD_ERR_ARG", "RSVD_ERR_OOM", "RSVD_ERR_CHOL", "RSVD_ERR_NOCONV", "RSVD_ERR_TIMEOUT",
     "RSVD_ERR_CUDA", "RSVD_ERR_UNSUPPORTED", "RSVD_WARN_K_GT_k", "RSVD_WARN_RANK_DEFICIENT", "RSVD_EXACT_GRAM", "RSVD_EXACT_QR_JACOBI",
-    "RSVD_FLAG_NO_CENTER", "RSVD_FLAG_GKL_TWO_PASS", "RSVD_FLAG_SMALL_F32", "RSVD_FLAG_SMALL_FP64", "RsvdError", "lib", "library_path", "header_functions",
+    "RSVD_FLAG_NO_CENTER", "RSVD_FLAG_GKL_TWO_PASS", "RSVD_FLAG_SMALL_F32", "RSVD_FLAG_SMALL_FP64", "RsvdError", "lib", "library_path", "header_functions", "RSVD_ERR_REDUCE", "ALLREDUCE_FN",
+    "allreduce_callback", "rsvd_sharded",
     "rsvd_plan_create", "rsvd_plan_destroy", "rsvd_plan_workspace_bytes", "rsvd_plan_set_flags",
     "rsvd_plan_sync", "rsvd", "svd_exact", "svd_truncated_krylov", "pca_threshold", "rsvd_plan_fro2",
     "rsvd_status_string", "check", "rsvd_plan_profile", "rsvd_plan_profile_read", "rsvd_launch_count",
@@ -38,6 +41,7 @@ RSVD_F64, RSVD_F32, RSVD_BF16, RSVD_FP8_E4M3 = 0, 1, 2, 3
 RSVD_OK, RSVD_ERR_ARG, RSVD_ERR_OOM, RSVD_ERR_CHOL, RSVD_ERR_NOCONV = 0, -1, -2, -3, -4
 RSVD_ERR_TIMEOUT, RSVD_ERR_CUDA, RSVD_ERR_UNSUPPORTED, RSVD_WARN_K_GT_k = -5, -6, -8, 1
 RSVD_WARN_RANK_DEFICIENT = 2
+RSVD_ERR_REDUCE = -9
 RSVD_EXACT_GRAM, RSVD_EXACT_QR_JACOBI = 0, 1
 RSVD_FLAG_NO_CENTER = 1
 RSVD_FLAG_GKL_TWO_PASS = 2
@@ -121,13 +125,15 @@ def lib() -> ctypes.CDLL:
     L.rsvd_block_krylov.argtypes = [vp, vp, vp, vp, vp, vp]
     L.rsvd_tune_clear.restype = None
     L.rsvd_set_jacobi_sweep_cap.argtypes = [i32]
+    L.rsvd_sharded.argtypes = [vp, i64, vp, vp, vp, vp, vp, ALLREDUCE_FN, vp]
     for f in ("rsvd_plan_create", "rsvd_plan_destroy", "rsvd_plan_set_flags", "rsvd_plan_sync", "rsvd",
               "svd_exact", "svd_truncated_krylov", "pca_threshold", "rsvd_plan_fro2", "rsvd_plan_profile",
               "rsvd_plan_profile_read", "rsvd_workspace_query", "rsvd_plan_create_in", "rsvd_batch_create",
               "rsvd_batch_run", "rsvd_batch_sync", "rsvd_batch_destroy", "rsvd_server_create",
               "rsvd_server_submit", "rsvd_server_poll", "rsvd_server_pending", "rsvd_server_destroy",
               "rsvd_autotune", "rsvd_tune_lookup", "rsvd_quantize", "rsvd_server_submit_ex",
-              "rsvd_plan_create_block_krylov", "rsvd_block_krylov", "rsvd_set_jacobi_sweep_cap"):
+              "rsvd_plan_create_block_krylov", "rsvd_block_krylov", "rsvd_set_jacobi_sweep_cap",
+              "rsvd_sharded"):
         getattr(L, f).restype = i32
     _lib = L
     return L
@@ -139,7 +145,7 @@ def header_functions() -> list[str]:
         text = f.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b([a-z_][a-z0-9_]*)\s*\(", text)) -
-                  {"if", "while", "for", "sizeof", "return", "defined"})
+                  {"if", "while", "for", "sizeof", "return", "defined", "int"})
 
 
 def rsvd_set_jacobi_sweep_cap(cap: int) -> int:
@@ -250,6 +256,30 @@ def rsvd_plan_sync(plan: Plan) -> int:
 
 def rsvd(plan: Plan, A, col_scales, Omega, S, U, V) -> int:
     return lib().rsvd(plan.handle, _ptr(A), _ptr(col_scales), _ptr(Omega), _ptr(S), _ptr(U), _ptr(V))
+
+
+# int allreduce(double *values, int64_t count, void *ctx): values <- their sum over all ranks
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.c_void_p)
+
+
+def allreduce_callback(reduce_inplace):
+    """Wrap reduce_inplace(buf) -- buf a float64 numpy array that must be replaced by its
+    elementwise sum over all ranks -- as the library's rsvd_allreduce_fn (returns 1 on an
+    exception).  Keep the returned object alive while the library may call it."""
+    def cb(values, count, ctx):
+        try:
+            reduce_inplace(np.ctypeslib.as_array(values, shape=(int(count),)))
+            return 0
+        except Exception:
+            return 1
+    return ALLREDUCE_FN(cb)
+
+
+def rsvd_sharded(plan: Plan, m_total: int, A, Omega, S, U, V, reduce_inplace) -> int:
+    """Row-sharded rsvd of this rank's rows A (see include/rsvd.h); reduce_inplace as for
+    allreduce_callback (e.g. shard.dist_allreduce() over a torch.distributed group)."""
+    fn = allreduce_callback(reduce_inplace)
+    return lib().rsvd_sharded(plan.handle, int(m_total), _ptr(A), _ptr(Omega), _ptr(S), _ptr(U), _ptr(V), fn, None)
 
 
 def rsvd_plan_create_block_krylov(m: int, n: int, k: int, b: int, iters: int, dtype: int = RSVD_F32,

@@ -82,6 +82,10 @@ cudaError_t column_sums(const T *X, int64_t rows, int64_t cols, int64_t ld, doub
                         cudaStream_t s);
 // *out = sum of count doubles (fixed order)
 cudaError_t sum_f64(const double *x, int64_t count, double *out, cudaStream_t s);
+// Column means from column sums over all row blocks of a row-sharded A: sum[i] *= inv_m
+// (in place) and mu_t = the means in T, zero-padded to npad.
+template <typename T>
+cudaError_t scale_means(double *sum, int64_t n, int64_t npad, double inv_m, T *mu_t, cudaStream_t s);
 // C[r][c] -= (x ? x[r] : 1) * y[c] for r < rows, c < cols
 template <typename T>
 cudaError_t rank1_sub(T *C, int64_t rows, int64_t cols, int64_t ldc, const T *x, const T *y, cudaStream_t s);

@@ -146,6 +146,21 @@ __global__ void mean_copy_kernel(const double *__restrict__ mu, int64_t n, int64
     if (i < npad) out[i] = i < n ? (T)mu[i] : T(0);
 }
 
+// sum[i] *= inv_m (column sums over all row blocks -> means), out = the means in T, padded
+template <typename T>
+__global__ void scale_means_kernel(double *__restrict__ sum, int64_t n, int64_t npad, double inv_m,
+                                   T *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npad) return;
+    if (i < n) {
+        const double mu = sum[i] * inv_m;
+        sum[i] = mu;
+        out[i] = (T)mu;
+    } else {
+        out[i] = T(0);
+    }
+}
+
 // C[r][c] -= (x ? x[r] : 1) * y[c]
 template <typename T>
 __global__ void rank1_sub_kernel(T *__restrict__ C, int64_t rows, int64_t cols, int64_t ldc, const T *__restrict__ x,
@@ -265,6 +280,13 @@ cudaError_t rank1_sub(T *C, int64_t rows, int64_t cols, int64_t ldc, const T *x,
 }
 
 template <typename T>
+cudaError_t scale_means(double *sum, int64_t n, int64_t npad, double inv_m, T *mu_t, cudaStream_t s) {
+    scale_means_kernel<T><<<(unsigned)ceil_div(npad, 256), 256, 0, s>>>(sum, n, npad, inv_m, mu_t);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t vecmat(const T *mu, const T *B, int64_t K, int64_t N, int64_t ldb, T *c, cudaStream_t s) {
     vecmat_kernel<T><<<(unsigned)ceil_div(N, 128), 128, 0, s>>>(mu, B, K, N, ldb, c);
     note_launch();
@@ -279,7 +301,8 @@ cudaError_t vecmat(const T *mu, const T *B, int64_t K, int64_t N, int64_t ldb, T
     template cudaError_t column_sums<T>(const T *, int64_t, int64_t, int64_t, double *, T *, double *,              \
                                         cudaStream_t);                                                            \
     template cudaError_t rank1_sub<T>(T *, int64_t, int64_t, int64_t, const T *, const T *, cudaStream_t);          \
-    template cudaError_t vecmat<T>(const T *, const T *, int64_t, int64_t, int64_t, T *, cudaStream_t);
+    template cudaError_t vecmat<T>(const T *, const T *, int64_t, int64_t, int64_t, T *, cudaStream_t);            \
+    template cudaError_t scale_means<T>(double *, int64_t, int64_t, double, T *, cudaStream_t);
 INST_CENTER(float)
 INST_CENTER(double)
 

@@ -98,6 +98,10 @@ struct rsvd_plan {
     int gkl_cap = 0;
     // Gram route beyond one CTA (n > kSmallMaxF64), allocated on the first such svd_exact
     void *gram_ws = nullptr;
+    // row-sharded solves: float64 staging of the partial sums (device, allocated on the first
+    // rsvd_sharded) and the host buffer the caller's reduction works on
+    double *shard_ws = nullptr;
+    std::vector<double> shard_host;
     // CUDA graph of the last rsvd solve, replayed while the caller's pointers and flags repeat
     cudaGraphExec_t graph = nullptr;
     const void *gkey[7] = {};
@@ -516,6 +520,9 @@ rsvd_status cqr2_f64(rsvd_plan *P, const float *X, int64_t rows, int w, int ld, 
 // block Krylov solve factors T in float64 (cqr2_f64): its Ritz values span the
 // whole Krylov space, far below what a float32 Gram matrix of T resolves.
 template <typename T>
+rsvd_status ritz_from_t(rsvd_plan *P, const T *Q, double *S, T *U, T *V);
+
+template <typename T>
 rsvd_status ritz(rsvd_plan *P, const T *A, const T *mu, const T *Q, double *S, T *U, T *V) {
     cudaStream_t s = P->stream;
     const int64_t m = P->m, n = P->n;
@@ -530,6 +537,18 @@ rsvd_status ritz(rsvd_plan *P, const T *A, const T *mu, const T *Q, double *S, T
         Span sp(P, RSVD_STAGE_ATX);
         CK(prod_tn<T>(P, m, n, A, n, Q, lp, Tn, lp, mu));                       // T = A^T Q  (= B^T)
     }
+    return ritz_from_t<T>(P, Q, S, U, V);
+}
+
+// The Rayleigh-Ritz steps after T = (A - 1 mu^T)^T Q (in P->Tn): the SVD of B = T^T
+// through T = Q_T R, R = U_R Sigma W^T, then V = Q_T U_R and U = Q W.
+template <typename T>
+rsvd_status ritz_from_t(rsvd_plan *P, const T *Q, double *S, T *U, T *V) {
+    cudaStream_t s = P->stream;
+    const int64_t m = P->m, n = P->n;
+    const int l = P->l, lp = P->lp, k = P->k;
+    T *Qz = (T *)P->Qz, *Tn = (T *)P->Tn, *Vt = (T *)P->Vt, *Tmpn = (T *)P->Tmpn;
+    rsvd_status st;
     T *UR = (T *)P->UR, *W = (T *)P->Wm;
     {
         Span sp(P, RSVD_STAGE_SMALL);
@@ -612,6 +631,115 @@ rsvd_status run_rsvd(rsvd_plan *P, T *A, const T *Omega, double *S, T *U, T *V) 
         }
     }
     return ritz<T>(P, A, mu, Q, S, U, V);
+}
+
+// ---------------------------------------------------------------- row-sharded solve
+// Sec. 3.1.2 over a row-block partition A = [A_1; ...; A_N] (one rank per block, this plan
+// holding A_r): every product with A is local (Y_r = (A_r - 1 mu^T) Omega, Y_r = (A_r - 1
+// mu^T) Z, U_r = Q_r W) and the quantities summed over rows are reduced across ranks by
+// the caller's function on the host: the column sums (mu), ||A - 1 mu^T||_F^2, the Gram
+// matrices Y^T Y = sum_r Y_r^T Y_r of every CholeskyQR pass and the final check,
+// Z = sum_r (A_r - 1 mu^T)^T Q_r and T = sum_r (A_r - 1 mu^T)^T Q_r.  Everything n x l
+// or l x l after a reduction (the factorisations of Z and T, the SVD of R, V) is computed
+// by every rank from identical inputs.  The reduced Gram matrices are factored in float64
+// (shift on breakdown); the fallback tiers of the single-GPU CholeskyQR, which re-read the
+// whole basis, are not available here.
+
+struct Reducer {
+    rsvd_allreduce_fn fn;
+    void *ctx;
+};
+
+// dev (count doubles, device) <- its sum over all ranks (through the host; synchronises)
+rsvd_status shard_reduce(rsvd_plan *P, const Reducer &r, double *dev, int64_t count) {
+    cudaStream_t s = P->stream;
+    P->shard_host.resize((size_t)count);
+    CK(cudaMemcpyAsync(P->shard_host.data(), dev, sizeof(double) * count, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (r.fn(P->shard_host.data(), count, r.ctx) != 0) return RSVD_ERR_REDUCE;
+    CK(cudaMemcpyAsync(dev, P->shard_host.data(), sizeof(double) * count, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    return RSVD_OK;
+}
+
+// X (rows x cols, ld, element type T) <- its sum over all ranks, staged in float64
+template <typename T>
+rsvd_status shard_reduce_mat(rsvd_plan *P, const Reducer &r, T *X, int64_t rows, int64_t cols, int64_t ld) {
+    CK(copy2d<T, double>(X, ld, P->shard_ws, cols, rows, cols, cols, P->stream));
+    rsvd_status st = shard_reduce(P, r, P->shard_ws, rows * cols);
+    if (st) return st;
+    CK(copy2d<double, T>(P->shard_ws, cols, X, ld, rows, cols, cols, P->stream));
+    return RSVD_OK;
+}
+
+// The global Gram matrix of the distributed basis X (local rows x lp) in P->shard_ws (float64)
+template <typename T>
+rsvd_status shard_gram(rsvd_plan *P, const Reducer &r, const T *X) {
+    const int lp = P->lp;
+    T *G = (T *)P->G;
+    CK(prod_tn<T>(P, P->m, lp, X, lp, X, lp, G, lp, nullptr, false));
+    CK(copy2d<T, double>(G, lp, P->shard_ws, lp, lp, lp, lp, P->stream));
+    return shard_reduce(P, r, P->shard_ws, (int64_t)lp * lp);
+}
+
+// CholeskyQR (one or two passes) of the distributed basis X: Qo_r = X_r R^{-1} with R the
+// Cholesky factor of the reduced Gram matrix (float64, shifted on breakdown)
+template <typename T>
+rsvd_status shard_cqr(rsvd_plan *P, const Reducer &r, int64_t m_total, const T *X, T *Qo, T *Tmp, int passes) {
+    cudaStream_t s = P->stream;
+    const int l = P->l, lp = P->lp;
+    const double u64 = DBL_EPSILON / 2;
+    T *Ric = (T *)P->Rinv_c;
+    rsvd_status st;
+    const T *in = X;
+    for (int pass = 0; pass < passes; pass++) {
+        T *out = pass == passes - 1 ? Qo : Tmp;
+        if ((st = shard_gram<T>(P, r, in))) return st;
+        double *R = pass == 0 ? P->R1 : P->R2, *Ri = pass == 0 ? P->R1i : P->R2i;
+        CK(chol_inv<double, double, T>(P->shard_ws, lp, l, m_total, u64, R, Ri, Ric, lp, P->status, s,
+                                       P->chol_ws));
+        CK(prod_nn<T>(P, P->m, lp, in, lp, Ric, lp, out, lp, nullptr, nullptr, true));
+        in = out;
+    }
+    return RSVD_OK;
+}
+
+template <typename T>
+rsvd_status run_rsvd_sharded(rsvd_plan *P, int64_t m_total, const T *A, const T *Omega, double *S, T *U, T *V,
+                             const Reducer &r) {
+    cudaStream_t s = P->stream;
+    P->nfact = 0;
+    const int64_t m = P->m, n = P->n;
+    const int l = P->l, lp = P->lp;
+    T *Y = (T *)P->Y, *Q = (T *)P->Qb, *Tmp = (T *)P->Tmp;
+    T *Ob = (T *)P->Ob, *Z = (T *)P->Z, *Qz = (T *)P->Qz, *Tmpn = (T *)P->Tmpn, *Tn = (T *)P->Tn;
+    rsvd_status st;
+    const bool centred = !(P->flags & RSVD_FLAG_NO_CENTER);
+    const T *mu = centred ? (const T *)P->mu_t : nullptr;
+    if (centred) {
+        CK(column_sums<T>(A, m, n, n, P->mu, (T *)P->mu_t, P->cpart, s));        // local column sums
+        if ((st = shard_reduce(P, r, P->mu, n))) return st;                       // over all rows
+        CK(scale_means<T>(P->mu, n, P->npad, 1.0 / (double)m_total, (T *)P->mu_t, s));
+    } else {
+        CK(cudaMemsetAsync(P->mu, 0, sizeof(double) * n, s));
+    }
+    CK(copy2d<T, T>(Omega, l, Ob, lp, n, l, lp, s));
+    CK(prod_nn<T>(P, m, n, A, n, Ob, lp, Y, lp, mu, P->fro2));                   // Y_r, ||A_r - 1 mu^T||_F^2
+    if ((st = shard_reduce(P, r, P->fro2, 1))) return st;
+    if ((st = shard_cqr<T>(P, r, m_total, Y, Q, Tmp, P->q > 0 ? 1 : 2))) return st;
+    for (int it = 0; it < P->q; it++) {
+        const bool last = it == P->q - 1;
+        CK(prod_tn<T>(P, m, n, A, n, Q, lp, Z, lp, mu));                          // Z_r
+        if ((st = shard_reduce_mat<T>(P, r, Z, n, lp, lp))) return st;           // Z
+        if ((st = cqr<T>(P, Z, n, l, lp, Qz, Tmpn, false, 1))) return st;        // same on every rank
+        CK(prod_nn<T>(P, m, n, A, n, Qz, lp, Y, lp, mu));
+        if ((st = shard_cqr<T>(P, r, m_total, Y, Q, Tmp, last ? 2 : 1))) return st;
+    }
+    if ((st = shard_gram<T>(P, r, Q))) return st;                                // Q^T Q = I (global)
+    CK(orth_check<double>(P->shard_ws, l, lp, sizeof(T) == 4 ? kOrthTolF32 : kOrthTolF64, P->status, s));
+    CK(prod_tn<T>(P, m, n, A, n, Q, lp, Tn, lp, mu));                             // T_r
+    if ((st = shard_reduce_mat<T>(P, r, Tn, n, lp, lp))) return st;              // T = A^T Q
+    return ritz_from_t<T>(P, Q, S, U, V);
 }
 
 // The plan's basis width switched for the Rayleigh-Ritz steps of a block Krylov solve.
@@ -1683,6 +1811,7 @@ rsvd_status rsvd_plan_destroy(rsvd_plan_t P) {
     drop_graph(P);
     if (P->gkl_ws) cudaFree(P->gkl_ws);
     if (P->gram_ws) cudaFree(P->gram_ws);
+    if (P->shard_ws) cudaFree(P->shard_ws);
     if (P->ws_owned) cudaFree(P->ws);
     delete P;
     return RSVD_OK;
@@ -1755,6 +1884,26 @@ rsvd_status rsvd(rsvd_plan_t P, void *A, const float *col_scales, const void *Om
     note_launch((int)P->glaunches);
     P->last_count = P->k;
     return RSVD_OK;
+}
+
+rsvd_status rsvd_sharded(rsvd_plan_t P, int64_t m_total, void *A, const void *Omega, double *S, void *U, void *V,
+                         rsvd_allreduce_fn allreduce, void *ctx) {
+    if (!P || !A || !Omega || !S || !U || !V || !allreduce || P->bk_blocks || m_total < P->m) return RSVD_ERR_ARG;
+    if (P->dtype != RSVD_F32 && P->dtype != RSVD_F64) return RSVD_ERR_UNSUPPORTED;
+    if (!P->shard_ws) {
+        const size_t bytes = sizeof(double) * (size_t)std::max<int64_t>(P->n, P->lp) * P->lp;
+        if (cudaMalloc(&P->shard_ws, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            P->shard_ws = nullptr;
+            return RSVD_ERR_OOM;
+        }
+    }
+    const Reducer r{allreduce, ctx};
+    if (P->dtype == RSVD_F32)
+        return run_rsvd_sharded<float>(P, m_total, (const float *)A, (const float *)Omega, S, (float *)U, (float *)V,
+                                       r);
+    return run_rsvd_sharded<double>(P, m_total, (const double *)A, (const double *)Omega, S, (double *)U,
+                                    (double *)V, r);
 }
 
 }  // extern "C"
@@ -2047,6 +2196,7 @@ const char *rsvd_status_string(rsvd_status s) {
         case RSVD_ERR_TIMEOUT: return "device wait timed out";
         case RSVD_ERR_CUDA: return "CUDA error";
         case RSVD_ERR_UNSUPPORTED: return "unsupported size or dtype";
+        case RSVD_ERR_REDUCE: return "the reduction over ranks failed";
         case RSVD_WARN_K_GT_k: return "threshold not reached within the returned values";
         case RSVD_WARN_RANK_DEFICIENT: return "numerically rank-deficient input or basis (handled; bases checked)";
     }

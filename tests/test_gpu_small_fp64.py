@@ -3,9 +3,10 @@ start refined by two Newton-type float64 steps built from l x l products.
 
 * float32 plans with RSVD_FLAG_SMALL_FP64 on an exactly rank-40 matrix (l = 48 > rank,
   so the sketch captures the range exactly): sigma within the float32 path's 1e-5 sigma_1
-  of the prescribed values and the Ritz pairs satisfy ||A v_i - sigma_i u_i|| <= 1e-6 sigma_1, no worse
-  than without the flag (the float32 Jacobi's rotations leave ~sqrt(l) u32 between the
-  vectors of R's SVD; the float64 ones leave only the float32 rounding of the output).
+  of the prescribed values, and the Ritz pairs satisfy A^T u_i = sigma_i v_i (exact for
+  U = Q W, V = Q_T U_R once R W = U_R Sigma) to 1e-6 sigma_1, no worse than without the
+  flag: the float32 Jacobi's accumulated rotations leave ~1e-6 in R W - U_R Sigma, the
+  float64 refinement only the float32 accuracy of T = A^T Q and of the outputs.
 * BF16 plans (refinement on by default) against RSVD_FLAG_SMALL_F32: both within the
   form's 1e-4 sigma_1 of the float64 oracle on the stored matrix, and within 1e-5
   sigma_1 of each other.
@@ -59,10 +60,10 @@ def test_f32_small_fp64_on_exact_rank(q):
         assert err <= 1e-5, (flags, err)
         A32 = A.double()
         Ac = A32 - A32.mean(dim=0, keepdim=True)
-        R = Ac @ V.double() - U.double() * S.unsqueeze(0)
+        R = Ac.T @ U.double() - V.double() * S.unsqueeze(0)   # A^T u_i = sigma_i v_i (A^T Q = B^T)
         res[flags] = R.norm(dim=0).max().item()
         assert torch.allclose(U.double().T @ U.double(), torch.eye(k, dtype=torch.float64, device="cuda"), atol=1e-5)
-    print(f"q={q}: max ||A v - sigma u|| float32 small SVD {res[0]:.2e}, float64 {res[g.RSVD_FLAG_SMALL_FP64]:.2e}")
+    print(f"q={q}: max ||A^T u - sigma v|| float32 small SVD {res[0]:.2e}, float64 {res[g.RSVD_FLAG_SMALL_FP64]:.2e}")
     assert res[g.RSVD_FLAG_SMALL_FP64] <= 1e-6
     assert res[g.RSVD_FLAG_SMALL_FP64] <= 1.5 * res[0] + 1e-7
 
