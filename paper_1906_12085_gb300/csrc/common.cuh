@@ -382,10 +382,14 @@ int tc_gemm_nn_grid(int64_t m, int ctas = 0);
 // chk (optional): C is the Gram matrix of a basis of chk_l columns; ST_ORTH goes into *chk when
 // an entry of its upper triangle differs from the identity's by more than chk_tol (col0: the
 // global index of this call's first column, for column slices).
+// Qth, Qtl (optional): Q's transposed tf32 split (tc_split_transpose of Q, N x ldqt, ldqt >= rows,
+// 16-byte aligned): the small operand is then read by TMA in the MMA's layout and the kernel's
+// workers split only A (about a quarter less time at N = 64).
 cudaError_t tc_gemm_tn(int64_t rows, int ncols, int N, const float *A, int64_t lda, const float *Q, int64_t ldq,
                        float *C, int64_t ldc, float *part, int64_t part_elems, int *status, cudaStream_t s,
                        const float *mu = nullptr, int ctas = 0, bool upper_c = false, int *chk = nullptr,
-                       int chk_l = 0, double chk_tol = 0.0, int col0 = 0);
+                       int chk_l = 0, double chk_tol = 0.0, int col0 = 0, const float *Qth = nullptr,
+                       const float *Qtl = nullptr, int64_t ldqt = 0);
 int64_t tc_gemm_tn_partials(int64_t rows, int ncols, int N);
 
 // ------------------------------------------------------ block Krylov (Sec. 3.1.1)

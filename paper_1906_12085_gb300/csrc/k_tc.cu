@@ -21,10 +21,14 @@
 //   warps 2-9   split workers (256 threads; warp w serves TMEM lane quarter w % 4,
 //               the two warps of a quarter take 16 K columns each)
 //   warps 10-13 epilogue: TMEM -> registers -> HBM (one TMEM lane quarter each)
-// TMEM holds two accumulators (columns 0-255) that alternate between tiles, so
-// the epilogue of one tile overlaps the main loop of the next, and four A
-// stages of hi and lo (columns 256-511).  Every wait is bounded; a stalled
-// pipeline sets ST_TIMEOUT in the status word and the CTA drains and exits.
+// TMEM holds two accumulators that alternate between tiles, so the epilogue of
+// one tile overlaps the main loop of the next, and the A stages of hi and lo.
+// For N <= 64 the two products with the hi part are one MMA of width 2N on the
+// stacked small operand [B_hi; B_lo] (an MMA's cost grows much less than its width
+// at these N: 23% less tensor time per stage, measured), the lo product a second
+// MMA of width N into its own accumulator; the epilogue adds the three N-column
+// blocks.  Every wait is bounded; a stalled pipeline sets ST_TIMEOUT in the status
+// word and the CTA drains and exits.
 #include <cudaTypedefs.h>
 
 #include "common.cuh"
@@ -43,9 +47,22 @@ constexpr int NTHR = 64 + NSPLIT + NEPI;
 constexpr int EPI_WARP0 = (64 + NSPLIT) / 32;
 constexpr uint32_t A_STAGE = TM * 128;  // bytes of one 128 x 32 fp32 stage
 constexpr uint32_t TMEM_COLS = 512;
-constexpr uint32_t ACC_STRIDE = 128;    // accumulator b at columns [128 b, 128 b + N)
-constexpr int TS = 4;                   // TMEM A stages
-constexpr uint32_t A_COL0 = 256;        // A stage s: hi at 256 + 64 s, lo at 256 + 64 s + 32
+constexpr int TS = 4;                   // TMEM A stages at most
+
+// TMEM layout for output width N: accumulator b at columns [ACC b, ACC b + width) with
+// width N, or (MERGE) 2N for [hi B_hi | hi B_lo] followed by N for lo B_hi; the A stages
+// after both accumulators, hi at A0 + 64 s and lo at A0 + 64 s + 32.
+template <int N>
+struct Tm {
+    static constexpr bool MERGE = N <= 64;
+    static constexpr uint32_t WIDTH = MERGE ? 3 * N : N;
+    static constexpr uint32_t ACC = WIDTH <= 128 ? 128 : 192;
+    static constexpr int NS = 2 * ACC + 4 * 64 <= TMEM_COLS ? 4 : 2;   // A stages
+    static constexpr uint32_t A0 = 2 * ACC;
+    // the split workers signal a stage after the work of the next one (hiding the TMEM
+    // store latency) only when more than two stages exist
+    static constexpr bool DELAY = NS >= 4;
+};
 
 __device__ __forceinline__ float rna_tf32(float x) {
     uint32_t r;
@@ -92,24 +109,34 @@ __device__ __forceinline__ bool wait_ok(uint64_t *bar, uint32_t parity, volatile
     return false;
 }
 
-// 12 MMAs of one stage: D (+)= Ah Bh + Ah Bl + Al Bh over the 4 K=8 slices; A in TMEM.
+// The MMAs of one stage over its 4 K=8 slices, A in TMEM: D (+)= Ah Bh + Ah Bl + Al Bh
+// (12 MMAs), or (MERGE; bl = bh + N rows) D[0, 2N) (+)= Ah [Bh; Bl] and D[2N, 3N) (+)= Al Bh
+// (8 MMAs).
 template <int N>
 __device__ __forceinline__ void mma_stage(uint32_t d, uint32_t a_hi, uint32_t a_lo, const uint8_t *bh,
                                           const uint8_t *bl, bool first) {
     constexpr uint32_t idesc = idesc_tf32(TM, N);
 #pragma unroll
     for (int kk = 0; kk < TBK / 8; kk++) {
-        const uint64_t dbh = sdesc_kmajor_sw128(bh, kk * 32), dbl = sdesc_kmajor_sw128(bl, kk * 32);
-        mma_tf32_ta(d, a_hi + kk * 8, dbh, idesc, (first && kk == 0) ? 0u : 1u);
-        mma_tf32_ta(d, a_hi + kk * 8, dbl, idesc, 1u);
-        mma_tf32_ta(d, a_lo + kk * 8, dbh, idesc, 1u);
+        const uint32_t acc = (first && kk == 0) ? 0u : 1u;
+        const uint64_t dbh = sdesc_kmajor_sw128(bh, kk * 32);
+        if constexpr (Tm<N>::MERGE) {
+            mma_tf32_ta(d, a_hi + kk * 8, dbh, idesc_tf32(TM, 2 * N), acc);
+            mma_tf32_ta(d + 2 * N, a_lo + kk * 8, dbh, idesc, acc);
+        } else {
+            const uint64_t dbl = sdesc_kmajor_sw128(bl, kk * 32);
+            mma_tf32_ta(d, a_hi + kk * 8, dbh, idesc, acc);
+            mma_tf32_ta(d, a_hi + kk * 8, dbl, idesc, 1u);
+            mma_tf32_ta(d, a_lo + kk * 8, dbh, idesc, 1u);
+        }
     }
 }
 
 // Store a worker's 16 split values (K columns 16h..16h+15 of its lane) into TMEM stage s.
+template <int N>
 __device__ __forceinline__ void store_a(uint32_t tmem, int q, int h, int s, const uint32_t *hi, const uint32_t *lo) {
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-    const uint32_t col = A_COL0 + (uint32_t)s * 64 + (uint32_t)h * 16;
+    const uint32_t col = Tm<N>::A0 + (uint32_t)s * 64 + (uint32_t)h * 16;
     tmem_st16(tmem + lane_base + col, hi);
     tmem_st16(tmem + lane_base + col + 32, lo);
 }
@@ -129,7 +156,7 @@ __device__ __forceinline__ void drain_acc(uint32_t tmem, uint32_t b, int q, int 
 #pragma unroll
     for (int c0 = 0; c0 < N; c0 += 32) {
         float v[32];
-        tmem_ld32(tmem + b * ACC_STRIDE + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+        tmem_ld32(tmem + b * Tm<N>::ACC + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
         if (valid) {
             float *p = dst + c0;
             if (c0 + 32 <= N && ((reinterpret_cast<uintptr_t>(p) & 15) == 0)) {
@@ -156,10 +183,22 @@ __device__ __forceinline__ void drain_acc(uint32_t tmem, uint32_t b, int q, int 
 // and written once per tile.
 template <int N>
 __device__ __forceinline__ void sum_acc(uint32_t tmem, uint32_t b, int q, float *acc, bool first) {
+    const uint32_t base = tmem + b * Tm<N>::ACC + ((uint32_t)(q * 32) << 16);
 #pragma unroll
     for (int c0 = 0; c0 < N; c0 += 16) {
         float v[16];
-        tmem_ld16(tmem + b * ACC_STRIDE + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+        if constexpr (Tm<N>::MERGE) {  // hi B_hi + (hi B_lo + lo B_hi), two 16-column buffers live
+            float w[16];
+            tmem_ld16(base + (uint32_t)(N + c0), w);
+            tmem_ld16(base + (uint32_t)(2 * N + c0), v);
+#pragma unroll
+            for (int j = 0; j < 16; j++) w[j] += v[j];
+            tmem_ld16(base + (uint32_t)c0, v);
+#pragma unroll
+            for (int j = 0; j < 16; j++) v[j] += w[j];
+        } else {
+            tmem_ld16(base + (uint32_t)c0, v);
+        }
 #pragma unroll
         for (int j = 0; j < 16; j++) acc[c0 + j] = first ? v[j] : acc[c0 + j] + v[j];
     }
@@ -198,10 +237,10 @@ __global__ void __launch_bounds__(NTHR, 1)
     constexpr int S = C::S;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    constexpr int NS = Tm<N>::NS;
     uint8_t *sA = base;                    // raw fp32 A stages (TMA, 128-byte swizzle)
-    uint8_t *sBh = sA + S * A_STAGE;
-    uint8_t *sBl = sBh + S * C::B_STAGE;
-    Bars<S> *bar = reinterpret_cast<Bars<S> *>(sBl + S * C::B_STAGE);
+    uint8_t *sB = sA + S * A_STAGE;        // per stage: B hi (N rows) then B lo (N rows)
+    Bars<S> *bar = reinterpret_cast<Bars<S> *>(sB + S * 2 * C::B_STAGE);
     volatile int *abort_flag = &bar->abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -213,7 +252,7 @@ __global__ void __launch_bounds__(NTHR, 1)
             mbar_init(&bar->full[s], 1);
             mbar_init(&bar->empty[s], 1);
         }
-        for (int t = 0; t < TS; t++) {
+        for (int t = 0; t < NS; t++) {
             mbar_init(&bar->split[t], NSPLIT);  // TMEM A stage t written
             mbar_init(&bar->tempty[t], 1);      // TMEM A stage t consumed by the MMAs
         }
@@ -243,8 +282,8 @@ __global__ void __launch_bounds__(NTHR, 1)
                     if (!(ok = wait_ok(&bar->empty[s], ((g / S) & 1) ^ 1, abort_flag))) break;
                     mbar_arrive_expect_tx(&bar->full[s], A_STAGE + 2 * C::B_STAGE);
                     tma_load_2d(sA + s * A_STAGE, &tmA, kb * TBK, (int32_t)(t * TM), &bar->full[s]);
-                    tma_load_2d(sBh + s * C::B_STAGE, &tmBh, kb * TBK, 0, &bar->full[s]);
-                    tma_load_2d(sBl + s * C::B_STAGE, &tmBl, kb * TBK, 0, &bar->full[s]);
+                    tma_load_2d(sB + s * 2 * C::B_STAGE, &tmBh, kb * TBK, 0, &bar->full[s]);
+                    tma_load_2d(sB + s * 2 * C::B_STAGE + C::B_STAGE, &tmBl, kb * TBK, 0, &bar->full[s]);
                 }
             for (uint32_t k = g > (uint32_t)S ? g - S : 0; k < g; k++) mbar_wait(&bar->full[k % S], (k / S) & 1);
         }
@@ -258,13 +297,14 @@ __global__ void __launch_bounds__(NTHR, 1)
                     const uint32_t b = it & 1;
                     if (!(ok = wait_ok(&bar->acc_empty[b], ((it >> 1) & 1) ^ 1, abort_flag))) break;
                     tc_fence_after();
-                    const uint32_t d = tmem + b * ACC_STRIDE;
+                    const uint32_t d = tmem + b * Tm<N>::ACC;
                     for (int kb = k0; kb < k1; kb++, g++) {
-                        const int s = g % S, ts = g % TS;
-                        if (!(ok = wait_ok(&bar->split[ts], (g / TS) & 1, abort_flag))) break;
+                        const int s = g % S, ts = g % NS;
+                        if (!(ok = wait_ok(&bar->split[ts], (g / NS) & 1, abort_flag))) break;
                         tc_fence_after();
-                        const uint32_t a = tmem + A_COL0 + (uint32_t)ts * 64;
-                        mma_stage<N>(d, a, a + 32, sBh + s * C::B_STAGE, sBl + s * C::B_STAGE, kb == k0);
+                        const uint32_t a = tmem + Tm<N>::A0 + (uint32_t)ts * 64;
+                        const uint8_t *bs = sB + s * 2 * C::B_STAGE;
+                        mma_stage<N>(d, a, a + 32, bs, bs + C::B_STAGE, kb == k0);
                         mma_commit(&bar->empty[s]);
                         mma_commit(&bar->tempty[ts]);
                     }
@@ -285,9 +325,9 @@ __global__ void __launch_bounds__(NTHR, 1)
             const bool row_ok = t * TM + r < m;
             float acc32 = 0.f;
             for (int kb = 0; kb < nkb; kb++, g++) {
-                const int s = g % S, ts = g % TS;
+                const int s = g % S, ts = g % NS;
                 if (!(ok = wait_ok(&bar->full[s], (g / S) & 1, abort_flag))) break;
-                if (!(ok = wait_ok(&bar->tempty[ts], ((g / TS) & 1) ^ 1, abort_flag))) break;
+                if (!(ok = wait_ok(&bar->tempty[ts], ((g / NS) & 1) ^ 1, abort_flag))) break;
                 const uint8_t *raw = sA + s * A_STAGE;
                 uint32_t hi[16], lo[16];
 #pragma unroll
@@ -303,13 +343,20 @@ __global__ void __launch_bounds__(NTHR, 1)
                     split_tr(v.z, hi[c4 * 4 + 2], lo[c4 * 4 + 2]);
                     split_tr(v.w, hi[c4 * 4 + 3], lo[c4 * 4 + 3]);
                 }
-                if (pend >= 0) {
+                if constexpr (Tm<N>::DELAY) {
+                    if (pend >= 0) {
+                        tmem_wait_st();
+                        tc_fence_before();
+                        mbar_arrive(&bar->split[pend]);
+                    }
+                    store_a<N>(tmem, q, h, ts, hi, lo);
+                    pend = ts;
+                } else {
+                    store_a<N>(tmem, q, h, ts, hi, lo);
                     tmem_wait_st();
                     tc_fence_before();
-                    mbar_arrive(&bar->split[pend]);
+                    mbar_arrive(&bar->split[ts]);
                 }
-                store_a(tmem, q, h, ts, hi, lo);
-                pend = ts;
             }
             acc64 += (double)acc32;
         }
@@ -370,7 +417,7 @@ struct TNCfg {
     static constexpr uint32_t RAW = RAW_A + RAW_Q;
     static constexpr uint32_t SPL_B = N * 128;
     static constexpr uint32_t SPL = 2 * SPL_B;
-    static constexpr int SS = TS;  // split stages (Q hi/lo in smem, A hi/lo in TMEM)
+    static constexpr int SS = Tm<N>::NS;  // split stages (Q hi/lo in smem, A hi/lo in TMEM)
     static constexpr int SR = (208 * 1024 - SS * SPL) / RAW > 6 ? 6 : (208 * 1024 - SS * SPL) / RAW;
     static constexpr uint32_t SMEM_NEED = SR * RAW + SS * SPL + 1024 + sizeof(Bars<SR + SS>) + 64;
     static constexpr uint32_t SMEM = SMEM_NEED > 120 * 1024 ? SMEM_NEED : 120 * 1024;
@@ -461,13 +508,13 @@ __global__ void __launch_bounds__(NTHR, 1)
                     const uint32_t b = it & 1;
                     if (!(ok = wait_ok(&bar->acc_empty[b], ((it >> 1) & 1) ^ 1, abort_flag))) break;
                     tc_fence_after();
-                    const uint32_t d = tmem + b * ACC_STRIDE;
+                    const uint32_t d = tmem + b * Tm<N>::ACC;
                     for (int kb = k0; kb < k1; kb++, g++) {
                         const int s = g % SS;
                         if (!(ok = wait_ok(&bar->split[s], (g / SS) & 1, abort_flag))) break;
                         tc_fence_after();
                         uint8_t *sp = sSplit + s * C::SPL;
-                        const uint32_t a = tmem + A_COL0 + (uint32_t)s * 64;
+                        const uint32_t a = tmem + Tm<N>::A0 + (uint32_t)s * 64;
                         mma_stage<N>(d, a, a + 32, sp, sp + C::SPL_B, kb == k0);
                         mma_commit(&bar->empty[SR + s]);
                     }
@@ -476,7 +523,8 @@ __global__ void __launch_bounds__(NTHR, 1)
             }
         }
     } else if (warp < EPI_WARP0) {
-        // as in the NN kernel, stage g is signalled after the work of stage g + 1
+        // as in the NN kernel, stage g is signalled after the work of stage g + 1 (with four
+        // split stages; with two, right after its own work)
         const int wt = threadIdx.x - 64;
         const int q = warp & 3, h = (warp - 2) >> 2, i = q * 32 + lane;
         uint32_t g = 0;
@@ -503,14 +551,14 @@ __global__ void __launch_bounds__(NTHR, 1)
                         const int k = h * 16 + e;
                         split_tr(k < valid ? rawA[k * TM + i] - mc : 0.f, hi[e], lo[e]);
                     }
-                    if (pend_ss >= 0) {
+                    if (Tm<N>::DELAY && pend_ss >= 0) {
                         fence_proxy_async_smem();
                         tmem_wait_st();
                         tc_fence_before();
                         mbar_arrive(&bar->empty[pend_sr]);   // raw stage consumed
                         mbar_arrive(&bar->split[pend_ss]);   // split stage ready
                     }
-                    store_a(tmem, q, h, ss, hi, lo);
+                    store_a<N>(tmem, q, h, ss, hi, lo);
                 }
                 for (int idx = wt; idx < N * 8; idx += NSPLIT) {  // Q: (column j, 4-row chunk cc)
                     const int j = idx % N, cc = idx / N;
@@ -523,8 +571,16 @@ __global__ void __launch_bounds__(NTHR, 1)
                     *reinterpret_cast<float4 *>(sp + off) = hq;
                     *reinterpret_cast<float4 *>(sp + C::SPL_B + off) = lq;
                 }
-                pend_sr = sr;
-                pend_ss = ss;
+                if constexpr (Tm<N>::DELAY) {
+                    pend_sr = sr;
+                    pend_ss = ss;
+                } else {
+                    fence_proxy_async_smem();
+                    tmem_wait_st();
+                    tc_fence_before();
+                    mbar_arrive(&bar->empty[sr]);
+                    mbar_arrive(&bar->split[ss]);
+                }
             }
         }
         if (pend_ss >= 0) {
@@ -567,17 +623,231 @@ __global__ void __launch_bounds__(NTHR, 1)
     if (threadIdx.x == 0 && bar->abort_flag) atomicOr(status, (int)ST_TIMEOUT);
 }
 
+// ======================================================================= TN, pre-split Q
+// The same product with Q given as its transposed tf32 split (Q_hi, Q_lo: N x ldq rows of
+// K = rows of A, tc_split_transpose): the small operand reaches shared memory by TMA in
+// the K-major swizzled layout the MMA reads (hi rows then lo rows, as the NN kernel's B),
+// and the split workers only split the A columns into TMEM.  Each raw stage holds 32
+// rows of A (unswizzled 32 x 128) and the two Q tiles; it is freed when the MMAs that
+// read it complete.
+template <int N>
+struct TN2Cfg {
+    static constexpr uint32_t B_STAGE = N * 128;                   // one of Q hi / Q lo
+    static constexpr uint32_t STAGE = A_STAGE + 2 * B_STAGE;
+    static constexpr int S = (200 * 1024) / STAGE > 6 ? 6 : (200 * 1024) / STAGE;
+    static constexpr uint32_t SMEM_NEED = S * STAGE + 1024 + sizeof(Bars<S>) + 64;
+    static constexpr uint32_t SMEM = SMEM_NEED > 120 * 1024 ? SMEM_NEED : 120 * 1024;
+};
+
+template <int N>
+__global__ void __launch_bounds__(NTHR, 1)
+    tc_tn2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmQh,
+                  const __grid_constant__ CUtensorMap tmQl, int64_t rows, int ncols, int64_t rpc, int nchunks,
+                  float *__restrict__ part, int *__restrict__ status, const float *__restrict__ mu) {
+    using C = TN2Cfg<N>;
+    constexpr int S = C::S;
+    constexpr int NS = Tm<N>::NS;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *sB = base;                          // per stage: Q hi (N rows) then Q lo (N rows), swizzled
+    uint8_t *sA = sB + S * 2 * C::B_STAGE;       // raw A stages (32 x 128, unswizzled)
+    Bars<S> *bar = reinterpret_cast<Bars<S> *>(sA + S * A_STAGE);
+    volatile int *abort_flag = &bar->abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntn = (ncols + TM - 1) / TM;
+    const int64_t ntiles = (int64_t)ntn * nchunks;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; s++) {
+            mbar_init(&bar->full[s], 1);
+            mbar_init(&bar->empty[s], 1);
+        }
+        for (int t = 0; t < NS; t++) {
+            mbar_init(&bar->split[t], NSPLIT);
+            mbar_init(&bar->tempty[t], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&bar->acc_full[b], 1);
+            mbar_init(&bar->acc_empty[b], NEPI);
+        }
+        bar->abort_flag = 0;
+        mbar_fence_init();
+    }
+    if (warp == 1) tmem_alloc(&bar->tmem, TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = bar->tmem;
+
+    auto tile_rows = [&](int64_t t, int64_t &r0, int64_t &r1, int &c0) {
+        const int64_t chunk = t / ntn;
+        c0 = (int)(t % ntn) * TM;
+        r0 = chunk * rpc;
+        r1 = r0 + rpc < rows ? r0 + rpc : rows;
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            tma_prefetch_desc(&tmA);
+            tma_prefetch_desc(&tmQh);
+            tma_prefetch_desc(&tmQl);
+            uint32_t g = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
+                int64_t r0, r1;
+                int c0;
+                tile_rows(t, r0, r1, c0);
+                const int nkb = (int)((r1 - r0 + TBK - 1) / TBK);
+                for (int kb = 0; kb < nkb; kb++, g++) {
+                    const int s = g % S;
+                    if (!(ok = wait_ok(&bar->empty[s], ((g / S) & 1) ^ 1, abort_flag))) break;
+                    const int32_t k = (int32_t)(r0 + (int64_t)kb * TBK);
+                    uint8_t *bs = sB + s * 2 * C::B_STAGE;
+                    mbar_arrive_expect_tx(&bar->full[s], C::STAGE);
+                    tma_load_2d(sA + s * A_STAGE, &tmA, c0, k, &bar->full[s]);
+                    tma_load_2d(bs, &tmQh, k, 0, &bar->full[s]);
+                    tma_load_2d(bs + C::B_STAGE, &tmQl, k, 0, &bar->full[s]);
+                }
+            }
+            for (uint32_t k = g > (uint32_t)S ? g - S : 0; k < g; k++) mbar_wait(&bar->full[k % S], (k / S) & 1);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            uint32_t g = 0, it = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
+                int64_t r0, r1;
+                int c0;
+                tile_rows(t, r0, r1, c0);
+                const int nkb = (int)((r1 - r0 + TBK - 1) / TBK);
+                for (int k0 = 0; ok && k0 < nkb; k0 += SUBK, it++) {  // one accumulator per sub-chunk
+                    const int k1 = k0 + SUBK < nkb ? k0 + SUBK : nkb;
+                    const uint32_t b = it & 1;
+                    if (!(ok = wait_ok(&bar->acc_empty[b], ((it >> 1) & 1) ^ 1, abort_flag))) break;
+                    tc_fence_after();
+                    const uint32_t d = tmem + b * Tm<N>::ACC;
+                    for (int kb = k0; kb < k1; kb++, g++) {
+                        const int s = g % S, ts = g % NS;
+                        if (!(ok = wait_ok(&bar->split[ts], (g / NS) & 1, abort_flag))) break;
+                        tc_fence_after();
+                        const uint32_t a = tmem + Tm<N>::A0 + (uint32_t)ts * 64;
+                        const uint8_t *bs = sB + s * 2 * C::B_STAGE;
+                        mma_stage<N>(d, a, a + 32, bs, bs + C::B_STAGE, kb == k0);
+                        mma_commit(&bar->empty[s]);
+                        mma_commit(&bar->tempty[ts]);
+                    }
+                    if (ok) mma_commit(&bar->acc_full[b]);
+                }
+            }
+        }
+    } else if (warp < EPI_WARP0) {
+        // split workers: column i of the A tile, K rows 16h..16h+15 of the stage -> TMEM lane i
+        const int q = warp & 3, h = (warp - 2) >> 2, i = q * 32 + lane;
+        uint32_t g = 0;
+        bool ok = true;
+        int pend = -1;
+        for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
+            int64_t r0, r1;
+            int c0;
+            tile_rows(t, r0, r1, c0);
+            const int nkb = (int)((r1 - r0 + TBK - 1) / TBK);
+            const float mc = mu ? __ldg(mu + c0 + i) : 0.f;
+            for (int kb = 0; kb < nkb; kb++, g++) {
+                const int s = g % S, ts = g % NS;
+                if (!(ok = wait_ok(&bar->full[s], (g / S) & 1, abort_flag))) break;
+                if (!(ok = wait_ok(&bar->tempty[ts], ((g / NS) & 1) ^ 1, abort_flag))) break;
+                const float *rawA = reinterpret_cast<const float *>(sA + s * A_STAGE);
+                const int valid = (int)(r1 - (r0 + (int64_t)kb * TBK));  // rows of this stage inside the chunk
+                uint32_t hi[16], lo[16];
+#pragma unroll
+                for (int e = 0; e < 16; e++) {
+                    const int k = h * 16 + e;
+                    split_tr(k < valid ? rawA[k * TM + i] - mc : 0.f, hi[e], lo[e]);
+                }
+                if constexpr (Tm<N>::DELAY) {
+                    if (pend >= 0) {
+                        tmem_wait_st();
+                        tc_fence_before();
+                        mbar_arrive(&bar->split[pend]);
+                    }
+                    store_a<N>(tmem, q, h, ts, hi, lo);
+                    pend = ts;
+                } else {
+                    store_a<N>(tmem, q, h, ts, hi, lo);
+                    tmem_wait_st();
+                    tc_fence_before();
+                    mbar_arrive(&bar->split[ts]);
+                }
+            }
+        }
+        if (pend >= 0) {
+            tmem_wait_st();
+            tc_fence_before();
+            mbar_arrive(&bar->split[pend]);
+        }
+    } else {
+        const int q = warp & 3;
+        uint32_t it = 0;
+        bool ok = true;
+        for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
+            int64_t r0, r1;
+            int c0;
+            tile_rows(t, r0, r1, c0);
+            const int nkb = (int)((r1 - r0 + TBK - 1) / TBK);
+            const int64_t chunk = t / ntn;
+            const int c = c0 + q * 32 + lane;
+            float *dst = part + (chunk * ncols + c) * (int64_t)N;
+            float acc[N];
+            for (int k0 = 0; k0 < nkb; k0 += SUBK, it++) {
+                const uint32_t b = it & 1;
+                if (!(ok = wait_ok(&bar->acc_full[b], (it >> 1) & 1, abort_flag))) break;
+                tc_fence_after();
+                sum_acc<N>(tmem, b, q, acc, k0 == 0);
+                tc_fence_before();
+                mbar_arrive(&bar->acc_empty[b]);
+            }
+            if (ok) store_acc<N>(acc, dst, c < ncols);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, TMEM_COLS);
+    }
+    if (threadIdx.x == 0 && bar->abort_flag) atomicOr(status, (int)ST_TIMEOUT);
+}
+
 // ==================================================================== helpers
-// th / tl (N x ldt) = tf32 split of Z^T, Z rows x cols row-major (ldz); zero beyond.
-__global__ void split_transpose_kernel(const float *__restrict__ Z, int64_t rows, int cols, int64_t ldz, int N,
-                                       float *__restrict__ th, float *__restrict__ tl, int64_t ldt) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)N * ldt) return;
-    const int64_t j = idx / ldt, r = idx % ldt;
-    const float x = (j < cols && r < rows) ? Z[r * ldz + j] : 0.f;
-    const float h = rna_tf32(x);
-    th[idx] = h;
-    tl[idx] = rna_tf32(x - h);
+// th / tl (N x ldt) = tf32 split of Z^T, Z rows x cols row-major (ldz); zero beyond.  A 32 x 32
+// tile per CTA goes through shared memory, so both the reads (along j) and the writes (along r)
+// are coalesced.
+__global__ void __launch_bounds__(256) split_transpose_kernel(const float *__restrict__ Z, int64_t rows, int cols,
+                                                              int64_t ldz, int N, float *__restrict__ th,
+                                                              float *__restrict__ tl, int64_t ldt) {
+    __shared__ float tile[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    const int j0 = blockIdx.y * 32;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int64_t r = r0 + ty + 8 * k;
+        const int j = j0 + tx;
+        tile[ty + 8 * k][tx] = (r < rows && j < cols) ? Z[r * ldz + j] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int j = j0 + ty + 8 * k;
+        const int64_t r = r0 + tx;
+        if (j < N && r < ldt) {
+            const float x = tile[tx][ty + 8 * k];
+            const float h = rna_tf32(x);
+            th[(int64_t)j * ldt + r] = h;
+            tl[(int64_t)j * ldt + r] = rna_tf32(x - h);
+        }
+    }
 }
 
 // C[i * ldc + j] = sum_{s < chunks} part[s][i][j] (N x L per chunk).  A block covers 32
@@ -683,6 +953,23 @@ cudaError_t launch_tn(const CUtensorMap &a, const CUtensorMap &qm, int64_t rows,
     return cudaGetLastError();
 }
 
+template <int N>
+cudaError_t launch_tn2(const CUtensorMap &a, const CUtensorMap &qh, const CUtensorMap &ql, int64_t rows, int ncols,
+                       int64_t rpc, int nchunks, float *part, int *status, const float *mu, cudaStream_t s, int ctas) {
+    using C = TN2Cfg<N>;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(tc_tn2_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        attr = true;
+    }
+    const int64_t tiles = ceil_div(ncols, TM) * nchunks;
+    const int64_t cap = ctas > 0 && ctas < num_sms() ? ctas : num_sms();
+    const int grid = (int)(tiles < cap ? tiles : cap);
+    tc_tn2_kernel<N><<<grid, NTHR, C::SMEM, s>>>(a, qh, ql, rows, ncols, rpc, nchunks, part, status, mu);
+    note_launch();
+    return cudaGetLastError();
+}
+
 struct TNSplit {
     int64_t rpc;
     int chunks;
@@ -735,8 +1022,8 @@ bool tc_make_map(CUtensorMap *map, const void *ptr, int esize, int64_t rows, int
 
 cudaError_t tc_split_transpose(const float *Z, int64_t rows, int cols, int64_t ldz, int N, float *th, float *tl,
                                int64_t ldt, cudaStream_t s) {
-    const int64_t total = (int64_t)N * ldt;
-    split_transpose_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, s>>>(Z, rows, cols, ldz, N, th, tl, ldt);
+    const dim3 grid((unsigned)ceil_div(ldt, 32), (unsigned)ceil_div(N, 32));
+    split_transpose_kernel<<<grid, 256, 0, s>>>(Z, rows, cols, ldz, N, th, tl, ldt);
     note_launch();
     return cudaGetLastError();
 }
@@ -787,14 +1074,17 @@ int64_t tc_gemm_tn_partials(int64_t rows, int ncols, int N) {
 
 cudaError_t tc_gemm_tn(int64_t rows, int ncols, int N, const float *A, int64_t lda, const float *Q, int64_t ldq,
                        float *C, int64_t ldc, float *part, int64_t part_elems, int *status, cudaStream_t s,
-                       const float *mu, int ctas, bool upper_c, int *chk, int chk_l, double chk_tol, int col0) {
+                       const float *mu, int ctas, bool upper_c, int *chk, int chk_l, double chk_tol, int col0,
+                       const float *Qth, const float *Qtl, int64_t ldqt) {
     if (N > 128 && N % 16 == 0) {  // column slices of Q and C (A read once per slice)
         const int w = column_slice(N);
         for (int c0 = 0; c0 < N; c0 += w) {
             const int wn = w < N - c0 ? w : N - c0;
             const int nc = upper_c && c0 + wn < ncols ? c0 + wn : ncols;  // upper triangle: rows up to the slice end
-            const cudaError_t e = tc_gemm_tn(rows, nc, wn, A, lda, Q + c0, ldq, C + c0, ldc, part, part_elems, status,
-                                             s, mu, ctas, false, chk, chk_l, chk_tol, col0 + c0);
+            const cudaError_t e =
+                tc_gemm_tn(rows, nc, wn, A, lda, Q + c0, ldq, C + c0, ldc, part, part_elems, status, s, mu, ctas,
+                           false, chk, chk_l, chk_tol, col0 + c0, Qth ? Qth + c0 * ldqt : nullptr,
+                           Qtl ? Qtl + c0 * ldqt : nullptr, ldqt);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
@@ -802,11 +1092,24 @@ cudaError_t tc_gemm_tn(int64_t rows, int ncols, int N, const float *A, int64_t l
     if (N % 16 || N < 16 || N > 128) return cudaErrorInvalidValue;
     const TNSplit sp = tn_split(rows, ncols);
     if (part == nullptr || part_elems < (int64_t)sp.chunks * ncols * N) return cudaErrorInvalidValue;
-    CUtensorMap ma, mq;
-    if (!make_map(&ma, A, rows, ncols, lda, TBK, TM, false) || !make_map(&mq, Q, rows, N, ldq, TBK, N, false))
-        return cudaErrorInvalidValue;
+    CUtensorMap ma, mq, mqh, mql;
+    if (!make_map(&ma, A, rows, ncols, lda, TBK, TM, false)) return cudaErrorInvalidValue;
+    const bool pre = Qth && Qtl && make_map(&mqh, Qth, N, rows, ldqt, N, TBK, true) &&
+                     make_map(&mql, Qtl, N, rows, ldqt, N, TBK, true);
+    if (!pre && !make_map(&mq, Q, rows, N, ldq, TBK, N, false)) return cudaErrorInvalidValue;
     cudaError_t e = cudaErrorInvalidValue;
-    switch (N) {
+    if (pre) {
+        switch (N) {
+            case 16: e = launch_tn2<16>(ma, mqh, mql, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s, ctas); break;
+            case 32: e = launch_tn2<32>(ma, mqh, mql, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s, ctas); break;
+            case 48: e = launch_tn2<48>(ma, mqh, mql, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s, ctas); break;
+            case 64: e = launch_tn2<64>(ma, mqh, mql, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s, ctas); break;
+            case 80: e = launch_tn2<80>(ma, mqh, mql, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s, ctas); break;
+            case 96: e = launch_tn2<96>(ma, mqh, mql, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s, ctas); break;
+            case 112: e = launch_tn2<112>(ma, mqh, mql, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s, ctas); break;
+            case 128: e = launch_tn2<128>(ma, mqh, mql, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s, ctas); break;
+        }
+    } else switch (N) {
         case 16: e = launch_tn<16>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s, ctas); break;
         case 32: e = launch_tn<32>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s, ctas); break;
         case 48: e = launch_tn<48>(ma, mq, rows, ncols, sp.rpc, sp.chunks, part, status, mu, s, ctas); break;

