@@ -254,7 +254,7 @@ def run_block_krylov(args):
     achieved = 4.0 * m * n / (per_pass_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm",
                 "kernel": "tc_nn_kernel (A X, 3xTF32 tcgen05)" if dom == "ax" else
-                          "tc_tn_kernel + sum_chunks_kernel (A^T X, 3xTF32 tcgen05)",
+                          "tc_tn_kernel + sum_chunks_kernel (A^T X, 3xTF32 tcgen05)",  # block Krylov: in-kernel split
                 "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": None, "algorithmic_bytes_per_launch": 4.0 * m * n,
                 "passes_over_A_per_step": passes,
@@ -783,8 +783,9 @@ def run_ours(args):
     if ax_ms >= atx_ms:
         dom, dom_ms, dom_n, dom_kernel = "tc_nn_kernel (Y = A Z, 3xTF32 tcgen05)", ax_ms, ax_n, "tc_nn_kernel"
     else:
-        dom, dom_ms, dom_n, dom_kernel = ("tc_tn_kernel + sum_chunks_kernel (Z = A^T Q, 3xTF32 tcgen05)", atx_ms,
-                                          atx_n, "tc_tn_kernel")
+        dom, dom_ms, dom_n, dom_kernel = ("tc_tn2_kernel + split_transpose_kernel + sum_chunks_kernel "
+                                          "(Z = A^T Q, 3xTF32 tcgen05; the basis split and transposed first)",
+                                          atx_ms, atx_n, "tc_tn2_kernel")
     per_launch_bytes = 4.0 * m * n
     achieved = per_launch_bytes / (dom_ms / dom_n * 1e-3) / 1e9 if dom_n else None
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
