@@ -576,8 +576,15 @@ cudaError_t gkl_recover(const float *x, float *Y, int j, int n, const float *bet
     return cudaGetLastError();
 }
 
+// Rows per block of the Gram-Schmidt kernels: 2048, or fewer for short vectors (the n-long
+// V side), so that a pass over a basis spreads over about two blocks per SM; a multiple of
+// 128 (32 E-wide loads per warp row for float32 and float64).
 constexpr int64_t kReorthRows = 2048;
-int64_t gkl_reorth_blocks(int64_t len) { return ceil_div(len, kReorthRows); }
+int64_t gkl_reorth_rows(int64_t len) {
+    const int64_t r = round_up(ceil_div(len, 2 * 152), 128);
+    return r < 128 ? 128 : (r > kReorthRows ? kReorthRows : r);
+}
+int64_t gkl_reorth_blocks(int64_t len) { return ceil_div(len, gkl_reorth_rows(len)); }
 
 // w <- w - B (B^T w) twice (classical Gram-Schmidt, twice) against the first cnt rows of
 // Bt (cnt x len, ld); then nrm[0] = ||w|| and out = w / nrm[0].  coef: cnt scratch,
@@ -593,7 +600,7 @@ template <typename T>
 cudaError_t gkl_reorth_normalize(const T *Bt, int64_t ld, int cnt, T *w, int64_t len, T *coef, T *part, T *sq,
                                  T *nrm, T *out, int *status, cudaStream_t s, T *ctot) {
     constexpr int E = V4<T>::n;
-    const int64_t rpb = kReorthRows;  // a multiple of 32 E
+    const int64_t rpb = gkl_reorth_rows(len);  // a multiple of 32 E
     const int64_t nblk = ceil_div(len, rpb);
     // E-wide loads need every vector (and w) to start on a 16-byte boundary and whole E-groups
     const bool vec = ld % E == 0 && len % E == 0 && (reinterpret_cast<uintptr_t>(Bt) & 15) == 0 &&

@@ -1190,7 +1190,7 @@ GklBufs gkl_carve(rsvd_plan *P, int steps, char *base, size_t *bytes) {
     const size_t es = esize(P->dtype);
     const int64_t m = P->m, n = P->n;
     const int64_t sp = round_up(steps, 16);
-    const int64_t nblk = gkl_reorth_blocks(m > n ? m : n);
+    const int64_t nblk = std::max(gkl_reorth_blocks(m), gkl_reorth_blocks(n));
     Carver c;
     c.base = base;
     GklBufs b;

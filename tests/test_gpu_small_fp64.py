@@ -55,7 +55,9 @@ def test_f32_small_fp64_on_exact_rank(q):
     res = {}
     for flags in (0, g.RSVD_FLAG_SMALL_FP64):
         st, S, U, V = _solve(A.clone(), g.RSVD_F32, k, p, q, Om, flags)
-        assert st == g.RSVD_OK
+        # l = 48 > rank 40: after power steps the basis carries 8 directions at rounding level,
+        # which its CholeskyQR removes and refills (reported as a warning)
+        assert st in (g.RSVD_OK, g.RSVD_WARN_RANK_DEFICIENT)
         err = (S.cpu() - sig).abs().max().item()
         assert err <= 1e-5, (flags, err)
         A32 = A.double()
