@@ -391,6 +391,15 @@ cudaError_t tc_gemm_tn(int64_t rows, int ncols, int N, const float *A, int64_t l
                        int chk_l = 0, double chk_tol = 0.0, int col0 = 0, const float *Qth = nullptr,
                        const float *Qtl = nullptr, int64_t ldqt = 0);
 int64_t tc_gemm_tn_partials(int64_t rows, int ncols, int N);
+// C (N x N, ldc) = X^T X for a basis X (rows x N, ldx; N in {16, 32, 48, 64}; X and ldx*4
+// 16-byte aligned): one pass over X, each 32-row stage split once into tf32 hi / lo and
+// transposed into one tile [X_hi^T; X_lo^T] whose product with itself (one 128 x 128 MMA
+// per K slice) carries the three products of the 3xTF32 sum; per-CTA partials in `part`
+// (tc_gram_partials elements), summed in chunk order.  chk / chk_l / chk_tol as tc_gemm_tn.
+cudaError_t tc_gram(int64_t rows, int N, const float *X, int64_t ldx, float *C, int64_t ldc, float *part,
+                    int64_t part_elems, int *status, cudaStream_t s, int *chk = nullptr, int chk_l = 0,
+                    double chk_tol = 0.0);
+int64_t tc_gram_partials(int64_t rows, int N);
 
 // ------------------------------------------------------ block Krylov (Sec. 3.1.1)
 // B ((jl + l) x lp, ld lp): rows below jl negated in place (they hold C = H^T Y),

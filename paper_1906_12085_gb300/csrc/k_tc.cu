@@ -819,6 +819,197 @@ __global__ void __launch_bounds__(NTHR, 1)
     if (threadIdx.x == 0 && bar->abort_flag) atomicOr(status, (int)ST_TIMEOUT);
 }
 
+// ======================================================================= Gram, N <= 64
+// G (N x N) = X^T X for a basis X (rows x N, N <= 64, row-major ld = N) in one pass over X:
+// each 32-row stage of X is split once into tf32 hi / lo and written transposed into one
+// K-major tile T = [X_hi^T; X_lo^T] (rows 0..63 hi, 64..127 lo; rows >= N of each half
+// unused), and a single MMA of shape 128 x 128 x 8 per K slice computes T T^T, whose
+// blocks are hi hi^T, hi lo^T, lo hi^T (lo lo^T, below float32 resolution, is discarded):
+// 4 MMAs per stage with both operands in shared memory.  Each CTA reduces one chunk of
+// rows; the epilogue adds the three blocks (the lo-hi block reaches the hi rows' threads
+// through shared memory) and writes the chunk's partial Gram matrix.
+constexpr uint32_t GR_TS = 128 * 128;   // bytes of one T tile (128 rows x 32 fp32, swizzled)
+constexpr int GR_SR = 8, GR_ST = 4;
+
+template <int N>
+struct GramCfg {
+    static constexpr uint32_t RAW = 32 * N * 4;
+    static constexpr uint32_t SMEM = GR_ST * GR_TS + GR_SR * RAW + 64 * 65 * 4 + 1024 + sizeof(Bars<GR_SR + GR_ST>) + 64;
+};
+
+template <int N>
+__global__ void __launch_bounds__(NTHR, 1)
+    tc_gram_kernel(const __grid_constant__ CUtensorMap tmX, int64_t rows, int64_t rpc, float *__restrict__ part,
+                   int *__restrict__ status) {
+    static_assert(N <= 64 && N % 16 == 0, "Gram kernel: N <= 64");
+    using C = GramCfg<N>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *sT = base;                                  // GR_ST T tiles (1024-aligned)
+    uint8_t *sRaw = sT + GR_ST * GR_TS;                  // GR_SR raw stages (32 x N, unswizzled)
+    float *xch = reinterpret_cast<float *>(sRaw + GR_SR * C::RAW);  // xch[i][j] = lo_i . hi_j, rows of 65
+    // barriers: full[0..SR) raw landed, empty[0..SR) raw read, split[0..ST) T written,
+    // empty[SR..SR+ST) T consumed by the MMAs, tempty[0] xch written, tempty[1] xch read
+    Bars<GR_SR + GR_ST> *bar = reinterpret_cast<Bars<GR_SR + GR_ST> *>(xch + 64 * 65);
+    volatile int *abort_flag = &bar->abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t r0 = (int64_t)blockIdx.x * rpc;
+    const int64_t r1 = r0 + rpc < rows ? r0 + rpc : rows;
+    const int nkb = r1 > r0 ? (int)((r1 - r0 + TBK - 1) / TBK) : 0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < GR_SR; s++) {
+            mbar_init(&bar->full[s], 1);
+            mbar_init(&bar->empty[s], NSPLIT);
+        }
+        for (int s = 0; s < GR_ST; s++) {
+            mbar_init(&bar->split[s], NSPLIT);
+            mbar_init(&bar->empty[GR_SR + s], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&bar->acc_full[b], 1);
+            mbar_init(&bar->acc_empty[b], NEPI);
+        }
+        mbar_init(&bar->tempty[0], NEPI / 2);
+        mbar_init(&bar->tempty[1], NEPI / 2);
+        bar->abort_flag = 0;
+        mbar_fence_init();
+    }
+    if (warp == 1) tmem_alloc(&bar->tmem, 256);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = bar->tmem;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            tma_prefetch_desc(&tmX);
+            bool ok = true;
+            uint32_t g = 0;
+            for (int kb = 0; kb < nkb; kb++, g++) {
+                const int s = g % GR_SR;
+                if (!(ok = wait_ok(&bar->empty[s], ((g / GR_SR) & 1) ^ 1, abort_flag))) break;
+                mbar_arrive_expect_tx(&bar->full[s], C::RAW);
+                tma_load_2d(sRaw + s * C::RAW, &tmX, 0, (int32_t)(r0 + (int64_t)kb * TBK), &bar->full[s]);
+            }
+            for (uint32_t k = g > (uint32_t)GR_SR ? g - GR_SR : 0; k < g; k++)
+                mbar_wait(&bar->full[k % GR_SR], (k / GR_SR) & 1);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_tf32(128, 128);
+            uint32_t g = 0, it = 0;
+            bool ok = true;
+            for (int k0 = 0; ok && k0 < nkb; k0 += SUBK, it++) {
+                const int k1 = k0 + SUBK < nkb ? k0 + SUBK : nkb;
+                const uint32_t b = it & 1;
+                if (!(ok = wait_ok(&bar->acc_empty[b], ((it >> 1) & 1) ^ 1, abort_flag))) break;
+                tc_fence_after();
+                const uint32_t d = tmem + b * 128;
+                for (int kb = k0; kb < k1; kb++, g++) {
+                    const int st = g % GR_ST;
+                    if (!(ok = wait_ok(&bar->split[st], (g / GR_ST) & 1, abort_flag))) break;
+                    tc_fence_after();
+                    const uint8_t *t = sT + st * GR_TS;
+#pragma unroll
+                    for (int kk = 0; kk < TBK / 8; kk++) {
+                        const uint64_t desc = sdesc_kmajor_sw128(t, kk * 32);
+                        mma_tf32(d, desc, desc, idesc, (kb == k0 && kk == 0) ? 0u : 1u);
+                    }
+                    mma_commit(&bar->empty[GR_SR + st]);
+                }
+                if (ok) mma_commit(&bar->acc_full[b]);
+            }
+        }
+    } else if (warp < EPI_WARP0) {
+        // worker t: column j = t % 64 of X, rows 8 kq .. 8 kq + 7 of the stage (kq = t / 64)
+        const int t = threadIdx.x - 64, j = t & 63, kq = t >> 6;
+        uint32_t g = 0;
+        bool ok = true;
+        for (int kb = 0; kb < nkb; kb++, g++) {
+            const int sr = g % GR_SR, st = g % GR_ST;
+            if (!(ok = wait_ok(&bar->full[sr], (g / GR_SR) & 1, abort_flag))) break;
+            if (!(ok = wait_ok(&bar->empty[GR_SR + st], ((g / GR_ST) & 1) ^ 1, abort_flag))) break;
+            if (j < N) {
+                const float *raw = reinterpret_cast<const float *>(sRaw + sr * C::RAW);
+                const int valid = (int)(r1 - (r0 + (int64_t)kb * TBK));  // rows of this stage in the chunk
+                float x[8];
+#pragma unroll
+                for (int e = 0; e < 8; e++) x[e] = kq * 8 + e < valid ? raw[(kq * 8 + e) * N + j] : 0.f;
+                float4 h0, l0, h1, l1;
+                split4(x, h0, l0);
+                split4(x + 4, h1, l1);
+                uint8_t *tt = sT + st * GR_TS;
+                *reinterpret_cast<float4 *>(tt + kmajor_off(j, 2 * kq)) = h0;
+                *reinterpret_cast<float4 *>(tt + kmajor_off(j, 2 * kq + 1)) = h1;
+                *reinterpret_cast<float4 *>(tt + kmajor_off(64 + j, 2 * kq)) = l0;
+                *reinterpret_cast<float4 *>(tt + kmajor_off(64 + j, 2 * kq + 1)) = l1;
+            }
+            fence_proxy_async_smem();
+            mbar_arrive(&bar->empty[sr]);   // raw stage read
+            mbar_arrive(&bar->split[st]);   // T stage written
+        }
+    } else {
+        // lanes 64..127 (quarters 2, 3) hold the lo rows: their block lo_i . hi_j reaches the
+        // hi rows' threads through xch (guarded by two mbarriers, so every wait is bounded)
+        const int q = warp & 3, i = q * 32 + lane;
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        uint32_t it = 0;
+        bool ok = true;
+        float acc[N];
+        for (int k0 = 0; k0 < nkb; k0 += SUBK, it++) {
+            const uint32_t b = it & 1;
+            if (!(ok = wait_ok(&bar->acc_full[b], (it >> 1) & 1, abort_flag))) break;
+            tc_fence_after();
+            const uint32_t dcol = tmem + b * 128 + lane_base;
+            if (q >= 2) {
+                if (!(ok = wait_ok(&bar->tempty[1], (it & 1) ^ 1, abort_flag))) break;   // xch free
+#pragma unroll
+                for (int c0 = 0; c0 < N; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(dcol + (uint32_t)c0, v);
+#pragma unroll
+                    for (int e = 0; e < 16; e++) xch[(i - 64) * 65 + c0 + e] = v[e];
+                }
+                tc_fence_before();
+                mbar_arrive(&bar->acc_empty[b]);
+                mbar_arrive(&bar->tempty[0]);
+            } else {
+                if (!(ok = wait_ok(&bar->tempty[0], it & 1, abort_flag))) break;       // xch written
+#pragma unroll
+                for (int c0 = 0; c0 < N; c0 += 16) {
+                    float v[16], w[16];
+                    tmem_ld16(dcol + (uint32_t)(64 + c0), w);   // hi_i . lo_j
+#pragma unroll
+                    for (int e = 0; e < 16; e++) w[e] += xch[i * 65 + c0 + e];   // + lo_i . hi_j
+                    tmem_ld16(dcol + (uint32_t)c0, v);          // hi_i . hi_j
+#pragma unroll
+                    for (int e = 0; e < 16; e++) {
+                        const float sm = v[e] + w[e];
+                        acc[c0 + e] = k0 == 0 ? sm : acc[c0 + e] + sm;
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&bar->acc_empty[b]);
+                mbar_arrive(&bar->tempty[1]);
+            }
+        }
+        if (ok && q < 2 && i < N && nkb > 0) {
+            float *dst = part + ((int64_t)blockIdx.x * N + i) * N;
+#pragma unroll
+            for (int jj = 0; jj < N; jj += 4)
+                *reinterpret_cast<float4 *>(dst + jj) = make_float4(acc[jj], acc[jj + 1], acc[jj + 2], acc[jj + 3]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 256);
+    }
+    if (threadIdx.x == 0 && bar->abort_flag) atomicOr(status, (int)ST_TIMEOUT);
+}
+
 // ==================================================================== helpers
 // th / tl (N x ldt) = tf32 split of Z^T, Z rows x cols row-major (ldz); zero beyond.  A 32 x 32
 // tile per CTA goes through shared memory, so both the reads (along j) and the writes (along r)
@@ -970,6 +1161,31 @@ cudaError_t launch_tn2(const CUtensorMap &a, const CUtensorMap &qh, const CUtens
     return cudaGetLastError();
 }
 
+template <int N>
+cudaError_t launch_gram(const CUtensorMap &x, int64_t rows, int64_t rpc, int nchunks, float *part, int *status,
+                        cudaStream_t s) {
+    using C = GramCfg<N>;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(tc_gram_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        attr = true;
+    }
+    tc_gram_kernel<N><<<nchunks, NTHR, C::SMEM, s>>>(x, rows, rpc, part, status);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// Row chunks of the Gram kernel: one per CTA, at most one per SM, 32-row aligned.
+struct GramSplit {
+    int64_t rpc;
+    int chunks;
+};
+GramSplit gram_split(int64_t rows) {
+    const int64_t want = std::min<int64_t>(num_sms(), ceil_div(rows, TBK));
+    const int64_t rpc = round_up(ceil_div(rows, want > 0 ? want : 1), TBK);
+    return {rpc, (int)ceil_div(rows, rpc)};
+}
+
 struct TNSplit {
     int64_t rpc;
     int chunks;
@@ -1065,6 +1281,30 @@ cudaError_t tc_gemm_nn(int64_t m, int n, int N, const float *A, int64_t lda, con
         case 128: return launch_nn<128>(ma, mbh, mbl, m, n, Y, ldy, status, mu, ssq, s, ctas);
     }
     return cudaErrorInvalidValue;
+}
+
+int64_t tc_gram_partials(int64_t rows, int N) { return (int64_t)gram_split(rows).chunks * N * N; }
+
+cudaError_t tc_gram(int64_t rows, int N, const float *X, int64_t ldx, float *C, int64_t ldc, float *part,
+                    int64_t part_elems, int *status, cudaStream_t s, int *chk, int chk_l, double chk_tol) {
+    if (N % 16 || N < 16 || N > 64 || rows < 1) return cudaErrorInvalidValue;
+    const GramSplit sp = gram_split(rows);
+    if (part == nullptr || part_elems < (int64_t)sp.chunks * N * N) return cudaErrorInvalidValue;
+    CUtensorMap mx;
+    if (!make_map(&mx, X, rows, N, ldx, TBK, N, false)) return cudaErrorInvalidValue;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (N) {
+        case 16: e = launch_gram<16>(mx, rows, sp.rpc, sp.chunks, part, status, s); break;
+        case 32: e = launch_gram<32>(mx, rows, sp.rpc, sp.chunks, part, status, s); break;
+        case 48: e = launch_gram<48>(mx, rows, sp.rpc, sp.chunks, part, status, s); break;
+        case 64: e = launch_gram<64>(mx, rows, sp.rpc, sp.chunks, part, status, s); break;
+    }
+    if (e != cudaSuccess) return e;
+    const int64_t total = (int64_t)N * N;
+    sum_chunks_kernel<<<(unsigned)ceil_div(total, 32), 256, 0, s>>>(part, sp.chunks, N, N, C, ldc, chk, chk_l, 0,
+                                                                     (float)chk_tol);
+    note_launch();
+    return cudaGetLastError();
 }
 
 int64_t tc_gemm_tn_partials(int64_t rows, int ncols, int N) {

@@ -353,6 +353,15 @@ cudaError_t prod_tn(rsvd_plan *P, int64_t rows, int64_t ncols, const T *X, int64
                     bool presplit = false) {
     const double tol = sizeof(T) == 4 ? kOrthTolF32 : kOrthTolF64;
     if constexpr (sizeof(T) == 4) {
+        // the Gram matrix of a basis of at most 64 columns: one split per stage serves both
+        // operands (tc_gram)
+        if (P->tc && X == Q && ldx == ldq && ncols == P->lp && P->lp <= 64 && al16(X, ldx, 4) &&
+            tc_gram_partials(rows, P->lp) <= P->tcpart_elems) {
+            cudaError_t e = tc_gram(rows, P->lp, X, ldx, C, ldc, P->tcpart, P->tcpart_elems, P->status, P->stream,
+                                    chk_l ? P->status : nullptr, chk_l, tol);
+            if (e != cudaErrorInvalidValue) return e;
+            cudaGetLastError();
+        }
         if (P->tc && al16(X, ldx, 4) && al16(Q, ldq, 4) &&
             tc_gemm_tn_partials(rows, (int)ncols, P->lp) <= P->tcpart_elems) {
             float *qth = nullptr, *qtl = nullptr;
