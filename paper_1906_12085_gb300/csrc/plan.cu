@@ -1449,7 +1449,7 @@ rsvd_status bcqr(BatchCtx &C, int count, rsvd_plan *const *Ps, int which, int pa
             bufs(P, X, Qo, Tmp, rows);
             const T *src = pass == 0 ? X : Tmp;
             T *dst = (pass == passes - 1) ? Qo : Tmp;
-            CK(prod_nn<T>(P, rows, lp, src, lp, (const T *)P->Rinv_c, lp, dst, lp));
+            CK(prod_nn<T>(P, rows, lp, src, lp, (const T *)P->Rinv_c, lp, dst, lp, nullptr, nullptr, true));
             if (sizeof(T) == 4)
                 CK(rinv64_fb({(const float *)src, rows, lp, pass ? P->R2i : P->R1i, (float *)dst, P->fb,
                               want_r ? nullptr : P->dflag, refill_seed(P), passes == 2 ? nullptr : P->dflag + l},
