@@ -148,36 +148,6 @@ __device__ __forceinline__ void store_a(uint32_t tmem, int q, int h, int s, cons
 // float32 additions in a fixed order.
 constexpr int SUBK = 8;
 
-// Epilogue: one TMEM lane quarter of accumulator b -> N floats per row at dst;
-// `add` accumulates into dst (written by the same thread for the previous sub-chunk).
-template <int N>
-__device__ __forceinline__ void drain_acc(uint32_t tmem, uint32_t b, int q, int lane, float *dst, bool valid,
-                                          bool add = false) {
-#pragma unroll
-    for (int c0 = 0; c0 < N; c0 += 32) {
-        float v[32];
-        tmem_ld32(tmem + b * Tm<N>::ACC + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-        if (valid) {
-            float *p = dst + c0;
-            if (c0 + 32 <= N && ((reinterpret_cast<uintptr_t>(p) & 15) == 0)) {
-#pragma unroll
-                for (int j = 0; j < 32; j += 4) {
-                    float4 w = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-                    if (add) {
-                        const float4 o = *reinterpret_cast<const float4 *>(p + j);
-                        w.x += o.x; w.y += o.y; w.z += o.z; w.w += o.w;
-                    }
-                    *reinterpret_cast<float4 *>(p + j) = w;
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < 32; j++)
-                    if (c0 + j < N) p[j] = add ? p[j] + v[j] : v[j];
-            }
-        }
-    }
-}
-
 // Sub-chunk results summed in registers (N floats per epilogue thread; beyond 64 the
 // 128-register budget of these 448-thread kernels spills part of them to local memory)
 // and written once per tile.
