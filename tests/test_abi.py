@@ -144,3 +144,39 @@ def test_autotune_argument_errors():
     g.rsvd_tune_clear()
     assert g.rsvd_tune_lookup(1000, 64, 8, 8)[0] == g.RSVD_ERR_ARG
     assert g.rsvd_tune_lookup(0, 64, 8, 8)[0] == g.RSVD_ERR_ARG
+
+
+def test_sharded_flags_and_sweep_cap_argument_errors():
+    """Entry points of the sharded solve, the plan flags and the sweep cap reject bad
+    arguments before any CUDA call."""
+    L = g.lib()
+    fn = g.allreduce_callback(lambda buf: None)
+    assert L.rsvd_sharded(None, 100, None, None, None, None, None, fn, None) == g.RSVD_ERR_ARG
+    assert L.rsvd_plan_set_flags(None, g.RSVD_FLAG_NO_CENTER) == g.RSVD_ERR_ARG
+    assert g.rsvd_set_jacobi_sweep_cap(-1) == g.RSVD_ERR_ARG
+    assert g.rsvd_set_jacobi_sweep_cap(0) == g.RSVD_OK          # restores the defaults
+    assert g.rsvd_status_string(g.RSVD_ERR_REDUCE) == "the reduction over ranks failed"
+    assert g.rsvd_status_string(g.RSVD_WARN_RANK_DEFICIENT).startswith("numerically rank-deficient")
+    # distinct flag bits, all accepted by the library's mask
+    flags = [g.RSVD_FLAG_NO_CENTER, g.RSVD_FLAG_GKL_TWO_PASS, g.RSVD_FLAG_SMALL_F32, g.RSVD_FLAG_SMALL_FP64]
+    assert len(set(flags)) == 4 and all(f & (f - 1) == 0 for f in flags)
+
+
+def test_allreduce_callback_marshalling():
+    """The reduction callback sees the library's buffer as a float64 array it can change in
+    place, and reports an exception as a non-zero return."""
+    seen = []
+
+    def double_it(buf):
+        seen.append(buf.dtype)
+        buf *= 2.0
+
+    fn = g.allreduce_callback(double_it)
+    arr = (ctypes.c_double * 5)(1, 2, 3, 4, 5)
+    assert fn(ctypes.cast(arr, ctypes.POINTER(ctypes.c_double)), 5, None) == 0
+    assert list(arr) == [2, 4, 6, 8, 10] and str(seen[0]) == "float64"
+
+    def boom(buf):
+        raise RuntimeError("peer gone")
+    bad = g.allreduce_callback(boom)
+    assert bad(ctypes.cast(arr, ctypes.POINTER(ctypes.c_double)), 5, None) == 1
